@@ -1,0 +1,355 @@
+"""Plain, slow, double-precision CPU oracle for GaBP on nonsymmetric systems.
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline / reference leg of ``bench.py`` may import this package.  The
+CUDA library never imports it and shares no code with it.
+
+The per-sweep arithmetic lives in ``gabp_oracle.c`` (plain C loops in the
+paper's notation, eq. nonsymmetric_GaBP_rules); this module compiles and loads
+it and writes out the drivers in the order the paper gives them:
+
+* ``solve``         Algorithm 1 with the flood schedule of Sec. 2.2, stopping
+                    on the infinity-norm residual;
+* ``MGOracle``      geometric V-cycle of Sec. 4 with GaBP as the
+                    error-correction smoother of Algorithm 3, full-weighting
+                    restriction, bilinear prolongation, a direct coarse solve;
+* ``adjoint``       implicit differentiation of x = A^{-1} b (plain definition
+                    via dense solves; the paper has no counterpart).
+
+Messages are stored per CSR slot: the message j -> i lives at the slot of the
+entry (i, j) and holds ``(tilde-Lambda_ji, m_ji)``.
+
+Parity pins for every function are in ``tests/test_oracle_pins.py``; the
+V-cycle composition is pinned only through invariants (fixed point,
+linearity, exact-smoother limit) and the transfer operators through their
+definitions: beyond those, the V-cycle is "parity unpinned".
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import sys
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "gabp_oracle.c")
+_OUT_DIR = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_OUT_DIR, "libgabp_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+OK, BREAKDOWN, DIVERGED, NOT_CONVERGED = 0, 4, 5, 6
+DIVERGENCE_LIMIT = 1e8  # relative residual above which a run counts as diverged
+
+
+def build(force: bool = False) -> str:
+    """Compile the C oracle with gcc (OpenMP when available)."""
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    base = ["gcc", "-O2", "-fPIC", "-shared", "-std=c11", _SRC, "-o", tmp, "-lm"]
+    try:
+        subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True,
+                       capture_output=True)
+    except subprocess.CalledProcessError:
+        subprocess.run(base, check=True, capture_output=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def lib() -> ctypes.CDLL:
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = build()
+            L = ctypes.CDLL(path)
+            i64, i32, dbl = ctypes.c_int64, ctypes.c_int, ctypes.c_double
+            P = ctypes.c_void_p
+            L.oracle_beliefs.argtypes = [i64, P, P, P, P, P, P, P, P]
+            L.oracle_beliefs.restype = None
+            L.oracle_update.argtypes = [i64, P, P, P, P, P, P, P, P]
+            L.oracle_update.restype = i32
+            L.oracle_residual_inf.argtypes = [i64, P, P, P, P, P]
+            L.oracle_residual_inf.restype = dbl
+            L.oracle_residual.argtypes = [i64, P, P, P, P, P, P]
+            L.oracle_residual.restype = None
+            L.oracle_sweeps.argtypes = [i64, P, P, P, P, i32, P, P, P, P, P, P]
+            L.oracle_sweeps.restype = i32
+            L.oracle_set_threads.argtypes = [i32]
+            L.oracle_set_threads.restype = None
+            L.oracle_max_threads.argtypes = []
+            L.oracle_max_threads.restype = i32
+            _lib = L
+    return _lib
+
+
+def set_threads(t: int) -> None:
+    lib().oracle_set_threads(int(t))
+
+
+def max_threads() -> int:
+    return int(lib().oracle_max_threads())
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _mat(A):
+    ip = np.ascontiguousarray(A.indptr, dtype=np.int64)
+    ix = np.ascontiguousarray(A.indices, dtype=np.int32)
+    dv = np.ascontiguousarray(A.data, dtype=np.float64)
+    return ip, ix, dv
+
+
+def zero_state(A):
+    """Zero messages (the initial state of Algorithm 1)."""
+    return np.zeros(A.nnz), np.zeros(A.nnz)
+
+
+def beliefs(A, b, lt, mm):
+    """Beliefs ``mu_i`` and precisions ``beta_i`` (eq. nonsymmetric_GaBP_rules)."""
+    ip, ix, dv = _mat(A)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    mu = np.empty(A.n)
+    beta = np.empty(A.n)
+    lib().oracle_beliefs(A.n, _p(ip), _p(ix), _p(dv), _p(b), _p(lt), _p(mm), _p(mu), _p(beta))
+    return mu, beta
+
+
+def update(A, b, lt, mm):
+    """One flood update of all messages; returns ``(lt_new, mm_new, status)``."""
+    ip, ix, dv = _mat(A)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    lt2 = np.empty(A.nnz)
+    mm2 = np.empty(A.nnz)
+    st = lib().oracle_update(A.n, _p(ip), _p(ix), _p(dv), _p(b), _p(lt), _p(mm), _p(lt2), _p(mm2))
+    return lt2, mm2, int(st)
+
+
+def sweeps(A, b, nsweeps: int, lt: np.ndarray, mm: np.ndarray):
+    """``nsweeps`` sweeps of Algorithm 1 (beliefs, then flood update), in place.
+
+    Returns ``(x, beta, status)``: the beliefs formed in the last sweep.
+    """
+    ip, ix, dv = _mat(A)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    assert lt.dtype == np.float64 and mm.dtype == np.float64
+    x = np.zeros(A.n)
+    beta = np.zeros(A.n)
+    lt2 = np.empty(A.nnz)
+    mm2 = np.empty(A.nnz)
+    st = lib().oracle_sweeps(A.n, _p(ip), _p(ix), _p(dv), _p(b), int(nsweeps), _p(lt), _p(mm),
+                             _p(lt2), _p(mm2), _p(x), _p(beta))
+    return x, beta, int(st)
+
+
+def residual_inf(A, b, x) -> float:
+    ip, ix, dv = _mat(A)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    return float(lib().oracle_residual_inf(A.n, _p(ip), _p(ix), _p(dv), _p(b), _p(x)))
+
+
+def residual(A, b, x) -> np.ndarray:
+    ip, ix, dv = _mat(A)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    r = np.empty(A.n)
+    lib().oracle_residual(A.n, _p(ip), _p(ix), _p(dv), _p(b), _p(x), _p(r))
+    return r
+
+
+def solve(A, b, tol: float, max_iter: int, lt=None, mm=None, history: bool = False):
+    """Algorithm 1 with the flood schedule, from zero messages unless given.
+
+    Every iteration is one sweep (beliefs from the current messages, then the
+    flood update) followed by ``rr = ||b - A x||_inf / ||b||_inf``; the loop
+    stops at ``rr <= tol`` (status OK), a breakdown (zero or non-finite
+    denominator), ``rr`` non-finite or above ``DIVERGENCE_LIMIT`` (DIVERGED),
+    or after ``max_iter`` sweeps (NOT_CONVERGED).
+    """
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    if lt is None or mm is None:
+        lt, mm = zero_state(A)
+    bn = float(np.max(np.abs(b))) if A.n else 0.0
+    hist = []
+    x = np.zeros(A.n)
+    rr = 0.0 if bn == 0.0 else 1.0
+    status = NOT_CONVERGED
+    it = 0
+    if bn == 0.0:
+        return dict(x=x, iters=0, rr=0.0, status=OK, history=hist, lt=lt, mm=mm)
+    while it < max_iter:
+        x, beta, st = sweeps(A, b, 1, lt, mm)
+        it += 1
+        rr = residual_inf(A, b, x) / bn
+        if history:
+            hist.append(rr)
+        if st == BREAKDOWN:
+            status = BREAKDOWN
+            break
+        if rr <= tol:
+            status = OK
+            break
+        if not np.isfinite(rr) or rr > DIVERGENCE_LIMIT:
+            status = DIVERGED
+            break
+    return dict(x=x, iters=it, rr=rr, status=status, history=hist, lt=lt, mm=mm)
+
+
+def dense_solve(A, b) -> np.ndarray:
+    """x = A^{-1} b by LAPACK's LU with partial pivoting (Theorem 1's target)."""
+    return np.linalg.solve(A.to_dense(), np.asarray(b, dtype=np.float64))
+
+
+def diag_contrib(A, lt) -> np.ndarray:
+    """Per-slot diagonal correction ``tilde-Lambda_ji * A_ji`` of the message j -> i.
+
+    This is the quantity the message carries into the precision of node i
+    (eq. nonsymmetric_GaBP_rules, ``beta_i``).
+    """
+    rows = np.repeat(np.arange(A.n), np.diff(A.indptr))
+    cols = A.indices.astype(np.int64)
+    Aji = np.zeros(A.nnz)
+    for p in range(A.nnz):
+        i, j = rows[p], cols[p]
+        if i == j:
+            continue
+        lo, hi = A.indptr[j], A.indptr[j + 1]
+        k = np.searchsorted(A.indices[lo:hi], i)
+        if k < hi - lo and A.indices[lo + k] == i:
+            Aji[p] = A.data[lo + k]
+    return lt * Aji
+
+
+# ---------------------------------------------------------------------------
+# Geometric multigrid (Sec. 4).  Grids have m = 2^J - 1 interior points per
+# side; the coarse point (I, J) coincides with the fine point (2I+1, 2J+1)
+# (0-based).  Values outside the interior are zero (Dirichlet).
+# ---------------------------------------------------------------------------
+
+def restrict_full_weighting(r_f: np.ndarray, m_f: int) -> np.ndarray:
+    """Full weighting, stencil (1/16)[1 2 1; 2 4 2; 1 2 1] (Trottenberg eq. 2.3.3)."""
+    assert (m_f - 1) % 2 == 0
+    R = np.asarray(r_f, dtype=np.float64).reshape(m_f, m_f)
+    c = R[1::2, 1::2]
+    e = R[1::2, 0:-1:2] + R[1::2, 2::2] + R[0:-1:2, 1::2] + R[2::2, 1::2]
+    k = R[0:-1:2, 0:-1:2] + R[0:-1:2, 2::2] + R[2::2, 0:-1:2] + R[2::2, 2::2]
+    return ((4.0 * c + 2.0 * e + k) / 16.0).reshape(-1)
+
+
+def prolong_bilinear(e_c: np.ndarray, m_c: int) -> np.ndarray:
+    """Bilinear interpolation (Trottenberg eq. 2.3.7) from m_c^2 to (2 m_c + 1)^2 points."""
+    m_f = 2 * m_c + 1
+    Ep = np.zeros((m_c + 2, m_c + 2))
+    Ep[1:-1, 1:-1] = np.asarray(e_c, dtype=np.float64).reshape(m_c, m_c)
+    F = np.zeros((m_f, m_f))
+    F[1::2, 1::2] = Ep[1:-1, 1:-1]
+    F[1::2, 0::2] = 0.5 * (Ep[1:-1, :-1] + Ep[1:-1, 1:])
+    F[0::2, 1::2] = 0.5 * (Ep[:-1, 1:-1] + Ep[1:, 1:-1])
+    F[0::2, 0::2] = 0.25 * (Ep[:-1, :-1] + Ep[:-1, 1:] + Ep[1:, :-1] + Ep[1:, 1:])
+    return F.reshape(-1)
+
+
+class MGOracle:
+    """V-cycle with GaBP as the error-correction smoother (Algorithm 3).
+
+    ``levels`` are CSR matrices from fine to coarse on grids of side
+    ``sides[l]``; ``transfer_scale`` multiplies every restricted residual (4
+    for operators whose rows are scaled by h^2).  The coarsest level is
+    solved directly.
+
+    ``mode`` says which messages a smoother call starts from:
+
+    * ``"cold"``  (default) every call runs nu sweeps of Algorithm 1 from zero
+      messages, the operator the paper's LFA analyses (Sec. 4.1);
+    * ``"warm"``  the tilde-Lambda messages of the level persist across calls
+      (they do not depend on the right-hand side, Sec. 2.3), the mean
+      messages restart from zero;
+    * ``"persist"`` both kinds of messages persist across calls.
+    """
+
+    MODES = ("cold", "warm", "persist")
+
+    def __init__(self, levels, sides, transfer_scale: float = 4.0, mode: str = "cold"):
+        assert len(levels) == len(sides) >= 1
+        assert mode in self.MODES
+        self.levels = levels
+        self.sides = list(sides)
+        self.scale = float(transfer_scale)
+        self.mode = mode
+        self.lt = [np.zeros(A.nnz) for A in levels]
+        self.mm = [np.zeros(A.nnz) for A in levels]
+        self.coarse = levels[-1].to_dense()
+
+    def smooth(self, lvl: int, b, x, nu: int):
+        """Algorithm 3: r = b - A x; nu GaBP sweeps on A e = r; x + e."""
+        A = self.levels[lvl]
+        r = residual(A, b, x)
+        if self.mode == "cold":
+            self.lt[lvl][:] = 0.0
+        if self.mode in ("cold", "warm"):
+            self.mm[lvl][:] = 0.0
+        e, _, st = sweeps(A, r, nu, self.lt[lvl], self.mm[lvl])
+        if st != OK:
+            raise FloatingPointError("GaBP breakdown in the smoother")
+        return x + e
+
+    def vcycle(self, b, x, nu_pre: int, nu_post: int, lvl: int = 0):
+        if lvl == len(self.levels) - 1:
+            return np.linalg.solve(self.coarse, b)
+        A = self.levels[lvl]
+        if nu_pre > 0:
+            x = self.smooth(lvl, b, x, nu_pre)
+        r = residual(A, b, x)
+        bc = self.scale * restrict_full_weighting(r, self.sides[lvl])
+        ec = self.vcycle(bc, np.zeros(self.levels[lvl + 1].n), nu_pre, nu_post, lvl + 1)
+        x = x + prolong_bilinear(ec, self.sides[lvl + 1])
+        if nu_post > 0:
+            x = self.smooth(lvl, b, x, nu_post)
+        return x
+
+    def solve(self, b, tol: float, max_cycles: int, nu_pre: int, nu_post: int):
+        A = self.levels[0]
+        b = np.asarray(b, dtype=np.float64)
+        bn = float(np.max(np.abs(b)))
+        x = np.zeros(A.n)
+        hist = []
+        for c in range(1, max_cycles + 1):
+            x = self.vcycle(b, x, nu_pre, nu_post)
+            rr = residual_inf(A, b, x) / bn
+            hist.append(rr)
+            if rr <= tol:
+                return dict(x=x, cycles=c, rr=rr, status=OK, history=hist)
+            if not np.isfinite(rr) or rr > DIVERGENCE_LIMIT:
+                return dict(x=x, cycles=c, rr=rr, status=DIVERGED, history=hist)
+        return dict(x=x, cycles=max_cycles, rr=hist[-1] if hist else 1.0,
+                    status=NOT_CONVERGED, history=hist)
+
+
+# ---------------------------------------------------------------------------
+# Implicit differentiation of x = A^{-1} b (no counterpart in the paper).
+# ---------------------------------------------------------------------------
+
+def adjoint(A, b, g):
+    """Given ``g = dL/dx`` at ``x = A^{-1} b``: ``lam = A^{-T} g = dL/db`` and
+    ``dL/dA_ij = -lam_i x_j`` on every stored entry (i, j).
+
+    Returns ``(x, lam, dA)`` with ``dA`` aligned with ``A.data``.
+    """
+    M = A.to_dense()
+    x = np.linalg.solve(M, np.asarray(b, dtype=np.float64))
+    lam = np.linalg.solve(M.T, np.asarray(g, dtype=np.float64))
+    rows = np.repeat(np.arange(A.n), np.diff(A.indptr))
+    dA = -lam[rows] * x[A.indices]
+    return x, lam, dA
+
+
+if __name__ == "__main__":  # pragma: no cover
+    print(build(force="--force" in sys.argv))

@@ -1,0 +1,421 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: the
+elimination formulas of Sec. 2.1, exactness on trees, the LFA stencils of
+Sec. 4.1, Theorem 1 against LAPACK, brute-force computation trees (App. A),
+the divergent 7x7 example of Sec. 3.4, invariants, and finite differences.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import problems as P
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _slot(A, i, j):
+    lo, hi = A.indptr[i], A.indptr[i + 1]
+    k = np.searchsorted(A.indices[lo:hi], j)
+    assert k < hi - lo and A.indices[lo + k] == j
+    return lo + k
+
+
+# --------------------------------------------------------------------------
+# Sec. 2.1: messages are the Schur-complement corrections of elimination.
+# --------------------------------------------------------------------------
+def test_toy5_matches_elimination_formulas():
+    """Converged messages on the 5-node tree equal eqs. elimination_5 / elimination_3.
+
+    Reading: the paper's elimination_3 writes b_5 - A_53 b_4 / A_44; eliminating
+    x_4 from row 5 uses A_54, which is what is tested.
+    """
+    A = P.paper_toy5_pattern()
+    M = A.to_dense()
+    a = lambda i, j: M[i - 1, j - 1]  # noqa: E731  (1-based as in the paper)
+    b = np.array([0.3, -1.2, 0.7, 2.0, -0.4])
+    bb = lambda i: b[i - 1]  # noqa: E731
+    lt, mm = oracle.zero_state(A)
+    x, beta, st = oracle.sweeps(A, b, 8, lt, mm)  # diameter 3: exact from sweep 4 on
+    assert st == oracle.OK
+    # eq. elimination_5: eliminate x1, x2 from row 3, then x3, x4 from row 5
+    A33t = a(3, 3) - a(3, 1) * a(1, 3) / a(1, 1) - a(3, 2) * a(2, 3) / a(2, 2)
+    b3t = bb(3) - a(3, 1) * bb(1) / a(1, 1) - a(3, 2) * bb(2) / a(2, 2)
+    beta5 = a(5, 5) - a(5, 3) * a(3, 5) / A33t - a(5, 4) * a(4, 5) / a(4, 4)
+    num5 = bb(5) - a(5, 3) * b3t / A33t - a(5, 4) * bb(4) / a(4, 4)
+    assert beta[4] == pytest.approx(beta5, rel=1e-14)
+    assert x[4] == pytest.approx(num5 / beta5, rel=1e-13)
+    # eq. toy_update_rules, in the tilde-Lambda / m form of Sec. 2.3:
+    # the message 3 -> 5 carries tilde-Lambda_35 = -A_53 / A33t and m_35 = -A_53 b3t / A33t
+    p = _slot(A, 4, 2)  # entry (5, 3)
+    assert lt[p] == pytest.approx(-a(5, 3) / A33t, rel=1e-14)
+    assert mm[p] == pytest.approx(-a(5, 3) * b3t / A33t, rel=1e-13)
+    # eq. elimination_3: eliminate x4 from row 5, then x5, x1, x2 from row 3
+    A55t = a(5, 5) - a(5, 4) * a(4, 5) / a(4, 4)
+    b5t = bb(5) - a(5, 4) * bb(4) / a(4, 4)
+    beta3 = (a(3, 3) - a(3, 5) * a(5, 3) / A55t - a(3, 1) * a(1, 3) / a(1, 1)
+             - a(3, 2) * a(2, 3) / a(2, 2))
+    num3 = (bb(3) - a(3, 1) * bb(1) / a(1, 1) - a(3, 2) * bb(2) / a(2, 2)
+            - a(3, 5) * b5t / A55t)
+    assert beta[2] == pytest.approx(beta3, rel=1e-14)
+    assert x[2] == pytest.approx(num3 / beta3, rel=1e-13)
+    # and the beliefs are the exact solution (GaBP is elimination on a tree)
+    np.testing.assert_allclose(x, np.linalg.solve(M, b), rtol=1e-13)
+
+
+# --------------------------------------------------------------------------
+# Tree exactness (Sec. 2.2): on a path of 64 nodes the beliefs become exact at
+# sweep 64 = diameter + 1, not earlier (belief is formed before the update).
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("kind", ["constant", "random"])
+def test_tree_exact_at_diameter_plus_one(kind):
+    n = 64
+    if kind == "constant":
+        A = P.tridiag(n, 2.0, -1.2, -0.8)
+    else:
+        rng = np.random.default_rng(11)
+        M = np.zeros((n, n))
+        i = np.arange(n)
+        sup = -rng.uniform(0.5, 1.5, n - 1)
+        sub = -rng.uniform(0.5, 1.5, n - 1)
+        M[i[:-1], i[:-1] + 1] = sup
+        M[i[1:], i[1:] - 1] = sub
+        rowsum = np.abs(M).sum(1)
+        M[i, i] = rowsum * 1.0000001 + 1e-3
+        A = P.dense_to_csr(M)
+    b = np.random.default_rng(3).uniform(-1, 1, n)
+    xs = np.linalg.solve(A.to_dense(), b)
+    lt, mm = oracle.zero_state(A)
+    errs = []
+    for _ in range(65):
+        x, beta, st = oracle.sweeps(A, b, 1, lt, mm)
+        errs.append(np.max(np.abs(x - xs)) / np.max(np.abs(xs)))
+    assert errs[62] > 1e-6  # sweep 63: the end messages have not arrived yet
+    assert errs[63] < 1e-12  # sweep 64: exact
+    assert errs[64] < 1e-12
+    # on a tree the precisions are exact too: 1/beta_i = (A^-1)_ii (Sec. 2.2)
+    np.testing.assert_allclose(1.0 / beta, np.diag(np.linalg.inv(A.to_dense())), rtol=1e-12)
+
+
+# --------------------------------------------------------------------------
+# Sec. 4.1: one and two parallel sweeps on the 5-point Laplacian give the
+# stencils S1 = h^2/4 and S2 = h^2/12 [1 4 1] (rows here are times h^2).
+# --------------------------------------------------------------------------
+def test_lfa_stencils_first_two_sweeps():
+    m = 9
+    A = P.convdiff_5pt(m, None, (0.0, 0.0))
+    assert A.to_dense()[40, 40] == 4.0
+    b = np.random.default_rng(5).uniform(-1, 1, m * m)
+    lt, mm = oracle.zero_state(A)
+    x1, _, _ = oracle.sweeps(A, b, 1, lt, mm)
+    np.testing.assert_allclose(x1, b / 4.0, rtol=1e-15)
+    x2, _, _ = oracle.sweeps(A, b, 1, lt, mm)
+    B = b.reshape(m, m)
+    X2 = x2.reshape(m, m)
+    nb = B[:-2, 1:-1] + B[2:, 1:-1] + B[1:-1, :-2] + B[1:-1, 2:]
+    np.testing.assert_allclose(X2[1:-1, 1:-1], (4.0 * B[1:-1, 1:-1] + nb) / 12.0, rtol=1e-14)
+
+
+# --------------------------------------------------------------------------
+# Theorem 1: a fixed point gives exactly A^{-1} b, on loopy, nonsymmetric and
+# structurally nonsymmetric matrices (M-matrices converge by the corollary).
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("n,density,seed,sym", [(8, 0.3, 1, False), (20, 0.15, 2, False),
+                                                 (40, 0.08, 3, False), (30, 0.1, 4, True)])
+def test_fixed_point_equals_dense_solve(n, density, seed, sym):
+    A = P.random_m_matrix(n, density, seed, nonsym_pattern=not sym)
+    Md = A.to_dense()
+    if not sym:
+        assert np.any((Md != 0) & (Md.T == 0)), "want a structurally nonsymmetric case"
+    b = np.random.default_rng(seed + 100).uniform(-1, 1, n)
+    res = oracle.solve(A, b, 1e-15, 5000)
+    assert res["status"] == oracle.OK
+    xs = np.linalg.solve(Md, b)
+    assert np.max(np.abs(res["x"] - xs)) / np.max(np.abs(xs)) < 1e-12
+
+
+# --------------------------------------------------------------------------
+# App. A: after u flood updates, the belief of node i equals the root of the
+# computation tree T_u(x_i) after eliminating all other variables.
+# Built by brute force on the 4x4 pattern of the paper's computation-tree
+# figure and on a random loopy nonsymmetric matrix.
+# --------------------------------------------------------------------------
+def _comp_tree_root(M, b, root, depth):
+    n = M.shape[0]
+    nbrs = [[k for k in range(n) if k != v and M[v, k] != 0.0] for v in range(n)]
+    nodes = [(root, -1, -1)]  # (variable, parent node index, parent variable)
+    frontier = [0]
+    for _ in range(depth):
+        nxt = []
+        for t in frontier:
+            v, _, pv = nodes[t]
+            for k in nbrs[v]:
+                if k == pv:
+                    continue
+                nodes.append((k, t, v))
+                nxt.append(len(nodes) - 1)
+        frontier = nxt
+    T = len(nodes)
+    B = np.zeros((T, T))
+    d = np.zeros(T)
+    for t, (v, par, pv) in enumerate(nodes):
+        B[t, t] = M[v, v]
+        d[t] = b[v]
+        if par >= 0:
+            B[par, t] = M[pv, v]
+            B[t, par] = M[v, pv]
+    return np.linalg.solve(B, d)[0]
+
+
+@pytest.mark.parametrize("case", ["figure", "random"])
+def test_computation_tree_brute_force(case):
+    if case == "figure":
+        M = np.array([[4.0, -1.0, 1.5, 0.0],
+                      [0.0, 5.0, -2.0, 1.0],
+                      [-1.0, 0.5, 6.0, -2.0],
+                      [0.0, 0.0, 0.0, 3.0]])
+    else:
+        rng = np.random.default_rng(9)
+        M = np.where(rng.random((5, 5)) < 0.5, rng.uniform(-1, 1, (5, 5)), 0.0)
+        np.fill_diagonal(M, 4.0 + rng.uniform(0, 1, 5))
+    A = P.dense_to_csr(M)
+    b = np.random.default_rng(2).uniform(-1, 1, M.shape[0])
+    lt, mm = oracle.zero_state(A)
+    for u in range(6):
+        x, _, _ = oracle.sweeps(A, b, 1, lt, mm)  # beliefs after u updates
+        for i in range(M.shape[0]):
+            assert x[i] == pytest.approx(_comp_tree_root(M, b, i, u), rel=1e-12, abs=1e-14)
+
+
+# --------------------------------------------------------------------------
+# Sec. 3.4: the printed 7x7 matrix has rho(|R~|) ~ 1.03 and GaBP diverges.
+# --------------------------------------------------------------------------
+def test_paper_7x7_diverges():
+    M = np.loadtxt(os.path.join(GOLDEN, "paper_7x7.txt"))
+    R = np.abs(M) / np.abs(np.diag(M))[:, None]
+    np.fill_diagonal(R, 0.0)
+    rho = max(abs(np.linalg.eigvals(R)))
+    assert round(rho, 2) == 1.03
+    A = P.dense_to_csr(M)
+    b = np.random.default_rng(1).uniform(-1, 1, 7)
+    res = oracle.solve(A, b, 1e-12, 1000)
+    assert res["status"] == oracle.DIVERGED
+
+
+# --------------------------------------------------------------------------
+# Theorem 2's condition and the M-matrix corollary on the workload matrices.
+# --------------------------------------------------------------------------
+def test_workload_matrices_are_convergent_m_matrices():
+    A, b = P.config_c1()
+    M = A.to_dense()
+    off = M - np.diag(np.diag(M))
+    assert np.all(np.diag(M) > 0) and np.all(off <= 0)
+    R = np.abs(off) / np.diag(M)[:, None]
+    assert max(abs(np.linalg.eigvals(R))) < 1.0
+    res = oracle.solve(A, b, 1e-10, 500)
+    assert res["status"] == oracle.OK
+    xs = np.linalg.solve(M, b)
+    assert np.max(np.abs(res["x"] - xs)) / np.max(np.abs(xs)) < 1e-8
+    # small instances of the other workloads are M-matrices too
+    for Am in [P.convdiff_5pt(15, P.lognormal_field(15, 0.5, np.random.default_rng(0)), (1.9, 0.6)),
+               P.convdiff_9pt_aniso(15, 0.01, (1.9, 0.6))]:
+        Md = Am.to_dense()
+        o = Md - np.diag(np.diag(Md))
+        assert np.all(o <= 0) and np.all(np.diag(Md) > 0)
+        assert np.all(np.diag(Md) >= np.abs(o).sum(1) - 1e-12)
+
+
+# --------------------------------------------------------------------------
+# Invariants: tilde-Lambda ignores b (Sec. 2.3), and the diagonal
+# corrections tilde-Lambda_ji A_ji are the same for A and A^T.
+# --------------------------------------------------------------------------
+def test_lambda_independent_of_b_and_transpose():
+    A = P.random_m_matrix(25, 0.15, 8, nonsym_pattern=True)
+    AT = A.transpose()
+    rng = np.random.default_rng(0)
+    b1, b2 = rng.uniform(-1, 1, 25), rng.uniform(-1, 1, 25)
+    l1, m1 = oracle.zero_state(A)
+    l2, m2 = oracle.zero_state(A)
+    lT, mT = oracle.zero_state(AT)
+    for _ in range(7):
+        oracle.sweeps(A, b1, 1, l1, m1)
+        oracle.sweeps(A, b2, 1, l2, m2)
+        oracle.sweeps(AT, b1, 1, lT, mT)
+        np.testing.assert_array_equal(l1, l2)
+        C = np.zeros((25, 25))
+        CT = np.zeros((25, 25))
+        rows = np.repeat(np.arange(25), np.diff(A.indptr))
+        C[rows, A.indices] = oracle.diag_contrib(A, l1)
+        rowsT = np.repeat(np.arange(25), np.diff(AT.indptr))
+        CT[rowsT, AT.indices] = oracle.diag_contrib(AT, lT)
+        np.testing.assert_allclose(C, CT, rtol=1e-13, atol=1e-15)
+
+
+# --------------------------------------------------------------------------
+# Sec. 5.2, soft: the paper's parallel GaBP needs fewer sweeps than Jacobi on
+# eq. stand_alone (3299 vs 4746).  The exact ratio depends on discretisation
+# details the paper omits; only the ordering is pinned.
+# --------------------------------------------------------------------------
+def test_stand_alone_gabp_fewer_sweeps_than_jacobi():
+    A, rhs, ue = P.stand_alone_e1(63)
+    h = 1.0 / 64
+    tol = 2e-4 * h * h  # ||r||_inf <= 2e-4 on the unscaled difference equations
+    res = oracle.solve(A, rhs, tol / np.max(np.abs(rhs)), 20000)
+    assert res["status"] == oracle.OK
+    dense = A.to_dense()
+    D = np.diag(dense)
+    x = np.zeros(A.n)
+    k = 0
+    while np.max(np.abs(rhs - dense @ x)) > tol:
+        x = x + (rhs - dense @ x) / D
+        k += 1
+    assert res["iters"] < k
+    assert np.max(np.abs(res["x"] - ue)) < 1e-3  # discretisation error level
+
+
+# --------------------------------------------------------------------------
+# Multigrid transfer operators (Sec. 4, Trottenberg eqs. 2.3.3 / 2.3.7).
+# --------------------------------------------------------------------------
+def test_transfer_operators():
+    mc = 7
+    mf = 2 * mc + 1
+    # prolongation of a coarse unit vector is the bilinear hat function
+    e = np.zeros(mc * mc)
+    e[3 + mc * 2] = 1.0
+    F = oracle.prolong_bilinear(e, mc).reshape(mf, mf)
+    cy, cx = 2 * 2 + 1, 2 * 3 + 1
+    hat = np.zeros((mf, mf))
+    for dy in (-1, 0, 1):
+        for dx in (-1, 0, 1):
+            hat[cy + dy, cx + dx] = (1 - abs(dx) / 2) * (1 - abs(dy) / 2)
+    np.testing.assert_array_equal(F, hat)
+    # full weighting is a quarter of the transposed bilinear prolongation
+    rng = np.random.default_rng(1)
+    r = rng.normal(size=mf * mf)
+    v = rng.normal(size=mc * mc)
+    lhs = 4.0 * oracle.restrict_full_weighting(r, mf) @ v
+    rhs = r @ oracle.prolong_bilinear(v, mc)
+    assert lhs == pytest.approx(rhs, rel=1e-13)
+    # a constant fine field restricts to the same constant
+    np.testing.assert_allclose(oracle.restrict_full_weighting(np.full(mf * mf, 2.5), mf), 2.5)
+    # linear fields are reproduced where the interpolation does not touch the boundary
+    xs = np.arange(1, mc + 1) * 2.0  # coarse point I sits at fine position 2I+1 (1-based 2I+2)
+    Xc, Yc = np.meshgrid(xs, xs)
+    lin_c = 0.3 * Xc - 0.7 * Yc + 1.0
+    Ff = oracle.prolong_bilinear(lin_c.reshape(-1), mc).reshape(mf, mf)
+    xf = np.arange(1, mf + 1).astype(float)
+    Xf, Yf = np.meshgrid(xf, xf)
+    lin_f = 0.3 * Xf - 0.7 * Yf + 1.0
+    np.testing.assert_allclose(Ff[1:-1, 1:-1], lin_f[1:-1, 1:-1], rtol=1e-14)
+
+
+# --------------------------------------------------------------------------
+# V-cycle invariants: exact solution is a fixed point; affine-linear in
+# (x, b) at fixed tilde-Lambda; converged smoother gives the exact solution;
+# with no smoothing it is the plain coarse-grid correction.
+# --------------------------------------------------------------------------
+def _small_hierarchy():
+    levels, sides, b = P.config_c3_levels(m_fine=31, m_coarse=7, seed=5)
+    return levels, sides, b
+
+
+@pytest.mark.parametrize("mode", ["cold", "warm"])
+def test_vcycle_invariants(mode):
+    levels, sides, b = _small_hierarchy()
+    A = levels[0]
+    xs = np.linalg.solve(A.to_dense(), b)
+    mg = oracle.MGOracle(levels, sides, mode=mode)
+    x1 = mg.vcycle(b, xs.copy(), 2, 2)
+    np.testing.assert_allclose(x1, xs, rtol=0, atol=1e-12 * np.max(np.abs(xs)))
+    # affine-linear in (x, b) at a fixed tilde-Lambda state: warm the messages first
+    mg.vcycle(b, np.zeros(A.n), 2, 2)
+    rng = np.random.default_rng(0)
+    xa, xb = rng.normal(size=A.n), rng.normal(size=A.n)
+    ba, bb = rng.normal(size=A.n), rng.normal(size=A.n)
+    import copy
+    m1, m2, m3 = copy.deepcopy(mg), copy.deepcopy(mg), copy.deepcopy(mg)
+    va = m1.vcycle(ba, xa, 2, 2)
+    vb = m2.vcycle(bb, xb, 2, 2)
+    vab = m3.vcycle(2.0 * ba - 0.5 * bb, 2.0 * xa - 0.5 * xb, 2, 2)
+    np.testing.assert_allclose(vab, 2.0 * va - 0.5 * vb, rtol=1e-10,
+                               atol=1e-12 * np.max(np.abs(vab)))
+    # no smoothing: x + P A_c^{-1} (4 R (b - A x)) for a two-level hierarchy
+    two = oracle.MGOracle(levels[:2], sides[:2], mode=mode)
+    x0 = rng.normal(size=A.n)
+    r = b - A.to_dense() @ x0
+    ec = np.linalg.solve(levels[1].to_dense(), 4.0 * oracle.restrict_full_weighting(r, sides[0]))
+    ref = x0 + oracle.prolong_bilinear(ec, sides[1])
+    np.testing.assert_allclose(two.vcycle(b, x0, 0, 0), ref, rtol=1e-12,
+                               atol=1e-13 * np.max(np.abs(ref)))
+
+
+def test_vcycle_cold_smoother_is_lfa_operator():
+    """A cold smoother call with nu = 1 is x + D^{-1}(b - A x) (S1 of Sec. 4.1)."""
+    levels, sides, b = _small_hierarchy()
+    A = levels[0]
+    mg = oracle.MGOracle(levels, sides, mode="cold")
+    x0 = np.random.default_rng(3).normal(size=A.n)
+    d = np.diag(A.to_dense())
+    np.testing.assert_allclose(mg.smooth(0, b, x0, 1), x0 + (b - A.to_dense() @ x0) / d,
+                               rtol=1e-13, atol=1e-14)
+
+
+def test_vcycle_converged_smoother_is_exact():
+    levels, sides, b = P.config_c3_levels(m_fine=15, m_coarse=7, seed=6)
+    mg = oracle.MGOracle(levels, sides)
+    x = mg.vcycle(b, np.zeros(levels[0].n), 1500, 0)
+    xs = np.linalg.solve(levels[0].to_dense(), b)
+    assert np.max(np.abs(x - xs)) / np.max(np.abs(xs)) < 1e-10
+
+
+def test_vcycle_cold_converges():
+    levels, sides, b = _small_hierarchy()
+    mg = oracle.MGOracle(levels, sides, mode="cold")
+    res = mg.solve(b, 1e-10, 200, 3, 3)
+    assert res["status"] == oracle.OK
+    h = res["history"]
+    assert h[-1] < 1e-10 and h[1] < h[0]
+
+
+def test_laplacian_lambda_fixed_point():
+    """Interior tilde-Lambda A on the 5-point Laplacian tends to the stable root
+    -1/3 of L = -1 / (4 + 3 L) (flood fixed point on the infinite lattice)."""
+    m = 61
+    A = P.convdiff_5pt(m, None, (0.0, 0.0))
+    b = np.zeros(A.n)
+    lt, mm = oracle.zero_state(A)
+    oracle.sweeps(A, b, 400, lt, mm)
+    C = oracle.diag_contrib(A, lt)
+    c = m // 2 + m * (m // 2)
+    lo, hi = A.indptr[c], A.indptr[c + 1]
+    vals = [C[p] for p in range(lo, hi) if A.indices[p] != c]
+    np.testing.assert_allclose(vals, -1.0 / 3.0, rtol=1e-3)
+
+
+# --------------------------------------------------------------------------
+# Adjoint: central finite differences of L = ||x - t||^2 through dense solves.
+# --------------------------------------------------------------------------
+def test_adjoint_against_finite_differences():
+    A = P.random_m_matrix(12, 0.25, 21, nonsym_pattern=True)
+    rng = np.random.default_rng(4)
+    b = rng.uniform(-1, 1, 12)
+    t = rng.uniform(-1, 1, 12)
+    M = A.to_dense()
+    loss = lambda Mx, bx: float(np.sum((np.linalg.solve(Mx, bx) - t) ** 2))  # noqa: E731
+    x = np.linalg.solve(M, b)
+    x_, lam, dA = oracle.adjoint(A, b, 2.0 * (x - t))
+    step = 1e-6
+    for i in range(12):
+        e = np.zeros(12)
+        e[i] = step
+        fd = (loss(M, b + e) - loss(M, b - e)) / (2 * step)
+        assert lam[i] == pytest.approx(fd, rel=1e-6, abs=1e-9)
+    rows = np.repeat(np.arange(12), np.diff(A.indptr))
+    for p in range(0, A.nnz, 3):
+        E = np.zeros_like(M)
+        E[rows[p], A.indices[p]] = step
+        fd = (loss(M + E, b) - loss(M - E, b)) / (2 * step)
+        assert dA[p] == pytest.approx(fd, rel=1e-6, abs=1e-9)
