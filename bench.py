@@ -1,0 +1,377 @@
+#!/usr/bin/env python3
+"""GaBP bench: directed-edge updates/s and time to a 1e-10 residual, mixed vs FP64.
+
+Workload (one GPU): the 2048 x 2048 convection-diffusion system (n = 4,194,304
+unknowns, 20,963,328 stored entries, 16,769,024 directed edges), 5-point
+first-order upwind, log-normal(0, 0.5^2) diffusion per node, flow angle 0.3,
+cell Peclet 1.0, b ~ U[-1, 1] (seed 1002), all synthetic.
+
+One step = one plain FP64 GaBP solve from zero messages to a relative
+residual ||b - A x||_inf / ||b||_inf <= 1e-10 (Algorithm 1, flood schedule).
+``value`` = directed-edge updates per second of that solve (edges x sweeps /
+time).  The same step is also timed for the mixed-precision solver (float
+messages inside double iterative refinement) and reported as
+``time_to_1e-10``.  The device state (~1.1 GB of messages and coefficients)
+is far larger than L2, so no flush is needed between steps.
+
+``--impl reference`` times the CPU oracle (plain FP64 C, OpenMP over rows) on
+the host cores on a bounded sample of the same workload.
+
+Under torchrun with N > 1 every rank solves its own replica (the solve needs
+no exchange between ranks: "replicas only"); ``value`` sums the ranks' work
+over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+TOL = 1e-10
+MAX_ITER = 200000
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--m", type=int, default=2048, help="grid side of the workload")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU sample")
+    return ap.parse_args()
+
+
+def dist_info():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ["index", "clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
+              "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+              "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, gpu_index: str | None):
+        self.gpu = gpu_index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        cmd = ["nvidia-smi", "--query-gpu=" + ",".join(self.FIELDS), "--format=csv,noheader,nounits",
+               "-lms", "200"]
+        if self.gpu is not None:
+            cmd += ["-i", self.gpu]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == len(self.FIELDS):
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=5)
+        return self.summary()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no nvidia-smi samples"]}
+        sm = []
+        smax = []
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        sm.sort()
+        med = sm[len(sm) // 2] if sm else None
+        return {"sm_mhz": med, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def gpu_index_for(local_rank: int):
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        ids = [v.strip() for v in vis.split(",") if v.strip()]
+        if local_rank < len(ids):
+            return ids[local_rank]
+    return str(local_rank)
+
+
+def cpu_oracle_rate(A, b, budget_s: float):
+    """Edge updates/s of the FP64 CPU oracle on the full matrix, bounded sample."""
+    import oracle
+    threads = os.cpu_count() or 1
+    oracle.set_threads(threads)
+    lt, mm = oracle.zero_state(A)
+    t0 = time.perf_counter()
+    oracle.sweeps(A, b, 1, lt, mm)
+    one = time.perf_counter() - t0
+    k = max(1, min(50, int(budget_s / max(one, 1e-6))))
+    t0 = time.perf_counter()
+    oracle.sweeps(A, b, k, lt, mm)
+    dt = time.perf_counter() - t0
+    edges = int(A.offdiag_count())
+    return edges * k / dt, k, dt, threads
+
+
+def run_reference(args):
+    world, rank, _ = dist_info()
+    if rank != 0:
+        return 0
+    import problems as P
+    A, b = P.config_c2(m=args.m)
+    edges = int(A.offdiag_count())
+    import oracle
+    threads = os.cpu_count() or 1
+    oracle.set_threads(threads)
+    lt, mm = oracle.zero_state(A)
+    t0 = time.perf_counter()
+    oracle.sweeps(A, b, 1, lt, mm)
+    one = time.perf_counter() - t0
+    # each step: a bounded sample of sweeps so the whole run ends within minutes
+    total_budget = 150.0
+    per_step = max(1, int(total_budget / max(1, args.steps + args.warmup) / max(one, 1e-6)))
+    per_step = min(per_step, 20)
+    for _ in range(args.warmup):
+        oracle.sweeps(A, b, per_step, lt, mm)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.sweeps(A, b, per_step, lt, mm)
+        times.append(time.perf_counter() - t0)
+    ms = 1e3 * sum(times) / len(times)
+    value = edges * per_step / (ms / 1e3)
+    sample = f"{per_step} FP64 oracle sweeps of the {args.m}x{args.m} system per step"
+    line = {
+        "impl": "reference", "metric": "GaBP directed-edge updates/s (FP64 solve to 1e-10)",
+        "value": value, "unit": "edge-updates/s", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"convdiff2d_5pt_upwind_lognormal_{args.m}x{args.m}", "m": args.m,
+                   "n": A.n, "nnz": A.nnz, "edges": edges, "tol": TOL},
+        "cpu_baseline": {"value": value, "unit": "edge-updates/s", "cores": threads, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "edge-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    world, rank, local = dist_info()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import paper_1904_04093_gb300 as g
+    import problems as P
+
+    g.load()
+    A, b = P.config_c2(m=args.m)
+    n = A.n
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    s64 = g.GabpSolver(A, "fp64", check_every=10)
+    sir = g.GabpSolver(A, "fp32_ir", check_every=10, ir_inner_tol=1e-4, ir_inner_max=2000)
+    info = s64.info()
+    info32 = sir.info()
+    edges = int(info["edges"])
+    bd = torch.as_tensor(b, device=dev)
+    x = torch.empty_like(bd)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    def max_over_ranks(v: float) -> float:
+        if world == 1:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+
+    def timed(solver, steps):
+        barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        its = []
+        for _ in range(steps):
+            _, it, rr, st = solver.solve(bd, TOL, MAX_ITER, x)
+            if st != g.OK:
+                raise RuntimeError(f"solve did not converge: status {st} rr {rr}")
+            its.append(it)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        return e0.elapsed_time(e1) / steps, its
+
+    # warm-up (graphs captured, clocks up)
+    for _ in range(max(3, args.warmup)):
+        s64.solve(bd, TOL, MAX_ITER, x)
+        sir.solve(bd, TOL, MAX_ITER, x)
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(gpu_index_for(local)) if rank == 0 else None
+    if sampler:
+        sampler.start()
+        time.sleep(0.4)
+    launches0 = g.launch_count()
+    ms64, its64 = timed(s64, args.steps)
+    launches = g.launch_count() - launches0
+    ms_ir, its_ir = timed(sir, args.steps)
+    # dominant kernel: the FP64 message sweep, timed alone on the solver's stream
+    nsw = 50
+    sweep_ms64 = s64.time_sweeps(bd, nsw) / nsw
+    sweep_ms32 = sir.time_sweeps(bd, nsw) / nsw
+    clocks = sampler.stop() if sampler else None
+
+    # end to end through the C ABI with host buffers (copies inside the timed region)
+    b_host = torch.as_tensor(b).pin_memory()
+    x_host = torch.empty(n, dtype=torch.float64).pin_memory()
+    barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        bd.copy_(b_host, non_blocking=True)
+        _, it_e2e, _, st = s64.solve(bd, TOL, MAX_ITER, x)
+        x_host.copy_(x, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms_e2e = e0.elapsed_time(e1) / args.steps
+
+    ms64_max = max_over_ranks(ms64)
+    ms_ir_max = max_over_ranks(ms_ir)
+    ms_e2e_max = max_over_ranks(ms_e2e)
+    sweeps64 = its64[-1]
+    value = world * edges * sweeps64 / (ms64_max / 1e3)
+    e2e_value = world * edges * it_e2e / (ms_e2e_max / 1e3)
+    peak, peak_kind = measured_peaks()
+    ach64 = info["sweep_bytes"] / (sweep_ms64 / 1e3) / 1e9
+    ach32 = info32["sweep_bytes"] / (sweep_ms32 / 1e3) / 1e9
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return 0
+
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        rate, k, dt, threads = cpu_oracle_rate(A, b, args.cpu_seconds)
+        cpu = {"value": rate, "unit": "edge-updates/s", "cores": threads, "kind": "oracle",
+               "sample": f"{k} FP64 oracle sweeps of the full {args.m}x{args.m} system "
+                         f"({dt:.1f} s); time to 1e-10 at {sweeps64} sweeps extrapolates to "
+                         f"{sweeps64 * dt / k:.1f} s"}
+
+    line = {
+        "metric": "GaBP directed-edge updates/s (FP64 solve to 1e-10)",
+        "value": value,
+        "unit": "edge-updates/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": max(3, args.warmup),
+        "ms_per_step": ms64_max,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {
+            "workload": f"convdiff2d_5pt_upwind_lognormal_{args.m}x{args.m}",
+            "m": args.m, "n": n, "nnz": A.nnz, "edges": edges, "tol": TOL,
+            "layout": info["layout"], "check_every": 10,
+            "l2": "inputs larger than L2 (message state and coefficients ~%.2f GB)" % (info["device_bytes"] / 1e9),
+            "parallelism": "replicas" if world > 1 else "single",
+        },
+        "time_to_1e-10": {
+            "fp64_ms": ms64_max, "fp64_sweeps": sweeps64,
+            "mixed_ms": ms_ir_max, "mixed_float_sweeps": its_ir[-1],
+            "mixed_speedup": ms64_max / ms_ir_max,
+        },
+        "roofline": {
+            "kernel": "k_sweep_stencil<double,4> (message sweep)",
+            "bound": "hbm", "achieved": ach64, "peak": peak, "unit": "GB/s",
+            "frac": ach64 / peak, "traffic": None,
+            "bytes_per_launch": info["sweep_bytes"], "launch_ms": sweep_ms64,
+            "peak_source": f"{peak_kind} hbm_gbs",
+        },
+        "roofline_fp32_sweep": {
+            "kernel": "k_sweep_stencil<float,4> (message sweep, mixed solver)",
+            "bound": "hbm", "achieved": ach32, "peak": peak, "unit": "GB/s", "frac": ach32 / peak,
+            "bytes_per_launch": info32["sweep_bytes"], "launch_ms": sweep_ms32,
+        },
+        "e2e": {"value": e2e_value, "unit": "edge-updates/s", "h2d_bytes_per_step": n * 8,
+                "d2h_bytes_per_step": n * 8, "ms_per_step": ms_e2e_max},
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

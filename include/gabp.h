@@ -1,0 +1,257 @@
+/*
+ * gabp.h -- C ABI of the GB300 Gaussian belief propagation (GaBP) library for
+ * sparse nonsymmetric systems A x = b.
+ *
+ * The method: each directed edge j -> i of the graph of A (the edge exists iff
+ * A_ij != 0, Sec. 2.3) carries a precision message tilde-Lambda_ji and a mean
+ * message m_ji (eq. nonsymmetric_GaBP_messages).  One flood sweep (Sec. 2.2)
+ * first forms the beliefs
+ *     x_i = (b_i + sum_j m_ji) / (A_ii + sum_j tilde-Lambda_ji A_ji)
+ * from the current messages and then replaces every message at once by
+ *     tilde-Lambda_ji = -A_ij / (A_jj + sum_{k in N(j)\i} tilde-Lambda_kj A_kj)
+ *     m_ji            =  tilde-Lambda_ji (b_j + sum_{k in N(j)\i} m_kj)
+ * (eq. nonsymmetric_GaBP_rules; the belief-before-update order of
+ * Algorithm 1).  Solves stop on ||b - A x||_inf / ||b||_inf (Algorithm 1).
+ *
+ * Conventions shared by every entry point:
+ *  - Matrices are square CSR: int64 row pointers (n+1), int32 column indices
+ *    sorted strictly ascending in each row, double values, the diagonal
+ *    stored and non-zero.  Matrix arrays passed to a setup call are HOST
+ *    arrays; the library copies them and the caller keeps ownership.
+ *  - Vectors (b, x, g, r, ...) are DEVICE pointers to double unless stated,
+ *    on the device that was current at setup, owned by the caller.  Work is
+ *    enqueued on the context's CUDA stream (the `stream` given at setup, NULL
+ *    = legacy default stream); calls that return a result on the host
+ *    synchronise that stream.
+ *  - Every call returns a gabp_status; nothing aborts.  gabp_last_error()
+ *    returns a message for the last non-OK status of the calling thread.
+ *  - A context is not thread-safe: one host thread at a time per context.
+ *  - Per-slot arrays (messages, gradients) follow the caller's CSR slot order
+ *    (length nnz); slots on the diagonal or holding an explicit zero carry
+ *    no message and read as 0.
+ */
+#ifndef GABP_H
+#define GABP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gabp_ctx gabp_ctx;
+typedef struct mg_ctx mg_ctx;
+typedef struct gabp_batch gabp_batch;
+
+typedef enum {
+    GABP_OK = 0,
+    GABP_E_INVALID_ARG = 1,   /* null pointer, negative size, bad option */
+    GABP_E_BAD_CSR = 2,       /* unsorted / duplicate / out-of-range index, non-finite value */
+    GABP_E_ZERO_DIAG = 3,     /* a diagonal entry missing or zero */
+    GABP_E_BREAKDOWN = 4,     /* a message denominator was zero or not finite */
+    GABP_E_DIVERGED = 5,      /* relative residual not finite or above 1e8 */
+    GABP_E_NOT_CONVERGED = 6, /* iteration cap reached; the outputs hold the last iterate */
+    GABP_E_CUDA = 7,          /* a CUDA runtime call failed (message in gabp_last_error) */
+    GABP_E_OOM = 8            /* device or host allocation failed */
+} gabp_status;
+
+typedef enum {
+    GABP_FP64 = 0,    /* messages, beliefs and residual in double */
+    GABP_FP32 = 1,    /* messages and beliefs in float, residual check in double */
+    GABP_FP32_IR = 2  /* float GaBP inside double iterative refinement (solve only) */
+} gabp_precision;
+
+typedef enum {
+    GABP_LAYOUT_AUTO = 0,    /* stencil layout when the matrix has few distinct diagonals */
+    GABP_LAYOUT_CSR = 1,     /* general layout: symmetrised CSR with a reverse-edge index */
+    GABP_LAYOUT_STENCIL = 2  /* per-diagonal (DIA) layout; GABP_E_INVALID_ARG if > 16 diagonals */
+} gabp_layout;
+
+typedef struct {
+    int precision;       /* gabp_precision */
+    int layout;          /* gabp_layout */
+    int check_every;     /* sweeps between residual checks in gabp_solve (>= 1) */
+    int use_graphs;      /* 1: replay each chunk of sweeps as a captured CUDA graph */
+    int ir_inner_max;    /* GABP_FP32_IR: float sweeps per refinement step, at most */
+    double ir_inner_tol; /* GABP_FP32_IR: inner relative residual that ends a refinement step */
+    int block_size;      /* threads per block of the sweep kernel (0 = tuned default) */
+} gabp_options;
+
+/* Fills `opt` with the defaults: FP64, auto layout, check_every 10, graphs on,
+ * ir_inner_max 400, ir_inner_tol 1e-4, block_size 0. */
+void gabp_default_options(gabp_options *opt);
+
+/* Text for a status code (static storage). */
+const char *gabp_status_str(gabp_status s);
+
+/* Message of the last non-OK status returned on the calling thread ("" if none). */
+const char *gabp_last_error(void);
+
+/* Number of CUDA kernel launches this library has enqueued in the process so
+ * far (a replayed graph counts each kernel it contains). */
+unsigned long long gabp_launch_count(void);
+
+/*
+ * Builds a context for the n x n CSR matrix A (host arrays, copied; Sec. 2.3:
+ * the graph of A).  Validates the matrix, symmetrises its pattern with
+ * explicit zeros (a message over an edge whose matrix entry is zero is zero,
+ * Sec. 2.3), builds the reverse-edge index, the per-edge coefficients and the
+ * device layout, allocates the double-buffered message state on the current
+ * device and zeroes it.  `opt` may be NULL (defaults).  `stream` is a
+ * cudaStream_t (NULL = default stream).  On success *out owns device memory
+ * until gabp_destroy.
+ * Errors: GABP_E_INVALID_ARG, GABP_E_BAD_CSR, GABP_E_ZERO_DIAG, GABP_E_OOM, GABP_E_CUDA.
+ */
+gabp_status gabp_setup(int32_t n, int64_t nnz, const int64_t *indptr, const int32_t *indices,
+                       const double *data, const gabp_options *opt, void *stream,
+                       gabp_ctx **out);
+
+/* Replaces the matrix values on the same pattern (host array `data`, nnz
+ * doubles in the setup slot order) and zeroes the messages.  Used when A
+ * depends on parameters (the differentiable solve). */
+gabp_status gabp_set_values(gabp_ctx *ctx, const double *data);
+
+/* Releases the context and its device memory (NULL is ignored). */
+void gabp_destroy(gabp_ctx *ctx);
+
+/* Sets every message to zero (the initial state of Algorithm 1). */
+gabp_status gabp_reset(gabp_ctx *ctx);
+
+/*
+ * Runs `nsweeps` >= 0 flood sweeps (Sec. 2.2, eq. nonsymmetric_GaBP_rules)
+ * from the current messages with right-hand side b (device, n doubles).  If
+ * x is not NULL it receives the beliefs formed in the last sweep (Algorithm
+ * 1 forms x_j before updating j's messages), so after one sweep from zero
+ * messages x = b / diag(A).  The messages stay in the context for the next
+ * call.  Asynchronous except for the status read at the end (one 16-byte
+ * device-to-host copy); GABP_E_BREAKDOWN if a denominator was zero or not finite.
+ */
+gabp_status gabp_sweep(gabp_ctx *ctx, const double *b, int nsweeps, double *x);
+
+/*
+ * Solves A x = b with GaBP from zero messages (Algorithm 1, flood schedule):
+ * sweeps in chunks of opt.check_every, after each chunk the relative residual
+ * rr = ||b - A x||_inf / ||b||_inf of the last beliefs in double; stops at
+ * rr <= tol (GABP_OK), at `max_iter` sweeps (GABP_E_NOT_CONVERGED), on
+ * GABP_E_BREAKDOWN or GABP_E_DIVERGED.  With GABP_FP32_IR the float solver
+ * runs inside double iterative refinement (x += s e, e from float GaBP on
+ * A e = r / s, s = ||r||_inf; tilde-Lambda messages are reused across
+ * refinement steps since they do not depend on the right-hand side, Sec.
+ * 2.3) and `max_iter` caps the total float sweeps.  x (device, n doubles)
+ * receives the last iterate in every case; iters / relres (host, nullable)
+ * receive the sweeps done and the final rr.  b == 0 gives x = 0, rr = 0.
+ */
+gabp_status gabp_solve(gabp_ctx *ctx, const double *b, double *x, double tol, int max_iter,
+                       int *iters, double *relres);
+
+/*
+ * Solves A^T lam = g the same way (the adjoint solve).  The transpose has the
+ * pattern of A after symmetrisation and the same precision messages (the
+ * diagonal corrections tilde-Lambda_ji A_ji are symmetric in the pair), so
+ * only the mean-message coefficients change.  Arguments as gabp_solve.
+ */
+gabp_status gabp_solve_transpose(gabp_ctx *ctx, const double *g, double *lam, double tol,
+                                  int max_iter, int *iters, double *relres);
+
+/*
+ * Gradient of a loss with respect to the stored entries of A at x = A^{-1} b,
+ * given lam = A^{-T} dL/dx: dA[p] = -lam_i x_j for the slot p of entry (i, j)
+ * (implicit differentiation; no counterpart in the paper).  lam, x: device,
+ * n doubles; dA: device, nnz doubles in setup slot order.
+ */
+gabp_status gabp_edge_grad(gabp_ctx *ctx, const double *lam, const double *x, double *dA);
+
+/*
+ * r = b - A x in double (device vectors; r may be NULL) and, on the host,
+ * rinf = ||r||_inf and binf = ||b||_inf (either may be NULL).  The stopping
+ * quantity of Algorithm 1.
+ */
+gabp_status gabp_residual(gabp_ctx *ctx, const double *b, const double *x, double *r,
+                          double *rinf, double *binf);
+
+/*
+ * Copies the message state out (device arrays in setup slot order, as
+ * double): lam[p] = tilde-Lambda_ji A_ji (the message's correction to the
+ * diagonal of row i) and m[p] = m_ji for the slot p of entry (i, j).  Either
+ * pointer may be NULL.
+ */
+gabp_status gabp_get_state(gabp_ctx *ctx, double *lam, double *m);
+
+/* Loads a message state in the format of gabp_get_state (device arrays). */
+gabp_status gabp_set_state(gabp_ctx *ctx, const double *lam, const double *m);
+
+/* Description of a context (host struct). */
+typedef struct {
+    int32_t n;              /* unknowns */
+    int64_t nnz;            /* stored entries of the setup matrix */
+    int64_t edges;          /* directed edges: off-diagonal entries with A_ij != 0 */
+    int layout;             /* gabp_layout actually used (STENCIL or CSR) */
+    int ndiag;              /* stencil layout: number of off-diagonal diagonals */
+    int precision;          /* gabp_precision */
+    int64_t slots;          /* message slots per buffer (padded edges) */
+    double sweep_bytes;     /* compulsory DRAM bytes of one sweep kernel launch */
+    double residual_bytes;  /* compulsory DRAM bytes of one residual kernel launch */
+    size_t device_bytes;    /* device memory held by the context */
+} gabp_info;
+
+gabp_status gabp_get_info(gabp_ctx *ctx, gabp_info *info);
+
+/*
+ * Times the sweep kernel alone: runs `nsweeps` sweeps exactly like
+ * gabp_sweep, with CUDA events recorded on the context's stream around the
+ * sweep launches only; *ms receives their total device time.  For the
+ * bench's roofline figure.
+ */
+gabp_status gabp_time_sweeps(gabp_ctx *ctx, const double *b, int nsweeps, float *ms);
+
+/* ---------------------------------------------------------------------------
+ * Geometric multigrid with GaBP as the smoother (Sec. 4).
+ * ------------------------------------------------------------------------- */
+
+typedef enum {
+    MG_SMOOTH_COLD = 0,    /* each smoother call: nu sweeps of Algorithm 1 from zero messages */
+    MG_SMOOTH_WARM = 1,    /* tilde-Lambda persists per level across calls, means restart at 0 */
+    MG_SMOOTH_PERSIST = 2  /* both kinds of messages persist across calls */
+} mg_smooth_mode;
+
+/*
+ * Builds a V-cycle over `levels` >= 1 contexts, finest first, on square grids
+ * of side grid_side[l] = 2^J_l - 1 with lexicographic numbering i = ix + m*iy
+ * (Sec. 4: grids with 2^J + 1 points including the boundary; the coarse point
+ * (I, J) is the fine point (2I+1, 2J+1), 0-based).  Consecutive sides must
+ * satisfy m_fine = 2 m_coarse + 1.  `transfer_scale` multiplies every
+ * restricted residual (4 when the rows of every level are scaled by h^2).
+ * The level contexts stay owned by the caller and must outlive the mg
+ * context; their messages are used as the smoother state.  The coarsest
+ * level is solved directly (its inverse is formed once here by LU with
+ * partial pivoting, the paper's coarse solver); it must have at most 4096
+ * unknowns.  `mode` is an mg_smooth_mode.
+ */
+gabp_status mg_setup(int levels, gabp_ctx *const *level_ctx, const int32_t *grid_side,
+                     double transfer_scale, int mode, void *stream, mg_ctx **out);
+
+/*
+ * One V-cycle in place on x (device, fine-level doubles) for right-hand side
+ * b: on each level nu_pre smoothing sweeps as Algorithm 3 (r = b - A x,
+ * nu sweeps of GaBP on A e = r, x += e), residual, full-weighting
+ * restriction (Trottenberg eq. 2.3.3), recursion, bilinear prolongation
+ * (eq. 2.3.7) and correction, nu_post smoothing sweeps; direct solve on the
+ * coarsest level.  `levels` = number of levels to use (0 = all).  Smoothing
+ * runs in the precision of each level context; residuals and transfers in
+ * double.
+ */
+gabp_status mg_vcycle(mg_ctx *mg, int levels, int nu_pre, int nu_post, const double *b,
+                      double *x);
+
+/* V-cycles from x = 0 until ||b - A x||_inf / ||b||_inf <= tol or max_cycles. */
+gabp_status mg_solve(mg_ctx *mg, const double *b, double *x, double tol, int max_cycles,
+                     int nu_pre, int nu_post, int *cycles, double *relres);
+
+void mg_destroy(mg_ctx *mg);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GABP_H */

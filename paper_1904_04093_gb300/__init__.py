@@ -1,0 +1,306 @@
+"""GB300 Gaussian belief propagation (GaBP) for sparse nonsymmetric ``A x = b``.
+
+Python binding over the C ABI of ``libgabp.so`` (declared in
+``include/gabp.h``).  This module only marshals arguments: every step of
+every solve runs in the library's CUDA kernels.  PyTorch supplies device
+memory and streams.  The binding fails loudly when the library is missing;
+there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = [
+    "GabpError", "GabpSolver", "Multigrid", "load", "library_path", "STATUS",
+    "OK", "BREAKDOWN", "DIVERGED", "NOT_CONVERGED",
+]
+
+OK, INVALID_ARG, BAD_CSR, ZERO_DIAG, BREAKDOWN, DIVERGED, NOT_CONVERGED, CUDA_ERR, OOM = range(9)
+STATUS = {0: "ok", 1: "invalid argument", 2: "malformed CSR matrix",
+          3: "missing or zero diagonal entry", 4: "breakdown", 5: "diverged",
+          6: "not converged", 7: "CUDA error", 8: "out of memory"}
+_PREC = {"fp64": 0, "fp32": 1, "fp32_ir": 2}
+_LAYOUT = {"auto": 0, "csr": 1, "stencil": 2}
+_MODE = {"cold": 0, "warm": 1, "persist": 2}
+
+
+class GabpError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("layout", ctypes.c_int),
+                ("check_every", ctypes.c_int), ("use_graphs", ctypes.c_int),
+                ("ir_inner_max", ctypes.c_int), ("ir_inner_tol", ctypes.c_double),
+                ("block_size", ctypes.c_int)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("nnz", ctypes.c_int64), ("edges", ctypes.c_int64),
+                ("layout", ctypes.c_int), ("ndiag", ctypes.c_int), ("precision", ctypes.c_int),
+                ("slots", ctypes.c_int64), ("sweep_bytes", ctypes.c_double),
+                ("residual_bytes", ctypes.c_double), ("device_bytes", ctypes.c_size_t)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load() -> ctypes.CDLL:
+    """Loads ``libgabp.so``; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"GaBP CUDA library not built ({path} missing); "
+                           "run __graft_entry__.build() or python -m paper_1904_04093_gb300.build")
+    L = ctypes.CDLL(path)
+    P, I, I64, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+    PI, PD, PF = ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_float)
+    sigs = {
+        "gabp_default_options": (None, [ctypes.POINTER(Options)]),
+        "gabp_status_str": (ctypes.c_char_p, [I]),
+        "gabp_last_error": (ctypes.c_char_p, []),
+        "gabp_launch_count": (ctypes.c_ulonglong, []),
+        "gabp_setup": (I, [ctypes.c_int32, I64, P, P, P, ctypes.POINTER(Options), P, ctypes.POINTER(P)]),
+        "gabp_set_values": (I, [P, P]),
+        "gabp_destroy": (None, [P]),
+        "gabp_reset": (I, [P]),
+        "gabp_sweep": (I, [P, P, I, P]),
+        "gabp_solve": (I, [P, P, P, D, I, PI, PD]),
+        "gabp_solve_transpose": (I, [P, P, P, D, I, PI, PD]),
+        "gabp_edge_grad": (I, [P, P, P, P]),
+        "gabp_residual": (I, [P, P, P, P, PD, PD]),
+        "gabp_get_state": (I, [P, P, P]),
+        "gabp_set_state": (I, [P, P, P]),
+        "gabp_get_info": (I, [P, ctypes.POINTER(Info)]),
+        "gabp_time_sweeps": (I, [P, P, I, PF]),
+        "mg_setup": (I, [I, ctypes.POINTER(P), ctypes.POINTER(ctypes.c_int32), D, I, P, ctypes.POINTER(P)]),
+        "mg_vcycle": (I, [P, I, I, I, P, P]),
+        "mg_solve": (I, [P, P, P, D, I, I, I, PI, PD]),
+        "mg_destroy": (None, [P]),
+    }
+    for name, (res, args) in sigs.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def launch_count() -> int:
+    """Kernel launches the library has enqueued in this process so far."""
+    return int(load().gabp_launch_count())
+
+
+def _err(st: int) -> GabpError:
+    return GabpError(st, load().gabp_last_error().decode(errors="replace"))
+
+
+def _check(st: int) -> None:
+    if st != OK:
+        raise _err(st)
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _dev_vec(t, n: int, name: str):
+    torch = _torch()
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64
+            and t.is_contiguous() and t.numel() == n):
+        raise ValueError(f"{name} must be a contiguous float64 CUDA tensor of {n} elements")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream_handle(stream):
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream), stream
+
+
+class GabpSolver:
+    """A GaBP context for one sparse matrix (see ``include/gabp.h``).
+
+    ``A`` is any object with ``n``, ``indptr`` (int64), ``indices`` (int32,
+    sorted per row) and ``data`` (float64) arrays, e.g. ``problems.CSR``.
+    """
+
+    def __init__(self, A, precision: str = "fp64", layout: str = "auto", check_every: int = 10,
+                 use_graphs: bool = True, ir_inner_max: int = 400, ir_inner_tol: float = 1e-4,
+                 block_size: int = 0, stream=None):
+        L = load()
+        torch = _torch()
+        self.n = int(A.n)
+        self.indptr = np.ascontiguousarray(A.indptr, dtype=np.int64)
+        self.indices = np.ascontiguousarray(A.indices, dtype=np.int32)
+        data = np.ascontiguousarray(A.data, dtype=np.float64)
+        self.nnz = int(self.indptr[-1]) if self.n else 0
+        opt = Options()
+        L.gabp_default_options(ctypes.byref(opt))
+        opt.precision = _PREC[precision]
+        opt.layout = _LAYOUT[layout]
+        opt.check_every = int(check_every)
+        opt.use_graphs = int(bool(use_graphs))
+        opt.ir_inner_max = int(ir_inner_max)
+        opt.ir_inner_tol = float(ir_inner_tol)
+        opt.block_size = int(block_size)
+        self.precision = precision
+        self.device = torch.cuda.current_device()
+        self._sh, self.stream = _stream_handle(stream)
+        h = ctypes.c_void_p()
+        _check(L.gabp_setup(self.n, self.nnz, self.indptr.ctypes.data, self.indices.ctypes.data,
+                            data.ctypes.data, ctypes.byref(opt), self._sh, ctypes.byref(h)))
+        self._h = h
+
+    # -- lifetime --------------------------------------------------------
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            load().gabp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _vec(self, t=None):
+        torch = _torch()
+        if t is None:
+            t = torch.empty(self.n, dtype=torch.float64, device=f"cuda:{self.device}")
+        return t
+
+    # -- calls -------------------------------------------------------------
+    def info(self) -> dict:
+        inf = Info()
+        _check(load().gabp_get_info(self._h, ctypes.byref(inf)))
+        d = {f: getattr(inf, f) for f, _ in Info._fields_}
+        d["layout"] = {1: "csr", 2: "stencil"}.get(d["layout"], d["layout"])
+        return d
+
+    def reset(self) -> None:
+        _check(load().gabp_reset(self._h))
+
+    def set_values(self, data) -> None:
+        data = np.ascontiguousarray(data, dtype=np.float64)
+        assert data.shape == (self.nnz,)
+        _check(load().gabp_set_values(self._h, data.ctypes.data))
+
+    def sweep(self, b, nsweeps: int, x=None):
+        x = self._vec(x)
+        _check(load().gabp_sweep(self._h, _dev_vec(b, self.n, "b"), int(nsweeps),
+                                 _dev_vec(x, self.n, "x")))
+        return x
+
+    def time_sweeps(self, b, nsweeps: int) -> float:
+        ms = ctypes.c_float()
+        _check(load().gabp_time_sweeps(self._h, _dev_vec(b, self.n, "b"), int(nsweeps),
+                                       ctypes.byref(ms)))
+        return float(ms.value)
+
+    def _solve(self, fn, b, tol, max_iter, x, raise_on):
+        x = self._vec(x)
+        it = ctypes.c_int()
+        rr = ctypes.c_double()
+        st = fn(self._h, _dev_vec(b, self.n, "b"), _dev_vec(x, self.n, "x"), float(tol),
+                int(max_iter), ctypes.byref(it), ctypes.byref(rr))
+        if st not in (OK, NOT_CONVERGED, BREAKDOWN, DIVERGED) or st in raise_on:
+            raise _err(st)
+        return x, int(it.value), float(rr.value), int(st)
+
+    def solve(self, b, tol: float = 1e-10, max_iter: int = 10000, x=None, raise_on=()):
+        """Returns ``(x, sweeps, relres, status)``."""
+        return self._solve(load().gabp_solve, b, tol, max_iter, x, raise_on)
+
+    def solve_transpose(self, g, tol: float = 1e-10, max_iter: int = 10000, lam=None, raise_on=()):
+        return self._solve(load().gabp_solve_transpose, g, tol, max_iter, lam, raise_on)
+
+    def edge_grad(self, lam, x, dA=None):
+        torch = _torch()
+        if dA is None:
+            dA = torch.empty(self.nnz, dtype=torch.float64, device=f"cuda:{self.device}")
+        _check(load().gabp_edge_grad(self._h, _dev_vec(lam, self.n, "lam"),
+                                     _dev_vec(x, self.n, "x"), _dev_vec(dA, self.nnz, "dA")))
+        return dA
+
+    def residual(self, b, x, r=None):
+        """Returns ``(r or None, ||b - A x||_inf, ||b||_inf)``."""
+        rinf, binf = ctypes.c_double(), ctypes.c_double()
+        rp = _dev_vec(r, self.n, "r") if r is not None else None
+        _check(load().gabp_residual(self._h, _dev_vec(b, self.n, "b"), _dev_vec(x, self.n, "x"),
+                                    rp, ctypes.byref(rinf), ctypes.byref(binf)))
+        return r, float(rinf.value), float(binf.value)
+
+    def get_state(self):
+        torch = _torch()
+        lam = torch.empty(self.nnz, dtype=torch.float64, device=f"cuda:{self.device}")
+        m = torch.empty_like(lam)
+        _check(load().gabp_get_state(self._h, _dev_vec(lam, self.nnz, "lam"),
+                                     _dev_vec(m, self.nnz, "m")))
+        return lam, m
+
+    def set_state(self, lam=None, m=None):
+        lp = _dev_vec(lam, self.nnz, "lam") if lam is not None else None
+        mp = _dev_vec(m, self.nnz, "m") if m is not None else None
+        _check(load().gabp_set_state(self._h, lp, mp))
+
+
+class Multigrid:
+    """V-cycle with GaBP smoothing over level solvers, finest first (Sec. 4)."""
+
+    def __init__(self, levels, sides, transfer_scale: float = 4.0, mode: str = "cold",
+                 stream=None):
+        L = load()
+        self.levels = list(levels)
+        self.sides = [int(s) for s in sides]
+        self._sh, self.stream = _stream_handle(stream)
+        arr = (ctypes.c_void_p * len(self.levels))(*[lv._h for lv in self.levels])
+        sides_c = (ctypes.c_int32 * len(self.sides))(*self.sides)
+        h = ctypes.c_void_p()
+        _check(L.mg_setup(len(self.levels), arr, sides_c, float(transfer_scale), _MODE[mode],
+                          self._sh, ctypes.byref(h)))
+        self._h = h
+        self.n = self.levels[0].n
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().mg_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def vcycle(self, b, x, nu_pre: int, nu_post: int, levels: int = 0):
+        _check(load().mg_vcycle(self._h, int(levels), int(nu_pre), int(nu_post),
+                                _dev_vec(b, self.n, "b"), _dev_vec(x, self.n, "x")))
+        return x
+
+    def solve(self, b, tol: float, max_cycles: int, nu_pre: int, nu_post: int, x=None):
+        torch = _torch()
+        if x is None:
+            x = torch.empty(self.n, dtype=torch.float64, device=b.device)
+        c, rr = ctypes.c_int(), ctypes.c_double()
+        st = load().mg_solve(self._h, _dev_vec(b, self.n, "b"), _dev_vec(x, self.n, "x"),
+                             float(tol), int(max_cycles), int(nu_pre), int(nu_post),
+                             ctypes.byref(c), ctypes.byref(rr))
+        if st not in (OK, NOT_CONVERGED, DIVERGED, BREAKDOWN):
+            raise _err(st)
+        return x, int(c.value), float(rr.value), int(st)

@@ -1,0 +1,1095 @@
+// C ABI of the GaBP library: context set-up, solve drivers, multigrid.
+// The declarations and their contracts are in include/gabp.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "gabp_internal.h"
+
+using namespace gabp;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+gabp_status fail(gabp_status s, const std::string &msg)
+{
+    g_last_error = msg;
+    return s;
+}
+
+gabp_status fail_cuda(cudaError_t e, const char *what)
+{
+    g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+    cudaGetLastError();  // clear a non-sticky error
+    return e == cudaErrorMemoryAllocation ? GABP_E_OOM : GABP_E_CUDA;
+}
+
+#define CK(call)                                            \
+    do {                                                    \
+        cudaError_t e_ = (call);                            \
+        if (e_ != cudaSuccess) return fail_cuda(e_, #call); \
+    } while (0)
+
+#define CKS(expr)                            \
+    do {                                     \
+        gabp_status s_ = (expr);             \
+        if (s_ != GABP_OK) return s_;        \
+    } while (0)
+
+constexpr double kDivergence = 1e8;  // relative residual that counts as divergence
+
+double bits_to_double(unsigned long long u)
+{
+    double d;
+    std::memcpy(&d, &u, sizeof d);
+    return d;
+}
+
+struct GraphEntry {
+    int k, parity, transposed;
+    cudaGraphExec_t exec;
+};
+
+}  // namespace
+
+struct gabp_ctx {
+    int dev = 0;
+    cudaStream_t stream = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    gabp_options opt{};
+    int prec = 0;  // message precision: 0 double, 1 float
+    int n = 0;
+    int64_t nnz = 0, edges = 0;
+    DevLayout L{};
+    // host copy of the caller's matrix
+    std::vector<int64_t> h_indptr;
+    std::vector<int32_t> h_indices;
+    std::vector<double> h_data;
+    // device allocations (tracked for cleanup)
+    std::vector<void *> allocs;
+    size_t dev_bytes = 0;
+    // coefficients
+    void *a = nullptr, *c = nullptr, *diagT = nullptr;  // message precision
+    double *a64 = nullptr, *diag64 = nullptr;           // double (residual)
+    void *aT = nullptr;                                 // transposed mean coefficients
+    double *aT64 = nullptr;
+    int64_t *slotmap = nullptr;                         // caller slot -> layout slot (-1: none)
+    int64_t *d_indptr = nullptr;                        // caller CSR on device (edge gradient)
+    int *d_indices = nullptr;
+    // state
+    void *Lm[2] = {nullptr, nullptr}, *Mm[2] = {nullptr, nullptr};
+    void *P[2] = {nullptr, nullptr}, *B[2] = {nullptr, nullptr};
+    int cur = 0;
+    void *bT = nullptr;       // rhs of the sweeps, message precision
+    double *bres = nullptr;   // rhs of the residual checks (double)
+    double *xbuf = nullptr;   // beliefs of the last sweep of a chunk
+    double *b0 = nullptr, *xacc = nullptr, *rbuf = nullptr;  // refinement (lazy)
+    DevStatus *dstat = nullptr;  // [0] chunk checks, [1] refinement / misc
+    DevStatus *hstat = nullptr;  // pinned host mirror
+    std::vector<GraphEntry> graphs;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+struct mg_ctx {
+    int dev = 0;
+    cudaStream_t stream = nullptr;
+    int levels = 0;
+    std::vector<gabp_ctx *> lv;
+    std::vector<int> side;
+    double scale = 4.0;
+    int mode = MG_SMOOTH_COLD;
+    std::vector<double *> b, x;  // per level >= 1
+    double *coarse_inv = nullptr;
+    int nc = 0;
+    DevStatus *dstat = nullptr, *hstat = nullptr;
+    std::vector<void *> allocs;
+    size_t dev_bytes = 0;
+};
+
+namespace {
+
+template <typename Ctx>
+gabp_status dalloc(Ctx *ctx, void **p, size_t bytes)
+{
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) return fail_cuda(e, "cudaMalloc");
+    ctx->allocs.push_back(*p);
+    ctx->dev_bytes += bytes;
+    return GABP_OK;
+}
+
+size_t esz(int prec) { return prec == 0 ? sizeof(double) : sizeof(float); }
+
+gabp_status set_dev(int dev)
+{
+    CK(cudaSetDevice(dev));
+    return GABP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// CSR validation and layout construction (host)
+// ---------------------------------------------------------------------------
+gabp_status validate_csr(int32_t n, int64_t nnz, const int64_t *indptr, const int32_t *indices,
+                         const double *data)
+{
+    if (n < 0 || nnz < 0) return fail(GABP_E_INVALID_ARG, "negative size");
+    if (n > 0 && (!indptr || (nnz > 0 && (!indices || !data))))
+        return fail(GABP_E_INVALID_ARG, "null matrix array");
+    if (n == 0) return GABP_OK;
+    if (indptr[0] != 0 || indptr[n] != nnz) return fail(GABP_E_BAD_CSR, "indptr[0] != 0 or indptr[n] != nnz");
+    for (int32_t r = 0; r < n; ++r) {
+        if (indptr[r + 1] < indptr[r]) return fail(GABP_E_BAD_CSR, "indptr not monotone");
+        bool diag = false;
+        for (int64_t p = indptr[r]; p < indptr[r + 1]; ++p) {
+            const int32_t c = indices[p];
+            if (c < 0 || c >= n) return fail(GABP_E_BAD_CSR, "column index out of range");
+            if (p > indptr[r] && indices[p - 1] >= c)
+                return fail(GABP_E_BAD_CSR, "columns not strictly ascending (unsorted or duplicate)");
+            if (!std::isfinite(data[p])) return fail(GABP_E_BAD_CSR, "non-finite matrix value");
+            if (c == r) {
+                if (data[p] == 0.0) return fail(GABP_E_ZERO_DIAG, "zero diagonal entry in row " + std::to_string(r));
+                diag = true;
+            }
+        }
+        if (!diag) return fail(GABP_E_ZERO_DIAG, "missing diagonal entry in row " + std::to_string(r));
+    }
+    return GABP_OK;
+}
+
+// Host-side coefficient arrays of a layout (double), before upload.
+struct HostLayout {
+    int kind = GABP_LAYOUT_CSR;
+    StencilParams sp{};
+    int64_t slots = 0;
+    std::vector<int> rowptr, col, rev;
+    std::vector<double> a, c, diag;
+    std::vector<int64_t> slotmap;
+};
+
+// Distinct off-diagonal offsets closed under negation; false if more than KMAX.
+bool stencil_offsets(int32_t n, const int64_t *indptr, const int32_t *indices, StencilParams &sp)
+{
+    std::vector<int> absoff;
+    for (int32_t r = 0; r < n; ++r)
+        for (int64_t p = indptr[r]; p < indptr[r + 1]; ++p) {
+            const int o = indices[p] - r;
+            if (o == 0) continue;
+            const int ao = o < 0 ? -o : o;
+            if (std::find(absoff.begin(), absoff.end(), ao) == absoff.end()) {
+                absoff.push_back(ao);
+                if ((int)absoff.size() * 2 > KMAX) return false;
+            }
+        }
+    std::sort(absoff.begin(), absoff.end());
+    const int h = (int)absoff.size();
+    sp.K = 2 * h;
+    for (int i = 0; i < h; ++i) {
+        sp.off[i] = -absoff[h - 1 - i];
+        sp.off[h + i] = absoff[i];
+    }
+    for (int k = 0; k < sp.K; ++k) sp.krev[k] = sp.K - 1 - k;  // off sorted symmetric
+    for (int k = sp.K; k < KMAX; ++k) sp.off[k] = sp.krev[k] = 0;
+    return true;
+}
+
+void build_stencil(int32_t n, const int64_t *indptr, const int32_t *indices, const double *data,
+                   const StencilParams &sp, HostLayout &H)
+{
+    H.kind = GABP_LAYOUT_STENCIL;
+    H.sp = sp;
+    const int K = sp.K;
+    H.slots = (int64_t)K * n;
+    H.a.assign((size_t)H.slots, 0.0);
+    H.c.assign((size_t)H.slots, 0.0);
+    H.diag.assign((size_t)n, 0.0);
+    H.slotmap.assign((size_t)indptr[n], -1);
+    for (int32_t r = 0; r < n; ++r) {
+        int k = 0;
+        for (int64_t p = indptr[r]; p < indptr[r + 1]; ++p) {
+            const int o = indices[p] - r;
+            if (o == 0) {
+                H.diag[r] = data[p];
+                continue;
+            }
+            while (sp.off[k] != o) ++k;  // columns ascend, offsets ascend
+            const int64_t e = (int64_t)k * n + r;
+            H.a[e] = -data[p];
+            H.slotmap[p] = e;
+        }
+    }
+    for (int k = 0; k < K; ++k) {
+        const int o = sp.off[k];
+        const int64_t kr = sp.krev[k];
+        for (int32_t r = 0; r < n; ++r) {
+            const int64_t e = (int64_t)k * n + r;
+            const int64_t s = (int64_t)r + o;
+            if (H.a[e] != 0.0 && s >= 0 && s < n) H.c[e] = -H.a[e] * H.a[kr * n + s];
+        }
+    }
+}
+
+void build_csr(int32_t n, const int64_t *indptr, const int32_t *indices, const double *data,
+               HostLayout &H)
+{
+    H.kind = GABP_LAYOUT_CSR;
+    // symmetrised off-diagonal pattern
+    std::vector<int64_t> cnt((size_t)n + 1, 0);
+    for (int32_t r = 0; r < n; ++r)
+        for (int64_t p = indptr[r]; p < indptr[r + 1]; ++p)
+            if (indices[p] != r) {
+                cnt[r + 1]++;
+                cnt[indices[p] + 1]++;
+            }
+    for (int32_t r = 0; r < n; ++r) cnt[r + 1] += cnt[r];
+    std::vector<int> tmp((size_t)cnt[n]);
+    std::vector<int64_t> fill(cnt.begin(), cnt.end() - 1);
+    for (int32_t r = 0; r < n; ++r)
+        for (int64_t p = indptr[r]; p < indptr[r + 1]; ++p)
+            if (indices[p] != r) {
+                tmp[fill[r]++] = indices[p];
+                tmp[fill[indices[p]]++] = r;
+            }
+    H.rowptr.assign((size_t)n + 1, 0);
+    H.col.clear();
+    H.col.reserve(tmp.size());
+    for (int32_t r = 0; r < n; ++r) {
+        auto b0 = tmp.begin() + cnt[r], b1 = tmp.begin() + cnt[r + 1];
+        std::sort(b0, b1);
+        auto e = std::unique(b0, b1);
+        for (auto it = b0; it != e; ++it) H.col.push_back(*it);
+        H.rowptr[r + 1] = (int)H.col.size();
+    }
+    H.slots = (int64_t)H.col.size();
+    auto find = [&](int r, int s) -> int64_t {
+        auto b0 = H.col.begin() + H.rowptr[r], b1 = H.col.begin() + H.rowptr[r + 1];
+        auto it = std::lower_bound(b0, b1, s);
+        return (it != b1 && *it == s) ? (int64_t)(it - H.col.begin()) : -1;
+    };
+    H.a.assign((size_t)H.slots, 0.0);
+    H.c.assign((size_t)H.slots, 0.0);
+    H.rev.assign((size_t)H.slots, 0);
+    H.diag.assign((size_t)n, 0.0);
+    H.slotmap.assign((size_t)indptr[n], -1);
+    for (int32_t r = 0; r < n; ++r)
+        for (int64_t p = indptr[r]; p < indptr[r + 1]; ++p) {
+            if (indices[p] == r) {
+                H.diag[r] = data[p];
+                continue;
+            }
+            const int64_t e = find(r, indices[p]);
+            H.a[e] = -data[p];
+            H.slotmap[p] = e;
+        }
+    for (int32_t r = 0; r < n; ++r)
+        for (int e = H.rowptr[r]; e < H.rowptr[r + 1]; ++e) {
+            const int64_t q = find(H.col[e], r);
+            H.rev[e] = (int)q;
+            H.c[e] = -H.a[e] * H.a[q];
+        }
+}
+
+template <typename T>
+std::vector<T> cast_vec(const std::vector<double> &v)
+{
+    std::vector<T> o(v.size());
+    for (size_t i = 0; i < v.size(); ++i) o[i] = (T)v[i];
+    return o;
+}
+
+gabp_status upload(gabp_ctx *ctx, void **dst, const void *src, size_t bytes)
+{
+    CKS(dalloc(ctx, dst, bytes));
+    if (bytes) CK(cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice));
+    return GABP_OK;
+}
+
+// Uploads the coefficient arrays (a, c, diag in both precisions) of H.
+gabp_status upload_coeffs(gabp_ctx *ctx, const HostLayout &H, bool realloc)
+{
+    const size_t S = (size_t)H.slots, n = (size_t)ctx->n;
+    auto put = [&](void **dst, const void *src, size_t bytes) -> gabp_status {
+        if (realloc) return upload(ctx, dst, src, bytes);
+        if (bytes) CK(cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice));
+        return GABP_OK;
+    };
+    CKS(put((void **)&ctx->a64, H.a.data(), S * sizeof(double)));
+    CKS(put((void **)&ctx->diag64, H.diag.data(), n * sizeof(double)));
+    if (ctx->prec == 0) {
+        ctx->a = ctx->a64;
+        ctx->diagT = ctx->diag64;
+        CKS(put(&ctx->c, H.c.data(), S * sizeof(double)));
+    } else {
+        auto af = cast_vec<float>(H.a), cf = cast_vec<float>(H.c), df = cast_vec<float>(H.diag);
+        CKS(put(&ctx->a, af.data(), S * sizeof(float)));
+        CKS(put(&ctx->c, cf.data(), S * sizeof(float)));
+        CKS(put(&ctx->diagT, df.data(), n * sizeof(float)));
+    }
+    return GABP_OK;
+}
+
+void free_all(std::vector<void *> &allocs)
+{
+    for (void *p : allocs) cudaFree(p);
+    allocs.clear();
+}
+
+// ---------------------------------------------------------------------------
+// Drivers
+// ---------------------------------------------------------------------------
+gabp_status zero_messages(gabp_ctx *ctx, bool lam, bool mean)
+{
+    const size_t bytes = (size_t)ctx->L.slots * esz(ctx->prec);
+    if (lam) CK(cudaMemsetAsync(ctx->Lm[ctx->cur], 0, bytes, ctx->stream));
+    if (mean) CK(cudaMemsetAsync(ctx->Mm[ctx->cur], 0, bytes, ctx->stream));
+    return GABP_OK;
+}
+
+// bres = b (double) and bT = b in message precision.
+gabp_status load_rhs(gabp_ctx *ctx, const double *b)
+{
+    const int64_t n = ctx->n;
+    if (b != ctx->bres) CK(cudaMemcpyAsync(ctx->bres, b, n * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+    if (ctx->prec == 1) CK(launch_convert_d2f(ctx->bres, (float *)ctx->bT, n, ctx->stream));
+    return GABP_OK;
+}
+
+gabp_status aggregate(gabp_ctx *ctx)
+{
+    CK(launch_aggregate(ctx->L, ctx->prec, ctx->diagT, ctx->bT, ctx->Lm[ctx->cur],
+                        ctx->Mm[ctx->cur], ctx->P[ctx->cur], ctx->B[ctx->cur], ctx->stream));
+    return GABP_OK;
+}
+
+int block_of(const gabp_ctx *ctx) { return ctx->opt.block_size > 0 ? ctx->opt.block_size : 256; }
+
+// One sweep from state cur into 1 - cur.
+cudaError_t sweep_once(gabp_ctx *ctx, bool transposed, double *x, cudaStream_t s)
+{
+    const int c0 = ctx->cur, c1 = c0 ^ 1;
+    SweepArgs a;
+    a.n = ctx->n;
+    a.a = transposed ? ctx->aT : ctx->a;
+    a.c = ctx->c;
+    a.diag = ctx->diagT;
+    a.b = ctx->bT;
+    a.Lin = ctx->Lm[c0];
+    a.Min = ctx->Mm[c0];
+    a.Pin = ctx->P[c0];
+    a.Bin = ctx->B[c0];
+    a.Lout = ctx->Lm[c1];
+    a.Mout = ctx->Mm[c1];
+    a.Pout = ctx->P[c1];
+    a.Bout = ctx->B[c1];
+    a.x = x;
+    a.flags = &ctx->dstat[0].flags;
+    ctx->cur = c1;
+    return launch_sweep(ctx->L, ctx->prec, a, block_of(ctx), s);
+}
+
+// k sweeps (beliefs of the last into xbuf), residual of (bres, xbuf) into
+// dstat[0], status copy to the pinned host mirror.
+cudaError_t enqueue_chunk(gabp_ctx *ctx, int k, bool transposed, cudaStream_t s)
+{
+    cudaError_t e;
+    for (int i = 0; i < k; ++i)
+        if ((e = sweep_once(ctx, transposed, i == k - 1 ? ctx->xbuf : nullptr, s)) != cudaSuccess)
+            return e;
+    if ((e = cudaMemsetAsync(ctx->dstat, 0, 2 * sizeof(unsigned long long), s)) != cudaSuccess) return e;
+    if ((e = launch_residual(ctx->L, transposed ? ctx->aT64 : ctx->a64, ctx->diag64, ctx->bres,
+                             ctx->xbuf, nullptr, &ctx->dstat[0], s)) != cudaSuccess)
+        return e;
+    return cudaMemcpyAsync(ctx->hstat, ctx->dstat, sizeof(DevStatus), cudaMemcpyDeviceToHost, s);
+}
+
+gabp_status run_chunk(gabp_ctx *ctx, int k, bool transposed)
+{
+    if (!ctx->opt.use_graphs) {
+        CK(enqueue_chunk(ctx, k, transposed, ctx->stream));
+    } else {
+        const int parity = ctx->cur;
+        cudaGraphExec_t exec = nullptr;
+        for (auto &g : ctx->graphs)
+            if (g.k == k && g.parity == parity && g.transposed == (int)transposed) exec = g.exec;
+        if (!exec) {
+            cudaGraph_t graph;
+            CK(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+            cudaError_t e = enqueue_chunk(ctx, k, transposed, ctx->cap_stream);
+            cudaError_t e2 = cudaStreamEndCapture(ctx->cap_stream, &graph);
+            ctx->cur = parity;
+            if (e != cudaSuccess) return fail_cuda(e, "chunk capture");
+            if (e2 != cudaSuccess) return fail_cuda(e2, "cudaStreamEndCapture");
+            e = cudaGraphInstantiate(&exec, graph, 0);
+            cudaGraphDestroy(graph);
+            if (e != cudaSuccess) return fail_cuda(e, "cudaGraphInstantiate");
+            ctx->graphs.push_back({k, parity, (int)transposed, exec});
+        }
+        CK(cudaGraphLaunch(exec, ctx->stream));
+        count_launches(ctx->stream, (unsigned long long)k + 1);  // k sweeps + residual
+        ctx->cur = parity ^ (k & 1);
+    }
+    CK(cudaStreamSynchronize(ctx->stream));
+    return GABP_OK;
+}
+
+gabp_status read_status(gabp_ctx *ctx, int which, double *rinf, double *binf, unsigned *flags)
+{
+    CK(cudaMemcpyAsync(ctx->hstat + which, ctx->dstat + which, sizeof(DevStatus),
+                       cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (rinf) *rinf = bits_to_double(ctx->hstat[which].rmax);
+    if (binf) *binf = bits_to_double(ctx->hstat[which].bmax);
+    if (flags) *flags = ctx->hstat[which].flags;
+    return GABP_OK;
+}
+
+gabp_status ensure_transpose(gabp_ctx *ctx)
+{
+    if (ctx->aT) return GABP_OK;
+    const size_t S = (size_t)ctx->L.slots;
+    CKS(dalloc(ctx, (void **)&ctx->aT64, S * sizeof(double)));
+    CK(launch_transpose_coeffs(ctx->L, 0, ctx->a64, ctx->aT64, ctx->stream));
+    if (ctx->prec == 0) {
+        ctx->aT = ctx->aT64;
+    } else {
+        CKS(dalloc(ctx, &ctx->aT, S * sizeof(float)));
+        CK(launch_transpose_coeffs(ctx->L, 1, ctx->a, ctx->aT, ctx->stream));
+    }
+    return GABP_OK;
+}
+
+gabp_status ensure_ir(gabp_ctx *ctx)
+{
+    if (ctx->b0) return GABP_OK;
+    const size_t nb = (size_t)ctx->n * sizeof(double);
+    CKS(dalloc(ctx, (void **)&ctx->b0, nb));
+    CKS(dalloc(ctx, (void **)&ctx->xacc, nb));
+    CKS(dalloc(ctx, (void **)&ctx->rbuf, nb));
+    return GABP_OK;
+}
+
+// Plain GaBP solve (Algorithm 1, flood schedule) on A or A^T.
+gabp_status solve_plain(gabp_ctx *ctx, const double *b, double *x, double tol, int max_iter,
+                        int *iters, double *relres, bool transposed)
+{
+    const int64_t n = ctx->n;
+    CKS(load_rhs(ctx, b));
+    CKS(zero_messages(ctx, true, true));
+    CKS(aggregate(ctx));
+    CK(cudaMemsetAsync(ctx->dstat, 0, sizeof(DevStatus), ctx->stream));
+    // ||b||_inf (residual of x = 0)
+    CK(cudaMemsetAsync(ctx->xbuf, 0, n * sizeof(double), ctx->stream));
+    CK(launch_residual(ctx->L, ctx->a64, ctx->diag64, ctx->bres, ctx->xbuf, nullptr, &ctx->dstat[0], ctx->stream));
+    double binf = 0.0;
+    CKS(read_status(ctx, 0, nullptr, &binf, nullptr));
+    int it = 0;
+    double rr = 0.0;
+    gabp_status st = GABP_E_NOT_CONVERGED;
+    if (binf == 0.0) {
+        st = GABP_OK;
+    } else {
+        const int every = std::max(1, ctx->opt.check_every);
+        while (it < max_iter) {
+            const int k = std::min(every, max_iter - it);
+            CKS(run_chunk(ctx, k, transposed));
+            it += k;
+            const DevStatus &h = ctx->hstat[0];
+            rr = bits_to_double(h.rmax) / binf;
+            if (h.flags & FLAG_BREAKDOWN) { st = fail(GABP_E_BREAKDOWN, "zero or non-finite message denominator"); break; }
+            if ((h.flags & FLAG_NAN) || !std::isfinite(rr) || rr > kDivergence) { st = fail(GABP_E_DIVERGED, "residual diverged"); break; }
+            if (rr <= tol) { st = GABP_OK; break; }
+        }
+        if (st == GABP_E_NOT_CONVERGED) fail(st, "iteration cap reached");
+    }
+    CK(cudaMemcpyAsync(x, ctx->xbuf, n * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (iters) *iters = it;
+    if (relres) *relres = rr;
+    return st;
+}
+
+// Float GaBP inside double iterative refinement.
+gabp_status solve_ir(gabp_ctx *ctx, const double *b, double *x, double tol, int max_iter,
+                     int *iters, double *relres)
+{
+    const int64_t n = ctx->n;
+    const size_t nb = n * sizeof(double);
+    CKS(ensure_ir(ctx));
+    cudaStream_t s = ctx->stream;
+    CK(cudaMemcpyAsync(ctx->b0, b, nb, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemsetAsync(ctx->xacc, 0, nb, s));
+    CK(cudaMemsetAsync(ctx->dstat, 0, 2 * sizeof(DevStatus), s));
+    // r = b, s = ||b||
+    CK(launch_residual(ctx->L, ctx->a64, ctx->diag64, ctx->b0, ctx->xacc, ctx->rbuf, &ctx->dstat[1], s));
+    double bn = 0.0;
+    CKS(read_status(ctx, 1, nullptr, &bn, nullptr));
+    int total = 0;
+    double rr = bn == 0.0 ? 0.0 : 1.0;
+    gabp_status st = GABP_E_NOT_CONVERGED;
+    CKS(zero_messages(ctx, true, true));
+    const int every = std::max(1, ctx->opt.check_every);
+    const int inner_max = ctx->opt.ir_inner_max > 0 ? ctx->opt.ir_inner_max : 400;
+    const double inner_tol = ctx->opt.ir_inner_tol > 0 ? ctx->opt.ir_inner_tol : 1e-4;
+    if (bn == 0.0) st = GABP_OK;
+    for (int outer = 0; st == GABP_E_NOT_CONVERGED && outer < 200 && total < max_iter; ++outer) {
+        // inner problem A e = r / ||r||: double copy for the checks, float copy for the sweeps
+        CK(launch_scale_rhs(ctx->rbuf, &ctx->dstat[1], ctx->bres, ctx->bT, ctx->prec, n, s));
+        CKS(zero_messages(ctx, false, true));  // tilde-Lambda kept warm
+        CKS(aggregate(ctx));
+        int inner = 0;
+        while (inner < inner_max && total < max_iter) {
+            const int k = std::min(std::min(every, inner_max - inner), max_iter - total);
+            CKS(run_chunk(ctx, k, false));
+            inner += k;
+            total += k;
+            const DevStatus &h = ctx->hstat[0];
+            if (h.flags & FLAG_BREAKDOWN) { st = fail(GABP_E_BREAKDOWN, "zero or non-finite message denominator"); break; }
+            const double rin = bits_to_double(h.rmax);  // ||r/s||_inf == 1
+            if ((h.flags & FLAG_NAN) || !std::isfinite(rin)) { st = fail(GABP_E_DIVERGED, "inner residual not finite"); break; }
+            if (rin <= inner_tol) break;
+        }
+        if (st != GABP_E_NOT_CONVERGED) break;
+        // x += s e;  r = b - A x;  s = ||r||
+        CK(launch_axpy_status(ctx->xacc, ctx->xbuf, &ctx->dstat[1], n, s));
+        CK(cudaMemsetAsync(&ctx->dstat[1], 0, 2 * sizeof(unsigned long long), s));
+        CK(launch_residual(ctx->L, ctx->a64, ctx->diag64, ctx->b0, ctx->xacc, ctx->rbuf, &ctx->dstat[1], s));
+        double rinf = 0.0;
+        unsigned fl = 0;
+        CKS(read_status(ctx, 1, &rinf, nullptr, &fl));
+        rr = rinf / bn;
+        if ((fl & FLAG_NAN) || !std::isfinite(rr) || rr > kDivergence) { st = fail(GABP_E_DIVERGED, "residual diverged"); break; }
+        if (rr <= tol) st = GABP_OK;
+    }
+    if (st == GABP_E_NOT_CONVERGED) fail(st, "iteration cap reached");
+    CK(cudaMemcpyAsync(x, ctx->xacc, nb, cudaMemcpyDeviceToDevice, s));
+    CK(cudaStreamSynchronize(s));
+    if (iters) *iters = total;
+    if (relres) *relres = rr;
+    return st;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+void gabp_default_options(gabp_options *opt)
+{
+    if (!opt) return;
+    opt->precision = GABP_FP64;
+    opt->layout = GABP_LAYOUT_AUTO;
+    opt->check_every = 10;
+    opt->use_graphs = 1;
+    opt->ir_inner_max = 400;
+    opt->ir_inner_tol = 1e-4;
+    opt->block_size = 0;
+}
+
+const char *gabp_status_str(gabp_status s)
+{
+    switch (s) {
+        case GABP_OK: return "ok";
+        case GABP_E_INVALID_ARG: return "invalid argument";
+        case GABP_E_BAD_CSR: return "malformed CSR matrix";
+        case GABP_E_ZERO_DIAG: return "missing or zero diagonal entry";
+        case GABP_E_BREAKDOWN: return "zero or non-finite message denominator";
+        case GABP_E_DIVERGED: return "diverged";
+        case GABP_E_NOT_CONVERGED: return "not converged";
+        case GABP_E_CUDA: return "CUDA error";
+        case GABP_E_OOM: return "out of memory";
+    }
+    return "unknown status";
+}
+
+const char *gabp_last_error(void) { return g_last_error.c_str(); }
+
+unsigned long long gabp_launch_count(void) { return launch_count(); }
+
+gabp_status gabp_setup(int32_t n, int64_t nnz, const int64_t *indptr, const int32_t *indices,
+                       const double *data, const gabp_options *opt, void *stream, gabp_ctx **out)
+{
+    if (!out) return fail(GABP_E_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    gabp_options o;
+    gabp_default_options(&o);
+    if (opt) o = *opt;
+    if (o.precision < 0 || o.precision > 2 || o.layout < 0 || o.layout > 2 || o.check_every < 0 ||
+        o.block_size < 0 || o.block_size > 1024 || (o.block_size % 32) != 0)
+        return fail(GABP_E_INVALID_ARG, "bad option");
+    CKS(validate_csr(n, nnz, indptr, indices, data));
+    int64_t nonzero_off = 0;
+    for (int32_t r = 0; r < n; ++r)
+        for (int64_t p = indptr[r]; p < indptr[r + 1]; ++p)
+            if (indices[p] != r && data[p] != 0.0) ++nonzero_off;
+
+    HostLayout H;
+    StencilParams sp{};
+    bool can_stencil = o.layout != GABP_LAYOUT_CSR && stencil_offsets(n, indptr, indices, sp);
+    if (o.layout == GABP_LAYOUT_STENCIL && !can_stencil)
+        return fail(GABP_E_INVALID_ARG, "stencil layout needs at most 16 off-diagonal diagonals");
+    const int64_t offd = nnz - n;
+    bool use_stencil = can_stencil &&
+                       (o.layout == GABP_LAYOUT_STENCIL || (int64_t)sp.K * n <= 3 * offd + 4096);
+    if (use_stencil) build_stencil(n, indptr, indices, data, sp, H);
+    else build_csr(n, indptr, indices, data, H);
+    if (H.kind == GABP_LAYOUT_CSR && H.slots >= (int64_t)1 << 31)
+        return fail(GABP_E_INVALID_ARG, "too many edges for the CSR layout");
+
+    gabp_ctx *ctx = new (std::nothrow) gabp_ctx;
+    if (!ctx) return fail(GABP_E_OOM, "host allocation");
+    auto bail = [&](gabp_status s) {
+        gabp_destroy(ctx);
+        return s;
+    };
+    cudaError_t e = cudaGetDevice(&ctx->dev);
+    if (e != cudaSuccess) return bail(fail_cuda(e, "cudaGetDevice"));
+    ctx->stream = (cudaStream_t)stream;
+    ctx->opt = o;
+    ctx->prec = o.precision == GABP_FP64 ? 0 : 1;
+    ctx->n = n;
+    ctx->nnz = nnz;
+    ctx->edges = nonzero_off;
+    ctx->h_indptr.assign(indptr, indptr + n + 1);
+    ctx->h_indices.assign(indices, indices + nnz);
+    ctx->h_data.assign(data, data + nnz);
+    e = cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return bail(fail_cuda(e, "cudaStreamCreate"));
+    if ((e = cudaEventCreate(&ctx->ev0)) != cudaSuccess || (e = cudaEventCreate(&ctx->ev1)) != cudaSuccess)
+        return bail(fail_cuda(e, "cudaEventCreate"));
+
+    DevLayout &L = ctx->L;
+    L.kind = H.kind;
+    L.n = n;
+    L.slots = H.slots;
+    L.sp = H.sp;
+    gabp_status s;
+    if (H.kind == GABP_LAYOUT_CSR) {
+        if ((s = upload(ctx, (void **)&L.rowptr, H.rowptr.data(), H.rowptr.size() * sizeof(int))) != GABP_OK) return bail(s);
+        if ((s = upload(ctx, (void **)&L.col, H.col.data(), H.col.size() * sizeof(int))) != GABP_OK) return bail(s);
+        if ((s = upload(ctx, (void **)&L.rev, H.rev.data(), H.rev.size() * sizeof(int))) != GABP_OK) return bail(s);
+    }
+    if ((s = upload_coeffs(ctx, H, true)) != GABP_OK) return bail(s);
+    if ((s = upload(ctx, (void **)&ctx->slotmap, H.slotmap.data(), H.slotmap.size() * sizeof(int64_t))) != GABP_OK) return bail(s);
+    const size_t S = (size_t)H.slots * esz(ctx->prec), NB = (size_t)n * esz(ctx->prec);
+    for (int i = 0; i < 2; ++i) {
+        if ((s = dalloc(ctx, &ctx->Lm[i], S)) != GABP_OK) return bail(s);
+        if ((s = dalloc(ctx, &ctx->Mm[i], S)) != GABP_OK) return bail(s);
+        if ((s = dalloc(ctx, &ctx->P[i], NB)) != GABP_OK) return bail(s);
+        if ((s = dalloc(ctx, &ctx->B[i], NB)) != GABP_OK) return bail(s);
+    }
+    if ((s = dalloc(ctx, (void **)&ctx->bres, (size_t)n * sizeof(double))) != GABP_OK) return bail(s);
+    if (ctx->prec == 0) ctx->bT = ctx->bres;
+    else if ((s = dalloc(ctx, &ctx->bT, NB)) != GABP_OK) return bail(s);
+    if ((s = dalloc(ctx, (void **)&ctx->xbuf, (size_t)n * sizeof(double))) != GABP_OK) return bail(s);
+    if ((s = dalloc(ctx, (void **)&ctx->dstat, 2 * sizeof(DevStatus))) != GABP_OK) return bail(s);
+    e = cudaMallocHost((void **)&ctx->hstat, 2 * sizeof(DevStatus));
+    if (e != cudaSuccess) return bail(fail_cuda(e, "cudaMallocHost"));
+    std::memset(ctx->hstat, 0, 2 * sizeof(DevStatus));
+    for (int i = 0; i < 2; ++i) {
+        if ((e = cudaMemset(ctx->Lm[i], 0, S)) != cudaSuccess) return bail(fail_cuda(e, "cudaMemset"));
+        if ((e = cudaMemset(ctx->Mm[i], 0, S)) != cudaSuccess) return bail(fail_cuda(e, "cudaMemset"));
+    }
+    if ((e = cudaMemset(ctx->dstat, 0, 2 * sizeof(DevStatus))) != cudaSuccess) return bail(fail_cuda(e, "cudaMemset"));
+    if ((e = cudaDeviceSynchronize()) != cudaSuccess) return bail(fail_cuda(e, "setup"));
+    *out = ctx;
+    return GABP_OK;
+}
+
+gabp_status gabp_set_values(gabp_ctx *ctx, const double *data)
+{
+    if (!ctx || (!data && ctx->nnz > 0)) return fail(GABP_E_INVALID_ARG, "null argument");
+    CKS(set_dev(ctx->dev));
+    CKS(validate_csr(ctx->n, ctx->nnz, ctx->h_indptr.data(), ctx->h_indices.data(), data));
+    HostLayout H;
+    if (ctx->L.kind == GABP_LAYOUT_STENCIL)
+        build_stencil(ctx->n, ctx->h_indptr.data(), ctx->h_indices.data(), data, ctx->L.sp, H);
+    else
+        build_csr(ctx->n, ctx->h_indptr.data(), ctx->h_indices.data(), data, H);
+    CK(cudaStreamSynchronize(ctx->stream));
+    CKS(upload_coeffs(ctx, H, false));
+    ctx->h_data.assign(data, data + ctx->nnz);
+    int64_t nz = 0;
+    for (int32_t r = 0; r < ctx->n; ++r)
+        for (int64_t p = ctx->h_indptr[r]; p < ctx->h_indptr[r + 1]; ++p)
+            if (ctx->h_indices[p] != r && data[p] != 0.0) ++nz;
+    ctx->edges = nz;
+    if (ctx->aT) {
+        CK(launch_transpose_coeffs(ctx->L, 0, ctx->a64, ctx->aT64, ctx->stream));
+        if (ctx->prec == 1) CK(launch_transpose_coeffs(ctx->L, 1, ctx->a, ctx->aT, ctx->stream));
+    }
+    CKS(zero_messages(ctx, true, true));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return GABP_OK;
+}
+
+void gabp_destroy(gabp_ctx *ctx)
+{
+    if (!ctx) return;
+    cudaSetDevice(ctx->dev);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    for (auto &g : ctx->graphs) cudaGraphExecDestroy(g.exec);
+    free_all(ctx->allocs);
+    if (ctx->hstat) cudaFreeHost(ctx->hstat);
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+    if (ctx->ev0) cudaEventDestroy(ctx->ev0);
+    if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+    delete ctx;
+}
+
+gabp_status gabp_reset(gabp_ctx *ctx)
+{
+    if (!ctx) return fail(GABP_E_INVALID_ARG, "null context");
+    CKS(set_dev(ctx->dev));
+    CKS(zero_messages(ctx, true, true));
+    return GABP_OK;
+}
+
+gabp_status gabp_sweep(gabp_ctx *ctx, const double *b, int nsweeps, double *x)
+{
+    if (!ctx || nsweeps < 0 || (!b && ctx->n > 0)) return fail(GABP_E_INVALID_ARG, "bad argument");
+    CKS(set_dev(ctx->dev));
+    CKS(load_rhs(ctx, b));
+    CKS(aggregate(ctx));
+    CK(cudaMemsetAsync(&ctx->dstat[0].flags, 0, sizeof(unsigned), ctx->stream));
+    for (int i = 0; i < nsweeps; ++i) CK(sweep_once(ctx, false, i == nsweeps - 1 ? x : nullptr, ctx->stream));
+    unsigned fl = 0;
+    CKS(read_status(ctx, 0, nullptr, nullptr, &fl));
+    if (fl & FLAG_BREAKDOWN) return fail(GABP_E_BREAKDOWN, "zero or non-finite message denominator");
+    return GABP_OK;
+}
+
+gabp_status gabp_time_sweeps(gabp_ctx *ctx, const double *b, int nsweeps, float *ms)
+{
+    if (!ctx || nsweeps < 1 || !ms || (!b && ctx->n > 0)) return fail(GABP_E_INVALID_ARG, "bad argument");
+    CKS(set_dev(ctx->dev));
+    CKS(load_rhs(ctx, b));
+    CKS(aggregate(ctx));
+    CK(cudaMemsetAsync(&ctx->dstat[0].flags, 0, sizeof(unsigned), ctx->stream));
+    CK(cudaEventRecord(ctx->ev0, ctx->stream));
+    for (int i = 0; i < nsweeps; ++i) CK(sweep_once(ctx, false, nullptr, ctx->stream));
+    CK(cudaEventRecord(ctx->ev1, ctx->stream));
+    CK(cudaEventSynchronize(ctx->ev1));
+    CK(cudaEventElapsedTime(ms, ctx->ev0, ctx->ev1));
+    unsigned fl = 0;
+    CKS(read_status(ctx, 0, nullptr, nullptr, &fl));
+    if (fl & FLAG_BREAKDOWN) return fail(GABP_E_BREAKDOWN, "zero or non-finite message denominator");
+    return GABP_OK;
+}
+
+gabp_status gabp_solve(gabp_ctx *ctx, const double *b, double *x, double tol, int max_iter,
+                       int *iters, double *relres)
+{
+    if (!ctx || max_iter < 0 || !(tol >= 0.0) || ((!b || !x) && ctx->n > 0))
+        return fail(GABP_E_INVALID_ARG, "bad argument");
+    CKS(set_dev(ctx->dev));
+    if (ctx->opt.precision == GABP_FP32_IR) return solve_ir(ctx, b, x, tol, max_iter, iters, relres);
+    return solve_plain(ctx, b, x, tol, max_iter, iters, relres, false);
+}
+
+gabp_status gabp_solve_transpose(gabp_ctx *ctx, const double *g, double *lam, double tol,
+                                  int max_iter, int *iters, double *relres)
+{
+    if (!ctx || max_iter < 0 || !(tol >= 0.0) || ((!g || !lam) && ctx->n > 0))
+        return fail(GABP_E_INVALID_ARG, "bad argument");
+    CKS(set_dev(ctx->dev));
+    CKS(ensure_transpose(ctx));
+    return solve_plain(ctx, g, lam, tol, max_iter, iters, relres, true);
+}
+
+gabp_status gabp_edge_grad(gabp_ctx *ctx, const double *lam, const double *x, double *dA)
+{
+    if (!ctx || ((!lam || !x || !dA) && ctx->n > 0)) return fail(GABP_E_INVALID_ARG, "null argument");
+    CKS(set_dev(ctx->dev));
+    if (!ctx->d_indptr) {
+        CKS(upload(ctx, (void **)&ctx->d_indptr, ctx->h_indptr.data(), ctx->h_indptr.size() * sizeof(int64_t)));
+        CKS(upload(ctx, (void **)&ctx->d_indices, ctx->h_indices.data(), ctx->h_indices.size() * sizeof(int)));
+    }
+    CK(launch_edge_grad(ctx->n, ctx->d_indptr, ctx->d_indices, lam, x, dA, ctx->stream));
+    return GABP_OK;
+}
+
+gabp_status gabp_residual(gabp_ctx *ctx, const double *b, const double *x, double *r, double *rinf,
+                          double *binf)
+{
+    if (!ctx || ((!b || !x) && ctx->n > 0)) return fail(GABP_E_INVALID_ARG, "null argument");
+    CKS(set_dev(ctx->dev));
+    CK(cudaMemsetAsync(&ctx->dstat[1], 0, sizeof(DevStatus), ctx->stream));
+    CK(launch_residual(ctx->L, ctx->a64, ctx->diag64, b, x, r, &ctx->dstat[1], ctx->stream));
+    if (rinf || binf) CKS(read_status(ctx, 1, rinf, binf, nullptr));
+    return GABP_OK;
+}
+
+gabp_status gabp_get_state(gabp_ctx *ctx, double *lam, double *m)
+{
+    if (!ctx) return fail(GABP_E_INVALID_ARG, "null context");
+    CKS(set_dev(ctx->dev));
+    CK(launch_get_state(ctx->slotmap, ctx->nnz, ctx->prec, ctx->Lm[ctx->cur], ctx->Mm[ctx->cur], lam, m, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return GABP_OK;
+}
+
+gabp_status gabp_set_state(gabp_ctx *ctx, const double *lam, const double *m)
+{
+    if (!ctx) return fail(GABP_E_INVALID_ARG, "null context");
+    CKS(set_dev(ctx->dev));
+    CKS(zero_messages(ctx, lam != nullptr, m != nullptr));
+    CK(launch_set_state(ctx->slotmap, ctx->nnz, ctx->prec, lam, m, ctx->Lm[ctx->cur], ctx->Mm[ctx->cur], ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return GABP_OK;
+}
+
+gabp_status gabp_get_info(gabp_ctx *ctx, gabp_info *info)
+{
+    if (!ctx || !info) return fail(GABP_E_INVALID_ARG, "null argument");
+    const double p = (double)esz(ctx->prec);
+    const double S = (double)ctx->L.slots, n = (double)ctx->n;
+    info->n = ctx->n;
+    info->nnz = ctx->nnz;
+    info->edges = ctx->edges;
+    info->layout = ctx->L.kind;
+    info->ndiag = ctx->L.kind == GABP_LAYOUT_STENCIL ? ctx->L.sp.K : 0;
+    info->precision = ctx->opt.precision;
+    info->slots = ctx->L.slots;
+    // per slot: a, c, L[rev], M[rev] read, L', M' written; per row: diag, b, P, B
+    // read, P', B' written; CSR adds col, rev (per slot) and the row pointer.
+    double sweep = 6.0 * p * S + 6.0 * p * n;
+    double resid = 8.0 * S + 8.0 * 4.0 * n;  // a64 per slot; diag, b, x read, r written
+    if (ctx->L.kind == GABP_LAYOUT_CSR) {
+        sweep += 8.0 * S + 4.0 * n;
+        resid += 4.0 * S + 4.0 * n;
+    }
+    info->sweep_bytes = sweep;
+    info->residual_bytes = resid;
+    info->device_bytes = ctx->dev_bytes;
+    return GABP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Multigrid
+// ---------------------------------------------------------------------------
+static gabp_status coarse_inverse(const gabp_ctx *c, std::vector<double> &inv)
+{
+    const int n = c->n;
+    std::vector<double> A((size_t)n * n, 0.0);
+    for (int r = 0; r < n; ++r)
+        for (int64_t p = c->h_indptr[r]; p < c->h_indptr[r + 1]; ++p)
+            A[(size_t)r * n + c->h_indices[p]] = c->h_data[p];
+    // LU with partial pivoting, P A = L U (in place)
+    std::vector<int> piv(n);
+    for (int k = 0; k < n; ++k) {
+        int pr = k;
+        double best = std::fabs(A[(size_t)k * n + k]);
+        for (int i = k + 1; i < n; ++i)
+            if (std::fabs(A[(size_t)i * n + k]) > best) {
+                best = std::fabs(A[(size_t)i * n + k]);
+                pr = i;
+            }
+        if (best == 0.0) return fail(GABP_E_INVALID_ARG, "singular coarsest-level matrix");
+        piv[k] = pr;
+        if (pr != k)
+            for (int j = 0; j < n; ++j) std::swap(A[(size_t)k * n + j], A[(size_t)pr * n + j]);
+        const double d = A[(size_t)k * n + k];
+        for (int i = k + 1; i < n; ++i) {
+            double &l = A[(size_t)i * n + k];
+            if (l == 0.0) continue;
+            l /= d;
+            const double *uk = &A[(size_t)k * n];
+            double *ai = &A[(size_t)i * n];
+            for (int j = k + 1; j < n; ++j) ai[j] -= l * uk[j];
+        }
+    }
+    // columns of the inverse: solve L U x = P e_j
+    inv.assign((size_t)n * n, 0.0);
+    std::vector<double> y(n);
+    for (int j = 0; j < n; ++j) {
+        std::fill(y.begin(), y.end(), 0.0);
+        y[j] = 1.0;
+        for (int k = 0; k < n; ++k) std::swap(y[k], y[piv[k]]);
+        for (int i = 0; i < n; ++i) {
+            double s = y[i];
+            for (int k = 0; k < i; ++k) s -= A[(size_t)i * n + k] * y[k];
+            y[i] = s;
+        }
+        for (int i = n - 1; i >= 0; --i) {
+            double s = y[i];
+            for (int k = i + 1; k < n; ++k) s -= A[(size_t)i * n + k] * y[k];
+            y[i] = s / A[(size_t)i * n + i];
+        }
+        for (int i = 0; i < n; ++i) inv[(size_t)i * n + j] = y[i];
+    }
+    return GABP_OK;
+}
+
+gabp_status mg_setup(int levels, gabp_ctx *const *level_ctx, const int32_t *grid_side,
+                     double transfer_scale, int mode, void *stream, mg_ctx **out)
+{
+    if (!out) return fail(GABP_E_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (levels < 1 || !level_ctx || !grid_side || mode < 0 || mode > 2 || !std::isfinite(transfer_scale))
+        return fail(GABP_E_INVALID_ARG, "bad argument");
+    for (int l = 0; l < levels; ++l) {
+        if (!level_ctx[l]) return fail(GABP_E_INVALID_ARG, "null level context");
+        const int m = grid_side[l];
+        if (m < 1 || (int64_t)m * m != level_ctx[l]->n) return fail(GABP_E_INVALID_ARG, "grid side does not match level size");
+        if (l > 0 && grid_side[l - 1] != 2 * m + 1) return fail(GABP_E_INVALID_ARG, "sides must satisfy m_fine = 2 m_coarse + 1");
+        if (level_ctx[l]->dev != level_ctx[0]->dev) return fail(GABP_E_INVALID_ARG, "levels on different devices");
+    }
+    if (level_ctx[levels - 1]->n > 4096) return fail(GABP_E_INVALID_ARG, "coarsest level above 4096 unknowns");
+    mg_ctx *mg = new (std::nothrow) mg_ctx;
+    if (!mg) return fail(GABP_E_OOM, "host allocation");
+    auto bail = [&](gabp_status s) {
+        mg_destroy(mg);
+        return s;
+    };
+    mg->dev = level_ctx[0]->dev;
+    gabp_status s;
+    if ((s = set_dev(mg->dev)) != GABP_OK) return bail(s);
+    mg->stream = (cudaStream_t)stream;
+    mg->levels = levels;
+    mg->lv.assign(level_ctx, level_ctx + levels);
+    mg->side.assign(grid_side, grid_side + levels);
+    mg->scale = transfer_scale;
+    mg->mode = mode;
+    mg->b.assign(levels, nullptr);
+    mg->x.assign(levels, nullptr);
+    for (int l = 1; l < levels; ++l) {
+        const size_t nb = (size_t)mg->lv[l]->n * sizeof(double);
+        if ((s = dalloc(mg, (void **)&mg->b[l], nb)) != GABP_OK) return bail(s);
+        if ((s = dalloc(mg, (void **)&mg->x[l], nb)) != GABP_OK) return bail(s);
+    }
+    std::vector<double> inv;
+    if ((s = coarse_inverse(mg->lv[levels - 1], inv)) != GABP_OK) return bail(s);
+    mg->nc = mg->lv[levels - 1]->n;
+    if ((s = dalloc(mg, (void **)&mg->coarse_inv, inv.size() * sizeof(double))) != GABP_OK) return bail(s);
+    cudaError_t e = cudaMemcpy(mg->coarse_inv, inv.data(), inv.size() * sizeof(double), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return bail(fail_cuda(e, "cudaMemcpy"));
+    if ((s = dalloc(mg, (void **)&mg->dstat, sizeof(DevStatus))) != GABP_OK) return bail(s);
+    if ((e = cudaMallocHost((void **)&mg->hstat, sizeof(DevStatus))) != cudaSuccess) return bail(fail_cuda(e, "cudaMallocHost"));
+    // every level works on the multigrid stream
+    for (auto *c : mg->lv) c->stream = mg->stream;
+    *out = mg;
+    return GABP_OK;
+}
+
+void mg_destroy(mg_ctx *mg)
+{
+    if (!mg) return;
+    cudaSetDevice(mg->dev);
+    if (mg->stream) cudaStreamSynchronize(mg->stream);
+    free_all(mg->allocs);
+    if (mg->hstat) cudaFreeHost(mg->hstat);
+    delete mg;
+}
+
+namespace {
+
+// Algorithm 3 on level l: r = b - A x; nu GaBP sweeps on A e = r; x += e.
+gabp_status mg_smooth(mg_ctx *mg, int l, const double *b, double *x, int nu)
+{
+    gabp_ctx *c = mg->lv[l];
+    cudaStream_t s = mg->stream;
+    CK(launch_residual(c->L, c->a64, c->diag64, b, x, c->bres, &c->dstat[1], s));
+    if (c->prec == 1) CK(launch_convert_d2f(c->bres, (float *)c->bT, c->n, s));
+    if (mg->mode == MG_SMOOTH_COLD) CKS(zero_messages(c, true, true));
+    else if (mg->mode == MG_SMOOTH_WARM) CKS(zero_messages(c, false, true));
+    CKS(aggregate(c));
+    for (int i = 0; i < nu; ++i) CK(sweep_once(c, false, i == nu - 1 ? c->xbuf : nullptr, s));
+    CK(launch_axpy(x, c->xbuf, 1.0, c->n, s));
+    return GABP_OK;
+}
+
+gabp_status mg_cycle(mg_ctx *mg, int l, int last, int nu_pre, int nu_post, const double *b, double *x)
+{
+    cudaStream_t s = mg->stream;
+    gabp_ctx *c = mg->lv[l];
+    if (l == last) {
+        if (l == mg->levels - 1) {
+            CK(launch_dense_gemv(mg->coarse_inv, b, x, mg->nc, s));
+        } else {
+            // truncated hierarchy: smooth on the last used level instead of a direct solve
+            CKS(mg_smooth(mg, l, b, x, std::max(1, nu_pre + nu_post)));
+        }
+        return GABP_OK;
+    }
+    if (nu_pre > 0) CKS(mg_smooth(mg, l, b, x, nu_pre));
+    CK(launch_residual(c->L, c->a64, c->diag64, b, x, c->bres, &c->dstat[1], s));
+    CK(launch_restrict_fw(c->bres, mg->side[l], mg->scale, mg->b[l + 1], s));
+    CK(cudaMemsetAsync(mg->x[l + 1], 0, (size_t)mg->lv[l + 1]->n * sizeof(double), s));
+    CKS(mg_cycle(mg, l + 1, last, nu_pre, nu_post, mg->b[l + 1], mg->x[l + 1]));
+    CK(launch_prolong_add(mg->x[l + 1], mg->side[l + 1], x, s));
+    if (nu_post > 0) CKS(mg_smooth(mg, l, b, x, nu_post));
+    return GABP_OK;
+}
+
+gabp_status mg_check_flags(mg_ctx *mg)
+{
+    for (auto *c : mg->lv) {
+        CK(cudaMemcpyAsync(&c->hstat[0].flags, &c->dstat[0].flags, sizeof(unsigned), cudaMemcpyDeviceToHost, mg->stream));
+    }
+    CK(cudaStreamSynchronize(mg->stream));
+    for (auto *c : mg->lv)
+        if (c->hstat[0].flags & FLAG_BREAKDOWN) return fail(GABP_E_BREAKDOWN, "zero or non-finite message denominator in a smoother");
+    return GABP_OK;
+}
+
+}  // namespace
+
+gabp_status mg_vcycle(mg_ctx *mg, int levels, int nu_pre, int nu_post, const double *b, double *x)
+{
+    if (!mg || levels < 0 || levels > mg->levels || nu_pre < 0 || nu_post < 0 || !b || !x)
+        return fail(GABP_E_INVALID_ARG, "bad argument");
+    CKS(set_dev(mg->dev));
+    const int last = (levels == 0 ? mg->levels : levels) - 1;
+    for (auto *c : mg->lv) CK(cudaMemsetAsync(&c->dstat[0].flags, 0, sizeof(unsigned), mg->stream));
+    CKS(mg_cycle(mg, 0, last, nu_pre, nu_post, b, x));
+    return mg_check_flags(mg);
+}
+
+gabp_status mg_solve(mg_ctx *mg, const double *b, double *x, double tol, int max_cycles, int nu_pre,
+                     int nu_post, int *cycles, double *relres)
+{
+    if (!mg || !b || !x || max_cycles < 0 || !(tol >= 0.0) || nu_pre < 0 || nu_post < 0)
+        return fail(GABP_E_INVALID_ARG, "bad argument");
+    CKS(set_dev(mg->dev));
+    gabp_ctx *f = mg->lv[0];
+    cudaStream_t s = mg->stream;
+    CK(cudaMemsetAsync(x, 0, (size_t)f->n * sizeof(double), s));
+    CK(cudaMemsetAsync(mg->dstat, 0, sizeof(DevStatus), s));
+    CK(launch_residual(f->L, f->a64, f->diag64, b, x, nullptr, mg->dstat, s));
+    CK(cudaMemcpyAsync(mg->hstat, mg->dstat, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const double bn = bits_to_double(mg->hstat->bmax);
+    double rr = bn == 0.0 ? 0.0 : 1.0;
+    int c = 0;
+    gabp_status st = bn == 0.0 ? GABP_OK : GABP_E_NOT_CONVERGED;
+    for (auto *lc : mg->lv) CK(cudaMemsetAsync(&lc->dstat[0].flags, 0, sizeof(unsigned), s));
+    while (st == GABP_E_NOT_CONVERGED && c < max_cycles) {
+        CKS(mg_cycle(mg, 0, mg->levels - 1, nu_pre, nu_post, b, x));
+        ++c;
+        CK(cudaMemsetAsync(mg->dstat, 0, sizeof(DevStatus), s));
+        CK(launch_residual(f->L, f->a64, f->diag64, b, x, nullptr, mg->dstat, s));
+        CK(cudaMemcpyAsync(mg->hstat, mg->dstat, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        rr = bits_to_double(mg->hstat->rmax) / bn;
+        gabp_status fs = mg_check_flags(mg);
+        if (fs != GABP_OK) { st = fs; break; }
+        if ((mg->hstat->flags & FLAG_NAN) || !std::isfinite(rr) || rr > kDivergence) { st = fail(GABP_E_DIVERGED, "residual diverged"); break; }
+        if (rr <= tol) st = GABP_OK;
+    }
+    if (st == GABP_E_NOT_CONVERGED) fail(st, "cycle cap reached");
+    if (cycles) *cycles = c;
+    if (relres) *relres = rr;
+    return st;
+}
+
+}  // extern "C"

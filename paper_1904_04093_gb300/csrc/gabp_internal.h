@@ -1,0 +1,93 @@
+// Internal declarations of the GaBP library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/gabp.h"
+
+namespace gabp {
+
+constexpr int KMAX = 16;  // most off-diagonal diagonals the stencil layout takes
+
+// Offsets of the stored diagonals (column - row), ascending, and for each the
+// index of the diagonal holding the reverse edges (offset -off[k]).
+struct StencilParams {
+    int K;
+    int off[KMAX];
+    int krev[KMAX];
+};
+
+// Device status word: residual and rhs maxima (bit patterns of non-negative
+// doubles, ordered like unsigned integers) and error flags.
+struct DevStatus {
+    unsigned long long rmax;
+    unsigned long long bmax;
+    unsigned int flags;
+    unsigned int pad;
+};
+enum : unsigned { FLAG_BREAKDOWN = 1u, FLAG_NAN = 2u };
+
+// Pointers one sweep kernel launch needs (T = float or double, erased).
+struct SweepArgs {
+    int n;
+    const void *a, *c, *diag, *b;
+    const void *Lin, *Min, *Pin, *Bin;
+    void *Lout, *Mout, *Pout, *Bout;
+    double *x;  // beliefs of this sweep (nullable)
+    unsigned *flags;
+};
+
+// Matrix description on the device in one layout.
+struct DevLayout {
+    int kind;  // GABP_LAYOUT_STENCIL or GABP_LAYOUT_CSR
+    int n;
+    int64_t slots;       // K*n (stencil) or symmetrised off-diagonal count (CSR)
+    StencilParams sp;    // stencil
+    const int *rowptr;   // CSR (int32, n+1)
+    const int *col;      // CSR
+    const int *rev;      // CSR reverse-edge index
+};
+
+// ---- launch accounting (kernels.cu) ----
+void count_launches(cudaStream_t s, unsigned long long k);
+unsigned long long launch_count();
+
+// ---- launchers (kernels.cu) ----
+// prec: 0 = double, 1 = float (message precision)
+cudaError_t launch_sweep(const DevLayout &L, int prec, const SweepArgs &a, int block, cudaStream_t s);
+cudaError_t launch_aggregate(const DevLayout &L, int prec, const void *diag, const void *b,
+                             const void *Lm, const void *Mm, void *P, void *B, cudaStream_t s);
+// r = b - A x in double with off-diagonal coefficients a64 = -A (layout slots), max |r|, |b| into st
+cudaError_t launch_residual(const DevLayout &L, const double *a64, const double *diag64,
+                            const double *b, const double *x, double *r, DevStatus *st,
+                            cudaStream_t s);
+cudaError_t launch_convert_d2f(const double *in, float *out, int64_t n, cudaStream_t s);
+cudaError_t launch_copy_vec(const double *in, double *out, int64_t n, cudaStream_t s);
+// out = in / ||in||_inf (scale read from st->rmax) in double, and as precision prec into outT
+cudaError_t launch_scale_rhs(const double *in, const DevStatus *st, double *out, void *outT,
+                             int prec, int64_t n, cudaStream_t s);
+// x += scale * e, scale = ||r||_inf read from st->rmax
+cudaError_t launch_axpy_status(double *x, const double *e, const DevStatus *st, int64_t n,
+                               cudaStream_t s);
+cudaError_t launch_axpy(double *x, const double *e, double alpha, int64_t n, cudaStream_t s);
+// state export / import through the caller's slot map (-1 = no message)
+cudaError_t launch_get_state(const int64_t *slotmap, int64_t nnz, int prec, const void *Lm,
+                             const void *Mm, double *lam, double *m, cudaStream_t s);
+cudaError_t launch_set_state(const int64_t *slotmap, int64_t nnz, int prec, const double *lam,
+                             const double *m, void *Lm, void *Mm, cudaStream_t s);
+cudaError_t launch_edge_grad(int n, const int64_t *indptr, const int *indices, const double *lam,
+                             const double *x, double *dA, cudaStream_t s);
+// a^T[e] = a[rev(e)] (mean-message coefficients of the transposed system)
+cudaError_t launch_transpose_coeffs(const DevLayout &L, int prec, const void *a, void *aT,
+                                    cudaStream_t s);
+// multigrid transfers on square grids (lexicographic, m_f = 2 m_c + 1)
+cudaError_t launch_restrict_fw(const double *rf, int mf, double scale, double *rc, cudaStream_t s);
+cudaError_t launch_prolong_add(const double *ec, int mc, double *xf, cudaStream_t s);
+// y = M x for a dense row-major n x n matrix (coarse-grid solve)
+cudaError_t launch_dense_gemv(const double *M, const double *x, double *y, int n, cudaStream_t s);
+
+}  // namespace gabp

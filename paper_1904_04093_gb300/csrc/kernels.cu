@@ -1,0 +1,687 @@
+// CUDA kernels of the GaBP library (sm_103a).
+//
+// Message state: for the directed edge s -> r (matrix entry (r, s), A_rs != 0,
+// Sec. 2.3) the library stores
+//     L[e] = tilde-Lambda_sr * A_sr   (the message's correction to the diagonal of row r)
+//     M[e] = m_sr                      (its correction to the right-hand side of row r)
+// and per node the aggregates
+//     P_r = A_rr + sum_{e in row r} L[e],   B_r = b_r + sum_{e in row r} M[e].
+// With a_e = -A_rs and c_e = -A_rs * A_sr, the flood update of
+// eq. nonsymmetric_GaBP_rules becomes, for e = (r, s) and its reverse edge
+// rev(e) = (s, r):
+//     d_e = P_s - L[rev(e)]                (node s's precision without r's message)
+//     L'[e] = c_e / d_e,   M'[e] = a_e (B_s - M[rev(e)]) / d_e
+// and the belief of Algorithm 1 is x_r = B_r / P_r, formed from the
+// aggregates before the update.  Every thread owns one row r, so the new
+// aggregates P'_r, B'_r are summed in registers (no atomics, deterministic).
+//
+// Two layouts:
+//  * stencil (per-diagonal): slot e = k*n + r holds the entry (r, r + off[k]);
+//    the reverse edge sits on the diagonal krev[k] (offset -off[k]) at row
+//    r + off[k], so every gather is a contiguous, shifted, coalesced stream
+//    and no index array is read;
+//  * CSR: symmetrised pattern with explicit column and reverse-edge indices.
+// Padded or explicit-zero slots have a_e = 0 and carry the zero message.
+#include <cuda_runtime.h>
+
+#include <atomic>
+
+#include "gabp_internal.h"
+
+namespace gabp {
+
+static std::atomic<unsigned long long> g_launches{0};
+
+// Counts `k` kernel launches enqueued on `s`, unless `s` is being captured
+// into a graph (graph replays are counted by the caller when launched).
+void count_launches(cudaStream_t s, unsigned long long k)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) return;
+    g_launches.fetch_add(k, std::memory_order_relaxed);
+}
+
+unsigned long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
+
+namespace {
+
+template <typename T>
+__device__ __forceinline__ bool bad_den(T d)
+{
+    return d == T(0) || !isfinite(d);
+}
+
+// ---------------------------------------------------------------------------
+// Message sweep, stencil layout
+// ---------------------------------------------------------------------------
+template <typename T, int K>
+__global__ void __launch_bounds__(1024) k_sweep_stencil(
+    int n, StencilParams sp, const T *__restrict__ a, const T *__restrict__ c,
+    const T *__restrict__ diag, const T *__restrict__ b, const T *__restrict__ Lin,
+    const T *__restrict__ Min, const T *__restrict__ Pin, const T *__restrict__ Bin,
+    T *__restrict__ Lout, T *__restrict__ Mout, T *__restrict__ Pout, T *__restrict__ Bout,
+    double *__restrict__ x, unsigned *__restrict__ flags)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const size_t nn = (size_t)n;
+    T pn = diag[r];
+    T bn = b[r];
+    if (x) x[r] = (double)(Bin[r] / Pin[r]);
+    bool bad = false;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const size_t e = (size_t)k * nn + r;
+        const T ae = a[e];
+        T lam = T(0), mu = T(0);
+        if (ae != T(0)) {
+            const int s = r + sp.off[k];
+            const size_t er = (size_t)sp.krev[k] * nn + s;
+            const T d = Pin[s] - Lin[er];
+            bad |= bad_den(d);
+            const T q = T(1) / d;
+            lam = c[e] * q;
+            mu = ae * (Bin[s] - Min[er]) * q;
+        }
+        Lout[e] = lam;
+        Mout[e] = mu;
+        pn += lam;
+        bn += mu;
+    }
+    Pout[r] = pn;
+    Bout[r] = bn;
+    if (bad) atomicOr(flags, FLAG_BREAKDOWN);
+}
+
+// ---------------------------------------------------------------------------
+// Message sweep, CSR layout
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(1024) k_sweep_csr(
+    int n, const int *__restrict__ rowptr, const int *__restrict__ col,
+    const int *__restrict__ rev, const T *__restrict__ a, const T *__restrict__ c,
+    const T *__restrict__ diag, const T *__restrict__ b, const T *__restrict__ Lin,
+    const T *__restrict__ Min, const T *__restrict__ Pin, const T *__restrict__ Bin,
+    T *__restrict__ Lout, T *__restrict__ Mout, T *__restrict__ Pout, T *__restrict__ Bout,
+    double *__restrict__ x, unsigned *__restrict__ flags)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    T pn = diag[r];
+    T bn = b[r];
+    if (x) x[r] = (double)(Bin[r] / Pin[r]);
+    bool bad = false;
+    const int lo = rowptr[r], hi = rowptr[r + 1];
+    for (int e = lo; e < hi; ++e) {
+        const T ae = a[e];
+        T lam = T(0), mu = T(0);
+        if (ae != T(0)) {
+            const int s = col[e];
+            const int er = rev[e];
+            const T d = Pin[s] - Lin[er];
+            bad |= bad_den(d);
+            const T q = T(1) / d;
+            lam = c[e] * q;
+            mu = ae * (Bin[s] - Min[er]) * q;
+        }
+        Lout[e] = lam;
+        Mout[e] = mu;
+        pn += lam;
+        bn += mu;
+    }
+    Pout[r] = pn;
+    Bout[r] = bn;
+    if (bad) atomicOr(flags, FLAG_BREAKDOWN);
+}
+
+// ---------------------------------------------------------------------------
+// Aggregates from a message state: P = diag + sum L, B = b + sum M (per row)
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_aggregate_stencil(int n, int K, const T *__restrict__ diag,
+                                    const T *__restrict__ b, const T *__restrict__ Lm,
+                                    const T *__restrict__ Mm, T *__restrict__ P,
+                                    T *__restrict__ B)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    T p = diag[r], q = b[r];
+    for (int k = 0; k < K; ++k) {
+        p += Lm[(size_t)k * n + r];
+        q += Mm[(size_t)k * n + r];
+    }
+    P[r] = p;
+    B[r] = q;
+}
+
+template <typename T>
+__global__ void k_aggregate_csr(int n, const int *__restrict__ rowptr, const T *__restrict__ diag,
+                                const T *__restrict__ b, const T *__restrict__ Lm,
+                                const T *__restrict__ Mm, T *__restrict__ P, T *__restrict__ B)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    T p = diag[r], q = b[r];
+    for (int e = rowptr[r]; e < rowptr[r + 1]; ++e) {
+        p += Lm[e];
+        q += Mm[e];
+    }
+    P[r] = p;
+    B[r] = q;
+}
+
+// ---------------------------------------------------------------------------
+// Residual r = b - A x in double with max |r|, max |b| (block reduction, then
+// one atomicMax per block on the bit pattern of a non-negative double).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void reduce_and_publish(double rmax, double bmax, bool nan,
+                                                   DevStatus *st)
+{
+    __shared__ double sr[32], sb[32];
+    __shared__ int snan;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (threadIdx.x == 0) snan = 0;
+    __syncthreads();
+    for (int o = 16; o > 0; o >>= 1) {
+        rmax = fmax(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
+        bmax = fmax(bmax, __shfl_xor_sync(0xffffffffu, bmax, o));
+    }
+    if (nan) snan = 1;
+    if (lane == 0) {
+        sr[wid] = rmax;
+        sb[wid] = bmax;
+    }
+    __syncthreads();
+    if (wid == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        rmax = lane < nw ? sr[lane] : 0.0;
+        bmax = lane < nw ? sb[lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) {
+            rmax = fmax(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
+            bmax = fmax(bmax, __shfl_xor_sync(0xffffffffu, bmax, o));
+        }
+        if (lane == 0) {
+            atomicMax(&st->rmax, (unsigned long long)__double_as_longlong(rmax));
+            atomicMax(&st->bmax, (unsigned long long)__double_as_longlong(bmax));
+            if (snan) atomicOr(&st->flags, FLAG_NAN);
+        }
+    }
+}
+
+template <int K>
+__global__ void __launch_bounds__(256) k_residual_stencil(
+    int n, StencilParams sp, const double *__restrict__ a64, const double *__restrict__ diag64,
+    const double *__restrict__ b, const double *__restrict__ x, double *__restrict__ r,
+    DevStatus *st)
+{
+    double rmax = 0.0, bmax = 0.0;
+    bool nan = false;
+    const size_t nn = (size_t)n;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double bi = b[i];
+        double acc = bi - diag64[i] * x[i];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const double ae = a64[(size_t)k * nn + i];
+            if (ae != 0.0) acc += ae * x[i + sp.off[k]];
+        }
+        if (r) r[i] = acc;
+        const double v = fabs(acc);
+        if (v != v) nan = true;
+        else rmax = fmax(rmax, v);
+        bmax = fmax(bmax, fabs(bi));
+    }
+    reduce_and_publish(rmax, bmax, nan, st);
+}
+
+__global__ void __launch_bounds__(256) k_residual_csr(
+    int n, const int *__restrict__ rowptr, const int *__restrict__ col,
+    const double *__restrict__ a64, const double *__restrict__ diag64,
+    const double *__restrict__ b, const double *__restrict__ x, double *__restrict__ r,
+    DevStatus *st)
+{
+    double rmax = 0.0, bmax = 0.0;
+    bool nan = false;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double bi = b[i];
+        double acc = bi - diag64[i] * x[i];
+        for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+            const double ae = a64[e];
+            if (ae != 0.0) acc += ae * x[col[e]];
+        }
+        if (r) r[i] = acc;
+        const double v = fabs(acc);
+        if (v != v) nan = true;
+        else rmax = fmax(rmax, v);
+        bmax = fmax(bmax, fabs(bi));
+    }
+    reduce_and_publish(rmax, bmax, nan, st);
+}
+
+// ---------------------------------------------------------------------------
+// Small vector kernels
+// ---------------------------------------------------------------------------
+__global__ void k_d2f(const double *__restrict__ in, float *__restrict__ out, int64_t n)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = (float)in[i];
+}
+
+__global__ void k_copy(const double *__restrict__ in, double *__restrict__ out, int64_t n)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = in[i];
+}
+
+template <typename T>
+__global__ void k_scale_rhs(const double *__restrict__ in, const DevStatus *st,
+                            double *__restrict__ out, T *__restrict__ outT, int64_t n)
+{
+    const double s = __longlong_as_double((long long)st->rmax);
+    const double inv = s > 0.0 ? 1.0 / s : 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double v = in[i] * inv;
+        out[i] = v;
+        if (outT) outT[i] = (T)v;
+    }
+}
+
+__global__ void k_axpy_status(double *__restrict__ x, const double *__restrict__ e,
+                              const DevStatus *st, int64_t n)
+{
+    const double s = __longlong_as_double((long long)st->rmax);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        x[i] += s * e[i];
+}
+
+__global__ void k_axpy(double *__restrict__ x, const double *__restrict__ e, double alpha,
+                       int64_t n)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        x[i] += alpha * e[i];
+}
+
+template <typename T>
+__global__ void k_get_state(const int64_t *__restrict__ slotmap, int64_t nnz,
+                            const T *__restrict__ Lm, const T *__restrict__ Mm,
+                            double *__restrict__ lam, double *__restrict__ m)
+{
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nnz;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t q = slotmap[p];
+        if (lam) lam[p] = q < 0 ? 0.0 : (double)Lm[q];
+        if (m) m[p] = q < 0 ? 0.0 : (double)Mm[q];
+    }
+}
+
+template <typename T>
+__global__ void k_set_state(const int64_t *__restrict__ slotmap, int64_t nnz,
+                            const double *__restrict__ lam, const double *__restrict__ m,
+                            T *__restrict__ Lm, T *__restrict__ Mm)
+{
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nnz;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t q = slotmap[p];
+        if (q < 0) continue;
+        if (lam) Lm[q] = (T)lam[p];
+        if (m) Mm[q] = (T)m[p];
+    }
+}
+
+__global__ void k_edge_grad(int n, const int64_t *__restrict__ indptr,
+                            const int *__restrict__ indices, const double *__restrict__ lam,
+                            const double *__restrict__ x, double *__restrict__ dA)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double li = lam[i];
+    for (int64_t p = indptr[i]; p < indptr[i + 1]; ++p) dA[p] = -li * x[indices[p]];
+}
+
+// Full weighting (Trottenberg eq. 2.3.3) onto the coarse point (I, J) = fine (2I+1, 2J+1).
+__global__ void k_restrict_fw(const double *__restrict__ rf, int mf, double scale,
+                              double *__restrict__ rc)
+{
+    const int mc = (mf - 1) / 2;
+    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)mc * mc) return;
+    const int I = (int)(idx % mc), J = (int)(idx / mc);
+    const int64_t f = (int64_t)(2 * J + 1) * mf + (2 * I + 1);
+    const double ctr = rf[f];
+    const double edg = rf[f - 1] + rf[f + 1] + rf[f - mf] + rf[f + mf];
+    const double crn = rf[f - mf - 1] + rf[f - mf + 1] + rf[f + mf - 1] + rf[f + mf + 1];
+    rc[idx] = scale * (4.0 * ctr + 2.0 * edg + crn) * (1.0 / 16.0);
+}
+
+__device__ __forceinline__ double coarse_at(const double *__restrict__ ec, int mc, int I, int J)
+{
+    return (I >= 0 && I < mc && J >= 0 && J < mc) ? ec[(int64_t)J * mc + I] : 0.0;
+}
+
+// Bilinear interpolation (Trottenberg eq. 2.3.7) added onto the fine grid.
+__global__ void k_prolong_add(const double *__restrict__ ec, int mc, double *__restrict__ xf)
+{
+    const int mf = 2 * mc + 1;
+    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)mf * mf) return;
+    const int fx = (int)(idx % mf), fy = (int)(idx / mf);
+    double v;
+    if (fx & 1) {
+        const int I = (fx - 1) >> 1;
+        if (fy & 1) v = coarse_at(ec, mc, I, (fy - 1) >> 1);
+        else v = 0.5 * (coarse_at(ec, mc, I, (fy >> 1) - 1) + coarse_at(ec, mc, I, fy >> 1));
+    } else {
+        const int I0 = (fx >> 1) - 1, I1 = fx >> 1;
+        if (fy & 1) {
+            const int J = (fy - 1) >> 1;
+            v = 0.5 * (coarse_at(ec, mc, I0, J) + coarse_at(ec, mc, I1, J));
+        } else {
+            const int J0 = (fy >> 1) - 1, J1 = fy >> 1;
+            v = 0.25 * (coarse_at(ec, mc, I0, J0) + coarse_at(ec, mc, I1, J0) +
+                        coarse_at(ec, mc, I0, J1) + coarse_at(ec, mc, I1, J1));
+        }
+    }
+    xf[idx] += v;
+}
+
+// y = M x, one warp per row of a dense row-major matrix.
+__global__ void k_dense_gemv(const double *__restrict__ M, const double *__restrict__ x,
+                             double *__restrict__ y, int n)
+{
+    const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (row >= n) return;
+    const double *Mr = M + (int64_t)row * n;
+    double acc = 0.0;
+    for (int j = lane; j < n; j += 32) acc += Mr[j] * x[j];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) y[row] = acc;
+}
+
+// Mean-message coefficients of the transposed system: a^T[e] = a[rev(e)].
+template <typename T>
+__global__ void k_transpose_stencil(int n, StencilParams sp, const T *__restrict__ a,
+                                    T *__restrict__ aT)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    for (int k = 0; k < sp.K; ++k) {
+        const int s = r + sp.off[k];
+        T v = T(0);
+        if (s >= 0 && s < n) v = a[(size_t)sp.krev[k] * n + s];
+        aT[(size_t)k * n + r] = v;
+    }
+}
+
+template <typename T>
+__global__ void k_transpose_csr(int64_t slots, const int *__restrict__ rev, const T *__restrict__ a,
+                                T *__restrict__ aT)
+{
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < slots;
+         e += (int64_t)gridDim.x * blockDim.x)
+        aT[e] = a[rev[e]];
+}
+
+inline int grid_for(int64_t n, int block, int cap = 152 * 32)
+{
+    int64_t g = (n + block - 1) / block;
+    if (g < 1) g = 1;
+    if (g > cap) g = cap;
+    return (int)g;
+}
+
+template <typename T>
+cudaError_t sweep_stencil_T(const DevLayout &L, const SweepArgs &a, int block, cudaStream_t s)
+{
+    const int grid = (int)((L.n + block - 1) / block);
+    const T *A = (const T *)a.a, *C = (const T *)a.c, *D = (const T *)a.diag, *Bv = (const T *)a.b;
+    const T *Li = (const T *)a.Lin, *Mi = (const T *)a.Min, *Pi = (const T *)a.Pin,
+            *Bi = (const T *)a.Bin;
+    T *Lo = (T *)a.Lout, *Mo = (T *)a.Mout, *Po = (T *)a.Pout, *Bo = (T *)a.Bout;
+#define GABP_SWEEP_CASE(KK)                                                                 \
+    case KK:                                                                                \
+        k_sweep_stencil<T, KK><<<grid, block, 0, s>>>(L.n, L.sp, A, C, D, Bv, Li, Mi, Pi,  \
+                                                       Bi, Lo, Mo, Po, Bo, a.x, a.flags); \
+        break;
+    switch (L.sp.K) {
+        GABP_SWEEP_CASE(0)
+        GABP_SWEEP_CASE(2)
+        GABP_SWEEP_CASE(4)
+        GABP_SWEEP_CASE(6)
+        GABP_SWEEP_CASE(8)
+        GABP_SWEEP_CASE(10)
+        GABP_SWEEP_CASE(12)
+        GABP_SWEEP_CASE(14)
+        GABP_SWEEP_CASE(16)
+        default:
+            return cudaErrorInvalidValue;
+    }
+#undef GABP_SWEEP_CASE
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t sweep_csr_T(const DevLayout &L, const SweepArgs &a, int block, cudaStream_t s)
+{
+    const int grid = (int)((L.n + block - 1) / block);
+    k_sweep_csr<T><<<grid, block, 0, s>>>(
+        L.n, L.rowptr, L.col, L.rev, (const T *)a.a, (const T *)a.c, (const T *)a.diag,
+        (const T *)a.b, (const T *)a.Lin, (const T *)a.Min, (const T *)a.Pin, (const T *)a.Bin,
+        (T *)a.Lout, (T *)a.Mout, (T *)a.Pout, (T *)a.Bout, a.x, a.flags);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_sweep(const DevLayout &L, int prec, const SweepArgs &a, int block,
+                         cudaStream_t s)
+{
+    if (L.n == 0) return cudaSuccess;
+    count_launches(s, 1);
+    if (L.kind == GABP_LAYOUT_STENCIL)
+        return prec == 0 ? sweep_stencil_T<double>(L, a, block, s)
+                         : sweep_stencil_T<float>(L, a, block, s);
+    return prec == 0 ? sweep_csr_T<double>(L, a, block, s) : sweep_csr_T<float>(L, a, block, s);
+}
+
+cudaError_t launch_aggregate(const DevLayout &L, int prec, const void *diag, const void *b,
+                             const void *Lm, const void *Mm, void *P, void *B, cudaStream_t s)
+{
+    if (L.n == 0) return cudaSuccess;
+    const int block = 256, grid = (L.n + block - 1) / block;
+    if (L.kind == GABP_LAYOUT_STENCIL) {
+        if (prec == 0)
+            k_aggregate_stencil<double><<<grid, block, 0, s>>>(
+                L.n, L.sp.K, (const double *)diag, (const double *)b, (const double *)Lm,
+                (const double *)Mm, (double *)P, (double *)B);
+        else
+            k_aggregate_stencil<float><<<grid, block, 0, s>>>(
+                L.n, L.sp.K, (const float *)diag, (const float *)b, (const float *)Lm,
+                (const float *)Mm, (float *)P, (float *)B);
+    } else {
+        if (prec == 0)
+            k_aggregate_csr<double><<<grid, block, 0, s>>>(
+                L.n, L.rowptr, (const double *)diag, (const double *)b, (const double *)Lm,
+                (const double *)Mm, (double *)P, (double *)B);
+        else
+            k_aggregate_csr<float><<<grid, block, 0, s>>>(
+                L.n, L.rowptr, (const float *)diag, (const float *)b, (const float *)Lm,
+                (const float *)Mm, (float *)P, (float *)B);
+    }
+    count_launches(s, 1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_residual(const DevLayout &L, const double *a64, const double *diag64,
+                            const double *b, const double *x, double *r, DevStatus *st,
+                            cudaStream_t s)
+{
+    if (L.n == 0) return cudaSuccess;
+    const int block = 256, grid = grid_for(L.n, block, 152 * 8);
+    if (L.kind == GABP_LAYOUT_STENCIL) {
+#define GABP_RES_CASE(KK)                                                                \
+    case KK:                                                                             \
+        k_residual_stencil<KK><<<grid, block, 0, s>>>(L.n, L.sp, a64, diag64, b, x, r, st); \
+        break;
+        switch (L.sp.K) {
+            GABP_RES_CASE(0)
+            GABP_RES_CASE(2)
+            GABP_RES_CASE(4)
+            GABP_RES_CASE(6)
+            GABP_RES_CASE(8)
+            GABP_RES_CASE(10)
+            GABP_RES_CASE(12)
+            GABP_RES_CASE(14)
+            GABP_RES_CASE(16)
+            default:
+                return cudaErrorInvalidValue;
+        }
+#undef GABP_RES_CASE
+    } else {
+        k_residual_csr<<<grid, block, 0, s>>>(L.n, L.rowptr, L.col, a64, diag64, b, x, r, st);
+    }
+    count_launches(s, 1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_convert_d2f(const double *in, float *out, int64_t n, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    k_d2f<<<grid_for(n, 256), 256, 0, s>>>(in, out, n);
+    count_launches(s, 1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_copy_vec(const double *in, double *out, int64_t n, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    k_copy<<<grid_for(n, 256), 256, 0, s>>>(in, out, n);
+    count_launches(s, 1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scale_rhs(const double *in, const DevStatus *st, double *out, void *outT,
+                             int prec, int64_t n, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    if (prec == 0 || outT == nullptr)
+        k_scale_rhs<double><<<grid_for(n, 256), 256, 0, s>>>(in, st, out, nullptr, n);
+    else
+        k_scale_rhs<float><<<grid_for(n, 256), 256, 0, s>>>(in, st, out, (float *)outT, n);
+    count_launches(s, 1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_axpy_status(double *x, const double *e, const DevStatus *st, int64_t n,
+                               cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    k_axpy_status<<<grid_for(n, 256), 256, 0, s>>>(x, e, st, n);
+    count_launches(s, 1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_axpy(double *x, const double *e, double alpha, int64_t n, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    k_axpy<<<grid_for(n, 256), 256, 0, s>>>(x, e, alpha, n);
+    count_launches(s, 1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_get_state(const int64_t *slotmap, int64_t nnz, int prec, const void *Lm,
+                             const void *Mm, double *lam, double *m, cudaStream_t s)
+{
+    if (nnz == 0) return cudaSuccess;
+    if (prec == 0)
+        k_get_state<double><<<grid_for(nnz, 256), 256, 0, s>>>(
+            slotmap, nnz, (const double *)Lm, (const double *)Mm, lam, m);
+    else
+        k_get_state<float><<<grid_for(nnz, 256), 256, 0, s>>>(
+            slotmap, nnz, (const float *)Lm, (const float *)Mm, lam, m);
+    count_launches(s, 1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_state(const int64_t *slotmap, int64_t nnz, int prec, const double *lam,
+                             const double *m, void *Lm, void *Mm, cudaStream_t s)
+{
+    if (nnz == 0) return cudaSuccess;
+    if (prec == 0)
+        k_set_state<double><<<grid_for(nnz, 256), 256, 0, s>>>(slotmap, nnz, lam, m,
+                                                               (double *)Lm, (double *)Mm);
+    else
+        k_set_state<float><<<grid_for(nnz, 256), 256, 0, s>>>(slotmap, nnz, lam, m,
+                                                              (float *)Lm, (float *)Mm);
+    count_launches(s, 1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_edge_grad(int n, const int64_t *indptr, const int *indices, const double *lam,
+                             const double *x, double *dA, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    k_edge_grad<<<(n + 255) / 256, 256, 0, s>>>(n, indptr, indices, lam, x, dA);
+    count_launches(s, 1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_restrict_fw(const double *rf, int mf, double scale, double *rc, cudaStream_t s)
+{
+    const int mc = (mf - 1) / 2;
+    const int64_t nc = (int64_t)mc * mc;
+    if (nc == 0) return cudaSuccess;
+    k_restrict_fw<<<(int)((nc + 255) / 256), 256, 0, s>>>(rf, mf, scale, rc);
+    count_launches(s, 1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prolong_add(const double *ec, int mc, double *xf, cudaStream_t s)
+{
+    const int64_t nf = (int64_t)(2 * mc + 1) * (2 * mc + 1);
+    k_prolong_add<<<(int)((nf + 255) / 256), 256, 0, s>>>(ec, mc, xf);
+    count_launches(s, 1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dense_gemv(const double *M, const double *x, double *y, int n, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    const int rows_per_block = 8;
+    k_dense_gemv<<<(n + rows_per_block - 1) / rows_per_block, 32 * rows_per_block, 0, s>>>(M, x,
+                                                                                          y, n);
+    count_launches(s, 1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_transpose_coeffs(const DevLayout &L, int prec, const void *a, void *aT,
+                                    cudaStream_t s)
+{
+    if (L.n == 0) return cudaSuccess;
+    if (L.kind == GABP_LAYOUT_STENCIL) {
+        const int grid = (L.n + 255) / 256;
+        if (prec == 0)
+            k_transpose_stencil<double><<<grid, 256, 0, s>>>(L.n, L.sp, (const double *)a,
+                                                              (double *)aT);
+        else
+            k_transpose_stencil<float><<<grid, 256, 0, s>>>(L.n, L.sp, (const float *)a,
+                                                             (float *)aT);
+    } else {
+        if (L.slots == 0) return cudaSuccess;
+        if (prec == 0)
+            k_transpose_csr<double><<<grid_for(L.slots, 256), 256, 0, s>>>(
+                L.slots, L.rev, (const double *)a, (double *)aT);
+        else
+            k_transpose_csr<float><<<grid_for(L.slots, 256), 256, 0, s>>>(
+                L.slots, L.rev, (const float *)a, (float *)aT);
+    }
+    count_launches(s, 1);
+    return cudaGetLastError();
+}
+
+}  // namespace gabp

@@ -1,0 +1,353 @@
+"""GPU parity: the CUDA library through its C ABI against the FP64 CPU oracle.
+
+Tolerances (double precision): one sweep from an identical state <= 1e-12
+relative (max-norm error over the max-norm of the oracle's value), a
+50-sweep trajectory <= 1e-10, converged solutions <= 1e-10.  Float results
+state their error against the oracle in the assertion bounds.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import problems as P
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device="cuda")
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    if a.size == 0:
+        return 0.0
+    scale = max(np.max(np.abs(b)), 1e-300)
+    return float(np.max(np.abs(a - b)) / scale)
+
+
+def figure_4x4():
+    return P.dense_to_csr(np.array([[4.0, -1.0, 1.5, 0.0],
+                                    [0.0, 5.0, -2.0, 1.0],
+                                    [-1.0, 0.5, 6.0, -2.0],
+                                    [0.0, 0.0, 0.0, 3.0]]))
+
+
+def matrices():
+    rng = np.random.default_rng(77)
+    return {
+        "c1_32": P.config_c1()[0],
+        "lognormal_33": P.convdiff_5pt(33, P.lognormal_field(33, 0.5, rng), (1.91, 0.59)),
+        "aniso9_31": P.convdiff_9pt_aniso(31, 0.01, (1.91, 0.59)),
+        "tridiag_64": P.tridiag(64, 2.0, -1.2, -0.8),
+        "random_300": P.random_m_matrix(300, 0.02, 5, nonsym_pattern=True),
+        "toy5": P.paper_toy5_pattern(),
+        "figure_4x4": figure_4x4(),
+        "paper_7x7": P.dense_to_csr(np.loadtxt(__file__.replace("test_gpu_parity.py", "golden/paper_7x7.txt"))),
+    }
+
+
+MATS = matrices()
+CONVERGENT = [k for k in MATS if k != "paper_7x7"]
+
+
+@pytest.fixture(scope="module")
+def g():
+    import paper_1904_04093_gb300 as g
+    g.load()
+    assert torch.cuda.is_available()
+    return g
+
+
+def _rhs(n, seed=0):
+    return np.random.default_rng(seed).uniform(-1.0, 1.0, n)
+
+
+@pytest.mark.parametrize("layout", ["auto", "csr"])
+@pytest.mark.parametrize("name", list(MATS))
+def test_single_sweep_from_injected_state(g, name, layout):
+    A = MATS[name]
+    b = _rhs(A.n, 1)
+    # a realistic precision state (a few sweeps) and random mean messages
+    lt, mm = oracle.zero_state(A)
+    oracle.sweeps(A, _rhs(A.n, 2), 3, lt, mm)
+    edge = (A.data != 0) & (np.repeat(np.arange(A.n), np.diff(A.indptr)) != A.indices)
+    mm = np.where(edge, np.random.default_rng(3).uniform(-1, 1, A.nnz), 0.0)
+    x_o, beta_o = oracle.beliefs(A, b, lt, mm)
+    lt2, mm2, st = oracle.update(A, b, lt, mm)
+    assert st == oracle.OK
+    s = g.GabpSolver(A, "fp64", layout=layout)
+    s.set_state(dev(oracle.diag_contrib(A, lt)), dev(mm))
+    x = s.sweep(dev(b), 1)
+    lam, m = s.get_state()
+    assert rel(host(x), x_o) <= 1e-12
+    assert rel(host(lam), oracle.diag_contrib(A, lt2)) <= 1e-12
+    assert rel(host(m), mm2) <= 1e-12
+    s.close()
+
+
+@pytest.mark.parametrize("name", CONVERGENT)
+def test_trajectory_50_sweeps(g, name):
+    A = MATS[name]
+    b = _rhs(A.n, 4)
+    lt, mm = oracle.zero_state(A)
+    x_o, _, _ = oracle.sweeps(A, b, 50, lt, mm)
+    s = g.GabpSolver(A, "fp64")
+    x = s.sweep(dev(b), 50)
+    lam, m = s.get_state()
+    assert rel(host(x), x_o) <= 1e-10
+    assert rel(host(lam), oracle.diag_contrib(A, lt)) <= 1e-10
+    assert rel(host(m), mm) <= 1e-10
+
+
+@pytest.mark.parametrize("graphs", [True, False])
+@pytest.mark.parametrize("name", ["c1_32", "lognormal_33", "aniso9_31", "random_300", "toy5"])
+def test_solve_matches_oracle_every_sweep(g, name, graphs):
+    A = MATS[name]
+    b = _rhs(A.n, 5)
+    ref = oracle.solve(A, b, 1e-10, 3000)
+    assert ref["status"] == oracle.OK
+    s = g.GabpSolver(A, "fp64", check_every=1, use_graphs=graphs)
+    x, it, rr, st = s.solve(dev(b), 1e-10, 3000)
+    assert st == g.OK
+    assert it == ref["iters"]
+    assert rr <= 1e-10
+    assert rel(host(x), ref["x"]) <= 1e-10
+
+
+def test_solve_c1_workload(g):
+    """Plain FP64 GaBP on the 32x32 convection-diffusion workload: rr <= 1e-10 within 500 sweeps."""
+    A, b = P.config_c1()
+    ref = oracle.solve(A, b, 1e-10, 500)
+    s = g.GabpSolver(A, "fp64", check_every=10)
+    x, it, rr, st = s.solve(dev(b), 1e-10, 500)
+    assert st == g.OK and rr <= 1e-10
+    assert it == int(math.ceil(ref["iters"] / 10.0)) * 10
+    xs = np.linalg.solve(A.to_dense(), b)
+    assert rel(host(x), xs) <= 1e-9
+    # the iterate after the same number of sweeps is the oracle's
+    lt, mm = oracle.zero_state(A)
+    x_o, _, _ = oracle.sweeps(A, b, it, lt, mm)
+    assert rel(host(x), x_o) <= 1e-10
+
+
+def test_tree_exact_at_diameter_plus_one_gpu(g):
+    A = MATS["tridiag_64"]
+    b = _rhs(64, 6)
+    xs = np.linalg.solve(A.to_dense(), b)
+    s = g.GabpSolver(A, "fp64")
+    x63 = host(s.sweep(dev(b), 63))
+    s.reset()
+    x64 = host(s.sweep(dev(b), 64))
+    assert rel(x63, xs) > 1e-6
+    assert rel(x64, xs) <= 1e-13
+
+
+def test_lfa_first_sweeps_gpu(g):
+    m = 9
+    A = P.convdiff_5pt(m, None, (0.0, 0.0))
+    b = _rhs(m * m, 7)
+    s = g.GabpSolver(A, "fp64")
+    x1 = host(s.sweep(dev(b), 1))
+    np.testing.assert_allclose(x1, b / 4.0, rtol=1e-15)
+    s.reset()
+    x2 = host(s.sweep(dev(b), 2)).reshape(m, m)
+    B = b.reshape(m, m)
+    nb = B[:-2, 1:-1] + B[2:, 1:-1] + B[1:-1, :-2] + B[1:-1, 2:]
+    np.testing.assert_allclose(x2[1:-1, 1:-1], (4 * B[1:-1, 1:-1] + nb) / 12.0, rtol=1e-14)
+
+
+def test_divergence_detected(g):
+    A = MATS["paper_7x7"]
+    b = _rhs(7, 1)
+    assert oracle.solve(A, b, 1e-12, 1000)["status"] == oracle.DIVERGED
+    s = g.GabpSolver(A, "fp64")
+    _, _, _, st = s.solve(dev(b), 1e-12, 1000)
+    assert st == g.DIVERGED
+
+
+def test_breakdown_detected(g):
+    # star: the message from the centre to one leaf has denominator
+    # A_00 + tilde-Lambda_20 A_20 = 1 - 1 = 0 at the second sweep
+    A = P.dense_to_csr(np.array([[1.0, 1.0, 1.0], [1.0, 1.0, 0.0], [1.0, 0.0, 1.0]]))
+    b = np.array([1.0, 2.0, 3.0])
+    assert oracle.solve(A, b, 1e-12, 50)["status"] == oracle.BREAKDOWN
+    s = g.GabpSolver(A, "fp64", check_every=1)
+    _, _, _, st = s.solve(dev(b), 1e-12, 50)
+    assert st == g.BREAKDOWN
+
+
+def test_iteration_cap_returns_last_iterate(g):
+    A, b = P.config_c1()
+    s = g.GabpSolver(A, "fp64", check_every=10)
+    x, it, rr, st = s.solve(dev(b), 1e-14, 27)
+    assert st == g.NOT_CONVERGED and it == 27
+    lt, mm = oracle.zero_state(A)
+    x_o, _, _ = oracle.sweeps(A, b, 27, lt, mm)
+    assert rel(host(x), x_o) <= 1e-12
+    assert rr == pytest.approx(oracle.residual_inf(A, b, x_o) / np.max(np.abs(b)), rel=1e-6)
+
+
+def test_degenerate_sizes(g):
+    # n = 1: x = b / a after one sweep; zero right-hand side; empty matrix
+    A1 = P.dense_to_csr(np.array([[2.5]]))
+    s = g.GabpSolver(A1, "fp64", check_every=1)
+    x, it, rr, st = s.solve(dev([5.0]), 1e-12, 10)
+    assert st == g.OK and host(x)[0] == 2.0 and it == 1
+    A, _ = P.config_c1()
+    s = g.GabpSolver(A, "fp64")
+    x, it, rr, st = s.solve(dev(np.zeros(A.n)), 1e-10, 100)
+    assert st == g.OK and it == 0 and np.all(host(x) == 0.0)
+    A0 = P.CSR(0, np.zeros(1, np.int64), np.zeros(0, np.int32), np.zeros(0))
+    s0 = g.GabpSolver(A0, "fp64")
+    x, it, rr, st = s0.solve(torch.zeros(0, dtype=torch.float64, device="cuda"), 1e-10, 10)
+    assert st == g.OK and it == 0
+
+
+def test_structurally_nonsymmetric_layouts_agree(g):
+    A = MATS["figure_4x4"]
+    b = _rhs(4, 8)
+    xs = np.linalg.solve(A.to_dense(), b)
+    for layout in ("auto", "csr", "stencil"):
+        s = g.GabpSolver(A, "fp64", layout=layout, check_every=1)
+        x, it, rr, st = s.solve(dev(b), 1e-14, 500)
+        assert st == g.OK
+        assert rel(host(x), xs) <= 1e-13
+
+
+# --------------------------------------------------------------------------
+# float messages and mixed precision
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("name", ["c1_32", "lognormal_33", "aniso9_31", "random_300"])
+def test_fp32_sweeps_error_against_oracle(g, name):
+    """Float messages: 50 sweeps stay within 1e-5 relative of the FP64 oracle."""
+    A = MATS[name]
+    b = _rhs(A.n, 9)
+    lt, mm = oracle.zero_state(A)
+    x_o, _, _ = oracle.sweeps(A, b, 50, lt, mm)
+    s = g.GabpSolver(A, "fp32")
+    x = host(s.sweep(dev(b), 50))
+    assert rel(x, x_o) <= 1e-5
+
+
+@pytest.mark.parametrize("name", ["c1_32", "lognormal_33", "aniso9_31", "random_300"])
+def test_mixed_precision_reaches_1e10(g, name):
+    A = MATS[name]
+    b = _rhs(A.n, 10)
+    s = g.GabpSolver(A, "fp32_ir", check_every=5)
+    x, it, rr, st = s.solve(dev(b), 1e-10, 20000)
+    assert st == g.OK and rr <= 1e-10
+    xs = np.linalg.solve(A.to_dense(), b)
+    r = b - A.to_dense() @ host(x)
+    assert np.max(np.abs(r)) / np.max(np.abs(b)) <= 1.05e-10
+    assert rel(host(x), xs) <= 1e-8
+
+
+# --------------------------------------------------------------------------
+# adjoint
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("name", ["c1_32", "lognormal_33", "random_300", "figure_4x4"])
+def test_transpose_solve_matches_oracle(g, name):
+    A = MATS[name]
+    AT = A.transpose()
+    gvec = _rhs(A.n, 11)
+    ref = oracle.solve(AT, gvec, 1e-10, 3000)
+    assert ref["status"] == oracle.OK
+    s = g.GabpSolver(A, "fp64", check_every=1)
+    lam, it, rr, st = s.solve_transpose(dev(gvec), 1e-10, 3000)
+    assert st == g.OK and it == ref["iters"]
+    assert rel(host(lam), ref["x"]) <= 1e-10
+
+
+def test_edge_grad_matches_definition(g):
+    A = MATS["random_300"]
+    b, gv = _rhs(300, 12), _rhs(300, 13)
+    x, lam, dA = oracle.adjoint(A, b, gv)
+    s = g.GabpSolver(A, "fp64")
+    out = host(s.edge_grad(dev(lam), dev(x)))
+    np.testing.assert_array_equal(out, dA)
+
+
+# --------------------------------------------------------------------------
+# multigrid
+# --------------------------------------------------------------------------
+def _hierarchy(mf=31, mc=7, seed=5):
+    return P.config_c3_levels(m_fine=mf, m_coarse=mc, seed=seed)
+
+
+@pytest.mark.parametrize("mode", ["cold", "warm", "persist"])
+def test_vcycle_matches_oracle(g, mode):
+    levels, sides, b = _hierarchy()
+    mo = oracle.MGOracle(levels, sides, mode=mode)
+    solvers = [g.GabpSolver(A, "fp64") for A in levels]
+    mg = g.Multigrid(solvers, sides, mode=mode)
+    xo = np.zeros(levels[0].n)
+    xg = torch.zeros(levels[0].n, dtype=torch.float64, device="cuda")
+    bd = dev(b)
+    for cyc in range(3):
+        xo = mo.vcycle(b, xo, 2, 2)
+        mg.vcycle(bd, xg, 2, 2)
+        assert rel(host(xg), xo) <= 1e-11, f"cycle {cyc}"
+
+
+def test_mg_solve_cold_matches_oracle(g):
+    levels, sides, b = _hierarchy()
+    ref = oracle.MGOracle(levels, sides).solve(b, 1e-10, 200, 3, 3)
+    assert ref["status"] == oracle.OK
+    solvers = [g.GabpSolver(A, "fp64") for A in levels]
+    mg = g.Multigrid(solvers, sides)
+    x, c, rr, st = mg.solve(dev(b), 1e-10, 200, 3, 3)
+    assert st == g.OK and c == ref["cycles"]
+    assert rel(host(x), ref["x"]) <= 1e-9
+
+
+def test_mg_float_smoothing_error_stated(g):
+    """Float smoothing, double residuals: one cycle within 1e-5 of the FP64 oracle."""
+    levels, sides, b = _hierarchy()
+    xo = oracle.MGOracle(levels, sides).vcycle(b, np.zeros(levels[0].n), 2, 2)
+    solvers = [g.GabpSolver(A, "fp32") for A in levels]
+    mg = g.Multigrid(solvers, sides)
+    xg = torch.zeros(levels[0].n, dtype=torch.float64, device="cuda")
+    mg.vcycle(dev(b), xg, 2, 2)
+    assert rel(host(xg), xo) <= 1e-5
+
+
+# --------------------------------------------------------------------------
+# full size (2048 x 2048 convection-diffusion, the bench workload)
+# --------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def c2():
+    return P.config_c2()
+
+
+def test_fullsize_first_sweeps_elementwise(g, c2):
+    A, b = c2
+    lt, mm = oracle.zero_state(A)
+    x_o, _, _ = oracle.sweeps(A, b, 3, lt, mm)
+    s = g.GabpSolver(A, "fp64")
+    assert s.info()["layout"] == "stencil"
+    x = host(s.sweep(dev(b), 3))
+    lam, m = s.get_state()
+    assert rel(x, x_o) <= 1e-12
+    assert rel(host(m), mm) <= 1e-12
+    del lam, m
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32_ir"])
+def test_fullsize_solve_reaches_1e10(g, c2, precision):
+    A, b = c2
+    s = g.GabpSolver(A, precision)
+    x, it, rr, st = s.solve(dev(b), 1e-10, 20000)
+    assert st == g.OK and rr <= 1e-10
+    xh = host(x)
+    r = b - A.matvec(xh)  # independent residual on the host
+    assert np.max(np.abs(r)) / np.max(np.abs(b)) <= 1.05e-10
