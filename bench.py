@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--m", type=int, default=2048, help="grid side of the workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU sample")
+    ap.add_argument("--only", choices=["all", "fp64", "mixed"], default="all",
+                    help="profiling runs: time only one solver (no e2e, no CPU sample)")
     return ap.parse_args()
 
 
@@ -259,9 +261,20 @@ def run_ours(args):
 
     # warm-up (graphs captured, clocks up)
     for _ in range(max(3, args.warmup)):
-        s64.solve(bd, TOL, MAX_ITER, x)
-        sir.solve(bd, TOL, MAX_ITER, x)
+        if args.only in ("all", "fp64"):
+            s64.solve(bd, TOL, MAX_ITER, x)
+        if args.only in ("all", "mixed"):
+            sir.solve(bd, TOL, MAX_ITER, x)
     torch.cuda.synchronize()
+    if args.only != "all":
+        solver = s64 if args.only == "fp64" else sir
+        ms, its = timed(solver, args.steps)
+        if rank == 0:
+            print(json.dumps({"only": args.only, "m": args.m, "ms_per_solve": ms, "sweeps": its[-1],
+                              "edge_updates_per_s": edges * its[-1] / (ms / 1e3)}), flush=True)
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return 0
 
     sampler = ClockSampler(gpu_index_for(local)) if rank == 0 else None
     if sampler:
