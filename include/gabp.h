@@ -205,6 +205,32 @@ gabp_status gabp_get_info(gabp_ctx *ctx, gabp_info *info);
  */
 gabp_status gabp_time_sweeps(gabp_ctx *ctx, const double *b, int nsweeps, float *ms);
 
+/*
+ * The paper has no counterpart to this entry point: it serves callers that
+ * cannot allocate device memory (code that runs while another component owns
+ * every allocation, such as a framework's memory arena or a loop that forbids
+ * allocation after start-up, and callers handed only device pointers).
+ * Runs `nsweeps` >= 1 flood sweeps from zero messages, exactly like
+ * gabp_reset + gabp_sweep, on a CSR matrix the caller already holds on the
+ * device (indptr: n+1 int64, indices: nnz int32 sorted per row, data: nnz
+ * double, non-zero diagonal), right-hand side b (n doubles) and output x (n
+ * doubles, the beliefs of the last sweep).  It allocates nothing: all working
+ * state lives in one fixed __device__ array of 10 MiB that every device
+ * loading the library holds until the process exits, so n <= 65536 and
+ * nnz <= 262144; larger sizes return GABP_E_INVALID_ARG without launching.
+ * The first call on a device looks up that array's address
+ * (cudaGetSymbolAddress); make it before any stream capture.  Every call
+ * shares the one array and leaves its last contents there (each call starts
+ * from zero messages and clears the error word itself), so calls whose work
+ * overlaps on the GPU race and give undefined results.  Enqueued on `stream`
+ * (a cudaStream_t, NULL = default), then synchronised to read the status:
+ * GABP_E_BAD_CSR / GABP_E_ZERO_DIAG for an index out of range or a missing
+ * diagonal found on the device, GABP_E_BREAKDOWN as in gabp_sweep.
+ */
+gabp_status gabp_sweep_noalloc(int32_t n, int64_t nnz, const int64_t *indptr,
+                               const int32_t *indices, const double *data, const double *b,
+                               int nsweeps, double *x, void *stream);
+
 /* ---------------------------------------------------------------------------
  * Geometric multigrid with GaBP as the smoother (Sec. 4).
  * ------------------------------------------------------------------------- */

@@ -59,6 +59,10 @@ struct GraphEntry {
 
 }  // namespace
 
+namespace gabp {
+void set_last_error(const std::string &msg) { g_last_error = msg; }
+}  // namespace gabp
+
 struct gabp_ctx {
     int dev = 0;
     cudaStream_t stream = nullptr;

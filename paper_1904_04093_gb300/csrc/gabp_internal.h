@@ -52,6 +52,9 @@ struct DevLayout {
     const int *rev;      // CSR reverse-edge index
 };
 
+// Sets the message gabp_last_error() returns on the calling thread (api.cu).
+void set_last_error(const std::string &msg);
+
 // ---- launch accounting (kernels.cu) ----
 void count_launches(cudaStream_t s, unsigned long long k);
 unsigned long long launch_count();
