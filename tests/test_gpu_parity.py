@@ -95,6 +95,26 @@ def test_single_sweep_from_injected_state(g, name, layout):
     s.close()
 
 
+@pytest.mark.parametrize("layout", ["stencil", "csr"])
+def test_first_update_within_a_few_ulps(g, layout):
+    """Error bound of the library's double reciprocal (approximation + one
+    third-order Newton-Raphson step): the first message update from zero
+    messages, L = -A_rs A_sr / A_ss and M = -A_rs b_s / A_ss, agrees with the
+    oracle's IEEE divisions to a few ulps, element by element."""
+    A = MATS["lognormal_33"]
+    b = _rhs(A.n, 21)
+    lt, mm = oracle.zero_state(A)
+    oracle.sweeps(A, b, 1, lt, mm)
+    s = g.GabpSolver(A, "fp64", layout=layout)
+    s.sweep(dev(b), 1)
+    lam, m = s.get_state()
+    ref_l = oracle.diag_contrib(A, lt)
+    for got, ref in ((host(lam), ref_l), (host(m), mm)):
+        nz = ref != 0
+        assert np.all(got[~nz] == 0.0)
+        assert np.max(np.abs(got[nz] - ref[nz]) / np.abs(ref[nz])) <= 1e-15
+
+
 @pytest.mark.parametrize("name", CONVERGENT)
 def test_trajectory_50_sweeps(g, name):
     A = MATS[name]
