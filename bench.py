@@ -38,6 +38,9 @@ if ROOT not in sys.path:
 
 TOL = 1e-10
 MAX_ITER = 200000
+IR_INNER_MAX = 2000   # float sweeps per refinement step (restarting early beats long inner solves)
+SM_COUNT = 152
+FP64_PER_CYCLE = 2    # FP64 arithmetic instructions per cycle per SM (GB300)
 
 
 def parse():
@@ -223,8 +226,9 @@ def run_ours(args):
     n = A.n
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
-    s64 = g.GabpSolver(A, "fp64", check_every=10)
-    sir = g.GabpSolver(A, "fp32_ir", check_every=10, ir_inner_tol=1e-4, ir_inner_max=2000)
+    s64 = g.GabpSolver(A, "fp64", check_every=10, freeze_lambda=0)
+    sfz = g.GabpSolver(A, "fp64", check_every=25, freeze_lambda=1)
+    sir = g.GabpSolver(A, "fp32_ir", check_every=25, ir_inner_tol=1e-3, ir_inner_max=IR_INNER_MAX)
     info = s64.info()
     info32 = sir.info()
     edges = int(info["edges"])
@@ -263,6 +267,8 @@ def run_ours(args):
     for _ in range(max(3, args.warmup)):
         if args.only in ("all", "fp64"):
             s64.solve(bd, TOL, MAX_ITER, x)
+        if args.only == "all":
+            sfz.solve(bd, TOL, MAX_ITER, x)
         if args.only in ("all", "mixed"):
             sir.solve(bd, TOL, MAX_ITER, x)
     torch.cuda.synchronize()
@@ -283,9 +289,13 @@ def run_ours(args):
     launches0 = g.launch_count()
     ms64, its64 = timed(s64, args.steps)
     launches = g.launch_count() - launches0
+    ms_fz, its_fz = timed(sfz, args.steps)
     ms_ir, its_ir = timed(sir, args.steps)
-    # dominant kernel: the FP64 message sweep, timed alone on the solver's stream
+    # dominant kernel: the FP64 message sweep, timed alone on the solver's stream;
+    # the others: the mean-message sweeps the frozen and mixed solvers spend their time in
     nsw = 50
+    mean_ms64 = sfz.time_sweeps(bd, nsw, frozen=True) / nsw
+    mean_ms32 = sir.time_sweeps(bd, nsw, frozen=True) / nsw
     sweep_ms64 = s64.time_sweeps(bd, nsw) / nsw
     sweep_ms32 = sir.time_sweeps(bd, nsw) / nsw
     clocks = sampler.stop() if sampler else None
@@ -308,6 +318,7 @@ def run_ours(args):
     ms_e2e = e0.elapsed_time(e1) / args.steps
 
     ms64_max = max_over_ranks(ms64)
+    ms_fz_max = max_over_ranks(ms_fz)
     ms_ir_max = max_over_ranks(ms_ir)
     ms_e2e_max = max_over_ranks(ms_e2e)
     sweeps64 = its64[-1]
@@ -316,6 +327,15 @@ def run_ours(args):
     peak, peak_kind = measured_peaks()
     ach64 = info["sweep_bytes"] / (sweep_ms64 / 1e3) / 1e9
     ach32 = info32["sweep_bytes"] / (sweep_ms32 / 1e3) / 1e9
+    achm64 = info["mean_sweep_bytes"] / (mean_ms64 / 1e3) / 1e9
+    achm32 = info32["mean_sweep_bytes"] / (mean_ms32 / 1e3) / 1e9
+    # FP64 sweep: algorithmic FP64 operations per directed edge (Sec. 2.3 rule in the
+    # stored form): d = P - L (1), 1/d (1), L' = c q (1), B - M (1), M' = a (.) q (2),
+    # P' += L', B' += M' (2) = 8; peak = FP64 instructions per cycle x SMs x SM clock
+    sm_mhz = (clocks or {}).get("sm_mhz") or 2070.0
+    fp64_peak = FP64_PER_CYCLE * SM_COUNT * sm_mhz * 1e6 / 1e12  # T ops/s
+    fp64_ops = 8.0 * edges
+    fp64_ach = fp64_ops / (sweep_ms64 / 1e3) / 1e12
 
     if rank != 0:
         if world > 1:
@@ -352,20 +372,30 @@ def run_ours(args):
         },
         "time_to_1e-10": {
             "fp64_ms": ms64_max, "fp64_sweeps": sweeps64,
+            "fp64_frozen_lambda_ms": ms_fz_max, "fp64_frozen_lambda_sweeps": its_fz[-1],
             "mixed_ms": ms_ir_max, "mixed_float_sweeps": its_ir[-1],
-            "mixed_speedup": ms64_max / ms_ir_max,
+            "mixed_speedup_vs_fp64": ms64_max / ms_ir_max,
+            "mixed_speedup_vs_fp64_frozen_lambda": ms_fz_max / ms_ir_max,
         },
         "roofline": {
-            "kernel": "k_sweep_stencil<double,4> (message sweep)",
-            "bound": "hbm", "achieved": ach64, "peak": peak, "unit": "GB/s",
-            "frac": ach64 / peak, "traffic": None,
-            "bytes_per_launch": info["sweep_bytes"], "launch_ms": sweep_ms64,
-            "peak_source": f"{peak_kind} hbm_gbs",
+            "kernel": "k_sweep_stencil<double,4> (message sweep of the FP64 solve)",
+            "bound": "alu", "achieved": fp64_ach, "peak": fp64_peak, "unit": "TFLOP/s",
+            "frac": fp64_ach / fp64_peak, "traffic": None,
+            "op_convention": "FP64 arithmetic instructions, add/mul/fma/reciprocal = 1 each; "
+                             "8 per directed edge; peak = 2 per cycle per SM x 152 SMs x median SM clock",
+            "launch_ms": sweep_ms64, "hbm_achieved_GBs": ach64, "hbm_frac": ach64 / peak,
+            "bytes_per_launch": info["sweep_bytes"], "hbm_peak_source": f"{peak_kind} hbm_gbs",
         },
-        "roofline_fp32_sweep": {
-            "kernel": "k_sweep_stencil<float,4> (message sweep, mixed solver)",
-            "bound": "hbm", "achieved": ach32, "peak": peak, "unit": "GB/s", "frac": ach32 / peak,
-            "bytes_per_launch": info32["sweep_bytes"], "launch_ms": sweep_ms32,
+        "roofline_other_kernels": {
+            "k_sweep_stencil<float,4>": {"bound": "hbm", "achieved": ach32, "peak": peak, "unit": "GB/s",
+                                         "frac": ach32 / peak, "launch_ms": sweep_ms32,
+                                         "bytes_per_launch": info32["sweep_bytes"]},
+            "k_sweep_mean_stencil<float,4>": {"bound": "hbm", "achieved": achm32, "peak": peak, "unit": "GB/s",
+                                              "frac": achm32 / peak, "launch_ms": mean_ms32,
+                                              "bytes_per_launch": info32["mean_sweep_bytes"]},
+            "k_sweep_mean_stencil<double,4>": {"bound": "hbm", "achieved": achm64, "peak": peak, "unit": "GB/s",
+                                               "frac": achm64 / peak, "launch_ms": mean_ms64,
+                                               "bytes_per_launch": info["mean_sweep_bytes"]},
         },
         "e2e": {"value": e2e_value, "unit": "edge-updates/s", "h2d_bytes_per_step": n * 8,
                 "d2h_bytes_per_step": n * 8, "ms_per_step": ms_e2e_max},

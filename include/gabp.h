@@ -76,10 +76,12 @@ typedef struct {
     int ir_inner_max;    /* GABP_FP32_IR: float sweeps per refinement step, at most */
     double ir_inner_tol; /* GABP_FP32_IR: inner relative residual that ends a refinement step */
     int block_size;      /* threads per block of the sweep kernel (0 = tuned default) */
+    int freeze_lambda;   /* precomputed precision messages (Sec. 4.2): 1 on, 0 off,
+                            -1 default (on for GABP_FP32_IR, off otherwise); see gabp_solve */
 } gabp_options;
 
 /* Fills `opt` with the defaults: FP64, auto layout, check_every 10, graphs on,
- * ir_inner_max 400, ir_inner_tol 1e-4, block_size 0. */
+ * ir_inner_max 400, ir_inner_tol 1e-4, block_size 0, freeze_lambda -1. */
 void gabp_default_options(gabp_options *opt);
 
 /* Text for a status code (static storage). */
@@ -138,7 +140,12 @@ gabp_status gabp_sweep(gabp_ctx *ctx, const double *b, int nsweeps, double *x);
  * runs inside double iterative refinement (x += s e, e from float GaBP on
  * A e = r / s, s = ||r||_inf; tilde-Lambda messages are reused across
  * refinement steps since they do not depend on the right-hand side, Sec.
- * 2.3) and `max_iter` caps the total float sweeps.  x (device, n doubles)
+ * 2.3) and `max_iter` caps the total float sweeps.  With freeze_lambda the
+ * precision messages are frozen once a sweep changes none of them by more
+ * than rounding (1e-14 relative in double, 1e-6 in float): they do not depend
+ * on b (Sec. 2.3) and the paper precomputes them (Sec. 4.2); from then on a
+ * sweep moves only the mean messages with the fixed gains a_e / d_e, which is
+ * the same update up to rounding.  x (device, n doubles)
  * receives the last iterate in every case; iters / relres (host, nullable)
  * receive the sweeps done and the final rr.  b == 0 gives x = 0, rr = 0.
  */
@@ -191,6 +198,7 @@ typedef struct {
     int precision;          /* gabp_precision */
     int64_t slots;          /* message slots per buffer (padded edges) */
     double sweep_bytes;     /* compulsory DRAM bytes of one sweep kernel launch */
+    double mean_sweep_bytes; /* the same for a sweep with frozen precision messages */
     double residual_bytes;  /* compulsory DRAM bytes of one residual kernel launch */
     size_t device_bytes;    /* device memory held by the context */
 } gabp_info;
@@ -198,12 +206,13 @@ typedef struct {
 gabp_status gabp_get_info(gabp_ctx *ctx, gabp_info *info);
 
 /*
- * Times the sweep kernel alone: runs `nsweeps` sweeps exactly like
- * gabp_sweep, with CUDA events recorded on the context's stream around the
- * sweep launches only; *ms receives their total device time.  For the
- * bench's roofline figure.
+ * Times the sweep kernel alone: runs `nsweeps` sweeps like gabp_sweep, with
+ * CUDA events recorded on the context's stream around the sweep launches
+ * only; *ms receives their total device time.  frozen = 1 times the
+ * mean-message sweep of a context whose precision messages a solve has
+ * frozen (GABP_E_INVALID_ARG otherwise).  For the bench's roofline figure.
  */
-gabp_status gabp_time_sweeps(gabp_ctx *ctx, const double *b, int nsweeps, float *ms);
+gabp_status gabp_time_sweeps(gabp_ctx *ctx, const double *b, int nsweeps, int frozen, float *ms);
 
 /*
  * The paper has no counterpart to this entry point: it serves callers that

@@ -39,13 +39,14 @@ class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("layout", ctypes.c_int),
                 ("check_every", ctypes.c_int), ("use_graphs", ctypes.c_int),
                 ("ir_inner_max", ctypes.c_int), ("ir_inner_tol", ctypes.c_double),
-                ("block_size", ctypes.c_int)]
+                ("block_size", ctypes.c_int), ("freeze_lambda", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int32), ("nnz", ctypes.c_int64), ("edges", ctypes.c_int64),
                 ("layout", ctypes.c_int), ("ndiag", ctypes.c_int), ("precision", ctypes.c_int),
                 ("slots", ctypes.c_int64), ("sweep_bytes", ctypes.c_double),
+                ("mean_sweep_bytes", ctypes.c_double),
                 ("residual_bytes", ctypes.c_double), ("device_bytes", ctypes.c_size_t)]
 
 
@@ -85,7 +86,7 @@ def load() -> ctypes.CDLL:
         "gabp_get_state": (I, [P, P, P]),
         "gabp_set_state": (I, [P, P, P]),
         "gabp_get_info": (I, [P, ctypes.POINTER(Info)]),
-        "gabp_time_sweeps": (I, [P, P, I, PF]),
+        "gabp_time_sweeps": (I, [P, P, I, I, PF]),
         "mg_setup": (I, [I, ctypes.POINTER(P), ctypes.POINTER(ctypes.c_int32), D, I, P, ctypes.POINTER(P)]),
         "mg_vcycle": (I, [P, I, I, I, P, P]),
         "mg_solve": (I, [P, P, P, D, I, I, I, PI, PD]),
@@ -142,7 +143,7 @@ class GabpSolver:
 
     def __init__(self, A, precision: str = "fp64", layout: str = "auto", check_every: int = 10,
                  use_graphs: bool = True, ir_inner_max: int = 400, ir_inner_tol: float = 1e-4,
-                 block_size: int = 0, stream=None):
+                 block_size: int = 0, freeze_lambda: int = -1, stream=None):
         L = load()
         torch = _torch()
         self.n = int(A.n)
@@ -159,6 +160,7 @@ class GabpSolver:
         opt.ir_inner_max = int(ir_inner_max)
         opt.ir_inner_tol = float(ir_inner_tol)
         opt.block_size = int(block_size)
+        opt.freeze_lambda = int(freeze_lambda)
         self.precision = precision
         self.device = torch.cuda.current_device()
         self._sh, self.stream = _stream_handle(stream)
@@ -207,10 +209,10 @@ class GabpSolver:
                                  _dev_vec(x, self.n, "x")))
         return x
 
-    def time_sweeps(self, b, nsweeps: int) -> float:
+    def time_sweeps(self, b, nsweeps: int, frozen: bool = False) -> float:
         ms = ctypes.c_float()
         _check(load().gabp_time_sweeps(self._h, _dev_vec(b, self.n, "b"), int(nsweeps),
-                                       ctypes.byref(ms)))
+                                       int(bool(frozen)), ctypes.byref(ms)))
         return float(ms.value)
 
     def _solve(self, fn, b, tol, max_iter, x, raise_on):

@@ -53,7 +53,7 @@ double bits_to_double(unsigned long long u)
 }
 
 struct GraphEntry {
-    int k, parity, transposed;
+    int k, parity, transposed, frozen;
     cudaGraphExec_t exec;
 };
 
@@ -95,7 +95,10 @@ struct gabp_ctx {
     double *bres = nullptr;   // rhs of the residual checks (double)
     double *xbuf = nullptr;   // beliefs of the last sweep of a chunk
     double *b0 = nullptr, *xacc = nullptr, *rbuf = nullptr;  // refinement (lazy)
-    DevStatus *dstat = nullptr;  // [0] chunk checks, [1] refinement / misc
+    void *g = nullptr;           // frozen mean-message gains a_e / d_e (lazy)
+    bool frozen = false;         // precision messages frozen (both L and P buffers equal)
+    bool frozen_transposed = false;
+    DevStatus *dstat = nullptr;  // [0] chunk checks, [1] refinement / misc, [2] Lambda change
     DevStatus *hstat = nullptr;  // pinned host mirror
     std::vector<GraphEntry> graphs;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -352,6 +355,7 @@ void free_all(std::vector<void *> &allocs)
 gabp_status zero_messages(gabp_ctx *ctx, bool lam, bool mean)
 {
     const size_t bytes = (size_t)ctx->L.slots * esz(ctx->prec);
+    if (lam) ctx->frozen = false;
     if (lam) CK(cudaMemsetAsync(ctx->Lm[ctx->cur], 0, bytes, ctx->stream));
     if (mean) CK(cudaMemsetAsync(ctx->Mm[ctx->cur], 0, bytes, ctx->stream));
     return GABP_OK;
@@ -375,10 +379,15 @@ gabp_status aggregate(gabp_ctx *ctx)
 
 int block_of(const gabp_ctx *ctx) { return ctx->opt.block_size > 0 ? ctx->opt.block_size : 256; }
 
-// One sweep from state cur into 1 - cur.
+// One sweep from state cur into 1 - cur (mean messages only while frozen).
 cudaError_t sweep_once(gabp_ctx *ctx, bool transposed, double *x, cudaStream_t s)
 {
     const int c0 = ctx->cur, c1 = c0 ^ 1;
+    if (ctx->frozen) {
+        ctx->cur = c1;
+        return launch_sweep_mean(ctx->L, ctx->prec, ctx->g, ctx->bT, ctx->P[c0], ctx->Mm[c0],
+                                 ctx->B[c0], ctx->Mm[c1], ctx->B[c1], x, block_of(ctx), s);
+    }
     SweepArgs a;
     a.n = ctx->n;
     a.a = transposed ? ctx->aT : ctx->a;
@@ -419,10 +428,11 @@ gabp_status run_chunk(gabp_ctx *ctx, int k, bool transposed)
     if (!ctx->opt.use_graphs) {
         CK(enqueue_chunk(ctx, k, transposed, ctx->stream));
     } else {
-        const int parity = ctx->cur;
+        const int parity = ctx->cur, frozen = ctx->frozen ? 1 : 0;
         cudaGraphExec_t exec = nullptr;
         for (auto &g : ctx->graphs)
-            if (g.k == k && g.parity == parity && g.transposed == (int)transposed) exec = g.exec;
+            if (g.k == k && g.parity == parity && g.transposed == (int)transposed && g.frozen == frozen)
+                exec = g.exec;
         if (!exec) {
             cudaGraph_t graph;
             CK(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
@@ -434,7 +444,7 @@ gabp_status run_chunk(gabp_ctx *ctx, int k, bool transposed)
             e = cudaGraphInstantiate(&exec, graph, 0);
             cudaGraphDestroy(graph);
             if (e != cudaSuccess) return fail_cuda(e, "cudaGraphInstantiate");
-            ctx->graphs.push_back({k, parity, (int)transposed, exec});
+            ctx->graphs.push_back({k, parity, (int)transposed, frozen, exec});
         }
         CK(cudaGraphLaunch(exec, ctx->stream));
         count_launches(ctx->stream, (unsigned long long)k + 1);  // k sweeps + residual
@@ -480,6 +490,44 @@ gabp_status ensure_ir(gabp_ctx *ctx)
     return GABP_OK;
 }
 
+// Freezes the precision messages at the current state: g = a / (P_s - L[rev]),
+// both L buffers and both P buffers set to the current ones.
+gabp_status freeze(gabp_ctx *ctx, bool transposed)
+{
+    const size_t S = (size_t)ctx->L.slots * esz(ctx->prec), NB = (size_t)ctx->n * esz(ctx->prec);
+    if (!ctx->g) CKS(dalloc(ctx, &ctx->g, S));
+    const int c0 = ctx->cur, c1 = c0 ^ 1;
+    CK(launch_freeze(ctx->L, ctx->prec, transposed ? ctx->aT : ctx->a, ctx->P[c0], ctx->Lm[c0],
+                     ctx->g, &ctx->dstat[0].flags, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->Lm[c1], ctx->Lm[c0], S, cudaMemcpyDeviceToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->P[c1], ctx->P[c0], NB, cudaMemcpyDeviceToDevice, ctx->stream));
+    ctx->frozen = true;
+    ctx->frozen_transposed = transposed;
+    return GABP_OK;
+}
+
+// Freezes once the last sweep changed no precision message by more than
+// `rel` times the largest one (rounding level).
+gabp_status maybe_freeze(gabp_ctx *ctx, bool transposed)
+{
+    if (ctx->frozen) return GABP_OK;
+    const double rel = ctx->prec == 0 ? 1e-14 : 1e-6;
+    CK(cudaMemsetAsync(&ctx->dstat[2], 0, sizeof(DevStatus), ctx->stream));
+    CK(launch_lambda_change(ctx->L.slots, ctx->prec, ctx->Lm[ctx->cur ^ 1], ctx->Lm[ctx->cur],
+                            &ctx->dstat[2], ctx->stream));
+    double dmax = 0.0, lmax = 0.0;
+    unsigned fl = 0;
+    CKS(read_status(ctx, 2, &dmax, &lmax, &fl));
+    if (!(fl & FLAG_NAN) && dmax <= rel * lmax) CKS(freeze(ctx, transposed));
+    return GABP_OK;
+}
+
+bool freeze_enabled(const gabp_ctx *ctx)
+{
+    if (ctx->opt.freeze_lambda < 0) return ctx->opt.precision == GABP_FP32_IR;
+    return ctx->opt.freeze_lambda > 0;
+}
+
 // Plain GaBP solve (Algorithm 1, flood schedule) on A or A^T.
 gabp_status solve_plain(gabp_ctx *ctx, const double *b, double *x, double tol, int max_iter,
                         int *iters, double *relres, bool transposed)
@@ -505,7 +553,8 @@ gabp_status solve_plain(gabp_ctx *ctx, const double *b, double *x, double tol, i
             const int k = std::min(every, max_iter - it);
             CKS(run_chunk(ctx, k, transposed));
             it += k;
-            const DevStatus &h = ctx->hstat[0];
+            const DevStatus h = ctx->hstat[0];
+            if (freeze_enabled(ctx) && !(h.flags & FLAG_BREAKDOWN)) CKS(maybe_freeze(ctx, transposed));
             rr = bits_to_double(h.rmax) / binf;
             if (h.flags & FLAG_BREAKDOWN) { st = fail(GABP_E_BREAKDOWN, "zero or non-finite message denominator"); break; }
             if ((h.flags & FLAG_NAN) || !std::isfinite(rr) || rr > kDivergence) { st = fail(GABP_E_DIVERGED, "residual diverged"); break; }
@@ -554,7 +603,8 @@ gabp_status solve_ir(gabp_ctx *ctx, const double *b, double *x, double tol, int 
             CKS(run_chunk(ctx, k, false));
             inner += k;
             total += k;
-            const DevStatus &h = ctx->hstat[0];
+            const DevStatus h = ctx->hstat[0];
+            if (freeze_enabled(ctx) && !(h.flags & FLAG_BREAKDOWN)) CKS(maybe_freeze(ctx, false));
             if (h.flags & FLAG_BREAKDOWN) { st = fail(GABP_E_BREAKDOWN, "zero or non-finite message denominator"); break; }
             const double rin = bits_to_double(h.rmax);  // ||r/s||_inf == 1
             if ((h.flags & FLAG_NAN) || !std::isfinite(rin)) { st = fail(GABP_E_DIVERGED, "inner residual not finite"); break; }
@@ -597,6 +647,7 @@ void gabp_default_options(gabp_options *opt)
     opt->ir_inner_max = 400;
     opt->ir_inner_tol = 1e-4;
     opt->block_size = 0;
+    opt->freeze_lambda = -1;
 }
 
 const char *gabp_status_str(gabp_status s)
@@ -628,7 +679,8 @@ gabp_status gabp_setup(int32_t n, int64_t nnz, const int64_t *indptr, const int3
     gabp_default_options(&o);
     if (opt) o = *opt;
     if (o.precision < 0 || o.precision > 2 || o.layout < 0 || o.layout > 2 || o.check_every < 0 ||
-        o.block_size < 0 || o.block_size > 1024 || (o.block_size % 32) != 0)
+        o.block_size < 0 || o.block_size > 1024 || (o.block_size % 32) != 0 ||
+        o.freeze_lambda < -1 || o.freeze_lambda > 1)
         return fail(GABP_E_INVALID_ARG, "bad option");
     CKS(validate_csr(n, nnz, indptr, indices, data));
     int64_t nonzero_off = 0;
@@ -695,15 +747,15 @@ gabp_status gabp_setup(int32_t n, int64_t nnz, const int64_t *indptr, const int3
     if (ctx->prec == 0) ctx->bT = ctx->bres;
     else if ((s = dalloc(ctx, &ctx->bT, NB)) != GABP_OK) return bail(s);
     if ((s = dalloc(ctx, (void **)&ctx->xbuf, (size_t)n * sizeof(double))) != GABP_OK) return bail(s);
-    if ((s = dalloc(ctx, (void **)&ctx->dstat, 2 * sizeof(DevStatus))) != GABP_OK) return bail(s);
-    e = cudaMallocHost((void **)&ctx->hstat, 2 * sizeof(DevStatus));
+    if ((s = dalloc(ctx, (void **)&ctx->dstat, 3 * sizeof(DevStatus))) != GABP_OK) return bail(s);
+    e = cudaMallocHost((void **)&ctx->hstat, 3 * sizeof(DevStatus));
     if (e != cudaSuccess) return bail(fail_cuda(e, "cudaMallocHost"));
-    std::memset(ctx->hstat, 0, 2 * sizeof(DevStatus));
+    std::memset(ctx->hstat, 0, 3 * sizeof(DevStatus));
     for (int i = 0; i < 2; ++i) {
         if ((e = cudaMemset(ctx->Lm[i], 0, S)) != cudaSuccess) return bail(fail_cuda(e, "cudaMemset"));
         if ((e = cudaMemset(ctx->Mm[i], 0, S)) != cudaSuccess) return bail(fail_cuda(e, "cudaMemset"));
     }
-    if ((e = cudaMemset(ctx->dstat, 0, 2 * sizeof(DevStatus))) != cudaSuccess) return bail(fail_cuda(e, "cudaMemset"));
+    if ((e = cudaMemset(ctx->dstat, 0, 3 * sizeof(DevStatus))) != cudaSuccess) return bail(fail_cuda(e, "cudaMemset"));
     if ((e = cudaDeviceSynchronize()) != cudaSuccess) return bail(fail_cuda(e, "setup"));
     *out = ctx;
     return GABP_OK;
@@ -762,6 +814,7 @@ gabp_status gabp_sweep(gabp_ctx *ctx, const double *b, int nsweeps, double *x)
 {
     if (!ctx || nsweeps < 0 || (!b && ctx->n > 0)) return fail(GABP_E_INVALID_ARG, "bad argument");
     CKS(set_dev(ctx->dev));
+    ctx->frozen = false;  // full sweeps; a frozen state is held in both buffers
     CKS(load_rhs(ctx, b));
     CKS(aggregate(ctx));
     CK(cudaMemsetAsync(&ctx->dstat[0].flags, 0, sizeof(unsigned), ctx->stream));
@@ -772,12 +825,20 @@ gabp_status gabp_sweep(gabp_ctx *ctx, const double *b, int nsweeps, double *x)
     return GABP_OK;
 }
 
-gabp_status gabp_time_sweeps(gabp_ctx *ctx, const double *b, int nsweeps, float *ms)
+gabp_status gabp_time_sweeps(gabp_ctx *ctx, const double *b, int nsweeps, int frozen, float *ms)
 {
-    if (!ctx || nsweeps < 1 || !ms || (!b && ctx->n > 0)) return fail(GABP_E_INVALID_ARG, "bad argument");
+    if (!ctx || nsweeps < 1 || !ms || (!b && ctx->n > 0) || frozen < 0 || frozen > 1)
+        return fail(GABP_E_INVALID_ARG, "bad argument");
+    if (frozen && !ctx->frozen) return fail(GABP_E_INVALID_ARG, "no frozen precision messages in this context");
     CKS(set_dev(ctx->dev));
     CKS(load_rhs(ctx, b));
     CKS(aggregate(ctx));
+    if (frozen) {
+        // the frozen L sits in both buffers; restore the frozen-sweep mode
+        ctx->frozen = true;
+    } else {
+        ctx->frozen = false;
+    }
     CK(cudaMemsetAsync(&ctx->dstat[0].flags, 0, sizeof(unsigned), ctx->stream));
     CK(cudaEventRecord(ctx->ev0, ctx->stream));
     for (int i = 0; i < nsweeps; ++i) CK(sweep_once(ctx, false, nullptr, ctx->stream));
@@ -872,7 +933,11 @@ gabp_status gabp_get_info(gabp_ctx *ctx, gabp_info *info)
         sweep += 8.0 * S + 4.0 * n;
         resid += 4.0 * S + 4.0 * n;
     }
+    // frozen precision messages: per slot g, M[rev] read, M' written; per row b, B read, B' written
+    double mean = 3.0 * p * S + 3.0 * p * n;
+    if (ctx->L.kind == GABP_LAYOUT_CSR) mean += 8.0 * S + 4.0 * n;
     info->sweep_bytes = sweep;
+    info->mean_sweep_bytes = mean;
     info->residual_bytes = resid;
     info->device_bytes = ctx->dev_bytes;
     return GABP_OK;

@@ -84,6 +84,14 @@ cudaError_t launch_set_state(const int64_t *slotmap, int64_t nnz, int prec, cons
                              const double *m, void *Lm, void *Mm, cudaStream_t s);
 cudaError_t launch_edge_grad(int n, const int64_t *indptr, const int *indices, const double *lam,
                              const double *x, double *dA, cudaStream_t s);
+// frozen precision messages: g = a / (P_s - L[rev]); mean-only sweep; convergence of L
+cudaError_t launch_freeze(const DevLayout &L, int prec, const void *a, const void *P, const void *Lm,
+                          void *g, unsigned *flags, cudaStream_t s);
+cudaError_t launch_sweep_mean(const DevLayout &L, int prec, const void *g, const void *b,
+                              const void *P, const void *Min, const void *Bin, void *Mout,
+                              void *Bout, double *x, int block, cudaStream_t s);
+cudaError_t launch_lambda_change(int64_t slots, int prec, const void *L0, const void *L1,
+                                 DevStatus *st, cudaStream_t s);
 // a^T[e] = a[rev(e)] (mean-message coefficients of the transposed system)
 cudaError_t launch_transpose_coeffs(const DevLayout &L, int prec, const void *a, void *aT,
                                     cudaStream_t s);

@@ -177,6 +177,120 @@ __global__ void __launch_bounds__(1024) k_sweep_csr(
 }
 
 // ---------------------------------------------------------------------------
+// Frozen precision messages (the precomputed tilde-Lambda of Sec. 4.2)
+//
+// tilde-Lambda does not depend on b (Sec. 2.3).  Once it has converged, the
+// precision update returns the same values, so a sweep only has to move the
+// mean messages: with the fixed g_e = a_e / d_e, d_e = P_s - L[rev e],
+//     M'[e] = g_e (B_s - M[rev e]),   B'_r = b_r + sum_{e in row r} M'[e],
+// and the beliefs are x_r = B_r / P_r with the fixed P.
+// ---------------------------------------------------------------------------
+template <typename T, int K>
+__global__ void __launch_bounds__(256) k_freeze_stencil(int n, StencilParams sp,
+                                                        const T *__restrict__ a,
+                                                        const T *__restrict__ P,
+                                                        const T *__restrict__ Lm,
+                                                        T *__restrict__ g,
+                                                        unsigned *__restrict__ flags)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const size_t nn = (size_t)n;
+    bool bad = false;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const size_t e = (size_t)k * nn + r;
+        const T ae = a[e];
+        T ge = T(0);
+        if (ae != T(0)) {
+            const int s = r + sp.off[k];
+            const T d = P[s] - Lm[(size_t)sp.krev[k] * nn + s];
+            bad |= bad_den(d);
+            ge = ae * fast_rcp(d);
+        }
+        g[e] = ge;
+    }
+    if (bad) atomicOr(flags, FLAG_BREAKDOWN);
+}
+
+template <typename T>
+__global__ void k_freeze_csr(int n, const int *__restrict__ rowptr, const int *__restrict__ col,
+                             const int *__restrict__ rev, const T *__restrict__ a,
+                             const T *__restrict__ P, const T *__restrict__ Lm,
+                             T *__restrict__ g, unsigned *__restrict__ flags)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    bool bad = false;
+    for (int e = rowptr[r]; e < rowptr[r + 1]; ++e) {
+        const T ae = a[e];
+        T ge = T(0);
+        if (ae != T(0)) {
+            const T d = P[col[e]] - Lm[rev[e]];
+            bad |= bad_den(d);
+            ge = ae * fast_rcp(d);
+        }
+        g[e] = ge;
+    }
+    if (bad) atomicOr(flags, FLAG_BREAKDOWN);
+}
+
+template <typename T, int K>
+__global__ void __launch_bounds__(256) k_sweep_mean_stencil(
+    int n, StencilParams sp, const T *__restrict__ g, const T *__restrict__ b,
+    const T *__restrict__ P, const T *__restrict__ Min, const T *__restrict__ Bin,
+    T *__restrict__ Mout, T *__restrict__ Bout, double *__restrict__ x)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const size_t nn = (size_t)n;
+    T ge[K > 0 ? K : 1], bs[K > 0 ? K : 1], mr[K > 0 ? K : 1];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const size_t e = (size_t)k * nn + r;
+        ge[k] = g[e];
+        int s = r + sp.off[k];
+        s = s < 0 ? 0 : (s >= n ? n - 1 : s);
+        bs[k] = Bin[s];
+        mr[k] = Min[(size_t)sp.krev[k] * nn + s];
+    }
+    T bn = b[r];
+    if (x) x[r] = (double)(Bin[r] / P[r]);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const T mu = ge[k] != T(0) ? ge[k] * (bs[k] - mr[k]) : T(0);
+        Mout[(size_t)k * nn + r] = mu;
+        bn += mu;
+    }
+    Bout[r] = bn;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024) k_sweep_mean_csr(
+    int n, const int *__restrict__ rowptr, const int *__restrict__ col,
+    const int *__restrict__ rev, const T *__restrict__ g, const T *__restrict__ b,
+    const T *__restrict__ P, const T *__restrict__ Min, const T *__restrict__ Bin,
+    T *__restrict__ Mout, T *__restrict__ Bout, double *__restrict__ x)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    T bn = b[r];
+    if (x) x[r] = (double)(Bin[r] / P[r]);
+    for (int e = rowptr[r]; e < rowptr[r + 1]; ++e) {
+        const T ge = g[e];
+        const T mu = ge != T(0) ? ge * (Bin[col[e]] - Min[rev[e]]) : T(0);
+        Mout[e] = mu;
+        bn += mu;
+    }
+    Bout[r] = bn;
+}
+
+// max |L1 - L0| and max |L1| over all slots (convergence of the precision messages)
+template <typename T>
+__global__ void __launch_bounds__(256) k_lambda_change(int64_t slots, const T *__restrict__ L0,
+                                                       const T *__restrict__ L1, DevStatus *st);
+
+// ---------------------------------------------------------------------------
 // Aggregates from a message state: P = diag + sum L, B = b + sum M (per row)
 // ---------------------------------------------------------------------------
 template <typename T>
@@ -298,6 +412,23 @@ __global__ void __launch_bounds__(256) k_residual_csr(
         bmax = fmax(bmax, fabs(bi));
     }
     reduce_and_publish(rmax, bmax, nan, st);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_lambda_change(int64_t slots, const T *__restrict__ L0,
+                                                       const T *__restrict__ L1, DevStatus *st)
+{
+    double dmax = 0.0, lmax = 0.0;
+    bool nan = false;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < slots;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const double l1 = (double)L1[e];
+        const double d = fabs(l1 - (double)L0[e]);
+        if (d != d) nan = true;
+        else dmax = fmax(dmax, d);
+        lmax = fmax(lmax, fabs(l1));
+    }
+    reduce_and_publish(dmax, lmax, nan, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -724,6 +855,116 @@ cudaError_t launch_transpose_coeffs(const DevLayout &L, int prec, const void *a,
                 L.slots, L.rev, (const float *)a, (float *)aT);
     }
     count_launches(s, 1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_freeze(const DevLayout &L, int prec, const void *a, const void *P, const void *Lm,
+                          void *g, unsigned *flags, cudaStream_t s)
+{
+    if (L.n == 0) return cudaSuccess;
+    const int grid = (L.n + 255) / 256;
+    count_launches(s, 1);
+    if (L.kind == GABP_LAYOUT_STENCIL) {
+#define GABP_FRZ_CASE(KK)                                                                     \
+    case KK:                                                                                  \
+        if (prec == 0)                                                                        \
+            k_freeze_stencil<double, KK><<<grid, 256, 0, s>>>(L.n, L.sp, (const double *)a,    \
+                                                              (const double *)P,              \
+                                                              (const double *)Lm, (double *)g, \
+                                                              flags);                         \
+        else                                                                                  \
+            k_freeze_stencil<float, KK><<<grid, 256, 0, s>>>(L.n, L.sp, (const float *)a,      \
+                                                             (const float *)P,                \
+                                                             (const float *)Lm, (float *)g,   \
+                                                             flags);                          \
+        break;
+        switch (L.sp.K) {
+            GABP_FRZ_CASE(0)
+            GABP_FRZ_CASE(2)
+            GABP_FRZ_CASE(4)
+            GABP_FRZ_CASE(6)
+            GABP_FRZ_CASE(8)
+            GABP_FRZ_CASE(10)
+            GABP_FRZ_CASE(12)
+            GABP_FRZ_CASE(14)
+            GABP_FRZ_CASE(16)
+            default:
+                return cudaErrorInvalidValue;
+        }
+#undef GABP_FRZ_CASE
+    } else {
+        if (prec == 0)
+            k_freeze_csr<double><<<grid, 256, 0, s>>>(L.n, L.rowptr, L.col, L.rev, (const double *)a,
+                                                      (const double *)P, (const double *)Lm,
+                                                      (double *)g, flags);
+        else
+            k_freeze_csr<float><<<grid, 256, 0, s>>>(L.n, L.rowptr, L.col, L.rev, (const float *)a,
+                                                     (const float *)P, (const float *)Lm,
+                                                     (float *)g, flags);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sweep_mean(const DevLayout &L, int prec, const void *g, const void *b,
+                              const void *P, const void *Min, const void *Bin, void *Mout,
+                              void *Bout, double *x, int block, cudaStream_t s)
+{
+    if (L.n == 0) return cudaSuccess;
+    count_launches(s, 1);
+    if (L.kind == GABP_LAYOUT_STENCIL) {
+        if (block > 256) block = 256;
+        const int grid = (L.n + block - 1) / block;
+#define GABP_MEAN_CASE(KK)                                                                     \
+    case KK:                                                                                   \
+        if (prec == 0)                                                                         \
+            k_sweep_mean_stencil<double, KK><<<grid, block, 0, s>>>(                           \
+                L.n, L.sp, (const double *)g, (const double *)b, (const double *)P,             \
+                (const double *)Min, (const double *)Bin, (double *)Mout, (double *)Bout, x);  \
+        else                                                                                   \
+            k_sweep_mean_stencil<float, KK><<<grid, block, 0, s>>>(                            \
+                L.n, L.sp, (const float *)g, (const float *)b, (const float *)P,                \
+                (const float *)Min, (const float *)Bin, (float *)Mout, (float *)Bout, x);      \
+        break;
+        switch (L.sp.K) {
+            GABP_MEAN_CASE(0)
+            GABP_MEAN_CASE(2)
+            GABP_MEAN_CASE(4)
+            GABP_MEAN_CASE(6)
+            GABP_MEAN_CASE(8)
+            GABP_MEAN_CASE(10)
+            GABP_MEAN_CASE(12)
+            GABP_MEAN_CASE(14)
+            GABP_MEAN_CASE(16)
+            default:
+                return cudaErrorInvalidValue;
+        }
+#undef GABP_MEAN_CASE
+    } else {
+        const int grid = (L.n + block - 1) / block;
+        if (prec == 0)
+            k_sweep_mean_csr<double><<<grid, block, 0, s>>>(
+                L.n, L.rowptr, L.col, L.rev, (const double *)g, (const double *)b,
+                (const double *)P, (const double *)Min, (const double *)Bin, (double *)Mout,
+                (double *)Bout, x);
+        else
+            k_sweep_mean_csr<float><<<grid, block, 0, s>>>(
+                L.n, L.rowptr, L.col, L.rev, (const float *)g, (const float *)b,
+                (const float *)P, (const float *)Min, (const float *)Bin, (float *)Mout,
+                (float *)Bout, x);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lambda_change(int64_t slots, int prec, const void *L0, const void *L1,
+                                 DevStatus *st, cudaStream_t s)
+{
+    if (slots == 0) return cudaSuccess;
+    count_launches(s, 1);
+    const int grid = grid_for(slots, 256, 152 * 8);
+    if (prec == 0)
+        k_lambda_change<double><<<grid, 256, 0, s>>>(slots, (const double *)L0, (const double *)L1, st);
+    else
+        k_lambda_change<float><<<grid, 256, 0, s>>>(slots, (const float *)L0, (const float *)L1, st);
     return cudaGetLastError();
 }
 

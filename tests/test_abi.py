@@ -50,6 +50,7 @@ def test_status_strings_and_defaults(lib):
     lib.gabp_default_options(ctypes.byref(opt))
     assert opt.precision == 0 and opt.check_every == 10 and opt.use_graphs == 1
     assert opt.ir_inner_max == 400 and abs(opt.ir_inner_tol - 1e-4) < 1e-18
+    assert opt.freeze_lambda == -1 and opt.block_size == 0
 
 
 def _setup_status(lib, n, indptr, indices, data):

@@ -244,6 +244,36 @@ def test_structurally_nonsymmetric_layouts_agree(g):
         assert rel(host(x), xs) <= 1e-13
 
 
+@pytest.mark.parametrize("name", ["c1_32", "lognormal_33", "aniso9_31", "random_300"])
+def test_frozen_precision_messages_same_solution(g, name):
+    """Precomputed tilde-Lambda (Sec. 4.2): freezing the precision messages once
+    they stop changing gives the plain solve's iterates up to rounding."""
+    A = MATS[name]
+    b = _rhs(A.n, 14)
+    ref = oracle.solve(A, b, 1e-10, 5000)
+    assert ref["status"] == oracle.OK
+    s = g.GabpSolver(A, "fp64", check_every=1, freeze_lambda=1)
+    x, it, rr, st = s.solve(dev(b), 1e-10, 5000)
+    assert st == g.OK and rr <= 1e-10
+    assert abs(it - ref["iters"]) <= 1
+    assert rel(host(x), ref["x"]) <= 1e-9
+    # the frozen mean-message sweep can be timed; a plain context has none frozen
+    assert s.time_sweeps(dev(b), 3, frozen=True) > 0.0
+    plain = g.GabpSolver(A, "fp64", check_every=1, freeze_lambda=0)
+    with pytest.raises(g.GabpError):
+        plain.time_sweeps(dev(b), 3, frozen=True)
+
+
+def test_frozen_transpose_solve(g):
+    A = MATS["lognormal_33"]
+    gvec = _rhs(A.n, 15)
+    ref = oracle.solve(A.transpose(), gvec, 1e-10, 5000)
+    s = g.GabpSolver(A, "fp64", check_every=1, freeze_lambda=1)
+    lam, it, rr, st = s.solve_transpose(dev(gvec), 1e-10, 5000)
+    assert st == g.OK and abs(it - ref["iters"]) <= 1
+    assert rel(host(lam), ref["x"]) <= 1e-9
+
+
 # --------------------------------------------------------------------------
 # float messages and mixed precision
 # --------------------------------------------------------------------------
@@ -259,11 +289,12 @@ def test_fp32_sweeps_error_against_oracle(g, name):
     assert rel(x, x_o) <= 1e-5
 
 
+@pytest.mark.parametrize("freeze", [-1, 0])
 @pytest.mark.parametrize("name", ["c1_32", "lognormal_33", "aniso9_31", "random_300"])
-def test_mixed_precision_reaches_1e10(g, name):
+def test_mixed_precision_reaches_1e10(g, name, freeze):
     A = MATS[name]
     b = _rhs(A.n, 10)
-    s = g.GabpSolver(A, "fp32_ir", check_every=5)
+    s = g.GabpSolver(A, "fp32_ir", check_every=5, freeze_lambda=freeze)
     x, it, rr, st = s.solve(dev(b), 1e-10, 20000)
     assert st == g.OK and rr <= 1e-10
     xs = np.linalg.solve(A.to_dense(), b)
