@@ -38,7 +38,7 @@ if ROOT not in sys.path:
 
 TOL = 1e-10
 MAX_ITER = 200000
-IR_INNER_MAX = 2000   # float sweeps per refinement step (restarting early beats long inner solves)
+IR_INNER_MAX = 400    # float sweeps per refinement step (restarting early beats long inner solves)
 SM_COUNT = 152
 FP64_PER_CYCLE = 2    # FP64 arithmetic instructions per cycle per SM (GB300)
 

@@ -81,7 +81,10 @@ typedef struct {
 } gabp_options;
 
 /* Fills `opt` with the defaults: FP64, auto layout, check_every 10, graphs on,
- * ir_inner_max 400, ir_inner_tol 1e-4, block_size 0, freeze_lambda -1. */
+ * ir_inner_max 400, ir_inner_tol 1e-3, block_size 0, freeze_lambda -1.
+ * (Short refinement steps win: restarting the float solve on a fresh double
+ * residual every few hundred sweeps reaches 1e-10 in fewer total sweeps
+ * than long inner solves.) */
 void gabp_default_options(gabp_options *opt);
 
 /* Text for a status code (static storage). */
@@ -239,6 +242,65 @@ gabp_status gabp_time_sweeps(gabp_ctx *ctx, const double *b, int nsweeps, int fr
 gabp_status gabp_sweep_noalloc(int32_t n, int64_t nnz, const int64_t *indptr,
                                const int32_t *indices, const double *data, const double *b,
                                int nsweeps, double *x, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Batched solver: many independent systems in one persistent launch.  The
+ * paper solves one system at a time; this is the same Algorithm 1 per
+ * system (flood sweeps, residual check every check_every sweeps, the same
+ * per-row arithmetic as gabp_solve, so a batched system follows gabp_solve's
+ * iterates), scheduled so that one kernel launch, replayed as a CUDA graph,
+ * serves the whole batch.
+ * ------------------------------------------------------------------------- */
+
+/*
+ * Groups `nsys` >= 1 contexts (created by gabp_setup, all in the stencil
+ * layout with at most 8 off-diagonal diagonals, one message precision, one
+ * device) into a batch.  The batch uses the contexts' coefficient and message
+ * buffers (their message state is overwritten by batch solves); the contexts
+ * stay owned by the caller and must outlive the batch.  Systems are queued
+ * largest first.
+ */
+gabp_status gabp_batch_setup(int nsys, gabp_ctx *const *systems, int check_every, void *stream,
+                             gabp_batch **out);
+
+/*
+ * Autotuner: times a whole batched solve (tolerance `tol`, sweep cap
+ * `max_iter`, as gabp_batch_solve) for each launch shape -- 256 or 512
+ * threads per CTA x 1, 2, 4 or 8 CTAs per thread-block cluster, as many
+ * clusters as can be resident -- and keeps the fastest.  Under a shape,
+ * systems with at least 4 rows per cluster thread are each solved by a whole
+ * cluster, the rest by single CTAs.  b, x: host arrays of nsys device
+ * pointers (n_i doubles each); x receives scratch values.  The first
+ * gabp_batch_solve tunes itself (with its own tol and max_iter) unless a
+ * shape was set.  block / cluster (nullable) receive the choice.
+ */
+gabp_status gabp_batch_tune(gabp_batch *batch, const double *const *b, double *const *x, double tol,
+                            int max_iter, int *block, int *cluster);
+
+/* Sets the launch shape without tuning: block 256 or 512, cluster 1, 2, 4 or 8. */
+gabp_status gabp_batch_set_shape(gabp_batch *batch, int block, int cluster);
+
+/*
+ * Solves every system A_i x_i = b_i from zero messages in one persistent
+ * launch: each thread-block cluster takes the next system from a queue
+ * (largest first), sweeps it with all its threads until
+ * ||b_i - A_i x_i||_inf / ||b_i||_inf <= tol (checked in double every
+ * check_every sweeps), breakdown, divergence or max_iter sweeps, then takes
+ * the next.  Contexts created with GABP_FP32_IR run float GaBP inside double
+ * iterative refinement per system (as gabp_solve does; max_iter caps the
+ * float sweeps).  b, x: host arrays of nsys device pointers.  iters / relres /
+ * status (host arrays of nsys, nullable) receive each system's sweeps, final
+ * relative residual and gabp_status.  Returns GABP_OK if every system
+ * converged, else the most severe per-system status.  Synchronises the
+ * stream.
+ */
+gabp_status gabp_batch_solve(gabp_batch *batch, const double *const *b, double *const *x, double tol,
+                             int max_iter, int *iters, double *relres, int *status);
+
+/* Launch shape in use: threads per CTA, CTAs per cluster, CTAs (0 before tuning). */
+gabp_status gabp_batch_info(gabp_batch *batch, int *block, int *cluster, int *grid);
+
+void gabp_batch_destroy(gabp_batch *batch);
 
 /* ---------------------------------------------------------------------------
  * Geometric multigrid with GaBP as the smoother (Sec. 4).

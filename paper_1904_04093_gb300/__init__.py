@@ -16,7 +16,7 @@ import numpy as np
 from . import build as _build
 
 __all__ = [
-    "GabpError", "GabpSolver", "Multigrid", "load", "library_path", "STATUS",
+    "GabpError", "GabpSolver", "Multigrid", "Batch", "load", "library_path", "STATUS",
     "OK", "BREAKDOWN", "DIVERGED", "NOT_CONVERGED",
 ]
 
@@ -91,6 +91,12 @@ def load() -> ctypes.CDLL:
         "mg_vcycle": (I, [P, I, I, I, P, P]),
         "mg_solve": (I, [P, P, P, D, I, I, I, PI, PD]),
         "mg_destroy": (None, [P]),
+        "gabp_batch_setup": (I, [I, ctypes.POINTER(P), I, P, ctypes.POINTER(P)]),
+        "gabp_batch_tune": (I, [P, ctypes.POINTER(P), ctypes.POINTER(P), D, I, PI, PI]),
+        "gabp_batch_set_shape": (I, [P, I, I]),
+        "gabp_batch_solve": (I, [P, ctypes.POINTER(P), ctypes.POINTER(P), D, I, PI, PD, PI]),
+        "gabp_batch_info": (I, [P, PI, PI, PI]),
+        "gabp_batch_destroy": (None, [P]),
     }
     for name, (res, args) in sigs.items():
         fn = getattr(L, name)
@@ -142,7 +148,7 @@ class GabpSolver:
     """
 
     def __init__(self, A, precision: str = "fp64", layout: str = "auto", check_every: int = 10,
-                 use_graphs: bool = True, ir_inner_max: int = 400, ir_inner_tol: float = 1e-4,
+                 use_graphs: bool = True, ir_inner_max: int = 400, ir_inner_tol: float = 1e-3,
                  block_size: int = 0, freeze_lambda: int = -1, stream=None):
         L = load()
         torch = _torch()
@@ -306,3 +312,62 @@ class Multigrid:
         if st not in (OK, NOT_CONVERGED, DIVERGED, BREAKDOWN):
             raise _err(st)
         return x, int(c.value), float(rr.value), int(st)
+
+
+class Batch:
+    """Many independent systems solved in one persistent launch (see ``include/gabp.h``)."""
+
+    def __init__(self, solvers, check_every: int = 10, stream=None):
+        L = load()
+        self.solvers = list(solvers)
+        self.nsys = len(self.solvers)
+        self._sh, self.stream = _stream_handle(stream)
+        arr = (ctypes.c_void_p * self.nsys)(*[s._h for s in self.solvers])
+        h = ctypes.c_void_p()
+        _check(L.gabp_batch_setup(self.nsys, arr, int(check_every), self._sh, ctypes.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().gabp_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _tables(self, bs, xs):
+        torch = _torch()
+        if xs is None:
+            xs = [torch.empty(s.n, dtype=torch.float64, device=b.device) for s, b in zip(self.solvers, bs)]
+        bt = (ctypes.c_void_p * self.nsys)(*[_dev_vec(b, s.n, "b").value for s, b in zip(self.solvers, bs)])
+        xt = (ctypes.c_void_p * self.nsys)(*[_dev_vec(x, s.n, "x").value for s, x in zip(self.solvers, xs)])
+        return xs, bt, xt
+
+    def tune(self, bs, tol: float, max_iter: int, xs=None):
+        xs, bt, xt = self._tables(bs, xs)
+        blk, cs = ctypes.c_int(), ctypes.c_int()
+        _check(load().gabp_batch_tune(self._h, bt, xt, float(tol), int(max_iter), ctypes.byref(blk),
+                                      ctypes.byref(cs)))
+        return int(blk.value), int(cs.value)
+
+    def set_shape(self, block: int, cluster: int):
+        _check(load().gabp_batch_set_shape(self._h, int(block), int(cluster)))
+
+    def info(self):
+        blk, cs, grid = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(load().gabp_batch_info(self._h, ctypes.byref(blk), ctypes.byref(cs), ctypes.byref(grid)))
+        return {"block": blk.value, "cluster": cs.value, "grid": grid.value}
+
+    def solve(self, bs, tol: float, max_iter: int, xs=None):
+        """Returns ``(xs, iters, relres, status)`` (lists over systems)."""
+        xs, bt, xt = self._tables(bs, xs)
+        it = (ctypes.c_int * self.nsys)()
+        rr = (ctypes.c_double * self.nsys)()
+        stt = (ctypes.c_int * self.nsys)()
+        st = load().gabp_batch_solve(self._h, bt, xt, float(tol), int(max_iter), it, rr, stt)
+        if st not in (OK, NOT_CONVERGED, BREAKDOWN, DIVERGED):
+            raise _err(st)
+        return xs, list(it), list(rr), list(stt)

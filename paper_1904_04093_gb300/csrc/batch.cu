@@ -1,0 +1,473 @@
+// Batched GaBP: many independent systems solved in one persistent launch.
+//
+// Each thread-block cluster (1 to 8 CTAs, one SM each) takes the next system
+// from a global queue (largest first), runs every flood sweep of that system
+// with all its threads (one thread per row, strided over the cluster),
+// checks its own double residual every `check_every` sweeps and stops it on
+// convergence, breakdown, divergence or the sweep cap; then it takes the next
+// system.  Sweeps are separated by the hardware cluster barrier and the
+// reductions combine the CTAs' partial results through distributed shared
+// memory.  Clusters never wait on one another: the only cross-cluster
+// operation is one atomicAdd on the queue, so every cluster finishes in
+// bounded time.  The per-row update is the
+// single-system kernel's (sweep_row_stencil), so a system solved in a batch
+// follows the same iterates as gabp_solve with the same check interval.
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <type_traits>
+#include <string>
+#include <vector>
+
+#include "gabp_internal.h"
+#include "sweep_row.cuh"
+
+namespace gabp {
+
+template <typename T>
+struct BatchSys {
+    int n;
+    int pad_;
+    int off[KMAX];
+    int krev[KMAX];
+    const T *a, *c, *diag;
+    const double *a64, *diag64;
+    T *L0, *L1, *M0, *M1, *P0, *P1, *B0, *B1, *bT;
+    double *e, *r;  // refinement: correction (beliefs of the inner solve), residual
+};
+
+struct BatchResult {
+    int iters;
+    int status;
+    double rr;
+};
+
+namespace {
+
+namespace cg = cooperative_groups;
+
+// Shared per-CTA state of the batched kernel.
+struct BatchShared {
+    int idx;             // system index taken from a queue
+    unsigned flags;      // 1 breakdown, 2 non-finite residual
+    double red[33];      // reduction scratch; red[32] = this CTA's partial result
+    int off[8], krev[8]; // diagonals of the current system
+};
+
+__device__ __forceinline__ double cta_max_partial(double v, BatchShared &sh)
+{
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    __syncthreads();
+    if (lane == 0) sh.red[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        v = lane < nw ? sh.red[lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+        if (lane == 0) sh.red[32] = v;
+    }
+    return v;
+}
+
+// A whole thread-block cluster works on one system: rows strided over all
+// its threads, sweeps separated by the hardware cluster barrier, reductions
+// combined through distributed shared memory, error flags in rank 0's copy.
+struct ClusterTeam {
+    cg::cluster_group cl;
+    BatchShared *sh, *root;
+    int t0, nt;
+    __device__ ClusterTeam(BatchShared *s) : cl(cg::this_cluster()), sh(s)
+    {
+        root = cl.map_shared_rank(s, 0);
+        t0 = (int)cl.block_rank() * blockDim.x + threadIdx.x;
+        nt = (int)cl.num_blocks() * blockDim.x;
+    }
+    __device__ void sync() { cl.sync(); }
+    __device__ unsigned *flags() { return &root->flags; }
+    __device__ double max(double v)
+    {
+        cta_max_partial(v, *sh);
+        cl.sync();
+        double m = 0.0;
+        const unsigned nb = cl.num_blocks();
+        for (unsigned r = 0; r < nb; ++r) m = fmax(m, cl.map_shared_rank(sh, r)->red[32]);
+        cl.sync();  // every CTA has read the partials before they are overwritten
+        return m;
+    }
+};
+
+// One CTA works on one system on its own.
+struct CtaTeam {
+    BatchShared *sh;
+    int t0, nt;
+    __device__ CtaTeam(BatchShared *s) : sh(s), t0(threadIdx.x), nt(blockDim.x) {}
+    __device__ void sync() { __syncthreads(); }
+    __device__ unsigned *flags() { return &sh->flags; }
+    __device__ double max(double v)
+    {
+        cta_max_partial(v, *sh);
+        __syncthreads();
+        const double m = sh->red[32];
+        __syncthreads();
+        return m;
+    }
+};
+
+// Residual max_r |rhs_r - (A y)_r| in double, rhs_r = src[r] * scale, over this
+// thread's rows; writes rhs - A y into `out` when not null.  src and y are
+// read coherently (written earlier in this launch).
+template <typename T, int K>
+__device__ double batch_residual(const BatchSys<T> &S, int n, const int *off, const double *src,
+                                 double scale, const double *y, double *out, int t0, int nt,
+                                 bool &nan)
+{
+    double rm = 0.0;
+    for (int r = t0; r < n; r += nt) {
+        double acc = __ldcg(src + r) * scale - S.diag64[r] * __ldcg(y + r);
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const double ae = S.a64[(size_t)k * n + r];
+            if (ae != 0.0) acc += ae * __ldcg(y + r + off[k]);
+        }
+        if (out) out[r] = acc;
+        const double v = fabs(acc);
+        if (v != v) nan = true;
+        else rm = fmax(rm, v);
+    }
+    return rm;
+}
+
+// `kk` flood sweeps of system S from state `cur` (beliefs of the last go to y).
+template <typename T, int K, typename Team>
+__device__ void batch_sweeps(const BatchSys<T> &S, int n, const int *off, const int *krev, int kk,
+                             int &cur, double *y, Team &tm)
+{
+    for (int j = 0; j < kk; ++j) {
+        T *Lin = cur ? S.L1 : S.L0, *Lout = cur ? S.L0 : S.L1;
+        T *Min = cur ? S.M1 : S.M0, *Mout = cur ? S.M0 : S.M1;
+        T *Pin = cur ? S.P1 : S.P0, *Pout = cur ? S.P0 : S.P1;
+        T *Bin = cur ? S.B1 : S.B0, *Bout = cur ? S.B0 : S.B1;
+        double *yo = j == kk - 1 ? y : nullptr;
+        bool bad = false;
+        for (int r = tm.t0; r < n; r += tm.nt)
+            bad |= sweep_row_stencil<T, K, true>(r, n, off, krev, S.a, S.c, S.diag, S.bT, Lin, Min,
+                                                 Pin, Bin, Lout, Mout, Pout, Bout, yo);
+        if (bad) atomicOr(tm.flags(), 1u);
+        tm.sync();
+        cur ^= 1;
+    }
+}
+
+// Solves system `id` with team `tm` (every thread of the team calls this with
+// the same arguments; all control flow below is uniform across the team).
+//
+// refine = 0: plain GaBP on A x = b (Algorithm 1).
+// refine = 1: GaBP in the message precision inside double iterative
+// refinement: x accumulates in double, every refinement step solves
+// A e = r / ||r||_inf from zero mean messages (precision messages kept warm:
+// they do not depend on the right-hand side) for at most inner_max sweeps or
+// until its own relative residual <= inner_tol, then x += ||r|| e and
+// r = b - A x in double; max_iter caps the total sweeps.
+template <typename T, int K, typename Team>
+__device__ void solve_system(const BatchSys<T> &S, int id, const double *b, double *x, Team &tm,
+                             double tol, int max_iter, int check_every, int refine,
+                             double inner_tol, int inner_max, BatchResult *res, bool leader)
+{
+    const int n = S.n, t0 = tm.t0, nt = tm.nt;
+    const int *off = tm.sh->off, *krev = tm.sh->krev;
+    unsigned *flags = tm.flags();
+    // zero messages: P = diag, B = b (plain) or the first refinement rhs b / ||b||
+    double bm = 0.0;
+    for (int r = t0; r < n; r += nt) bm = fmax(bm, fabs(b[r]));
+    const double bnorm = tm.max(bm);
+    const double inv0 = bnorm > 0.0 ? 1.0 / bnorm : 0.0;
+    for (int r = t0; r < n; r += nt) {
+        const double bv = b[r];
+        const T bt = (T)(refine ? bv * inv0 : bv);
+        S.bT[r] = bt;
+        S.P0[r] = S.diag[r];
+        S.B0[r] = bt;
+        if (refine) {
+            x[r] = 0.0;
+            S.r[r] = bv;
+        }
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            S.L0[(size_t)k * n + r] = T(0);
+            S.M0[(size_t)k * n + r] = T(0);
+        }
+    }
+    if (bnorm == 0.0)
+        for (int r = t0; r < n; r += nt) x[r] = 0.0;
+    tm.sync();
+    int it = 0, cur = 0, status = bnorm == 0.0 ? GABP_OK : GABP_E_NOT_CONVERGED;
+    double rr = 0.0;
+    if (!refine) {
+        while (status == GABP_E_NOT_CONVERGED && it < max_iter) {
+            const int kk = min(check_every, max_iter - it);
+            batch_sweeps<T, K>(S, n, off, krev, kk, cur, x, tm);
+            it += kk;
+            bool nan = false;
+            double rm = batch_residual<T, K>(S, n, off, b, 1.0, x, nullptr, t0, nt, nan);
+            if (nan) atomicOr(flags, 2u);
+            rm = tm.max(rm);
+            rr = rm / bnorm;
+            const unsigned fl = *flags;
+            if (fl & 1u) status = GABP_E_BREAKDOWN;
+            else if ((fl & 2u) || !(rr <= 1e8)) status = GABP_E_DIVERGED;
+            else if (rr <= tol) status = GABP_OK;
+        }
+    } else {
+        double scale = bnorm;  // ||r||_inf of the current refinement step
+        bool first = true;
+        while (status == GABP_E_NOT_CONVERGED && it < max_iter) {
+            if (!first) {
+                // new inner problem A e = r / ||r||: zero mean messages, warm precision messages
+                const double inv = 1.0 / scale;
+                T *Lc = cur ? S.L1 : S.L0, *Mc = cur ? S.M1 : S.M0;
+                T *Pc = cur ? S.P1 : S.P0, *Bc = cur ? S.B1 : S.B0;
+                for (int r = t0; r < n; r += nt) {
+                    const T bt = (T)(__ldcg(S.r + r) * inv);
+                    S.bT[r] = bt;
+                    T p = S.diag[r];
+#pragma unroll
+                    for (int k = 0; k < K; ++k) {
+                        p += __ldcg(Lc + (size_t)k * n + r);
+                        Mc[(size_t)k * n + r] = T(0);
+                    }
+                    Pc[r] = p;
+                    Bc[r] = bt;
+                }
+                tm.sync();
+            }
+            first = false;
+            int inner = 0;
+            while (inner < inner_max && it < max_iter) {
+                const int kk = min(min(check_every, inner_max - inner), max_iter - it);
+                batch_sweeps<T, K>(S, n, off, krev, kk, cur, S.e, tm);
+                inner += kk;
+                it += kk;
+                bool nan = false;
+                double rin = batch_residual<T, K>(S, n, off, S.r, 1.0 / scale, S.e, nullptr, t0,
+                                                  nt, nan);
+                if (nan) atomicOr(flags, 2u);
+                rin = tm.max(rin);
+                if (*flags) break;
+                if (rin <= inner_tol) break;
+            }
+            if (*flags & 1u) {
+                status = GABP_E_BREAKDOWN;
+                break;
+            }
+            // x += ||r|| e ;  r = b - A x
+            for (int r = t0; r < n; r += nt) x[r] = __ldcg(x + r) + scale * __ldcg(S.e + r);
+            tm.sync();
+            bool nan = false;
+            double rm = batch_residual<T, K>(S, n, off, b, 1.0, x, S.r, t0, nt, nan);
+            if (nan) atomicOr(flags, 2u);
+            rm = tm.max(rm);
+            rr = rm / bnorm;
+            scale = rm;
+            if ((*flags & 2u) || !(rr <= 1e8)) status = GABP_E_DIVERGED;
+            else if (rr <= tol) status = GABP_OK;
+        }
+    }
+    if (leader) {
+        res[id].iters = it;
+        res[id].status = status;
+        res[id].rr = rr;
+    }
+    tm.sync();
+}
+
+// Persistent kernel.  Phase 1: each cluster takes the next of the first
+// `nbig` systems (largest first) from queue[0] and solves it with all its
+// CTAs.  Phase 2: once those are taken, every CTA on its own takes the next
+// remaining system from queue[1].  Message state written earlier in this
+// launch is read back with coherent loads (sweep_row_stencil<..., true>,
+// __ldcg), never through the non-coherent read-only path; the barriers order
+// it across the team.
+template <typename T, int K>
+__global__ void __launch_bounds__(512) k_batch_solve(
+    const BatchSys<T> *__restrict__ sys, const int *__restrict__ order, int nsys, int nbig,
+    const double *const *__restrict__ bptr, double *const *__restrict__ xptr, int *queue,
+    double tol, int max_iter, int check_every, int refine, double inner_tol, int inner_max,
+    BatchResult *__restrict__ res)
+{
+    __shared__ BatchShared sh;
+    const int tid = threadIdx.x;
+    {
+        ClusterTeam tm(&sh);
+        const bool rank0 = tm.cl.block_rank() == 0;
+        for (;;) {
+            if (rank0 && tid == 0) {
+                sh.idx = atomicAdd(&queue[0], 1);
+                sh.flags = 0u;
+            }
+            tm.cl.sync();
+            const int q = tm.root->idx;
+            tm.cl.sync();  // every CTA has read rank 0's shared memory before it changes
+            if (q >= nbig) break;
+            const int id = order[q];
+            if (tid < K) {
+                sh.off[tid] = sys[id].off[tid];
+                sh.krev[tid] = sys[id].krev[tid];
+            }
+            solve_system<T, K>(sys[id], id, bptr[id], xptr[id], tm, tol, max_iter, check_every,
+                               refine, inner_tol, inner_max, res, rank0 && tid == 0);
+        }
+    }
+    // phase 2: no distributed shared memory from here on
+    CtaTeam tm(&sh);
+    for (;;) {
+        if (tid == 0) {
+            sh.idx = nbig + atomicAdd(&queue[1], 1);
+            sh.flags = 0u;
+        }
+        __syncthreads();
+        const int q = sh.idx;
+        if (q >= nsys) break;
+        const int id = order[q];
+        if (tid < K) {
+            sh.off[tid] = sys[id].off[tid];
+            sh.krev[tid] = sys[id].krev[tid];
+        }
+        solve_system<T, K>(sys[id], id, bptr[id], xptr[id], tm, tol, max_iter, check_every, refine,
+                           inner_tol, inner_max, res, tid == 0);
+    }
+}
+
+}  // namespace
+
+template <typename T, int K>
+cudaError_t launch_batch_k(int cs, int grid, int block, const void *sys, const int *order, int nsys,
+                           int nbig, const double *const *bptr, double *const *xptr, int *queue, double tol,
+                           int max_iter, int check_every, int refine, double inner_tol,
+                           int inner_max, void *res, cudaStream_t s)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid, 1, 1);
+    cfg.blockDim = dim3(block, 1, 1);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_batch_solve<T, K>, (const BatchSys<T> *)sys, order, nsys, nbig, bptr,
+                              xptr, queue, tol, max_iter, check_every, refine, inner_tol, inner_max,
+                              (BatchResult *)res);
+}
+
+template <typename T>
+cudaError_t launch_batch(int K, int cs, int grid, int block, const void *sys, const int *order,
+                         int nsys, int nbig, const double *const *bptr, double *const *xptr, int *queue,
+                         double tol, int max_iter, int check_every, int refine, double inner_tol,
+                         int inner_max, void *res, cudaStream_t s)
+{
+#define GABP_BATCH_CASE(KK)                                                                     \
+    case KK:                                                                                    \
+        return launch_batch_k<T, KK>(cs, grid, block, sys, order, nsys, nbig, bptr, xptr, queue, tol, \
+                                     max_iter, check_every, refine, inner_tol, inner_max, res, s);
+    switch (K) {
+        GABP_BATCH_CASE(0)
+        GABP_BATCH_CASE(2)
+        GABP_BATCH_CASE(4)
+        GABP_BATCH_CASE(6)
+        GABP_BATCH_CASE(8)
+        default:
+            return cudaErrorInvalidValue;
+    }
+#undef GABP_BATCH_CASE
+}
+
+// Clusters of `cs` CTAs of `block` threads that can be resident at once (0 = none).
+template <typename T, int K>
+int batch_max_clusters_k(int cs, int block)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cs, 1, 1);
+    cfg.blockDim = dim3(block, 1, 1);
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int nc = 0;
+    if (cudaOccupancyMaxActiveClusters(&nc, k_batch_solve<T, K>, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return nc;
+}
+
+template <typename T>
+int batch_max_clusters(int K, int cs, int block)
+{
+    switch (K) {
+        case 0: return batch_max_clusters_k<T, 0>(cs, block);
+        case 2: return batch_max_clusters_k<T, 2>(cs, block);
+        case 4: return batch_max_clusters_k<T, 4>(cs, block);
+        case 6: return batch_max_clusters_k<T, 6>(cs, block);
+        case 8: return batch_max_clusters_k<T, 8>(cs, block);
+        default: return 0;
+    }
+}
+
+template cudaError_t launch_batch<float>(int, int, int, int, const void *, const int *, int, int,
+                                         const double *const *, double *const *, int *, double,
+                                         int, int, int, double, int, void *, cudaStream_t);
+template cudaError_t launch_batch<double>(int, int, int, int, const void *, const int *, int, int,
+                                          const double *const *, double *const *, int *, double,
+                                          int, int, int, double, int, void *, cudaStream_t);
+template int batch_max_clusters<float>(int, int, int);
+template int batch_max_clusters<double>(int, int, int);
+
+void fill_batch_sys(int prec, void *dst, int n, const StencilParams &sp, const void *a, const void *c,
+                    const void *diag, const double *a64, const double *diag64, void *const L[2],
+                    void *const M[2], void *const P[2], void *const B[2], void *bT, double *e,
+                    double *r)
+{
+    auto fill = [&](auto *S, auto *tag) {
+        using T = std::remove_pointer_t<decltype(tag)>;
+        std::memset(S, 0, sizeof(*S));
+        S->n = n;
+        for (int k = 0; k < KMAX; ++k) {
+            S->off[k] = sp.off[k];
+            S->krev[k] = sp.krev[k];
+        }
+        S->a = (const T *)a;
+        S->c = (const T *)c;
+        S->diag = (const T *)diag;
+        S->a64 = a64;
+        S->diag64 = diag64;
+        S->L0 = (T *)L[0];
+        S->L1 = (T *)L[1];
+        S->M0 = (T *)M[0];
+        S->M1 = (T *)M[1];
+        S->P0 = (T *)P[0];
+        S->P1 = (T *)P[1];
+        S->B0 = (T *)B[0];
+        S->B1 = (T *)B[1];
+        S->bT = (T *)bT;
+        S->e = e;
+        S->r = r;
+    };
+    if (prec == 0) fill((BatchSys<double> *)dst, (double *)nullptr);
+    else fill((BatchSys<float> *)dst, (float *)nullptr);
+}
+
+size_t batch_sys_bytes(int prec) { return prec == 0 ? sizeof(BatchSys<double>) : sizeof(BatchSys<float>); }
+size_t batch_result_bytes() { return sizeof(BatchResult); }
+
+}  // namespace gabp

@@ -101,4 +101,21 @@ cudaError_t launch_prolong_add(const double *ec, int mc, double *xf, cudaStream_
 // y = M x for a dense row-major n x n matrix (coarse-grid solve)
 cudaError_t launch_dense_gemv(const double *M, const double *x, double *y, int n, cudaStream_t s);
 
+// ---- batched persistent solver (batch.cu) ----
+// cs = CTAs per thread-block cluster (1..8), grid a multiple of cs; the first
+// nbig systems of `order` are solved by whole clusters, the rest by single CTAs
+template <typename T>
+cudaError_t launch_batch(int K, int cs, int grid, int block, const void *sys, const int *order,
+                         int nsys, int nbig, const double *const *bptr, double *const *xptr, int *queue,
+                         double tol, int max_iter, int check_every, int refine, double inner_tol,
+                         int inner_max, void *res, cudaStream_t s);
+template <typename T>
+int batch_max_clusters(int K, int cs, int block);
+void fill_batch_sys(int prec, void *dst, int n, const StencilParams &sp, const void *a, const void *c,
+                    const void *diag, const double *a64, const double *diag64, void *const L[2],
+                    void *const M[2], void *const P[2], void *const B[2], void *bT, double *e,
+                    double *r);
+size_t batch_sys_bytes(int prec);
+size_t batch_result_bytes();  // {int iters; int status; double rr;}
+
 }  // namespace gabp

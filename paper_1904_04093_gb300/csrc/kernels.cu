@@ -27,6 +27,7 @@
 #include <atomic>
 
 #include "gabp_internal.h"
+#include "sweep_row.cuh"
 
 namespace gabp {
 
@@ -45,44 +46,9 @@ unsigned long long launch_count() { return g_launches.load(std::memory_order_rel
 
 namespace {
 
-template <typename T>
-__device__ __forceinline__ bool bad_den(T d)
-{
-    return d == T(0) || !isfinite(d);
-}
-
-// Reciprocal used by the message update.  Float: the correctly rounded
-// reciprocal intrinsic.  Double: the hardware approximation rcp.approx.ftz.f64
-// refined by one third-order Newton-Raphson step, y <- y (1 + e + e^2) with
-// e = 1 - d y (the truncated series of 1 / (1 - e)); from the approximation's
-// ~2^-22 relative error this lands within rounding of 1/d in three FMAs,
-// against the longer sequence of an IEEE division.  A zero or non-finite d
-// gives a non-finite result and is flagged by the caller.
-template <typename T>
-__device__ __forceinline__ T fast_rcp(T d);
-
-template <>
-__device__ __forceinline__ float fast_rcp<float>(float d)
-{
-    return __frcp_rn(d);
-}
-
-template <>
-__device__ __forceinline__ double fast_rcp<double>(double d)
-{
-    double y;
-    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(d));
-    const double e = fma(-d, y, 1.0);
-    const double e2 = fma(e, e, e);
-    return fma(y, e2, y);
-}
-
 // ---------------------------------------------------------------------------
-// Message sweep, stencil layout
-//
-// All loads of a row are issued before any arithmetic: the reverse-edge
-// gathers use an index clamped into [0, n) so they are always in bounds and
-// need not wait for a_e; a padded slot (a_e == 0) discards what it loaded.
+// Message sweep, stencil layout: one thread per row (sweep_row_stencil in
+// sweep_row.cuh, shared with the batched solver).
 // ---------------------------------------------------------------------------
 template <typename T, int K>
 __global__ void __launch_bounds__(256) k_sweep_stencil(
@@ -94,45 +60,9 @@ __global__ void __launch_bounds__(256) k_sweep_stencil(
 {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n) return;
-    const size_t nn = (size_t)n;
-    T ae[K > 0 ? K : 1], ce[K > 0 ? K : 1], ps[K > 0 ? K : 1], bs[K > 0 ? K : 1],
-        lr[K > 0 ? K : 1], mr[K > 0 ? K : 1];
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-        const size_t e = (size_t)k * nn + r;
-        ae[k] = a[e];
-        ce[k] = c[e];
-        int s = r + sp.off[k];
-        s = s < 0 ? 0 : (s >= n ? n - 1 : s);
-        const size_t er = (size_t)sp.krev[k] * nn + s;
-        ps[k] = Pin[s];
-        bs[k] = Bin[s];
-        lr[k] = Lin[er];
-        mr[k] = Min[er];
-    }
-    T pn = diag[r];
-    T bn = b[r];
-    if (x) x[r] = (double)(Bin[r] / Pin[r]);
-    bool bad = false;
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-        const size_t e = (size_t)k * nn + r;
-        T lam = T(0), mu = T(0);
-        if (ae[k] != T(0)) {
-            const T d = ps[k] - lr[k];
-            bad |= bad_den(d);
-            const T q = fast_rcp(d);
-            lam = ce[k] * q;
-            mu = ae[k] * (bs[k] - mr[k]) * q;
-        }
-        Lout[e] = lam;
-        Mout[e] = mu;
-        pn += lam;
-        bn += mu;
-    }
-    Pout[r] = pn;
-    Bout[r] = bn;
-    if (bad) atomicOr(flags, FLAG_BREAKDOWN);
+    if (sweep_row_stencil<T, K>(r, n, sp.off, sp.krev, a, c, diag, b, Lin, Min, Pin, Bin, Lout,
+                                Mout, Pout, Bout, x))
+        atomicOr(flags, FLAG_BREAKDOWN);
 }
 
 // ---------------------------------------------------------------------------

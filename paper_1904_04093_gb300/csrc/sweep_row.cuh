@@ -1,0 +1,110 @@
+// Per-row flood update shared by the single-system and batched sweep kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace gabp {
+
+template <typename T>
+__device__ __forceinline__ bool bad_den(T d)
+{
+    return d == T(0) || !isfinite(d);
+}
+
+// Reciprocal used by the message update.  Float: the correctly rounded
+// reciprocal intrinsic.  Double: the hardware approximation rcp.approx.ftz.f64
+// refined by one third-order Newton-Raphson step, y <- y (1 + e + e^2) with
+// e = 1 - d y (the truncated series of 1 / (1 - e)); from the approximation's
+// ~2^-22 relative error this lands within rounding of 1/d in three FMAs,
+// against the longer sequence of an IEEE division.  A zero or non-finite d
+// gives a non-finite result and is flagged by the caller.
+template <typename T>
+__device__ __forceinline__ T fast_rcp(T d);
+
+template <>
+__device__ __forceinline__ float fast_rcp<float>(float d)
+{
+    return __frcp_rn(d);
+}
+
+template <>
+__device__ __forceinline__ double fast_rcp<double>(double d)
+{
+    double y;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(d));
+    const double e = fma(-d, y, 1.0);
+    const double e2 = fma(e, e, e);
+    return fma(y, e2, y);
+}
+
+// Load of message state.  kCoherent (the batched solver, which reads state it
+// wrote earlier in the same launch) goes through L2 with ld.global.cg and
+// never through the non-coherent read-only path.
+template <bool kCoherent, typename T>
+__device__ __forceinline__ T ld_state(const T *p)
+{
+    if (kCoherent) return __ldcg(p);
+    return *p;
+}
+
+// Flood update of row r in the stencil (per-diagonal) layout: slot k*n + r
+// holds the entry (r, r + off[k]); its reverse edge is slot krev[k]*n + s,
+// s = r + off[k].  With a_e = -A_rs, c_e = -A_rs A_sr and the aggregates
+// P = diag + sum L, B = b + sum M of the previous state:
+//     d = P_s - L[rev],  L' = c / d,  M' = a (B_s - M[rev]) / d,
+// and the belief x_r = B_r / P_r of the previous state (Algorithm 1 forms the
+// belief before the update).  All loads of the row are issued before any
+// arithmetic: the reverse-edge gathers use an index clamped into [0, n), so
+// they are always in bounds and need not wait for a_e; a padded slot
+// (a_e == 0) discards what it loaded.  Returns true on a zero or non-finite
+// denominator.
+template <typename T, int K, bool kCoherent = false>
+__device__ __forceinline__ bool sweep_row_stencil(
+    int r, int n, const int *off, const int *krev, const T *__restrict__ a,
+    const T *__restrict__ c, const T *__restrict__ diag, const T *__restrict__ b,
+    const T *__restrict__ Lin, const T *__restrict__ Min, const T *__restrict__ Pin,
+    const T *__restrict__ Bin, T *__restrict__ Lout, T *__restrict__ Mout,
+    T *__restrict__ Pout, T *__restrict__ Bout, double *__restrict__ x)
+{
+    const size_t nn = (size_t)n;
+    T ae[K > 0 ? K : 1], ce[K > 0 ? K : 1], ps[K > 0 ? K : 1], bs[K > 0 ? K : 1],
+        lr[K > 0 ? K : 1], mr[K > 0 ? K : 1];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const size_t e = (size_t)k * nn + r;
+        ae[k] = a[e];
+        ce[k] = c[e];
+        int s = r + off[k];
+        s = s < 0 ? 0 : (s >= n ? n - 1 : s);
+        const size_t er = (size_t)krev[k] * nn + s;
+        ps[k] = ld_state<kCoherent>(Pin + s);
+        bs[k] = ld_state<kCoherent>(Bin + s);
+        lr[k] = ld_state<kCoherent>(Lin + er);
+        mr[k] = ld_state<kCoherent>(Min + er);
+    }
+    T pn = diag[r];
+    T bn = ld_state<kCoherent>(b + r);
+    if (x) x[r] = (double)(ld_state<kCoherent>(Bin + r) / ld_state<kCoherent>(Pin + r));
+    bool bad = false;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const size_t e = (size_t)k * nn + r;
+        T lam = T(0), mu = T(0);
+        if (ae[k] != T(0)) {
+            const T d = ps[k] - lr[k];
+            bad |= bad_den(d);
+            const T q = fast_rcp(d);
+            lam = ce[k] * q;
+            mu = ae[k] * (bs[k] - mr[k]) * q;
+        }
+        Lout[e] = lam;
+        Mout[e] = mu;
+        pn += lam;
+        bn += mu;
+    }
+    Pout[r] = pn;
+    Bout[r] = bn;
+    return bad;
+}
+
+}  // namespace gabp

@@ -1,0 +1,114 @@
+"""Batched persistent solver: every system of a batch equals its single solve,
+and matches the FP64 oracle."""
+import numpy as np
+import pytest
+
+import oracle
+import problems as P
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device="cuda")
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+def rel(a, b):
+    return float(np.max(np.abs(np.asarray(a) - np.asarray(b))) / max(np.max(np.abs(b)), 1e-300))
+
+
+@pytest.fixture(scope="module")
+def g():
+    import paper_1904_04093_gb300 as g
+    g.load()
+    return g
+
+
+def _systems(nsys=9, smin=16, smax=41, seed=7):
+    # uneven sides (ragged against every block size), as in the batched workload
+    return P.config_c4_batch(nsys=nsys, smin=smin, smax=smax, seed=seed)
+
+
+@pytest.mark.parametrize("shape", [(256, 1), (256, 2), (512, 4), (256, 8)])
+@pytest.mark.parametrize("check_every", [1, 7])
+def test_batch_equals_single_solves(g, check_every, shape):
+    systems = _systems()
+    solvers = [g.GabpSolver(A, "fp64", check_every=check_every) for A, _ in systems]
+    batch = g.Batch(solvers, check_every=check_every)
+    batch.set_shape(*shape)
+    bs = [dev(b) for _, b in systems]
+    xs, its, rrs, sts = batch.solve(bs, 1e-10, 5000)
+    assert all(s == g.OK for s in sts)
+    for (A, b), x, it, rr in zip(systems, xs, its, rrs):
+        single = g.GabpSolver(A, "fp64", check_every=check_every)
+        xs1, it1, rr1, st1 = single.solve(dev(b), 1e-10, 5000)
+        assert st1 == g.OK and it == it1
+        assert rr == pytest.approx(rr1, rel=1e-12)
+        assert rel(host(x), host(xs1)) <= 1e-14
+
+
+def test_batch_matches_oracle(g):
+    systems = _systems(nsys=5, seed=11)
+    solvers = [g.GabpSolver(A, "fp64", check_every=1) for A, _ in systems]
+    batch = g.Batch(solvers, check_every=1)
+    xs, its, rrs, sts = batch.solve([dev(b) for _, b in systems], 1e-10, 5000)
+    for (A, b), x, it, st in zip(systems, xs, its, sts):
+        ref = oracle.solve(A, b, 1e-10, 5000)
+        assert st == g.OK and it == ref["iters"]
+        assert rel(host(x), ref["x"]) <= 1e-10
+
+
+def test_batch_float_plain(g):
+    """Float messages without refinement: the float beliefs bound the attainable
+    residual, so the target here is 1e-4."""
+    systems = _systems(nsys=6, smin=16, smax=40, seed=17)
+    solvers = [g.GabpSolver(A, "fp32") for A, _ in systems]
+    batch = g.Batch(solvers, check_every=10)
+    xs, its, rrs, sts = batch.solve([dev(b) for _, b in systems], 1e-4, 20000)
+    assert all(s == g.OK for s in sts)
+    for (A, b), x in zip(systems, xs):
+        xh = host(x)
+        assert np.max(np.abs(b - A.matvec(xh))) / np.max(np.abs(b)) <= 1.01e-4
+
+
+def test_batch_float_workload_tolerance(g):
+    """Float messages inside double refinement, per-system stop at rr <= 1e-6
+    (the batched workload's target)."""
+    systems = _systems(nsys=12, smin=16, smax=64, seed=13)
+    solvers = [g.GabpSolver(A, "fp32_ir") for A, _ in systems]
+    batch = g.Batch(solvers, check_every=10)
+    blk, cs = batch.tune([dev(b) for _, b in systems], 1e-6, 20000)
+    assert blk in (256, 512) and cs in (1, 2, 4, 8)
+    xs, its, rrs, sts = batch.solve([dev(b) for _, b in systems], 1e-6, 20000)
+    assert all(s == g.OK for s in sts)
+    for (A, b), x, rr in zip(systems, xs, rrs):
+        assert rr <= 1e-6
+        xh = host(x)
+        assert np.max(np.abs(b - A.matvec(xh))) / np.max(np.abs(b)) <= 1.01e-6
+        xs_ = np.linalg.solve(A.to_dense(), b)
+        assert rel(xh, xs_) <= 1e-4
+
+
+def test_batch_edge_cases(g):
+    # a 2x2 grid, a zero right-hand side, and a sweep cap that stops a system
+    A1 = P.convdiff_5pt(2, None, (0.3, 0.1))
+    b1 = np.array([1.0, -2.0, 0.5, 3.0])
+    A2, b2 = P.config_c1(m=17)
+    solvers = [g.GabpSolver(A1, "fp64"), g.GabpSolver(A2, "fp64"), g.GabpSolver(A2, "fp64")]
+    batch = g.Batch(solvers, check_every=4)
+    bs = [dev(b1), dev(np.zeros(A2.n)), dev(b2)]
+    xs, its, rrs, sts = batch.solve(bs, 1e-12, 100000)
+    assert sts == [g.OK, g.OK, g.OK]
+    assert rel(host(xs[0]), np.linalg.solve(A1.to_dense(), b1)) <= 1e-12
+    assert its[1] == 0 and np.all(host(xs[1]) == 0.0)
+    xs, its, rrs, sts = batch.solve(bs, 1e-12, 6)
+    assert sts[2] == g.NOT_CONVERGED and its[2] == 6
+    lt, mm = oracle.zero_state(A2)
+    x_o, _, _ = oracle.sweeps(A2, b2, 6, lt, mm)
+    assert rel(host(xs[2]), x_o) <= 1e-12
