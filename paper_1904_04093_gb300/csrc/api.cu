@@ -595,10 +595,11 @@ gabp_status solve_plain(gabp_ctx *ctx, const double *b, double *x, double tol, i
     return st;
 }
 
-// Float GaBP inside double iterative refinement.
+// Float GaBP inside double iterative refinement (on A, or on A^T).
 gabp_status solve_ir(gabp_ctx *ctx, const double *b, double *x, double tol, int max_iter,
-                     int *iters, double *relres)
+                     int *iters, double *relres, bool transposed = false)
 {
+    const double *A64 = transposed ? ctx->aT64 : ctx->a64;
     const int64_t n = ctx->n;
     const size_t nb = n * sizeof(double);
     CKS(ensure_ir(ctx));
@@ -607,7 +608,7 @@ gabp_status solve_ir(gabp_ctx *ctx, const double *b, double *x, double tol, int 
     CK(cudaMemsetAsync(ctx->xacc, 0, nb, s));
     CK(cudaMemsetAsync(ctx->dstat, 0, 2 * sizeof(DevStatus), s));
     // r = b, s = ||b||
-    CK(launch_residual(ctx->L, ctx->a64, ctx->diag64, ctx->b0, ctx->xacc, ctx->rbuf, &ctx->dstat[1], s));
+    CK(launch_residual(ctx->L, A64, ctx->diag64, ctx->b0, ctx->xacc, ctx->rbuf, &ctx->dstat[1], s));
     double bn = 0.0;
     CKS(read_status(ctx, 1, nullptr, &bn, nullptr));
     int total = 0;
@@ -626,11 +627,11 @@ gabp_status solve_ir(gabp_ctx *ctx, const double *b, double *x, double tol, int 
         int inner = 0;
         while (inner < inner_max && total < max_iter) {
             const int k = std::min(std::min(every, inner_max - inner), max_iter - total);
-            CKS(run_chunk(ctx, k, false));
+            CKS(run_chunk(ctx, k, transposed));
             inner += k;
             total += k;
             const DevStatus h = ctx->hstat[0];
-            if (freeze_enabled(ctx) && !(h.flags & FLAG_BREAKDOWN)) CKS(maybe_freeze(ctx, false));
+            if (freeze_enabled(ctx) && !(h.flags & FLAG_BREAKDOWN)) CKS(maybe_freeze(ctx, transposed));
             if (h.flags & FLAG_BREAKDOWN) { st = fail(GABP_E_BREAKDOWN, "zero or non-finite message denominator"); break; }
             const double rin = bits_to_double(h.rmax);  // ||r/s||_inf == 1
             if ((h.flags & FLAG_NAN) || !std::isfinite(rin)) { st = fail(GABP_E_DIVERGED, "inner residual not finite"); break; }
@@ -640,7 +641,7 @@ gabp_status solve_ir(gabp_ctx *ctx, const double *b, double *x, double tol, int 
         // x += s e;  r = b - A x;  s = ||r||
         CK(launch_axpy_status(ctx->xacc, ctx->xbuf, &ctx->dstat[1], n, s));
         CK(cudaMemsetAsync(&ctx->dstat[1], 0, 2 * sizeof(unsigned long long), s));
-        CK(launch_residual(ctx->L, ctx->a64, ctx->diag64, ctx->b0, ctx->xacc, ctx->rbuf, &ctx->dstat[1], s));
+        CK(launch_residual(ctx->L, A64, ctx->diag64, ctx->b0, ctx->xacc, ctx->rbuf, &ctx->dstat[1], s));
         double rinf = 0.0;
         unsigned fl = 0;
         CKS(read_status(ctx, 1, &rinf, nullptr, &fl));
@@ -898,6 +899,7 @@ gabp_status gabp_solve_transpose(gabp_ctx *ctx, const double *g, double *lam, do
         return fail(GABP_E_INVALID_ARG, "bad argument");
     CKS(set_dev(ctx->dev));
     CKS(ensure_transpose(ctx));
+    if (ctx->opt.precision == GABP_FP32_IR) return solve_ir(ctx, g, lam, tol, max_iter, iters, relres, true);
     return solve_plain(ctx, g, lam, tol, max_iter, iters, relres, true);
 }
 

@@ -375,3 +375,42 @@ def config_c5(m: int = 512, seed: int = 1005, sigma: float = 0.3):
     b = uniform_rhs(m * m, rng)
     theta_t = np.random.default_rng(seed + 1).normal(0.0, sigma, size=(m, m))
     return theta, b, theta_t
+
+
+def convdiff_5pt_torch(m: int, D, hv=(0.0, 0.0)):
+    """Differentiable twin of ``convdiff_5pt``: the CSR values as a torch tensor.
+
+    ``D`` is a torch tensor of shape ``(m, m)`` (node diffusion); gradients flow
+    from the returned values to ``D``.  Returns ``(pattern, values)`` where
+    ``pattern`` is the ``CSR`` of ``convdiff_5pt(m, D, hv)`` (the pattern does not
+    depend on positive ``D``) and ``values`` its data in the same slot order.
+    Used for the differentiable-solve workload ``kappa = exp(theta)``.
+    """
+    import torch
+
+    hvx, hvy = float(hv[0]), float(hv[1])
+    Dd = D.detach().cpu().numpy().astype(np.float64)
+    pattern = convdiff_5pt(m, Dd, hv)
+
+    def harm(a, b):
+        return 2.0 * a * b / (a + b)
+
+    Dw = torch.cat([D[:, :1], harm(D[:, 1:], D[:, :-1])], dim=1)
+    De = torch.cat([harm(D[:, :-1], D[:, 1:]), D[:, -1:]], dim=1)
+    Ds = torch.cat([D[:1, :], harm(D[1:, :], D[:-1, :])], dim=0)
+    Dn = torch.cat([harm(D[:-1, :], D[1:, :]), D[-1:, :]], dim=0)
+    coeffs = torch.stack([
+        -Ds - max(hvy, 0.0),
+        -Dw - max(hvx, 0.0),
+        Dw + De + Ds + Dn + abs(hvx) + abs(hvy),
+        -De - max(-hvx, 0.0),
+        -Dn - max(-hvy, 0.0),
+    ], dim=2)
+    iy, ix = np.meshgrid(np.arange(m), np.arange(m), indexing="ij")
+    keep = np.empty((m, m, 5), dtype=bool)
+    for k, (dx, dy) in enumerate(_OFF5):
+        inside = (ix + dx >= 0) & (ix + dx < m) & (iy + dy >= 0) & (iy + dy < m)
+        keep[:, :, k] = True if (dx == 0 and dy == 0) else inside & (coeffs[:, :, k].detach().cpu().numpy() != 0.0)
+    flat_idx = torch.as_tensor(np.flatnonzero(keep.reshape(-1)), device=D.device)
+    values = coeffs.reshape(-1)[flat_idx]
+    return pattern, values
