@@ -39,6 +39,9 @@ if ROOT not in sys.path:
 TOL = 1e-10
 MAX_ITER = 200000
 IR_INNER_MAX = 400    # float sweeps per refinement step (restarting early beats long inner solves)
+# DRAM read + write bytes per launch of k_sweep_stencil<double,4> at 2048 x 2048, measured with
+# ncu (profiles/traffic_sweep_fp64_2048.md); valid for that kernel version and size only.
+TRAFFIC_FP64_SWEEP_2048 = 971.85e6
 SM_COUNT = 152
 FP64_PER_CYCLE = 2    # FP64 arithmetic instructions per cycle per SM (GB300)
 
@@ -54,6 +57,11 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU sample")
     ap.add_argument("--only", choices=["all", "fp64", "mixed"], default="all",
                     help="profiling runs: time only one solver (no e2e, no CPU sample)")
+    ap.add_argument("--workload", choices=["convdiff", "batch", "mg", "adjoint"], default="convdiff",
+                    help="convdiff (default, the headline line); batch / mg / adjoint print "
+                         "secondary lines for the other hot-path workloads")
+    ap.add_argument("--nsys", type=int, default=512, help="batch: number of systems")
+    ap.add_argument("--smax", type=int, default=256, help="batch: largest grid side")
     return ap.parse_args()
 
 
@@ -380,7 +388,8 @@ def run_ours(args):
         "roofline": {
             "kernel": "k_sweep_stencil<double,4> (message sweep of the FP64 solve)",
             "bound": "alu", "achieved": fp64_ach, "peak": fp64_peak, "unit": "TFLOP/s",
-            "frac": fp64_ach / fp64_peak, "traffic": None,
+            "frac": fp64_ach / fp64_peak,
+            "traffic": TRAFFIC_FP64_SWEEP_2048 if args.m == 2048 else None,
             "op_convention": "FP64 arithmetic instructions, add/mul/fma/reciprocal = 1 each; "
                              "8 per directed edge; peak = 2 per cycle per SM x 152 SMs x median SM clock",
             "launch_ms": sweep_ms64, "hbm_achieved_GBs": ach64, "hbm_frac": ach64 / peak,
@@ -409,10 +418,145 @@ def run_ours(args):
     return 0
 
 
+def _timed_region(fn, steps):
+    import torch
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    out = None
+    for _ in range(steps):
+        out = fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps, out
+
+
+def run_batch(args):
+    """Many convection-diffusion systems (sides 16..smax, log-normal diffusion, cell
+    Peclet U[0.1, 2], flow angle U[0, 2 pi)) in one persistent launch, float
+    messages inside double refinement, every system to rr <= 1e-6."""
+    import torch
+    import paper_1904_04093_gb300 as g
+    import problems as P
+    g.load()
+    systems = P.config_c4_batch(nsys=args.nsys, smax=args.smax)
+    solvers = [g.GabpSolver(A, "fp32_ir") for A, _ in systems]
+    bs = [torch.as_tensor(b, device="cuda") for _, b in systems]
+    batch = g.Batch(solvers, check_every=10)
+    blk, cs = batch.tune(bs, 1e-6, 20000)
+    xs, its, rrs, sts = batch.solve(bs, 1e-6, 20000)
+    for _ in range(max(0, args.warmup - 1)):
+        batch.solve(bs, 1e-6, 20000, xs)
+    l0 = g.launch_count()
+    ms, res = _timed_region(lambda: batch.solve(bs, 1e-6, 20000, xs), args.steps)
+    launches = g.launch_count() - l0
+    _, its, rrs, sts = res
+    edges = sum(s.info()["edges"] * it for s, it in zip(solvers, its))
+    sweep_bytes = sum(s.info()["sweep_bytes"] * it for s, it in zip(solvers, its))
+    peak, kind = measured_peaks()
+    line = {"metric": "batched GaBP directed-edge updates/s (every system to rr <= 1e-6)",
+            "value": edges / (ms / 1e3), "unit": "edge-updates/s", "ms_per_step": ms,
+            "steps": args.steps, "dtype": "f32 messages + f64 refinement", "data": "synthetic",
+            "config": {"workload": f"batch_{args.nsys}_convdiff_sides_16_{args.smax}",
+                       "rows": sum(s.n for s in solvers), "block": blk, "cluster": cs},
+            "systems_converged": sum(1 for q in sts if q == g.OK), "sweeps_total": int(sum(its)),
+            "sweeps_max": int(max(its)), "gpu_launches": launches,
+            "roofline": {"kernel": "k_batch_solve<float,4>", "bound": "hbm",
+                         "achieved": sweep_bytes / (ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+                         "frac": sweep_bytes / (ms / 1e3) / 1e9 / peak,
+                         "note": "sweep bytes only (residual checks excluded); critical path = "
+                                 "the slowest system"}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_mg(args):
+    """GaBP-smoothed V-cycles on the 9-point anisotropic hierarchy (eps 0.01),
+    float smoothing, double residuals and transfers, direct coarse solve."""
+    import torch
+    import paper_1904_04093_gb300 as g
+    import problems as P
+    g.load()
+    m = args.m if args.m != 2048 else 4095
+    levels, sides, b = P.config_c3_levels(m_fine=m)
+    solvers = [g.GabpSolver(A, "fp32") for A in levels]
+    mg = g.Multigrid(solvers, sides, mode="cold")
+    bd = torch.as_tensor(b, device="cuda")
+    x = torch.zeros_like(bd)
+    for _ in range(max(3, args.warmup)):
+        mg.vcycle(bd, x, 2, 2)
+    x.zero_()
+    ms, _ = _timed_region(lambda: mg.vcycle(bd, x, 2, 2), args.steps)
+    _, rinf, binf = solvers[0].residual(bd, x)
+    nsw = 20
+    sw_ms = solvers[0].time_sweeps(bd, nsw) / nsw
+    info = solvers[0].info()
+    peak, kind = measured_peaks()
+    ach = info["sweep_bytes"] / (sw_ms / 1e3) / 1e9
+    line = {"metric": "GaBP-smoothed V(2,2) cycle time", "value": ms, "unit": "ms/cycle",
+            "higher_is_better": False, "steps": args.steps, "dtype": "f32 smoothing + f64 residual",
+            "data": "synthetic",
+            "config": {"workload": f"aniso9_eps0.01_{m}x{m}_levels_{len(sides)}", "sides": sides,
+                       "smoother": "cold (Algorithm 3 from zero messages)"},
+            "rr_after_timed_cycles": rinf / binf,
+            "roofline": {"kernel": "k_sweep_stencil<float,8> (fine level)", "bound": "hbm",
+                         "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                         "launch_ms": sw_ms, "bytes_per_launch": info["sweep_bytes"]}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_adjoint(args):
+    """Differentiable solve at 512^2: forward (mixed) + adjoint (mixed) + edge gradient."""
+    import math as _m
+    import numpy as np
+    import torch
+    import paper_1904_04093_gb300 as g
+    from paper_1904_04093_gb300.autograd import gabp_solve
+    import problems as P
+    g.load()
+    m = args.m if args.m != 2048 else 512
+    hv = (2.0 * _m.cos(0.3), 2.0 * _m.sin(0.3))
+    theta, b, theta_t = P.config_c5(m=m)
+    bd = torch.as_tensor(b, device="cuda")
+    xt, _, _, _ = g.GabpSolver(P.convdiff_5pt(m, np.exp(theta_t), hv), "fp32_ir").solve(bd, 1e-10, 200000)
+    pattern, _ = P.convdiff_5pt_torch(m, torch.exp(torch.tensor(theta)), hv)
+    solver = g.GabpSolver(pattern, "fp32_ir")
+
+    def step():
+        th = torch.tensor(theta, dtype=torch.float64, requires_grad=True)
+        _, vals = P.convdiff_5pt_torch(m, torch.exp(th), hv)
+        x = gabp_solve(vals, bd, solver, tol=1e-10)
+        L = ((x - xt) ** 2).sum()
+        L.backward()
+        return float(L.detach())
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        L = step()
+    ms = (time.perf_counter() - t0) * 1e3 / args.steps
+    line = {"metric": "differentiable solve: forward + adjoint to 1e-10", "value": ms,
+            "unit": "ms/step", "higher_is_better": False, "steps": args.steps,
+            "dtype": "f32 messages + f64 refinement", "data": "synthetic",
+            "config": {"workload": f"convdiff2d_5pt_kappa_exp_theta_{m}x{m}", "loss": L},
+            "note": "host wall clock including the host-side matrix assembly and value upload"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch":
+        return run_batch(args)
+    if args.workload == "mg":
+        return run_mg(args)
+    if args.workload == "adjoint":
+        return run_adjoint(args)
     return run_ours(args)
 
 
