@@ -236,7 +236,7 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     s64 = g.GabpSolver(A, "fp64", check_every=10, freeze_lambda=0)
     sfz = g.GabpSolver(A, "fp64", check_every=25, freeze_lambda=1)
-    sir = g.GabpSolver(A, "fp32_ir", check_every=25, ir_inner_tol=1e-3, ir_inner_max=IR_INNER_MAX)
+    sir = g.GabpSolver(A, "fp32_ir", check_every=100, ir_inner_tol=1e-3, ir_inner_max=IR_INNER_MAX)
     info = s64.info()
     info32 = sir.info()
     edges = int(info["edges"])
@@ -472,8 +472,9 @@ def run_batch(args):
 
 
 def run_mg(args):
-    """GaBP-smoothed V-cycles on the 9-point anisotropic hierarchy (eps 0.01),
-    float smoothing, double residuals and transfers, direct coarse solve."""
+    """GaBP-smoothed V(2,2) cycles on the 9-point anisotropic hierarchy (eps 0.01),
+    float smoothing, double residuals and transfers, direct coarse solve; the flood
+    smoother (Sec. 2.2) and the 4-colour smoother (Sec. 5.1), each to rr <= 1e-10."""
     import torch
     import paper_1904_04093_gb300 as g
     import problems as P
@@ -481,28 +482,37 @@ def run_mg(args):
     m = args.m if args.m != 2048 else 4095
     levels, sides, b = P.config_c3_levels(m_fine=m)
     solvers = [g.GabpSolver(A, "fp32") for A in levels]
-    mg = g.Multigrid(solvers, sides, mode="cold")
     bd = torch.as_tensor(b, device="cuda")
-    x = torch.zeros_like(bd)
-    for _ in range(max(3, args.warmup)):
-        mg.vcycle(bd, x, 2, 2)
-    x.zero_()
-    ms, _ = _timed_region(lambda: mg.vcycle(bd, x, 2, 2), args.steps)
-    _, rinf, binf = solvers[0].residual(bd, x)
-    nsw = 20
-    sw_ms = solvers[0].time_sweeps(bd, nsw) / nsw
-    info = solvers[0].info()
     peak, kind = measured_peaks()
-    ach = info["sweep_bytes"] / (sw_ms / 1e3) / 1e9
-    line = {"metric": "GaBP-smoothed V(2,2) cycle time", "value": ms, "unit": "ms/cycle",
-            "higher_is_better": False, "steps": args.steps, "dtype": "f32 smoothing + f64 residual",
-            "data": "synthetic",
+    out = {}
+    for schedule in ("flood", "colored"):
+        mg = g.Multigrid(solvers, sides, mode="cold", schedule=schedule)
+        x = torch.zeros_like(bd)
+        for _ in range(max(3, args.warmup)):
+            mg.vcycle(bd, x, 2, 2)
+        x.zero_()
+        ms, _ = _timed_region(lambda: mg.vcycle(bd, x, 2, 2), args.steps)
+        t0 = time.perf_counter()
+        xs, cycles, rr, st = mg.solve(bd, 1e-10, 400, 2, 2)
+        torch.cuda.synchronize()
+        solve_s = time.perf_counter() - t0
+        nsw = 10
+        sw_ms = solvers[0].time_sweeps(bd, nsw) / nsw
+        out[schedule] = {"ms_per_cycle": ms, "cycles_to_1e-10": cycles, "rr": rr,
+                         "converged": st == g.OK, "solve_s": solve_s,
+                         "fine_sweep_ms": sw_ms}
+        mg.close()
+    info = solvers[0].info()
+    ach = info["sweep_bytes"] / (out["flood"]["fine_sweep_ms"] / 1e3) / 1e9
+    line = {"metric": "GaBP-smoothed multigrid, V(2,2) to rr <= 1e-10", "value": out["colored"]["solve_s"] * 1e3,
+            "unit": "ms", "higher_is_better": False, "steps": args.steps,
+            "dtype": "f32 smoothing + f64 residual", "data": "synthetic",
             "config": {"workload": f"aniso9_eps0.01_{m}x{m}_levels_{len(sides)}", "sides": sides,
-                       "smoother": "cold (Algorithm 3 from zero messages)"},
-            "rr_after_timed_cycles": rinf / binf,
-            "roofline": {"kernel": "k_sweep_stencil<float,8> (fine level)", "bound": "hbm",
+                       "smoother": "Algorithm 3, cold; value = 4-colour schedule"},
+            "schedules": out,
+            "roofline": {"kernel": "k_sweep_stencil<float,8> (fine level, flood)", "bound": "hbm",
                          "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                         "launch_ms": sw_ms, "bytes_per_launch": info["sweep_bytes"]}}
+                         "launch_ms": out["flood"]["fine_sweep_ms"], "bytes_per_launch": info["sweep_bytes"]}}
     print(json.dumps(line), flush=True)
     return 0
 

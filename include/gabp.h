@@ -120,6 +120,22 @@ gabp_status gabp_set_values(gabp_ctx *ctx, const double *data);
 /* Releases the context and its device memory (NULL is ignored). */
 void gabp_destroy(gabp_ctx *ctx);
 
+/*
+ * Selects the message schedule of every later sweep (gabp_sweep, gabp_solve,
+ * the multigrid smoother).  coloured = 0: the flood schedule (Sec. 2.2, the
+ * default).  coloured = 1: a coloured schedule (red-black / 4-colour GaBP,
+ * Sec. 5.1): a sweep visits the colour classes in order and, for every node
+ * of the current class, forms its belief and replaces the messages it sends
+ * from the current messages (Algorithm 1 with the nodes of one class
+ * processed together).  `color` (host, n ints, nullable) gives each node's
+ * class in [0, 254]; adjacent nodes must differ (GABP_E_INVALID_ARG
+ * otherwise).  NULL colours the graph greedily in natural order, which gives
+ * red-black for 5-point and 4 colours for 9-point grids.  *ncolors
+ * (nullable) receives the number of classes.  Precision messages are not
+ * frozen under a coloured schedule; the batched solver always floods.
+ */
+gabp_status gabp_set_schedule(gabp_ctx *ctx, int coloured, const int32_t *color, int *ncolors);
+
 /* Sets every message to zero (the initial state of Algorithm 1). */
 gabp_status gabp_reset(gabp_ctx *ctx);
 

@@ -80,6 +80,8 @@ def lib() -> ctypes.CDLL:
             L.oracle_residual.restype = None
             L.oracle_sweeps.argtypes = [i64, P, P, P, P, i32, P, P, P, P, P, P]
             L.oracle_sweeps.restype = i32
+            L.oracle_sweeps_colored.argtypes = [i64, P, P, P, P, P, i32, i32, P, P, P, P]
+            L.oracle_sweeps_colored.restype = i32
             L.oracle_set_threads.argtypes = [i32]
             L.oracle_set_threads.restype = None
             L.oracle_max_threads.argtypes = []
@@ -149,6 +151,22 @@ def sweeps(A, b, nsweeps: int, lt: np.ndarray, mm: np.ndarray):
     return x, beta, int(st)
 
 
+def sweeps_colored(A, b, color, ncolors: int, nsweeps: int, lt: np.ndarray, mm: np.ndarray):
+    """``nsweeps`` sweeps of Algorithm 1 with a coloured schedule, in place.
+
+    ``color[j]`` in ``[0, ncolors)``, adjacent nodes coloured differently.
+    Returns ``(x, beta, status)``: every node's belief from the sweep it was visited in.
+    """
+    ip, ix, dv = _mat(A)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    col = np.ascontiguousarray(color, dtype=np.int32)
+    x = np.zeros(A.n)
+    beta = np.zeros(A.n)
+    st = lib().oracle_sweeps_colored(A.n, _p(ip), _p(ix), _p(dv), _p(b), _p(col), int(ncolors),
+                                     int(nsweeps), _p(lt), _p(mm), _p(x), _p(beta))
+    return x, beta, int(st)
+
+
 def residual_inf(A, b, x) -> float:
     ip, ix, dv = _mat(A)
     b = np.ascontiguousarray(b, dtype=np.float64)
@@ -165,7 +183,8 @@ def residual(A, b, x) -> np.ndarray:
     return r
 
 
-def solve(A, b, tol: float, max_iter: int, lt=None, mm=None, history: bool = False):
+def solve(A, b, tol: float, max_iter: int, lt=None, mm=None, history: bool = False,
+          color=None, ncolors: int = 0):
     """Algorithm 1 with the flood schedule, from zero messages unless given.
 
     Every iteration is one sweep (beliefs from the current messages, then the
@@ -186,7 +205,10 @@ def solve(A, b, tol: float, max_iter: int, lt=None, mm=None, history: bool = Fal
     if bn == 0.0:
         return dict(x=x, iters=0, rr=0.0, status=OK, history=hist, lt=lt, mm=mm)
     while it < max_iter:
-        x, beta, st = sweeps(A, b, 1, lt, mm)
+        if color is None:
+            x, beta, st = sweeps(A, b, 1, lt, mm)
+        else:
+            x, beta, st = sweeps_colored(A, b, color, ncolors, 1, lt, mm)
         it += 1
         rr = residual_inf(A, b, x) / bn
         if history:
@@ -257,6 +279,20 @@ def prolong_bilinear(e_c: np.ndarray, m_c: int) -> np.ndarray:
     return F.reshape(-1)
 
 
+def grid_colors(m: int, ncolors: int) -> np.ndarray:
+    """Colouring of the m x m grid (i = ix + m iy) with no two stencil neighbours alike:
+    2 colours (red-black, (ix + iy) mod 2) for 5-point operators, 4 colours
+    ((ix mod 2) + 2 (iy mod 2)) for 9-point ones."""
+    iy, ix = np.meshgrid(np.arange(m), np.arange(m), indexing="ij")
+    if ncolors == 2:
+        c = (ix + iy) % 2
+    elif ncolors == 4:
+        c = (ix % 2) + 2 * (iy % 2)
+    else:
+        raise ValueError("ncolors must be 2 or 4")
+    return c.reshape(-1).astype(np.int32)
+
+
 class MGOracle:
     """V-cycle with GaBP as the error-correction smoother (Algorithm 3).
 
@@ -273,13 +309,19 @@ class MGOracle:
       (they do not depend on the right-hand side, Sec. 2.3), the mean
       messages restart from zero;
     * ``"persist"`` both kinds of messages persist across calls.
+
+    ``ncolors`` = 0 smooths with flood sweeps (Sec. 2.2); 2 or 4 with the
+    red-black or 4-colour schedule (Sec. 5.1) on the grid colouring ``grid_colors``.
     """
 
     MODES = ("cold", "warm", "persist")
 
-    def __init__(self, levels, sides, transfer_scale: float = 4.0, mode: str = "cold"):
+    def __init__(self, levels, sides, transfer_scale: float = 4.0, mode: str = "cold",
+                 ncolors: int = 0):
         assert len(levels) == len(sides) >= 1
         assert mode in self.MODES
+        self.ncolors = ncolors
+        self.colors = [grid_colors(m, ncolors) if ncolors else None for m in sides]
         self.levels = levels
         self.sides = list(sides)
         self.scale = float(transfer_scale)
@@ -296,7 +338,10 @@ class MGOracle:
             self.lt[lvl][:] = 0.0
         if self.mode in ("cold", "warm"):
             self.mm[lvl][:] = 0.0
-        e, _, st = sweeps(A, r, nu, self.lt[lvl], self.mm[lvl])
+        if self.ncolors:
+            e, _, st = sweeps_colored(A, r, self.colors[lvl], self.ncolors, nu, self.lt[lvl], self.mm[lvl])
+        else:
+            e, _, st = sweeps(A, r, nu, self.lt[lvl], self.mm[lvl])
         if st != OK:
             raise FloatingPointError("GaBP breakdown in the smoother")
         return x + e

@@ -186,3 +186,68 @@ int oracle_sweeps(int64_t n, const int64_t *indptr, const int32_t *indices,
     }
     return status;
 }
+
+/*
+ * `nsweeps` sweeps of Algorithm 1 with a coloured schedule (Sec. 5.1: red-black
+ * and 4-colour GaBP process one colour class at a time).  color[j] in
+ * [0, ncolors) must give adjacent nodes different colours.  One sweep visits
+ * the colours in order; for every node j of the current colour it forms the
+ * belief x_j from the current messages and then replaces every message j -> i
+ * it sends (eq. nonsymmetric_GaBP_rules), in place.  The messages into a node
+ * of the current colour come from nodes of other colours, so the order of the
+ * nodes inside one colour does not matter.
+ */
+int oracle_sweeps_colored(int64_t n, const int64_t *indptr, const int32_t *indices,
+                          const double *data, const double *b, const int32_t *color,
+                          int ncolors, int nsweeps, double *lt, double *mm, double *x,
+                          double *beta)
+{
+    int breakdown = 0;
+    for (int s = 0; s < nsweeps; ++s) {
+        for (int c = 0; c < ncolors; ++c) {
+            int64_t j;
+            /* beliefs of the colour class from the current messages */
+#pragma omp parallel for schedule(static)
+            for (j = 0; j < n; ++j) {
+                if (color[j] != c) continue;
+                double prec = aval(indptr, indices, data, j, j);
+                double mean = b[j];
+                for (int64_t p = indptr[j]; p < indptr[j + 1]; ++p) {
+                    int64_t k = indices[p];
+                    if (k == j || data[p] == 0.0) continue;
+                    prec += lt[p] * aval(indptr, indices, data, k, j);
+                    mean += mm[p];
+                }
+                beta[j] = prec;
+                x[j] = mean / prec;
+            }
+            /* messages sent by the colour class: j -> i lives in row i at column j */
+            int64_t i;
+#pragma omp parallel for schedule(static) reduction(| : breakdown)
+            for (i = 0; i < n; ++i) {
+                for (int64_t p = indptr[i]; p < indptr[i + 1]; ++p) {
+                    int64_t jj = indices[p];
+                    if (jj == i || color[jj] != c) continue;
+                    if (data[p] == 0.0) {
+                        lt[p] = 0.0;
+                        mm[p] = 0.0;
+                        continue;
+                    }
+                    double den = aval(indptr, indices, data, jj, jj);
+                    double num = b[jj];
+                    for (int64_t q = indptr[jj]; q < indptr[jj + 1]; ++q) {
+                        int64_t k = indices[q];
+                        if (k == jj || k == i || data[q] == 0.0) continue;
+                        den += lt[q] * aval(indptr, indices, data, k, jj);
+                        num += mm[q];
+                    }
+                    if (den == 0.0 || !isfinite(den)) breakdown |= 1;
+                    double lt_ji = -data[p] / den;
+                    lt[p] = lt_ji;
+                    mm[p] = lt_ji * num;
+                }
+            }
+        }
+    }
+    return breakdown ? ORACLE_BREAKDOWN : ORACLE_OK;
+}

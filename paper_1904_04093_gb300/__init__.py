@@ -78,6 +78,7 @@ def load() -> ctypes.CDLL:
         "gabp_set_values": (I, [P, P]),
         "gabp_destroy": (None, [P]),
         "gabp_reset": (I, [P]),
+        "gabp_set_schedule": (I, [P, I, P, PI]),
         "gabp_sweep": (I, [P, P, I, P]),
         "gabp_solve": (I, [P, P, P, D, I, PI, PD]),
         "gabp_solve_transpose": (I, [P, P, P, D, I, PI, PD]),
@@ -204,6 +205,17 @@ class GabpSolver:
     def reset(self) -> None:
         _check(load().gabp_reset(self._h))
 
+    def set_schedule(self, schedule: str = "flood", colors=None) -> int:
+        """``"flood"`` (Sec. 2.2) or ``"colored"`` (red-black / 4-colour, Sec. 5.1);
+        ``colors`` (n ints) or greedy colouring.  Returns the number of colours."""
+        nc = ctypes.c_int()
+        cp = None
+        if colors is not None:
+            self._colors = np.ascontiguousarray(colors, dtype=np.int32)
+            cp = self._colors.ctypes.data
+        _check(load().gabp_set_schedule(self._h, 0 if schedule == "flood" else 1, cp, ctypes.byref(nc)))
+        return int(nc.value)
+
     def set_values(self, data) -> None:
         data = np.ascontiguousarray(data, dtype=np.float64)
         assert data.shape == (self.nnz,)
@@ -272,9 +284,11 @@ class Multigrid:
     """V-cycle with GaBP smoothing over level solvers, finest first (Sec. 4)."""
 
     def __init__(self, levels, sides, transfer_scale: float = 4.0, mode: str = "cold",
-                 stream=None):
+                 schedule: str = "flood", stream=None):
         L = load()
         self.levels = list(levels)
+        for lv in self.levels:
+            lv.set_schedule(schedule)
         self.sides = [int(s) for s in sides]
         self._sh, self.stream = _stream_handle(stream)
         arr = (ctypes.c_void_p * len(self.levels))(*[lv._h for lv in self.levels])

@@ -96,6 +96,8 @@ struct gabp_ctx {
     double *xbuf = nullptr;   // beliefs of the last sweep of a chunk
     double *b0 = nullptr, *xacc = nullptr, *rbuf = nullptr;  // refinement (lazy)
     void *g = nullptr;           // frozen mean-message gains a_e / d_e (lazy)
+    unsigned char *color = nullptr;  // coloured schedule (lazy); ncolors == 0: flood
+    int ncolors = 0;
     bool frozen = false;         // precision messages frozen (both L and P buffers equal)
     bool frozen_transposed = false;
     DevStatus *dstat = nullptr;  // [0] chunk checks, [1] refinement / misc, [2] Lambda change
@@ -405,10 +407,21 @@ gabp_status aggregate(gabp_ctx *ctx)
 
 int block_of(const gabp_ctx *ctx) { return ctx->opt.block_size > 0 ? ctx->opt.block_size : 256; }
 
-// One sweep from state cur into 1 - cur (mean messages only while frozen).
+// One sweep from state cur into 1 - cur (mean messages only while frozen);
+// with a coloured schedule, one in-place phase per colour class.
 cudaError_t sweep_once(gabp_ctx *ctx, bool transposed, double *x, cudaStream_t s)
 {
     const int c0 = ctx->cur, c1 = c0 ^ 1;
+    if (ctx->ncolors > 0) {
+        for (int c = 0; c < ctx->ncolors; ++c) {
+            cudaError_t e = launch_sweep_color(ctx->L, ctx->prec, ctx->color, c,
+                                               transposed ? ctx->aT : ctx->a, ctx->c, ctx->diagT,
+                                               ctx->bT, ctx->Lm[c0], ctx->Mm[c0], ctx->P[c0],
+                                               ctx->B[c0], x, &ctx->dstat[0].flags, s);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
     if (ctx->frozen) {
         ctx->cur = c1;
         return launch_sweep_mean(ctx->L, ctx->prec, ctx->g, ctx->bT, ctx->P[c0], ctx->Mm[c0],
@@ -473,8 +486,9 @@ gabp_status run_chunk(gabp_ctx *ctx, int k, bool transposed)
             ctx->graphs.push_back({k, parity, (int)transposed, frozen, exec});
         }
         CK(cudaGraphLaunch(exec, ctx->stream));
-        count_launches(ctx->stream, (unsigned long long)k + 1);  // k sweeps + residual
-        ctx->cur = parity ^ (k & 1);
+        const int per_sweep = ctx->ncolors > 0 ? ctx->ncolors : 1;
+        count_launches(ctx->stream, (unsigned long long)k * per_sweep + 1);  // sweeps + residual
+        ctx->cur = ctx->ncolors > 0 ? parity : parity ^ (k & 1);  // coloured sweeps work in place
     }
     CK(cudaStreamSynchronize(ctx->stream));
     return GABP_OK;
@@ -550,6 +564,7 @@ gabp_status maybe_freeze(gabp_ctx *ctx, bool transposed)
 
 bool freeze_enabled(const gabp_ctx *ctx)
 {
+    if (ctx->ncolors > 0) return false;  // frozen sweeps use the flood schedule
     if (ctx->opt.freeze_lambda < 0) return ctx->opt.precision == GABP_FP32_IR;
     return ctx->opt.freeze_lambda > 0;
 }
@@ -831,6 +846,64 @@ void gabp_destroy(gabp_ctx *ctx)
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
     delete ctx;
+}
+
+gabp_status gabp_set_schedule(gabp_ctx *ctx, int coloured, const int32_t *color, int *ncolors)
+{
+    if (!ctx || coloured < 0 || coloured > 1) return fail(GABP_E_INVALID_ARG, "bad argument");
+    CKS(set_dev(ctx->dev));
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (auto &g : ctx->graphs) cudaGraphExecDestroy(g.exec);
+    ctx->graphs.clear();
+    if (!coloured) {
+        ctx->ncolors = 0;
+        if (ncolors) *ncolors = 0;
+        return GABP_OK;
+    }
+    const int n = ctx->n;
+    const int64_t *ip = ctx->h_indptr.data();
+    const int32_t *ix = ctx->h_indices.data();
+    std::vector<int> col(n, -1);
+    if (color) {
+        for (int i = 0; i < n; ++i) {
+            if (color[i] < 0 || color[i] > 254) return fail(GABP_E_INVALID_ARG, "colours must lie in [0, 254]");
+            col[i] = color[i];
+        }
+    } else {
+        // greedy colouring of the symmetrised graph in natural order
+        std::vector<int64_t> tp(n + 1, 0);
+        for (int64_t p = 0; p < ip[n]; ++p) tp[ix[p] + 1]++;
+        for (int i = 0; i < n; ++i) tp[i + 1] += tp[i];
+        std::vector<int> trow(ip[n]);
+        std::vector<int64_t> fill(tp.begin(), tp.end() - 1);
+        for (int i = 0; i < n; ++i)
+            for (int64_t p = ip[i]; p < ip[i + 1]; ++p) trow[fill[ix[p]]++] = i;
+        std::vector<int> mark(256, -1);
+        for (int i = 0; i < n; ++i) {
+            for (int64_t p = ip[i]; p < ip[i + 1]; ++p)
+                if (ix[p] != i && col[ix[p]] >= 0) mark[col[ix[p]]] = i;
+            for (int64_t p = tp[i]; p < tp[i + 1]; ++p)
+                if (trow[p] != i && col[trow[p]] >= 0) mark[col[trow[p]]] = i;
+            int c = 0;
+            while (c < 255 && mark[c] == i) ++c;
+            if (c >= 255) return fail(GABP_E_INVALID_ARG, "graph needs more than 255 colours");
+            col[i] = c;
+        }
+    }
+    int nc = 0;
+    for (int i = 0; i < n; ++i) nc = std::max(nc, col[i] + 1);
+    for (int i = 0; i < n; ++i)
+        for (int64_t p = ip[i]; p < ip[i + 1]; ++p)
+            if (ix[p] != i && col[ix[p]] == col[i])
+                return fail(GABP_E_INVALID_ARG, "adjacent nodes share a colour");
+    std::vector<unsigned char> c8(n);
+    for (int i = 0; i < n; ++i) c8[i] = (unsigned char)col[i];
+    if (!ctx->color) CKS(dalloc(ctx, (void **)&ctx->color, (size_t)std::max(n, 1)));
+    if (n) CK(cudaMemcpy(ctx->color, c8.data(), (size_t)n, cudaMemcpyHostToDevice));
+    ctx->ncolors = nc;
+    ctx->frozen = false;
+    if (ncolors) *ncolors = nc;
+    return GABP_OK;
 }
 
 gabp_status gabp_reset(gabp_ctx *ctx)

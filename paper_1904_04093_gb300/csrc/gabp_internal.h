@@ -92,6 +92,11 @@ cudaError_t launch_sweep_mean(const DevLayout &L, int prec, const void *g, const
                               void *Bout, double *x, int block, cudaStream_t s);
 cudaError_t launch_lambda_change(int64_t slots, int prec, const void *L0, const void *L1,
                                  DevStatus *st, cudaStream_t s);
+// one colour phase of the coloured schedule (in place on L, M, P, B)
+cudaError_t launch_sweep_color(const DevLayout &L, int prec, const unsigned char *color, int cphase,
+                               const void *a, const void *c, const void *diag, const void *b,
+                               void *Lm, void *Mm, void *P, void *B, double *x, unsigned *flags,
+                               cudaStream_t s);
 // a^T[e] = a[rev(e)] (mean-message coefficients of the transposed system)
 cudaError_t launch_transpose_coeffs(const DevLayout &L, int prec, const void *a, void *aT,
                                     cudaStream_t s);

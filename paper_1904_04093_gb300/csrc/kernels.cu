@@ -188,7 +188,7 @@ __global__ void __launch_bounds__(256) k_sweep_mean_stencil(
     if (x) x[r] = (double)(Bin[r] / P[r]);
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-        const T mu = ge[k] != T(0) ? ge[k] * (bs[k] - mr[k]) : T(0);
+        const T mu = nonzero(ge[k]) ? ge[k] * (bs[k] - mr[k]) : T(0);
         Mout[(size_t)k * nn + r] = mu;
         bn += mu;
     }
@@ -219,6 +219,98 @@ __global__ void __launch_bounds__(1024) k_sweep_mean_csr(
 template <typename T>
 __global__ void __launch_bounds__(256) k_lambda_change(int64_t slots, const T *__restrict__ L0,
                                                        const T *__restrict__ L1, DevStatus *st);
+
+// ---------------------------------------------------------------------------
+// Coloured schedule (red-black / 4-colour GaBP, Sec. 5.1): one launch per
+// colour class c.  Phase c replaces, in place, every message sent by a node
+// of colour c (stored in its recipients' rows) from the current messages,
+// then every row not of colour c recomputes its aggregates from its current
+// slots.  Race-free in place: phase c reads the aggregates and the incoming
+// messages only of colour-c nodes, and writes only slots sent by colour-c
+// nodes and aggregates of other colours (adjacent nodes differ in colour).
+// A row of colour c forms its belief in phase c from the aggregates it has
+// then (Algorithm 1: the belief before the node's messages are replaced).
+// ---------------------------------------------------------------------------
+template <typename T, int K>
+__global__ void __launch_bounds__(256) k_sweep_color_stencil(
+    int n, StencilParams sp, const unsigned char *__restrict__ color, int cphase,
+    const T *__restrict__ a, const T *__restrict__ c, const T *__restrict__ diag,
+    const T *__restrict__ b, T *Lm, T *Mm, T *P, T *B, double *__restrict__ x,
+    unsigned *__restrict__ flags)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const size_t nn = (size_t)n;
+    if (color[r] == cphase) {
+        if (x) x[r] = (double)(B[r] / P[r]);
+        return;
+    }
+    T pn = diag[r], bn = b[r];
+    bool bad = false;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const size_t e = (size_t)k * nn + r;
+        const T ae = a[e];
+        T lam = Lm[e], mu = Mm[e];
+        if (nonzero(ae)) {
+            const int s = r + sp.off[k];
+            if (color[s] == cphase) {
+                const size_t er = (size_t)sp.krev[k] * nn + s;
+                const T d = P[s] - Lm[er];
+                bad |= bad_den(d);
+                const T q = fast_rcp(d);
+                lam = c[e] * q;
+                mu = ae * (B[s] - Mm[er]) * q;
+                Lm[e] = lam;
+                Mm[e] = mu;
+            }
+        }
+        pn += lam;
+        bn += mu;
+    }
+    P[r] = pn;
+    B[r] = bn;
+    if (bad) atomicOr(flags, FLAG_BREAKDOWN);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_sweep_color_csr(
+    int n, const int *__restrict__ rowptr, const int *__restrict__ col, const int *__restrict__ rev,
+    const unsigned char *__restrict__ color, int cphase, const T *__restrict__ a,
+    const T *__restrict__ c, const T *__restrict__ diag, const T *__restrict__ b, T *Lm, T *Mm,
+    T *P, T *B, double *__restrict__ x, unsigned *__restrict__ flags)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    if (color[r] == cphase) {
+        if (x) x[r] = (double)(B[r] / P[r]);
+        return;
+    }
+    T pn = diag[r], bn = b[r];
+    bool bad = false;
+    for (int e = rowptr[r]; e < rowptr[r + 1]; ++e) {
+        const T ae = a[e];
+        T lam = Lm[e], mu = Mm[e];
+        if (nonzero(ae)) {
+            const int s = col[e];
+            if (color[s] == cphase) {
+                const int er = rev[e];
+                const T d = P[s] - Lm[er];
+                bad |= bad_den(d);
+                const T q = fast_rcp(d);
+                lam = c[e] * q;
+                mu = ae * (B[s] - Mm[er]) * q;
+                Lm[e] = lam;
+                Mm[e] = mu;
+            }
+        }
+        pn += lam;
+        bn += mu;
+    }
+    P[r] = pn;
+    B[r] = bn;
+    if (bad) atomicOr(flags, FLAG_BREAKDOWN);
+}
 
 // ---------------------------------------------------------------------------
 // Aggregates from a message state: P = diag + sum L, B = b + sum M (per row)
@@ -295,6 +387,23 @@ __device__ __forceinline__ void reduce_and_publish(double rmax, double bmax, boo
 }
 
 template <int K>
+__device__ __forceinline__ double residual_row(int i, size_t nn, const StencilParams &sp,
+                                               const double *__restrict__ a64,
+                                               const double *__restrict__ diag64,
+                                               const double *__restrict__ b,
+                                               const double *__restrict__ x)
+{
+    double acc = b[i] - diag64[i] * x[i];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const double ae = a64[(size_t)k * nn + i];
+        if (ae != 0.0) acc += ae * x[i + sp.off[k]];
+    }
+    return acc;
+}
+
+// Four rows per thread per step (independent loads in flight), grid-strided.
+template <int K>
 __global__ void __launch_bounds__(256) k_residual_stencil(
     int n, StencilParams sp, const double *__restrict__ a64, const double *__restrict__ diag64,
     const double *__restrict__ b, const double *__restrict__ x, double *__restrict__ r,
@@ -303,19 +412,29 @@ __global__ void __launch_bounds__(256) k_residual_stencil(
     double rmax = 0.0, bmax = 0.0;
     bool nan = false;
     const size_t nn = (size_t)n;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const double bi = b[i];
-        double acc = bi - diag64[i] * x[i];
+    const int stride = gridDim.x * blockDim.x;
+    for (int i0 = blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += 4 * stride) {
+        double acc[4], bb[4];
 #pragma unroll
-        for (int k = 0; k < K; ++k) {
-            const double ae = a64[(size_t)k * nn + i];
-            if (ae != 0.0) acc += ae * x[i + sp.off[k]];
+        for (int u = 0; u < 4; ++u) {
+            const int i = i0 + u * stride;
+            if (i < n) {
+                acc[u] = residual_row<K>(i, nn, sp, a64, diag64, b, x);
+                bb[u] = b[i];
+            } else {
+                acc[u] = 0.0;
+                bb[u] = 0.0;
+            }
         }
-        if (r) r[i] = acc;
-        const double v = fabs(acc);
-        if (v != v) nan = true;
-        else rmax = fmax(rmax, v);
-        bmax = fmax(bmax, fabs(bi));
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int i = i0 + u * stride;
+            if (i < n && r) r[i] = acc[u];
+            const double v = fabs(acc[u]);
+            if (v != v) nan = true;
+            else rmax = fmax(rmax, v);
+            bmax = fmax(bmax, fabs(bb[u]));
+        }
     }
     reduce_and_publish(rmax, bmax, nan, st);
 }
@@ -626,7 +745,7 @@ cudaError_t launch_residual(const DevLayout &L, const double *a64, const double 
                             cudaStream_t s)
 {
     if (L.n == 0) return cudaSuccess;
-    const int block = 256, grid = grid_for(L.n, block, 152 * 8);
+    const int block = 256, grid = grid_for(L.n, block, 152 * 16);
     if (L.kind == GABP_LAYOUT_STENCIL) {
 #define GABP_RES_CASE(KK)                                                                \
     case KK:                                                                             \
@@ -895,6 +1014,57 @@ cudaError_t launch_lambda_change(int64_t slots, int prec, const void *L0, const 
         k_lambda_change<double><<<grid, 256, 0, s>>>(slots, (const double *)L0, (const double *)L1, st);
     else
         k_lambda_change<float><<<grid, 256, 0, s>>>(slots, (const float *)L0, (const float *)L1, st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sweep_color(const DevLayout &L, int prec, const unsigned char *color, int cphase,
+                               const void *a, const void *c, const void *diag, const void *b,
+                               void *Lm, void *Mm, void *P, void *B, double *x, unsigned *flags,
+                               cudaStream_t s)
+{
+    if (L.n == 0) return cudaSuccess;
+    count_launches(s, 1);
+    const int grid = (L.n + 255) / 256;
+    if (L.kind == GABP_LAYOUT_STENCIL) {
+#define GABP_COL_CASE(KK)                                                                        \
+    case KK:                                                                                     \
+        if (prec == 0)                                                                           \
+            k_sweep_color_stencil<double, KK><<<grid, 256, 0, s>>>(                              \
+                L.n, L.sp, color, cphase, (const double *)a, (const double *)c,                  \
+                (const double *)diag, (const double *)b, (double *)Lm, (double *)Mm, (double *)P, \
+                (double *)B, x, flags);                                                          \
+        else                                                                                     \
+            k_sweep_color_stencil<float, KK><<<grid, 256, 0, s>>>(                               \
+                L.n, L.sp, color, cphase, (const float *)a, (const float *)c,                    \
+                (const float *)diag, (const float *)b, (float *)Lm, (float *)Mm, (float *)P,     \
+                (float *)B, x, flags);                                                           \
+        break;
+        switch (L.sp.K) {
+            GABP_COL_CASE(0)
+            GABP_COL_CASE(2)
+            GABP_COL_CASE(4)
+            GABP_COL_CASE(6)
+            GABP_COL_CASE(8)
+            GABP_COL_CASE(10)
+            GABP_COL_CASE(12)
+            GABP_COL_CASE(14)
+            GABP_COL_CASE(16)
+            default:
+                return cudaErrorInvalidValue;
+        }
+#undef GABP_COL_CASE
+    } else {
+        if (prec == 0)
+            k_sweep_color_csr<double><<<grid, 256, 0, s>>>(
+                L.n, L.rowptr, L.col, L.rev, color, cphase, (const double *)a, (const double *)c,
+                (const double *)diag, (const double *)b, (double *)Lm, (double *)Mm, (double *)P,
+                (double *)B, x, flags);
+        else
+            k_sweep_color_csr<float><<<grid, 256, 0, s>>>(
+                L.n, L.rowptr, L.col, L.rev, color, cphase, (const float *)a, (const float *)c,
+                (const float *)diag, (const float *)b, (float *)Lm, (float *)Mm, (float *)P,
+                (float *)B, x, flags);
+    }
     return cudaGetLastError();
 }
 

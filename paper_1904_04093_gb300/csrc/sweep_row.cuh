@@ -5,10 +5,34 @@
 
 namespace gabp {
 
+// d == 0 or d not finite, decided on the bit pattern (integer pipe): the
+// exponent field all ones is inf / NaN, all bits but the sign zero is +-0.
 template <typename T>
-__device__ __forceinline__ bool bad_den(T d)
+__device__ __forceinline__ bool bad_den(T d);
+
+template <>
+__device__ __forceinline__ bool bad_den<double>(double d)
 {
-    return d == T(0) || !isfinite(d);
+    const unsigned long long u = (unsigned long long)__double_as_longlong(d);
+    return ((u >> 52) & 0x7ffull) == 0x7ffull || (u << 1) == 0ull;
+}
+
+template <>
+__device__ __forceinline__ bool bad_den<float>(float d)
+{
+    const unsigned u = (unsigned)__float_as_int(d);
+    return ((u >> 23) & 0xffu) == 0xffu || (u << 1) == 0u;
+}
+
+// x != 0 on the bit pattern (+-0 count as zero).
+__device__ __forceinline__ bool nonzero(double x)
+{
+    return ((unsigned long long)__double_as_longlong(x) << 1) != 0ull;
+}
+
+__device__ __forceinline__ bool nonzero(float x)
+{
+    return ((unsigned)__float_as_int(x) << 1) != 0u;
 }
 
 // Reciprocal used by the message update.  Float: the correctly rounded
@@ -90,7 +114,7 @@ __device__ __forceinline__ bool sweep_row_stencil(
     for (int k = 0; k < K; ++k) {
         const size_t e = (size_t)k * nn + r;
         T lam = T(0), mu = T(0);
-        if (ae[k] != T(0)) {
+        if (nonzero(ae[k])) {
             const T d = ps[k] - lr[k];
             bad |= bad_den(d);
             const T q = fast_rcp(d);

@@ -55,7 +55,7 @@ def _gabp_loss_grad(g, m, theta, b, x_target, precision, tol):
     x = gabp_solve(vals, bd, solver, tol=tol)
     L = ((x - torch.as_tensor(x_target, device="cuda")) ** 2).sum()
     L.backward()
-    return float(L), th.grad.numpy().copy(), bd.grad.cpu().numpy().copy()
+    return float(L.detach()), th.grad.numpy().copy(), bd.grad.cpu().numpy().copy()
 
 
 @pytest.mark.parametrize("precision,tol,bound", [("fp64", 1e-13, 1e-8), ("fp32_ir", 1e-11, 1e-6)])

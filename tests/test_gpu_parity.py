@@ -275,6 +275,110 @@ def test_frozen_transpose_solve(g):
 
 
 # --------------------------------------------------------------------------
+# coloured schedule (red-black / 4-colour GaBP, Sec. 5.1)
+# --------------------------------------------------------------------------
+def _greedy_colors(A):
+    """Greedy colouring of the symmetrised graph in natural order (test helper)."""
+    n = A.n
+    rows = np.repeat(np.arange(n), np.diff(A.indptr))
+    nbrs = [set() for _ in range(n)]
+    for r, c in zip(rows, A.indices):
+        if r != c:
+            nbrs[r].add(int(c))
+            nbrs[int(c)].add(int(r))
+    col = -np.ones(n, dtype=np.int32)
+    for i in range(n):
+        used = {col[j] for j in nbrs[i] if col[j] >= 0}
+        c = 0
+        while c in used:
+            c += 1
+        col[i] = c
+    return col
+
+
+COLORED = {"c1_32": 2, "lognormal_33": 2, "aniso9_31": 4, "random_300": None, "figure_4x4": None}
+
+
+@pytest.mark.parametrize("layout", ["auto", "csr"])
+@pytest.mark.parametrize("name", list(COLORED))
+def test_colored_sweeps_match_oracle(g, name, layout):
+    A = MATS[name]
+    m = int(round(A.n ** 0.5))
+    colors = oracle.grid_colors(m, COLORED[name]) if COLORED[name] else _greedy_colors(A)
+    nc = int(colors.max()) + 1
+    b = _rhs(A.n, 31)
+    # one sweep from an injected state, then a 30-sweep trajectory
+    lt, mm = oracle.zero_state(A)
+    oracle.sweeps(A, _rhs(A.n, 32), 3, lt, mm)
+    edge = (A.data != 0) & (np.repeat(np.arange(A.n), np.diff(A.indptr)) != A.indices)
+    mm = np.where(edge, np.random.default_rng(33).uniform(-1, 1, A.nnz), 0.0)
+    s = g.GabpSolver(A, "fp64", layout=layout)
+    assert s.set_schedule("colored", None if COLORED[name] is None else colors) == nc
+    s.set_state(dev(oracle.diag_contrib(A, lt)), dev(mm))
+    x_o, _, st = oracle.sweeps_colored(A, b, colors, nc, 1, lt, mm)
+    x = s.sweep(dev(b), 1)
+    lam, mg_ = s.get_state()
+    assert rel(host(x), x_o) <= 1e-12
+    assert rel(host(lam), oracle.diag_contrib(A, lt)) <= 1e-12
+    assert rel(host(mg_), mm) <= 1e-12
+    x_o, _, _ = oracle.sweeps_colored(A, b, colors, nc, 29, lt, mm)
+    x = s.sweep(dev(b), 29)
+    assert rel(host(x), x_o) <= 1e-10
+
+
+@pytest.mark.parametrize("name", ["c1_32", "aniso9_31"])
+def test_colored_solve_matches_oracle(g, name):
+    A = MATS[name]
+    m = int(round(A.n ** 0.5))
+    colors = oracle.grid_colors(m, COLORED[name])
+    b = _rhs(A.n, 34)
+    ref = oracle.solve(A, b, 1e-10, 5000, color=colors, ncolors=COLORED[name])
+    flood = oracle.solve(A, b, 1e-10, 5000)
+    assert ref["status"] == oracle.OK and ref["iters"] < flood["iters"]
+    s = g.GabpSolver(A, "fp64", check_every=1)
+    s.set_schedule("colored")
+    x, it, rr, st = s.solve(dev(b), 1e-10, 5000)
+    assert st == g.OK and it == ref["iters"]
+    assert rel(host(x), ref["x"]) <= 1e-10
+    s.set_schedule("flood")
+    x, it, rr, st = s.solve(dev(b), 1e-10, 5000)
+    assert it == flood["iters"]
+
+
+def test_invalid_coloring_rejected(g):
+    A = MATS["c1_32"]
+    s = g.GabpSolver(A, "fp64")
+    with pytest.raises(g.GabpError):
+        s.set_schedule("colored", np.zeros(A.n, dtype=np.int32))
+
+
+@pytest.mark.parametrize("mode", ["cold", "warm"])
+def test_colored_vcycle_matches_oracle(g, mode):
+    levels, sides, b = _hierarchy()
+    mo = oracle.MGOracle(levels, sides, mode=mode, ncolors=4)
+    solvers = [g.GabpSolver(A, "fp64") for A in levels]
+    mg = g.Multigrid(solvers, sides, mode=mode, schedule="colored")
+    xo = np.zeros(levels[0].n)
+    xg = torch.zeros(levels[0].n, dtype=torch.float64, device="cuda")
+    bd = dev(b)
+    for cyc in range(3):
+        xo = mo.vcycle(b, xo, 2, 2)
+        mg.vcycle(bd, xg, 2, 2)
+        assert rel(host(xg), xo) <= 1e-11, f"cycle {cyc}"
+
+
+def test_colored_mg_solve_converges_faster(g):
+    levels, sides, b = _hierarchy()
+    ref = oracle.MGOracle(levels, sides, ncolors=4).solve(b, 1e-10, 200, 2, 2)
+    assert ref["status"] == oracle.OK
+    solvers = [g.GabpSolver(A, "fp64") for A in levels]
+    mg = g.Multigrid(solvers, sides, schedule="colored")
+    x, c, rr, st = mg.solve(dev(b), 1e-10, 200, 2, 2)
+    assert st == g.OK and c == ref["cycles"]
+    assert rel(host(x), ref["x"]) <= 1e-9
+
+
+# --------------------------------------------------------------------------
 # float messages and mixed precision
 # --------------------------------------------------------------------------
 @pytest.mark.parametrize("name", ["c1_32", "lognormal_33", "aniso9_31", "random_300"])

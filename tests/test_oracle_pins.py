@@ -419,3 +419,50 @@ def test_adjoint_against_finite_differences():
         E[rows[p], A.indices[p]] = step
         fd = (loss(M + E, b) - loss(M - E, b)) / (2 * step)
         assert dA[p] == pytest.approx(fd, rel=1e-6, abs=1e-9)
+
+
+# --------------------------------------------------------------------------
+# Coloured schedule (Sec. 5.1).  A red-black sweep is the flood update of the
+# red senders' messages from the current state, followed by the flood update
+# of the black senders' messages from the state with the red ones replaced;
+# its fixed point is still A^{-1} b (Theorem 1 does not depend on the order).
+# --------------------------------------------------------------------------
+def test_red_black_sweep_is_two_half_flood_updates():
+    m = 9
+    A = P.convdiff_5pt(m, P.lognormal_field(m, 0.5, np.random.default_rng(2)), (1.2, 0.4))
+    colors = oracle.grid_colors(m, 2)
+    b = np.random.default_rng(3).uniform(-1, 1, A.n)
+    lt0, mm0 = oracle.zero_state(A)
+    oracle.sweeps(A, b, 3, lt0, mm0)
+    rows = np.repeat(np.arange(A.n), np.diff(A.indptr))
+    sender = A.indices
+    # reference from flood updates
+    lt_f, mm_f, _ = oracle.update(A, b, lt0, mm0)
+    red = colors[sender] == 0
+    lt1 = np.where(red, lt_f, lt0)
+    mm1 = np.where(red, mm_f, mm0)
+    lt_f2, mm_f2, _ = oracle.update(A, b, lt1, mm1)
+    black = colors[sender] == 1
+    lt_ref = np.where(black, lt_f2, lt1)
+    mm_ref = np.where(black, mm_f2, mm1)
+    # coloured sweep
+    lt, mm = lt0.copy(), mm0.copy()
+    oracle.sweeps_colored(A, b, colors, 2, 1, lt, mm)
+    np.testing.assert_allclose(lt, lt_ref, rtol=1e-15, atol=0)
+    np.testing.assert_allclose(mm, mm_ref, rtol=1e-15, atol=0)
+    assert np.all(rows[~(red | black)] == sender[~(red | black)])  # only diagonal slots left
+
+
+@pytest.mark.parametrize("ncolors,kind", [(2, "5pt"), (4, "9pt")])
+def test_colored_fixed_point_and_fewer_sweeps(ncolors, kind):
+    m = 15
+    A = (P.convdiff_5pt(m, None, (0.8, 0.3)) if kind == "5pt"
+         else P.convdiff_9pt_aniso(m, 0.01, (0.8, 0.3)))
+    b = np.random.default_rng(4).uniform(-1, 1, A.n)
+    colors = oracle.grid_colors(m, ncolors)
+    rc = oracle.solve(A, b, 1e-13, 20000, color=colors, ncolors=ncolors)
+    rf = oracle.solve(A, b, 1e-13, 20000)
+    assert rc["status"] == oracle.OK and rf["status"] == oracle.OK
+    xs = np.linalg.solve(A.to_dense(), b)
+    assert np.max(np.abs(rc["x"] - xs)) / np.max(np.abs(xs)) < 1e-11
+    assert rc["iters"] < rf["iters"]
