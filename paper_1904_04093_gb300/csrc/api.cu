@@ -98,6 +98,8 @@ struct gabp_ctx {
     void *g = nullptr;           // frozen mean-message gains a_e / d_e (lazy)
     unsigned char *color = nullptr;  // coloured schedule (lazy); ncolors == 0: flood
     int ncolors = 0;
+    bool has_masks = false;          // stencil layout: per-colour slot masks valid
+    ColorMasks masks{};
     bool frozen = false;         // precision messages frozen (both L and P buffers equal)
     bool frozen_transposed = false;
     DevStatus *dstat = nullptr;  // [0] chunk checks, [1] refinement / misc, [2] Lambda change
@@ -415,9 +417,10 @@ cudaError_t sweep_once(gabp_ctx *ctx, bool transposed, double *x, cudaStream_t s
     if (ctx->ncolors > 0) {
         for (int c = 0; c < ctx->ncolors; ++c) {
             cudaError_t e = launch_sweep_color(ctx->L, ctx->prec, ctx->color, c,
-                                               transposed ? ctx->aT : ctx->a, ctx->c, ctx->diagT,
-                                               ctx->bT, ctx->Lm[c0], ctx->Mm[c0], ctx->P[c0],
-                                               ctx->B[c0], x, &ctx->dstat[0].flags, s);
+                                               ctx->has_masks ? &ctx->masks : nullptr,
+                                               transposed ? ctx->aT : ctx->a, ctx->c, ctx->Lm[c0],
+                                               ctx->Mm[c0], ctx->P[c0], ctx->B[c0], x,
+                                               &ctx->dstat[0].flags, s);
             if (e != cudaSuccess) return e;
         }
         return cudaSuccess;
@@ -898,6 +901,33 @@ gabp_status gabp_set_schedule(gabp_ctx *ctx, int coloured, const int32_t *color,
                 return fail(GABP_E_INVALID_ARG, "adjacent nodes share a colour");
     std::vector<unsigned char> c8(n);
     for (int i = 0; i < n; ++i) c8[i] = (unsigned char)col[i];
+    // stencil layout: one sender colour per (row colour, diagonal) -> slot masks
+    ctx->has_masks = false;
+    if (ctx->L.kind == GABP_LAYOUT_STENCIL && nc <= KMAXCOLOR) {
+        const int K = ctx->L.sp.K;
+        std::vector<int> tab((size_t)nc * KMAX, -1);
+        bool ok = true;
+        for (int r = 0; r < n && ok; ++r)
+            for (int64_t p = ip[r]; p < ip[r + 1]; ++p) {
+                const int j = ix[p];
+                if (j == r) continue;
+                int k = 0;
+                while (k < K && ctx->L.sp.off[k] != j - r) ++k;
+                if (k == K) { ok = false; break; }
+                int &t = tab[(size_t)col[r] * KMAX + k];
+                if (t < 0) t = col[j];
+                else if (t != col[j]) { ok = false; break; }
+            }
+        if (ok) {
+            std::memset(&ctx->masks, 0, sizeof ctx->masks);
+            for (int cr = 0; cr < nc; ++cr)
+                for (int k = 0; k < K; ++k) {
+                    const int t = tab[(size_t)cr * KMAX + k];
+                    if (t >= 0) ctx->masks.m[cr][t] |= (unsigned short)(1u << k);
+                }
+            ctx->has_masks = true;
+        }
+    }
     if (!ctx->color) CKS(dalloc(ctx, (void **)&ctx->color, (size_t)std::max(n, 1)));
     if (n) CK(cudaMemcpy(ctx->color, c8.data(), (size_t)n, cudaMemcpyHostToDevice));
     ctx->ncolors = nc;

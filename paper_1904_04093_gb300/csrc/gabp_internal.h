@@ -21,6 +21,13 @@ struct StencilParams {
     int krev[KMAX];
 };
 
+// Coloured schedule on a stencil layout: m[cr][c] has bit k set when slot k of
+// a row of colour cr carries a message sent by colour c.
+constexpr int KMAXCOLOR = 8;
+struct ColorMasks {
+    unsigned short m[KMAXCOLOR][KMAXCOLOR];
+};
+
 // Device status word: residual and rhs maxima (bit patterns of non-negative
 // doubles, ordered like unsigned integers) and error flags.
 struct DevStatus {
@@ -93,9 +100,10 @@ cudaError_t launch_sweep_mean(const DevLayout &L, int prec, const void *g, const
 cudaError_t launch_lambda_change(int64_t slots, int prec, const void *L0, const void *L1,
                                  DevStatus *st, cudaStream_t s);
 // one colour phase of the coloured schedule (in place on L, M, P, B)
+// (cm = nullptr: read each sender's colour instead of the table)
 cudaError_t launch_sweep_color(const DevLayout &L, int prec, const unsigned char *color, int cphase,
-                               const void *a, const void *c, const void *diag, const void *b,
-                               void *Lm, void *Mm, void *P, void *B, double *x, unsigned *flags,
+                               const ColorMasks *cm, const void *a, const void *c, void *Lm,
+                               void *Mm, void *P, void *B, double *x, unsigned *flags,
                                cudaStream_t s);
 // a^T[e] = a[rev(e)] (mean-message coefficients of the transposed system)
 cudaError_t launch_transpose_coeffs(const DevLayout &L, int prec, const void *a, void *aT,

@@ -224,19 +224,20 @@ __global__ void __launch_bounds__(256) k_lambda_change(int64_t slots, const T *_
 // Coloured schedule (red-black / 4-colour GaBP, Sec. 5.1): one launch per
 // colour class c.  Phase c replaces, in place, every message sent by a node
 // of colour c (stored in its recipients' rows) from the current messages,
-// then every row not of colour c recomputes its aggregates from its current
-// slots.  Race-free in place: phase c reads the aggregates and the incoming
-// messages only of colour-c nodes, and writes only slots sent by colour-c
-// nodes and aggregates of other colours (adjacent nodes differ in colour).
+// and every row not of colour c moves its aggregates by the change of its
+// messages.  Race-free in place: phase c reads the aggregates and the
+// incoming messages only of colour-c nodes, and writes only slots sent by
+// colour-c nodes and aggregates of other colours (adjacent nodes differ in
+// colour).
 // A row of colour c forms its belief in phase c from the aggregates it has
 // then (Algorithm 1: the belief before the node's messages are replaced).
 // ---------------------------------------------------------------------------
+// Stencil layout without a table: the sender's colour is read per slot.
 template <typename T, int K>
-__global__ void __launch_bounds__(256) k_sweep_color_stencil(
+__global__ void __launch_bounds__(256) k_sweep_color_stencil_gather(
     int n, StencilParams sp, const unsigned char *__restrict__ color, int cphase,
-    const T *__restrict__ a, const T *__restrict__ c, const T *__restrict__ diag,
-    const T *__restrict__ b, T *Lm, T *Mm, T *P, T *B, double *__restrict__ x,
-    unsigned *__restrict__ flags)
+    const T *__restrict__ a, const T *__restrict__ c, T *Lm, T *Mm, T *P, T *B,
+    double *__restrict__ x, unsigned *__restrict__ flags)
 {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n) return;
@@ -245,31 +246,74 @@ __global__ void __launch_bounds__(256) k_sweep_color_stencil(
         if (x) x[r] = (double)(B[r] / P[r]);
         return;
     }
-    T pn = diag[r], bn = b[r];
+    T dp = T(0), db = T(0);
     bool bad = false;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
         const size_t e = (size_t)k * nn + r;
         const T ae = a[e];
-        T lam = Lm[e], mu = Mm[e];
-        if (nonzero(ae)) {
-            const int s = r + sp.off[k];
-            if (color[s] == cphase) {
-                const size_t er = (size_t)sp.krev[k] * nn + s;
-                const T d = P[s] - Lm[er];
-                bad |= bad_den(d);
-                const T q = fast_rcp(d);
-                lam = c[e] * q;
-                mu = ae * (B[s] - Mm[er]) * q;
-                Lm[e] = lam;
-                Mm[e] = mu;
-            }
-        }
-        pn += lam;
-        bn += mu;
+        if (!nonzero(ae)) continue;
+        const int s = r + sp.off[k];
+        if (color[s] != cphase) continue;
+        const size_t er = (size_t)sp.krev[k] * nn + s;
+        const T d = P[s] - Lm[er];
+        bad |= bad_den(d);
+        const T q = fast_rcp(d);
+        const T lam = c[e] * q;
+        const T mu = ae * (B[s] - Mm[er]) * q;
+        dp += lam - Lm[e];
+        db += mu - Mm[e];
+        Lm[e] = lam;
+        Mm[e] = mu;
     }
-    P[r] = pn;
-    B[r] = bn;
+    P[r] += dp;
+    B[r] += db;
+    if (bad) atomicOr(flags, FLAG_BREAKDOWN);
+}
+
+// Stencil layout with a colour table: masks[cr][cphase] has bit k set when the
+// slot k of a row of colour cr carries a message sent by colour cphase (the
+// same for every row of colour cr: checked when the schedule is set).  Only
+// those slots are touched, and the row's aggregates move by the change of
+// its messages, so every slot is read and written once per sweep.
+template <typename T, int K>
+__global__ void __launch_bounds__(256) k_sweep_color_stencil(
+    int n, StencilParams sp, ColorMasks cm, const unsigned char *__restrict__ color, int cphase,
+    const T *__restrict__ a, const T *__restrict__ c, T *Lm, T *Mm, T *P, T *B,
+    double *__restrict__ x, unsigned *__restrict__ flags)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const size_t nn = (size_t)n;
+    const int cr = color[r];
+    if (cr == cphase) {
+        if (x) x[r] = (double)(B[r] / P[r]);
+        return;
+    }
+    const unsigned mask = cm.m[cr][cphase];
+    if (!mask) return;
+    T dp = T(0), db = T(0);
+    bool bad = false;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        if (!(mask & (1u << k))) continue;
+        const size_t e = (size_t)k * nn + r;
+        const T ae = a[e];
+        if (!nonzero(ae)) continue;
+        const int s = r + sp.off[k];
+        const size_t er = (size_t)sp.krev[k] * nn + s;
+        const T d = P[s] - Lm[er];
+        bad |= bad_den(d);
+        const T q = fast_rcp(d);
+        const T lam = c[e] * q;
+        const T mu = ae * (B[s] - Mm[er]) * q;
+        dp += lam - Lm[e];
+        db += mu - Mm[e];
+        Lm[e] = lam;
+        Mm[e] = mu;
+    }
+    P[r] += dp;
+    B[r] += db;
     if (bad) atomicOr(flags, FLAG_BREAKDOWN);
 }
 
@@ -277,8 +321,8 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_sweep_color_csr(
     int n, const int *__restrict__ rowptr, const int *__restrict__ col, const int *__restrict__ rev,
     const unsigned char *__restrict__ color, int cphase, const T *__restrict__ a,
-    const T *__restrict__ c, const T *__restrict__ diag, const T *__restrict__ b, T *Lm, T *Mm,
-    T *P, T *B, double *__restrict__ x, unsigned *__restrict__ flags)
+    const T *__restrict__ c, T *Lm, T *Mm, T *P, T *B, double *__restrict__ x,
+    unsigned *__restrict__ flags)
 {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n) return;
@@ -286,29 +330,26 @@ __global__ void __launch_bounds__(256) k_sweep_color_csr(
         if (x) x[r] = (double)(B[r] / P[r]);
         return;
     }
-    T pn = diag[r], bn = b[r];
+    T dp = T(0), db = T(0);
     bool bad = false;
     for (int e = rowptr[r]; e < rowptr[r + 1]; ++e) {
+        const int s = col[e];
+        if (color[s] != cphase) continue;
         const T ae = a[e];
-        T lam = Lm[e], mu = Mm[e];
-        if (nonzero(ae)) {
-            const int s = col[e];
-            if (color[s] == cphase) {
-                const int er = rev[e];
-                const T d = P[s] - Lm[er];
-                bad |= bad_den(d);
-                const T q = fast_rcp(d);
-                lam = c[e] * q;
-                mu = ae * (B[s] - Mm[er]) * q;
-                Lm[e] = lam;
-                Mm[e] = mu;
-            }
-        }
-        pn += lam;
-        bn += mu;
+        if (!nonzero(ae)) continue;
+        const int er = rev[e];
+        const T d = P[s] - Lm[er];
+        bad |= bad_den(d);
+        const T q = fast_rcp(d);
+        const T lam = c[e] * q;
+        const T mu = ae * (B[s] - Mm[er]) * q;
+        dp += lam - Lm[e];
+        db += mu - Mm[e];
+        Lm[e] = lam;
+        Mm[e] = mu;
     }
-    P[r] = pn;
-    B[r] = bn;
+    P[r] += dp;
+    B[r] += db;
     if (bad) atomicOr(flags, FLAG_BREAKDOWN);
 }
 
@@ -1018,8 +1059,8 @@ cudaError_t launch_lambda_change(int64_t slots, int prec, const void *L0, const 
 }
 
 cudaError_t launch_sweep_color(const DevLayout &L, int prec, const unsigned char *color, int cphase,
-                               const void *a, const void *c, const void *diag, const void *b,
-                               void *Lm, void *Mm, void *P, void *B, double *x, unsigned *flags,
+                               const ColorMasks *cm, const void *a, const void *c, void *Lm,
+                               void *Mm, void *P, void *B, double *x, unsigned *flags,
                                cudaStream_t s)
 {
     if (L.n == 0) return cudaSuccess;
@@ -1028,16 +1069,25 @@ cudaError_t launch_sweep_color(const DevLayout &L, int prec, const unsigned char
     if (L.kind == GABP_LAYOUT_STENCIL) {
 #define GABP_COL_CASE(KK)                                                                        \
     case KK:                                                                                     \
-        if (prec == 0)                                                                           \
-            k_sweep_color_stencil<double, KK><<<grid, 256, 0, s>>>(                              \
-                L.n, L.sp, color, cphase, (const double *)a, (const double *)c,                  \
-                (const double *)diag, (const double *)b, (double *)Lm, (double *)Mm, (double *)P, \
-                (double *)B, x, flags);                                                          \
-        else                                                                                     \
-            k_sweep_color_stencil<float, KK><<<grid, 256, 0, s>>>(                               \
-                L.n, L.sp, color, cphase, (const float *)a, (const float *)c,                    \
-                (const float *)diag, (const float *)b, (float *)Lm, (float *)Mm, (float *)P,     \
-                (float *)B, x, flags);                                                           \
+        if (cm) {                                                                                \
+            if (prec == 0)                                                                       \
+                k_sweep_color_stencil<double, KK><<<grid, 256, 0, s>>>(                          \
+                    L.n, L.sp, *cm, color, cphase, (const double *)a, (const double *)c,         \
+                    (double *)Lm, (double *)Mm, (double *)P, (double *)B, x, flags);             \
+            else                                                                                 \
+                k_sweep_color_stencil<float, KK><<<grid, 256, 0, s>>>(                           \
+                    L.n, L.sp, *cm, color, cphase, (const float *)a, (const float *)c,           \
+                    (float *)Lm, (float *)Mm, (float *)P, (float *)B, x, flags);                 \
+        } else {                                                                                 \
+            if (prec == 0)                                                                       \
+                k_sweep_color_stencil_gather<double, KK><<<grid, 256, 0, s>>>(                   \
+                    L.n, L.sp, color, cphase, (const double *)a, (const double *)c,              \
+                    (double *)Lm, (double *)Mm, (double *)P, (double *)B, x, flags);             \
+            else                                                                                 \
+                k_sweep_color_stencil_gather<float, KK><<<grid, 256, 0, s>>>(                    \
+                    L.n, L.sp, color, cphase, (const float *)a, (const float *)c, (float *)Lm,   \
+                    (float *)Mm, (float *)P, (float *)B, x, flags);                              \
+        }                                                                                        \
         break;
         switch (L.sp.K) {
             GABP_COL_CASE(0)
@@ -1057,13 +1107,11 @@ cudaError_t launch_sweep_color(const DevLayout &L, int prec, const unsigned char
         if (prec == 0)
             k_sweep_color_csr<double><<<grid, 256, 0, s>>>(
                 L.n, L.rowptr, L.col, L.rev, color, cphase, (const double *)a, (const double *)c,
-                (const double *)diag, (const double *)b, (double *)Lm, (double *)Mm, (double *)P,
-                (double *)B, x, flags);
+                (double *)Lm, (double *)Mm, (double *)P, (double *)B, x, flags);
         else
             k_sweep_color_csr<float><<<grid, 256, 0, s>>>(
                 L.n, L.rowptr, L.col, L.rev, color, cphase, (const float *)a, (const float *)c,
-                (const float *)diag, (const float *)b, (float *)Lm, (float *)Mm, (float *)P,
-                (float *)B, x, flags);
+                (float *)Lm, (float *)Mm, (float *)P, (float *)B, x, flags);
     }
     return cudaGetLastError();
 }
