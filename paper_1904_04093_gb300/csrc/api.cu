@@ -114,6 +114,7 @@ struct gabp_batch {
     cudaStream_t cap_stream = nullptr;
     int nsys = 0, prec = 0, K = 0, check_every = 10;
     int refine = 0, inner_max = 2000;  // refinement (contexts created with GABP_FP32_IR)
+    int freeze = 0;                    // freeze precision messages per system once converged
     double inner_tol = 1e-3;
     int block = 0, cs = 0, grid = 0, nbig = 0, sms = 0;  // launch shape (0 = not tuned)
     std::vector<gabp_ctx *> sys;
@@ -1347,6 +1348,7 @@ gabp_status gabp_batch_setup(int nsys, gabp_ctx *const *systems, int check_every
     bt->refine = systems[0]->opt.precision == GABP_FP32_IR ? 1 : 0;
     bt->inner_max = systems[0]->opt.ir_inner_max > 0 ? systems[0]->opt.ir_inner_max : 400;
     bt->inner_tol = systems[0]->opt.ir_inner_tol > 0 ? systems[0]->opt.ir_inner_tol : 1e-3;
+    bt->freeze = freeze_enabled(systems[0]) ? 1 : 0;
     bt->sys.assign(systems, systems + nsys);
     cudaError_t e;
     if ((e = cudaDeviceGetAttribute(&bt->sms, cudaDevAttrMultiProcessorCount, bt->dev)) != cudaSuccess)
@@ -1359,8 +1361,11 @@ gabp_status gabp_batch_setup(int nsys, gabp_ctx *const *systems, int check_every
     std::vector<unsigned char> desc(dsz * nsys);
     for (int i = 0; i < nsys; ++i) {
         gabp_ctx *c = systems[i];
+        if (!c->g) {
+            if ((st = dalloc(c, &c->g, (size_t)c->L.slots * esz(c->prec))) != GABP_OK) return bail(st);
+        }
         fill_batch_sys(bt->prec, desc.data() + i * dsz, c->n, c->L.sp, c->a, c->c, c->diagT, c->a64,
-                       c->diag64, c->Lm, c->Mm, c->P, c->B, c->bT, c->xbuf, c->bres);
+                       c->diag64, c->Lm, c->Mm, c->P, c->B, c->bT, c->xbuf, c->bres, c->g);
         c->frozen = false;  // the batch owns these buffers while it runs
     }
     std::vector<int> order(nsys);
@@ -1404,10 +1409,10 @@ cudaError_t batch_enqueue(gabp_batch *bt, int block, int cs, int grid, double to
     e = bt->prec == 0
             ? launch_batch<double>(bt->K, cs, grid, block, bt->d_sys, bt->d_order, bt->nsys, nbig, bt->d_b,
                                    bt->d_x, bt->d_queue, tol, max_iter, bt->check_every, bt->refine,
-                                   bt->inner_tol, bt->inner_max, bt->d_res, s)
+                                   bt->inner_tol, bt->inner_max, bt->freeze, bt->d_res, s)
             : launch_batch<float>(bt->K, cs, grid, block, bt->d_sys, bt->d_order, bt->nsys, nbig, bt->d_b,
                                   bt->d_x, bt->d_queue, tol, max_iter, bt->check_every, bt->refine,
-                                  bt->inner_tol, bt->inner_max, bt->d_res, s);
+                                  bt->inner_tol, bt->inner_max, bt->freeze, bt->d_res, s);
     if (e != cudaSuccess) return e;
     count_launches(s, 1);
     return cudaMemcpyAsync(bt->h_res, bt->d_res, (size_t)bt->nsys * batch_result_bytes(),

@@ -38,6 +38,7 @@ struct BatchSys {
     const double *a64, *diag64;
     T *L0, *L1, *M0, *M1, *P0, *P1, *B0, *B1, *bT;
     double *e, *r;  // refinement: correction (beliefs of the inner solve), residual
+    T *g;           // frozen gains a_e / d_e (precision messages frozen once converged)
 };
 
 struct BatchResult {
@@ -142,11 +143,26 @@ __device__ double batch_residual(const BatchSys<T> &S, int n, const int *off, co
     return rm;
 }
 
-// `kk` flood sweeps of system S from state `cur` (beliefs of the last go to y).
+// `kk` flood sweeps of system S from state `cur` (beliefs of the last go to y);
+// with frozen precision messages only the mean messages move.
 template <typename T, int K, typename Team>
 __device__ void batch_sweeps(const BatchSys<T> &S, int n, const int *off, const int *krev, int kk,
-                             int &cur, double *y, Team &tm)
+                             int &cur, double *y, Team &tm, bool frozen)
 {
+    if (frozen) {
+        for (int j = 0; j < kk; ++j) {
+            T *Min = cur ? S.M1 : S.M0, *Mout = cur ? S.M0 : S.M1;
+            T *Bin = cur ? S.B1 : S.B0, *Bout = cur ? S.B0 : S.B1;
+            T *Pc = cur ? S.P1 : S.P0;
+            double *yo = j == kk - 1 ? y : nullptr;
+            for (int r = tm.t0; r < n; r += tm.nt)
+                sweep_row_mean_stencil<T, K, true>(r, n, off, krev, S.g, S.bT, Pc, Min, Bin, Mout,
+                                                   Bout, yo);
+            tm.sync();
+            cur ^= 1;
+        }
+        return;
+    }
     for (int j = 0; j < kk; ++j) {
         T *Lin = cur ? S.L1 : S.L0, *Lout = cur ? S.L0 : S.L1;
         T *Min = cur ? S.M1 : S.M0, *Mout = cur ? S.M0 : S.M1;
@@ -163,6 +179,46 @@ __device__ void batch_sweeps(const BatchSys<T> &S, int n, const int *off, const 
     }
 }
 
+// Freezes the precision messages of S once the last sweep changed none of them
+// by more than `rel` times the largest (returns the new frozen state): gains
+// g = a / (P_s - L[rev]) from the current state, both L and both P buffers
+// set to the current ones.
+template <typename T, int K, typename Team>
+__device__ bool batch_maybe_freeze(const BatchSys<T> &S, int n, const int *off, const int *krev,
+                                   int cur, double rel, Team &tm)
+{
+    const T *Lc = cur ? S.L1 : S.L0, *Lp = cur ? S.L0 : S.L1;
+    double dm = 0.0, lm = 0.0;
+    for (int r = tm.t0; r < n; r += tm.nt)
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const double l1 = (double)__ldcg(Lc + (size_t)k * n + r);
+            dm = fmax(dm, fabs(l1 - (double)__ldcg(Lp + (size_t)k * n + r)));
+            lm = fmax(lm, fabs(l1));
+        }
+    dm = tm.max(dm);
+    lm = tm.max(lm);
+    if (!(dm <= rel * lm)) return false;
+    T *Lo = cur ? S.L0 : S.L1, *Pc = cur ? S.P1 : S.P0, *Po = cur ? S.P0 : S.P1;
+    for (int r = tm.t0; r < n; r += tm.nt) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const size_t e = (size_t)k * n + r;
+            const T ae = S.a[e];
+            T ge = T(0);
+            if (nonzero(ae)) {
+                const int s = r + off[k];
+                ge = ae * fast_rcp(__ldcg(Pc + s) - __ldcg(Lc + (size_t)krev[k] * n + s));
+            }
+            S.g[e] = ge;
+            Lo[e] = __ldcg(Lc + e);
+        }
+        Po[r] = __ldcg(Pc + r);
+    }
+    tm.sync();
+    return true;
+}
+
 // Solves system `id` with team `tm` (every thread of the team calls this with
 // the same arguments; all control flow below is uniform across the team).
 //
@@ -176,8 +232,11 @@ __device__ void batch_sweeps(const BatchSys<T> &S, int n, const int *off, const 
 template <typename T, int K, typename Team>
 __device__ void solve_system(const BatchSys<T> &S, int id, const double *b, double *x, Team &tm,
                              double tol, int max_iter, int check_every, int refine,
-                             double inner_tol, int inner_max, BatchResult *res, bool leader)
+                             double inner_tol, int inner_max, int freeze, BatchResult *res,
+                             bool leader)
 {
+    bool frozen = false;
+    const double frz_rel = sizeof(T) == 8 ? 1e-14 : 1e-6;
     const int n = S.n, t0 = tm.t0, nt = tm.nt;
     const int *off = tm.sh->off, *krev = tm.sh->krev;
     unsigned *flags = tm.flags();
@@ -210,8 +269,9 @@ __device__ void solve_system(const BatchSys<T> &S, int id, const double *b, doub
     if (!refine) {
         while (status == GABP_E_NOT_CONVERGED && it < max_iter) {
             const int kk = min(check_every, max_iter - it);
-            batch_sweeps<T, K>(S, n, off, krev, kk, cur, x, tm);
+            batch_sweeps<T, K>(S, n, off, krev, kk, cur, x, tm, frozen);
             it += kk;
+            if (freeze && !frozen && !*flags) frozen = batch_maybe_freeze<T, K>(S, n, off, krev, cur, frz_rel, tm);
             bool nan = false;
             double rm = batch_residual<T, K>(S, n, off, b, 1.0, x, nullptr, t0, nt, nan);
             if (nan) atomicOr(flags, 2u);
@@ -249,9 +309,11 @@ __device__ void solve_system(const BatchSys<T> &S, int id, const double *b, doub
             int inner = 0;
             while (inner < inner_max && it < max_iter) {
                 const int kk = min(min(check_every, inner_max - inner), max_iter - it);
-                batch_sweeps<T, K>(S, n, off, krev, kk, cur, S.e, tm);
+                batch_sweeps<T, K>(S, n, off, krev, kk, cur, S.e, tm, frozen);
                 inner += kk;
                 it += kk;
+                if (freeze && !frozen && !*flags)
+                    frozen = batch_maybe_freeze<T, K>(S, n, off, krev, cur, frz_rel, tm);
                 bool nan = false;
                 double rin = batch_residual<T, K>(S, n, off, S.r, 1.0 / scale, S.e, nullptr, t0,
                                                   nt, nan);
@@ -297,7 +359,7 @@ __global__ void __launch_bounds__(512) k_batch_solve(
     const BatchSys<T> *__restrict__ sys, const int *__restrict__ order, int nsys, int nbig,
     const double *const *__restrict__ bptr, double *const *__restrict__ xptr, int *queue,
     double tol, int max_iter, int check_every, int refine, double inner_tol, int inner_max,
-    BatchResult *__restrict__ res)
+    int freeze, BatchResult *__restrict__ res)
 {
     __shared__ BatchShared sh;
     const int tid = threadIdx.x;
@@ -319,7 +381,7 @@ __global__ void __launch_bounds__(512) k_batch_solve(
                 sh.krev[tid] = sys[id].krev[tid];
             }
             solve_system<T, K>(sys[id], id, bptr[id], xptr[id], tm, tol, max_iter, check_every,
-                               refine, inner_tol, inner_max, res, rank0 && tid == 0);
+                               refine, inner_tol, inner_max, freeze, res, rank0 && tid == 0);
         }
     }
     // phase 2: no distributed shared memory from here on
@@ -338,7 +400,7 @@ __global__ void __launch_bounds__(512) k_batch_solve(
             sh.krev[tid] = sys[id].krev[tid];
         }
         solve_system<T, K>(sys[id], id, bptr[id], xptr[id], tm, tol, max_iter, check_every, refine,
-                           inner_tol, inner_max, res, tid == 0);
+                           inner_tol, inner_max, freeze, res, tid == 0);
     }
 }
 
@@ -348,7 +410,7 @@ template <typename T, int K>
 cudaError_t launch_batch_k(int cs, int grid, int block, const void *sys, const int *order, int nsys,
                            int nbig, const double *const *bptr, double *const *xptr, int *queue, double tol,
                            int max_iter, int check_every, int refine, double inner_tol,
-                           int inner_max, void *res, cudaStream_t s)
+                           int inner_max, int freeze, void *res, cudaStream_t s)
 {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid, 1, 1);
@@ -364,19 +426,20 @@ cudaError_t launch_batch_k(int cs, int grid, int block, const void *sys, const i
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, k_batch_solve<T, K>, (const BatchSys<T> *)sys, order, nsys, nbig, bptr,
                               xptr, queue, tol, max_iter, check_every, refine, inner_tol, inner_max,
-                              (BatchResult *)res);
+                              freeze, (BatchResult *)res);
 }
 
 template <typename T>
 cudaError_t launch_batch(int K, int cs, int grid, int block, const void *sys, const int *order,
                          int nsys, int nbig, const double *const *bptr, double *const *xptr, int *queue,
                          double tol, int max_iter, int check_every, int refine, double inner_tol,
-                         int inner_max, void *res, cudaStream_t s)
+                         int inner_max, int freeze, void *res, cudaStream_t s)
 {
 #define GABP_BATCH_CASE(KK)                                                                     \
     case KK:                                                                                    \
         return launch_batch_k<T, KK>(cs, grid, block, sys, order, nsys, nbig, bptr, xptr, queue, tol, \
-                                     max_iter, check_every, refine, inner_tol, inner_max, res, s);
+                                     max_iter, check_every, refine, inner_tol, inner_max, freeze, \
+                                     res, s);
     switch (K) {
         GABP_BATCH_CASE(0)
         GABP_BATCH_CASE(2)
@@ -426,17 +489,17 @@ int batch_max_clusters(int K, int cs, int block)
 
 template cudaError_t launch_batch<float>(int, int, int, int, const void *, const int *, int, int,
                                          const double *const *, double *const *, int *, double,
-                                         int, int, int, double, int, void *, cudaStream_t);
+                                         int, int, int, double, int, int, void *, cudaStream_t);
 template cudaError_t launch_batch<double>(int, int, int, int, const void *, const int *, int, int,
                                           const double *const *, double *const *, int *, double,
-                                          int, int, int, double, int, void *, cudaStream_t);
+                                          int, int, int, double, int, int, void *, cudaStream_t);
 template int batch_max_clusters<float>(int, int, int);
 template int batch_max_clusters<double>(int, int, int);
 
 void fill_batch_sys(int prec, void *dst, int n, const StencilParams &sp, const void *a, const void *c,
                     const void *diag, const double *a64, const double *diag64, void *const L[2],
                     void *const M[2], void *const P[2], void *const B[2], void *bT, double *e,
-                    double *r)
+                    double *r, void *g)
 {
     auto fill = [&](auto *S, auto *tag) {
         using T = std::remove_pointer_t<decltype(tag)>;
@@ -462,6 +525,7 @@ void fill_batch_sys(int prec, void *dst, int n, const StencilParams &sp, const v
         S->bT = (T *)bT;
         S->e = e;
         S->r = r;
+        S->g = (T *)g;
     };
     if (prec == 0) fill((BatchSys<double> *)dst, (double *)nullptr);
     else fill((BatchSys<float> *)dst, (float *)nullptr);

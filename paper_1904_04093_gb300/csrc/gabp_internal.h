@@ -121,13 +121,13 @@ template <typename T>
 cudaError_t launch_batch(int K, int cs, int grid, int block, const void *sys, const int *order,
                          int nsys, int nbig, const double *const *bptr, double *const *xptr, int *queue,
                          double tol, int max_iter, int check_every, int refine, double inner_tol,
-                         int inner_max, void *res, cudaStream_t s);
+                         int inner_max, int freeze, void *res, cudaStream_t s);
 template <typename T>
 int batch_max_clusters(int K, int cs, int block);
 void fill_batch_sys(int prec, void *dst, int n, const StencilParams &sp, const void *a, const void *c,
                     const void *diag, const double *a64, const double *diag64, void *const L[2],
                     void *const M[2], void *const P[2], void *const B[2], void *bT, double *e,
-                    double *r);
+                    double *r, void *g);
 size_t batch_sys_bytes(int prec);
 size_t batch_result_bytes();  // {int iters; int status; double rr;}
 

@@ -131,4 +131,34 @@ __device__ __forceinline__ bool sweep_row_stencil(
     return bad;
 }
 
+// Mean-message update of row r with frozen precision messages (the fixed
+// gains g_e = a_e / d_e): M'[e] = g_e (B_s - M[rev e]), B'_r = b_r + sum M'.
+template <typename T, int K, bool kCoherent = false>
+__device__ __forceinline__ void sweep_row_mean_stencil(
+    int r, int n, const int *off, const int *krev, const T *__restrict__ g,
+    const T *__restrict__ b, const T *__restrict__ P, const T *__restrict__ Min,
+    const T *__restrict__ Bin, T *__restrict__ Mout, T *__restrict__ Bout, double *__restrict__ x)
+{
+    const size_t nn = (size_t)n;
+    T ge[K > 0 ? K : 1], bs[K > 0 ? K : 1], mr[K > 0 ? K : 1];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const size_t e = (size_t)k * nn + r;
+        ge[k] = ld_state<kCoherent>(g + e);
+        int s = r + off[k];
+        s = s < 0 ? 0 : (s >= n ? n - 1 : s);
+        bs[k] = ld_state<kCoherent>(Bin + s);
+        mr[k] = ld_state<kCoherent>(Min + (size_t)krev[k] * nn + s);
+    }
+    T bn = ld_state<kCoherent>(b + r);
+    if (x) x[r] = (double)(ld_state<kCoherent>(Bin + r) / ld_state<kCoherent>(P + r));
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const T mu = nonzero(ge[k]) ? ge[k] * (bs[k] - mr[k]) : T(0);
+        Mout[(size_t)k * nn + r] = mu;
+        bn += mu;
+    }
+    Bout[r] = bn;
+}
+
 }  // namespace gabp

@@ -112,3 +112,19 @@ def test_batch_edge_cases(g):
     lt, mm = oracle.zero_state(A2)
     x_o, _, _ = oracle.sweeps(A2, b2, 6, lt, mm)
     assert rel(host(xs[2]), x_o) <= 1e-12
+
+
+def test_batch_frozen_precision_messages_match_single(g):
+    """With freeze_lambda the batched systems freeze their precision messages at
+    the same check as gabp_solve does and follow the same iterates."""
+    systems = _systems(nsys=6, seed=19)
+    solvers = [g.GabpSolver(A, "fp64", check_every=5, freeze_lambda=1) for A, _ in systems]
+    batch = g.Batch(solvers, check_every=5)
+    batch.set_shape(256, 2)
+    xs, its, rrs, sts = batch.solve([dev(b) for _, b in systems], 1e-10, 5000)
+    assert all(s == g.OK for s in sts)
+    for (A, b), x, it in zip(systems, xs, its):
+        single = g.GabpSolver(A, "fp64", check_every=5, freeze_lambda=1)
+        x1, it1, rr1, st1 = single.solve(dev(b), 1e-10, 5000)
+        assert st1 == g.OK and abs(it - it1) <= 5
+        assert rel(host(x), host(x1)) <= 1e-9
