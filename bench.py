@@ -157,6 +157,23 @@ def gpu_index_for(local_rank: int):
     return str(local_rank)
 
 
+def max_over_ranks(v: float, device=None) -> float:
+    """Largest value of v over all ranks (the slowest rank's time); v itself at one rank."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(v)
+    t = torch.tensor([float(v)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, ms_max: float, world: int) -> float:
+    """Units per second of the whole job: every rank's units over the slowest rank's time
+    (each rank runs an independent replica of the same workload)."""
+    return world * units_per_rank / (ms_max / 1e3)
+
+
 def cpu_oracle_rate(A, b, budget_s: float):
     """Edge updates/s of the FP64 CPU oracle on the full matrix, bounded sample."""
     import oracle
@@ -247,12 +264,6 @@ def run_ours(args):
         if world > 1:
             torch.distributed.barrier()
 
-    def max_over_ranks(v: float) -> float:
-        if world == 1:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        return float(t.item())
 
     def timed(solver, steps):
         barrier()
@@ -325,13 +336,13 @@ def run_ours(args):
     barrier()
     ms_e2e = e0.elapsed_time(e1) / args.steps
 
-    ms64_max = max_over_ranks(ms64)
-    ms_fz_max = max_over_ranks(ms_fz)
-    ms_ir_max = max_over_ranks(ms_ir)
-    ms_e2e_max = max_over_ranks(ms_e2e)
+    ms64_max = max_over_ranks(ms64, dev)
+    ms_fz_max = max_over_ranks(ms_fz, dev)
+    ms_ir_max = max_over_ranks(ms_ir, dev)
+    ms_e2e_max = max_over_ranks(ms_e2e, dev)
     sweeps64 = its64[-1]
-    value = world * edges * sweeps64 / (ms64_max / 1e3)
-    e2e_value = world * edges * it_e2e / (ms_e2e_max / 1e3)
+    value = whole_job_rate(edges * sweeps64, ms64_max, world)
+    e2e_value = whole_job_rate(edges * it_e2e, ms_e2e_max, world)
     peak, peak_kind = measured_peaks()
     ach64 = info["sweep_bytes"] / (sweep_ms64 / 1e3) / 1e9
     ach32 = info32["sweep_bytes"] / (sweep_ms32 / 1e3) / 1e9
