@@ -398,3 +398,89 @@ def adjoint(A, b, g):
 
 if __name__ == "__main__":  # pragma: no cover
     print(build(force="--force" in sys.argv))
+
+
+# ---------------------------------------------------------------------------
+# Line GaBP: Algorithm 2 (two-layer generalized GaBP, Sec. 3.2-3.4) with the
+# grid lines as large regions and single nodes as small regions (the
+# partition the paper calls "line GaBP").  Valid for 5-point grids, where
+# every edge lies inside a row or a column.
+# ---------------------------------------------------------------------------
+
+def _line_nodes(m: int, family: str, k: int) -> np.ndarray:
+    if family == "row":
+        return k * m + np.arange(m)
+    return np.arange(m) * m + k
+
+
+def _line_matrix(A, idx: np.ndarray) -> np.ndarray:
+    """[A]_L: the entries of A between the nodes of one line (Sec. 3.2 brackets)."""
+    pos = {int(v): t for t, v in enumerate(idx)}
+    T = np.zeros((len(idx), len(idx)))
+    for t, v in enumerate(idx):
+        for p in range(A.indptr[v], A.indptr[v + 1]):
+            j = int(A.indices[p])
+            if j in pos:
+                T[t, pos[j]] = A.data[p]
+    return T
+
+
+def line_zero_state(n: int):
+    """Messages from every row and every column region to each node: (Lambda, m) pairs."""
+    return {"LH": np.zeros(n), "MH": np.zeros(n), "LV": np.zeros(n), "MV": np.zeros(n)}
+
+
+def line_sweeps(A, m: int, b, nsweeps: int, state):
+    """``nsweeps`` sweeps of Algorithm 2 over the region graph of rows and
+    columns: first every row region, then every column region (regions of one
+    family share no node, so each family is processed at once).  For a region
+    L with children l and the other parent L' of each child:
+
+        b0 = [b]_L + sum_l m_{L'l},   Lam0 = [A]_L + sum_l Lambda_{L'l}
+        [x]_L = Lam0^{-1} b0
+        m_{Ll}      = ([Lam0^{-1}]_l)^{-1} x_l - b_l - m_{L'l}
+        Lambda_{Ll} = ([Lam0^{-1}]_l)^{-1} - A_ll - Lambda_{L'l}
+
+    In place on ``state``; returns x as last written (by the column regions).
+    """
+    b = np.asarray(b, dtype=np.float64)
+    n = m * m
+    diag = np.zeros(n)
+    rows = np.repeat(np.arange(n), np.diff(A.indptr))
+    dmask = rows == A.indices
+    diag[rows[dmask]] = A.data[dmask]
+    x = np.zeros(n)
+    for _ in range(nsweeps):
+        for family, (Lown, Mown, Loth, Moth) in (("row", ("LH", "MH", "LV", "MV")),
+                                                 ("col", ("LV", "MV", "LH", "MH"))):
+            newL = state[Lown].copy()
+            newM = state[Mown].copy()
+            for k in range(m):
+                idx = _line_nodes(m, family, k)
+                Lam0 = _line_matrix(A, idx) + np.diag(state[Loth][idx])
+                b0 = b[idx] + state[Moth][idx]
+                xl = np.linalg.solve(Lam0, b0)
+                S = 1.0 / np.diag(np.linalg.inv(Lam0))
+                newM[idx] = S * xl - b[idx] - state[Moth][idx]
+                newL[idx] = S - diag[idx] - state[Loth][idx]
+                x[idx] = xl
+            state[Lown] = newL
+            state[Mown] = newM
+    return x
+
+
+def line_solve(A, m: int, b, tol: float, max_iter: int):
+    """Line GaBP iterated until ||b - A x||_inf / ||b||_inf <= tol (Algorithm 2's loop)."""
+    b = np.asarray(b, dtype=np.float64)
+    bn = float(np.max(np.abs(b)))
+    st = line_zero_state(A.n)
+    x = np.zeros(A.n)
+    rr = 1.0
+    for it in range(1, max_iter + 1):
+        x = line_sweeps(A, m, b, 1, st)
+        rr = residual_inf(A, b, x) / bn
+        if rr <= tol:
+            return dict(x=x, iters=it, rr=rr, status=OK, state=st)
+        if not np.isfinite(rr) or rr > DIVERGENCE_LIMIT:
+            return dict(x=x, iters=it, rr=rr, status=DIVERGED, state=st)
+    return dict(x=x, iters=max_iter, rr=rr, status=NOT_CONVERGED, state=st)

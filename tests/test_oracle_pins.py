@@ -466,3 +466,50 @@ def test_colored_fixed_point_and_fewer_sweeps(ncolors, kind):
     xs = np.linalg.solve(A.to_dense(), b)
     assert np.max(np.abs(rc["x"] - xs)) / np.max(np.abs(xs)) < 1e-11
     assert rc["iters"] < rf["iters"]
+
+
+# --------------------------------------------------------------------------
+# Line GaBP (Algorithm 2 with grid lines as large regions, Sec. 3).
+# --------------------------------------------------------------------------
+def test_line_first_messages_are_block_schur_complements():
+    """From zero messages, a row region's message to node l is the correction of
+    eq. single_region_corrections: -A_{l,rest} A_{rest,rest}^{-1} A_{rest,l} for
+    the precision and -A_{l,rest} A_{rest,rest}^{-1} b_rest for the mean."""
+    m = 7
+    A = P.convdiff_5pt(m, P.lognormal_field(m, 0.5, np.random.default_rng(5)), (1.3, 0.7))
+    b = np.random.default_rng(6).uniform(-1, 1, m * m)
+    st = oracle.line_zero_state(A.n)
+    oracle.line_sweeps(A, m, b, 1, st)  # rows see zero column messages in the first sweep
+    M = A.to_dense()
+    for row in (0, 3, 6):
+        idx = row * m + np.arange(m)
+        T = M[np.ix_(idx, idx)]
+        for t in range(m):
+            rest = [u for u in range(m) if u != t]
+            W = T[np.ix_([t], rest)] @ np.linalg.inv(T[np.ix_(rest, rest)])
+            assert st["LH"][idx[t]] == pytest.approx(-(W @ T[np.ix_(rest, [t])]).item(), rel=1e-12)
+            assert st["MH"][idx[t]] == pytest.approx(-(W @ b[idx[rest]]).item(), rel=1e-11, abs=1e-14)
+
+
+def test_line_decoupled_rows_exact_in_one_sweep():
+    """Without vertical couplings every row is its own region's tree: exact at once."""
+    m = 9
+    A = P.convdiff_9pt_aniso(m, 0.0, (0.9, 0.0))  # eps = 0, no vertical flow: rows decouple
+    Md = A.to_dense()
+    assert all(Md[i, j] == 0 for i in range(m * m) for j in range(m * m) if abs(i - j) == m)
+    b = np.random.default_rng(7).uniform(-1, 1, m * m)
+    st = oracle.line_zero_state(A.n)
+    x = oracle.line_sweeps(A, m, b, 1, st)
+    np.testing.assert_allclose(x, np.linalg.solve(Md, b), rtol=1e-12)
+
+
+def test_line_fixed_point_and_fewer_sweeps():
+    """Generalized consistency (Sec. 3.4): the fixed point is A^{-1} b; on the
+    convection-diffusion workload it needs fewer sweeps than flood GaBP."""
+    m = 16
+    A, b = P.config_c2(m=m)
+    r = oracle.line_solve(A, m, b, 1e-13, 2000)
+    assert r["status"] == oracle.OK
+    xs = np.linalg.solve(A.to_dense(), b)
+    assert np.max(np.abs(r["x"] - xs)) / np.max(np.abs(xs)) < 1e-11
+    assert r["iters"] < oracle.solve(A, b, 1e-13, 20000)["iters"]
