@@ -122,19 +122,36 @@ void gabp_destroy(gabp_ctx *ctx);
 
 /*
  * Selects the message schedule of every later sweep (gabp_sweep, gabp_solve,
- * the multigrid smoother).  coloured = 0: the flood schedule (Sec. 2.2, the
- * default).  coloured = 1: a coloured schedule (red-black / 4-colour GaBP,
- * Sec. 5.1): a sweep visits the colour classes in order and, for every node
- * of the current class, forms its belief and replaces the messages it sends
- * from the current messages (Algorithm 1 with the nodes of one class
- * processed together).  `color` (host, n ints, nullable) gives each node's
- * class in [0, 254]; adjacent nodes must differ (GABP_E_INVALID_ARG
- * otherwise).  NULL colours the graph greedily in natural order, which gives
- * red-black for 5-point and 4 colours for 9-point grids.  *ncolors
- * (nullable) receives the number of classes.  Precision messages are not
- * frozen under a coloured schedule; the batched solver always floods.
+ * the multigrid smoother); the messages restart from zero.
+ *  schedule = 0: the flood schedule (Sec. 2.2, the default).
+ *  schedule = 1: a coloured schedule (red-black / 4-colour GaBP, Sec. 5.1): a
+ *    sweep visits the colour classes in order and, for every node of the
+ *    current class, forms its belief and replaces the messages it sends from
+ *    the current messages (Algorithm 1 with the nodes of one class processed
+ *    together).  `color` (host, n ints, nullable) gives each node's class in
+ *    [0, 254]; adjacent nodes must differ (GABP_E_INVALID_ARG otherwise).
+ *    NULL colours the graph greedily in natural order, which gives red-black
+ *    for 5-point and 4 colours for 9-point grids.  *ncolors (nullable)
+ *    receives the number of classes.
+ *  schedule = 2: line GaBP -- Algorithm 2 (Sec. 3) with the rows and columns
+ *    of an m x m grid (node i = ix + m iy) as large regions and single nodes
+ *    as small regions: a sweep updates every row region, then every column
+ *    region (regions of one family share no node), each by an exact
+ *    tridiagonal solve; the beliefs are the column regions' solutions.
+ *    Needs n = m^2 and every edge inside a row or a column (5-point grids),
+ *    GABP_E_INVALID_ARG otherwise.  The transposed solve is not available
+ *    under this schedule; gabp_get_line_state reads its messages.
+ * Precision messages are not frozen under schedules 1 and 2; the batched
+ * solver always floods.
  */
-gabp_status gabp_set_schedule(gabp_ctx *ctx, int coloured, const int32_t *color, int *ncolors);
+gabp_status gabp_set_schedule(gabp_ctx *ctx, int schedule, const int32_t *color, int *ncolors);
+
+/*
+ * Line schedule: copies the node messages out (device arrays of n doubles,
+ * natural node order): LH/MH = (Lambda, m) from each node's row region,
+ * LV/MV from its column region.  Any pointer may be NULL.
+ */
+gabp_status gabp_get_line_state(gabp_ctx *ctx, double *LH, double *MH, double *LV, double *MV);
 
 /* Sets every message to zero (the initial state of Algorithm 1). */
 gabp_status gabp_reset(gabp_ctx *ctx);

@@ -79,6 +79,7 @@ def load() -> ctypes.CDLL:
         "gabp_destroy": (None, [P]),
         "gabp_reset": (I, [P]),
         "gabp_set_schedule": (I, [P, I, P, PI]),
+        "gabp_get_line_state": (I, [P, P, P, P, P]),
         "gabp_sweep": (I, [P, P, I, P]),
         "gabp_solve": (I, [P, P, P, D, I, PI, PD]),
         "gabp_solve_transpose": (I, [P, P, P, D, I, PI, PD]),
@@ -206,15 +207,24 @@ class GabpSolver:
         _check(load().gabp_reset(self._h))
 
     def set_schedule(self, schedule: str = "flood", colors=None) -> int:
-        """``"flood"`` (Sec. 2.2) or ``"colored"`` (red-black / 4-colour, Sec. 5.1);
-        ``colors`` (n ints) or greedy colouring.  Returns the number of colours."""
+        """``"flood"`` (Sec. 2.2), ``"colored"`` (red-black / 4-colour, Sec. 5.1;
+        ``colors`` n ints or greedy colouring) or ``"lines"`` (line GaBP,
+        Algorithm 2 on the rows and columns of a square grid).  Returns the
+        number of colours (0 unless coloured)."""
         nc = ctypes.c_int()
         cp = None
         if colors is not None:
             self._colors = np.ascontiguousarray(colors, dtype=np.int32)
             cp = self._colors.ctypes.data
-        _check(load().gabp_set_schedule(self._h, 0 if schedule == "flood" else 1, cp, ctypes.byref(nc)))
+        code = {"flood": 0, "colored": 1, "lines": 2}[schedule]
+        _check(load().gabp_set_schedule(self._h, code, cp, ctypes.byref(nc)))
         return int(nc.value)
+
+    def get_line_state(self):
+        torch = _torch()
+        out = [torch.empty(self.n, dtype=torch.float64, device=f"cuda:{self.device}") for _ in range(4)]
+        _check(load().gabp_get_line_state(self._h, *[_dev_vec(t, self.n, "state") for t in out]))
+        return {"LH": out[0], "MH": out[1], "LV": out[2], "MV": out[3]}
 
     def set_values(self, data) -> None:
         data = np.ascontiguousarray(data, dtype=np.float64)

@@ -100,6 +100,14 @@ struct gabp_ctx {
     int ncolors = 0;
     bool has_masks = false;          // stencil layout: per-colour slot masks valid
     ColorMasks masks{};
+    // line schedule (lazy): grid side, couplings along columns (natural order)
+    // and along rows (transposed order), node messages of both families
+    int lines_m = 0;
+    void *lsubN = nullptr, *lsupN = nullptr, *lsubT = nullptr, *lsupT = nullptr;
+    void *ldiagT = nullptr, *lbT = nullptr;
+    void *LH = nullptr, *MH = nullptr, *LV = nullptr, *MV = nullptr;
+    void *LHt = nullptr, *MHt = nullptr, *LVt = nullptr, *MVt = nullptr;
+    void *lf = nullptr, *ly = nullptr;
     bool frozen = false;         // precision messages frozen (both L and P buffers equal)
     bool frozen_transposed = false;
     DevStatus *dstat = nullptr;  // [0] chunk checks, [1] refinement / misc, [2] Lambda change
@@ -387,6 +395,13 @@ gabp_status zero_messages(gabp_ctx *ctx, bool lam, bool mean)
 {
     const size_t bytes = (size_t)ctx->L.slots * esz(ctx->prec);
     if (lam) ctx->frozen = false;
+    if (ctx->lines_m > 0) {
+        const size_t nb = (size_t)ctx->n * esz(ctx->prec);
+        if (lam) CK(cudaMemsetAsync(ctx->LH, 0, nb, ctx->stream));
+        if (lam) CK(cudaMemsetAsync(ctx->LV, 0, nb, ctx->stream));
+        if (mean) CK(cudaMemsetAsync(ctx->MH, 0, nb, ctx->stream));
+        if (mean) CK(cudaMemsetAsync(ctx->MV, 0, nb, ctx->stream));
+    }
     if (lam) CK(cudaMemsetAsync(ctx->Lm[ctx->cur], 0, bytes, ctx->stream));
     if (mean) CK(cudaMemsetAsync(ctx->Mm[ctx->cur], 0, bytes, ctx->stream));
     return GABP_OK;
@@ -398,6 +413,7 @@ gabp_status load_rhs(gabp_ctx *ctx, const double *b)
     const int64_t n = ctx->n;
     if (b != ctx->bres) CK(cudaMemcpyAsync(ctx->bres, b, n * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
     if (ctx->prec == 1) CK(launch_convert_d2f(ctx->bres, (float *)ctx->bT, n, ctx->stream));
+    if (ctx->lines_m > 0) CK(launch_transpose(ctx->prec, ctx->lines_m, ctx->bT, ctx->lbT, ctx->stream));
     return GABP_OK;
 }
 
@@ -415,6 +431,21 @@ int block_of(const gabp_ctx *ctx) { return ctx->opt.block_size > 0 ? ctx->opt.bl
 cudaError_t sweep_once(gabp_ctx *ctx, bool transposed, double *x, cudaStream_t s)
 {
     const int c0 = ctx->cur, c1 = c0 ^ 1;
+    if (ctx->lines_m > 0) {
+        // Algorithm 2 over rows (transposed order), then columns (natural order)
+        const int m = ctx->lines_m, pr = ctx->prec;
+        unsigned *fl = &ctx->dstat[0].flags;
+        cudaError_t e;
+        if ((e = launch_transpose(pr, m, ctx->LV, ctx->LVt, s)) != cudaSuccess) return e;
+        if ((e = launch_transpose(pr, m, ctx->MV, ctx->MVt, s)) != cudaSuccess) return e;
+        if ((e = launch_line_phase(pr, m, ctx->lsubT, ctx->lsupT, ctx->ldiagT, ctx->lbT, ctx->LVt,
+                                   ctx->MVt, ctx->LHt, ctx->MHt, ctx->lf, ctx->ly, nullptr, fl, s)) != cudaSuccess)
+            return e;
+        if ((e = launch_transpose(pr, m, ctx->LHt, ctx->LH, s)) != cudaSuccess) return e;
+        if ((e = launch_transpose(pr, m, ctx->MHt, ctx->MH, s)) != cudaSuccess) return e;
+        return launch_line_phase(pr, m, ctx->lsubN, ctx->lsupN, ctx->diagT, ctx->bT, ctx->LH,
+                                 ctx->MH, ctx->LV, ctx->MV, ctx->lf, ctx->ly, x, fl, s);
+    }
     if (ctx->ncolors > 0) {
         for (int c = 0; c < ctx->ncolors; ++c) {
             cudaError_t e = launch_sweep_color(ctx->L, ctx->prec, ctx->color, c,
@@ -490,9 +521,10 @@ gabp_status run_chunk(gabp_ctx *ctx, int k, bool transposed)
             ctx->graphs.push_back({k, parity, (int)transposed, frozen, exec});
         }
         CK(cudaGraphLaunch(exec, ctx->stream));
-        const int per_sweep = ctx->ncolors > 0 ? ctx->ncolors : 1;
+        const int per_sweep = ctx->lines_m > 0 ? 6 : (ctx->ncolors > 0 ? ctx->ncolors : 1);
         count_launches(ctx->stream, (unsigned long long)k * per_sweep + 1);  // sweeps + residual
-        ctx->cur = ctx->ncolors > 0 ? parity : parity ^ (k & 1);  // coloured sweeps work in place
+        const bool in_place = ctx->ncolors > 0 || ctx->lines_m > 0;
+        ctx->cur = in_place ? parity : parity ^ (k & 1);
     }
     CK(cudaStreamSynchronize(ctx->stream));
     return GABP_OK;
@@ -568,7 +600,7 @@ gabp_status maybe_freeze(gabp_ctx *ctx, bool transposed)
 
 bool freeze_enabled(const gabp_ctx *ctx)
 {
-    if (ctx->ncolors > 0) return false;  // frozen sweeps use the flood schedule
+    if (ctx->ncolors > 0 || ctx->lines_m > 0) return false;  // frozen sweeps use the flood schedule
     if (ctx->opt.freeze_lambda < 0) return ctx->opt.precision == GABP_FP32_IR;
     return ctx->opt.freeze_lambda > 0;
 }
@@ -641,6 +673,7 @@ gabp_status solve_ir(gabp_ctx *ctx, const double *b, double *x, double tol, int 
     for (int outer = 0; st == GABP_E_NOT_CONVERGED && outer < 200 && total < max_iter; ++outer) {
         // inner problem A e = r / ||r||: double copy for the checks, float copy for the sweeps
         CK(launch_scale_rhs(ctx->rbuf, &ctx->dstat[1], ctx->bres, ctx->bT, ctx->prec, n, s));
+        if (ctx->lines_m > 0) CK(launch_transpose(ctx->prec, ctx->lines_m, ctx->bT, ctx->lbT, s));
         CKS(zero_messages(ctx, false, true));  // tilde-Lambda kept warm
         CKS(aggregate(ctx));
         int inner = 0;
@@ -852,18 +885,78 @@ void gabp_destroy(gabp_ctx *ctx)
     delete ctx;
 }
 
-gabp_status gabp_set_schedule(gabp_ctx *ctx, int coloured, const int32_t *color, int *ncolors)
+static gabp_status setup_lines(gabp_ctx *ctx)
 {
-    if (!ctx || coloured < 0 || coloured > 1) return fail(GABP_E_INVALID_ARG, "bad argument");
+    const int n = ctx->n;
+    int m = 0;
+    while ((int64_t)m * m < n) ++m;
+    if ((int64_t)m * m != n || n == 0) return fail(GABP_E_INVALID_ARG, "line schedule needs an m x m grid");
+    const int64_t *ip = ctx->h_indptr.data();
+    const int32_t *ix = ctx->h_indices.data();
+    const double *dv = ctx->h_data.data();
+    std::vector<double> subN(n, 0.0), supN(n, 0.0), subT(n, 0.0), supT(n, 0.0), dT(n, 0.0);
+    std::vector<double> dg(n, 0.0);
+    for (int r = 0; r < n; ++r) {
+        const int rx = r % m, ry = r / m;
+        for (int64_t p = ip[r]; p < ip[r + 1]; ++p) {
+            const int j = ix[p];
+            const int jx = j % m, jy = j / m;
+            if (j == r) dg[r] = dv[p];
+            else if (jy == ry && jx == rx - 1) subT[(size_t)rx * m + ry] = dv[p];   // west, along the row
+            else if (jy == ry && jx == rx + 1) supT[(size_t)rx * m + ry] = dv[p];   // east
+            else if (jx == rx && jy == ry - 1) subN[r] = dv[p];                      // south, along the column
+            else if (jx == rx && jy == ry + 1) supN[r] = dv[p];                      // north
+            else return fail(GABP_E_INVALID_ARG, "line schedule needs a 5-point grid matrix (every edge inside a row or a column)");
+        }
+    }
+    for (int r = 0; r < n; ++r) dT[(size_t)(r % m) * m + r / m] = dg[r];
+    const size_t nb = (size_t)n * esz(ctx->prec);
+    auto put = [&](void **dst, const std::vector<double> &v) -> gabp_status {
+        if (!*dst) CKS(dalloc(ctx, dst, nb));
+        if (ctx->prec == 0) {
+            CK(cudaMemcpy(*dst, v.data(), nb, cudaMemcpyHostToDevice));
+        } else {
+            auto f = cast_vec<float>(v);
+            CK(cudaMemcpy(*dst, f.data(), nb, cudaMemcpyHostToDevice));
+        }
+        return GABP_OK;
+    };
+    CKS(put(&ctx->lsubN, subN));
+    CKS(put(&ctx->lsupN, supN));
+    CKS(put(&ctx->lsubT, subT));
+    CKS(put(&ctx->lsupT, supT));
+    CKS(put(&ctx->ldiagT, dT));
+    void **bufs[] = {&ctx->lbT, &ctx->LH, &ctx->MH, &ctx->LV, &ctx->MV, &ctx->LHt, &ctx->MHt,
+                     &ctx->LVt, &ctx->MVt, &ctx->lf, &ctx->ly};
+    for (void **bp : bufs) {
+        if (!*bp) CKS(dalloc(ctx, bp, nb));
+        CK(cudaMemset(*bp, 0, nb));
+    }
+    ctx->lines_m = m;
+    return GABP_OK;
+}
+
+gabp_status gabp_set_schedule(gabp_ctx *ctx, int schedule, const int32_t *color, int *ncolors)
+{
+    if (!ctx || schedule < 0 || schedule > 2) return fail(GABP_E_INVALID_ARG, "bad argument");
     CKS(set_dev(ctx->dev));
     CK(cudaStreamSynchronize(ctx->stream));
     for (auto &g : ctx->graphs) cudaGraphExecDestroy(g.exec);
     ctx->graphs.clear();
-    if (!coloured) {
+    ctx->frozen = false;
+    if (schedule != 1) {
         ctx->ncolors = 0;
         if (ncolors) *ncolors = 0;
+    }
+    if (schedule == 0) {
+        ctx->lines_m = 0;
         return GABP_OK;
     }
+    if (schedule == 2) {
+        ctx->lines_m = 0;
+        return setup_lines(ctx);
+    }
+    ctx->lines_m = 0;
     const int n = ctx->n;
     const int64_t *ip = ctx->h_indptr.data();
     const int32_t *ix = ctx->h_indices.data();
@@ -1002,6 +1095,7 @@ gabp_status gabp_solve_transpose(gabp_ctx *ctx, const double *g, double *lam, do
     if (!ctx || max_iter < 0 || !(tol >= 0.0) || ((!g || !lam) && ctx->n > 0))
         return fail(GABP_E_INVALID_ARG, "bad argument");
     CKS(set_dev(ctx->dev));
+    if (ctx->lines_m > 0) return fail(GABP_E_INVALID_ARG, "the transposed solve floods or colours; select one of those schedules");
     CKS(ensure_transpose(ctx));
     if (ctx->opt.precision == GABP_FP32_IR) return solve_ir(ctx, g, lam, tol, max_iter, iters, relres, true);
     return solve_plain(ctx, g, lam, tol, max_iter, iters, relres, true);
@@ -1045,6 +1139,20 @@ gabp_status gabp_set_state(gabp_ctx *ctx, const double *lam, const double *m)
     CKS(set_dev(ctx->dev));
     CKS(zero_messages(ctx, lam != nullptr, m != nullptr));
     CK(launch_set_state(ctx->slotmap, ctx->nnz, ctx->prec, lam, m, ctx->Lm[ctx->cur], ctx->Mm[ctx->cur], ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return GABP_OK;
+}
+
+gabp_status gabp_get_line_state(gabp_ctx *ctx, double *LH, double *MH, double *LV, double *MV)
+{
+    if (!ctx) return fail(GABP_E_INVALID_ARG, "null context");
+    if (ctx->lines_m == 0) return fail(GABP_E_INVALID_ARG, "the line schedule is not selected");
+    CKS(set_dev(ctx->dev));
+    const int64_t n = ctx->n;
+    if (LH) CK(launch_to_double(ctx->prec, ctx->LH, LH, n, ctx->stream));
+    if (MH) CK(launch_to_double(ctx->prec, ctx->MH, MH, n, ctx->stream));
+    if (LV) CK(launch_to_double(ctx->prec, ctx->LV, LV, n, ctx->stream));
+    if (MV) CK(launch_to_double(ctx->prec, ctx->MV, MV, n, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     return GABP_OK;
 }

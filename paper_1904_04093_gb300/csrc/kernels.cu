@@ -531,6 +531,13 @@ __global__ void k_d2f(const double *__restrict__ in, float *__restrict__ out, in
         out[i] = (float)in[i];
 }
 
+__global__ void k_f2d(const float *__restrict__ in, double *__restrict__ out, int64_t n)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = (double)in[i];
+}
+
 __global__ void k_copy(const double *__restrict__ in, double *__restrict__ out, int64_t n)
 {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -817,6 +824,18 @@ cudaError_t launch_convert_d2f(const double *in, float *out, int64_t n, cudaStre
 {
     if (n == 0) return cudaSuccess;
     k_d2f<<<grid_for(n, 256), 256, 0, s>>>(in, out, n);
+    count_launches(s, 1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_to_double(int prec, const void *in, double *out, int64_t n, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    if (prec == 0) {
+        k_copy<<<grid_for(n, 256), 256, 0, s>>>((const double *)in, out, n);
+    } else {
+        k_f2d<<<grid_for(n, 256), 256, 0, s>>>((const float *)in, out, n);
+    }
     count_launches(s, 1);
     return cudaGetLastError();
 }
