@@ -57,7 +57,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU sample")
     ap.add_argument("--only", choices=["all", "fp64", "mixed"], default="all",
                     help="profiling runs: time only one solver (no e2e, no CPU sample)")
-    ap.add_argument("--workload", choices=["convdiff", "batch", "mg", "adjoint"], default="convdiff",
+    ap.add_argument("--workload", choices=["convdiff", "batch", "mg", "adjoint", "lines"], default="convdiff",
                     help="convdiff (default, the headline line); batch / mg / adjoint print "
                          "secondary lines for the other hot-path workloads")
     ap.add_argument("--nsys", type=int, default=512, help="batch: number of systems")
@@ -530,6 +530,37 @@ def run_mg(args):
     return 0
 
 
+def run_lines(args):
+    """Line GaBP (Algorithm 2, grid rows and columns as large regions) on the
+    convection-diffusion workload: FP64 and mixed precision to rr <= 1e-10."""
+    import torch
+    import paper_1904_04093_gb300 as g
+    import problems as P
+    g.load()
+    A, b = P.config_c2(m=args.m)
+    bd = torch.as_tensor(b, device="cuda")
+    x = torch.empty_like(bd)
+    out = {}
+    for prec in ("fp64", "fp32_ir"):
+        s = g.GabpSolver(A, prec, check_every=10)
+        s.set_schedule("lines")
+        for _ in range(max(1, args.warmup)):
+            s.solve(bd, TOL, MAX_ITER, x)
+        ms, res = _timed_region(lambda: s.solve(bd, TOL, MAX_ITER, x), args.steps)
+        sw = s.time_sweeps(bd, 10) / 10
+        out[prec] = {"ms": ms, "sweeps": res[1], "rr": res[2], "converged": res[3] == g.OK,
+                     "sweep_ms": sw}
+        s.close()
+    line = {"metric": "line GaBP time to rr <= 1e-10", "value": out["fp64"]["ms"], "unit": "ms",
+            "higher_is_better": False, "steps": args.steps, "dtype": "f64 (and f32 + f64 refinement)",
+            "data": "synthetic",
+            "config": {"workload": f"convdiff2d_5pt_upwind_lognormal_{args.m}x{args.m}",
+                       "schedule": "lines (rows then columns, one thread per line)"},
+            "solves": out}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_adjoint(args):
     """Differentiable solve at 512^2: forward (mixed) + adjoint (mixed) + edge gradient."""
     import math as _m
@@ -580,6 +611,8 @@ def main():
         return run_mg(args)
     if args.workload == "adjoint":
         return run_adjoint(args)
+    if args.workload == "lines":
+        return run_lines(args)
     return run_ours(args)
 
 

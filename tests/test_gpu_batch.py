@@ -128,3 +128,35 @@ def test_batch_frozen_precision_messages_match_single(g):
         x1, it1, rr1, st1 = single.solve(dev(b), 1e-10, 5000)
         assert st1 == g.OK and abs(it - it1) <= 5
         assert rel(host(x), host(x1)) <= 1e-9
+
+
+def _divergent_5pt():
+    """A 6 x 6 5-point matrix (unit diagonal, couplings U(-0.8, 0.8), seed 2) on
+    which flood GaBP diverges (found with the oracle)."""
+    m = 6
+    rng = np.random.default_rng(2)
+    c = np.empty((m, m, 5))
+    c[:, :, 2] = 1.0
+    for k in (0, 1, 3, 4):
+        c[:, :, k] = rng.uniform(-0.8, 0.8, (m, m))
+    A = P.stencil_csr(m, P._OFF5, c)
+    b = rng.uniform(-1, 1, m * m)
+    return A, b
+
+
+def test_batch_faults_stay_per_system(g):
+    """A breakdown and a divergence in a batch are reported for their own systems;
+    the other systems still converge."""
+    Ad, bd_ = _divergent_5pt()
+    assert oracle.solve(Ad, bd_, 1e-12, 3000)["status"] == oracle.DIVERGED
+    Ab = P.dense_to_csr(np.array([[1.0, 1.0, 1.0], [1.0, 1.0, 0.0], [1.0, 0.0, 1.0]]))
+    bb = np.array([1.0, 2.0, 3.0])
+    assert oracle.solve(Ab, bb, 1e-12, 50)["status"] == oracle.BREAKDOWN
+    Ag, bg = P.config_c1(m=20)
+    systems = [(Ag, bg), (Ad, bd_), (Ab, bb), (Ag, bg)]
+    solvers = [g.GabpSolver(A, "fp64", layout="stencil") for A, _ in systems]
+    batch = g.Batch(solvers, check_every=5)
+    xs, its, rrs, sts = batch.solve([dev(b) for _, b in systems], 1e-10, 3000)
+    assert sts == [g.OK, g.DIVERGED, g.BREAKDOWN, g.OK]
+    xs_ = np.linalg.solve(Ag.to_dense(), bg)
+    assert rel(host(xs[0]), xs_) <= 1e-8 and rel(host(xs[3]), xs_) <= 1e-8
