@@ -141,6 +141,12 @@ void gabp_destroy(gabp_ctx *ctx);
  *    Needs n = m^2 and every edge inside a row or a column (5-point grids),
  *    GABP_E_INVALID_ARG otherwise.  The transposed solve is not available
  *    under this schedule; gabp_get_line_state reads its messages.
+ *    On an m x m grid stencil (m >= 3, couplings inside the 3 x 3
+ *    neighbourhood) whose colours are unions of the parity classes
+ *    (x mod 2, y mod 2) -- red-black and the 4-colour grid colouring -- the
+ *    messages are kept by sender, class by class, so a sweep streams every
+ *    message once; gabp_info.parity_layout reports it.  Other colourings run
+ *    on the slot layout.
  * Precision messages are not frozen under schedules 1 and 2; the batched
  * solver always floods.
  */
@@ -237,6 +243,8 @@ typedef struct {
     double mean_sweep_bytes; /* the same for a sweep with frozen precision messages */
     double residual_bytes;  /* compulsory DRAM bytes of one residual kernel launch */
     size_t device_bytes;    /* device memory held by the context */
+    int parity_layout;      /* 1: the coloured schedule runs on the parity-class layout */
+    double colored_sweep_bytes; /* compulsory DRAM bytes of one sweep on that layout */
 } gabp_info;
 
 gabp_status gabp_get_info(gabp_ctx *ctx, gabp_info *info);

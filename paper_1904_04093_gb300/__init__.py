@@ -47,7 +47,8 @@ class Info(ctypes.Structure):
                 ("layout", ctypes.c_int), ("ndiag", ctypes.c_int), ("precision", ctypes.c_int),
                 ("slots", ctypes.c_int64), ("sweep_bytes", ctypes.c_double),
                 ("mean_sweep_bytes", ctypes.c_double),
-                ("residual_bytes", ctypes.c_double), ("device_bytes", ctypes.c_size_t)]
+                ("residual_bytes", ctypes.c_double), ("device_bytes", ctypes.c_size_t),
+                ("parity_layout", ctypes.c_int), ("colored_sweep_bytes", ctypes.c_double)]
 
 
 _lib = None

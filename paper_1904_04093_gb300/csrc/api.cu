@@ -100,6 +100,12 @@ struct gabp_ctx {
     int ncolors = 0;
     bool has_masks = false;          // stencil layout: per-colour slot masks valid
     ColorMasks masks{};
+    // coloured schedule on the parity-class layout (grids whose colours are
+    // unions of parity classes): messages Lm/Mm held by sender, class by class
+    bool parity = false;
+    ParityGrid pg{};
+    std::vector<PhaseClasses> phases;
+    void *pa = nullptr, *pc = nullptr, *paT = nullptr;  // a, c, a^T in class layout
     // line schedule (lazy): grid side, couplings along columns (natural order)
     // and along rows (transposed order), node messages of both families
     int lines_m = 0;
@@ -419,6 +425,7 @@ gabp_status load_rhs(gabp_ctx *ctx, const double *b)
 
 gabp_status aggregate(gabp_ctx *ctx)
 {
+    if (ctx->parity) return GABP_OK;  // the parity-class sweep keeps no aggregates
     CK(launch_aggregate(ctx->L, ctx->prec, ctx->diagT, ctx->bT, ctx->Lm[ctx->cur],
                         ctx->Mm[ctx->cur], ctx->P[ctx->cur], ctx->B[ctx->cur], ctx->stream));
     return GABP_OK;
@@ -445,6 +452,16 @@ cudaError_t sweep_once(gabp_ctx *ctx, bool transposed, double *x, cudaStream_t s
         if ((e = launch_transpose(pr, m, ctx->MHt, ctx->MH, s)) != cudaSuccess) return e;
         return launch_line_phase(pr, m, ctx->lsubN, ctx->lsupN, ctx->diagT, ctx->bT, ctx->LH,
                                  ctx->MH, ctx->LV, ctx->MV, ctx->lf, ctx->ly, x, fl, s);
+    }
+    if (ctx->parity) {
+        for (const PhaseClasses &ph : ctx->phases) {
+            if (ph.nq == 0) continue;
+            cudaError_t e = launch_sweep_parity(ctx->pg, ph, ctx->prec, transposed ? ctx->paT : ctx->pa,
+                                                ctx->pc, ctx->diagT, ctx->bT, ctx->Lm[c0],
+                                                ctx->Mm[c0], x, &ctx->dstat[0].flags, s);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
     }
     if (ctx->ncolors > 0) {
         for (int c = 0; c < ctx->ncolors; ++c) {
@@ -521,7 +538,11 @@ gabp_status run_chunk(gabp_ctx *ctx, int k, bool transposed)
             ctx->graphs.push_back({k, parity, (int)transposed, frozen, exec});
         }
         CK(cudaGraphLaunch(exec, ctx->stream));
-        const int per_sweep = ctx->lines_m > 0 ? 6 : (ctx->ncolors > 0 ? ctx->ncolors : 1);
+        int per_sweep = ctx->lines_m > 0 ? 6 : (ctx->ncolors > 0 ? ctx->ncolors : 1);
+        if (ctx->parity) {
+            per_sweep = 0;
+            for (const PhaseClasses &ph : ctx->phases) per_sweep += ph.nq > 0 ? 1 : 0;
+        }
         count_launches(ctx->stream, (unsigned long long)k * per_sweep + 1);  // sweeps + residual
         const bool in_place = ctx->ncolors > 0 || ctx->lines_m > 0;
         ctx->cur = in_place ? parity : parity ^ (k & 1);
@@ -541,9 +562,20 @@ gabp_status read_status(gabp_ctx *ctx, int which, double *rinf, double *binf, un
     return GABP_OK;
 }
 
+gabp_status ensure_parity_transpose(gabp_ctx *ctx)
+{
+    if (!ctx->parity || !ctx->aT) return GABP_OK;
+    if (!ctx->paT) CKS(dalloc(ctx, &ctx->paT, (size_t)ctx->L.slots * esz(ctx->prec)));
+    CK(launch_parity_convert(ctx->pg, ctx->prec, 1, ctx->aT, ctx->paT, ctx->stream));
+    return GABP_OK;
+}
+
 gabp_status ensure_transpose(gabp_ctx *ctx)
 {
-    if (ctx->aT) return GABP_OK;
+    if (ctx->aT) {
+        if (ctx->parity && !ctx->paT) CKS(ensure_parity_transpose(ctx));
+        return GABP_OK;
+    }
     const size_t S = (size_t)ctx->L.slots;
     CKS(dalloc(ctx, (void **)&ctx->aT64, S * sizeof(double)));
     CK(launch_transpose_coeffs(ctx->L, 0, ctx->a64, ctx->aT64, ctx->stream));
@@ -553,7 +585,7 @@ gabp_status ensure_transpose(gabp_ctx *ctx)
         CKS(dalloc(ctx, &ctx->aT, S * sizeof(float)));
         CK(launch_transpose_coeffs(ctx->L, 1, ctx->a, ctx->aT, ctx->stream));
     }
-    return GABP_OK;
+    return ensure_parity_transpose(ctx);
 }
 
 gabp_status ensure_ir(gabp_ctx *ctx)
@@ -866,6 +898,11 @@ gabp_status gabp_set_values(gabp_ctx *ctx, const double *data)
         CK(launch_transpose_coeffs(ctx->L, 0, ctx->a64, ctx->aT64, ctx->stream));
         if (ctx->prec == 1) CK(launch_transpose_coeffs(ctx->L, 1, ctx->a, ctx->aT, ctx->stream));
     }
+    if (ctx->parity) {
+        CK(launch_parity_convert(ctx->pg, ctx->prec, 1, ctx->a, ctx->pa, ctx->stream));
+        CK(launch_parity_convert(ctx->pg, ctx->prec, 1, ctx->c, ctx->pc, ctx->stream));
+        if (ctx->paT) CKS(ensure_parity_transpose(ctx));
+    }
     CKS(zero_messages(ctx, true, true));
     CK(cudaStreamSynchronize(ctx->stream));
     return GABP_OK;
@@ -936,6 +973,79 @@ static gabp_status setup_lines(gabp_ctx *ctx)
     return GABP_OK;
 }
 
+// Coloured schedule on the parity-class layout when A is an m x m grid
+// stencil (m >= 3, every coupling inside the 3 x 3 neighbourhood, none
+// wrapping around a grid row) and every colour is a union of parity classes.
+// Leaves ctx->parity false when A or the colouring does not fit.
+static gabp_status setup_parity(gabp_ctx *ctx, const std::vector<int> &col, int nc)
+{
+    ctx->parity = false;
+    const int n = ctx->n;
+    const StencilParams &sp = ctx->L.sp;
+    if (ctx->L.kind != GABP_LAYOUT_STENCIL || sp.K == 0 || sp.K > KMAXPG) return GABP_OK;
+    int m = 0;
+    while ((int64_t)m * m < n) ++m;
+    if ((int64_t)m * m != n || m < 3) return GABP_OK;
+    ParityGrid g{};
+    g.m = m;
+    g.K = sp.K;
+    for (int k = 0; k < sp.K; ++k) {
+        bool found = false;
+        for (int dy = -1; dy <= 1 && !found; ++dy)
+            for (int dx = -1; dx <= 1 && !found; ++dx)
+                if ((dx || dy) && dy * m + dx == sp.off[k]) {
+                    g.dx[k] = dx;
+                    g.dy[k] = dy;
+                    found = true;
+                }
+        if (!found) return GABP_OK;
+        g.krev[k] = sp.krev[k];
+    }
+    const int64_t *ip = ctx->h_indptr.data();
+    const int32_t *ix = ctx->h_indices.data();
+    for (int r = 0; r < n; ++r)
+        for (int64_t p = ip[r]; p < ip[r + 1]; ++p) {
+            const int j = ix[p];
+            if (j == r) continue;
+            const int ddx = j % m - r % m, ddy = j / m - r / m;
+            if (ddx < -1 || ddx > 1 || ddy < -1 || ddy > 1) return GABP_OK;
+        }
+    int qc[4] = {-1, -1, -1, -1};
+    for (int i = 0; i < n; ++i) {
+        const int q = ((i % m) & 1) | (((i / m) & 1) << 1);
+        if (qc[q] < 0) qc[q] = col[i];
+        else if (qc[q] != col[i]) return GABP_OK;
+    }
+    long long size[4], acc = 0;
+    for (int q = 0; q < 4; ++q) {
+        g.w[q] = (m - (q & 1) + 1) / 2;
+        size[q] = (long long)g.w[q] * ((m - (q >> 1) + 1) / 2);
+        g.base[q] = acc;
+        acc += size[q];
+    }
+    std::vector<PhaseClasses> phases((size_t)nc);
+    for (int c = 0; c < nc; ++c) {
+        PhaseClasses &ph = phases[(size_t)c];
+        ph = PhaseClasses{};
+        for (int q = 0; q < 4; ++q)
+            if (qc[q] == c) {
+                ph.q[ph.nq] = q;
+                ph.start[ph.nq + 1] = ph.start[ph.nq] + size[q];
+                ++ph.nq;
+            }
+    }
+    const size_t S = (size_t)ctx->L.slots * esz(ctx->prec);
+    if (!ctx->pa) CKS(dalloc(ctx, &ctx->pa, S));
+    if (!ctx->pc) CKS(dalloc(ctx, &ctx->pc, S));
+    CK(launch_parity_convert(g, ctx->prec, 1, ctx->a, ctx->pa, ctx->stream));
+    CK(launch_parity_convert(g, ctx->prec, 1, ctx->c, ctx->pc, ctx->stream));
+    ctx->pg = g;
+    ctx->phases.swap(phases);
+    ctx->parity = true;
+    if (ctx->aT) CKS(ensure_parity_transpose(ctx));
+    return GABP_OK;
+}
+
 gabp_status gabp_set_schedule(gabp_ctx *ctx, int schedule, const int32_t *color, int *ncolors)
 {
     if (!ctx || schedule < 0 || schedule > 2) return fail(GABP_E_INVALID_ARG, "bad argument");
@@ -944,12 +1054,16 @@ gabp_status gabp_set_schedule(gabp_ctx *ctx, int schedule, const int32_t *color,
     for (auto &g : ctx->graphs) cudaGraphExecDestroy(g.exec);
     ctx->graphs.clear();
     ctx->frozen = false;
+    ctx->parity = false;
+    CKS(zero_messages(ctx, true, true));
+    CKS(aggregate(ctx));
     if (schedule != 1) {
         ctx->ncolors = 0;
         if (ncolors) *ncolors = 0;
     }
     if (schedule == 0) {
         ctx->lines_m = 0;
+        CK(cudaStreamSynchronize(ctx->stream));
         return GABP_OK;
     }
     if (schedule == 2) {
@@ -1026,6 +1140,8 @@ gabp_status gabp_set_schedule(gabp_ctx *ctx, int schedule, const int32_t *color,
     if (n) CK(cudaMemcpy(ctx->color, c8.data(), (size_t)n, cudaMemcpyHostToDevice));
     ctx->ncolors = nc;
     ctx->frozen = false;
+    CKS(setup_parity(ctx, col, nc));
+    CK(cudaStreamSynchronize(ctx->stream));
     if (ncolors) *ncolors = nc;
     return GABP_OK;
 }
@@ -1128,7 +1244,15 @@ gabp_status gabp_get_state(gabp_ctx *ctx, double *lam, double *m)
 {
     if (!ctx) return fail(GABP_E_INVALID_ARG, "null context");
     CKS(set_dev(ctx->dev));
-    CK(launch_get_state(ctx->slotmap, ctx->nnz, ctx->prec, ctx->Lm[ctx->cur], ctx->Mm[ctx->cur], lam, m, ctx->stream));
+    const void *Ls = ctx->Lm[ctx->cur], *Ms = ctx->Mm[ctx->cur];
+    if (ctx->parity) {  // class layout -> slot layout in the idle buffers
+        const int o = ctx->cur ^ 1;
+        CK(launch_parity_convert(ctx->pg, ctx->prec, 0, ctx->Lm[ctx->cur], ctx->Lm[o], ctx->stream));
+        CK(launch_parity_convert(ctx->pg, ctx->prec, 0, ctx->Mm[ctx->cur], ctx->Mm[o], ctx->stream));
+        Ls = ctx->Lm[o];
+        Ms = ctx->Mm[o];
+    }
+    CK(launch_get_state(ctx->slotmap, ctx->nnz, ctx->prec, Ls, Ms, lam, m, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     return GABP_OK;
 }
@@ -1138,6 +1262,16 @@ gabp_status gabp_set_state(gabp_ctx *ctx, const double *lam, const double *m)
     if (!ctx) return fail(GABP_E_INVALID_ARG, "null context");
     CKS(set_dev(ctx->dev));
     CKS(zero_messages(ctx, lam != nullptr, m != nullptr));
+    if (ctx->parity) {  // through the slot layout in the idle buffers
+        const int o = ctx->cur ^ 1;
+        CK(launch_parity_convert(ctx->pg, ctx->prec, 0, ctx->Lm[ctx->cur], ctx->Lm[o], ctx->stream));
+        CK(launch_parity_convert(ctx->pg, ctx->prec, 0, ctx->Mm[ctx->cur], ctx->Mm[o], ctx->stream));
+        CK(launch_set_state(ctx->slotmap, ctx->nnz, ctx->prec, lam, m, ctx->Lm[o], ctx->Mm[o], ctx->stream));
+        CK(launch_parity_convert(ctx->pg, ctx->prec, 1, ctx->Lm[o], ctx->Lm[ctx->cur], ctx->stream));
+        CK(launch_parity_convert(ctx->pg, ctx->prec, 1, ctx->Mm[o], ctx->Mm[ctx->cur], ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        return GABP_OK;
+    }
     CK(launch_set_state(ctx->slotmap, ctx->nnz, ctx->prec, lam, m, ctx->Lm[ctx->cur], ctx->Mm[ctx->cur], ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     return GABP_OK;
@@ -1184,6 +1318,10 @@ gabp_status gabp_get_info(gabp_ctx *ctx, gabp_info *info)
     info->mean_sweep_bytes = mean;
     info->residual_bytes = resid;
     info->device_bytes = ctx->dev_bytes;
+    info->parity_layout = ctx->parity ? 1 : 0;
+    // parity-class coloured sweep: per slot a, c, incoming L, M read and L', M'
+    // written; per node diag and b read (no aggregates)
+    info->colored_sweep_bytes = 6.0 * p * S + 2.0 * p * n;
     return GABP_OK;
 }
 

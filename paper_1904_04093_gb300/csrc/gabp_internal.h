@@ -28,6 +28,27 @@ struct ColorMasks {
     unsigned short m[KMAXCOLOR][KMAXCOLOR];
 };
 
+// Coloured schedule on an m x m grid (node i = x + m y) whose colours are
+// constant on the four parity classes q = (x mod 2) + 2 (y mod 2).  Messages
+// are stored by their sender: slot k * n + pos(s) holds the message s -> s +
+// off[k] (as its effect on the recipient, like the slot layout), where pos(s)
+// = base[q] + (y / 2) w[q] + x / 2 numbers the class of s row by row.  One
+// phase reads only other classes' slots and writes only its own, contiguously.
+constexpr int KMAXPG = 8;
+struct ParityGrid {
+    int m, K;
+    int dx[KMAXPG], dy[KMAXPG], krev[KMAXPG];
+    int w[4];
+    long long base[4];
+};
+// The parity classes one colour covers: q[j] for j < nq, its threads
+// start[j] <= t < start[j + 1].
+struct PhaseClasses {
+    int nq;
+    int q[4];
+    long long start[5];
+};
+
 // Device status word: residual and rhs maxima (bit patterns of non-negative
 // doubles, ordered like unsigned integers) and error flags.
 struct DevStatus {
@@ -85,6 +106,15 @@ cudaError_t launch_axpy_status(double *x, const double *e, const DevStatus *st, 
                                cudaStream_t s);
 cudaError_t launch_axpy(double *x, const double *e, double alpha, int64_t n, cudaStream_t s);
 // state export / import through the caller's slot map (-1 = no message)
+// Parity-class layout (parity.cu).  to_class = 1: dst (class layout) from src
+// (slot layout); 0: the reverse.  Both K * n elements of message precision.
+cudaError_t launch_parity_convert(const ParityGrid &g, int prec, int to_class, const void *src,
+                                  void *dst, cudaStream_t s);
+// One in-place phase of the coloured schedule over the classes of ph:
+// a, c in class layout; diag, b in natural order; Lo, Mo the class-layout state.
+cudaError_t launch_sweep_parity(const ParityGrid &g, const PhaseClasses &ph, int prec,
+                                const void *a, const void *c, const void *diag, const void *b,
+                                void *Lo, void *Mo, double *x, unsigned *flags, cudaStream_t s);
 cudaError_t launch_get_state(const int64_t *slotmap, int64_t nnz, int prec, const void *Lm,
                              const void *Mm, double *lam, double *m, cudaStream_t s);
 cudaError_t launch_set_state(const int64_t *slotmap, int64_t nnz, int prec, const double *lam,

@@ -1,0 +1,191 @@
+// Coloured schedule (red-black / 4-colour GaBP, Sec. 5.1) on grids whose
+// colours are unions of the four parity classes (x mod 2, y mod 2): red-black
+// on 5-point grids is classes {0, 3} then {1, 2}; 4-colour on 9-point grids is
+// one class per colour.
+//
+// The messages are stored by their sender, class by class (ParityGrid).  A
+// node s of the current colour pulls its incoming messages from the slots of
+// its neighbours (other classes), forms its aggregates and belief (the second
+// line of eq. nonsymmetric_GaBP_rules) and writes the messages it sends (the
+// first line) to its own slots.  Consecutive threads take consecutive nodes of
+// one class, so every load and store of a slot array is contiguous, every slot
+// is read once and written once per sweep, and no aggregate arrays are kept.
+#include <cuda_runtime.h>
+
+#include "gabp_internal.h"
+#include "sweep_row.cuh"
+
+namespace gabp {
+namespace {
+
+// v[q] by selects (a runtime index into a kernel parameter array would copy
+// the array to local memory).
+template <typename V>
+__device__ __forceinline__ V pick4(const V (&v)[4], int q)
+{
+    return q == 0 ? v[0] : q == 1 ? v[1] : q == 2 ? v[2] : v[3];
+}
+
+// Node of the class position p (base[q] <= p < base[q] + |class q|).
+__device__ __forceinline__ void class_node(const ParityGrid &g, long long p, int &q, int &x,
+                                           int &y)
+{
+    q = p >= g.base[3] ? 3 : p >= g.base[2] ? 2 : p >= g.base[1] ? 1 : 0;
+    const int i = (int)(p - pick4(g.base, q));
+    const int w = pick4(g.w, q);
+    const int cy = i / w;
+    x = 2 * (i - cy * w) + (q & 1);
+    y = 2 * cy + (q >> 1);
+}
+
+__device__ __forceinline__ long long class_pos(const ParityGrid &g, int x, int y)
+{
+    const int q = (x & 1) | ((y & 1) << 1);
+    return pick4(g.base, q) + (long long)(y >> 1) * pick4(g.w, q) + (x >> 1);
+}
+
+__device__ __forceinline__ bool in_grid(const ParityGrid &g, int x, int y)
+{
+    return (unsigned)x < (unsigned)g.m && (unsigned)y < (unsigned)g.m;
+}
+
+// Class layout <-> slot layout (slot k * n + r holds the entry (r, r + off[k]),
+// i.e. the message r + off[k] -> r).  Every destination element is written.
+template <typename T>
+__global__ void k_parity_convert(ParityGrid g, int to_class, const T *__restrict__ src,
+                                 T *__restrict__ dst)
+{
+    const long long n = (long long)g.m * g.m;
+    const long long total = n * g.K;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int k = (int)(t / n);
+        const long long p = t - (long long)k * n;
+        int x, y;
+        if (to_class) {
+            int q;
+            class_node(g, p, q, x, y);  // sender s; recipient r = s + off[k]
+            const int rx = x + g.dx[k], ry = y + g.dy[k];
+            dst[t] = in_grid(g, rx, ry) ? src[(long long)g.krev[k] * n + (long long)ry * g.m + rx]
+                                        : T(0);
+        } else {
+            x = (int)(p % g.m);  // recipient r; sender s = r + off[k]
+            y = (int)(p / g.m);
+            const int sx = x + g.dx[k], sy = y + g.dy[k];
+            dst[t] = in_grid(g, sx, sy) ? src[(long long)g.krev[k] * n + class_pos(g, sx, sy)]
+                                        : T(0);
+        }
+    }
+}
+
+template <typename T, int K>
+__global__ void __launch_bounds__(256) k_sweep_parity(ParityGrid g, PhaseClasses ph,
+                                                      const T *__restrict__ a,
+                                                      const T *__restrict__ c,
+                                                      const T *__restrict__ diag,
+                                                      const T *__restrict__ b, T *Lo, T *Mo,
+                                                      double *__restrict__ x,
+                                                      unsigned *__restrict__ flags)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long end = ph.nq >= 4 ? ph.start[4] : ph.nq == 3 ? ph.start[3] : ph.nq == 2 ? ph.start[2] : ph.start[1];
+    if (t >= end) return;
+    int q = ph.q[0];
+    long long t0 = 0;
+#pragma unroll
+    for (int j = 1; j < 4; ++j)
+        if (j < ph.nq && t >= ph.start[j]) {
+            q = ph.q[j];
+            t0 = ph.start[j];
+        }
+    const int i = (int)(t - t0);
+    const int w = pick4(g.w, q);
+    const int cy = i / w;
+    const int sx = 2 * (i - cy * w) + (q & 1), sy = 2 * cy + (q >> 1);
+    const long long n = (long long)g.m * g.m;
+    const long long pos = pick4(g.base, q) + i;
+    const long long s = (long long)sy * g.m + sx;
+    // every load of the node first: incoming messages (the neighbour's slot
+    // krev[k] is its message to s), the coefficients of the outgoing ones
+    T lin[K], min_[K], av[K], cv[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const int nx = sx + g.dx[k], ny = sy + g.dy[k];
+        const bool in = in_grid(g, nx, ny);
+        const long long src = in ? (long long)g.krev[k] * n + class_pos(g, nx, ny)
+                                 : (long long)k * n + pos;  // any valid address
+        const T l = Lo[src], mm = Mo[src];
+        lin[k] = in ? l : T(0);
+        min_[k] = in ? mm : T(0);
+        av[k] = a[(long long)k * n + pos];
+        cv[k] = c[(long long)k * n + pos];
+    }
+    T P = diag[s], B = b[s];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        P += lin[k];
+        B += min_[k];
+    }
+    if (x) x[s] = (double)(B / P);
+    bool bad = false;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        if (!nonzero(av[k])) continue;  // no recipient: the slot stays zero
+        const T d = P - lin[k];
+        bad |= bad_den(d);
+        const T qd = fast_rcp(d);
+        Lo[(long long)k * n + pos] = cv[k] * qd;
+        Mo[(long long)k * n + pos] = av[k] * (B - min_[k]) * qd;
+    }
+    if (bad) atomicOr(flags, FLAG_BREAKDOWN);
+}
+
+}  // namespace
+
+cudaError_t launch_parity_convert(const ParityGrid &g, int prec, int to_class, const void *src,
+                                  void *dst, cudaStream_t s)
+{
+    const long long total = (long long)g.m * g.m * g.K;
+    if (total == 0) return cudaSuccess;
+    count_launches(s, 1);
+    const long long want = (total + 255) / 256;
+    const int grid = (int)(want < 152 * 32 ? want : 152 * 32);
+    if (prec == 0)
+        k_parity_convert<double><<<grid, 256, 0, s>>>(g, to_class, (const double *)src, (double *)dst);
+    else
+        k_parity_convert<float><<<grid, 256, 0, s>>>(g, to_class, (const float *)src, (float *)dst);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sweep_parity(const ParityGrid &g, const PhaseClasses &ph, int prec,
+                                const void *a, const void *c, const void *diag, const void *b,
+                                void *Lo, void *Mo, double *x, unsigned *flags, cudaStream_t s)
+{
+    const long long nodes = ph.start[ph.nq];
+    if (nodes == 0) return cudaSuccess;
+    count_launches(s, 1);
+    const int grid = (int)((nodes + 255) / 256);
+#define GABP_PAR_CASE(KK)                                                                         \
+    case KK:                                                                                      \
+        if (prec == 0)                                                                            \
+            k_sweep_parity<double, KK><<<grid, 256, 0, s>>>(                                      \
+                g, ph, (const double *)a, (const double *)c, (const double *)diag,                \
+                (const double *)b, (double *)Lo, (double *)Mo, x, flags);                         \
+        else                                                                                      \
+            k_sweep_parity<float, KK><<<grid, 256, 0, s>>>(                                       \
+                g, ph, (const float *)a, (const float *)c, (const float *)diag,                   \
+                (const float *)b, (float *)Lo, (float *)Mo, x, flags);                            \
+        break;
+    switch (g.K) {
+        GABP_PAR_CASE(2)
+        GABP_PAR_CASE(4)
+        GABP_PAR_CASE(6)
+        GABP_PAR_CASE(8)
+        default:
+            return cudaErrorInvalidValue;
+    }
+#undef GABP_PAR_CASE
+    return cudaGetLastError();
+}
+
+}  // namespace gabp

@@ -324,6 +324,67 @@ def test_colored_sweeps_match_oracle(g, name, layout):
     x_o, _, _ = oracle.sweeps_colored(A, b, colors, nc, 29, lt, mm)
     x = s.sweep(dev(b), 29)
     assert rel(host(x), x_o) <= 1e-10
+    # grid colourings run on the parity-class layout, the others on slots
+    assert s.info()["parity_layout"] == (1 if (COLORED[name] and layout == "auto") else 0)
+    lam, mg_ = s.get_state()
+    assert rel(host(lam), oracle.diag_contrib(A, lt)) <= 1e-10
+    assert rel(host(mg_), mm) <= 1e-10
+
+
+@pytest.mark.parametrize("name", ["c1_32", "lognormal_33"])
+def test_colored_three_colours_on_slot_layout(g, name):
+    """(x + 2y) mod 3 colours a 5-point grid properly but is no union of parity
+    classes: it runs on the slot layout, against the oracle."""
+    A = MATS[name]
+    m = int(round(A.n ** 0.5))
+    iy, ix = np.meshgrid(np.arange(m), np.arange(m), indexing="ij")
+    colors = ((ix + 2 * iy) % 3).reshape(-1).astype(np.int32)
+    b = _rhs(A.n, 35)
+    s = g.GabpSolver(A, "fp64")
+    assert s.set_schedule("colored", colors) == 3
+    assert s.info()["parity_layout"] == 0
+    lt, mm = oracle.zero_state(A)
+    x_o, _, _ = oracle.sweeps_colored(A, b, colors, 3, 40, lt, mm)
+    x = s.sweep(dev(b), 40)
+    assert rel(host(x), x_o) <= 1e-10
+
+
+@pytest.mark.parametrize("name", ["c1_32", "aniso9_31"])
+def test_colored_transpose_on_parity_layout(g, name):
+    """The transposed coloured solve (adjoint) on the parity-class layout equals
+    the oracle's coloured solve of A^T."""
+    A = MATS[name]
+    m = int(round(A.n ** 0.5))
+    colors = oracle.grid_colors(m, COLORED[name])
+    gvec = _rhs(A.n, 36)
+    ref = oracle.solve(A.transpose(), gvec, 1e-10, 5000, color=colors, ncolors=COLORED[name])
+    assert ref["status"] == oracle.OK
+    s = g.GabpSolver(A, "fp64", check_every=1)
+    s.set_schedule("colored", colors)
+    assert s.info()["parity_layout"] == 1
+    lam, it, rr, st = s.solve_transpose(dev(gvec), 1e-10, 5000)
+    assert st == g.OK and it == ref["iters"]
+    assert rel(host(lam), ref["x"]) <= 1e-10
+    # and the forward solve after it still uses A
+    ref = oracle.solve(A, gvec, 1e-10, 5000, color=colors, ncolors=COLORED[name])
+    x, it, rr, st = s.solve(dev(gvec), 1e-10, 5000)
+    assert st == g.OK and it == ref["iters"]
+    assert rel(host(x), ref["x"]) <= 1e-10
+
+
+def test_colored_float_parity_layout(g):
+    """Float messages on the parity-class layout follow the FP64 oracle to float
+    accuracy over a 60-sweep trajectory (9-point, 4 colours, odd side)."""
+    A = MATS["aniso9_31"]
+    colors = oracle.grid_colors(31, 4)
+    b = _rhs(A.n, 37)
+    s = g.GabpSolver(A, "fp32")
+    s.set_schedule("colored")
+    assert s.info()["parity_layout"] == 1
+    lt, mm = oracle.zero_state(A)
+    x_o, _, _ = oracle.sweeps_colored(A, b, colors, 4, 60, lt, mm)
+    x = s.sweep(dev(b), 60)
+    assert rel(host(x), x_o) <= 2e-5
 
 
 @pytest.mark.parametrize("name", ["c1_32", "aniso9_31"])
