@@ -1019,9 +1019,18 @@ static gabp_status setup_parity(gabp_ctx *ctx, const std::vector<int> &col, int 
     long long size[4], acc = 0;
     for (int q = 0; q < 4; ++q) {
         g.w[q] = (m - (q & 1) + 1) / 2;
-        size[q] = (long long)g.w[q] * ((m - (q >> 1) + 1) / 2);
+        g.h[q] = (m - (q >> 1) + 1) / 2;
+        size[q] = (long long)g.w[q] * g.h[q];
         g.base[q] = acc;
         acc += size[q];
+    }
+    // the full 3 x 3 neighbourhood (or its 5-point part) in ascending order
+    static const int dx4[4] = {0, -1, 1, 0}, dy4[4] = {-1, 0, 0, 1};
+    static const int dx8[8] = {-1, 0, 1, -1, 1, -1, 0, 1}, dy8[8] = {-1, -1, -1, 0, 0, 1, 1, 1};
+    g.std_order = (g.K == 4 || g.K == 8) && (long long)g.K * n < (1LL << 31);
+    for (int k = 0; k < g.K && g.std_order; ++k) {
+        const int ex = g.K == 4 ? dx4[k] : dx8[k], ey = g.K == 4 ? dy4[k] : dy8[k];
+        if (g.dx[k] != ex || g.dy[k] != ey || g.krev[k] != g.K - 1 - k) g.std_order = 0;
     }
     std::vector<PhaseClasses> phases((size_t)nc);
     for (int c = 0; c < nc; ++c) {

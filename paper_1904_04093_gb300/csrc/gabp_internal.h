@@ -35,11 +35,15 @@ struct ColorMasks {
 // = base[q] + (y / 2) w[q] + x / 2 numbers the class of s row by row.  One
 // phase reads only other classes' slots and writes only its own, contiguously.
 constexpr int KMAXPG = 8;
+// std_order = 1: the diagonals are the full 5-point (K = 4) or 9-point (K = 8)
+// neighbourhood in ascending offset order and K n < 2^31, which the sweep
+// specialises at compile time.
 struct ParityGrid {
     int m, K;
     int dx[KMAXPG], dy[KMAXPG], krev[KMAXPG];
-    int w[4];
+    int w[4], h[4];
     long long base[4];
+    int std_order;
 };
 // The parity classes one colour covers: q[j] for j < nq, its threads
 // start[j] <= t < start[j + 1].

@@ -140,6 +140,95 @@ __global__ void __launch_bounds__(256) k_sweep_parity(ParityGrid g, PhaseClasses
     if (bad) atomicOr(flags, FLAG_BREAKDOWN);
 }
 
+// Compile-time neighbourhood of the standard diagonal orders: offsets
+// ascending, 5-point (K = 4) or 9-point (K = 8); krev[k] = K - 1 - k.
+template <int K>
+__device__ constexpr int std_dx(int k)
+{
+    return K == 4 ? (k == 1 ? -1 : k == 2 ? 1 : 0) : ((k == 0 || k == 3 || k == 5) ? -1 : (k == 1 || k == 6) ? 0 : 1);
+}
+template <int K>
+__device__ constexpr int std_dy(int k)
+{
+    return K == 4 ? (k == 0 ? -1 : k == 3 ? 1 : 0) : (k < 3 ? -1 : k < 5 ? 0 : 1);
+}
+__device__ constexpr int floor_half(int v) { return v >= 0 ? v / 2 : -((-v + 1) / 2); }
+
+// One node (cx, cy) of the class (PX, PY): the neighbour in direction k lies
+// in the class QT at class row cy + DY2 and column cx + DX2, all known at
+// compile time; only the grid edge is tested at run time.
+template <typename T, int K, int PX, int PY>
+__device__ __forceinline__ void parity_node(const ParityGrid &g, unsigned cx, unsigned cy,
+                                            const T *__restrict__ a, const T *__restrict__ c,
+                                            const T *__restrict__ diag,
+                                            const T *__restrict__ b, T *Lo, T *Mo,
+                                            double *__restrict__ x, bool &bad)
+{
+    constexpr int Q = PX | (PY << 1);
+    const unsigned m = (unsigned)g.m, n = m * m;
+    const unsigned pos = (unsigned)g.base[Q] + cy * (unsigned)g.w[Q] + cx;
+    const unsigned sx = 2u * cx + PX, sy = 2u * cy + PY;
+    T lin[K], min_[K], av[K], cv[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const int dx = std_dx<K>(k), dy = std_dy<K>(k);
+        const int qt = ((PX + dx) & 1) | (((PY + dy) & 1) << 1);
+        const int dx2 = floor_half(PX + dx), dy2 = floor_half(PY + dy);
+        const bool in = (sx + dx < m) && (sy + dy < m);  // unsigned: -1 wraps high
+        const unsigned src =
+            in ? (unsigned)(K - 1 - k) * n + (unsigned)g.base[qt] +
+                     (cy + dy2) * (unsigned)g.w[qt] + (cx + dx2)
+               : (unsigned)k * n + pos;  // any valid address
+        const T l = Lo[src], mm = Mo[src];
+        lin[k] = in ? l : T(0);
+        min_[k] = in ? mm : T(0);
+        av[k] = a[(unsigned)k * n + pos];
+        cv[k] = c[(unsigned)k * n + pos];
+    }
+    const unsigned s = sy * m + sx;
+    T P = diag[s], B = b[s];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        P += lin[k];
+        B += min_[k];
+    }
+    if (x) x[s] = (double)(B / P);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        if (!nonzero(av[k])) continue;
+        const T d = P - lin[k];
+        bad |= bad_den(d);
+        const T qd = fast_rcp(d);
+        Lo[(unsigned)k * n + pos] = cv[k] * qd;
+        Mo[(unsigned)k * n + pos] = av[k] * (B - min_[k]) * qd;
+    }
+}
+
+// Standard orders: block (x, y, z) = (class columns, class row, class of the
+// phase), so a thread finds its node without division.
+template <typename T, int K>
+__global__ void __launch_bounds__(256) k_sweep_parity_std(ParityGrid g, PhaseClasses ph,
+                                                          const T *__restrict__ a,
+                                                          const T *__restrict__ c,
+                                                          const T *__restrict__ diag,
+                                                          const T *__restrict__ b, T *Lo, T *Mo,
+                                                          double *__restrict__ x,
+                                                          unsigned *__restrict__ flags)
+{
+    const int z = blockIdx.z;
+    const int q = z == 0 ? ph.q[0] : z == 1 ? ph.q[1] : z == 2 ? ph.q[2] : ph.q[3];
+    const unsigned cx = blockIdx.x * blockDim.x + threadIdx.x, cy = blockIdx.y;
+    if (cx >= (unsigned)pick4(g.w, q) || cy >= (unsigned)pick4(g.h, q)) return;
+    bool bad = false;
+    switch (q) {
+        case 0: parity_node<T, K, 0, 0>(g, cx, cy, a, c, diag, b, Lo, Mo, x, bad); break;
+        case 1: parity_node<T, K, 1, 0>(g, cx, cy, a, c, diag, b, Lo, Mo, x, bad); break;
+        case 2: parity_node<T, K, 0, 1>(g, cx, cy, a, c, diag, b, Lo, Mo, x, bad); break;
+        default: parity_node<T, K, 1, 1>(g, cx, cy, a, c, diag, b, Lo, Mo, x, bad); break;
+    }
+    if (bad) atomicOr(flags, FLAG_BREAKDOWN);
+}
+
 }  // namespace
 
 cudaError_t launch_parity_convert(const ParityGrid &g, int prec, int to_class, const void *src,
@@ -164,6 +253,36 @@ cudaError_t launch_sweep_parity(const ParityGrid &g, const PhaseClasses &ph, int
     const long long nodes = ph.start[ph.nq];
     if (nodes == 0) return cudaSuccess;
     count_launches(s, 1);
+    if (g.std_order) {
+        int wmax = 0, hmax = 0;
+        for (int j = 0; j < ph.nq; ++j) {
+            wmax = wmax > g.w[ph.q[j]] ? wmax : g.w[ph.q[j]];
+            hmax = hmax > g.h[ph.q[j]] ? hmax : g.h[ph.q[j]];
+        }
+        const int block = wmax >= 256 ? 256 : ((wmax + 31) / 32) * 32;
+        const dim3 grid3((unsigned)((wmax + block - 1) / block), (unsigned)hmax, (unsigned)ph.nq);
+        if (hmax > 65535) return cudaErrorInvalidValue;
+        if (g.K == 4) {
+            if (prec == 0)
+                k_sweep_parity_std<double, 4><<<grid3, block, 0, s>>>(
+                    g, ph, (const double *)a, (const double *)c, (const double *)diag,
+                    (const double *)b, (double *)Lo, (double *)Mo, x, flags);
+            else
+                k_sweep_parity_std<float, 4><<<grid3, block, 0, s>>>(
+                    g, ph, (const float *)a, (const float *)c, (const float *)diag,
+                    (const float *)b, (float *)Lo, (float *)Mo, x, flags);
+        } else {
+            if (prec == 0)
+                k_sweep_parity_std<double, 8><<<grid3, block, 0, s>>>(
+                    g, ph, (const double *)a, (const double *)c, (const double *)diag,
+                    (const double *)b, (double *)Lo, (double *)Mo, x, flags);
+            else
+                k_sweep_parity_std<float, 8><<<grid3, block, 0, s>>>(
+                    g, ph, (const float *)a, (const float *)c, (const float *)diag,
+                    (const float *)b, (float *)Lo, (float *)Mo, x, flags);
+        }
+        return cudaGetLastError();
+    }
     const int grid = (int)((nodes + 255) / 256);
 #define GABP_PAR_CASE(KK)                                                                         \
     case KK:                                                                                      \

@@ -372,6 +372,38 @@ def test_colored_transpose_on_parity_layout(g, name):
     assert rel(host(x), ref["x"]) <= 1e-10
 
 
+def _seven_point(m, seed):
+    """7-point grid operator ((+-1, 0), (0, +-1), (1, -1), (-1, 1)), nonsymmetric,
+    strictly diagonally dominant M-matrix: six stored diagonals."""
+    rng = np.random.default_rng(seed)
+    off = [(1, -1), (0, -1), (-1, 0), (0, 0), (1, 0), (0, 1), (-1, 1)]
+    off.sort(key=lambda o: o[0] + m * o[1])
+    c = np.zeros((m, m, 7))
+    for k, o in enumerate(off):
+        c[:, :, k] = 1.0 if o == (0, 0) else -rng.uniform(0.02, 0.16, (m, m))
+    return P.stencil_csr(m, off, c)
+
+
+@pytest.mark.parametrize("m", [17, 24])
+def test_colored_parity_layout_six_diagonals(g, m):
+    """Six stored diagonals take the general parity-class kernel (the 5- and
+    9-point orders have their own): 4-colour grid colouring, against the oracle."""
+    A = _seven_point(m, 40 + m)
+    colors = oracle.grid_colors(m, 4)
+    b = _rhs(A.n, 38)
+    s = g.GabpSolver(A, "fp64")
+    assert s.info()["ndiag"] == 6
+    s.set_schedule("colored", colors)
+    assert s.info()["parity_layout"] == 1
+    lt, mm = oracle.zero_state(A)
+    x_o, _, _ = oracle.sweeps_colored(A, b, colors, 4, 6, lt, mm)
+    x = s.sweep(dev(b), 6)
+    assert rel(host(x), x_o) <= 1e-12
+    lam, mg_ = s.get_state()
+    assert rel(host(lam), oracle.diag_contrib(A, lt)) <= 1e-12
+    assert rel(host(mg_), mm) <= 1e-12
+
+
 def test_colored_float_parity_layout(g):
     """Float messages on the parity-class layout follow the FP64 oracle to float
     accuracy over a 60-sweep trajectory (9-point, 4 colours, odd side)."""
