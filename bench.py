@@ -55,15 +55,18 @@ def parse():
     ap.add_argument("--m", type=int, default=2048, help="grid side of the workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU sample")
-    ap.add_argument("--only", choices=["all", "fp64", "mixed"], default="all",
-                    help="profiling runs: time only one solver (no e2e, no CPU sample)")
+    ap.add_argument("--only", choices=["all", "fp64", "mixed", "sweeps"], default="all",
+                    help="profiling runs: time only one solver (no e2e, no CPU sample); "
+                         "csr workload: 'sweeps' runs a few sweeps of one context only")
+    ap.add_argument("--order", choices=["natural", "permuted"], default="natural",
+                    help="csr workload with --only sweeps: node order of the matrix")
     ap.add_argument("--schedule", choices=["all", "colored", "lines"], default="all",
                     help="schedules workload: which schedule to run")
     ap.add_argument("--prec", choices=["all", "fp64", "fp32_ir"], default="all",
                     help="schedules workload: which precision to run")
-    ap.add_argument("--workload", choices=["convdiff", "batch", "mg", "adjoint", "schedules"], default="convdiff",
-                    help="convdiff (default, the headline line); batch / mg / adjoint print "
-                         "secondary lines for the other hot-path workloads")
+    ap.add_argument("--workload", choices=["convdiff", "batch", "mg", "adjoint", "schedules", "csr"], default="convdiff",
+                    help="convdiff (default, the headline line); batch / mg / adjoint / "
+                         "schedules / csr print secondary lines for the other hot-path workloads")
     ap.add_argument("--nsys", type=int, default=512, help="batch: number of systems")
     ap.add_argument("--smax", type=int, default=256, help="batch: largest grid side")
     return ap.parse_args()
@@ -591,6 +594,81 @@ def run_schedules(args):
     return 0
 
 
+def run_csr(args):
+    """The convection-diffusion workload on the general CSR layout (edge-parallel
+    sweeps with the reverse-edge index), in natural node order and after a
+    seeded random symmetric permutation (an unstructured numbering): FP64 and
+    mixed-precision solves to rr <= 1e-10 and the sweep kernels timed alone."""
+    import torch
+    import paper_1904_04093_gb300 as g
+    import problems as P
+    g.load()
+    A0, b0 = P.config_c2(m=args.m)
+    peak, kind = measured_peaks()
+    if args.only == "sweeps":
+        # profiling run: one context, a handful of sweeps (no solves)
+        A, b = A0, b0
+        if args.order == "permuted":
+            A, perm = P.permute_symmetric(A0, 1002)
+            b = b0[perm]
+        prec = "fp32" if args.prec == "all" else ("fp64" if args.prec == "fp64" else "fp32")
+        s = g.GabpSolver(A, prec, layout="csr")
+        ms = s.time_sweeps(torch.as_tensor(b, device="cuda"), 6) / 6
+        print(json.dumps({"only": "sweeps", "m": args.m, "order": args.order, "prec": prec,
+                          "sweep_ms": ms, "GBps": s.info()["sweep_bytes"] / (ms / 1e3) / 1e9}))
+        return 0
+    out = {}
+    for order in ("natural", "permuted"):
+        if order == "natural":
+            A, b = A0, b0
+        else:
+            A, perm = P.permute_symmetric(A0, 1002)
+            b = b0[perm]
+        bd = torch.as_tensor(b, device="cuda")
+        x = torch.empty_like(bd)
+        r = {}
+        for prec in ("fp64", "fp32_ir"):
+            s = g.GabpSolver(A, prec, layout="csr", check_every=10 if prec == "fp64" else 100,
+                             freeze_lambda=0 if prec == "fp64" else -1, ir_inner_max=IR_INNER_MAX)
+            inf = s.info()
+            for _ in range(max(1, args.warmup)):
+                s.solve(bd, TOL, MAX_ITER, x)
+            ms, res = _timed_region(lambda: s.solve(bd, TOL, MAX_ITER, x), args.steps)
+            if res[3] != g.OK:
+                raise RuntimeError(f"CSR solve did not converge: status {res[3]} rr {res[2]}")
+            nsw = 50
+            # the mixed solver ends with frozen precision messages: time those sweeps first
+            mw = s.time_sweeps(bd, nsw, frozen=True) / nsw if prec == "fp32_ir" else None
+            sw = s.time_sweeps(bd, nsw) / nsw
+            r[prec] = {"ms": ms, "sweeps": res[1], "rr": res[2],
+                       "edge_updates_per_s": inf["edges"] * res[1] / (ms / 1e3),
+                       "sweep_ms": sw, "sweep_GBps": inf["sweep_bytes"] / (sw / 1e3) / 1e9,
+                       "sweep_bytes": inf["sweep_bytes"]}
+            if mw is not None:
+                r[prec]["mean_sweep_ms"] = mw
+                r[prec]["mean_sweep_GBps"] = inf["mean_sweep_bytes"] / (mw / 1e3) / 1e9
+                r[prec]["mean_sweep_bytes"] = inf["mean_sweep_bytes"]
+            s.close()
+        out[order] = r
+    nat = out["natural"]
+    f32 = nat["fp32_ir"]
+    line = {"metric": "GaBP directed-edge updates/s (FP64 solve to 1e-10), CSR layout",
+            "value": nat["fp64"]["edge_updates_per_s"], "unit": "edge-updates/s",
+            "higher_is_better": True, "steps": args.steps, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"convdiff2d_5pt_upwind_lognormal_{args.m}x{args.m}_csr",
+                       "orders": "natural = lexicographic grid order; permuted = seeded random "
+                                 "symmetric permutation (seed 1002)",
+                       "l2": "inputs larger than L2"},
+            "time_to_1e-10_ms": {o: {p: out[o][p]["ms"] for p in out[o]} for o in out},
+            "solves": out,
+            "roofline": {"kernel": "k_sweep_csr<float,4,full> (natural order, mixed inner sweeps)",
+                         "bound": "hbm", "achieved": f32["sweep_GBps"], "peak": peak, "unit": "GB/s",
+                         "frac": f32["sweep_GBps"] / peak, "peak_kind": kind,
+                         "bytes_per_launch": f32["sweep_bytes"], "launch_ms": f32["sweep_ms"]}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_adjoint(args):
     """Differentiable solve at 512^2: forward (mixed) + adjoint (mixed) + edge gradient."""
     import math as _m
@@ -643,6 +721,8 @@ def main():
         return run_adjoint(args)
     if args.workload == "schedules":
         return run_schedules(args)
+    if args.workload == "csr":
+        return run_csr(args)
     return run_ours(args)
 
 

@@ -94,6 +94,11 @@ unsigned long long launch_count();
 // ---- launchers (kernels.cu) ----
 // prec: 0 = double, 1 = float (message precision)
 cudaError_t launch_sweep(const DevLayout &L, int prec, const SweepArgs &a, int block, cudaStream_t s);
+// CSR layout, edge-parallel (csr.cu): the full sweep and the mean-only sweep with gains g
+cudaError_t launch_sweep_csr_edge(const DevLayout &L, int prec, const SweepArgs &a, cudaStream_t s);
+cudaError_t launch_sweep_mean_csr_edge(const DevLayout &L, int prec, const void *g, const void *b,
+                                       const void *P, const void *Min, const void *Bin, void *Mout,
+                                       void *Bout, double *x, cudaStream_t s);
 cudaError_t launch_aggregate(const DevLayout &L, int prec, const void *diag, const void *b,
                              const void *Lm, const void *Mm, void *P, void *B, cudaStream_t s);
 // r = b - A x in double with off-diagonal coefficients a64 = -A (layout slots), max |r|, |b| into st

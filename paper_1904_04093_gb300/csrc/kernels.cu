@@ -66,47 +66,6 @@ __global__ void __launch_bounds__(256) k_sweep_stencil(
 }
 
 // ---------------------------------------------------------------------------
-// Message sweep, CSR layout
-// ---------------------------------------------------------------------------
-template <typename T>
-__global__ void __launch_bounds__(1024) k_sweep_csr(
-    int n, const int *__restrict__ rowptr, const int *__restrict__ col,
-    const int *__restrict__ rev, const T *__restrict__ a, const T *__restrict__ c,
-    const T *__restrict__ diag, const T *__restrict__ b, const T *__restrict__ Lin,
-    const T *__restrict__ Min, const T *__restrict__ Pin, const T *__restrict__ Bin,
-    T *__restrict__ Lout, T *__restrict__ Mout, T *__restrict__ Pout, T *__restrict__ Bout,
-    double *__restrict__ x, unsigned *__restrict__ flags)
-{
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= n) return;
-    T pn = diag[r];
-    T bn = b[r];
-    if (x) x[r] = (double)(Bin[r] / Pin[r]);
-    bool bad = false;
-    const int lo = rowptr[r], hi = rowptr[r + 1];
-    for (int e = lo; e < hi; ++e) {
-        const T ae = a[e];
-        T lam = T(0), mu = T(0);
-        if (ae != T(0)) {
-            const int s = col[e];
-            const int er = rev[e];
-            const T d = Pin[s] - Lin[er];
-            bad |= bad_den(d);
-            const T q = fast_rcp(d);
-            lam = c[e] * q;
-            mu = ae * (Bin[s] - Min[er]) * q;
-        }
-        Lout[e] = lam;
-        Mout[e] = mu;
-        pn += lam;
-        bn += mu;
-    }
-    Pout[r] = pn;
-    Bout[r] = bn;
-    if (bad) atomicOr(flags, FLAG_BREAKDOWN);
-}
-
-// ---------------------------------------------------------------------------
 // Frozen precision messages (the precomputed tilde-Lambda of Sec. 4.2)
 //
 // tilde-Lambda does not depend on b (Sec. 2.3).  Once it has converged, the
@@ -190,26 +149,6 @@ __global__ void __launch_bounds__(256) k_sweep_mean_stencil(
     for (int k = 0; k < K; ++k) {
         const T mu = nonzero(ge[k]) ? ge[k] * (bs[k] - mr[k]) : T(0);
         Mout[(size_t)k * nn + r] = mu;
-        bn += mu;
-    }
-    Bout[r] = bn;
-}
-
-template <typename T>
-__global__ void __launch_bounds__(1024) k_sweep_mean_csr(
-    int n, const int *__restrict__ rowptr, const int *__restrict__ col,
-    const int *__restrict__ rev, const T *__restrict__ g, const T *__restrict__ b,
-    const T *__restrict__ P, const T *__restrict__ Min, const T *__restrict__ Bin,
-    T *__restrict__ Mout, T *__restrict__ Bout, double *__restrict__ x)
-{
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= n) return;
-    T bn = b[r];
-    if (x) x[r] = (double)(Bin[r] / P[r]);
-    for (int e = rowptr[r]; e < rowptr[r + 1]; ++e) {
-        const T ge = g[e];
-        const T mu = ge != T(0) ? ge * (Bin[col[e]] - Min[rev[e]]) : T(0);
-        Mout[e] = mu;
         bn += mu;
     }
     Bout[r] = bn;
@@ -736,17 +675,6 @@ cudaError_t sweep_stencil_T(const DevLayout &L, const SweepArgs &a, int block, c
     return cudaGetLastError();
 }
 
-template <typename T>
-cudaError_t sweep_csr_T(const DevLayout &L, const SweepArgs &a, int block, cudaStream_t s)
-{
-    const int grid = (int)((L.n + block - 1) / block);
-    k_sweep_csr<T><<<grid, block, 0, s>>>(
-        L.n, L.rowptr, L.col, L.rev, (const T *)a.a, (const T *)a.c, (const T *)a.diag,
-        (const T *)a.b, (const T *)a.Lin, (const T *)a.Min, (const T *)a.Pin, (const T *)a.Bin,
-        (T *)a.Lout, (T *)a.Mout, (T *)a.Pout, (T *)a.Bout, a.x, a.flags);
-    return cudaGetLastError();
-}
-
 }  // namespace
 
 cudaError_t launch_sweep(const DevLayout &L, int prec, const SweepArgs &a, int block,
@@ -757,7 +685,7 @@ cudaError_t launch_sweep(const DevLayout &L, int prec, const SweepArgs &a, int b
     if (L.kind == GABP_LAYOUT_STENCIL)
         return prec == 0 ? sweep_stencil_T<double>(L, a, block, s)
                          : sweep_stencil_T<float>(L, a, block, s);
-    return prec == 0 ? sweep_csr_T<double>(L, a, block, s) : sweep_csr_T<float>(L, a, block, s);
+    return launch_sweep_csr_edge(L, prec, a, s);
 }
 
 cudaError_t launch_aggregate(const DevLayout &L, int prec, const void *diag, const void *b,
@@ -1049,17 +977,7 @@ cudaError_t launch_sweep_mean(const DevLayout &L, int prec, const void *g, const
         }
 #undef GABP_MEAN_CASE
     } else {
-        const int grid = (L.n + block - 1) / block;
-        if (prec == 0)
-            k_sweep_mean_csr<double><<<grid, block, 0, s>>>(
-                L.n, L.rowptr, L.col, L.rev, (const double *)g, (const double *)b,
-                (const double *)P, (const double *)Min, (const double *)Bin, (double *)Mout,
-                (double *)Bout, x);
-        else
-            k_sweep_mean_csr<float><<<grid, block, 0, s>>>(
-                L.n, L.rowptr, L.col, L.rev, (const float *)g, (const float *)b,
-                (const float *)P, (const float *)Min, (const float *)Bin, (float *)Mout,
-                (float *)Bout, x);
+        return launch_sweep_mean_csr_edge(L, prec, g, b, P, Min, Bin, Mout, Bout, x, s);
     }
     return cudaGetLastError();
 }

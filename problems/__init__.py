@@ -51,6 +51,8 @@ __all__ = [
     "config_c4_batch",
     "config_c5",
     "lognormal_field",
+    "sparse_random_m_matrix",
+    "permute_symmetric",
 ]
 
 
@@ -224,6 +226,65 @@ def random_m_matrix(n: int, density: float, seed: int, *, nonsym_pattern: bool =
     cs = np.abs(M).sum(axis=0)
     np.fill_diagonal(M, dominance * np.maximum(np.maximum(rs, cs), 0.5))
     return dense_to_csr(M)
+
+
+def _coo_to_csr(n: int, rows: np.ndarray, cols: np.ndarray, vals: np.ndarray) -> CSR:
+    """CSR from coordinates without duplicates (sorted by row, then column)."""
+    order = np.lexsort((cols, rows))
+    rows, cols, vals = rows[order], cols[order], vals[order]
+    indptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(np.bincount(rows, minlength=n), out=indptr[1:])
+    return CSR(n, indptr, cols.astype(np.int32), vals.astype(np.float64))
+
+
+def sparse_random_m_matrix(n: int, mean_degree: float, seed: int, *, hubs: int = 0,
+                           hub_degree: int = 0, isolated: int = 0,
+                           dominance: float = 1.2) -> CSR:
+    """Sparse random M-matrix with an irregular degree distribution.
+
+    About ``n * mean_degree`` off-diagonal entries ``-U(0.1, 1)`` at uniformly
+    random positions (a structurally nonsymmetric pattern), plus ``hubs`` rows
+    with ``hub_degree`` entries each (long rows) and their transposed
+    entries in part, and ``isolated`` rows and columns left with the diagonal
+    only.  The diagonal is ``dominance`` times the larger of the absolute row
+    and column sums (at least 0.5), so the Jacobi matrix has spectral radius
+    below one.  Built without a dense array, for sizes in the millions.
+    """
+    rng = np.random.default_rng(seed)
+    m = int(round(n * mean_degree))
+    rows = rng.integers(0, n, size=m)
+    cols = rng.integers(0, n, size=m)
+    if hubs > 0 and hub_degree > 0:
+        hub_ids = rng.choice(n, size=hubs, replace=False)
+        hr = np.repeat(hub_ids, hub_degree)
+        hc = rng.integers(0, n, size=hubs * hub_degree)
+        back = rng.random(hr.size) < 0.5      # half of them also as (c, hub)
+        rows = np.concatenate([rows, hr, hc[back]])
+        cols = np.concatenate([cols, hc, hr[back]])
+    keep = rows != cols
+    if isolated > 0:
+        iso = np.zeros(n, dtype=bool)
+        iso[rng.choice(n, size=isolated, replace=False)] = True
+        keep &= ~iso[rows] & ~iso[cols]
+    key = np.unique(rows[keep].astype(np.int64) * n + cols[keep])
+    rows, cols = key // n, key % n
+    vals = -rng.uniform(0.1, 1.0, size=key.size)
+    rs = np.bincount(rows, weights=-vals, minlength=n)
+    cs = np.bincount(cols, weights=-vals, minlength=n)
+    diag = dominance * np.maximum(np.maximum(rs, cs), 0.5)
+    idx = np.arange(n, dtype=np.int64)
+    return _coo_to_csr(n, np.concatenate([rows, idx]), np.concatenate([cols, idx]),
+                       np.concatenate([vals, diag]))
+
+
+def permute_symmetric(A: CSR, seed: int):
+    """``(Q A Q^T, perm)`` for a seeded random permutation: new node ``k`` is
+    old node ``perm[k]``, so ``x_new = x_old[perm]`` and ``b_new = b_old[perm]``."""
+    perm = np.random.default_rng(seed).permutation(A.n)
+    inv = np.empty(A.n, dtype=np.int64)
+    inv[perm] = np.arange(A.n)
+    rows = np.repeat(np.arange(A.n, dtype=np.int64), np.diff(A.indptr))
+    return _coo_to_csr(A.n, inv[rows], inv[A.indices.astype(np.int64)], A.data.copy()), perm
 
 
 def paper_toy5_pattern(seed: int = 7) -> CSR:
