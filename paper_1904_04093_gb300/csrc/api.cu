@@ -106,10 +106,13 @@ struct gabp_ctx {
     ParityGrid pg{};
     std::vector<PhaseClasses> phases;
     void *pa = nullptr, *pc = nullptr, *paT = nullptr;  // a, c, a^T in class layout
-    // line schedule (lazy): grid side, couplings along columns (natural order)
-    // and along rows (transposed order), node messages of both families
+    // line schedule (lazy): grid side; couplings along rows (natural order, a
+    // row line contiguous) and along columns (transposed order, a column line
+    // contiguous) with the diagonal and b transposed; node messages of both
+    // families in natural order, plus the transposed copies the column phase
+    // reads (LHt, MHt) and writes (LVt, MVt); scratch for very long lines
     int lines_m = 0;
-    void *lsubN = nullptr, *lsupN = nullptr, *lsubT = nullptr, *lsupT = nullptr;
+    void *lsubH = nullptr, *lsupH = nullptr, *lsubV = nullptr, *lsupV = nullptr;
     void *ldiagT = nullptr, *lbT = nullptr;
     void *LH = nullptr, *MH = nullptr, *LV = nullptr, *MV = nullptr;
     void *LHt = nullptr, *MHt = nullptr, *LVt = nullptr, *MVt = nullptr;
@@ -439,19 +442,20 @@ cudaError_t sweep_once(gabp_ctx *ctx, bool transposed, double *x, cudaStream_t s
 {
     const int c0 = ctx->cur, c1 = c0 ^ 1;
     if (ctx->lines_m > 0) {
-        // Algorithm 2 over rows (transposed order), then columns (natural order)
+        // Algorithm 2 over the rows (natural order), then the columns (transposed order)
         const int m = ctx->lines_m, pr = ctx->prec;
         unsigned *fl = &ctx->dstat[0].flags;
         cudaError_t e;
-        if ((e = launch_transpose(pr, m, ctx->LV, ctx->LVt, s)) != cudaSuccess) return e;
-        if ((e = launch_transpose(pr, m, ctx->MV, ctx->MVt, s)) != cudaSuccess) return e;
-        if ((e = launch_line_phase(pr, m, ctx->lsubT, ctx->lsupT, ctx->ldiagT, ctx->lbT, ctx->LVt,
-                                   ctx->MVt, ctx->LHt, ctx->MHt, ctx->lf, ctx->ly, nullptr, fl, s)) != cudaSuccess)
+        if ((e = launch_line_phase(pr, m, ctx->lsubH, ctx->lsupH, ctx->diagT, ctx->bT, ctx->LV,
+                                   ctx->MV, ctx->LH, ctx->MH, ctx->lf, ctx->ly, nullptr, 0, fl, s)) != cudaSuccess)
             return e;
-        if ((e = launch_transpose(pr, m, ctx->LHt, ctx->LH, s)) != cudaSuccess) return e;
-        if ((e = launch_transpose(pr, m, ctx->MHt, ctx->MH, s)) != cudaSuccess) return e;
-        return launch_line_phase(pr, m, ctx->lsubN, ctx->lsupN, ctx->diagT, ctx->bT, ctx->LH,
-                                 ctx->MH, ctx->LV, ctx->MV, ctx->lf, ctx->ly, x, fl, s);
+        if ((e = launch_transpose(pr, m, ctx->LH, ctx->LHt, s)) != cudaSuccess) return e;
+        if ((e = launch_transpose(pr, m, ctx->MH, ctx->MHt, s)) != cudaSuccess) return e;
+        if ((e = launch_line_phase(pr, m, ctx->lsubV, ctx->lsupV, ctx->ldiagT, ctx->lbT, ctx->LHt,
+                                   ctx->MHt, ctx->LVt, ctx->MVt, ctx->lf, ctx->ly, x, 1, fl, s)) != cudaSuccess)
+            return e;
+        if ((e = launch_transpose(pr, m, ctx->LVt, ctx->LV, s)) != cudaSuccess) return e;
+        return launch_transpose(pr, m, ctx->MVt, ctx->MV, s);
     }
     if (ctx->parity) {
         for (const PhaseClasses &ph : ctx->phases) {
@@ -931,7 +935,7 @@ static gabp_status setup_lines(gabp_ctx *ctx)
     const int64_t *ip = ctx->h_indptr.data();
     const int32_t *ix = ctx->h_indices.data();
     const double *dv = ctx->h_data.data();
-    std::vector<double> subN(n, 0.0), supN(n, 0.0), subT(n, 0.0), supT(n, 0.0), dT(n, 0.0);
+    std::vector<double> subH(n, 0.0), supH(n, 0.0), subV(n, 0.0), supV(n, 0.0), dT(n, 0.0);
     std::vector<double> dg(n, 0.0);
     for (int r = 0; r < n; ++r) {
         const int rx = r % m, ry = r / m;
@@ -939,10 +943,10 @@ static gabp_status setup_lines(gabp_ctx *ctx)
             const int j = ix[p];
             const int jx = j % m, jy = j / m;
             if (j == r) dg[r] = dv[p];
-            else if (jy == ry && jx == rx - 1) subT[(size_t)rx * m + ry] = dv[p];   // west, along the row
-            else if (jy == ry && jx == rx + 1) supT[(size_t)rx * m + ry] = dv[p];   // east
-            else if (jx == rx && jy == ry - 1) subN[r] = dv[p];                      // south, along the column
-            else if (jx == rx && jy == ry + 1) supN[r] = dv[p];                      // north
+            else if (jy == ry && jx == rx - 1) subH[r] = dv[p];                      // west, along the row
+            else if (jy == ry && jx == rx + 1) supH[r] = dv[p];                      // east
+            else if (jx == rx && jy == ry - 1) subV[(size_t)rx * m + ry] = dv[p];   // south, along the column
+            else if (jx == rx && jy == ry + 1) supV[(size_t)rx * m + ry] = dv[p];   // north
             else return fail(GABP_E_INVALID_ARG, "line schedule needs a 5-point grid matrix (every edge inside a row or a column)");
         }
     }
@@ -958,17 +962,22 @@ static gabp_status setup_lines(gabp_ctx *ctx)
         }
         return GABP_OK;
     };
-    CKS(put(&ctx->lsubN, subN));
-    CKS(put(&ctx->lsupN, supN));
-    CKS(put(&ctx->lsubT, subT));
-    CKS(put(&ctx->lsupT, supT));
+    CKS(put(&ctx->lsubH, subH));
+    CKS(put(&ctx->lsupH, supH));
+    CKS(put(&ctx->lsubV, subV));
+    CKS(put(&ctx->lsupV, supV));
     CKS(put(&ctx->ldiagT, dT));
     void **bufs[] = {&ctx->lbT, &ctx->LH, &ctx->MH, &ctx->LV, &ctx->MV, &ctx->LHt, &ctx->MHt,
-                     &ctx->LVt, &ctx->MVt, &ctx->lf, &ctx->ly};
+                     &ctx->LVt, &ctx->MVt};
     for (void **bp : bufs) {
         if (!*bp) CKS(dalloc(ctx, bp, nb));
         CK(cudaMemset(*bp, 0, nb));
     }
+    if (line_needs_scratch(ctx->prec, m)) {
+        if (!ctx->lf) CKS(dalloc(ctx, &ctx->lf, nb));
+        if (!ctx->ly) CKS(dalloc(ctx, &ctx->ly, nb));
+    }
+    CK(prepare_line_kernels(ctx->prec, m));
     ctx->lines_m = m;
     return GABP_OK;
 }

@@ -144,12 +144,17 @@ cudaError_t launch_sweep_color(const DevLayout &L, int prec, const unsigned char
                                const ColorMasks *cm, const void *a, const void *c, void *Lm,
                                void *Mm, void *P, void *B, double *x, unsigned *flags,
                                cudaStream_t s);
-// line GaBP (lines.cu): one phase over the m lines of a layout (element i of
-// line c at i*m + c), and an m x m transpose
+// line GaBP (lines.cu): one phase over the m lines of a layout in which line c
+// is contiguous (element i at c * m + i); x (nullable) receives the lines'
+// solutions at c * m + i, or at i * m + c when x_transposed; f, y: scratch of
+// m * m elements, needed only when line_needs_scratch(prec, m)
 cudaError_t launch_line_phase(int prec, int m, const void *sub, const void *sup, const void *diag,
                               const void *b, const void *Loth, const void *Moth, void *Lown,
-                              void *Mown, void *f, void *y, double *x, unsigned *flags,
-                              cudaStream_t s);
+                              void *Mown, void *f, void *y, double *x, int x_transposed,
+                              unsigned *flags, cudaStream_t s);
+bool line_needs_scratch(int prec, int m);
+// raises the kernel's dynamic shared-memory limit for lines of length m (once, at setup)
+cudaError_t prepare_line_kernels(int prec, int m);
 cudaError_t launch_transpose(int prec, int m, const void *in, void *out, cudaStream_t s);
 cudaError_t launch_to_double(int prec, const void *in, double *out, int64_t n, cudaStream_t s);
 // a^T[e] = a[rev(e)] (mean-message coefficients of the transposed system)

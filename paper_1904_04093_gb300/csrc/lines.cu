@@ -8,15 +8,36 @@
 //     d_i = A_ii + Lambda'_i,  r_i = b_i + m'_i
 //     T   = tridiagonal(sub_i, d_i, sup_i)     ([A]_L plus the diagonal corrections)
 //     x   = T^{-1} r                           (the region's solution)
-//     S_i = 1 / (T^{-1})_ii = f_i + g_i - d_i  (f, g: forward and backward pivots)
+//     S_i = 1 / (T^{-1})_ii
 //     Lambda_i = S_i - d_i,   m_i = S_i x_i - r_i
 // which is the message rule of Algorithm 2 written for a tridiagonal block.
-// One thread walks one line (Thomas elimination; the loads of a step do not
-// depend on the recurrence, so unrolling keeps several steps' loads in
-// flight); lines are laid out so that consecutive threads touch consecutive
-// addresses: element i of line c sits at i * m + c.  Columns are lines in the natural (row-major) order; rows are
-// lines in the transposed order, so the messages cross between the two
-// orders through tiled transposes.
+//
+// Both quantities come from the forward and the backward elimination of T:
+//     f_i = d_i - sub_i sup_{i-1} / f_{i-1},   yF_i = r_i - sub_i yF_{i-1} / f_{i-1}
+//     g_i = d_i - sup_i sub_{i+1} / g_{i+1},   yB_i = r_i - sup_i yB_{i+1} / g_{i+1}
+// Adding the two eliminated forms of row i (f_i x_i + sup_i x_{i+1} = yF_i and
+// sub_i x_{i-1} + g_i x_i = yB_i) and subtracting row i itself gives
+//     (f_i + g_i - d_i) x_i = yF_i + yB_i - r_i,
+// so S_i = f_i + g_i - d_i (the twisted-factorisation pivot, the inverse of
+// the diagonal of T^{-1}) and
+//     Lambda_i = (f_i - d_i) + (g_i - d_i),   m_i = (yF_i - r_i) + (yB_i - r_i).
+//
+// Parallel form.  One CTA per line; thread t owns the contiguous chunk
+// [t C, t C + C) of the line.  In homogeneous coordinates (N, D, Y) with
+// f = N / D and yF = Y / D the forward elimination is linear:
+//     (N, D, Y)_i = [[d_i, -p_i, 0], [1, 0, 0], [r_i, 0, -sub_i]] (N, D, Y)_{i-1},
+// p_i = sub_i sup_{i-1}, starting from (1, 0, 0); the backward one likewise
+// with sup_i, q_i = sup_i sub_{i+1}.  Each thread forms the product of its
+// chunk's matrices, a block scan of the products (warp shuffles, then the
+// warp totals) gives every chunk its exact entry state, and each thread then
+// runs the ordinary recurrences over its chunk from that state.  Products and
+// states are rescaled by powers of two (exact; the ratios N/D, Y/D are what
+// matter).  The line's data are staged in shared memory and the results leave
+// through coalesced copies; lines too long for shared memory run the same
+// algorithm on global memory.
+//
+// Layout: element i of line c sits at c * m + i (rows: natural order;
+// columns: transposed order), so a line is contiguous.
 #include <cuda_runtime.h>
 
 #include "gabp_internal.h"
@@ -25,69 +46,338 @@
 namespace gabp {
 namespace {
 
+constexpr int kLineMaxThreads = 256;
+constexpr int kLineMaxWarps = kLineMaxThreads / 32;
+constexpr size_t kLineSmemMax = 220 * 1024;  // dynamic part; the scan's own arrays are static
+
+// [[a, b, 0], [c, e, 0], [g, h, k]]
 template <typename T>
-__global__ void __launch_bounds__(32) k_line_phase(int m, const T *__restrict__ sub,
-                                                   const T *__restrict__ sup,
-                                                   const T *__restrict__ diag,
-                                                   const T *__restrict__ b,
-                                                   const T *__restrict__ Loth,
-                                                   const T *__restrict__ Moth, T *__restrict__ Lown,
-                                                   T *__restrict__ Mown, T *__restrict__ f,
-                                                   T *__restrict__ y, double *__restrict__ x,
-                                                   unsigned *__restrict__ flags)
+struct Xf {
+    T a, b, c, e, g, h, k;
+};
+
+template <typename T>
+__device__ __forceinline__ Xf<T> xf_identity()
 {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= m) return;
-    const size_t mm = (size_t)m;
-    bool bad = false;
-    // forward elimination: f_i = d_i - sub_i sup_{i-1} / f_{i-1},  y_i = r_i - (sub_i / f_{i-1}) y_{i-1}
-    T fp = T(0), yp = T(0), supp = T(0);
-#pragma unroll 8
-    for (int i = 0; i < m; ++i) {
-        const size_t p = (size_t)i * mm + c;
-        const T d = diag[p] + Loth[p];
-        const T r = b[p] + Moth[p];
-        T fi, yi;
-        if (i == 0) {
-            fi = d;
-            yi = r;
-        } else {
-            const T w = sub[p] * fast_rcp(fp);
-            fi = d - w * supp;
-            yi = r - w * yp;
+    return {T(1), T(0), T(0), T(1), T(0), T(0), T(1)};
+}
+
+// t2 * t1 (t1 applied first)
+template <typename T>
+__device__ __forceinline__ Xf<T> xf_mul(const Xf<T> &t2, const Xf<T> &t1)
+{
+    Xf<T> r;
+    r.a = t2.a * t1.a + t2.b * t1.c;
+    r.b = t2.a * t1.b + t2.b * t1.e;
+    r.c = t2.c * t1.a + t2.e * t1.c;
+    r.e = t2.c * t1.b + t2.e * t1.e;
+    r.g = t2.g * t1.a + t2.h * t1.c + t2.k * t1.g;
+    r.h = t2.g * t1.b + t2.h * t1.e + t2.k * t1.h;
+    r.k = t2.k * t1.k;
+    return r;
+}
+
+template <typename T>
+__device__ __forceinline__ Xf<T> xf_shfl_up(const Xf<T> &v, int off)
+{
+    const unsigned F = 0xffffffffu;
+    return {__shfl_up_sync(F, v.a, off), __shfl_up_sync(F, v.b, off), __shfl_up_sync(F, v.c, off),
+            __shfl_up_sync(F, v.e, off), __shfl_up_sync(F, v.g, off), __shfl_up_sync(F, v.h, off),
+            __shfl_up_sync(F, v.k, off)};
+}
+
+template <typename T>
+__device__ __forceinline__ Xf<T> xf_shfl_down(const Xf<T> &v, int off)
+{
+    const unsigned F = 0xffffffffu;
+    return {__shfl_down_sync(F, v.a, off), __shfl_down_sync(F, v.b, off),
+            __shfl_down_sync(F, v.c, off), __shfl_down_sync(F, v.e, off),
+            __shfl_down_sync(F, v.g, off), __shfl_down_sync(F, v.h, off),
+            __shfl_down_sync(F, v.k, off)};
+}
+
+// Biased exponent field and the power of two 2^(bias - e) that scales a
+// number with exponent field e to about 1 (exact).
+__device__ __forceinline__ int expo(double v)
+{
+    return (int)(((unsigned long long)__double_as_longlong(v) >> 52) & 0x7ffull);
+}
+__device__ __forceinline__ int expo(float v) { return (int)(((unsigned)__float_as_int(v) >> 23) & 0xffu); }
+__device__ __forceinline__ bool expo_scalable(int e, double) { return e > 0 && e < 0x7ff; }
+__device__ __forceinline__ bool expo_scalable(int e, float) { return e > 0 && e < 0xff; }
+__device__ __forceinline__ double pow2_inv(int e, double)
+{
+    int f = 2046 - e;
+    f = f < 1 ? 1 : f;
+    return __longlong_as_double((long long)f << 52);
+}
+__device__ __forceinline__ float pow2_inv(int e, float)
+{
+    int f = 254 - e;
+    f = f < 1 ? 1 : f;
+    return __int_as_float(f << 23);
+}
+
+// Rescales a product by the exponent of its larger pivot entry (a or b, the
+// N components of the images of (1, 0, 0) and (0, 1, 0)).  These carry the
+// growth of the pivots; the Y row then holds ratios Y / N = yF / f, bounded by
+// the data, while c, e trail a, b by one step and k only shrinks.  Scaling by
+// a larger Y entry instead would leave a, b tiny, and the squaring in the
+// block scan would flush them to zero.
+template <typename T>
+__device__ __forceinline__ void xf_normalize(Xf<T> &t)
+{
+    const int e = max(expo(t.a), expo(t.b));
+    if (!expo_scalable(e, T(0))) return;
+    const T s = pow2_inv(e, T(0));
+    t.a *= s; t.b *= s; t.c *= s; t.e *= s; t.g *= s; t.h *= s; t.k *= s;
+}
+
+// Same for a state (N, D, Y): by the exponent of N or D (f = N / D, yF = Y / D).
+template <typename T>
+__device__ __forceinline__ void st_normalize(T &N, T &D, T &Y)
+{
+    const int e = max(expo(N), expo(D));
+    if (!expo_scalable(e, T(0))) return;
+    const T s = pow2_inv(e, T(0));
+    N *= s; D *= s; Y *= s;
+}
+
+// One elimination step (forward or backward) applied on the left of t:
+// t <- [[d, -p, 0], [1, 0, 0], [r, 0, -s]] t
+template <typename T>
+__device__ __forceinline__ void xf_step(Xf<T> &t, T d, T p, T r, T s)
+{
+    const T na = d * t.a - p * t.c, nb = d * t.b - p * t.e;
+    const T ng = r * t.a - s * t.g, nh = r * t.b - s * t.h;
+    t.c = t.a;
+    t.e = t.b;
+    t.a = na;
+    t.b = nb;
+    t.g = ng;
+    t.h = nh;
+    t.k = -s * t.k;
+}
+
+// Steps between rescalings of a chunk product: the entries grow by about the
+// pivot per step, so float rescales more often.
+template <typename T>
+constexpr int kRescaleMask = sizeof(T) == 8 ? 7 : 3;
+
+// Reciprocal of the line recurrences: the double one of the sweep; for float
+// the hardware approximation and one Newton-Raphson step (within an ulp or
+// so, enough for float messages; the IEEE-rounded intrinsic costs more).
+template <typename T>
+__device__ __forceinline__ T line_rcp(T d)
+{
+    return fast_rcp(d);
+}
+template <>
+__device__ __forceinline__ float line_rcp<float>(float d)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(d));
+    return fmaf(y, fmaf(-d, y, 1.0f), y);
+}
+
+template <typename T>
+constexpr int kPadShift = sizeof(T) == 8 ? 4 : 5;
+
+// Length of a padded shared array of m elements (pad shift sh).
+__host__ __device__ __forceinline__ int line_padded(int m, int sh) { return m + (m >> sh) + 1; }
+
+template <typename T, bool kSmem>
+__global__ void __launch_bounds__(kLineMaxThreads) k_line_scan(
+    int m, const T *__restrict__ sub, const T *__restrict__ sup, const T *__restrict__ diag,
+    const T *__restrict__ b, const T *__restrict__ Loth, const T *__restrict__ Moth,
+    T *__restrict__ Lown, T *__restrict__ Mown, T *__restrict__ fws, T *__restrict__ yws,
+    double *__restrict__ x, int x_transposed, unsigned *__restrict__ flags)
+{
+    extern __shared__ __align__(16) unsigned char line_smem[];
+    __shared__ Xf<T> wF[kLineMaxWarps], wB[kLineMaxWarps];
+    __shared__ T stF[kLineMaxWarps][3], stB[kLineMaxWarps][3];
+
+    const int line = blockIdx.x, tid = threadIdx.x, NT = blockDim.x;
+    const int lane = tid & 31, w = tid >> 5, NW = NT >> 5;
+    const size_t base = (size_t)line * m;
+    const T *gd = diag + base, *gLo = Loth + base, *gb = b + base, *gMo = Moth + base;
+    // per element: d, r, the couplings sub, sup and their products
+    // p_i = sub_i sup_{i-1} (forward) and q_i = sup_i sub_{i+1} (backward);
+    // the forward results f, yF later take the places of p and sub, which the
+    // backward recurrences no longer read
+    const T *su, *sq;
+    const T *sp, *sl;
+    T *sd = nullptr, *sr = nullptr, *sf, *sy;
+    // shared arrays hold element i at i + (i >> kPadShift): one pad word per
+    // 32 floats (16 doubles), so that the threads' chunk walks (stride C)
+    // fall in distinct banks; global arrays use plain indices
+    const int sh = kSmem ? kPadShift<T> : 31;
+    auto ix = [&](int i) -> int { return i + (i >> sh); };
+    if (kSmem) {
+        const int mp = line_padded(m, kPadShift<T>);
+        T *sm = reinterpret_cast<T *>(line_smem);
+        sd = sm;
+        sr = sm + mp;
+        T *wl = sm + 2 * (size_t)mp, *wu = sm + 3 * (size_t)mp;
+        T *wp = sm + 4 * (size_t)mp, *wq = sm + 5 * (size_t)mp;
+        const T *gl = sub + base, *gu = sup + base;
+        for (int i = tid; i < m; i += NT) {
+            const T li = gl[i], ui = gu[i];
+            const int j = ix(i);
+            sd[j] = gd[i] + gLo[i];
+            sr[j] = gb[i] + gMo[i];
+            wl[j] = li;
+            wu[j] = ui;
+            wp[j] = i > 0 ? li * gu[i - 1] : T(0);
+            wq[j] = i + 1 < m ? ui * gl[i + 1] : T(0);
         }
-        bad |= bad_den(fi);
-        f[p] = fi;
-        y[p] = yi;
-        fp = fi;
-        yp = yi;
-        supp = sup[p];
+        sl = wl;
+        su = wu;
+        sp = wp;
+        sq = wq;
+        sf = wp;
+        sy = wl;
+        __syncthreads();
+    } else {
+        sl = sub + base;
+        su = sup + base;
+        sp = nullptr;
+        sq = nullptr;
+        sf = fws + base;
+        sy = yws + base;
     }
-    // back substitution with the backward pivots g_i = d_i - sup_i sub_{i+1} / g_{i+1}
-    T xn = T(0), gn = T(0), subn = T(0);
-#pragma unroll 8
-    for (int i = m - 1; i >= 0; --i) {
-        const size_t p = (size_t)i * mm + c;
-        const T d = diag[p] + Loth[p];
-        const T r = b[p] + Moth[p];
-        const T fi = f[p];
-        const T su = sup[p];
-        T xi, gi;
-        if (i == m - 1) {
-            xi = y[p] * fast_rcp(fi);
-            gi = d;
-        } else {
-            xi = (y[p] - su * xn) * fast_rcp(fi);
-            gi = d - su * subn * fast_rcp(gn);
+    auto Dv = [&](int i) -> T { return kSmem ? sd[ix(i)] : gd[i] + gLo[i]; };
+    auto Rv = [&](int i) -> T { return kSmem ? sr[ix(i)] : gb[i] + gMo[i]; };
+    auto Lv = [&](int i) -> T { return sl[ix(i)]; };
+    auto Uv = [&](int i) -> T { return su[ix(i)]; };
+    auto Pv = [&](int i) -> T { return kSmem ? sp[ix(i)] : (i > 0 ? sl[i] * su[i - 1] : T(0)); };
+    auto Qv = [&](int i) -> T { return kSmem ? sq[ix(i)] : (i + 1 < m ? su[i] * sl[i + 1] : T(0)); };
+
+    const int C = (m + NT - 1) / NT;
+    const int lo = min(m, tid * C), hi = min(m, lo + C);
+
+    // chunk products, forward (ascending i) and backward (descending i)
+    Xf<T> pf = xf_identity<T>(), pb = xf_identity<T>();
+    for (int i = lo, k = 0; i < hi; ++i, ++k) {
+        xf_step(pf, Dv(i), Pv(i), Rv(i), Lv(i));
+        if ((k & kRescaleMask<T>) == kRescaleMask<T>) xf_normalize(pf);
+    }
+    xf_normalize(pf);
+    for (int i = hi - 1, k = 0; i >= lo; --i, ++k) {
+        xf_step(pb, Dv(i), Qv(i), Rv(i), Uv(i));
+        if ((k & kRescaleMask<T>) == kRescaleMask<T>) xf_normalize(pb);
+    }
+    xf_normalize(pb);
+
+    // inclusive prefix (forward) and suffix (backward) products within the warp
+    for (int off = 1; off < 32; off <<= 1) {
+        const Xf<T> o = xf_shfl_up(pf, off);
+        if (lane >= off) {
+            pf = xf_mul(pf, o);
+            xf_normalize(pf);
         }
-        bad |= bad_den(gi);
-        const T S = fi + gi - d;
-        Lown[p] = S - d;
-        Mown[p] = S * xi - r;
-        if (x) x[p] = (double)xi;
-        xn = xi;
-        gn = gi;
-        subn = sub[p];
+    }
+    for (int off = 1; off < 32; off <<= 1) {
+        const Xf<T> o = xf_shfl_down(pb, off);
+        if (lane + off < 32) {
+            pb = xf_mul(pb, o);
+            xf_normalize(pb);
+        }
+    }
+    if (lane == 31) wF[w] = pf;
+    if (lane == 0) wB[w] = pb;
+    __syncthreads();
+    if (tid == 0) {
+        // entry state of every warp, forward from (1, 0, 0) at the line start
+        T N = T(1), D = T(0), Y = T(0);
+        for (int v = 0; v < NW; ++v) {
+            stF[v][0] = N;
+            stF[v][1] = D;
+            stF[v][2] = Y;
+            const Xf<T> &t = wF[v];
+            const T n2 = t.a * N + t.b * D, d2 = t.c * N + t.e * D, y2 = t.g * N + t.h * D + t.k * Y;
+            N = n2;
+            D = d2;
+            Y = y2;
+            st_normalize(N, D, Y);
+        }
+        // and backward from (1, 0, 0) past the line end
+        N = T(1);
+        D = T(0);
+        Y = T(0);
+        for (int v = NW - 1; v >= 0; --v) {
+            stB[v][0] = N;
+            stB[v][1] = D;
+            stB[v][2] = Y;
+            const Xf<T> &t = wB[v];
+            const T n2 = t.a * N + t.b * D, d2 = t.c * N + t.e * D, y2 = t.g * N + t.h * D + t.k * Y;
+            N = n2;
+            D = d2;
+            Y = y2;
+            st_normalize(N, D, Y);
+        }
+    }
+    __syncthreads();
+    Xf<T> ef = xf_shfl_up(pf, 1), eb = xf_shfl_down(pb, 1);
+    if (lane == 0) ef = xf_identity<T>();
+    if (lane == 31) eb = xf_identity<T>();
+
+    bool bad = false;
+    // forward recurrences over the chunk from its entry state
+    {
+        const T N0 = stF[w][0], D0 = stF[w][1], Y0 = stF[w][2];
+        const T N = ef.a * N0 + ef.b * D0, D = ef.c * N0 + ef.e * D0,
+                Y = ef.g * N0 + ef.h * D0 + ef.k * Y0;
+        const T rn = line_rcp(N);
+        T inv = D * rn, wv = Y * rn;  // 1 / f_{i-1}, yF_{i-1} / f_{i-1}
+        for (int i = lo; i < hi; ++i) {
+            const T s = Lv(i);
+            const T f = Dv(i) - Pv(i) * inv;
+            const T y = Rv(i) - s * wv;
+            bad |= bad_den(f);
+            inv = line_rcp(f);
+            wv = y * inv;
+            sf[ix(i)] = f;
+            sy[ix(i)] = y;
+        }
+    }
+    // backward recurrences and the outputs
+    {
+        const T N0 = stB[w][0], D0 = stB[w][1], Y0 = stB[w][2];
+        const T N = eb.a * N0 + eb.b * D0, D = eb.c * N0 + eb.e * D0,
+                Y = eb.g * N0 + eb.h * D0 + eb.k * Y0;
+        const T rn = line_rcp(N);
+        T inv = D * rn, wv = Y * rn;  // 1 / g_{i+1}, yB_{i+1} / g_{i+1}
+        for (int i = hi - 1; i >= lo; --i) {
+            const T u = Uv(i);
+            const T d = Dv(i), r = Rv(i);
+            const T g = d - Qv(i) * inv;
+            const T yb = r - u * wv;
+            bad |= bad_den(g);
+            inv = line_rcp(g);
+            wv = yb * inv;
+            const T f = sf[ix(i)], y = sy[ix(i)];
+            const T lam = (f - d) + (g - d);
+            const T mu = (y - r) + (yb - r);
+            if (x) {
+                const double xi = (double)(((y - r) + yb) / ((f - d) + g));
+                x[x_transposed ? (size_t)i * m + line : base + i] = xi;
+            }
+            if (kSmem) {
+                sf[ix(i)] = lam;
+                sy[ix(i)] = mu;
+            } else {
+                Lown[base + i] = lam;
+                Mown[base + i] = mu;
+            }
+        }
+    }
+    if (kSmem) {
+        __syncthreads();
+        for (int i = tid; i < m; i += NT) {
+            Lown[base + i] = sf[ix(i)];
+            Mown[base + i] = sy[ix(i)];
+        }
     }
     if (bad) atomicOr(flags, FLAG_BREAKDOWN);
 }
@@ -109,28 +399,77 @@ __global__ void k_transpose(int m, const T *__restrict__ in, T *__restrict__ out
     }
 }
 
+// Threads per line: chunks of at least m / 64 (double) or m / 128 (float)
+// elements, rounded up to whole warps.  Long chunks keep the scan's share of
+// the work small; double is bound by the FP64 pipe, not by occupancy.
+#ifndef GABP_LINE_NT_F64
+#define GABP_LINE_NT_F64 128
+#endif
+#ifndef GABP_LINE_NT_F32
+#define GABP_LINE_NT_F32 256
+#endif
+int line_threads(int prec, int m)
+{
+    const int ntmax = prec == 0 ? GABP_LINE_NT_F64 : GABP_LINE_NT_F32;
+    const int C = (m + ntmax - 1) / ntmax;
+    const int nt = (m + C - 1) / C;
+    return ((nt + 31) / 32) * 32;
+}
+
+size_t line_smem_bytes(int prec, int m)
+{
+    return prec == 0 ? 6 * (size_t)line_padded(m, kPadShift<double>) * 8
+                     : 6 * (size_t)line_padded(m, kPadShift<float>) * 4;
+}
+
+template <typename T>
+cudaError_t launch_T(int m, const void *sub, const void *sup, const void *diag, const void *b,
+                     const void *Loth, const void *Moth, void *Lown, void *Mown, void *f, void *y,
+                     double *x, int x_transposed, unsigned *flags, cudaStream_t s)
+{
+    const int prec = sizeof(T) == 8 ? 0 : 1;
+    const int nt = line_threads(prec, m);
+    const size_t smem = line_smem_bytes(prec, m);
+    if (smem <= kLineSmemMax) {
+        k_line_scan<T, true><<<m, nt, smem, s>>>(
+            m, (const T *)sub, (const T *)sup, (const T *)diag, (const T *)b, (const T *)Loth,
+            (const T *)Moth, (T *)Lown, (T *)Mown, nullptr, nullptr, x, x_transposed, flags);
+    } else {
+        if (!f || !y) return cudaErrorInvalidValue;
+        k_line_scan<T, false><<<m, nt, 0, s>>>(
+            m, (const T *)sub, (const T *)sup, (const T *)diag, (const T *)b, (const T *)Loth,
+            (const T *)Moth, (T *)Lown, (T *)Mown, (T *)f, (T *)y, x, x_transposed, flags);
+    }
+    return cudaGetLastError();
+}
+
 }  // namespace
+
+bool line_needs_scratch(int prec, int m) { return line_smem_bytes(prec, m) > kLineSmemMax; }
+
+cudaError_t prepare_line_kernels(int prec, int m)
+{
+    const size_t smem = line_smem_bytes(prec, m);
+    if (smem > kLineSmemMax) return cudaSuccess;  // the global-memory form runs instead
+    if (prec == 0)
+        return cudaFuncSetAttribute(k_line_scan<double, true>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return cudaFuncSetAttribute(k_line_scan<float, true>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
 
 cudaError_t launch_line_phase(int prec, int m, const void *sub, const void *sup, const void *diag,
                               const void *b, const void *Loth, const void *Moth, void *Lown,
-                              void *Mown, void *f, void *y, double *x, unsigned *flags,
-                              cudaStream_t s)
+                              void *Mown, void *f, void *y, double *x, int x_transposed,
+                              unsigned *flags, cudaStream_t s)
 {
     if (m == 0) return cudaSuccess;
     count_launches(s, 1);
-    // few threads exist (one per line): small blocks spread them over more SMs
-    const int block = 32, grid = (m + block - 1) / block;
     if (prec == 0)
-        k_line_phase<double><<<grid, block, 0, s>>>(
-            m, (const double *)sub, (const double *)sup, (const double *)diag, (const double *)b,
-            (const double *)Loth, (const double *)Moth, (double *)Lown, (double *)Mown,
-            (double *)f, (double *)y, x, flags);
-    else
-        k_line_phase<float><<<grid, block, 0, s>>>(
-            m, (const float *)sub, (const float *)sup, (const float *)diag, (const float *)b,
-            (const float *)Loth, (const float *)Moth, (float *)Lown, (float *)Mown, (float *)f,
-            (float *)y, x, flags);
-    return cudaGetLastError();
+        return launch_T<double>(m, sub, sup, diag, b, Loth, Moth, Lown, Mown, f, y, x,
+                                x_transposed, flags, s);
+    return launch_T<float>(m, sub, sup, diag, b, Loth, Moth, Lown, Mown, f, y, x, x_transposed,
+                           flags, s);
 }
 
 cudaError_t launch_transpose(int prec, int m, const void *in, void *out, cudaStream_t s)

@@ -100,3 +100,27 @@ def test_line_solve_full_size(g, precision):
     assert st == g.OK and rr <= 1e-10
     r = b - A.matvec(host(x))
     assert np.max(np.abs(r)) / np.max(np.abs(b)) <= 1.05e-10
+
+
+def test_line_float_large_rhs_multiwarp(g):
+    """Float lines of 1024 nodes (chunks of eight, four warps per line) with a
+    right-hand side of size ~200: the chunk products are rescaled by their
+    pivot entries, so the eliminated right-hand side cannot push those to zero
+    in the block scan.  The state stays finite and within float rounding of
+    the double line sweeps (which the oracle pins at small sizes)."""
+    m = 1024
+    A, _ = P.config_c2(m=m, seed=77)
+    b = np.random.default_rng(6).uniform(-200.0, 200.0, A.n)
+    s64 = g.GabpSolver(A, "fp64")
+    s64.set_schedule("lines")
+    s32 = g.GabpSolver(A, "fp32")
+    s32.set_schedule("lines")
+    x64 = host(s64.sweep(dev(b), 30))
+    x32 = host(s32.sweep(dev(b), 30))
+    st64 = {k: host(v) for k, v in s64.get_line_state().items()}
+    st32 = {k: host(v) for k, v in s32.get_line_state().items()}
+    assert np.all(np.isfinite(x32))
+    assert rel(x32, x64) <= 1e-4
+    for key in ("LH", "MH", "LV", "MV"):
+        assert np.all(np.isfinite(st32[key])), key
+        assert rel(st32[key], st64[key]) <= 1e-4, key
