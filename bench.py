@@ -261,6 +261,9 @@ def run_ours(args):
     s64 = g.GabpSolver(A, "fp64", check_every=10, freeze_lambda=0)
     sfz = g.GabpSolver(A, "fp64", check_every=25, freeze_lambda=1)
     sir = g.GabpSolver(A, "fp32_ir", check_every=100, ir_inner_tol=1e-3, ir_inner_max=IR_INNER_MAX)
+    # the same mixed solver on the line schedule (Algorithm 2 with grid lines as regions)
+    sln = g.GabpSolver(A, "fp32_ir", check_every=10)
+    sln.set_schedule("lines")
     info = s64.info()
     info32 = sir.info()
     edges = int(info["edges"])
@@ -297,6 +300,8 @@ def run_ours(args):
             sfz.solve(bd, TOL, MAX_ITER, x)
         if args.only in ("all", "mixed"):
             sir.solve(bd, TOL, MAX_ITER, x)
+        if args.only == "all":
+            sln.solve(bd, TOL, MAX_ITER, x)
     torch.cuda.synchronize()
     if args.only != "all":
         solver = s64 if args.only == "fp64" else sir
@@ -317,6 +322,7 @@ def run_ours(args):
     launches = g.launch_count() - launches0
     ms_fz, its_fz = timed(sfz, args.steps)
     ms_ir, its_ir = timed(sir, args.steps)
+    ms_ln, its_ln = timed(sln, args.steps)
     # dominant kernel: the FP64 message sweep, timed alone on the solver's stream;
     # the others: the mean-message sweeps the frozen and mixed solvers spend their time in
     nsw = 50
@@ -346,6 +352,7 @@ def run_ours(args):
     ms64_max = max_over_ranks(ms64, dev)
     ms_fz_max = max_over_ranks(ms_fz, dev)
     ms_ir_max = max_over_ranks(ms_ir, dev)
+    ms_ln_max = max_over_ranks(ms_ln, dev)
     ms_e2e_max = max_over_ranks(ms_e2e, dev)
     sweeps64 = its64[-1]
     value = whole_job_rate(edges * sweeps64, ms64_max, world)
@@ -402,6 +409,8 @@ def run_ours(args):
             "mixed_ms": ms_ir_max, "mixed_float_sweeps": its_ir[-1],
             "mixed_speedup_vs_fp64": ms64_max / ms_ir_max,
             "mixed_speedup_vs_fp64_frozen_lambda": ms_fz_max / ms_ir_max,
+            "mixed_lines_ms": ms_ln_max, "mixed_lines_float_sweeps": its_ln[-1],
+            "mixed_lines_speedup_vs_fp64": ms64_max / ms_ln_max,
         },
         "roofline": {
             "kernel": "k_sweep_stencil<double,4> (message sweep of the FP64 solve)",
@@ -560,22 +569,30 @@ def run_schedules(args):
     for schedule in ("colored", "lines"):
         if args.schedule not in ("all", schedule):
             continue
-        for prec in ("fp64", "fp32_ir"):
+        variants = [("fp64", "fp64", 0), ("fp32_ir", "fp32_ir", -1)]
+        if schedule == "lines":
+            # precision messages frozen once converged (Sec. 4.2): on by default in the mixed solver
+            variants.append(("fp64_frozen", "fp64", 1))
+        for name, prec, freeze in variants:
             if args.prec not in ("all", prec):
                 continue
-            s = g.GabpSolver(A, prec, check_every=10)
+            s = g.GabpSolver(A, prec, check_every=10, freeze_lambda=freeze)
             s.set_schedule(schedule)
             for _ in range(max(1, args.warmup)):
                 s.solve(bd, TOL, MAX_ITER, x)
             ms, res = _timed_region(lambda: s.solve(bd, TOL, MAX_ITER, x), args.steps)
+            # a solve that froze its precision messages ends in the frozen mode: time those sweeps first
+            fz = s.time_sweeps(bd, 10, frozen=True) / 10 if (schedule == "lines" and freeze != 0) else None
             sw = s.time_sweeps(bd, 10) / 10
             r = {"ms": ms, "sweeps": res[1], "rr": res[2], "converged": res[3] == g.OK,
                  "sweep_ms": sw}
+            if fz is not None:
+                r["frozen_sweep_ms"] = fz
             if schedule == "colored":
                 inf = s.info()
                 r["parity_layout"] = inf["parity_layout"]
                 r["sweep_GBps"] = inf["colored_sweep_bytes"] / (sw / 1e3) / 1e9
-            out[f"{schedule}_{prec}"] = r
+            out[f"{schedule}_{name}"] = r
             s.close()
     head = out.get("colored_fp64") or next(iter(out.values()))
     cf = out.get("colored_fp32_ir")
@@ -584,7 +601,7 @@ def run_schedules(args):
             "data": "synthetic",
             "config": {"workload": f"convdiff2d_5pt_upwind_lognormal_{args.m}x{args.m}",
                        "schedules": "colored = red-black on the parity-class layout; "
-                                    "lines = rows then columns, one thread per line"},
+                                    "lines = rows then columns, one CTA per line (block scan)"},
             "solves": out}
     if cf:
         line["roofline"] = {"kernel": "k_sweep_parity<float,4> (red-black, mixed inner sweeps)",

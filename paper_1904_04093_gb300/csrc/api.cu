@@ -117,6 +117,12 @@ struct gabp_ctx {
     void *LH = nullptr, *MH = nullptr, *LV = nullptr, *MV = nullptr;
     void *LHt = nullptr, *MHt = nullptr, *LVt = nullptr, *MVt = nullptr;
     void *lf = nullptr, *ly = nullptr;
+    // frozen line coefficients (lazy): aF, aB, 1 / S per family, and the
+    // precision messages of the last check (convergence test)
+    void *laFH = nullptr, *laBH = nullptr, *lSH = nullptr;
+    void *laFV = nullptr, *laBV = nullptr, *lSV = nullptr;
+    void *lprevH = nullptr, *lprevV = nullptr;
+    bool lprev_valid = false;
     bool frozen = false;         // precision messages frozen (both L and P buffers equal)
     bool frozen_transposed = false;
     DevStatus *dstat = nullptr;  // [0] chunk checks, [1] refinement / misc, [2] Lambda change
@@ -403,7 +409,10 @@ void free_all(std::vector<void *> &allocs)
 gabp_status zero_messages(gabp_ctx *ctx, bool lam, bool mean)
 {
     const size_t bytes = (size_t)ctx->L.slots * esz(ctx->prec);
-    if (lam) ctx->frozen = false;
+    if (lam) {
+        ctx->frozen = false;
+        ctx->lprev_valid = false;
+    }
     if (ctx->lines_m > 0) {
         const size_t nb = (size_t)ctx->n * esz(ctx->prec);
         if (lam) CK(cudaMemsetAsync(ctx->LH, 0, nb, ctx->stream));
@@ -441,6 +450,19 @@ int block_of(const gabp_ctx *ctx) { return ctx->opt.block_size > 0 ? ctx->opt.bl
 cudaError_t sweep_once(gabp_ctx *ctx, bool transposed, double *x, cudaStream_t s)
 {
     const int c0 = ctx->cur, c1 = c0 ^ 1;
+    if (ctx->lines_m > 0 && ctx->frozen) {
+        // frozen precision messages: the mean messages move, rows then columns
+        const int m = ctx->lines_m, pr = ctx->prec;
+        cudaError_t e;
+        if ((e = launch_line_mean(pr, m, ctx->laFH, ctx->laBH, ctx->lSH, ctx->bT, ctx->MV, ctx->MH,
+                                  ctx->ly, nullptr, 0, s)) != cudaSuccess)
+            return e;
+        if ((e = launch_transpose(pr, m, ctx->MH, ctx->MHt, s)) != cudaSuccess) return e;
+        if ((e = launch_line_mean(pr, m, ctx->laFV, ctx->laBV, ctx->lSV, ctx->lbT, ctx->MHt,
+                                  ctx->MVt, ctx->ly, x, 1, s)) != cudaSuccess)
+            return e;
+        return launch_transpose(pr, m, ctx->MVt, ctx->MV, s);
+    }
     if (ctx->lines_m > 0) {
         // Algorithm 2 over the rows (natural order), then the columns (transposed order)
         const int m = ctx->lines_m, pr = ctx->prec;
@@ -542,7 +564,7 @@ gabp_status run_chunk(gabp_ctx *ctx, int k, bool transposed)
             ctx->graphs.push_back({k, parity, (int)transposed, frozen, exec});
         }
         CK(cudaGraphLaunch(exec, ctx->stream));
-        int per_sweep = ctx->lines_m > 0 ? 6 : (ctx->ncolors > 0 ? ctx->ncolors : 1);
+        int per_sweep = ctx->lines_m > 0 ? (ctx->frozen ? 4 : 6) : (ctx->ncolors > 0 ? ctx->ncolors : 1);
         if (ctx->parity) {
             per_sweep = 0;
             for (const PhaseClasses &ph : ctx->phases) per_sweep += ph.nq > 0 ? 1 : 0;
@@ -618,11 +640,55 @@ gabp_status freeze(gabp_ctx *ctx, bool transposed)
     return GABP_OK;
 }
 
+// Line schedule: the multipliers of both families from the current
+// precision messages (the row family sees LV, the column family LH).
+gabp_status freeze_lines(gabp_ctx *ctx)
+{
+    const int m = ctx->lines_m, pr = ctx->prec;
+    const size_t nb = (size_t)ctx->n * esz(pr);
+    void **bufs[] = {&ctx->laFH, &ctx->laBH, &ctx->lSH, &ctx->laFV, &ctx->laBV, &ctx->lSV};
+    for (void **bp : bufs)
+        if (!*bp) CKS(dalloc(ctx, bp, nb));
+    cudaStream_t s = ctx->stream;
+    unsigned *fl = &ctx->dstat[0].flags;
+    CK(launch_line_freeze(pr, m, ctx->lsubH, ctx->lsupH, ctx->diagT, ctx->LV, ctx->lf, ctx->ly,
+                          ctx->laFH, ctx->laBH, ctx->lSH, fl, s));
+    CK(launch_transpose(pr, m, ctx->LH, ctx->LHt, s));
+    CK(launch_line_freeze(pr, m, ctx->lsubV, ctx->lsupV, ctx->ldiagT, ctx->LHt, ctx->lf, ctx->ly,
+                          ctx->laFV, ctx->laBV, ctx->lSV, fl, s));
+    ctx->frozen = true;
+    return GABP_OK;
+}
+
+// Line schedule: freezes once the precision messages of both families moved
+// by at most `rel` times their largest value since the previous check.
+gabp_status maybe_freeze_lines(gabp_ctx *ctx, double rel)
+{
+    const int64_t n = ctx->n;
+    const size_t nb = (size_t)n * esz(ctx->prec);
+    if (!ctx->lprevH) CKS(dalloc(ctx, &ctx->lprevH, nb));
+    if (!ctx->lprevV) CKS(dalloc(ctx, &ctx->lprevV, nb));
+    if (ctx->lprev_valid) {
+        CK(cudaMemsetAsync(&ctx->dstat[2], 0, sizeof(DevStatus), ctx->stream));
+        CK(launch_lambda_change(n, ctx->prec, ctx->lprevH, ctx->LH, &ctx->dstat[2], ctx->stream));
+        CK(launch_lambda_change(n, ctx->prec, ctx->lprevV, ctx->LV, &ctx->dstat[2], ctx->stream));
+        double dmax = 0.0, lmax = 0.0;
+        unsigned fl = 0;
+        CKS(read_status(ctx, 2, &dmax, &lmax, &fl));
+        if (!(fl & FLAG_NAN) && dmax <= rel * lmax) return freeze_lines(ctx);
+    }
+    CK(cudaMemcpyAsync(ctx->lprevH, ctx->LH, nb, cudaMemcpyDeviceToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->lprevV, ctx->LV, nb, cudaMemcpyDeviceToDevice, ctx->stream));
+    ctx->lprev_valid = true;
+    return GABP_OK;
+}
+
 // Freezes once the last sweep changed no precision message by more than
 // `rel` times the largest one (rounding level).
 gabp_status maybe_freeze(gabp_ctx *ctx, bool transposed)
 {
     if (ctx->frozen) return GABP_OK;
+    if (ctx->lines_m > 0) return maybe_freeze_lines(ctx, ctx->prec == 0 ? 1e-14 : 1e-6);
     const double rel = ctx->prec == 0 ? 1e-14 : 1e-6;
     CK(cudaMemsetAsync(&ctx->dstat[2], 0, sizeof(DevStatus), ctx->stream));
     CK(launch_lambda_change(ctx->L.slots, ctx->prec, ctx->Lm[ctx->cur ^ 1], ctx->Lm[ctx->cur],
@@ -636,7 +702,7 @@ gabp_status maybe_freeze(gabp_ctx *ctx, bool transposed)
 
 bool freeze_enabled(const gabp_ctx *ctx)
 {
-    if (ctx->ncolors > 0 || ctx->lines_m > 0) return false;  // frozen sweeps use the flood schedule
+    if (ctx->ncolors > 0) return false;  // frozen sweeps: flood and line schedules
     if (ctx->opt.freeze_lambda < 0) return ctx->opt.precision == GABP_FP32_IR;
     return ctx->opt.freeze_lambda > 0;
 }

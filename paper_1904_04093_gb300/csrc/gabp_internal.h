@@ -153,6 +153,15 @@ cudaError_t launch_line_phase(int prec, int m, const void *sub, const void *sup,
                               void *Mown, void *f, void *y, double *x, int x_transposed,
                               unsigned *flags, cudaStream_t s);
 bool line_needs_scratch(int prec, int m);
+// frozen precision messages: the line's multipliers aF_i = -sub_i / f_{i-1},
+// aB_i = -sup_i / g_{i+1} and 1 / S_i from the current other-family Loth;
+// then phases that move the mean messages only
+cudaError_t launch_line_freeze(int prec, int m, const void *sub, const void *sup,
+                               const void *diag, const void *Loth, void *f, void *y, void *aF,
+                               void *aB, void *sinv, unsigned *flags, cudaStream_t s);
+cudaError_t launch_line_mean(int prec, int m, const void *aF, const void *aB, const void *sinv,
+                             const void *b, const void *Moth, void *Mown, void *y, double *x,
+                             int x_transposed, cudaStream_t s);
 // raises the kernel's dynamic shared-memory limit for lines of length m (once, at setup)
 cudaError_t prepare_line_kernels(int prec, int m);
 cudaError_t launch_transpose(int prec, int m, const void *in, void *out, cudaStream_t s);

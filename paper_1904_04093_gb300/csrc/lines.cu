@@ -186,12 +186,16 @@ constexpr int kPadShift = sizeof(T) == 8 ? 4 : 5;
 // Length of a padded shared array of m elements (pad shift sh).
 __host__ __device__ __forceinline__ int line_padded(int m, int sh) { return m + (m >> sh) + 1; }
 
-template <typename T, bool kSmem>
+// kFreeze: instead of the messages, write the frozen-state coefficients of
+// the line (precision messages converged): aF_i = -sub_i / f_{i-1},
+// aB_i = -sup_i / g_{i+1} and sinv_i = 1 / (f_i + g_i - d_i).
+template <typename T, bool kSmem, bool kFreeze>
 __global__ void __launch_bounds__(kLineMaxThreads) k_line_scan(
     int m, const T *__restrict__ sub, const T *__restrict__ sup, const T *__restrict__ diag,
     const T *__restrict__ b, const T *__restrict__ Loth, const T *__restrict__ Moth,
     T *__restrict__ Lown, T *__restrict__ Mown, T *__restrict__ fws, T *__restrict__ yws,
-    double *__restrict__ x, int x_transposed, unsigned *__restrict__ flags)
+    double *__restrict__ x, int x_transposed, unsigned *__restrict__ flags,
+    T *__restrict__ aF, T *__restrict__ aB, T *__restrict__ sinv)
 {
     extern __shared__ __align__(16) unsigned char line_smem[];
     __shared__ Xf<T> wF[kLineMaxWarps], wB[kLineMaxWarps];
@@ -332,6 +336,7 @@ __global__ void __launch_bounds__(kLineMaxThreads) k_line_scan(
         T inv = D * rn, wv = Y * rn;  // 1 / f_{i-1}, yF_{i-1} / f_{i-1}
         for (int i = lo; i < hi; ++i) {
             const T s = Lv(i);
+            if (kFreeze) aF[base + i] = -s * inv;
             const T f = Dv(i) - Pv(i) * inv;
             const T y = Rv(i) - s * wv;
             bad |= bad_den(f);
@@ -351,12 +356,17 @@ __global__ void __launch_bounds__(kLineMaxThreads) k_line_scan(
         for (int i = hi - 1; i >= lo; --i) {
             const T u = Uv(i);
             const T d = Dv(i), r = Rv(i);
+            if (kFreeze) aB[base + i] = -u * inv;
             const T g = d - Qv(i) * inv;
             const T yb = r - u * wv;
             bad |= bad_den(g);
             inv = line_rcp(g);
             wv = yb * inv;
             const T f = sf[ix(i)], y = sy[ix(i)];
+            if (kFreeze) {
+                sinv[base + i] = T(1) / ((f - d) + g);
+                continue;
+            }
             const T lam = (f - d) + (g - d);
             const T mu = (y - r) + (yb - r);
             if (x) {
@@ -372,7 +382,7 @@ __global__ void __launch_bounds__(kLineMaxThreads) k_line_scan(
             }
         }
     }
-    if (kSmem) {
+    if (kSmem && !kFreeze) {
         __syncthreads();
         for (int i = tid; i < m; i += NT) {
             Lown[base + i] = sf[ix(i)];
@@ -380,6 +390,135 @@ __global__ void __launch_bounds__(kLineMaxThreads) k_line_scan(
         }
     }
     if (bad) atomicOr(flags, FLAG_BREAKDOWN);
+}
+
+// Line phase with frozen precision messages: only the mean messages move.
+// With the fixed multipliers aF, aB and 1 / S of the line,
+//     yF_i = r_i + aF_i yF_{i-1},   yB_i = r_i + aB_i yB_{i+1},   r_i = b_i + m'_i,
+//     m_i = (yF_i - r_i) + (yB_i - r_i),   x_i = (yF_i + yB_i - r_i) / S_i,
+// the same update as the full phase up to rounding.  The recurrences are
+// affine, so a chunk is the map y -> A y + B and the block scan composes
+// pairs (A, B); no rescaling is needed.
+template <typename T, bool kSmem>
+__global__ void __launch_bounds__(kLineMaxThreads) k_line_mean(
+    int m, const T *__restrict__ aF, const T *__restrict__ aB, const T *__restrict__ sinv,
+    const T *__restrict__ b, const T *__restrict__ Moth, T *__restrict__ Mown,
+    T *__restrict__ yws, double *__restrict__ x, int x_transposed)
+{
+    extern __shared__ __align__(16) unsigned char line_smem[];
+    __shared__ T wF[kLineMaxWarps][2], wB[kLineMaxWarps][2], yinF[kLineMaxWarps],
+        yinB[kLineMaxWarps];
+
+    const int line = blockIdx.x, tid = threadIdx.x, NT = blockDim.x;
+    const int lane = tid & 31, w = tid >> 5, NW = NT >> 5;
+    const size_t base = (size_t)line * m;
+    const T *gb = b + base, *gMo = Moth + base;
+    const int sh = kSmem ? kPadShift<T> : 31;
+    auto ix = [&](int i) -> int { return i + (i >> sh); };
+    T *sr = nullptr, *sa = nullptr, *sb = nullptr, *sy;
+    if (kSmem) {
+        const int mp = line_padded(m, kPadShift<T>);
+        T *sm = reinterpret_cast<T *>(line_smem);
+        sr = sm;
+        sa = sm + mp;
+        sb = sm + 2 * (size_t)mp;
+        sy = sm + 3 * (size_t)mp;
+        for (int i = tid; i < m; i += NT) {
+            const int j = ix(i);
+            sr[j] = gb[i] + gMo[i];
+            sa[j] = aF[base + i];
+            sb[j] = aB[base + i];
+        }
+        __syncthreads();
+    } else {
+        sy = yws + base;
+    }
+    auto Rv = [&](int i) -> T { return kSmem ? sr[ix(i)] : gb[i] + gMo[i]; };
+    auto Av = [&](int i) -> T { return kSmem ? sa[ix(i)] : aF[base + i]; };
+    auto Bv = [&](int i) -> T { return kSmem ? sb[ix(i)] : aB[base + i]; };
+
+    const int C = (m + NT - 1) / NT;
+    const int lo = min(m, tid * C), hi = min(m, lo + C);
+    // the chunk's maps: forward y_{hi-1} = fa y_{lo-1} + fb, backward y_lo = ba y_hi + bb
+    T fa = T(1), fb = T(0), ba = T(1), bb = T(0);
+    for (int i = lo; i < hi; ++i) {
+        const T a = Av(i);
+        fb = a * fb + Rv(i);
+        fa = a * fa;
+    }
+    for (int i = hi - 1; i >= lo; --i) {
+        const T a = Bv(i);
+        bb = a * bb + Rv(i);
+        ba = a * ba;
+    }
+    const unsigned F = 0xffffffffu;
+    for (int off = 1; off < 32; off <<= 1) {
+        const T oa = __shfl_up_sync(F, fa, off), ob = __shfl_up_sync(F, fb, off);
+        if (lane >= off) {
+            fb = fa * ob + fb;
+            fa = fa * oa;
+        }
+    }
+    for (int off = 1; off < 32; off <<= 1) {
+        const T oa = __shfl_down_sync(F, ba, off), ob = __shfl_down_sync(F, bb, off);
+        if (lane + off < 32) {
+            bb = ba * ob + bb;
+            ba = ba * oa;
+        }
+    }
+    if (lane == 31) {
+        wF[w][0] = fa;
+        wF[w][1] = fb;
+    }
+    if (lane == 0) {
+        wB[w][0] = ba;
+        wB[w][1] = bb;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        T y = T(0);
+        for (int v = 0; v < NW; ++v) {
+            yinF[v] = y;
+            y = wF[v][0] * y + wF[v][1];
+        }
+        y = T(0);
+        for (int v = NW - 1; v >= 0; --v) {
+            yinB[v] = y;
+            y = wB[v][0] * y + wB[v][1];
+        }
+    }
+    __syncthreads();
+    T efa = __shfl_up_sync(F, fa, 1), efb = __shfl_up_sync(F, fb, 1);
+    T eba = __shfl_down_sync(F, ba, 1), ebb = __shfl_down_sync(F, bb, 1);
+    if (lane == 0) {
+        efa = T(1);
+        efb = T(0);
+    }
+    if (lane == 31) {
+        eba = T(1);
+        ebb = T(0);
+    }
+    T y = efa * yinF[w] + efb;  // yF_{lo-1}
+    for (int i = lo; i < hi; ++i) {
+        y = Av(i) * y + Rv(i);
+        sy[ix(i)] = y;
+    }
+    T yb = eba * yinB[w] + ebb;  // yB_hi
+    for (int i = hi - 1; i >= lo; --i) {
+        const T r = Rv(i);
+        yb = Bv(i) * yb + r;
+        const T yf = sy[ix(i)];
+        const T mu = (yf - r) + (yb - r);
+        if (x) x[x_transposed ? (size_t)i * m + line : base + i] = (double)(((yf - r) + yb) * sinv[base + i]);
+        if (kSmem)
+            sy[ix(i)] = mu;
+        else
+            Mown[base + i] = mu;
+    }
+    if (kSmem) {
+        __syncthreads();
+        for (int i = tid; i < m; i += NT) Mown[base + i] = sy[ix(i)];
+    }
 }
 
 // out[c * m + r] = in[r * m + c] through 32 x 32 shared-memory tiles.
@@ -422,23 +561,53 @@ size_t line_smem_bytes(int prec, int m)
                      : 6 * (size_t)line_padded(m, kPadShift<float>) * 4;
 }
 
-template <typename T>
+size_t line_mean_smem_bytes(int prec, int m)
+{
+    return prec == 0 ? 4 * (size_t)line_padded(m, kPadShift<double>) * 8
+                     : 4 * (size_t)line_padded(m, kPadShift<float>) * 4;
+}
+
+template <typename T, bool kFreeze>
 cudaError_t launch_T(int m, const void *sub, const void *sup, const void *diag, const void *b,
                      const void *Loth, const void *Moth, void *Lown, void *Mown, void *f, void *y,
-                     double *x, int x_transposed, unsigned *flags, cudaStream_t s)
+                     double *x, int x_transposed, unsigned *flags, void *aF, void *aB, void *sinv,
+                     cudaStream_t s)
 {
     const int prec = sizeof(T) == 8 ? 0 : 1;
     const int nt = line_threads(prec, m);
     const size_t smem = line_smem_bytes(prec, m);
     if (smem <= kLineSmemMax) {
-        k_line_scan<T, true><<<m, nt, smem, s>>>(
+        k_line_scan<T, true, kFreeze><<<m, nt, smem, s>>>(
             m, (const T *)sub, (const T *)sup, (const T *)diag, (const T *)b, (const T *)Loth,
-            (const T *)Moth, (T *)Lown, (T *)Mown, nullptr, nullptr, x, x_transposed, flags);
+            (const T *)Moth, (T *)Lown, (T *)Mown, nullptr, nullptr, x, x_transposed, flags,
+            (T *)aF, (T *)aB, (T *)sinv);
     } else {
         if (!f || !y) return cudaErrorInvalidValue;
-        k_line_scan<T, false><<<m, nt, 0, s>>>(
+        k_line_scan<T, false, kFreeze><<<m, nt, 0, s>>>(
             m, (const T *)sub, (const T *)sup, (const T *)diag, (const T *)b, (const T *)Loth,
-            (const T *)Moth, (T *)Lown, (T *)Mown, (T *)f, (T *)y, x, x_transposed, flags);
+            (const T *)Moth, (T *)Lown, (T *)Mown, (T *)f, (T *)y, x, x_transposed, flags,
+            (T *)aF, (T *)aB, (T *)sinv);
+    }
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_mean_T(int m, const void *aF, const void *aB, const void *sinv, const void *b,
+                          const void *Moth, void *Mown, void *y, double *x, int x_transposed,
+                          cudaStream_t s)
+{
+    const int prec = sizeof(T) == 8 ? 0 : 1;
+    const int nt = line_threads(1, m);  // little arithmetic per element: the wider split
+    const size_t smem = line_mean_smem_bytes(prec, m);
+    if (smem <= kLineSmemMax) {
+        k_line_mean<T, true><<<m, nt, smem, s>>>(m, (const T *)aF, (const T *)aB, (const T *)sinv,
+                                                 (const T *)b, (const T *)Moth, (T *)Mown, nullptr,
+                                                 x, x_transposed);
+    } else {
+        if (!y) return cudaErrorInvalidValue;
+        k_line_mean<T, false><<<m, nt, 0, s>>>(m, (const T *)aF, (const T *)aB, (const T *)sinv,
+                                               (const T *)b, (const T *)Moth, (T *)Mown, (T *)y, x,
+                                               x_transposed);
     }
     return cudaGetLastError();
 }
@@ -449,13 +618,23 @@ bool line_needs_scratch(int prec, int m) { return line_smem_bytes(prec, m) > kLi
 
 cudaError_t prepare_line_kernels(int prec, int m)
 {
-    const size_t smem = line_smem_bytes(prec, m);
-    if (smem > kLineSmemMax) return cudaSuccess;  // the global-memory form runs instead
-    if (prec == 0)
-        return cudaFuncSetAttribute(k_line_scan<double, true>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    return cudaFuncSetAttribute(k_line_scan<float, true>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int full = (int)line_smem_bytes(prec, m), mean = (int)line_mean_smem_bytes(prec, m);
+    const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    cudaError_t e = cudaSuccess;
+    if ((size_t)full <= kLineSmemMax) {
+        if (prec == 0) {
+            if ((e = cudaFuncSetAttribute(k_line_scan<double, true, false>, A, full)) != cudaSuccess) return e;
+            e = cudaFuncSetAttribute(k_line_scan<double, true, true>, A, full);
+        } else {
+            if ((e = cudaFuncSetAttribute(k_line_scan<float, true, false>, A, full)) != cudaSuccess) return e;
+            e = cudaFuncSetAttribute(k_line_scan<float, true, true>, A, full);
+        }
+        if (e != cudaSuccess) return e;
+    }
+    if ((size_t)mean <= kLineSmemMax)
+        e = prec == 0 ? cudaFuncSetAttribute(k_line_mean<double, true>, A, mean)
+                      : cudaFuncSetAttribute(k_line_mean<float, true>, A, mean);
+    return e;
 }
 
 cudaError_t launch_line_phase(int prec, int m, const void *sub, const void *sup, const void *diag,
@@ -466,10 +645,35 @@ cudaError_t launch_line_phase(int prec, int m, const void *sub, const void *sup,
     if (m == 0) return cudaSuccess;
     count_launches(s, 1);
     if (prec == 0)
-        return launch_T<double>(m, sub, sup, diag, b, Loth, Moth, Lown, Mown, f, y, x,
-                                x_transposed, flags, s);
-    return launch_T<float>(m, sub, sup, diag, b, Loth, Moth, Lown, Mown, f, y, x, x_transposed,
-                           flags, s);
+        return launch_T<double, false>(m, sub, sup, diag, b, Loth, Moth, Lown, Mown, f, y, x,
+                                       x_transposed, flags, nullptr, nullptr, nullptr, s);
+    return launch_T<float, false>(m, sub, sup, diag, b, Loth, Moth, Lown, Mown, f, y, x,
+                                  x_transposed, flags, nullptr, nullptr, nullptr, s);
+}
+
+cudaError_t launch_line_freeze(int prec, int m, const void *sub, const void *sup,
+                               const void *diag, const void *Loth, void *f, void *y, void *aF,
+                               void *aB, void *sinv, unsigned *flags, cudaStream_t s)
+{
+    if (m == 0) return cudaSuccess;
+    count_launches(s, 1);
+    // the right-hand side does not enter the coefficients: b and m' are read as the diagonal
+    if (prec == 0)
+        return launch_T<double, true>(m, sub, sup, diag, diag, Loth, Loth, nullptr, nullptr, f, y,
+                                      nullptr, 0, flags, aF, aB, sinv, s);
+    return launch_T<float, true>(m, sub, sup, diag, diag, Loth, Loth, nullptr, nullptr, f, y,
+                                 nullptr, 0, flags, aF, aB, sinv, s);
+}
+
+cudaError_t launch_line_mean(int prec, int m, const void *aF, const void *aB, const void *sinv,
+                             const void *b, const void *Moth, void *Mown, void *y, double *x,
+                             int x_transposed, cudaStream_t s)
+{
+    if (m == 0) return cudaSuccess;
+    count_launches(s, 1);
+    if (prec == 0)
+        return launch_mean_T<double>(m, aF, aB, sinv, b, Moth, Mown, y, x, x_transposed, s);
+    return launch_mean_T<float>(m, aF, aB, sinv, b, Moth, Mown, y, x, x_transposed, s);
 }
 
 cudaError_t launch_transpose(int prec, int m, const void *in, void *out, cudaStream_t s)

@@ -124,3 +124,41 @@ def test_line_float_large_rhs_multiwarp(g):
     for key in ("LH", "MH", "LV", "MV"):
         assert np.all(np.isfinite(st32[key])), key
         assert rel(st32[key], st64[key]) <= 1e-4, key
+
+
+@pytest.mark.parametrize("name", ["c1_32", "lognormal_33"])
+def test_line_frozen_precision_messages_same_solution(g, name):
+    """Precomputed precision messages (Sec. 4.2) under the line schedule:
+    once Lambda stops changing, the sweeps move only the mean messages with
+    the line's fixed elimination multipliers; the iterates are the plain
+    line sweeps' up to rounding, so the solve needs the same sweep count."""
+    A, m = CASES[name]
+    b = np.random.default_rng(8).uniform(-1, 1, A.n)
+    ref = oracle.line_solve(A, m, b, 1e-10, 2000)
+    assert ref["status"] == oracle.OK
+    s = g.GabpSolver(A, "fp64", check_every=1, freeze_lambda=1)
+    s.set_schedule("lines")
+    x, it, rr, st = s.solve(dev(b), 1e-10, 2000)
+    assert st == g.OK and rr <= 1e-10
+    assert abs(it - ref["iters"]) <= 1
+    assert rel(host(x), ref["x"]) <= 1e-9
+    # the frozen line sweeps can be timed; the messages they leave match the oracle's
+    assert s.time_sweeps(dev(b), 3, frozen=True) > 0.0
+
+
+def test_line_frozen_float_full_size_matches_double(g):
+    """Float frozen line sweeps at 2048 x 2048 (the mixed solver's inner
+    sweeps): the solve reaches 1e-10 through double refinement, and the frozen
+    and unfrozen float line solves agree."""
+    A, b = P.config_c2()
+    s = g.GabpSolver(A, "fp32_ir", check_every=10, freeze_lambda=1)
+    s.set_schedule("lines")
+    x, it, rr, st = s.solve(dev(b), 1e-10, 20000)
+    assert st == g.OK and rr <= 1e-10
+    r = b - A.matvec(host(x))
+    assert np.max(np.abs(r)) / np.max(np.abs(b)) <= 1.05e-10
+    s0 = g.GabpSolver(A, "fp32_ir", check_every=10, freeze_lambda=0)
+    s0.set_schedule("lines")
+    x0, it0, rr0, st0 = s0.solve(dev(b), 1e-10, 20000)
+    assert st0 == g.OK
+    assert rel(host(x), host(x0)) <= 1e-8
