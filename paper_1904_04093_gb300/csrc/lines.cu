@@ -521,21 +521,171 @@ __global__ void __launch_bounds__(kLineMaxThreads) k_line_mean(
     }
 }
 
-// out[c * m + r] = in[r * m + c] through 32 x 32 shared-memory tiles.
-template <typename T>
-__global__ void k_transpose(int m, const T *__restrict__ in, T *__restrict__ out)
+// Loads n <= C consecutive elements p[0..n) into v (v[j] = fill for j >= n),
+// with 16-byte vector loads when the whole chunk is present and aligned.
+template <typename T, int C>
+__device__ __forceinline__ void load_chunk(T (&v)[C], const T *__restrict__ p, int n, bool vec, T fill)
 {
-    __shared__ T tile[32][33];
-    const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
-    for (int j = threadIdx.y; j < 32; j += blockDim.y) {
-        const int r = by + j, c = bx + threadIdx.x;
-        if (r < m && c < m) tile[j][threadIdx.x] = in[(size_t)r * m + c];
+    constexpr int V = 16 / sizeof(T);
+    if (C % V == 0 && vec && n == C) {
+#pragma unroll
+        for (int j = 0; j < C; j += V) {
+            if (sizeof(T) == 4) {
+                const float4 q = *reinterpret_cast<const float4 *>(p + j);
+                v[j] = (T)q.x; v[j + 1] = (T)q.y; v[j + 2] = (T)q.z; v[j + 3] = (T)q.w;
+            } else {
+                const double2 q = *reinterpret_cast<const double2 *>(p + j);
+                v[j] = (T)q.x; v[j + 1] = (T)q.y;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < C; ++j) v[j] = j < n ? p[j] : fill;
+    }
+}
+
+// The frozen line phase with each thread's chunk of C elements held in
+// registers (no shared-memory staging): the loads are issued up front as
+// vectors, the chunk maps, the block scan and the recurrences then run on
+// registers.  Used when the line splits into at most 256 chunks of C <= 16.
+template <typename T, int C>
+__global__ void __launch_bounds__(kLineMaxThreads) k_line_mean_reg(
+    int m, const T *__restrict__ aF, const T *__restrict__ aB, const T *__restrict__ sinv,
+    const T *__restrict__ b, const T *__restrict__ Moth, T *__restrict__ Mown,
+    double *__restrict__ x, int x_transposed, int vec)
+{
+    __shared__ T wF[kLineMaxWarps][2], wB[kLineMaxWarps][2], yinF[kLineMaxWarps],
+        yinB[kLineMaxWarps];
+    const int line = blockIdx.x, tid = threadIdx.x, NT = blockDim.x;
+    const int lane = tid & 31, w = tid >> 5, NW = NT >> 5;
+    const size_t base = (size_t)line * m;
+    const int lo = tid * C;
+    const int n = max(0, min(C, m - lo));
+    const size_t p0 = base + (n > 0 ? lo : 0);
+    T r[C], a[C], c[C], mo[C];
+    // past the line end: identity steps (a = c = 1, r = 0)
+    load_chunk<T, C>(r, b + p0, n, vec != 0, T(0));
+    load_chunk<T, C>(mo, Moth + p0, n, vec != 0, T(0));
+    load_chunk<T, C>(a, aF + p0, n, vec != 0, T(1));
+    load_chunk<T, C>(c, aB + p0, n, vec != 0, T(1));
+#pragma unroll
+    for (int j = 0; j < C; ++j) r[j] += mo[j];
+
+    T fa = T(1), fb = T(0), ba = T(1), bb = T(0);
+#pragma unroll
+    for (int j = 0; j < C; ++j) {
+        fb = a[j] * fb + r[j];
+        fa = a[j] * fa;
+    }
+#pragma unroll
+    for (int j = C - 1; j >= 0; --j) {
+        bb = c[j] * bb + r[j];
+        ba = c[j] * ba;
+    }
+    const unsigned F = 0xffffffffu;
+    for (int off = 1; off < 32; off <<= 1) {
+        const T oa = __shfl_up_sync(F, fa, off), ob = __shfl_up_sync(F, fb, off);
+        const T qa = __shfl_down_sync(F, ba, off), qb = __shfl_down_sync(F, bb, off);
+        if (lane >= off) {
+            fb = fa * ob + fb;
+            fa = fa * oa;
+        }
+        if (lane + off < 32) {
+            bb = ba * qb + bb;
+            ba = ba * qa;
+        }
+    }
+    if (lane == 31) {
+        wF[w][0] = fa;
+        wF[w][1] = fb;
+    }
+    if (lane == 0) {
+        wB[w][0] = ba;
+        wB[w][1] = bb;
     }
     __syncthreads();
-    for (int j = threadIdx.y; j < 32; j += blockDim.y) {
-        const int r = bx + j, c = by + threadIdx.x;  // output row = input column
-        if (r < m && c < m) out[(size_t)r * m + c] = tile[threadIdx.x][j];
+    if (tid == 0) {
+        T y = T(0);
+        for (int v = 0; v < NW; ++v) {
+            yinF[v] = y;
+            y = wF[v][0] * y + wF[v][1];
+        }
+        y = T(0);
+        for (int v = NW - 1; v >= 0; --v) {
+            yinB[v] = y;
+            y = wB[v][0] * y + wB[v][1];
+        }
     }
+    __syncthreads();
+    T efa = __shfl_up_sync(F, fa, 1), efb = __shfl_up_sync(F, fb, 1);
+    T eba = __shfl_down_sync(F, ba, 1), ebb = __shfl_down_sync(F, bb, 1);
+    if (lane == 0) {
+        efa = T(1);
+        efb = T(0);
+    }
+    if (lane == 31) {
+        eba = T(1);
+        ebb = T(0);
+    }
+    T yf[C];
+    T y = efa * yinF[w] + efb;
+#pragma unroll
+    for (int j = 0; j < C; ++j) {
+        y = a[j] * y + r[j];
+        yf[j] = y;
+    }
+    T yb = eba * yinB[w] + ebb;
+    T mu[C];
+#pragma unroll
+    for (int j = C - 1; j >= 0; --j) {
+        yb = c[j] * yb + r[j];
+        mu[j] = (yf[j] - r[j]) + (yb - r[j]);
+        if (x && j < n)
+            x[x_transposed ? (size_t)(lo + j) * m + line : base + lo + j] =
+                (double)(((yf[j] - r[j]) + yb) * sinv[base + lo + j]);
+    }
+    constexpr int V = 16 / sizeof(T);
+    if (C % V == 0 && vec && n == C) {
+#pragma unroll
+        for (int j = 0; j < C; j += V) {
+            if (sizeof(T) == 4) {
+                *reinterpret_cast<float4 *>(Mown + p0 + j) =
+                    make_float4((float)mu[j], (float)mu[j + 1], (float)mu[j + 2], (float)mu[j + 3]);
+            } else {
+                *reinterpret_cast<double2 *>(Mown + p0 + j) = make_double2((double)mu[j], (double)mu[j + 1]);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < C; ++j)
+            if (j < n) Mown[p0 + j] = mu[j];
+    }
+}
+
+// out[c * m + r] = in[r * m + c] through 64 x 64 shared-memory tiles: a
+// 32 x 8 block moves 16 elements per thread, enough loads in flight to run
+// near the copy bandwidth.
+constexpr int kTile = 64;
+template <typename T>
+__global__ void __launch_bounds__(256) k_transpose(int m, const T *__restrict__ in, T *__restrict__ out)
+{
+    __shared__ T tile[kTile][kTile + 1];
+    const int bx = blockIdx.x * kTile, by = blockIdx.y * kTile;
+#pragma unroll
+    for (int j = threadIdx.y; j < kTile; j += 8)
+#pragma unroll
+        for (int k = 0; k < kTile; k += 32) {
+            const int r = by + j, c = bx + threadIdx.x + k;
+            if (r < m && c < m) tile[j][threadIdx.x + k] = in[(size_t)r * m + c];
+        }
+    __syncthreads();
+#pragma unroll
+    for (int j = threadIdx.y; j < kTile; j += 8)
+#pragma unroll
+        for (int k = 0; k < kTile; k += 32) {
+            const int r = bx + j, c = by + threadIdx.x + k;  // output row = input column
+            if (r < m && c < m) out[(size_t)r * m + c] = tile[threadIdx.x + k][j];
+        }
 }
 
 // Threads per line: chunks of at least m / 64 (double) or m / 128 (float)
@@ -596,6 +746,30 @@ cudaError_t launch_mean_T(int m, const void *aF, const void *aB, const void *sin
                           const void *Moth, void *Mown, void *y, double *x, int x_transposed,
                           cudaStream_t s)
 {
+    // register form: chunks of a power-of-two length C <= 16 over at most 256 threads
+    int C = 1;
+    while (C < 16 && (long long)C * kLineMaxThreads < m) C *= 2;
+    if ((long long)C * kLineMaxThreads >= m) {
+        const int nt = ((m + C - 1) / C + 31) / 32 * 32;
+        const int vec = m % (16 / (int)sizeof(T)) == 0;
+#define GABP_MEAN_REG(CC)                                                                       \
+    case CC:                                                                                    \
+        k_line_mean_reg<T, CC><<<m, nt, 0, s>>>(m, (const T *)aF, (const T *)aB,                \
+                                                (const T *)sinv, (const T *)b, (const T *)Moth, \
+                                                (T *)Mown, x, x_transposed, vec);               \
+        break;
+        switch (C) {
+            GABP_MEAN_REG(1)
+            GABP_MEAN_REG(2)
+            GABP_MEAN_REG(4)
+            GABP_MEAN_REG(8)
+            GABP_MEAN_REG(16)
+            default:
+                return cudaErrorInvalidValue;
+        }
+#undef GABP_MEAN_REG
+        return cudaGetLastError();
+    }
     const int prec = sizeof(T) == 8 ? 0 : 1;
     const int nt = line_threads(1, m);  // little arithmetic per element: the wider split
     const size_t smem = line_mean_smem_bytes(prec, m);
@@ -680,7 +854,7 @@ cudaError_t launch_transpose(int prec, int m, const void *in, void *out, cudaStr
 {
     if (m == 0) return cudaSuccess;
     count_launches(s, 1);
-    const dim3 block(32, 8), grid((m + 31) / 32, (m + 31) / 32);
+    const dim3 block(32, 8), grid((m + kTile - 1) / kTile, (m + kTile - 1) / kTile);
     if (prec == 0)
         k_transpose<double><<<grid, block, 0, s>>>(m, (const double *)in, (double *)out);
     else
