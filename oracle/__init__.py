@@ -445,10 +445,6 @@ def line_sweeps(A, m: int, b, nsweeps: int, state):
     """
     b = np.asarray(b, dtype=np.float64)
     n = m * m
-    diag = np.zeros(n)
-    rows = np.repeat(np.arange(n), np.diff(A.indptr))
-    dmask = rows == A.indices
-    diag[rows[dmask]] = A.data[dmask]
     x = np.zeros(n)
     for _ in range(nsweeps):
         for family, (Lown, Mown, Loth, Moth) in (("row", ("LH", "MH", "LV", "MV")),
@@ -457,16 +453,30 @@ def line_sweeps(A, m: int, b, nsweeps: int, state):
             newM = state[Mown].copy()
             for k in range(m):
                 idx = _line_nodes(m, family, k)
-                Lam0 = _line_matrix(A, idx) + np.diag(state[Loth][idx])
-                b0 = b[idx] + state[Moth][idx]
-                xl = np.linalg.solve(Lam0, b0)
-                S = 1.0 / np.diag(np.linalg.inv(Lam0))
-                newM[idx] = S * xl - b[idx] - state[Moth][idx]
-                newL[idx] = S - diag[idx] - state[Loth][idx]
-                x[idx] = xl
+                newL[idx], newM[idx], x[idx] = line_region_update(A, m, b, family, k,
+                                                                  state[Loth], state[Moth])
             state[Lown] = newL
             state[Mown] = newM
     return x
+
+
+def line_region_update(A, m: int, b, family: str, k: int, Loth, Moth):
+    """The messages region ``k`` of ``family`` ("row" or "col") sends to its
+    nodes, given the other family's messages ``Loth, Moth`` (full-length
+    arrays), and the region's solution: one step of Algorithm 2 for one large
+    region (see ``line_sweeps``).  Returns ``(Lambda, m, x)`` on the region's
+    nodes in line order."""
+    b = np.asarray(b, dtype=np.float64)
+    idx = _line_nodes(m, family, k)
+    rows = np.concatenate([np.full(A.indptr[v + 1] - A.indptr[v], v) for v in idx])
+    cols = np.concatenate([A.indices[A.indptr[v]:A.indptr[v + 1]] for v in idx])
+    vals = np.concatenate([A.data[A.indptr[v]:A.indptr[v + 1]] for v in idx])
+    diag = vals[rows == cols]
+    Lam0 = _line_matrix(A, idx) + np.diag(Loth[idx])
+    b0 = b[idx] + Moth[idx]
+    xl = np.linalg.solve(Lam0, b0)
+    S = 1.0 / np.diag(np.linalg.inv(Lam0))
+    return S - diag - Loth[idx], S * xl - b[idx] - Moth[idx], xl
 
 
 def line_solve(A, m: int, b, tol: float, max_iter: int):

@@ -162,3 +162,59 @@ def test_line_frozen_float_full_size_matches_double(g):
     x0, it0, rr0, st0 = s0.solve(dev(b), 1e-10, 20000)
     assert st0 == g.OK
     assert rel(host(x), host(x0)) <= 1e-8
+
+
+@pytest.fixture(scope="module")
+def long_lines():
+    """A 4700 x 4700 grid: double lines of 4700 nodes exceed shared memory
+    (the full phase runs on global memory) and split into chunks longer than
+    16 (the frozen phase stages in shared memory)."""
+    m = 4700
+    A, b = P.config_c2(m=m, seed=4700)
+    return A, b, m
+
+
+def _line_slice(v, m, family, k):
+    return v[k * m:(k + 1) * m] if family == "row" else v[k::m]
+
+
+def test_long_lines_sampled_against_oracle(g, long_lines):
+    """One more sweep from a GPU state, checked on sampled rows and columns
+    against the oracle's update of those single regions (dense solves)."""
+    A, b, m = long_lines
+    s = g.GabpSolver(A, "fp64")
+    s.set_schedule("lines")
+    s.sweep(dev(b), 3)
+    s3 = {k: host(v) for k, v in s.get_line_state().items()}
+    x = host(s.sweep(dev(b), 1))
+    s4 = {k: host(v) for k, v in s.get_line_state().items()}
+    for k in (0, 2349, m - 1):
+        lam, mu, _ = oracle.line_region_update(A, m, b, "row", k, s3["LV"], s3["MV"])
+        assert rel(_line_slice(s4["LH"], m, "row", k), lam) <= 1e-12
+        assert rel(_line_slice(s4["MH"], m, "row", k), mu) <= 1e-12
+    for k in (1, 4000):
+        lam, mu, xl = oracle.line_region_update(A, m, b, "col", k, s4["LH"], s4["MH"])
+        assert rel(_line_slice(s4["LV"], m, "col", k), lam) <= 1e-12
+        assert rel(_line_slice(s4["MV"], m, "col", k), mu) <= 1e-12
+        assert rel(_line_slice(x, m, "col", k), xl) <= 1e-12
+    s.close()
+
+
+def test_long_lines_frozen_sweep_against_oracle(g, long_lines):
+    """After the precision messages froze, one frozen sweep (mean messages
+    only) agrees with the oracle's full update of sampled regions."""
+    A, b, m = long_lines
+    s = g.GabpSolver(A, "fp64", check_every=5, freeze_lambda=1)
+    s.set_schedule("lines")
+    _, it, _, st = s.solve(dev(b), 1e-30, 600)
+    assert st == g.NOT_CONVERGED and it == 600
+    before = {k: host(v) for k, v in s.get_line_state().items()}
+    s.time_sweeps(dev(b), 1, frozen=True)  # raises unless the solve froze Lambda
+    after = {k: host(v) for k, v in s.get_line_state().items()}
+    for k in (7, 3333):
+        lam, mu, _ = oracle.line_region_update(A, m, b, "row", k, before["LV"], before["MV"])
+        assert rel(_line_slice(after["MH"], m, "row", k), mu) <= 1e-11
+        assert rel(_line_slice(after["LH"], m, "row", k), lam) <= 1e-11
+    lam, mu, _ = oracle.line_region_update(A, m, b, "col", 4699, after["LH"], after["MH"])
+    assert rel(_line_slice(after["MV"], m, "col", 4699), mu) <= 1e-11
+    s.close()
