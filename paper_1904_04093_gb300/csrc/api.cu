@@ -1528,13 +1528,27 @@ void mg_destroy(mg_ctx *mg)
 
 namespace {
 
+// Where the smoother's right-hand side r = b - A x comes from: computed, equal
+// to b because x is zero (every level below the finest starts from zero), or
+// already in the level's residual buffer (the finest level's convergence check
+// computed it for the same x).
+enum MgRes { MG_RES_COMPUTE, MG_RES_XZERO, MG_RES_READY };
+
 // Algorithm 3 on level l: r = b - A x; nu GaBP sweeps on A e = r; x += e.
-gabp_status mg_smooth(mg_ctx *mg, int l, const double *b, double *x, int nu)
+gabp_status mg_smooth(mg_ctx *mg, int l, const double *b, double *x, int nu, MgRes res)
 {
     gabp_ctx *c = mg->lv[l];
     cudaStream_t s = mg->stream;
-    CK(launch_residual(c->L, c->a64, c->diag64, b, x, c->bres, &c->dstat[1], s));
-    if (c->prec == 1) CK(launch_convert_d2f(c->bres, (float *)c->bT, c->n, s));
+    const double *r = c->bres;
+    if (res == MG_RES_COMPUTE)
+        CK(launch_residual(c->L, c->a64, c->diag64, b, x, c->bres, &c->dstat[1], s));
+    else if (res == MG_RES_XZERO)
+        r = b;
+    if (c->prec == 1) {
+        CK(launch_convert_d2f(r, (float *)c->bT, c->n, s));
+    } else if (r != c->bres) {
+        CK(cudaMemcpyAsync(c->bres, r, (size_t)c->n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    }
     if (mg->mode == MG_SMOOTH_COLD) CKS(zero_messages(c, true, true));
     else if (mg->mode == MG_SMOOTH_WARM) CKS(zero_messages(c, false, true));
     CKS(aggregate(c));
@@ -1543,7 +1557,10 @@ gabp_status mg_smooth(mg_ctx *mg, int l, const double *b, double *x, int nu)
     return GABP_OK;
 }
 
-gabp_status mg_cycle(mg_ctx *mg, int l, int last, int nu_pre, int nu_post, const double *b, double *x)
+// One V-cycle from level l; `top` says where level l's first residual comes
+// from (levels below start from x = 0).
+gabp_status mg_cycle(mg_ctx *mg, int l, int last, int nu_pre, int nu_post, const double *b, double *x,
+                     MgRes top)
 {
     cudaStream_t s = mg->stream;
     gabp_ctx *c = mg->lv[l];
@@ -1552,17 +1569,17 @@ gabp_status mg_cycle(mg_ctx *mg, int l, int last, int nu_pre, int nu_post, const
             CK(launch_dense_gemv(mg->coarse_inv, b, x, mg->nc, s));
         } else {
             // truncated hierarchy: smooth on the last used level instead of a direct solve
-            CKS(mg_smooth(mg, l, b, x, std::max(1, nu_pre + nu_post)));
+            CKS(mg_smooth(mg, l, b, x, std::max(1, nu_pre + nu_post), top));
         }
         return GABP_OK;
     }
-    if (nu_pre > 0) CKS(mg_smooth(mg, l, b, x, nu_pre));
+    if (nu_pre > 0) CKS(mg_smooth(mg, l, b, x, nu_pre, top));
     CK(launch_residual(c->L, c->a64, c->diag64, b, x, c->bres, &c->dstat[1], s));
     CK(launch_restrict_fw(c->bres, mg->side[l], mg->scale, mg->b[l + 1], s));
     CK(cudaMemsetAsync(mg->x[l + 1], 0, (size_t)mg->lv[l + 1]->n * sizeof(double), s));
-    CKS(mg_cycle(mg, l + 1, last, nu_pre, nu_post, mg->b[l + 1], mg->x[l + 1]));
+    CKS(mg_cycle(mg, l + 1, last, nu_pre, nu_post, mg->b[l + 1], mg->x[l + 1], MG_RES_XZERO));
     CK(launch_prolong_add(mg->x[l + 1], mg->side[l + 1], x, s));
-    if (nu_post > 0) CKS(mg_smooth(mg, l, b, x, nu_post));
+    if (nu_post > 0) CKS(mg_smooth(mg, l, b, x, nu_post, MG_RES_COMPUTE));
     return GABP_OK;
 }
 
@@ -1586,7 +1603,7 @@ gabp_status mg_vcycle(mg_ctx *mg, int levels, int nu_pre, int nu_post, const dou
     CKS(set_dev(mg->dev));
     const int last = (levels == 0 ? mg->levels : levels) - 1;
     for (auto *c : mg->lv) CK(cudaMemsetAsync(&c->dstat[0].flags, 0, sizeof(unsigned), mg->stream));
-    CKS(mg_cycle(mg, 0, last, nu_pre, nu_post, b, x));
+    CKS(mg_cycle(mg, 0, last, nu_pre, nu_post, b, x, MG_RES_COMPUTE));
     return mg_check_flags(mg);
 }
 
@@ -1609,10 +1626,11 @@ gabp_status mg_solve(mg_ctx *mg, const double *b, double *x, double tol, int max
     gabp_status st = bn == 0.0 ? GABP_OK : GABP_E_NOT_CONVERGED;
     for (auto *lc : mg->lv) CK(cudaMemsetAsync(&lc->dstat[0].flags, 0, sizeof(unsigned), s));
     while (st == GABP_E_NOT_CONVERGED && c < max_cycles) {
-        CKS(mg_cycle(mg, 0, mg->levels - 1, nu_pre, nu_post, b, x));
+        // the first cycle starts from x = 0; later ones reuse the check's residual of the same x
+        CKS(mg_cycle(mg, 0, mg->levels - 1, nu_pre, nu_post, b, x, c == 0 ? MG_RES_XZERO : MG_RES_READY));
         ++c;
         CK(cudaMemsetAsync(mg->dstat, 0, sizeof(DevStatus), s));
-        CK(launch_residual(f->L, f->a64, f->diag64, b, x, nullptr, mg->dstat, s));
+        CK(launch_residual(f->L, f->a64, f->diag64, b, x, f->bres, mg->dstat, s));
         CK(cudaMemcpyAsync(mg->hstat, mg->dstat, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
         rr = bits_to_double(mg->hstat->rmax) / bn;

@@ -366,57 +366,95 @@ __device__ __forceinline__ void reduce_and_publish(double rmax, double bmax, boo
     }
 }
 
-template <int K>
-__device__ __forceinline__ double residual_row(int i, size_t nn, const StencilParams &sp,
-                                               const double *__restrict__ a64,
-                                               const double *__restrict__ diag64,
-                                               const double *__restrict__ b,
-                                               const double *__restrict__ x)
+// Block maxima of |r| and |b| as bit patterns of non-negative doubles (their
+// order is the unsigned integer order), so the comparisons run on the integer
+// pipe; one atomicMax per block.
+__device__ __forceinline__ void reduce_and_publish_bits(unsigned long long rbits,
+                                                        unsigned long long bbits, bool nan,
+                                                        DevStatus *st)
 {
-    double acc = b[i] - diag64[i] * x[i];
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-        const double ae = a64[(size_t)k * nn + i];
-        if (ae != 0.0) acc += ae * x[i + sp.off[k]];
+    __shared__ unsigned long long sr[32], sb[32];
+    __shared__ int snan;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (threadIdx.x == 0) snan = 0;
+    __syncthreads();
+    for (int o = 16; o > 0; o >>= 1) {
+        rbits = max(rbits, __shfl_xor_sync(0xffffffffu, rbits, o));
+        bbits = max(bbits, __shfl_xor_sync(0xffffffffu, bbits, o));
     }
-    return acc;
+    if (nan) snan = 1;
+    if (lane == 0) {
+        sr[wid] = rbits;
+        sb[wid] = bbits;
+    }
+    __syncthreads();
+    if (wid == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        rbits = lane < nw ? sr[lane] : 0ull;
+        bbits = lane < nw ? sb[lane] : 0ull;
+        for (int o = 16; o > 0; o >>= 1) {
+            rbits = max(rbits, __shfl_xor_sync(0xffffffffu, rbits, o));
+            bbits = max(bbits, __shfl_xor_sync(0xffffffffu, bbits, o));
+        }
+        if (lane == 0) {
+            atomicMax(&st->rmax, rbits);
+            atomicMax(&st->bmax, bbits);
+            if (snan) atomicOr(&st->flags, FLAG_NAN);
+        }
+    }
 }
 
-// Four rows per thread per step (independent loads in flight), grid-strided.
+__device__ __forceinline__ unsigned long long abs_bits(double v)
+{
+    return (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull;
+}
+
+// Two rows per thread per step, grid-strided; every load of both rows (the
+// coefficients and the x gathers at clamped, always in-bounds indices) is
+// issued before the arithmetic, so no gather waits for its coefficient.  A
+// padded slot has a = 0 and contributes 0 * x (x finite).
 template <int K>
 __global__ void __launch_bounds__(256) k_residual_stencil(
     int n, StencilParams sp, const double *__restrict__ a64, const double *__restrict__ diag64,
     const double *__restrict__ b, const double *__restrict__ x, double *__restrict__ r,
     DevStatus *st)
 {
-    double rmax = 0.0, bmax = 0.0;
+    constexpr int KK = K > 0 ? K : 1;
+    unsigned long long rbits = 0ull, bbits = 0ull;
     bool nan = false;
     const size_t nn = (size_t)n;
     const int stride = gridDim.x * blockDim.x;
-    for (int i0 = blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += 4 * stride) {
-        double acc[4], bb[4];
+    for (int i0 = blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += 2 * stride) {
+        double av[2][KK], xv[2][KK], bi[2], di[2], xi[2];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int i = i0 + u * stride;
-            if (i < n) {
-                acc[u] = residual_row<K>(i, nn, sp, a64, diag64, b, x);
-                bb[u] = b[i];
-            } else {
-                acc[u] = 0.0;
-                bb[u] = 0.0;
+        for (int u = 0; u < 2; ++u) {
+            const int i = min(i0 + u * stride, n - 1);
+            bi[u] = b[i];
+            di[u] = diag64[i];
+            xi[u] = x[i];
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                int s = i + sp.off[k];
+                s = s < 0 ? 0 : (s >= n ? n - 1 : s);
+                av[u][k] = a64[(size_t)k * nn + i];
+                xv[u][k] = x[s];
             }
         }
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < 2; ++u) {
             const int i = i0 + u * stride;
-            if (i < n && r) r[i] = acc[u];
-            const double v = fabs(acc[u]);
-            if (v != v) nan = true;
-            else rmax = fmax(rmax, v);
-            bmax = fmax(bmax, fabs(bb[u]));
+            if (i >= n) continue;
+            double acc = fma(-di[u], xi[u], bi[u]);
+#pragma unroll
+            for (int k = 0; k < K; ++k) acc = fma(av[u][k], xv[u][k], acc);
+            if (r) r[i] = acc;
+            const unsigned long long ab = abs_bits(acc);
+            if (ab > 0x7ff0000000000000ull) nan = true;
+            else rbits = max(rbits, ab);
+            bbits = max(bbits, abs_bits(bi[u]));
         }
     }
-    reduce_and_publish(rmax, bmax, nan, st);
+    reduce_and_publish_bits(rbits, bbits, nan, st);
 }
 
 __global__ void __launch_bounds__(256) k_residual_csr(
