@@ -147,8 +147,11 @@ void gabp_destroy(gabp_ctx *ctx);
  *    messages are kept by sender, class by class, so a sweep streams every
  *    message once; gabp_info.parity_layout reports it.  Other colourings run
  *    on the slot layout.
- * Precision messages are not frozen under schedules 1 and 2; the batched
- * solver always floods.
+ * Under schedule 2 the precision messages freeze as under the flood schedule
+ * (freeze_lambda): once both families' messages stop changing, the lines'
+ * elimination multipliers are stored and later sweeps move only the mean
+ * messages.  They are not frozen under schedule 1; the batched solver always
+ * floods.
  */
 gabp_status gabp_set_schedule(gabp_ctx *ctx, int schedule, const int32_t *color, int *ncolors);
 
