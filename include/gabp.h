@@ -117,6 +117,16 @@ gabp_status gabp_setup(int32_t n, int64_t nnz, const int64_t *indptr, const int3
  * depends on parameters (the differentiable solve). */
 gabp_status gabp_set_values(gabp_ctx *ctx, const double *data);
 
+/* gabp_set_values with the values in DEVICE memory (nnz doubles on the
+ * context's device, setup slot order, owned by the caller): the coefficient
+ * arrays are rebuilt by kernels from the values where they lie, so a caller
+ * that assembles A on the GPU (the differentiable solve) has no host round
+ * trip for them.  The library still copies the values to the host once per
+ * call to validate them (same checks and errors as gabp_set_values) and to
+ * keep its host-side consumers (line couplings, the multigrid coarse solve)
+ * in step.  Zeroes the messages. */
+gabp_status gabp_set_values_device(gabp_ctx *ctx, const double *data);
+
 /* Releases the context and its device memory (NULL is ignored). */
 void gabp_destroy(gabp_ctx *ctx);
 

@@ -77,6 +77,7 @@ def load() -> ctypes.CDLL:
         "gabp_launch_count": (ctypes.c_ulonglong, []),
         "gabp_setup": (I, [ctypes.c_int32, I64, P, P, P, ctypes.POINTER(Options), P, ctypes.POINTER(P)]),
         "gabp_set_values": (I, [P, P]),
+        "gabp_set_values_device": (I, [P, P]),
         "gabp_destroy": (None, [P]),
         "gabp_reset": (I, [P]),
         "gabp_set_schedule": (I, [P, I, P, PI]),
@@ -228,6 +229,17 @@ class GabpSolver:
         return {"LH": out[0], "MH": out[1], "LV": out[2], "MV": out[3]}
 
     def set_values(self, data) -> None:
+        """New matrix values on the same pattern (setup slot order): a numpy
+        array or a host tensor goes through ``gabp_set_values``, a CUDA tensor
+        through ``gabp_set_values_device`` (no host assembly)."""
+        torch = _torch()
+        if isinstance(data, torch.Tensor) and data.is_cuda:
+            t = data.detach().to(torch.float64).contiguous()
+            assert t.shape == (self.nnz,)
+            _check(load().gabp_set_values_device(self._h, _dev_vec(t, self.nnz, "values")))
+            return
+        if isinstance(data, torch.Tensor):
+            data = data.detach().cpu().numpy()
         data = np.ascontiguousarray(data, dtype=np.float64)
         assert data.shape == (self.nnz,)
         _check(load().gabp_set_values(self._h, data.ctypes.data))

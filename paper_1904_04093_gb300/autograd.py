@@ -24,7 +24,8 @@ class GabpSolveFunction(torch.autograd.Function):
 
     @staticmethod
     def forward(ctx, values, b, solver, tol, max_iter):
-        solver.set_values(values.detach().double().cpu().numpy())
+        # CUDA values stay on the device (gabp_set_values_device)
+        solver.set_values(values.detach())
         x, it, rr, st = solver.solve(b.detach().contiguous(), tol, max_iter)
         if st != OK:
             raise GabpError(st, f"forward solve stopped with status {st} (rr={rr:.3e})")

@@ -85,6 +85,7 @@ struct gabp_ctx {
     void *aT = nullptr;                                 // transposed mean coefficients
     double *aT64 = nullptr;
     int64_t *slotmap = nullptr;                         // caller slot -> layout slot (-1: none)
+    int64_t *diagpos = nullptr;                         // entry index of each row's diagonal (lazy)
     int64_t *d_indptr = nullptr;                        // caller CSR on device (edge gradient)
     int *d_indices = nullptr;
     // state
@@ -946,19 +947,15 @@ gabp_status gabp_setup(int32_t n, int64_t nnz, const int64_t *indptr, const int3
     return GABP_OK;
 }
 
-gabp_status gabp_set_values(gabp_ctx *ctx, const double *data)
+static gabp_status setup_lines(gabp_ctx *ctx);
+
+namespace {
+
+// After new matrix values: the edge count, the derived coefficient copies
+// (transposed, parity-class, line schedule) and zero messages.
+gabp_status after_new_values(gabp_ctx *ctx)
 {
-    if (!ctx || (!data && ctx->nnz > 0)) return fail(GABP_E_INVALID_ARG, "null argument");
-    CKS(set_dev(ctx->dev));
-    CKS(validate_csr(ctx->n, ctx->nnz, ctx->h_indptr.data(), ctx->h_indices.data(), data));
-    HostLayout H;
-    if (ctx->L.kind == GABP_LAYOUT_STENCIL)
-        build_stencil(ctx->n, ctx->h_indptr.data(), ctx->h_indices.data(), data, ctx->L.sp, H);
-    else
-        build_csr(ctx->n, ctx->h_indptr.data(), ctx->h_indices.data(), data, H);
-    CK(cudaStreamSynchronize(ctx->stream));
-    CKS(upload_coeffs(ctx, H, false));
-    ctx->h_data.assign(data, data + ctx->nnz);
+    const double *data = ctx->h_data.data();
     int64_t nz = 0;
     for (int32_t r = 0; r < ctx->n; ++r)
         for (int64_t p = ctx->h_indptr[r]; p < ctx->h_indptr[r + 1]; ++p)
@@ -973,9 +970,53 @@ gabp_status gabp_set_values(gabp_ctx *ctx, const double *data)
         CK(launch_parity_convert(ctx->pg, ctx->prec, 1, ctx->c, ctx->pc, ctx->stream));
         if (ctx->paT) CKS(ensure_parity_transpose(ctx));
     }
+    if (ctx->lines_m > 0) CKS(setup_lines(ctx));  // couplings of the line regions
     CKS(zero_messages(ctx, true, true));
     CK(cudaStreamSynchronize(ctx->stream));
     return GABP_OK;
+}
+
+}  // namespace
+
+gabp_status gabp_set_values(gabp_ctx *ctx, const double *data)
+{
+    if (!ctx || (!data && ctx->nnz > 0)) return fail(GABP_E_INVALID_ARG, "null argument");
+    CKS(set_dev(ctx->dev));
+    CKS(validate_csr(ctx->n, ctx->nnz, ctx->h_indptr.data(), ctx->h_indices.data(), data));
+    HostLayout H;
+    if (ctx->L.kind == GABP_LAYOUT_STENCIL)
+        build_stencil(ctx->n, ctx->h_indptr.data(), ctx->h_indices.data(), data, ctx->L.sp, H);
+    else
+        build_csr(ctx->n, ctx->h_indptr.data(), ctx->h_indices.data(), data, H);
+    CK(cudaStreamSynchronize(ctx->stream));
+    CKS(upload_coeffs(ctx, H, false));
+    ctx->h_data.assign(data, data + ctx->nnz);
+    return after_new_values(ctx);
+}
+
+gabp_status gabp_set_values_device(gabp_ctx *ctx, const double *data)
+{
+    if (!ctx || (!data && ctx->nnz > 0)) return fail(GABP_E_INVALID_ARG, "null argument");
+    CKS(set_dev(ctx->dev));
+    // the host copy keeps the host-side consumers (line couplings, multigrid
+    // coarse solve, validation) in step with the device values
+    std::vector<double> h((size_t)ctx->nnz);
+    if (ctx->nnz) {
+        CK(cudaMemcpyAsync(h.data(), data, (size_t)ctx->nnz * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+    }
+    CKS(validate_csr(ctx->n, ctx->nnz, ctx->h_indptr.data(), ctx->h_indices.data(), h.data()));
+    if (!ctx->diagpos) {
+        std::vector<int64_t> dp((size_t)ctx->n, 0);
+        for (int32_t r = 0; r < ctx->n; ++r)
+            for (int64_t p = ctx->h_indptr[r]; p < ctx->h_indptr[r + 1]; ++p)
+                if (ctx->h_indices[p] == r) dp[r] = p;
+        CKS(upload(ctx, (void **)&ctx->diagpos, dp.data(), dp.size() * sizeof(int64_t)));
+    }
+    CK(launch_coeffs_from_values(ctx->L, ctx->prec, ctx->nnz, ctx->slotmap, ctx->diagpos, data,
+                                 ctx->a64, ctx->diag64, ctx->a, ctx->c, ctx->diagT, ctx->stream));
+    ctx->h_data.swap(h);
+    return after_new_values(ctx);
 }
 
 void gabp_destroy(gabp_ctx *ctx)

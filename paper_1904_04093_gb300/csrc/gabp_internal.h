@@ -166,6 +166,13 @@ cudaError_t launch_line_mean(int prec, int m, const void *aF, const void *aB, co
 cudaError_t prepare_line_kernels(int prec, int m);
 cudaError_t launch_transpose(int prec, int m, const void *in, void *out, cudaStream_t s);
 cudaError_t launch_to_double(int prec, const void *in, double *out, int64_t n, cudaStream_t s);
+// a64, diag64 (and a, c, diagT in the message precision) from CSR values on
+// the device: slotmap[p] = layout slot of entry p (-1 on the diagonal),
+// diagpos[r] = entry index of the diagonal of row r
+cudaError_t launch_coeffs_from_values(const DevLayout &L, int prec, int64_t nnz,
+                                      const int64_t *slotmap, const int64_t *diagpos,
+                                      const double *data, double *a64, double *diag64, void *a,
+                                      void *c, void *diagT, cudaStream_t s);
 // a^T[e] = a[rev(e)] (mean-message coefficients of the transposed system)
 cudaError_t launch_transpose_coeffs(const DevLayout &L, int prec, const void *a, void *aT,
                                     cudaStream_t s);

@@ -24,6 +24,7 @@
 // Padded or explicit-zero slots have a_e = 0 and carry the zero message.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 
 #include "gabp_internal.h"
@@ -674,6 +675,50 @@ __global__ void k_transpose_csr(int64_t slots, const int *__restrict__ rev, cons
         aT[e] = a[rev[e]];
 }
 
+// Coefficients from matrix values held on the device (gabp_set_values_device):
+// a64[e] = -A_rs for every stored off-diagonal entry p of row r (slotmap[p] =
+// e), diag64[r] = A_rr (diagpos[r] = p of the diagonal).  Slots no entry maps
+// to (pattern symmetrisation, stencil padding) keep their zero.
+__global__ void k_values_scatter(int64_t nnz, int n, const int64_t *__restrict__ slotmap,
+                                 const int64_t *__restrict__ diagpos,
+                                 const double *__restrict__ data, double *__restrict__ a64,
+                                 double *__restrict__ diag64)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nnz; p += stride) {
+        const int64_t e = slotmap[p];
+        if (e >= 0) a64[e] = -data[p];
+    }
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += stride)
+        diag64[r] = data[diagpos[r]];
+}
+
+// c_e = -A_rs A_sr = -a_e a_{rev e} (in double, then in the message precision
+// with a and diag).
+template <typename T>
+__global__ void k_coeffs_c(const DevLayout L, const double *__restrict__ a64,
+                           const double *__restrict__ diag64, T *__restrict__ a, T *__restrict__ c,
+                           T *__restrict__ diagT)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < L.slots; e += stride) {
+        double ar = 0.0;
+        if (L.kind == GABP_LAYOUT_STENCIL) {
+            const int k = (int)(e / L.n), r = (int)(e - (int64_t)k * L.n);
+            const int s = r + L.sp.off[k];
+            if (s >= 0 && s < L.n) ar = a64[(size_t)L.sp.krev[k] * L.n + s];
+        } else {
+            ar = a64[L.rev[e]];
+        }
+        const double ae = a64[e];
+        c[e] = (T)(-ae * ar);
+        if (a != (const T *)a64) a[e] = (T)ae;
+    }
+    if (diagT != (const T *)diag64)
+        for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < L.n; r += stride)
+            diagT[r] = (T)diag64[r];
+}
+
 inline int grid_for(int64_t n, int block, int cap = 152 * 32)
 {
     int64_t g = (n + block - 1) / block;
@@ -905,6 +950,23 @@ cudaError_t launch_dense_gemv(const double *M, const double *x, double *y, int n
     k_dense_gemv<<<(n + rows_per_block - 1) / rows_per_block, 32 * rows_per_block, 0, s>>>(M, x,
                                                                                           y, n);
     count_launches(s, 1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_coeffs_from_values(const DevLayout &L, int prec, int64_t nnz,
+                                      const int64_t *slotmap, const int64_t *diagpos,
+                                      const double *data, double *a64, double *diag64, void *a,
+                                      void *c, void *diagT, cudaStream_t s)
+{
+    if (L.n == 0) return cudaSuccess;
+    k_values_scatter<<<grid_for(std::max<int64_t>(nnz, L.n), 256), 256, 0, s>>>(nnz, L.n, slotmap, diagpos,
+                                                                              data, a64, diag64);
+    const int grid = grid_for(std::max<int64_t>(L.slots, L.n), 256);
+    if (prec == 0)
+        k_coeffs_c<double><<<grid, 256, 0, s>>>(L, a64, diag64, (double *)a, (double *)c, (double *)diagT);
+    else
+        k_coeffs_c<float><<<grid, 256, 0, s>>>(L, a64, diag64, (float *)a, (float *)c, (float *)diagT);
+    count_launches(s, 2);
     return cudaGetLastError();
 }
 

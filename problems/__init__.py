@@ -51,6 +51,8 @@ __all__ = [
     "config_c4_batch",
     "config_c5",
     "lognormal_field",
+    "ConvDiff5ptTorch",
+    "convdiff_5pt_torch",
     "sparse_random_m_matrix",
     "permute_symmetric",
 ]
@@ -438,40 +440,70 @@ def config_c5(m: int = 512, seed: int = 1005, sigma: float = 0.3):
     return theta, b, theta_t
 
 
+class ConvDiff5ptTorch:
+    """Differentiable assembly of ``convdiff_5pt`` values for one grid and flow.
+
+    The CSR pattern and the map from the ``(m, m, 5)`` stencil coefficients to
+    the CSR slots are built once (the pattern is the same for every positive
+    diffusion field); ``values(D)`` then assembles the values from a torch
+    tensor ``D`` of shape ``(m, m)`` on ``D``'s device, differentiably, with no
+    host work.
+    """
+
+    def __init__(self, m: int, hv=(0.0, 0.0), device=None):
+        import torch
+
+        self.m = m
+        self.hv = (float(hv[0]), float(hv[1]))
+        self.pattern = convdiff_5pt(m, None, hv)
+        iy, ix = np.meshgrid(np.arange(m), np.arange(m), indexing="ij")
+        keep = np.empty((m, m, 5), dtype=bool)
+        for k, (dx, dy) in enumerate(_OFF5):
+            keep[:, :, k] = (ix + dx >= 0) & (ix + dx < m) & (iy + dy >= 0) & (iy + dy < m)
+        self._flat = np.flatnonzero(keep.reshape(-1))
+        self._idx = {}
+        if device is not None:
+            self._index(torch.device(device))
+
+    def _index(self, device):
+        import torch
+
+        key = str(device)
+        if key not in self._idx:
+            self._idx[key] = torch.as_tensor(self._flat, device=device)
+        return self._idx[key]
+
+    def values(self, D):
+        import torch
+
+        hvx, hvy = self.hv
+
+        def harm(a, b):
+            return 2.0 * a * b / (a + b)
+
+        Dw = torch.cat([D[:, :1], harm(D[:, 1:], D[:, :-1])], dim=1)
+        De = torch.cat([harm(D[:, :-1], D[:, 1:]), D[:, -1:]], dim=1)
+        Ds = torch.cat([D[:1, :], harm(D[1:, :], D[:-1, :])], dim=0)
+        Dn = torch.cat([harm(D[:-1, :], D[1:, :]), D[-1:, :]], dim=0)
+        coeffs = torch.stack([
+            -Ds - max(hvy, 0.0),
+            -Dw - max(hvx, 0.0),
+            Dw + De + Ds + Dn + abs(hvx) + abs(hvy),
+            -De - max(-hvx, 0.0),
+            -Dn - max(-hvy, 0.0),
+        ], dim=2)
+        return coeffs.reshape(-1)[self._index(D.device)]
+
+
 def convdiff_5pt_torch(m: int, D, hv=(0.0, 0.0)):
     """Differentiable twin of ``convdiff_5pt``: the CSR values as a torch tensor.
 
-    ``D`` is a torch tensor of shape ``(m, m)`` (node diffusion); gradients flow
-    from the returned values to ``D``.  Returns ``(pattern, values)`` where
-    ``pattern`` is the ``CSR`` of ``convdiff_5pt(m, D, hv)`` (the pattern does not
-    depend on positive ``D``) and ``values`` its data in the same slot order.
-    Used for the differentiable-solve workload ``kappa = exp(theta)``.
+    ``D`` is a torch tensor of shape ``(m, m)`` (positive node diffusion);
+    gradients flow from the returned values to ``D``.  Returns ``(pattern,
+    values)`` where ``pattern`` is the ``CSR`` of ``convdiff_5pt(m, D, hv)``
+    and ``values`` its data in the same slot order, on ``D``'s device.  Used
+    for the differentiable-solve workload ``kappa = exp(theta)``; for repeated
+    assembly on one grid, ``ConvDiff5ptTorch`` builds the pattern once.
     """
-    import torch
-
-    hvx, hvy = float(hv[0]), float(hv[1])
-    Dd = D.detach().cpu().numpy().astype(np.float64)
-    pattern = convdiff_5pt(m, Dd, hv)
-
-    def harm(a, b):
-        return 2.0 * a * b / (a + b)
-
-    Dw = torch.cat([D[:, :1], harm(D[:, 1:], D[:, :-1])], dim=1)
-    De = torch.cat([harm(D[:, :-1], D[:, 1:]), D[:, -1:]], dim=1)
-    Ds = torch.cat([D[:1, :], harm(D[1:, :], D[:-1, :])], dim=0)
-    Dn = torch.cat([harm(D[:-1, :], D[1:, :]), D[-1:, :]], dim=0)
-    coeffs = torch.stack([
-        -Ds - max(hvy, 0.0),
-        -Dw - max(hvx, 0.0),
-        Dw + De + Ds + Dn + abs(hvx) + abs(hvy),
-        -De - max(-hvx, 0.0),
-        -Dn - max(-hvy, 0.0),
-    ], dim=2)
-    iy, ix = np.meshgrid(np.arange(m), np.arange(m), indexing="ij")
-    keep = np.empty((m, m, 5), dtype=bool)
-    for k, (dx, dy) in enumerate(_OFF5):
-        inside = (ix + dx >= 0) & (ix + dx < m) & (iy + dy >= 0) & (iy + dy < m)
-        keep[:, :, k] = True if (dx == 0 and dy == 0) else inside & (coeffs[:, :, k].detach().cpu().numpy() != 0.0)
-    flat_idx = torch.as_tensor(np.flatnonzero(keep.reshape(-1)), device=D.device)
-    values = coeffs.reshape(-1)[flat_idx]
-    return pattern, values
+    asm = ConvDiff5ptTorch(m, hv)
+    return asm.pattern, asm.values(D)
