@@ -707,29 +707,36 @@ def run_adjoint(args):
     xt, _, _, _ = g.GabpSolver(P.convdiff_5pt(m, np.exp(theta_t), hv), "fp32_ir").solve(bd, 1e-10, 200000)
     # the matrix is assembled from theta on the GPU (pattern and slot map built once)
     asm = P.ConvDiff5ptTorch(m, hv, device="cuda")
-    solver = g.GabpSolver(asm.pattern, "fp32_ir")
     theta_d = torch.as_tensor(theta, device="cuda")
+    per = {}
+    for schedule in ("flood", "lines"):
+        solver = g.GabpSolver(asm.pattern, "fp32_ir")
+        if schedule == "lines":
+            solver.set_schedule("lines")
 
-    def step():
-        th = theta_d.clone().requires_grad_(True)
-        x = gabp_solve(asm.values(torch.exp(th)), bd, solver, tol=1e-10)
-        L = ((x - xt) ** 2).sum()
-        L.backward()
-        return L.detach()
+        def step():
+            th = theta_d.clone().requires_grad_(True)
+            x = gabp_solve(asm.values(torch.exp(th)), bd, solver, tol=1e-10)
+            L = ((x - xt) ** 2).sum()
+            L.backward()
+            return L.detach()
 
-    for _ in range(max(3, args.warmup)):
-        step()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        Ld = step()
-    torch.cuda.synchronize()
-    ms = (time.perf_counter() - t0) * 1e3 / args.steps
-    L = float(Ld)
+        for _ in range(max(3, args.warmup)):
+            step()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            Ld = step()
+        torch.cuda.synchronize()
+        per[schedule] = {"ms_per_step": (time.perf_counter() - t0) * 1e3 / args.steps, "loss": float(Ld)}
+        solver.close()
+    ms = per["flood"]["ms_per_step"]
+    L = per["flood"]["loss"]
     line = {"metric": "differentiable solve: forward + adjoint to 1e-10", "value": ms,
             "unit": "ms/step", "higher_is_better": False, "steps": args.steps,
             "dtype": "f32 messages + f64 refinement", "data": "synthetic",
             "config": {"workload": f"convdiff2d_5pt_kappa_exp_theta_{m}x{m}", "loss": L},
+            "schedules": per,
             "note": "host wall clock of the whole step: GPU assembly of A(theta), forward solve, "
                     "adjoint solve, edge gradient and the chain to theta"}
     print(json.dumps(line), flush=True)

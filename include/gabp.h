@@ -149,8 +149,9 @@ void gabp_destroy(gabp_ctx *ctx);
  *    region (regions of one family share no node), each by an exact
  *    tridiagonal solve; the beliefs are the column regions' solutions.
  *    Needs n = m^2 and every edge inside a row or a column (5-point grids),
- *    GABP_E_INVALID_ARG otherwise.  The transposed solve is not available
- *    under this schedule; gabp_get_line_state reads its messages.
+ *    GABP_E_INVALID_ARG otherwise.  The transposed solve runs the same
+ *    schedule on A^T (line couplings sub_i, sup_i become sup_{i-1},
+ *    sub_{i+1}); gabp_get_line_state reads the messages.
  *    On an m x m grid stencil (m >= 3, couplings inside the 3 x 3
  *    neighbourhood) whose colours are unions of the parity classes
  *    (x mod 2, y mod 2) -- red-black and the 4-colour grid colouring -- the

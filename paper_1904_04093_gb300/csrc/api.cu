@@ -114,6 +114,7 @@ struct gabp_ctx {
     // reads (LHt, MHt) and writes (LVt, MVt); scratch for very long lines
     int lines_m = 0;
     void *lsubH = nullptr, *lsupH = nullptr, *lsubV = nullptr, *lsupV = nullptr;
+    void *lsubHT = nullptr, *lsupHT = nullptr, *lsubVT = nullptr, *lsupVT = nullptr;  // of A^T (lazy)
     void *ldiagT = nullptr, *lbT = nullptr;
     void *LH = nullptr, *MH = nullptr, *LV = nullptr, *MV = nullptr;
     void *LHt = nullptr, *MHt = nullptr, *LVt = nullptr, *MVt = nullptr;
@@ -451,6 +452,9 @@ int block_of(const gabp_ctx *ctx) { return ctx->opt.block_size > 0 ? ctx->opt.bl
 cudaError_t sweep_once(gabp_ctx *ctx, bool transposed, double *x, cudaStream_t s)
 {
     const int c0 = ctx->cur, c1 = c0 ^ 1;
+    // line couplings of A, or of A^T for the transposed solve
+    void *lsH = transposed ? ctx->lsubHT : ctx->lsubH, *luH = transposed ? ctx->lsupHT : ctx->lsupH;
+    void *lsV = transposed ? ctx->lsubVT : ctx->lsubV, *luV = transposed ? ctx->lsupVT : ctx->lsupV;
     if (ctx->lines_m > 0 && ctx->frozen) {
         // frozen precision messages: the mean messages move, rows then columns
         const int m = ctx->lines_m, pr = ctx->prec;
@@ -469,12 +473,12 @@ cudaError_t sweep_once(gabp_ctx *ctx, bool transposed, double *x, cudaStream_t s
         const int m = ctx->lines_m, pr = ctx->prec;
         unsigned *fl = &ctx->dstat[0].flags;
         cudaError_t e;
-        if ((e = launch_line_phase(pr, m, ctx->lsubH, ctx->lsupH, ctx->diagT, ctx->bT, ctx->LV,
+        if ((e = launch_line_phase(pr, m, lsH, luH, ctx->diagT, ctx->bT, ctx->LV,
                                    ctx->MV, ctx->LH, ctx->MH, ctx->lf, ctx->ly, nullptr, 0, fl, s)) != cudaSuccess)
             return e;
         if ((e = launch_transpose(pr, m, ctx->LH, ctx->LHt, s)) != cudaSuccess) return e;
         if ((e = launch_transpose(pr, m, ctx->MH, ctx->MHt, s)) != cudaSuccess) return e;
-        if ((e = launch_line_phase(pr, m, ctx->lsubV, ctx->lsupV, ctx->ldiagT, ctx->lbT, ctx->LHt,
+        if ((e = launch_line_phase(pr, m, lsV, luV, ctx->ldiagT, ctx->lbT, ctx->LHt,
                                    ctx->MHt, ctx->LVt, ctx->MVt, ctx->lf, ctx->ly, x, 1, fl, s)) != cudaSuccess)
             return e;
         if ((e = launch_transpose(pr, m, ctx->LVt, ctx->LV, s)) != cudaSuccess) return e;
@@ -643,7 +647,7 @@ gabp_status freeze(gabp_ctx *ctx, bool transposed)
 
 // Line schedule: the multipliers of both families from the current
 // precision messages (the row family sees LV, the column family LH).
-gabp_status freeze_lines(gabp_ctx *ctx)
+gabp_status freeze_lines(gabp_ctx *ctx, bool transposed)
 {
     const int m = ctx->lines_m, pr = ctx->prec;
     const size_t nb = (size_t)ctx->n * esz(pr);
@@ -652,18 +656,20 @@ gabp_status freeze_lines(gabp_ctx *ctx)
         if (!*bp) CKS(dalloc(ctx, bp, nb));
     cudaStream_t s = ctx->stream;
     unsigned *fl = &ctx->dstat[0].flags;
-    CK(launch_line_freeze(pr, m, ctx->lsubH, ctx->lsupH, ctx->diagT, ctx->LV, ctx->lf, ctx->ly,
-                          ctx->laFH, ctx->laBH, ctx->lSH, fl, s));
+    CK(launch_line_freeze(pr, m, transposed ? ctx->lsubHT : ctx->lsubH,
+                          transposed ? ctx->lsupHT : ctx->lsupH, ctx->diagT, ctx->LV, ctx->lf,
+                          ctx->ly, ctx->laFH, ctx->laBH, ctx->lSH, fl, s));
     CK(launch_transpose(pr, m, ctx->LH, ctx->LHt, s));
-    CK(launch_line_freeze(pr, m, ctx->lsubV, ctx->lsupV, ctx->ldiagT, ctx->LHt, ctx->lf, ctx->ly,
-                          ctx->laFV, ctx->laBV, ctx->lSV, fl, s));
+    CK(launch_line_freeze(pr, m, transposed ? ctx->lsubVT : ctx->lsubV,
+                          transposed ? ctx->lsupVT : ctx->lsupV, ctx->ldiagT, ctx->LHt, ctx->lf,
+                          ctx->ly, ctx->laFV, ctx->laBV, ctx->lSV, fl, s));
     ctx->frozen = true;
     return GABP_OK;
 }
 
 // Line schedule: freezes once the precision messages of both families moved
 // by at most `rel` times their largest value since the previous check.
-gabp_status maybe_freeze_lines(gabp_ctx *ctx, double rel)
+gabp_status maybe_freeze_lines(gabp_ctx *ctx, double rel, bool transposed)
 {
     const int64_t n = ctx->n;
     const size_t nb = (size_t)n * esz(ctx->prec);
@@ -676,7 +682,7 @@ gabp_status maybe_freeze_lines(gabp_ctx *ctx, double rel)
         double dmax = 0.0, lmax = 0.0;
         unsigned fl = 0;
         CKS(read_status(ctx, 2, &dmax, &lmax, &fl));
-        if (!(fl & FLAG_NAN) && dmax <= rel * lmax) return freeze_lines(ctx);
+        if (!(fl & FLAG_NAN) && dmax <= rel * lmax) return freeze_lines(ctx, transposed);
     }
     CK(cudaMemcpyAsync(ctx->lprevH, ctx->LH, nb, cudaMemcpyDeviceToDevice, ctx->stream));
     CK(cudaMemcpyAsync(ctx->lprevV, ctx->LV, nb, cudaMemcpyDeviceToDevice, ctx->stream));
@@ -689,7 +695,7 @@ gabp_status maybe_freeze_lines(gabp_ctx *ctx, double rel)
 gabp_status maybe_freeze(gabp_ctx *ctx, bool transposed)
 {
     if (ctx->frozen) return GABP_OK;
-    if (ctx->lines_m > 0) return maybe_freeze_lines(ctx, ctx->prec == 0 ? 1e-14 : 1e-6);
+    if (ctx->lines_m > 0) return maybe_freeze_lines(ctx, ctx->prec == 0 ? 1e-14 : 1e-6, transposed);
     const double rel = ctx->prec == 0 ? 1e-14 : 1e-6;
     CK(cudaMemsetAsync(&ctx->dstat[2], 0, sizeof(DevStatus), ctx->stream));
     CK(launch_lambda_change(ctx->L.slots, ctx->prec, ctx->Lm[ctx->cur ^ 1], ctx->Lm[ctx->cur],
@@ -970,7 +976,15 @@ gabp_status after_new_values(gabp_ctx *ctx)
         CK(launch_parity_convert(ctx->pg, ctx->prec, 1, ctx->c, ctx->pc, ctx->stream));
         if (ctx->paT) CKS(ensure_parity_transpose(ctx));
     }
-    if (ctx->lines_m > 0) CKS(setup_lines(ctx));  // couplings of the line regions
+    if (ctx->lines_m > 0) {
+        // couplings of the line regions: from the stencil layout on the device, else on the host
+        if (ctx->L.kind == GABP_LAYOUT_STENCIL)
+            CK(launch_line_couplings_from_stencil(ctx->prec, ctx->lines_m, ctx->L.sp, ctx->a64,
+                                                  ctx->diag64, ctx->lsubH, ctx->lsupH, ctx->lsubV,
+                                                  ctx->lsupV, ctx->ldiagT, ctx->stream));
+        else
+            CKS(setup_lines(ctx));
+    }
     CKS(zero_messages(ctx, true, true));
     CK(cudaStreamSynchronize(ctx->stream));
     return GABP_OK;
@@ -1336,8 +1350,18 @@ gabp_status gabp_solve_transpose(gabp_ctx *ctx, const double *g, double *lam, do
     if (!ctx || max_iter < 0 || !(tol >= 0.0) || ((!g || !lam) && ctx->n > 0))
         return fail(GABP_E_INVALID_ARG, "bad argument");
     CKS(set_dev(ctx->dev));
-    if (ctx->lines_m > 0) return fail(GABP_E_INVALID_ARG, "the transposed solve floods or colours; select one of those schedules");
     CKS(ensure_transpose(ctx));
+    if (ctx->lines_m > 0) {
+        // line couplings of A^T (rebuilt every call: they follow the current values)
+        const size_t nb = (size_t)ctx->n * esz(ctx->prec);
+        void **bufs[] = {&ctx->lsubHT, &ctx->lsupHT, &ctx->lsubVT, &ctx->lsupVT};
+        for (void **bp : bufs)
+            if (!*bp) CKS(dalloc(ctx, bp, nb));
+        CK(launch_line_couplings_transpose(ctx->prec, ctx->lines_m, ctx->lsubH, ctx->lsupH,
+                                           ctx->lsubHT, ctx->lsupHT, ctx->stream));
+        CK(launch_line_couplings_transpose(ctx->prec, ctx->lines_m, ctx->lsubV, ctx->lsupV,
+                                           ctx->lsubVT, ctx->lsupVT, ctx->stream));
+    }
     if (ctx->opt.precision == GABP_FP32_IR) return solve_ir(ctx, g, lam, tol, max_iter, iters, relres, true);
     return solve_plain(ctx, g, lam, tol, max_iter, iters, relres, true);
 }

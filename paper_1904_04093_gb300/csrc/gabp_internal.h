@@ -153,6 +153,15 @@ cudaError_t launch_line_phase(int prec, int m, const void *sub, const void *sup,
                               void *Mown, void *f, void *y, double *x, int x_transposed,
                               unsigned *flags, cudaStream_t s);
 bool line_needs_scratch(int prec, int m);
+// line couplings (rows natural, columns transposed) and the transposed
+// diagonal from the stencil layout of a 5-point m x m grid
+cudaError_t launch_line_couplings_from_stencil(int prec, int m, const StencilParams &sp,
+                                               const double *a64, const double *diag64,
+                                               void *subH, void *supH, void *subV, void *supV,
+                                               void *diagV, cudaStream_t s);
+// couplings of A^T along the same contiguous lines: subT_i = sup_{i-1}, supT_i = sub_{i+1}
+cudaError_t launch_line_couplings_transpose(int prec, int m, const void *sub, const void *sup,
+                                            void *subT, void *supT, cudaStream_t s);
 // frozen precision messages: the line's multipliers aF_i = -sub_i / f_{i-1},
 // aB_i = -sup_i / g_{i+1} and 1 / S_i from the current other-family Loth;
 // then phases that move the mean messages only

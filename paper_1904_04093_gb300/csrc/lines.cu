@@ -40,6 +40,8 @@
 // columns: transposed order), so a line is contiguous.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "gabp_internal.h"
 #include "sweep_row.cuh"
 
@@ -688,6 +690,55 @@ __global__ void __launch_bounds__(256) k_transpose(int m, const T *__restrict__ 
         }
 }
 
+// Couplings of the transposed system along contiguous lines of length m:
+// (A^T)_{i,i-1} = A_{i-1,i}, so subT_i = sup_{i-1} and supT_i = sub_{i+1}
+// (zero past the line ends).
+template <typename T>
+__global__ void k_line_couplings_transpose(int m, int64_t total, const T *__restrict__ sub,
+                                           const T *__restrict__ sup, T *__restrict__ subT,
+                                           T *__restrict__ supT)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < total; p += stride) {
+        const int i = (int)(p % m);
+        subT[p] = i > 0 ? sup[p - 1] : T(0);
+        supT[p] = i + 1 < m ? sub[p + 1] : T(0);
+    }
+}
+
+// Line couplings from the stencil layout's coefficients (a_e = -A_rs at
+// slot k * n + r, offset off[k]): along the rows (natural order) the west and
+// east entries, along the columns (transposed order) the south and north ones
+// and the diagonal.  The matrix is a 5-point grid (checked at setup), so a
+// missing offset or a slot past a line end holds zero.
+template <typename T>
+__global__ void k_line_couplings_from_stencil(int n, int m, StencilParams sp,
+                                              const double *__restrict__ a64,
+                                              const double *__restrict__ diag64,
+                                              T *__restrict__ subH, T *__restrict__ supH,
+                                              T *__restrict__ subV, T *__restrict__ supV,
+                                              T *__restrict__ diagV)
+{
+    int kw = -1, ke = -1, ks = -1, kn = -1;
+    for (int k = 0; k < sp.K; ++k) {
+        if (sp.off[k] == -1) kw = k;
+        if (sp.off[k] == 1) ke = k;
+        if (sp.off[k] == -m) ks = k;
+        if (sp.off[k] == m) kn = k;
+    }
+    const size_t nn = (size_t)n;
+    const int stride = gridDim.x * blockDim.x;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += stride) {
+        const int x = r % m, y = r / m;
+        const size_t t = (size_t)x * m + y;
+        subH[r] = (T)(x > 0 && kw >= 0 ? -a64[kw * nn + r] : 0.0);
+        supH[r] = (T)(x + 1 < m && ke >= 0 ? -a64[ke * nn + r] : 0.0);
+        subV[t] = (T)(y > 0 && ks >= 0 ? -a64[ks * nn + r] : 0.0);
+        supV[t] = (T)(y + 1 < m && kn >= 0 ? -a64[kn * nn + r] : 0.0);
+        diagV[t] = (T)diag64[r];
+    }
+}
+
 // Threads per line: chunks of at least m / 64 (double) or m / 128 (float)
 // elements, rounded up to whole warps.  Long chunks keep the scan's share of
 // the work small; double is bound by the FP64 pipe, not by occupancy.
@@ -848,6 +899,44 @@ cudaError_t launch_line_mean(int prec, int m, const void *aF, const void *aB, co
     if (prec == 0)
         return launch_mean_T<double>(m, aF, aB, sinv, b, Moth, Mown, y, x, x_transposed, s);
     return launch_mean_T<float>(m, aF, aB, sinv, b, Moth, Mown, y, x, x_transposed, s);
+}
+
+cudaError_t launch_line_couplings_from_stencil(int prec, int m, const StencilParams &sp,
+                                               const double *a64, const double *diag64,
+                                               void *subH, void *supH, void *subV, void *supV,
+                                               void *diagV, cudaStream_t s)
+{
+    const int n = m * m;
+    if (n == 0) return cudaSuccess;
+    count_launches(s, 1);
+    const int grid = std::min((n + 255) / 256, 152 * 16);
+    if (prec == 0)
+        k_line_couplings_from_stencil<double><<<grid, 256, 0, s>>>(
+            n, m, sp, a64, diag64, (double *)subH, (double *)supH, (double *)subV, (double *)supV,
+            (double *)diagV);
+    else
+        k_line_couplings_from_stencil<float><<<grid, 256, 0, s>>>(
+            n, m, sp, a64, diag64, (float *)subH, (float *)supH, (float *)subV, (float *)supV,
+            (float *)diagV);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_line_couplings_transpose(int prec, int m, const void *sub, const void *sup,
+                                            void *subT, void *supT, cudaStream_t s)
+{
+    if (m == 0) return cudaSuccess;
+    count_launches(s, 1);
+    const int64_t total = (int64_t)m * m;
+    const int grid = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
+    if (prec == 0)
+        k_line_couplings_transpose<double><<<grid, 256, 0, s>>>(m, total, (const double *)sub,
+                                                               (const double *)sup, (double *)subT,
+                                                               (double *)supT);
+    else
+        k_line_couplings_transpose<float><<<grid, 256, 0, s>>>(m, total, (const float *)sub,
+                                                              (const float *)sup, (float *)subT,
+                                                              (float *)supT);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_transpose(int prec, int m, const void *in, void *out, cudaStream_t s)

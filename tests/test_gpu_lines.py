@@ -218,3 +218,49 @@ def test_long_lines_frozen_sweep_against_oracle(g, long_lines):
     lam, mu, _ = oracle.line_region_update(A, m, b, "col", 4699, after["LH"], after["MH"])
     assert rel(_line_slice(after["MV"], m, "col", 4699), mu) <= 1e-11
     s.close()
+
+
+@pytest.mark.parametrize("freeze", [0, 1])
+@pytest.mark.parametrize("name", ["c1_32", "lognormal_33"])
+def test_line_transposed_solve_matches_oracle(g, name, freeze):
+    """The adjoint solve under the line schedule: line GaBP on A^T (the same
+    grid lines, couplings shifted to sup_{i-1}, sub_{i+1}) against the
+    oracle's line solve of the transposed matrix, with and without frozen
+    precision messages."""
+    A, m = CASES[name]
+    gvec = np.random.default_rng(12).uniform(-1, 1, A.n)
+    ref = oracle.line_solve(A.transpose(), m, gvec, 1e-10, 2000)
+    assert ref["status"] == oracle.OK
+    s = g.GabpSolver(A, "fp64", check_every=1, freeze_lambda=freeze)
+    s.set_schedule("lines")
+    lam, it, rr, st = s.solve_transpose(dev(gvec), 1e-10, 2000)
+    assert st == g.OK and abs(it - ref["iters"]) <= freeze
+    assert rel(host(lam), ref["x"]) <= (1e-10 if freeze == 0 else 1e-9)
+    # and the forward solve on the same context still is the forward one
+    b = np.random.default_rng(13).uniform(-1, 1, A.n)
+    fwd = oracle.line_solve(A, m, b, 1e-10, 2000)
+    x, it2, _, st2 = s.solve(dev(b), 1e-10, 2000)
+    assert st2 == g.OK and abs(it2 - fwd["iters"]) <= freeze
+    assert rel(host(x), fwd["x"]) <= (1e-10 if freeze == 0 else 1e-9)
+
+
+def test_line_differentiable_solve_full_size(g):
+    """Forward and adjoint of the mixed solver under the line schedule at
+    512 x 512: the gradient matches the flood schedule's."""
+    from paper_1904_04093_gb300.autograd import gabp_solve
+    import math
+    m = 512
+    hv = (2.0 * math.cos(0.3), 2.0 * math.sin(0.3))
+    theta, b, _ = P.config_c5(m=m)
+    xt = torch.zeros(m * m, dtype=torch.float64, device="cuda")
+    grads = []
+    for schedule in ("flood", "lines"):
+        asm = P.ConvDiff5ptTorch(m, hv, device="cuda")
+        solver = g.GabpSolver(asm.pattern, "fp32_ir", check_every=10)
+        if schedule == "lines":
+            solver.set_schedule("lines")
+        th = torch.tensor(theta, dtype=torch.float64, device="cuda", requires_grad=True)
+        x = gabp_solve(asm.values(torch.exp(th)), dev(b), solver, tol=1e-10)
+        ((x - xt) ** 2).sum().backward()
+        grads.append(host(th.grad))
+    assert rel(grads[1], grads[0]) <= 1e-7
