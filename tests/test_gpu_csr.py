@@ -201,3 +201,31 @@ def test_fullsize_csr_first_sweeps_elementwise(g, c2, order):
     assert rel(host(m), mm) <= 1e-12
     assert rel(host(lam), oracle.diag_contrib(A, lt)) <= 1e-12
     s.close()
+
+
+@pytest.mark.parametrize("n", [1, 31, 1000])
+def test_csr_without_off_diagonals(g, n):
+    """A diagonal matrix on the CSR layout: no slots at all, every warp's
+    slot range empty; the belief is b / diag after one sweep and the solve
+    converges at once."""
+    d = np.random.default_rng(n).uniform(0.5, 2.0, n)
+    A = P.CSR(n, np.arange(n + 1, dtype=np.int64), np.arange(n, dtype=np.int32), d)
+    b = np.random.default_rng(n + 1).uniform(-1, 1, n)
+    s = g.GabpSolver(A, "fp64", layout="csr", check_every=1)
+    assert s.info()["layout"] == "csr" and s.info()["slots"] == 0
+    x = host(s.sweep(dev(b), 1))
+    np.testing.assert_allclose(x, b / d, rtol=1e-15, atol=0)
+    xs, it, rr, st = s.solve(dev(b), 1e-14, 10)
+    assert st == g.OK and it == 1
+    s.close()
+
+
+def test_csr_single_edge_pair(g):
+    """Two unknowns, one pair of edges (a path of length one: GaBP is exact
+    after diameter + 1 = 2 sweeps, Sec. 2.2)."""
+    M = np.array([[3.0, -1.2], [0.7, 2.0]])
+    A = P.dense_to_csr(M)
+    b = np.array([1.0, -2.0])
+    s = g.GabpSolver(A, "fp64", layout="csr")
+    x = host(s.sweep(dev(b), 2))
+    assert rel(x, np.linalg.solve(M, b)) <= 1e-15

@@ -264,3 +264,24 @@ def test_line_differentiable_solve_full_size(g):
         ((x - xt) ** 2).sum().backward()
         grads.append(host(th.grad))
     assert rel(grads[1], grads[0]) <= 1e-7
+
+
+@pytest.mark.parametrize("m", [1, 2, 3, 5])
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_line_tiny_grids(g, m, precision):
+    """Lines shorter than a warp (one CTA of 32 threads, most chunks empty)
+    and transposes of a single partial tile: sweeps against the oracle, and
+    the solve with frozen precision messages reaches the dense solution."""
+    A = P.convdiff_5pt(m, np.exp(np.random.default_rng(m).normal(0, 0.4, (m, m))), (0.7, -0.4))
+    b = np.random.default_rng(30 + m).uniform(-1, 1, A.n)
+    st = oracle.line_zero_state(A.n)
+    x_o = oracle.line_sweeps(A, m, b, 4, st)
+    s = g.GabpSolver(A, precision)
+    s.set_schedule("lines")
+    x = host(s.sweep(dev(b), 4))
+    assert rel(x, x_o) <= (1e-12 if precision == "fp64" else 1e-5)
+    s2 = g.GabpSolver(A, "fp64" if precision == "fp64" else "fp32_ir", check_every=1, freeze_lambda=1)
+    s2.set_schedule("lines")
+    xs, it, rr, st2 = s2.solve(dev(b), 1e-10, 500)
+    assert st2 == g.OK and rr <= 1e-10
+    assert rel(host(xs), np.linalg.solve(A.to_dense(), b)) <= 1e-9
