@@ -82,44 +82,64 @@ __device__ __forceinline__ T ld_state(const T *p)
 // they are always in bounds and need not wait for a_e; a padded slot
 // (a_e == 0) discards what it loaded.  Returns true on a zero or non-finite
 // denominator.
+// The loads of one row of the stencil flood update (below), held in registers.
+template <typename T, int K>
+struct StencilRow {
+    T ae[K > 0 ? K : 1], ce[K > 0 ? K : 1], ps[K > 0 ? K : 1], bs[K > 0 ? K : 1],
+        lr[K > 0 ? K : 1], mr[K > 0 ? K : 1];
+    T dg, bb, bx, px;
+};
+
 template <typename T, int K, bool kCoherent = false>
-__device__ __forceinline__ bool sweep_row_stencil(
+__device__ __forceinline__ void stencil_row_load(
     int r, int n, const int *off, const int *krev, const T *__restrict__ a,
     const T *__restrict__ c, const T *__restrict__ diag, const T *__restrict__ b,
     const T *__restrict__ Lin, const T *__restrict__ Min, const T *__restrict__ Pin,
-    const T *__restrict__ Bin, T *__restrict__ Lout, T *__restrict__ Mout,
-    T *__restrict__ Pout, T *__restrict__ Bout, double *__restrict__ x)
+    const T *__restrict__ Bin, bool belief, StencilRow<T, K> &R)
 {
     const size_t nn = (size_t)n;
-    T ae[K > 0 ? K : 1], ce[K > 0 ? K : 1], ps[K > 0 ? K : 1], bs[K > 0 ? K : 1],
-        lr[K > 0 ? K : 1], mr[K > 0 ? K : 1];
 #pragma unroll
     for (int k = 0; k < K; ++k) {
         const size_t e = (size_t)k * nn + r;
-        ae[k] = a[e];
-        ce[k] = c[e];
+        R.ae[k] = a[e];
+        R.ce[k] = c[e];
         int s = r + off[k];
         s = s < 0 ? 0 : (s >= n ? n - 1 : s);
         const size_t er = (size_t)krev[k] * nn + s;
-        ps[k] = ld_state<kCoherent>(Pin + s);
-        bs[k] = ld_state<kCoherent>(Bin + s);
-        lr[k] = ld_state<kCoherent>(Lin + er);
-        mr[k] = ld_state<kCoherent>(Min + er);
+        R.ps[k] = ld_state<kCoherent>(Pin + s);
+        R.bs[k] = ld_state<kCoherent>(Bin + s);
+        R.lr[k] = ld_state<kCoherent>(Lin + er);
+        R.mr[k] = ld_state<kCoherent>(Min + er);
     }
-    T pn = diag[r];
-    T bn = ld_state<kCoherent>(b + r);
-    if (x) x[r] = (double)(ld_state<kCoherent>(Bin + r) / ld_state<kCoherent>(Pin + r));
+    R.dg = diag[r];
+    R.bb = ld_state<kCoherent>(b + r);
+    if (belief) {
+        R.bx = ld_state<kCoherent>(Bin + r);
+        R.px = ld_state<kCoherent>(Pin + r);
+    }
+}
+
+template <typename T, int K>
+__device__ __forceinline__ bool stencil_row_update(int r, int n, const StencilRow<T, K> &R,
+                                                   T *__restrict__ Lout, T *__restrict__ Mout,
+                                                   T *__restrict__ Pout, T *__restrict__ Bout,
+                                                   double *__restrict__ x)
+{
+    const size_t nn = (size_t)n;
+    T pn = R.dg;
+    T bn = R.bb;
+    if (x) x[r] = (double)(R.bx / R.px);
     bool bad = false;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
         const size_t e = (size_t)k * nn + r;
         T lam = T(0), mu = T(0);
-        if (nonzero(ae[k])) {
-            const T d = ps[k] - lr[k];
+        if (nonzero(R.ae[k])) {
+            const T d = R.ps[k] - R.lr[k];
             bad |= bad_den(d);
             const T q = fast_rcp(d);
-            lam = ce[k] * q;
-            mu = ae[k] * (bs[k] - mr[k]) * q;
+            lam = R.ce[k] * q;
+            mu = R.ae[k] * (R.bs[k] - R.mr[k]) * q;
         }
         Lout[e] = lam;
         Mout[e] = mu;
@@ -129,6 +149,30 @@ __device__ __forceinline__ bool sweep_row_stencil(
     Pout[r] = pn;
     Bout[r] = bn;
     return bad;
+}
+
+// Flood update of row r in the stencil (per-diagonal) layout: slot k*n + r
+// holds the entry (r, r + off[k]); its reverse edge is slot krev[k]*n + s,
+// s = r + off[k].  With a_e = -A_rs, c_e = -A_rs A_sr and the aggregates
+// P = diag + sum L, B = b + sum M of the previous state:
+//     d = P_s - L[rev],  L' = c / d,  M' = a (B_s - M[rev]) / d,
+// and the belief x_r = B_r / P_r of the previous state (Algorithm 1 forms the
+// belief before the update).  All loads of the row are issued before any
+// arithmetic: the reverse-edge gathers use an index clamped into [0, n), so
+// they are always in bounds and need not wait for a_e; a padded slot
+// (a_e == 0) discards what it loaded.  Returns true on a zero or non-finite
+// denominator.
+template <typename T, int K, bool kCoherent = false>
+__device__ __forceinline__ bool sweep_row_stencil(
+    int r, int n, const int *off, const int *krev, const T *__restrict__ a,
+    const T *__restrict__ c, const T *__restrict__ diag, const T *__restrict__ b,
+    const T *__restrict__ Lin, const T *__restrict__ Min, const T *__restrict__ Pin,
+    const T *__restrict__ Bin, T *__restrict__ Lout, T *__restrict__ Mout,
+    T *__restrict__ Pout, T *__restrict__ Bout, double *__restrict__ x)
+{
+    StencilRow<T, K> R;
+    stencil_row_load<T, K, kCoherent>(r, n, off, krev, a, c, diag, b, Lin, Min, Pin, Bin, x != nullptr, R);
+    return stencil_row_update<T, K>(r, n, R, Lout, Mout, Pout, Bout, x);
 }
 
 // Mean-message update of row r with frozen precision messages (the fixed
