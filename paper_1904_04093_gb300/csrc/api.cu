@@ -123,6 +123,7 @@ struct gabp_ctx {
     // precision messages of the last check (convergence test)
     void *laFH = nullptr, *laBH = nullptr, *lSH = nullptr;
     void *laFV = nullptr, *laBV = nullptr, *lSV = nullptr;
+    void *laFVn = nullptr, *laBVn = nullptr, *lSVn = nullptr;  // the same in natural order
     void *lprevH = nullptr, *lprevV = nullptr;
     bool lprev_valid = false;
     bool frozen = false;         // precision messages frozen (both L and P buffers equal)
@@ -455,6 +456,16 @@ cudaError_t sweep_once(gabp_ctx *ctx, bool transposed, double *x, cudaStream_t s
     // line couplings of A, or of A^T for the transposed solve
     void *lsH = transposed ? ctx->lsubHT : ctx->lsubH, *luH = transposed ? ctx->lsupHT : ctx->lsupH;
     void *lsV = transposed ? ctx->lsubVT : ctx->lsubV, *luV = transposed ? ctx->lsupVT : ctx->lsupV;
+    if (ctx->lines_m > 0 && ctx->frozen && line_cols_natural(ctx->prec, ctx->lines_m)) {
+        // frozen precision messages, both families in the natural order: no transposes
+        const int m = ctx->lines_m, pr = ctx->prec;
+        cudaError_t e;
+        if ((e = launch_line_mean(pr, m, ctx->laFH, ctx->laBH, ctx->lSH, ctx->bT, ctx->MV, ctx->MH,
+                                  ctx->ly, nullptr, 0, s)) != cudaSuccess)
+            return e;
+        return launch_line_mean_cols(pr, m, ctx->laFVn, ctx->laBVn, ctx->lSVn, ctx->bT, ctx->MH,
+                                     ctx->MV, x, s);
+    }
     if (ctx->lines_m > 0 && ctx->frozen) {
         // frozen precision messages: the mean messages move, rows then columns
         const int m = ctx->lines_m, pr = ctx->prec;
@@ -569,7 +580,9 @@ gabp_status run_chunk(gabp_ctx *ctx, int k, bool transposed)
             ctx->graphs.push_back({k, parity, (int)transposed, frozen, exec});
         }
         CK(cudaGraphLaunch(exec, ctx->stream));
-        int per_sweep = ctx->lines_m > 0 ? (ctx->frozen ? 4 : 6) : (ctx->ncolors > 0 ? ctx->ncolors : 1);
+        int per_sweep = ctx->ncolors > 0 ? ctx->ncolors : 1;
+        if (ctx->lines_m > 0)
+            per_sweep = !ctx->frozen ? 6 : (line_cols_natural(ctx->prec, ctx->lines_m) ? 2 : 4);
         if (ctx->parity) {
             per_sweep = 0;
             for (const PhaseClasses &ph : ctx->phases) per_sweep += ph.nq > 0 ? 1 : 0;
@@ -663,6 +676,15 @@ gabp_status freeze_lines(gabp_ctx *ctx, bool transposed)
     CK(launch_line_freeze(pr, m, transposed ? ctx->lsubVT : ctx->lsubV,
                           transposed ? ctx->lsupVT : ctx->lsupV, ctx->ldiagT, ctx->LHt, ctx->lf,
                           ctx->ly, ctx->laFV, ctx->laBV, ctx->lSV, fl, s));
+    if (line_cols_natural(pr, m)) {
+        // the column family's coefficients in natural order, for the transpose-free frozen sweep
+        void **nbufs[] = {&ctx->laFVn, &ctx->laBVn, &ctx->lSVn};
+        for (void **bp : nbufs)
+            if (!*bp) CKS(dalloc(ctx, bp, nb));
+        CK(launch_transpose(pr, m, ctx->laFV, ctx->laFVn, s));
+        CK(launch_transpose(pr, m, ctx->laBV, ctx->laBVn, s));
+        CK(launch_transpose(pr, m, ctx->lSV, ctx->lSVn, s));
+    }
     ctx->frozen = true;
     return GABP_OK;
 }

@@ -168,6 +168,13 @@ cudaError_t launch_line_couplings_transpose(int prec, int m, const void *sub, co
 cudaError_t launch_line_freeze(int prec, int m, const void *sub, const void *sup,
                                const void *diag, const void *Loth, void *f, void *y, void *aF,
                                void *aB, void *sinv, unsigned *flags, cudaStream_t s);
+// the frozen column phase on the natural node order (no transposes): float
+// messages and m <= 2048 only (line_cols_natural); aF, aB, sinv, b, Moth, Mown
+// and x in natural order
+bool line_cols_natural(int prec, int m);
+cudaError_t launch_line_mean_cols(int prec, int m, const void *aF, const void *aB,
+                                  const void *sinv, const void *b, const void *Moth, void *Mown,
+                                  double *x, cudaStream_t s);
 cudaError_t launch_line_mean(int prec, int m, const void *aF, const void *aB, const void *sinv,
                              const void *b, const void *Moth, void *Mown, void *y, double *x,
                              int x_transposed, cudaStream_t s);

@@ -664,6 +664,119 @@ __global__ void __launch_bounds__(kLineMaxThreads) k_line_mean_reg(
     }
 }
 
+// Frozen column phase read and written in the natural node order (no
+// transposes).  A CTA owns kColLines adjacent column lines; thread (warp w,
+// lane l) takes line x0 + l % kColLines and chunk k = (32 / kColLines) w +
+// l / kColLines of C consecutive rows y (node y m + x).  A warp instruction
+// then touches row segments of kColLines adjacent columns.  The chunk maps of
+// a line are scanned across its lanes (shuffles by multiples of kColLines),
+// then across the warps (one thread per line and direction).  Float
+// messages, lines of at most 128 C rows.
+constexpr int kColLines = 8;  // 8 adjacent columns: 32-byte row segments (4 lines measured slower)
+template <typename T, int C>
+__global__ void __launch_bounds__(1024, 1) k_line_mean_cols(
+    int m, const T *__restrict__ aF, const T *__restrict__ aB, const T *__restrict__ sinv,
+    const T *__restrict__ b, const T *__restrict__ Moth, T *__restrict__ Mown,
+    double *__restrict__ x)
+{
+    constexpr int QW = 32 / kColLines;  // chunks of each line per warp
+    __shared__ T wF[32][kColLines][2], wB[32][kColLines][2], yinF[32][kColLines],
+        yinB[32][kColLines];
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, NW = blockDim.x >> 5;
+    const int li = lane % kColLines, q = lane / kColLines;
+    const int xc = blockIdx.x * kColLines + li;
+    const int lo = (QW * w + q) * C;
+    const int n = xc < m ? max(0, min(C, m - lo)) : 0;
+    T r[C], a[C], c[C];
+#pragma unroll
+    for (int j = 0; j < C; ++j) {
+        if (j < n) {
+            const size_t idx = (size_t)(lo + j) * m + xc;
+            r[j] = b[idx] + Moth[idx];
+            a[j] = aF[idx];
+            c[j] = aB[idx];
+        } else {  // identity steps
+            r[j] = T(0);
+            a[j] = T(1);
+            c[j] = T(1);
+        }
+    }
+    // forward map y_{hi-1} = fa y_{lo-1} + fb; backward map y_lo = ba y_hi + bb,
+    // composed in ascending order on the right
+    T fa = T(1), fb = T(0), ba = T(1), bb = T(0);
+#pragma unroll
+    for (int j = 0; j < C; ++j) {
+        fb = a[j] * fb + r[j];
+        fa = a[j] * fa;
+        bb = ba * r[j] + bb;
+        ba = ba * c[j];
+    }
+    const unsigned F = 0xffffffffu;
+    for (int off = kColLines; off < 32; off <<= 1) {
+        const T oa = __shfl_up_sync(F, fa, off), ob = __shfl_up_sync(F, fb, off);
+        const T pa = __shfl_down_sync(F, ba, off), pb = __shfl_down_sync(F, bb, off);
+        if (lane >= off) {
+            fb = fa * ob + fb;
+            fa = fa * oa;
+        }
+        if (lane + off < 32) {
+            bb = ba * pb + bb;
+            ba = ba * pa;
+        }
+    }
+    if (q == QW - 1) {
+        wF[w][li][0] = fa;
+        wF[w][li][1] = fb;
+    }
+    if (q == 0) {
+        wB[w][li][0] = ba;
+        wB[w][li][1] = bb;
+    }
+    __syncthreads();
+    if (tid < kColLines) {
+        T y = T(0);
+        for (int v = 0; v < NW; ++v) {
+            yinF[v][tid] = y;
+            y = wF[v][tid][0] * y + wF[v][tid][1];
+        }
+    } else if (tid < 2 * kColLines) {
+        const int l2 = tid - kColLines;
+        T y = T(0);
+        for (int v = NW - 1; v >= 0; --v) {
+            yinB[v][l2] = y;
+            y = wB[v][l2][0] * y + wB[v][l2][1];
+        }
+    }
+    __syncthreads();
+    T efa = __shfl_up_sync(F, fa, kColLines), efb = __shfl_up_sync(F, fb, kColLines);
+    T eba = __shfl_down_sync(F, ba, kColLines), ebb = __shfl_down_sync(F, bb, kColLines);
+    if (q == 0) {
+        efa = T(1);
+        efb = T(0);
+    }
+    if (q == QW - 1) {
+        eba = T(1);
+        ebb = T(0);
+    }
+    T yf[C];
+    T y = efa * yinF[w][li] + efb;
+#pragma unroll
+    for (int j = 0; j < C; ++j) {
+        y = a[j] * y + r[j];
+        yf[j] = y;
+    }
+    T yb = eba * yinB[w][li] + ebb;
+#pragma unroll
+    for (int j = C - 1; j >= 0; --j) {
+        yb = c[j] * yb + r[j];
+        if (j < n) {
+            const size_t idx = (size_t)(lo + j) * m + xc;
+            Mown[idx] = (yf[j] - r[j]) + (yb - r[j]);
+            if (x) x[idx] = (double)(((yf[j] - r[j]) + yb) * sinv[idx]);
+        }
+    }
+}
+
 // out[c * m + r] = in[r * m + c] through 64 x 64 shared-memory tiles: a
 // 32 x 8 block moves 16 elements per thread, enough loads in flight to run
 // near the copy bandwidth.
@@ -888,6 +1001,31 @@ cudaError_t launch_line_freeze(int prec, int m, const void *sub, const void *sup
                                       nullptr, 0, flags, aF, aB, sinv, s);
     return launch_T<float, true>(m, sub, sup, diag, diag, Loth, Loth, nullptr, nullptr, f, y,
                                  nullptr, 0, flags, aF, aB, sinv, s);
+}
+
+bool line_cols_natural(int prec, int m) { return prec == 1 && m >= 1 && m <= 128 * 16; }
+
+cudaError_t launch_line_mean_cols(int prec, int m, const void *aF, const void *aB,
+                                  const void *sinv, const void *b, const void *Moth, void *Mown,
+                                  double *x, cudaStream_t s)
+{
+    if (m == 0) return cudaSuccess;
+    if (!line_cols_natural(prec, m)) return cudaErrorInvalidValue;
+    count_launches(s, 1);
+    const int C = m <= 128 * 8 ? 8 : 16;
+    const int nch = (m + C - 1) / C;              // chunks per line
+    const int qw = 32 / kColLines;                 // chunks of each line per warp
+    const int nt = ((nch + qw - 1) / qw) * 32;
+    const int grid = (m + kColLines - 1) / kColLines;
+    if (C == 8)
+        k_line_mean_cols<float, 8><<<grid, nt, 0, s>>>(m, (const float *)aF, (const float *)aB,
+                                                       (const float *)sinv, (const float *)b,
+                                                       (const float *)Moth, (float *)Mown, x);
+    else
+        k_line_mean_cols<float, 16><<<grid, nt, 0, s>>>(m, (const float *)aF, (const float *)aB,
+                                                        (const float *)sinv, (const float *)b,
+                                                        (const float *)Moth, (float *)Mown, x);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_line_mean(int prec, int m, const void *aF, const void *aB, const void *sinv,
