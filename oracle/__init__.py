@@ -312,15 +312,20 @@ class MGOracle:
 
     ``ncolors`` = 0 smooths with flood sweeps (Sec. 2.2); 2 or 4 with the
     red-black or 4-colour schedule (Sec. 5.1) on the grid colouring ``grid_colors``.
+    ``lines=True`` smooths with line GaBP (Algorithm 2 with the grid's rows and
+    columns as regions, ``line_sweeps``; 5-point levels only), the beliefs
+    being the column regions' solutions.
     """
 
     MODES = ("cold", "warm", "persist")
 
     def __init__(self, levels, sides, transfer_scale: float = 4.0, mode: str = "cold",
-                 ncolors: int = 0):
+                 ncolors: int = 0, lines: bool = False):
         assert len(levels) == len(sides) >= 1
         assert mode in self.MODES
         self.ncolors = ncolors
+        self.lines = lines
+        self.lstate = [line_zero_state(A.n) for A in levels] if lines else None
         self.colors = [grid_colors(m, ncolors) if ncolors else None for m in sides]
         self.levels = levels
         self.sides = list(sides)
@@ -338,7 +343,15 @@ class MGOracle:
             self.lt[lvl][:] = 0.0
         if self.mode in ("cold", "warm"):
             self.mm[lvl][:] = 0.0
-        if self.ncolors:
+        if self.lines:
+            stl = self.lstate[lvl]
+            for key in ("LH", "LV") if self.mode == "cold" else ():
+                stl[key][:] = 0.0
+            for key in ("MH", "MV") if self.mode in ("cold", "warm") else ():
+                stl[key][:] = 0.0
+            e = line_sweeps(A, self.sides[lvl], r, nu, stl)
+            st = OK if np.all(np.isfinite(e)) else BREAKDOWN
+        elif self.ncolors:
             e, _, st = sweeps_colored(A, r, self.colors[lvl], self.ncolors, nu, self.lt[lvl], self.mm[lvl])
         else:
             e, _, st = sweeps(A, r, nu, self.lt[lvl], self.mm[lvl])

@@ -1636,6 +1636,8 @@ gabp_status mg_smooth(mg_ctx *mg, int l, const double *b, double *x, int nu, MgR
     } else if (r != c->bres) {
         CK(cudaMemcpyAsync(c->bres, r, (size_t)c->n * sizeof(double), cudaMemcpyDeviceToDevice, s));
     }
+    // the line schedule's column phase reads the right-hand side in transposed order
+    if (c->lines_m > 0) CK(launch_transpose(c->prec, c->lines_m, c->bT, c->lbT, s));
     if (mg->mode == MG_SMOOTH_COLD) CKS(zero_messages(c, true, true));
     else if (mg->mode == MG_SMOOTH_WARM) CKS(zero_messages(c, false, true));
     CKS(aggregate(c));

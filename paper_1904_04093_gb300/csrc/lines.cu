@@ -954,25 +954,24 @@ cudaError_t launch_mean_T(int m, const void *aF, const void *aB, const void *sin
 
 bool line_needs_scratch(int prec, int m) { return line_smem_bytes(prec, m) > kLineSmemMax; }
 
+// The dynamic shared-memory limit of the staged line kernels is a property of
+// the kernel, shared by every context in the process: it is raised to the
+// largest size the launches may request (not to this context's), so contexts
+// of different line lengths can coexist.
 cudaError_t prepare_line_kernels(int prec, int m)
 {
-    const int full = (int)line_smem_bytes(prec, m), mean = (int)line_mean_smem_bytes(prec, m);
+    (void)m;
     const cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
-    cudaError_t e = cudaSuccess;
-    if ((size_t)full <= kLineSmemMax) {
-        if (prec == 0) {
-            if ((e = cudaFuncSetAttribute(k_line_scan<double, true, false>, A, full)) != cudaSuccess) return e;
-            e = cudaFuncSetAttribute(k_line_scan<double, true, true>, A, full);
-        } else {
-            if ((e = cudaFuncSetAttribute(k_line_scan<float, true, false>, A, full)) != cudaSuccess) return e;
-            e = cudaFuncSetAttribute(k_line_scan<float, true, true>, A, full);
-        }
-        if (e != cudaSuccess) return e;
+    const int cap = (int)kLineSmemMax;
+    cudaError_t e;
+    if (prec == 0) {
+        if ((e = cudaFuncSetAttribute(k_line_scan<double, true, false>, A, cap)) != cudaSuccess) return e;
+        if ((e = cudaFuncSetAttribute(k_line_scan<double, true, true>, A, cap)) != cudaSuccess) return e;
+        return cudaFuncSetAttribute(k_line_mean<double, true>, A, cap);
     }
-    if ((size_t)mean <= kLineSmemMax)
-        e = prec == 0 ? cudaFuncSetAttribute(k_line_mean<double, true>, A, mean)
-                      : cudaFuncSetAttribute(k_line_mean<float, true>, A, mean);
-    return e;
+    if ((e = cudaFuncSetAttribute(k_line_scan<float, true, false>, A, cap)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k_line_scan<float, true, true>, A, cap)) != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_line_mean<float, true>, A, cap);
 }
 
 cudaError_t launch_line_phase(int prec, int m, const void *sub, const void *sup, const void *diag,

@@ -47,6 +47,7 @@ __all__ = [
     "uniform_rhs",
     "config_c1",
     "config_c2",
+    "config_c2_levels",
     "config_c3_levels",
     "config_c4_batch",
     "config_c5",
@@ -402,6 +403,35 @@ def config_c3_levels(m_fine: int = 4095, m_coarse: int = 31, eps: float = 0.01,
         levels.append(convdiff_9pt_aniso(ms, eps, hv))
     rng = np.random.default_rng(seed)
     b = uniform_rhs(m_fine * m_fine, rng)
+    return levels, sides, b
+
+
+def config_c2_levels(m_fine: int = 2047, m_coarse: int = 31, sigma: float = 0.5,
+                     theta: float = 0.3, pe_h: float = 1.0, seed: int = 1002):
+    """Rediscretised 5-point hierarchy of the log-normal convection-diffusion
+    problem of ``config_c2`` on vertex-centred grids of side 2^J - 1.
+
+    The diffusion field is drawn on the finest grid and injected to the coarse
+    nodes (coarse node (I, J) is fine node (2I + 1, 2J + 1)); the velocity is
+    fixed in physical units (cell Peclet ``pe_h`` on the finest grid).
+    Returns ``(levels, sides, b)`` finest first; ``b ~ U[-1, 1]`` on the finest grid.
+    """
+    sides = []
+    m = m_fine
+    while True:
+        sides.append(m)
+        if m <= m_coarse:
+            break
+        assert (m - 1) % 2 == 0, "grid sides must be 2^J - 1"
+        m = (m - 1) // 2
+    rng = np.random.default_rng(seed)
+    D = lognormal_field(m_fine, sigma, rng)
+    b = uniform_rhs(m_fine * m_fine, rng)
+    levels = []
+    for lvl, ms in enumerate(sides):
+        hv = _hv(pe_h * (2 ** lvl), theta)
+        levels.append(convdiff_5pt(ms, D, hv))
+        D = D[1::2, 1::2]
     return levels, sides, b
 
 
