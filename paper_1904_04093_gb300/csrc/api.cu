@@ -174,6 +174,18 @@ struct mg_ctx {
     DevStatus *dstat = nullptr, *hstat = nullptr;
     std::vector<void *> allocs;
     size_t dev_bytes = 0;
+    // mg_solve replays its cycles (V-cycle, convergence residual, status and
+    // flag copies) as CUDA graphs captured on cap_stream, one per (b, x, nu)
+    struct CycleGraph {
+        const double *b;
+        double *x;
+        int nu_pre, nu_post;
+        cudaGraphExec_t exec;
+        unsigned long long kernels;
+    };
+    cudaStream_t cap_stream = nullptr;
+    std::vector<CycleGraph> graphs;
+    unsigned *hflags = nullptr;  // pinned: each level's breakdown flags after a replay
 };
 
 namespace {
@@ -440,7 +452,8 @@ gabp_status load_rhs(gabp_ctx *ctx, const double *b)
 
 gabp_status aggregate(gabp_ctx *ctx)
 {
-    if (ctx->parity) return GABP_OK;  // the parity-class sweep keeps no aggregates
+    // the parity-class and line sweeps keep no aggregates
+    if (ctx->parity || ctx->lines_m > 0) return GABP_OK;
     CK(launch_aggregate(ctx->L, ctx->prec, ctx->diagT, ctx->bT, ctx->Lm[ctx->cur],
                         ctx->Mm[ctx->cur], ctx->P[ctx->cur], ctx->B[ctx->cur], ctx->stream));
     return GABP_OK;
@@ -1597,6 +1610,10 @@ gabp_status mg_setup(int levels, gabp_ctx *const *level_ctx, const int32_t *grid
     if (e != cudaSuccess) return bail(fail_cuda(e, "cudaMemcpy"));
     if ((s = dalloc(mg, (void **)&mg->dstat, sizeof(DevStatus))) != GABP_OK) return bail(s);
     if ((e = cudaMallocHost((void **)&mg->hstat, sizeof(DevStatus))) != cudaSuccess) return bail(fail_cuda(e, "cudaMallocHost"));
+    if ((e = cudaMallocHost((void **)&mg->hflags, (size_t)levels * sizeof(unsigned))) != cudaSuccess)
+        return bail(fail_cuda(e, "cudaMallocHost"));
+    if ((e = cudaStreamCreateWithFlags(&mg->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
+        return bail(fail_cuda(e, "cudaStreamCreate"));
     // every level works on the multigrid stream
     for (auto *c : mg->lv) c->stream = mg->stream;
     *out = mg;
@@ -1608,8 +1625,11 @@ void mg_destroy(mg_ctx *mg)
     if (!mg) return;
     cudaSetDevice(mg->dev);
     if (mg->stream) cudaStreamSynchronize(mg->stream);
+    for (auto &g : mg->graphs) cudaGraphExecDestroy(g.exec);
     free_all(mg->allocs);
     if (mg->hstat) cudaFreeHost(mg->hstat);
+    if (mg->hflags) cudaFreeHost(mg->hflags);
+    if (mg->cap_stream) cudaStreamDestroy(mg->cap_stream);
     delete mg;
 }
 
@@ -1672,6 +1692,82 @@ gabp_status mg_cycle(mg_ctx *mg, int l, int last, int nu_pre, int nu_post, const
     return GABP_OK;
 }
 
+// After a cycle of mg_solve: the convergence residual b - A x of the finest
+// level (left in its residual buffer for the next cycle), its maxima and every
+// level's breakdown flags copied to pinned host memory.
+gabp_status mg_cycle_tail(mg_ctx *mg, const double *b, double *x, cudaStream_t s)
+{
+    gabp_ctx *f = mg->lv[0];
+    CK(cudaMemsetAsync(mg->dstat, 0, sizeof(DevStatus), s));
+    CK(launch_residual(f->L, f->a64, f->diag64, b, x, f->bres, mg->dstat, s));
+    CK(cudaMemcpyAsync(mg->hstat, mg->dstat, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
+    for (int l = 0; l < mg->levels; ++l)
+        CK(cudaMemcpyAsync(&mg->hflags[l], &mg->lv[l]->dstat[0].flags, sizeof(unsigned),
+                           cudaMemcpyDeviceToHost, s));
+    return GABP_OK;
+}
+
+// A replayed cycle starts from the message buffers it was captured with.
+// That is right when the smoother restarts from zero messages (cold), when
+// every level updates its messages in place (coloured and line schedules),
+// or when a cycle does an even number of double-buffered sweeps per level.
+bool mg_graph_safe(const mg_ctx *mg, int nu_pre, int nu_post)
+{
+    if (mg->mode == MG_SMOOTH_COLD || (nu_pre + nu_post) % 2 == 0) return true;
+    for (const gabp_ctx *c : mg->lv)
+        if (!(c->ncolors > 0 || c->lines_m > 0)) return false;
+    return true;
+}
+
+// One cycle of mg_solve after the first (pre-smoothing residual known) and
+// its tail, replayed from a graph captured on the first use of (b, x, nu).
+gabp_status mg_cycle_graph(mg_ctx *mg, const double *b, double *x, int nu_pre, int nu_post)
+{
+    cudaGraphExec_t exec = nullptr;
+    unsigned long long kernels = 0;
+    for (auto &g : mg->graphs)
+        if (g.b == b && g.x == x && g.nu_pre == nu_pre && g.nu_post == nu_post) {
+            exec = g.exec;
+            kernels = g.kernels;
+        }
+    if (!exec) {
+        // enqueue everything on the capture stream: the multigrid and every level
+        cudaStream_t home = mg->stream;
+        mg->stream = mg->cap_stream;
+        for (auto *c : mg->lv) c->stream = mg->cap_stream;
+        cudaGraph_t graph = nullptr;
+        gabp_status st = GABP_OK;
+        cudaError_t e = cudaStreamBeginCapture(mg->cap_stream, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            st = mg_cycle(mg, 0, mg->levels - 1, nu_pre, nu_post, b, x, MG_RES_READY);
+            if (st == GABP_OK) st = mg_cycle_tail(mg, b, x, mg->cap_stream);
+            e = cudaStreamEndCapture(mg->cap_stream, &graph);
+        }
+        mg->stream = home;
+        for (auto *c : mg->lv) c->stream = home;
+        if (st != GABP_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return st;
+        }
+        if (e != cudaSuccess) return fail_cuda(e, "multigrid cycle capture");
+        size_t nn = 0;
+        cudaGraphGetNodes(graph, nullptr, &nn);
+        std::vector<cudaGraphNode_t> nodes(nn);
+        if (nn) cudaGraphGetNodes(graph, nodes.data(), &nn);
+        for (auto &nd : nodes) {
+            cudaGraphNodeType t;
+            if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++kernels;
+        }
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return fail_cuda(e, "cudaGraphInstantiate");
+        mg->graphs.push_back({b, x, nu_pre, nu_post, exec, kernels});
+    }
+    CK(cudaGraphLaunch(exec, mg->stream));
+    count_launches(mg->stream, kernels);
+    return GABP_OK;
+}
+
 gabp_status mg_check_flags(mg_ctx *mg)
 {
     for (auto *c : mg->lv) {
@@ -1715,15 +1811,24 @@ gabp_status mg_solve(mg_ctx *mg, const double *b, double *x, double tol, int max
     gabp_status st = bn == 0.0 ? GABP_OK : GABP_E_NOT_CONVERGED;
     for (auto *lc : mg->lv) CK(cudaMemsetAsync(&lc->dstat[0].flags, 0, sizeof(unsigned), s));
     while (st == GABP_E_NOT_CONVERGED && c < max_cycles) {
-        // the first cycle starts from x = 0; later ones reuse the check's residual of the same x
-        CKS(mg_cycle(mg, 0, mg->levels - 1, nu_pre, nu_post, b, x, c == 0 ? MG_RES_XZERO : MG_RES_READY));
+        if (c == 0) {
+            // the first cycle starts from x = 0
+            CKS(mg_cycle(mg, 0, mg->levels - 1, nu_pre, nu_post, b, x, MG_RES_XZERO));
+            CKS(mg_cycle_tail(mg, b, x, s));
+        } else if (mg_graph_safe(mg, nu_pre, nu_post)) {
+            // later cycles reuse the check's residual of the same x: one graph replay each
+            CKS(mg_cycle_graph(mg, b, x, nu_pre, nu_post));
+        } else {
+            CKS(mg_cycle(mg, 0, mg->levels - 1, nu_pre, nu_post, b, x, MG_RES_READY));
+            CKS(mg_cycle_tail(mg, b, x, s));
+        }
         ++c;
-        CK(cudaMemsetAsync(mg->dstat, 0, sizeof(DevStatus), s));
-        CK(launch_residual(f->L, f->a64, f->diag64, b, x, f->bres, mg->dstat, s));
-        CK(cudaMemcpyAsync(mg->hstat, mg->dstat, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
         rr = bits_to_double(mg->hstat->rmax) / bn;
-        gabp_status fs = mg_check_flags(mg);
+        gabp_status fs = GABP_OK;
+        for (int l = 0; l < mg->levels; ++l)
+            if (mg->hflags[l] & FLAG_BREAKDOWN)
+                fs = fail(GABP_E_BREAKDOWN, "zero or non-finite message denominator in a smoother");
         if (fs != GABP_OK) { st = fs; break; }
         if ((mg->hstat->flags & FLAG_NAN) || !std::isfinite(rr) || rr > kDivergence) { st = fail(GABP_E_DIVERGED, "residual diverged"); break; }
         if (rr <= tol) st = GABP_OK;

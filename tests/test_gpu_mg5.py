@@ -74,3 +74,37 @@ def test_line_smoothed_mg_full_size(g):
     assert st == g.OK and c <= 40
     r = b - levels[0].matvec(host(x))
     assert np.max(np.abs(r)) / np.max(np.abs(b)) <= 1.05e-10
+
+
+@pytest.mark.parametrize("mode,nu", [("cold", (2, 1)), ("cold", (1, 1)), ("warm", (1, 1)),
+                                     ("warm", (2, 1)), ("persist", (1, 2))])
+def test_graph_replayed_cycles_match_oracle(g, mode, nu):
+    """mg_solve replays its cycles from a captured graph where that is exact
+    (cold smoothing, in-place schedules, an even number of sweeps per level)
+    and runs them eagerly otherwise; either way four cycles of the solve are
+    the oracle's four V-cycles (the warm and persist readings need not
+    converge here: the cycles are compared, not the solution), a second solve
+    reuses the graphs and continues like the oracle, and the finest level's
+    context still solves on its own afterwards."""
+    levels, sides, b = P.config_c2_levels(m_fine=31, m_coarse=7)
+    mo = oracle.MGOracle(levels, sides, mode=mode)
+    xo = np.zeros(levels[0].n)
+    for _ in range(4):
+        xo = mo.vcycle(b, xo, *nu)
+    solvers = [g.GabpSolver(A, "fp64", check_every=1) for A in levels]
+    mg = g.Multigrid(solvers, sides, mode=mode)
+    x, c, rr, st = mg.solve(dev(b), 1e-30, 4, *nu)
+    assert st == g.NOT_CONVERGED and c == 4
+    assert rel(host(x), xo) <= 1e-11
+    # a second solve reuses the graphs; in the warm and persist readings the
+    # messages carry over from the first solve, as in the oracle
+    xo2 = np.zeros(levels[0].n)
+    for _ in range(4):
+        xo2 = mo.vcycle(b, xo2, *nu)
+    x2, c2, _, _ = mg.solve(dev(b), 1e-30, 4, *nu)
+    assert c2 == 4 and rel(host(x2), xo2) <= 1e-11
+    if mode == "cold":
+        assert rel(host(x2), host(x)) <= 1e-13
+    ref1 = oracle.solve(levels[0], b, 1e-10, 5000)
+    x1, it1, _, st1 = solvers[0].solve(dev(b), 1e-10, 5000)
+    assert st1 == g.OK and it1 == ref1["iters"]
