@@ -321,7 +321,8 @@ gabp_status gabp_batch_setup(int nsys, gabp_ctx *const *systems, int check_every
 /*
  * Autotuner: times a whole batched solve (tolerance `tol`, sweep cap
  * `max_iter`, as gabp_batch_solve) for each launch shape -- 256 or 512
- * threads per CTA x 1, 2, 4 or 8 CTAs per thread-block cluster, as many
+ * threads per CTA x 1, 2, 4, 8 or 16 CTAs per thread-block cluster (16
+ * where the non-portable cluster size fits), as many
  * clusters as can be resident -- and keeps the fastest.  Under a shape,
  * systems with at least 4 rows per cluster thread are each solved by a whole
  * cluster, the rest by single CTAs.  b, x: host arrays of nsys device
@@ -332,7 +333,8 @@ gabp_status gabp_batch_setup(int nsys, gabp_ctx *const *systems, int check_every
 gabp_status gabp_batch_tune(gabp_batch *batch, const double *const *b, double *const *x, double tol,
                             int max_iter, int *block, int *cluster);
 
-/* Sets the launch shape without tuning: block 256 or 512, cluster 1, 2, 4 or 8. */
+/* Sets the launch shape without tuning: block 256 or 512, cluster 1, 2, 4, 8 or 16
+ * (GABP_E_INVALID_ARG when the shape cannot be resident). */
 gabp_status gabp_batch_set_shape(gabp_batch *batch, int block, int cluster);
 
 /*

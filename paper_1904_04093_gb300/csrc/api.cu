@@ -1993,8 +1993,9 @@ static gabp_status batch_set_shape(gabp_batch *bt, int blk, int cs)
 
 gabp_status gabp_batch_set_shape(gabp_batch *bt, int block, int cluster)
 {
-    if (!bt || (block != 256 && block != 512) || !(cluster == 1 || cluster == 2 || cluster == 4 || cluster == 8))
-        return fail(GABP_E_INVALID_ARG, "block must be 256 or 512, cluster 1, 2, 4 or 8");
+    if (!bt || (block != 256 && block != 512) ||
+        !(cluster == 1 || cluster == 2 || cluster == 4 || cluster == 8 || cluster == 16))
+        return fail(GABP_E_INVALID_ARG, "block must be 256 or 512, cluster 1, 2, 4, 8 or 16");
     CKS(set_dev(bt->dev));
     return batch_set_shape(bt, block, cluster);
 }
@@ -2006,7 +2007,7 @@ gabp_status gabp_batch_tune(gabp_batch *bt, const double *const *b, double *cons
     CKS(set_dev(bt->dev));
     CKS(batch_stage(bt, b, x));
     const int blocks[] = {256, 512};
-    const int clusters[] = {1, 2, 4, 8};
+    const int clusters[] = {1, 2, 4, 8, 16};  // 16: non-portable cluster size, where it fits
     float best = -1.0f;
     int bb = 0, bc = 0;
     for (int blk : blocks)

@@ -1,6 +1,6 @@
 // Batched GaBP: many independent systems solved in one persistent launch.
 //
-// Each thread-block cluster (1 to 8 CTAs, one SM each) takes the next system
+// Each thread-block cluster (1 to 16 CTAs, one SM each) takes the next system
 // from a global queue (largest first), runs every flood sweep of that system
 // with all its threads (one thread per row, strided over the cluster),
 // checks its own double residual every `check_every` sweeps and stops it on
@@ -406,12 +406,22 @@ __global__ void __launch_bounds__(512) k_batch_solve(
 
 }  // namespace
 
+// Clusters above the portable 8 CTAs (16 on this GPU) need the kernel's
+// non-portable attribute; set before every occupancy query and launch.
+template <typename T, int K>
+void allow_big_clusters()
+{
+    if (cudaFuncSetAttribute(k_batch_solve<T, K>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
+        cudaGetLastError();
+}
+
 template <typename T, int K>
 cudaError_t launch_batch_k(int cs, int grid, int block, const void *sys, const int *order, int nsys,
                            int nbig, const double *const *bptr, double *const *xptr, int *queue, double tol,
                            int max_iter, int check_every, int refine, double inner_tol,
                            int inner_max, int freeze, void *res, cudaStream_t s)
 {
+    if (cs > 8) allow_big_clusters<T, K>();
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid, 1, 1);
     cfg.blockDim = dim3(block, 1, 1);
@@ -456,6 +466,7 @@ cudaError_t launch_batch(int K, int cs, int grid, int block, const void *sys, co
 template <typename T, int K>
 int batch_max_clusters_k(int cs, int block)
 {
+    if (cs > 8) allow_big_clusters<T, K>();
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(cs, 1, 1);
     cfg.blockDim = dim3(block, 1, 1);

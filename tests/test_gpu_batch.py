@@ -160,3 +160,29 @@ def test_batch_faults_stay_per_system(g):
     assert sts == [g.OK, g.DIVERGED, g.BREAKDOWN, g.OK]
     xs_ = np.linalg.solve(Ag.to_dense(), bg)
     assert rel(host(xs[0]), xs_) <= 1e-8 and rel(host(xs[3]), xs_) <= 1e-8
+
+
+@pytest.mark.parametrize("block", [256, 512])
+def test_batch_sixteen_cta_clusters(g, block):
+    """Clusters of 16 CTAs (the non-portable size): systems with at least 4
+    rows per cluster thread (here 128^2 and 136^2 with 256 threads per CTA)
+    are solved by a whole 16-CTA cluster, the rest by single CTAs; every
+    system equals its single solve."""
+    systems = P.config_c4_batch(nsys=3, smin=16, smax=40, seed=11)
+    for side in (136, 128):
+        A = P.convdiff_5pt(side, P.lognormal_field(side, 0.5, np.random.default_rng(side)), (1.0, 0.6))
+        systems.append((A, np.random.default_rng(side + 1).uniform(-1, 1, A.n)))
+    solvers = [g.GabpSolver(A, "fp64", check_every=5) for A, _ in systems]
+    batch = g.Batch(solvers, check_every=5)
+    try:
+        batch.set_shape(block, 16)
+    except g.GabpError:
+        pytest.skip("16-CTA clusters of this block size cannot be resident")
+    bs = [dev(b) for _, b in systems]
+    xs, its, rrs, sts = batch.solve(bs, 1e-10, 20000)
+    assert all(s == g.OK for s in sts)
+    for (A, b), x, it in zip(systems, xs, its):
+        single = g.GabpSolver(A, "fp64", check_every=5)
+        xs1, it1, rr1, st1 = single.solve(dev(b), 1e-10, 20000)
+        assert st1 == g.OK and it == it1
+        assert rel(host(x), host(xs1)) <= 1e-14
