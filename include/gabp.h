@@ -78,10 +78,15 @@ typedef struct {
     int block_size;      /* threads per block of the sweep kernel (0 = tuned default) */
     int freeze_lambda;   /* precomputed precision messages (Sec. 4.2): 1 on, 0 off,
                             -1 default (on for GABP_FP32_IR, off otherwise); see gabp_solve */
+    int reorder;         /* CSR layout only: renumber the unknowns internally by reverse
+                            Cuthill-McKee (1), keep the caller's numbering (0), or -1 (default)
+                            renumber when that at least halves the mean index distance |i - j|
+                            of the coupled unknowns.  Invisible at the interface: vectors,
+                            per-slot arrays and colours stay in the caller's order. */
 } gabp_options;
 
 /* Fills `opt` with the defaults: FP64, auto layout, check_every 10, graphs on,
- * ir_inner_max 400, ir_inner_tol 1e-3, block_size 0, freeze_lambda -1.
+ * ir_inner_max 400, ir_inner_tol 1e-3, block_size 0, freeze_lambda -1, reorder -1.
  * (Short refinement steps win: restarting the float solve on a fresh double
  * residual every few hundred sweeps reaches 1e-10 in fewer total sweeps
  * than long inner solves.) */
@@ -259,6 +264,7 @@ typedef struct {
     size_t device_bytes;    /* device memory held by the context */
     int parity_layout;      /* 1: the coloured schedule runs on the parity-class layout */
     double colored_sweep_bytes; /* compulsory DRAM bytes of one sweep on that layout */
+    int reordered;          /* 1: the unknowns are renumbered internally (gabp_options.reorder) */
 } gabp_info;
 
 gabp_status gabp_get_info(gabp_ctx *ctx, gabp_info *info);

@@ -39,7 +39,8 @@ class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("layout", ctypes.c_int),
                 ("check_every", ctypes.c_int), ("use_graphs", ctypes.c_int),
                 ("ir_inner_max", ctypes.c_int), ("ir_inner_tol", ctypes.c_double),
-                ("block_size", ctypes.c_int), ("freeze_lambda", ctypes.c_int)]
+                ("block_size", ctypes.c_int), ("freeze_lambda", ctypes.c_int),
+                ("reorder", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -48,7 +49,8 @@ class Info(ctypes.Structure):
                 ("slots", ctypes.c_int64), ("sweep_bytes", ctypes.c_double),
                 ("mean_sweep_bytes", ctypes.c_double),
                 ("residual_bytes", ctypes.c_double), ("device_bytes", ctypes.c_size_t),
-                ("parity_layout", ctypes.c_int), ("colored_sweep_bytes", ctypes.c_double)]
+                ("parity_layout", ctypes.c_int), ("colored_sweep_bytes", ctypes.c_double),
+                ("reordered", ctypes.c_int)]
 
 
 _lib = None
@@ -153,7 +155,7 @@ class GabpSolver:
 
     def __init__(self, A, precision: str = "fp64", layout: str = "auto", check_every: int = 10,
                  use_graphs: bool = True, ir_inner_max: int = 400, ir_inner_tol: float = 1e-3,
-                 block_size: int = 0, freeze_lambda: int = -1, stream=None):
+                 block_size: int = 0, freeze_lambda: int = -1, reorder: int = -1, stream=None):
         L = load()
         torch = _torch()
         self.n = int(A.n)
@@ -171,6 +173,7 @@ class GabpSolver:
         opt.ir_inner_tol = float(ir_inner_tol)
         opt.block_size = int(block_size)
         opt.freeze_lambda = int(freeze_lambda)
+        opt.reorder = int(reorder)
         self.precision = precision
         self.device = torch.cuda.current_device()
         self._sh, self.stream = _stream_handle(stream)

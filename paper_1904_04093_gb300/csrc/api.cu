@@ -86,6 +86,14 @@ struct gabp_ctx {
     double *aT64 = nullptr;
     int64_t *slotmap = nullptr;                         // caller slot -> layout slot (-1: none)
     int64_t *diagpos = nullptr;                         // entry index of each row's diagonal (lazy)
+    // internal renumbering (reverse Cuthill-McKee, CSR layout): internal node i
+    // is the caller's node perm[i]; the CSR in internal order and, for every
+    // caller entry, its position there
+    bool reordered = false;
+    int *d_perm = nullptr;
+    std::vector<int32_t> h_perm;
+    std::vector<int64_t> h_pindptr, h_pmap;
+    std::vector<int32_t> h_pindices;
     int64_t *d_indptr = nullptr;                        // caller CSR on device (edge gradient)
     int *d_indices = nullptr;
     // state
@@ -444,9 +452,23 @@ gabp_status zero_messages(gabp_ctx *ctx, bool lam, bool mean)
 gabp_status load_rhs(gabp_ctx *ctx, const double *b)
 {
     const int64_t n = ctx->n;
-    if (b != ctx->bres) CK(cudaMemcpyAsync(ctx->bres, b, n * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+    if (b != ctx->bres) {
+        if (ctx->reordered)  // caller order -> internal order
+            CK(launch_permute((int)n, ctx->d_perm, b, ctx->bres, 0, ctx->stream));
+        else
+            CK(cudaMemcpyAsync(ctx->bres, b, n * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+    }
     if (ctx->prec == 1) CK(launch_convert_d2f(ctx->bres, (float *)ctx->bT, n, ctx->stream));
     if (ctx->lines_m > 0) CK(launch_transpose(ctx->prec, ctx->lines_m, ctx->bT, ctx->lbT, ctx->stream));
+    return GABP_OK;
+}
+
+// An internal-order vector out to the caller's order.
+gabp_status store_vector(gabp_ctx *ctx, const double *in, double *out, cudaStream_t s)
+{
+    if (ctx->n == 0) return GABP_OK;
+    if (ctx->reordered) CK(launch_permute(ctx->n, ctx->d_perm, in, out, 1, s));
+    else CK(cudaMemcpyAsync(out, in, (size_t)ctx->n * sizeof(double), cudaMemcpyDeviceToDevice, s));
     return GABP_OK;
 }
 
@@ -783,7 +805,7 @@ gabp_status solve_plain(gabp_ctx *ctx, const double *b, double *x, double tol, i
         }
         if (st == GABP_E_NOT_CONVERGED) fail(st, "iteration cap reached");
     }
-    CK(cudaMemcpyAsync(x, ctx->xbuf, n * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream));
+    CKS(store_vector(ctx, ctx->xbuf, x, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     if (iters) *iters = it;
     if (relres) *relres = rr;
@@ -799,7 +821,8 @@ gabp_status solve_ir(gabp_ctx *ctx, const double *b, double *x, double tol, int 
     const size_t nb = n * sizeof(double);
     CKS(ensure_ir(ctx));
     cudaStream_t s = ctx->stream;
-    CK(cudaMemcpyAsync(ctx->b0, b, nb, cudaMemcpyDeviceToDevice, s));
+    if (ctx->reordered) CK(launch_permute((int)n, ctx->d_perm, b, ctx->b0, 0, s));
+    else CK(cudaMemcpyAsync(ctx->b0, b, nb, cudaMemcpyDeviceToDevice, s));
     CK(cudaMemsetAsync(ctx->xacc, 0, nb, s));
     CK(cudaMemsetAsync(ctx->dstat, 0, 2 * sizeof(DevStatus), s));
     // r = b, s = ||b||
@@ -846,7 +869,7 @@ gabp_status solve_ir(gabp_ctx *ctx, const double *b, double *x, double tol, int 
         if (rr <= tol) st = GABP_OK;
     }
     if (st == GABP_E_NOT_CONVERGED) fail(st, "iteration cap reached");
-    CK(cudaMemcpyAsync(x, ctx->xacc, nb, cudaMemcpyDeviceToDevice, s));
+    CKS(store_vector(ctx, ctx->xacc, x, s));
     CK(cudaStreamSynchronize(s));
     if (iters) *iters = total;
     if (relres) *relres = rr;
@@ -860,6 +883,142 @@ gabp_status solve_ir(gabp_ctx *ctx, const double *b, double *x, double tol, int 
 // ===========================================================================
 extern "C" {
 
+namespace {
+
+// Symmetrised adjacency of A without the diagonal, rows sorted, no duplicates.
+void sym_adjacency(int32_t n, const int64_t *indptr, const int32_t *indices,
+                   std::vector<int64_t> &ap, std::vector<int32_t> &aj)
+{
+    std::vector<int64_t> cnt((size_t)n + 1, 0);
+    for (int32_t r = 0; r < n; ++r)
+        for (int64_t p = indptr[r]; p < indptr[r + 1]; ++p)
+            if (indices[p] != r) {
+                cnt[r + 1]++;
+                cnt[indices[p] + 1]++;
+            }
+    for (int32_t r = 0; r < n; ++r) cnt[r + 1] += cnt[r];
+    std::vector<int32_t> tmp((size_t)cnt[n]);
+    std::vector<int64_t> fill(cnt.begin(), cnt.end() - 1);
+    for (int32_t r = 0; r < n; ++r)
+        for (int64_t p = indptr[r]; p < indptr[r + 1]; ++p)
+            if (indices[p] != r) {
+                tmp[fill[r]++] = indices[p];
+                tmp[fill[indices[p]]++] = r;
+            }
+    ap.assign((size_t)n + 1, 0);
+    aj.clear();
+    aj.reserve(tmp.size());
+    for (int32_t r = 0; r < n; ++r) {
+        auto b0 = tmp.begin() + cnt[r], b1 = tmp.begin() + cnt[r + 1];
+        std::sort(b0, b1);
+        auto e = std::unique(b0, b1);
+        aj.insert(aj.end(), b0, e);
+        ap[r + 1] = (int64_t)aj.size();
+    }
+}
+
+// Reverse Cuthill-McKee order of the symmetrised graph: for each connected
+// component a breadth-first search from a pseudo-peripheral node (the last
+// node a search from a minimum-degree node reaches), each node's unvisited
+// neighbours taken by ascending degree; the whole order reversed.  perm[i] is
+// the node placed at position i.  Returns whether the renumbering is worth it
+// (`force`, or it at least halves the mean |i - j| over the coupled pairs).
+bool rcm_order(int32_t n, const int64_t *indptr, const int32_t *indices, bool force,
+               std::vector<int32_t> &perm)
+{
+    std::vector<int64_t> ap;
+    std::vector<int32_t> aj;
+    sym_adjacency(n, indptr, indices, ap, aj);
+    auto deg = [&](int32_t v) { return ap[v + 1] - ap[v]; };
+    std::vector<int32_t> byDeg((size_t)n);
+    for (int32_t i = 0; i < n; ++i) byDeg[i] = i;
+    std::stable_sort(byDeg.begin(), byDeg.end(), [&](int32_t a, int32_t b) { return deg(a) < deg(b); });
+    std::vector<int32_t> stamp((size_t)n, -1);
+    std::vector<char> placed((size_t)n, 0);
+    std::vector<int32_t> order, queue, nb;
+    order.reserve(n);
+    queue.reserve(n);
+    int32_t comp = 0;
+    for (int32_t v0 : byDeg) {
+        if (placed[v0]) continue;
+        // pseudo-peripheral start: the last node reached from v0
+        queue.clear();
+        queue.push_back(v0);
+        stamp[v0] = comp;
+        for (size_t h = 0; h < queue.size(); ++h)
+            for (int64_t p = ap[queue[h]]; p < ap[queue[h] + 1]; ++p)
+                if (stamp[aj[p]] != comp) {
+                    stamp[aj[p]] = comp;
+                    queue.push_back(aj[p]);
+                }
+        const int32_t u = queue.back();
+        // Cuthill-McKee from u
+        const size_t first = order.size();
+        order.push_back(u);
+        placed[u] = 1;
+        for (size_t h = first; h < order.size(); ++h) {
+            const int32_t w = order[h];
+            nb.clear();
+            for (int64_t p = ap[w]; p < ap[w + 1]; ++p)
+                if (!placed[aj[p]]) {
+                    placed[aj[p]] = 1;
+                    nb.push_back(aj[p]);
+                }
+            std::stable_sort(nb.begin(), nb.end(), [&](int32_t a, int32_t b) { return deg(a) < deg(b); });
+            order.insert(order.end(), nb.begin(), nb.end());
+        }
+        ++comp;
+    }
+    std::reverse(order.begin(), order.end());
+    perm.swap(order);
+    if (force) return true;
+    std::vector<int32_t> iperm((size_t)n);
+    for (int32_t i = 0; i < n; ++i) iperm[perm[i]] = i;
+    double before = 0.0, after = 0.0;
+    for (int32_t r = 0; r < n; ++r)
+        for (int64_t p = ap[r]; p < ap[r + 1]; ++p) {
+            before += std::abs((double)aj[p] - r);
+            after += std::abs((double)iperm[aj[p]] - iperm[r]);
+        }
+    return after * 2.0 <= before;
+}
+
+// The CSR of P A P^T for the order perm (internal row i = caller row perm[i]),
+// rows sorted, and pmap[p] = position of the caller's entry p in it.
+void permute_csr(int32_t n, const int64_t *indptr, const int32_t *indices,
+                 const std::vector<int32_t> &perm, std::vector<int64_t> &pindptr,
+                 std::vector<int32_t> &pindices, std::vector<int64_t> &pmap)
+{
+    std::vector<int32_t> iperm((size_t)n);
+    for (int32_t i = 0; i < n; ++i) iperm[perm[i]] = i;
+    pindptr.assign((size_t)n + 1, 0);
+    for (int32_t i = 0; i < n; ++i) pindptr[i + 1] = pindptr[i] + (indptr[perm[i] + 1] - indptr[perm[i]]);
+    pindices.assign((size_t)indptr[n], 0);
+    pmap.assign((size_t)indptr[n], 0);
+    std::vector<std::pair<int32_t, int64_t>> row;
+    for (int32_t i = 0; i < n; ++i) {
+        const int32_t r = perm[i];
+        row.clear();
+        for (int64_t p = indptr[r]; p < indptr[r + 1]; ++p) row.emplace_back(iperm[indices[p]], p);
+        std::sort(row.begin(), row.end());
+        int64_t q = pindptr[i];
+        for (auto &cp : row) {
+            pindices[q] = cp.first;
+            pmap[cp.second] = q;
+            ++q;
+        }
+    }
+}
+
+std::vector<double> permute_values(const std::vector<int64_t> &pmap, const double *data)
+{
+    std::vector<double> v(pmap.size());
+    for (size_t p = 0; p < pmap.size(); ++p) v[pmap[p]] = data[p];
+    return v;
+}
+
+}  // namespace
+
 void gabp_default_options(gabp_options *opt)
 {
     if (!opt) return;
@@ -871,6 +1030,7 @@ void gabp_default_options(gabp_options *opt)
     opt->ir_inner_tol = 1e-3;
     opt->block_size = 0;
     opt->freeze_lambda = -1;
+    opt->reorder = -1;
 }
 
 #define GABP_BATCH_RES_ITERS(h, i) (((int *)((char *)(h) + (i) * batch_result_bytes()))[0])
@@ -907,7 +1067,7 @@ gabp_status gabp_setup(int32_t n, int64_t nnz, const int64_t *indptr, const int3
     if (opt) o = *opt;
     if (o.precision < 0 || o.precision > 2 || o.layout < 0 || o.layout > 2 || o.check_every < 0 ||
         o.block_size < 0 || o.block_size > 1024 || (o.block_size % 32) != 0 ||
-        o.freeze_lambda < -1 || o.freeze_lambda > 1)
+        o.freeze_lambda < -1 || o.freeze_lambda > 1 || o.reorder < -1 || o.reorder > 1)
         return fail(GABP_E_INVALID_ARG, "bad option");
     CKS(validate_csr(n, nnz, indptr, indices, data));
     int64_t nonzero_off = 0;
@@ -923,8 +1083,24 @@ gabp_status gabp_setup(int32_t n, int64_t nnz, const int64_t *indptr, const int3
     const int64_t offd = nnz - n;
     bool use_stencil = can_stencil &&
                        (o.layout == GABP_LAYOUT_STENCIL || (int64_t)sp.K * n <= 3 * offd + 4096);
-    if (use_stencil) build_stencil(n, indptr, indices, data, sp, H);
-    else build_csr(n, indptr, indices, data, H);
+    std::vector<int32_t> perm;
+    std::vector<int64_t> pindptr, pmap;
+    std::vector<int32_t> pindices;
+    bool reordered = false;
+    if (use_stencil) {
+        build_stencil(n, indptr, indices, data, sp, H);
+    } else if (o.reorder != 0 && n > 2 && rcm_order(n, indptr, indices, o.reorder == 1, perm)) {
+        // the layout is built on P A P^T; the caller's entries map through pmap
+        permute_csr(n, indptr, indices, perm, pindptr, pindices, pmap);
+        const std::vector<double> pdata = permute_values(pmap, data);
+        build_csr(n, pindptr.data(), pindices.data(), pdata.data(), H);
+        std::vector<int64_t> sm((size_t)nnz);
+        for (int64_t p = 0; p < nnz; ++p) sm[p] = H.slotmap[pmap[p]];
+        H.slotmap.swap(sm);
+        reordered = true;
+    } else {
+        build_csr(n, indptr, indices, data, H);
+    }
     if (H.kind == GABP_LAYOUT_CSR && H.slots >= (int64_t)1 << 31)
         return fail(GABP_E_INVALID_ARG, "too many edges for the CSR layout");
 
@@ -963,6 +1139,14 @@ gabp_status gabp_setup(int32_t n, int64_t nnz, const int64_t *indptr, const int3
     }
     if ((s = upload_coeffs(ctx, H, true)) != GABP_OK) return bail(s);
     if ((s = upload(ctx, (void **)&ctx->slotmap, H.slotmap.data(), H.slotmap.size() * sizeof(int64_t))) != GABP_OK) return bail(s);
+    if (reordered) {
+        ctx->reordered = true;
+        if ((s = upload(ctx, (void **)&ctx->d_perm, perm.data(), perm.size() * sizeof(int32_t))) != GABP_OK) return bail(s);
+        ctx->h_perm.swap(perm);
+        ctx->h_pindptr.swap(pindptr);
+        ctx->h_pindices.swap(pindices);
+        ctx->h_pmap.swap(pmap);
+    }
     const size_t S = (size_t)H.slots * esz(ctx->prec), NB = (size_t)n * esz(ctx->prec);
     for (int i = 0; i < 2; ++i) {
         if ((s = dalloc(ctx, &ctx->Lm[i], S)) != GABP_OK) return bail(s);
@@ -1033,10 +1217,14 @@ gabp_status gabp_set_values(gabp_ctx *ctx, const double *data)
     CKS(set_dev(ctx->dev));
     CKS(validate_csr(ctx->n, ctx->nnz, ctx->h_indptr.data(), ctx->h_indices.data(), data));
     HostLayout H;
-    if (ctx->L.kind == GABP_LAYOUT_STENCIL)
+    if (ctx->L.kind == GABP_LAYOUT_STENCIL) {
         build_stencil(ctx->n, ctx->h_indptr.data(), ctx->h_indices.data(), data, ctx->L.sp, H);
-    else
+    } else if (ctx->reordered) {
+        const std::vector<double> pdata = permute_values(ctx->h_pmap, data);
+        build_csr(ctx->n, ctx->h_pindptr.data(), ctx->h_pindices.data(), pdata.data(), H);
+    } else {
         build_csr(ctx->n, ctx->h_indptr.data(), ctx->h_indices.data(), data, H);
+    }
     CK(cudaStreamSynchronize(ctx->stream));
     CKS(upload_coeffs(ctx, H, false));
     ctx->h_data.assign(data, data + ctx->nnz);
@@ -1056,10 +1244,12 @@ gabp_status gabp_set_values_device(gabp_ctx *ctx, const double *data)
     }
     CKS(validate_csr(ctx->n, ctx->nnz, ctx->h_indptr.data(), ctx->h_indices.data(), h.data()));
     if (!ctx->diagpos) {
-        std::vector<int64_t> dp((size_t)ctx->n, 0);
-        for (int32_t r = 0; r < ctx->n; ++r)
+        std::vector<int64_t> dp((size_t)ctx->n, 0);  // by internal row
+        for (int32_t i = 0; i < ctx->n; ++i) {
+            const int32_t r = ctx->reordered ? ctx->h_perm[i] : i;
             for (int64_t p = ctx->h_indptr[r]; p < ctx->h_indptr[r + 1]; ++p)
-                if (ctx->h_indices[p] == r) dp[r] = p;
+                if (ctx->h_indices[p] == r) dp[i] = p;
+        }
         CKS(upload(ctx, (void **)&ctx->diagpos, dp.data(), dp.size() * sizeof(int64_t)));
     }
     CK(launch_coeffs_from_values(ctx->L, ctx->prec, ctx->nnz, ctx->slotmap, ctx->diagpos, data,
@@ -1084,6 +1274,8 @@ void gabp_destroy(gabp_ctx *ctx)
 
 static gabp_status setup_lines(gabp_ctx *ctx)
 {
+    if (ctx->reordered)
+        return fail(GABP_E_INVALID_ARG, "the line schedule needs the caller's grid numbering (reorder = 0)");
     const int n = ctx->n;
     int m = 0;
     while ((int64_t)m * m < n) ++m;
@@ -1282,7 +1474,7 @@ gabp_status gabp_set_schedule(gabp_ctx *ctx, int schedule, const int32_t *color,
             if (ix[p] != i && col[ix[p]] == col[i])
                 return fail(GABP_E_INVALID_ARG, "adjacent nodes share a colour");
     std::vector<unsigned char> c8(n);
-    for (int i = 0; i < n; ++i) c8[i] = (unsigned char)col[i];
+    for (int i = 0; i < n; ++i) c8[i] = (unsigned char)col[ctx->reordered ? ctx->h_perm[i] : i];
     // stencil layout: one sender colour per (row colour, diagonal) -> slot masks
     ctx->has_masks = false;
     if (ctx->L.kind == GABP_LAYOUT_STENCIL && nc <= KMAXCOLOR) {
@@ -1336,7 +1528,9 @@ gabp_status gabp_sweep(gabp_ctx *ctx, const double *b, int nsweeps, double *x)
     CKS(load_rhs(ctx, b));
     CKS(aggregate(ctx));
     CK(cudaMemsetAsync(&ctx->dstat[0].flags, 0, sizeof(unsigned), ctx->stream));
-    for (int i = 0; i < nsweeps; ++i) CK(sweep_once(ctx, false, i == nsweeps - 1 ? x : nullptr, ctx->stream));
+    double *xo = ctx->reordered && x ? ctx->xbuf : x;  // beliefs in internal order first
+    for (int i = 0; i < nsweeps; ++i) CK(sweep_once(ctx, false, i == nsweeps - 1 ? xo : nullptr, ctx->stream));
+    if (xo != x && nsweeps > 0) CKS(store_vector(ctx, xo, x, ctx->stream));
     unsigned fl = 0;
     CKS(read_status(ctx, 0, nullptr, nullptr, &fl));
     if (fl & FLAG_BREAKDOWN) return fail(GABP_E_BREAKDOWN, "zero or non-finite message denominator");
@@ -1419,7 +1613,17 @@ gabp_status gabp_residual(gabp_ctx *ctx, const double *b, const double *x, doubl
     if (!ctx || ((!b || !x) && ctx->n > 0)) return fail(GABP_E_INVALID_ARG, "null argument");
     CKS(set_dev(ctx->dev));
     CK(cudaMemsetAsync(&ctx->dstat[1], 0, sizeof(DevStatus), ctx->stream));
-    CK(launch_residual(ctx->L, ctx->a64, ctx->diag64, b, x, r, &ctx->dstat[1], ctx->stream));
+    if (ctx->reordered) {
+        // through the refinement vectors: caller order in, caller order out
+        CKS(ensure_ir(ctx));
+        CK(launch_permute(ctx->n, ctx->d_perm, b, ctx->b0, 0, ctx->stream));
+        CK(launch_permute(ctx->n, ctx->d_perm, x, ctx->xacc, 0, ctx->stream));
+        CK(launch_residual(ctx->L, ctx->a64, ctx->diag64, ctx->b0, ctx->xacc, r ? ctx->rbuf : nullptr,
+                           &ctx->dstat[1], ctx->stream));
+        if (r) CKS(store_vector(ctx, ctx->rbuf, r, ctx->stream));
+    } else {
+        CK(launch_residual(ctx->L, ctx->a64, ctx->diag64, b, x, r, &ctx->dstat[1], ctx->stream));
+    }
     if (rinf || binf) CKS(read_status(ctx, 1, rinf, binf, nullptr));
     return GABP_OK;
 }
@@ -1503,6 +1707,7 @@ gabp_status gabp_get_info(gabp_ctx *ctx, gabp_info *info)
     info->residual_bytes = resid;
     info->device_bytes = ctx->dev_bytes;
     info->parity_layout = ctx->parity ? 1 : 0;
+    info->reordered = ctx->reordered ? 1 : 0;
     // parity-class coloured sweep: per slot a, c, incoming L, M read and L', M'
     // written; per node diag and b read (no aggregates)
     info->colored_sweep_bytes = 6.0 * p * S + 2.0 * p * n;
@@ -1580,6 +1785,9 @@ gabp_status mg_setup(int levels, gabp_ctx *const *level_ctx, const int32_t *grid
         if (level_ctx[l]->dev != level_ctx[0]->dev) return fail(GABP_E_INVALID_ARG, "levels on different devices");
     }
     if (level_ctx[levels - 1]->n > 4096) return fail(GABP_E_INVALID_ARG, "coarsest level above 4096 unknowns");
+    for (int l = 0; l < levels; ++l)
+        if (level_ctx[l]->reordered)
+            return fail(GABP_E_INVALID_ARG, "multigrid levels need the grid numbering (reorder = 0)");
     mg_ctx *mg = new (std::nothrow) mg_ctx;
     if (!mg) return fail(GABP_E_OOM, "host allocation");
     auto bail = [&](gabp_status s) {

@@ -182,6 +182,9 @@ cudaError_t launch_line_mean(int prec, int m, const void *aF, const void *aB, co
 cudaError_t prepare_line_kernels(int prec, int m);
 cudaError_t launch_transpose(int prec, int m, const void *in, void *out, cudaStream_t s);
 cudaError_t launch_to_double(int prec, const void *in, double *out, int64_t n, cudaStream_t s);
+// internal renumbering: out[i] = in[idx[i]] (scatter = 0) or out[idx[i]] = in[i]
+cudaError_t launch_permute(int n, const int *idx, const double *in, double *out, int scatter,
+                           cudaStream_t s);
 // a64, diag64 (and a, c, diagT in the message precision) from CSR values on
 // the device: slotmap[p] = layout slot of entry p (-1 on the diagonal),
 // diagpos[r] = entry index of the diagonal of row r

@@ -953,6 +953,26 @@ cudaError_t launch_dense_gemv(const double *M, const double *x, double *y, int n
     return cudaGetLastError();
 }
 
+// out[i] = in[idx[i]] (gather) or out[idx[i]] = in[i] (scatter), n doubles.
+__global__ void k_permute(int n, const int *__restrict__ idx, const double *__restrict__ in,
+                          double *__restrict__ out, int scatter)
+{
+    const int stride = gridDim.x * blockDim.x;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        if (scatter) out[idx[i]] = in[i];
+        else out[i] = in[idx[i]];
+    }
+}
+
+cudaError_t launch_permute(int n, const int *idx, const double *in, double *out, int scatter,
+                           cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    k_permute<<<grid_for(n, 256), 256, 0, s>>>(n, idx, in, out, scatter);
+    count_launches(s, 1);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_coeffs_from_values(const DevLayout &L, int prec, int64_t nnz,
                                       const int64_t *slotmap, const int64_t *diagpos,
                                       const double *data, double *a64, double *diag64, void *a,

@@ -229,3 +229,62 @@ def test_csr_single_edge_pair(g):
     s = g.GabpSolver(A, "fp64", layout="csr")
     x = host(s.sweep(dev(b), 2))
     assert rel(x, np.linalg.solve(M, b)) <= 1e-15
+
+
+def test_internal_renumbering_is_invisible(g):
+    """Reverse Cuthill-McKee renumbering of a CSR context (gabp_options
+    reorder) is invisible at the interface: on a randomly numbered grid every
+    call returns in the caller's order what the unrenumbered context returns,
+    up to the rounding of a different summation order."""
+    A0, b = P.config_c2(m=48, seed=41)
+    A, perm = P.permute_symmetric(A0, 42)
+    b = b[perm]
+    gv = np.random.default_rng(43).uniform(-1, 1, A.n)
+    ctx = {}
+    for reorder in (0, 1):
+        s = g.GabpSolver(A, "fp64", layout="csr", check_every=1, reorder=reorder)
+        assert s.info()["reordered"] == reorder
+        ctx[reorder] = s
+    out = {}
+    for reorder, s in ctx.items():
+        r = {}
+        x, r["it"], _, st = s.solve(dev(b), 1e-10, 5000)
+        assert st == g.OK
+        r["x"] = host(x)
+        lam, r["itT"], _, stT = s.solve_transpose(dev(gv), 1e-10, 5000)
+        assert stT == g.OK
+        r["lam"] = host(lam)
+        r["x3"] = host(s.sweep(dev(b), 3))
+        L, M = s.get_state()
+        r["L"], r["M"] = host(L), host(M)
+        rt = torch.empty(A.n, dtype=torch.float64, device="cuda")
+        s.residual(dev(b), dev(r["x3"]), rt)  # an O(1) residual (at the solution it is rounding)
+        r["res"] = host(rt)
+        r["dA"] = host(s.edge_grad(dev(r["lam"]), dev(r["x"])))
+        vals = A.data * np.random.default_rng(44).uniform(0.9, 1.1, A.nnz)
+        rows = np.repeat(np.arange(A.n), np.diff(A.indptr))
+        vals[rows == A.indices] = A.data[rows == A.indices] * 1.5  # keep it dominant
+        s.set_values(vals)
+        r["xh"] = host(s.solve(dev(b), 1e-10, 5000)[0])
+        s.set_values(dev(vals))
+        r["xd"] = host(s.solve(dev(b), 1e-10, 5000)[0])
+        s.set_schedule("colored")
+        r["xc"] = host(s.solve(dev(b), 1e-10, 5000)[0])
+        s.set_schedule("flood")
+        sm = g.GabpSolver(A, "fp32_ir", layout="csr", check_every=5, reorder=reorder)
+        r["xm"] = host(sm.solve(dev(b), 1e-10, 20000)[0])
+        out[reorder] = r
+    a, c = out[0], out[1]
+    assert abs(a["it"] - c["it"]) <= 1 and abs(a["itT"] - c["itT"]) <= 1
+    for key in ("x", "lam", "x3", "L", "M", "res", "dA", "xh", "xd", "xc", "xm"):
+        assert rel(c[key], a[key]) <= 1e-9, key
+    with pytest.raises(g.GabpError):
+        ctx[1].set_schedule("lines")
+
+
+def test_renumbered_context_refused_by_multigrid(g):
+    levels, sides, _ = P.config_c2_levels(m_fine=15, m_coarse=7)
+    solvers = [g.GabpSolver(levels[0], "fp64", layout="csr", reorder=1),
+               g.GabpSolver(levels[1], "fp64")]
+    with pytest.raises(g.GabpError):
+        g.Multigrid(solvers, sides)
