@@ -71,17 +71,6 @@ __device__ __forceinline__ T ld_state(const T *p)
     return *p;
 }
 
-// Flood update of row r in the stencil (per-diagonal) layout: slot k*n + r
-// holds the entry (r, r + off[k]); its reverse edge is slot krev[k]*n + s,
-// s = r + off[k].  With a_e = -A_rs, c_e = -A_rs A_sr and the aggregates
-// P = diag + sum L, B = b + sum M of the previous state:
-//     d = P_s - L[rev],  L' = c / d,  M' = a (B_s - M[rev]) / d,
-// and the belief x_r = B_r / P_r of the previous state (Algorithm 1 forms the
-// belief before the update).  All loads of the row are issued before any
-// arithmetic: the reverse-edge gathers use an index clamped into [0, n), so
-// they are always in bounds and need not wait for a_e; a padded slot
-// (a_e == 0) discards what it loaded.  Returns true on a zero or non-finite
-// denominator.
 // The loads of one row of the stencil flood update (below), held in registers.
 template <typename T, int K>
 struct StencilRow {

@@ -588,3 +588,58 @@ def test_line_fixed_point_and_fewer_sweeps():
     xs = np.linalg.solve(A.to_dense(), b)
     assert np.max(np.abs(r["x"] - xs)) / np.max(np.abs(xs)) < 1e-11
     assert r["iters"] < oracle.solve(A, b, 1e-13, 20000)["iters"]
+
+
+# --------------------------------------------------------------------------
+# the oracle V-cycle with the line-GaBP smoother (Algorithm 3 with Algorithm 2
+# sweeps) and the rediscretised 5-point hierarchy
+# --------------------------------------------------------------------------
+def test_c2_levels_are_m_matrices():
+    """Every level of the 5-point hierarchy is a non-singular M-matrix
+    (positive diagonal, non-positive couplings, weak row dominance with strict
+    dominance somewhere), so GaBP converges on it (corollary to Theorem 2)."""
+    levels, sides, _ = P.config_c2_levels(m_fine=63, m_coarse=7)
+    assert sides == [63, 31, 15, 7]
+    for A, m in zip(levels, sides):
+        M = A.to_dense()
+        assert M.shape == (m * m, m * m)
+        off = M - np.diag(np.diag(M))
+        assert np.all(np.diag(M) > 0) and np.all(off <= 0)
+        slack = np.diag(M) - np.abs(off).sum(axis=1)
+        assert np.all(slack >= -1e-12) and np.any(slack > 1e-6)
+
+
+@pytest.mark.parametrize("mode", ["cold", "warm"])
+def test_line_smoothed_vcycle_invariants(mode):
+    """The exact solution is a fixed point of the line-smoothed cycle, and at a
+    fixed precision-message state the cycle is affine in (x, b)."""
+    levels, sides, b = P.config_c2_levels(m_fine=31, m_coarse=7, seed=12)
+    A = levels[0]
+    xs = np.linalg.solve(A.to_dense(), b)
+    mg = oracle.MGOracle(levels, sides, mode=mode, lines=True)
+    np.testing.assert_allclose(mg.vcycle(b, xs.copy(), 1, 1), xs, rtol=0,
+                               atol=1e-12 * np.max(np.abs(xs)))
+    mg.vcycle(b, np.zeros(A.n), 1, 1)
+    rng = np.random.default_rng(1)
+    xa, xb, ba, bb = (rng.normal(size=A.n) for _ in range(4))
+    import copy
+    m1, m2, m3 = copy.deepcopy(mg), copy.deepcopy(mg), copy.deepcopy(mg)
+    va, vb = m1.vcycle(ba, xa, 1, 1), m2.vcycle(bb, xb, 1, 1)
+    vab = m3.vcycle(2.0 * ba - 0.5 * bb, 2.0 * xa - 0.5 * xb, 1, 1)
+    np.testing.assert_allclose(vab, 2.0 * va - 0.5 * vb, rtol=1e-10,
+                               atol=1e-12 * np.max(np.abs(vab)))
+
+
+def test_line_smoother_exact_on_decoupled_rows():
+    """Without vertical couplings every grid row is a tree (a path), so one
+    cold line sweep solves the level exactly (exactness on trees, Sec. 2):
+    a single V(1, 0) cycle from x = 0 returns A^{-1} b, whatever the coarse
+    levels do."""
+    sides = [15, 7, 3]
+    levels = [P.convdiff_9pt_aniso(m, 0.0, (0.9 * 2 ** l, 0.0)) for l, m in enumerate(sides)]
+    M = levels[0].to_dense()
+    assert all(M[i, j] == 0 for i in range(225) for j in range(225) if abs(i - j) >= 15)
+    b = np.random.default_rng(13).uniform(-1, 1, 225)
+    mg = oracle.MGOracle(levels, sides, lines=True)
+    x = mg.vcycle(b, np.zeros(225), 1, 0)
+    np.testing.assert_allclose(x, np.linalg.solve(M, b), rtol=1e-11, atol=1e-13)
