@@ -242,6 +242,42 @@ def run_reference(args):
     return 0
 
 
+def accuracy_vs_fp64(A, b, bd, solvers, ref="fp64"):
+    """Error of every result against the FP64 GaBP solution, outside any timed region.
+
+    The workload matrix is a nonsingular M-matrix (positive diagonal, non-positive
+    couplings, weak row dominance that is strict on the boundary rows), so A^{-1} >= 0
+    and ||A^{-1}||_inf = ||A^{-1} 1||_inf.  With y the FP64 solve of A y = 1,
+    ||A^{-1}||_inf <= ||y||_inf / (1 - ||1 - A y||_inf), and every pair of solutions
+    obeys ||x - x64||_inf <= ||A^{-1}||_inf (||b - A x||_inf + ||b - A x64||_inf).
+    Residuals are taken on the host in FP64 from the returned vectors."""
+    import numpy as np
+    import torch
+
+    bmax = float(np.max(np.abs(b)))
+    xs, rinf = {}, {}
+    for name, s in solvers.items():
+        x, _, _, st = s.solve(bd, TOL, MAX_ITER)
+        xs[name] = x.cpu().numpy()
+        rinf[name] = float(np.max(np.abs(b - A.matvec(xs[name]))))
+    y, _, _, _ = solvers[ref].solve(torch.ones_like(bd), TOL, MAX_ITER)
+    y = y.cpu().numpy()
+    ry = float(np.max(np.abs(1.0 - A.matvec(y))))
+    inv_norm = float(np.max(y)) / (1.0 - ry) if ry < 1.0 else float("inf")
+    x64 = xs[ref]
+    xmax = float(np.max(np.abs(x64)))
+    out = {"x_ref": f"{ref} GaBP solution on this GPU (matches the FP64 oracle per sweep "
+                    "and at convergence in the parity tests)",
+           "norm_inv_A_inf_upper": inv_norm, "min_A_inv_1": float(np.min(y))}
+    for name, x in xs.items():
+        e = {"rr_host": rinf[name] / bmax}
+        if name != ref:
+            e["err_vs_fp64"] = float(np.max(np.abs(x - x64))) / xmax
+            e["err_bound"] = inv_norm * (rinf[name] + rinf[ref]) / xmax
+        out[name] = e
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -387,6 +423,9 @@ def run_ours(args):
                "single_thread": {"value": rate1, "unit": "edge-updates/s", "cores": 1,
                                  "sample": f"{k1} FP64 oracle sweeps of the full system ({dt1:.1f} s)"}}
 
+    acc = accuracy_vs_fp64(A, b, bd, {"fp64": s64, "fp64_frozen_lambda": sfz,
+                                      "mixed": sir, "mixed_lines": sln})
+
     line = {
         "metric": "GaBP directed-edge updates/s (FP64 solve to 1e-10)",
         "value": value,
@@ -415,6 +454,7 @@ def run_ours(args):
             "mixed_speedup_vs_fp64_frozen_lambda": ms_fz_max / ms_ir_max,
             "mixed_lines_ms": ms_ln_max, "mixed_lines_float_sweeps": its_ln[-1],
             "mixed_lines_speedup_vs_fp64": ms64_max / ms_ln_max,
+            "accuracy": acc,
         },
         "roofline": {
             "kernel": "k_sweep_stencil<double,4> (message sweep of the FP64 solve)",

@@ -120,6 +120,38 @@ __device__ __forceinline__ float pow2_inv(int e, float)
     return __int_as_float(f << 23);
 }
 
+// Exact power-of-two prescale of a line.  Between two rescalings the chunk
+// product of kRescaleMask + 1 steps grows like |d|^(kRescaleMask + 1), which
+// leaves the exponent range once |d| passes about 2^31 (float) or 2^127
+// (double).  A line whose first pivot d0 lies outside 2^(+-kScaleSlack) is
+// therefore brought to |d0| in [1, 2): returns sc = 2^-k and sets isc = 2^k,
+// with the shift k clamped so that sc^2 stays representable; otherwise 1.
+template <typename T>
+constexpr int kScaleSlack = sizeof(T) == 8 ? 64 : 12;
+
+__device__ __forceinline__ double line_scale(double d0, double &isc)
+{
+    const int k = expo(d0) - 1023;
+    if (expo(d0) == 0 || expo(d0) == 0x7ff || abs(k) <= kScaleSlack<double>) {
+        isc = 1.0;
+        return 1.0;
+    }
+    const int c = max(-500, min(500, k));
+    isc = __longlong_as_double((long long)(1023 + c) << 52);
+    return __longlong_as_double((long long)(1023 - c) << 52);
+}
+__device__ __forceinline__ float line_scale(float d0, float &isc)
+{
+    const int k = expo(d0) - 127;
+    if (expo(d0) == 0 || expo(d0) == 0xff || abs(k) <= kScaleSlack<float>) {
+        isc = 1.0f;
+        return 1.0f;
+    }
+    const int c = max(-62, min(62, k));
+    isc = __int_as_float((127 + c) << 23);
+    return __int_as_float((127 - c) << 23);
+}
+
 // Rescales a product by the exponent of its larger pivot entry (a or b, the
 // N components of the images of (1, 0, 0) and (0, 1, 0)).  These carry the
 // growth of the pivots; the Y row then holds ratios Y / N = yF / f, bounded by
@@ -219,6 +251,15 @@ __global__ void __launch_bounds__(kLineMaxThreads) k_line_scan(
     // fall in distinct banks; global arrays use plain indices
     const int sh = kSmem ? kPadShift<T> : 31;
     auto ix = [&](int i) -> int { return i + (i >> sh); };
+    // the line's prescale (line_scale): d, the couplings and their products are
+    // taken times sc, the right-hand sides r are not.  The pivots f, g then come
+    // out times sc, while yF, yB, the mean messages and the multipliers aF, aB
+    // are unchanged; every product is exact, so the results are those of the
+    // unscaled recurrences wherever these stay in range.
+    T isc;
+    const T sc = line_scale(m > 0 ? gd[0] + gLo[0] : T(1), isc);
+    const bool scaled = sc != T(1);
+    const T sc2 = sc * sc;
     if (kSmem) {
         const int mp = line_padded(m, kPadShift<T>);
         T *sm = reinterpret_cast<T *>(line_smem);
@@ -227,15 +268,31 @@ __global__ void __launch_bounds__(kLineMaxThreads) k_line_scan(
         T *wl = sm + 2 * (size_t)mp, *wu = sm + 3 * (size_t)mp;
         T *wp = sm + 4 * (size_t)mp, *wq = sm + 5 * (size_t)mp;
         const T *gl = sub + base, *gu = sup + base;
-        for (int i = tid; i < m; i += NT) {
-            const T li = gl[i], ui = gu[i];
-            const int j = ix(i);
-            sd[j] = gd[i] + gLo[i];
-            sr[j] = gb[i] + gMo[i];
-            wl[j] = li;
-            wu[j] = ui;
-            wp[j] = i > 0 ? li * gu[i - 1] : T(0);
-            wq[j] = i + 1 < m ? ui * gl[i + 1] : T(0);
+        // an unscaled double line (the usual case) takes a loop without the
+        // multiplies, which would cost FP64-pipe issue; float always multiplies
+        // (sc = 1 when unscaled)
+        if (sizeof(T) == 8 && !scaled) {
+            for (int i = tid; i < m; i += NT) {
+                const T li = gl[i], ui = gu[i];
+                const int j = ix(i);
+                sd[j] = gd[i] + gLo[i];
+                sr[j] = gb[i] + gMo[i];
+                wl[j] = li;
+                wu[j] = ui;
+                wp[j] = i > 0 ? li * gu[i - 1] : T(0);
+                wq[j] = i + 1 < m ? ui * gl[i + 1] : T(0);
+            }
+        } else {
+            for (int i = tid; i < m; i += NT) {
+                const T li = gl[i], ui = gu[i];
+                const int j = ix(i);
+                sd[j] = (gd[i] + gLo[i]) * sc;
+                sr[j] = gb[i] + gMo[i];
+                wl[j] = li * sc;
+                wu[j] = ui * sc;
+                wp[j] = i > 0 ? (li * gu[i - 1]) * sc2 : T(0);
+                wq[j] = i + 1 < m ? (ui * gl[i + 1]) * sc2 : T(0);
+            }
         }
         sl = wl;
         su = wu;
@@ -252,12 +309,15 @@ __global__ void __launch_bounds__(kLineMaxThreads) k_line_scan(
         sf = fws + base;
         sy = yws + base;
     }
-    auto Dv = [&](int i) -> T { return kSmem ? sd[ix(i)] : gd[i] + gLo[i]; };
+    // staged values carry the prescale already; values read from global memory
+    // (lines too long for shared memory) take it here
+    auto G = [&](T v, T f) -> T { return (!kSmem && scaled) ? v * f : v; };
+    auto Dv = [&](int i) -> T { return kSmem ? sd[ix(i)] : G(gd[i] + gLo[i], sc); };
     auto Rv = [&](int i) -> T { return kSmem ? sr[ix(i)] : gb[i] + gMo[i]; };
-    auto Lv = [&](int i) -> T { return sl[ix(i)]; };
-    auto Uv = [&](int i) -> T { return su[ix(i)]; };
-    auto Pv = [&](int i) -> T { return kSmem ? sp[ix(i)] : (i > 0 ? sl[i] * su[i - 1] : T(0)); };
-    auto Qv = [&](int i) -> T { return kSmem ? sq[ix(i)] : (i + 1 < m ? su[i] * sl[i + 1] : T(0)); };
+    auto Lv = [&](int i) -> T { return G(sl[ix(i)], sc); };
+    auto Uv = [&](int i) -> T { return G(su[ix(i)], sc); };
+    auto Pv = [&](int i) -> T { return kSmem ? sp[ix(i)] : G(i > 0 ? sl[i] * su[i - 1] : T(0), sc2); };
+    auto Qv = [&](int i) -> T { return kSmem ? sq[ix(i)] : G(i + 1 < m ? su[i] * sl[i + 1] : T(0), sc2); };
 
     const int C = (m + NT - 1) / NT;
     const int lo = min(m, tid * C), hi = min(m, lo + C);
@@ -366,29 +426,40 @@ __global__ void __launch_bounds__(kLineMaxThreads) k_line_scan(
             wv = yb * inv;
             const T f = sf[ix(i)], y = sy[ix(i)];
             if (kFreeze) {
-                sinv[base + i] = T(1) / ((f - d) + g);
+                const T si = T(1) / ((f - d) + g);
+                sinv[base + i] = scaled ? si * sc : si;
                 continue;
             }
+            // times sc when the line is prescaled: undone where it is written
             const T lam = (f - d) + (g - d);
             const T mu = (y - r) + (yb - r);
             if (x) {
-                const double xi = (double)(((y - r) + yb) / ((f - d) + g));
+                T xs = ((y - r) + yb) / ((f - d) + g);
+                if (scaled) xs *= sc;
+                const double xi = (double)xs;
                 x[x_transposed ? (size_t)i * m + line : base + i] = xi;
             }
             if (kSmem) {
                 sf[ix(i)] = lam;
                 sy[ix(i)] = mu;
             } else {
-                Lown[base + i] = lam;
+                Lown[base + i] = scaled ? lam * isc : lam;
                 Mown[base + i] = mu;
             }
         }
     }
     if (kSmem && !kFreeze) {
         __syncthreads();
-        for (int i = tid; i < m; i += NT) {
-            Lown[base + i] = sf[ix(i)];
-            Mown[base + i] = sy[ix(i)];
+        if (scaled) {
+            for (int i = tid; i < m; i += NT) {
+                Lown[base + i] = sf[ix(i)] * isc;
+                Mown[base + i] = sy[ix(i)];
+            }
+        } else {
+            for (int i = tid; i < m; i += NT) {
+                Lown[base + i] = sf[ix(i)];
+                Mown[base + i] = sy[ix(i)];
+            }
         }
     }
     if (bad) atomicOr(flags, FLAG_BREAKDOWN);

@@ -599,3 +599,86 @@ def test_fullsize_solve_reaches_1e10(g, c2, precision):
     xh = host(x)
     r = b - A.matvec(xh)  # independent residual on the host
     assert np.max(np.abs(r)) / np.max(np.abs(b)) <= 1.05e-10
+
+
+@pytest.fixture(scope="module")
+def c2_fp64(g, c2):
+    """FP64 GaBP solution of the full-size system, its residual, and an upper bound
+    on ||A^{-1}||_inf from y = A^{-1} 1 (A is an M-matrix, so A^{-1} >= 0 and
+    ||A^{-1}||_inf = ||A^{-1} 1||_inf <= ||y||_inf / (1 - ||1 - A y||_inf))."""
+    A, b = c2
+    s = g.GabpSolver(A, "fp64")
+    x, _, _, st = s.solve(dev(b), 1e-10, 20000)
+    assert st == g.OK
+    y, _, _, st = s.solve(dev(np.ones(A.n)), 1e-10, 20000)
+    assert st == g.OK
+    y = host(y)
+    assert np.min(y) > 0
+    ry = np.max(np.abs(1.0 - A.matvec(y)))
+    xh = host(x)
+    s.close()
+    return xh, np.max(np.abs(b - A.matvec(xh))), np.max(y) / (1.0 - ry)
+
+
+@pytest.mark.parametrize("schedule", ["flood", "lines"])
+def test_fullsize_mixed_solution_within_forward_error_bound(g, c2, c2_fp64, schedule):
+    """The mixed-precision solution differs from the FP64 one by no more than
+    ||A^{-1}||_inf (||r_mixed||_inf + ||r_fp64||_inf), with residuals taken on the host."""
+    A, b = c2
+    x64, r64, inv_norm = c2_fp64
+    s = g.GabpSolver(A, "fp32_ir", check_every=10)
+    if schedule == "lines":
+        s.set_schedule("lines")
+    x, _, rr, st = s.solve(dev(b), 1e-10, 20000)
+    assert st == g.OK
+    xh = host(x)
+    r = np.max(np.abs(b - A.matvec(xh)))
+    assert r / np.max(np.abs(b)) <= 1.05e-10
+    err = np.max(np.abs(xh - x64))
+    assert err <= inv_norm * (r + r64)
+    s.close()
+
+
+# --------------------------------------------------------------------------
+# exponent range of the double-precision reciprocal
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("prec,k", [("fp64", -400), ("fp64", 400), ("fp32", -40), ("fp32", 40)])
+@pytest.mark.parametrize("name,layout,schedule", [
+    ("lognormal_33", "auto", "flood"), ("lognormal_33", "csr", "flood"),
+    ("random_300", "csr", "flood"), ("lognormal_33", "auto", "colored"),
+    ("lognormal_33", "auto", "lines")])
+def test_power_of_two_scaling_is_exact(g, name, layout, schedule, prec, k):
+    """With A, b scaled by s = 2^k the update rules (eq. nonsymmetric_GaBP_rules)
+    scale exactly: c by s^2, a, P, B, d and the stored messages by s, the beliefs
+    not at all.  Every reciprocal then sees a denominator with the same significand
+    and an exponent shifted by k, so in double precision the beliefs are bitwise
+    equal and the messages equal after division by s; k = +-400 takes the
+    denominators across most of the double exponent range.  In float (k = +-40,
+    pivots near 2^52 and 2^-28) the results agree to the float rounding of the
+    hardware reciprocal approximation; the line recurrences, whose products of a
+    few pivots would leave the float range unscaled, must stay finite."""
+    A = MATS[name]
+    b = _rhs(A.n, 3)
+    s = math.ldexp(1.0, k)
+    As = P.CSR(A.n, A.indptr, A.indices, A.data * s)
+    outs = []
+    for M, rhs in ((A, b), (As, b * s)):
+        sv = g.GabpSolver(M, prec, layout=layout)
+        if schedule != "flood":
+            sv.set_schedule(schedule)
+        x = host(sv.sweep(dev(rhs), 20))
+        st = None if schedule == "lines" else tuple(host(t) for t in sv.get_state())
+        outs.append((x, st))
+        sv.close()
+    (x0, st0), (x1, st1) = outs
+    assert np.all(np.isfinite(x0)) and np.all(np.isfinite(x1)) and np.max(np.abs(x0)) > 0
+    if prec == "fp64":
+        np.testing.assert_array_equal(x1, x0)
+    else:
+        assert rel(x1, x0) <= 1e-5
+    if st0 is not None:
+        for u0, u1 in zip(st0, st1):
+            if prec == "fp64":
+                np.testing.assert_array_equal(u1 / s, u0)
+            else:
+                assert rel(u1 / s, u0) <= 1e-5

@@ -643,3 +643,26 @@ def test_line_smoother_exact_on_decoupled_rows():
     mg = oracle.MGOracle(levels, sides, lines=True)
     x = mg.vcycle(b, np.zeros(225), 1, 0)
     np.testing.assert_allclose(x, np.linalg.solve(M, b), rtol=1e-11, atol=1e-13)
+
+
+def test_c2_workload_is_irreducible_m_matrix():
+    """The 2048^2 convection-diffusion matrix has a positive diagonal, strictly
+    negative couplings to all grid neighbours (so its graph is the connected grid)
+    and non-negative row sums, positive on the boundary rows: an irreducibly
+    diagonally dominant M-matrix, hence A^{-1} >= 0 entrywise.  Forward-error
+    bounds on the solution use ||A^{-1}||_inf = ||A^{-1} 1||_inf, which rests on this."""
+    A, _ = P.config_c2()
+    m = 2048
+    rows = np.repeat(np.arange(A.n), np.diff(A.indptr))
+    diag = rows == A.indices
+    assert np.count_nonzero(diag) == A.n and np.all(A.data[diag] > 0)
+    off = ~diag
+    assert np.all(A.data[off] < 0)
+    deg = np.diff(A.indptr) - 1
+    i, j = np.divmod(np.arange(A.n), m)
+    inner = (i > 0) & (i < m - 1) & (j > 0) & (j < m - 1)
+    assert np.all(deg[inner] == 4) and np.all(deg[~inner] < 4)
+    rowsum = np.bincount(rows, weights=A.data, minlength=A.n)
+    scale = np.abs(A.data[diag])
+    assert np.all(rowsum >= -1e-12 * scale)
+    assert np.all(rowsum[~inner] > 1e-6 * scale[~inner])
