@@ -285,3 +285,32 @@ def test_line_tiny_grids(g, m, precision):
     xs, it, rr, st2 = s2.solve(dev(b), 1e-10, 500)
     assert st2 == g.OK and rr <= 1e-10
     assert rel(host(xs), np.linalg.solve(A.to_dense(), b)) <= 1e-9
+
+
+@pytest.mark.parametrize("m", [45, 300, 777, 1100, 2601, 4096])
+def test_line_frozen_float_natural_columns_against_oracle(g, m):
+    """Float frozen sweeps: up to 2048 nodes per line the column family is read
+    and written in the natural node order (one CTA per 8 adjacent columns, a
+    ragged last group at 45, 777, 1100), beyond that through transposes (2601,
+    4096).  After the precision messages froze, one frozen sweep agrees on
+    sampled lines with the oracle's full update of those regions from the same
+    state (Algorithm 2; float rounding and the freeze threshold bound the
+    difference), beliefs included."""
+    A, b = P.config_c2(m=m, seed=m)
+    s = g.GabpSolver(A, "fp32", check_every=5, freeze_lambda=1)
+    s.set_schedule("lines")
+    _, it, _, st = s.solve(dev(b), 1e-30, 600)
+    assert st == g.NOT_CONVERGED and it == 600
+    s.time_sweeps(dev(b), 1, frozen=True)  # raises unless the solve froze Lambda
+    before = {k: host(v) for k, v in s.get_line_state().items()}
+    x = host(s.sweep(dev(b), 1))
+    after = {k: host(v) for k, v in s.get_line_state().items()}
+    cols = (0, m // 2 + 3, m - 1) if m <= 2601 else (5, m - 1)
+    for k in cols:
+        lam, mu, xl = oracle.line_region_update(A, m, b, "col", k, after["LH"], after["MH"])
+        assert rel(_line_slice(after["MV"], m, "col", k), mu) <= 1e-4
+        assert rel(_line_slice(x, m, "col", k), xl) <= 1e-4
+    k = m // 3
+    lam, mu, _ = oracle.line_region_update(A, m, b, "row", k, before["LV"], before["MV"])
+    assert rel(_line_slice(after["MH"], m, "row", k), mu) <= 1e-4
+    s.close()
