@@ -923,18 +923,16 @@ __global__ void k_line_couplings_from_stencil(int n, int m, StencilParams sp,
     }
 }
 
-// Threads per line: chunks of at least m / 64 (double) or m / 128 (float)
-// elements, rounded up to whole warps.  Long chunks keep the scan's share of
-// the work small; double is bound by the FP64 pipe, not by occupancy.
-#ifndef GABP_LINE_NT_F64
-#define GABP_LINE_NT_F64 128
-#endif
-#ifndef GABP_LINE_NT_F32
-#define GABP_LINE_NT_F32 256
-#endif
+// Threads per line: at most 128 (double) or 256 (float), chunks of at least
+// m / 128 or m / 256 elements, rounded up to whole warps.  Long chunks keep the
+// scan's share of the work small; double is bound by the FP64 pipe, not by
+// occupancy.  At 2048 nodes fewer threads per line ran slower (the chunk
+// recurrences are latency-bound) and more added scan work.
+constexpr int kLineThreadsF64 = 128;
+constexpr int kLineThreadsF32 = 256;
 int line_threads(int prec, int m)
 {
-    const int ntmax = prec == 0 ? GABP_LINE_NT_F64 : GABP_LINE_NT_F32;
+    const int ntmax = prec == 0 ? kLineThreadsF64 : kLineThreadsF32;
     const int C = (m + ntmax - 1) / ntmax;
     const int nt = (m + C - 1) / C;
     return ((nt + 31) / 32) * 32;
