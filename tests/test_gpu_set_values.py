@@ -44,12 +44,11 @@ def _pair(m=24, seed=3):
     return A0, A1, m
 
 
-@pytest.mark.parametrize("schedule", ["flood", "colored", "lines"])
-@pytest.mark.parametrize("layout", ["stencil", "csr"])
+# the coloured and line schedules on grids run on the stencil-derived layouts
+@pytest.mark.parametrize("layout,schedule", [("stencil", "flood"), ("csr", "flood"),
+                                             ("stencil", "colored"), ("stencil", "lines")])
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_device_values_equal_host_values(g, precision, layout, schedule):
-    if schedule != "flood" and layout == "csr":
-        pytest.skip("coloured and line schedules on grids use the stencil-derived layouts")
     A0, A1, m = _pair()
     b = np.random.default_rng(1).uniform(-1, 1, A0.n)
     outs = []
