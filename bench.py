@@ -41,7 +41,7 @@ MAX_ITER = 200000
 IR_INNER_MAX = 400    # float sweeps per refinement step (restarting early beats long inner solves)
 # DRAM read + write bytes per launch of k_sweep_stencil<double,4> at 2048 x 2048, measured with
 # ncu (profiles/traffic_sweep_fp64_2048.md); valid for that kernel version and size only.
-TRAFFIC_FP64_SWEEP_2048 = 971.85e6
+TRAFFIC_FP64_SWEEP_2048 = 971.92e6
 SM_COUNT = 152
 FP64_PER_CYCLE = 2    # FP64 arithmetic instructions per cycle per SM (GB300)
 
