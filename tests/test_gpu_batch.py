@@ -186,3 +186,36 @@ def test_batch_sixteen_cta_clusters(g, block):
         xs1, it1, rr1, st1 = single.solve(dev(b), 1e-10, 20000)
         assert st1 == g.OK and it == it1
         assert rel(host(x), host(xs1)) <= 1e-14
+
+
+def test_batch_full_workload(g):
+    """The batched workload as the bench runs it: 512 systems with sides 16..256,
+    float messages inside double refinement, the tuned launch shape, every system
+    to rr <= 1e-6.  Every residual is recomputed on the host; on sampled systems
+    (the largest, the smallest and three at random) the solution lies within the
+    forward-error bound of a sparse direct solve: each system is an M-matrix, so
+    ||A^{-1}||_inf = ||A^{-1} 1||_inf and ||x - x_direct||_inf <=
+    ||A^{-1}||_inf (||r||_inf + ||r_direct||_inf)."""
+    sp = pytest.importorskip("scipy.sparse")
+    spla = pytest.importorskip("scipy.sparse.linalg")
+    systems = P.config_c4_batch(nsys=512, smax=256)
+    solvers = [g.GabpSolver(A, "fp32_ir") for A, _ in systems]
+    bs = [dev(b) for _, b in systems]
+    batch = g.Batch(solvers, check_every=10)
+    batch.tune(bs, 1e-6, 20000)
+    xs, its, rrs, sts = batch.solve(bs, 1e-6, 20000)
+    assert all(s == g.OK for s in sts)
+    xh = [host(x) for x in xs]
+    for (A, b), x in zip(systems, xh):
+        assert np.max(np.abs(b - A.matvec(x))) / np.max(np.abs(b)) <= 1.01e-6
+    sizes = [A.n for A, _ in systems]
+    pick = {int(np.argmax(sizes)), int(np.argmin(sizes))}
+    pick |= set(int(i) for i in np.random.default_rng(3).choice(len(systems), 3, replace=False))
+    for i in sorted(pick):
+        A, b = systems[i]
+        lu = spla.splu(sp.csr_matrix((A.data, A.indices, A.indptr), shape=(A.n, A.n)).tocsc())
+        xd, y = lu.solve(b), lu.solve(np.ones(A.n))
+        assert np.min(y) > 0
+        rb = np.max(np.abs(b - A.matvec(xh[i])))
+        rd = np.max(np.abs(b - A.matvec(xd)))
+        assert np.max(np.abs(xh[i] - xd)) <= np.max(y) * (rb + rd) * (1 + 1e-6)
