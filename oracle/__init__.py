@@ -20,9 +20,11 @@ Messages are stored per CSR slot: the message j -> i lives at the slot of the
 entry (i, j) and holds ``(tilde-Lambda_ji, m_ji)``.
 
 Parity pins for every function are in ``tests/test_oracle_pins.py``; the
-V-cycle composition is pinned only through invariants (fixed point,
-linearity, exact-smoother limit) and the transfer operators through their
-definitions: beyond those, the V-cycle is "parity unpinned".
+V-cycle is pinned through invariants (fixed point, linearity, exact-smoother
+limit), the transfer operators through their definitions, and its whole
+composition through the nu = 1 cold smoother, which is Jacobi: a V(1,1) cycle
+equals an independently written dense Jacobi multigrid recursion.  Its
+convergence rates have no printed values to pin ("parity unpinned").
 """
 from __future__ import annotations
 

@@ -666,3 +666,51 @@ def test_c2_workload_is_irreducible_m_matrix():
     scale = np.abs(A.data[diag])
     assert np.all(rowsum >= -1e-12 * scale)
     assert np.all(rowsum[~inner] > 1e-6 * scale[~inner])
+
+
+def _dense_bilinear(mc):
+    """Bilinear interpolation as a dense (mf^2 x mc^2) matrix written from the hat
+    function: coarse point (I, J) sits at fine (2I+1, 2J+1) (0-based) and gives
+    weight (1 - |dx|/2)(1 - |dy|/2) to the fine points around it."""
+    mf = 2 * mc + 1
+    Pm = np.zeros((mf * mf, mc * mc))
+    for J in range(mc):
+        for I in range(mc):
+            for dy in (-1, 0, 1):
+                for dx in (-1, 0, 1):
+                    Pm[(2 * J + 1 + dy) * mf + 2 * I + 1 + dx, J * mc + I] = \
+                        (1 - abs(dx) / 2) * (1 - abs(dy) / 2)
+    return Pm
+
+
+@pytest.mark.parametrize("family", ["aniso9", "convdiff5"])
+def test_vcycle_composition_is_dense_jacobi_multigrid(family):
+    """A cold GaBP smoother call with nu = 1 is Jacobi, x + D^{-1} r (S1 of
+    Sec. 4.1, pinned above), so the oracle's V(1,1) cycle (Algorithm 3 with the
+    V-cycle) must equal a dense three-level recursion written here from scratch:
+    Jacobi pre-smoothing, the residual restricted by P^T (full weighting = P^T/4,
+    times the transfer scale 4), the same cycle on the next level from zero, an
+    exact solve on the coarsest level, bilinear prolongation P, Jacobi
+    post-smoothing."""
+    if family == "aniso9":
+        levels, sides, b = P.config_c3_levels(m_fine=31, m_coarse=7, seed=8)
+    else:
+        levels, sides, b = P.config_c2_levels(m_fine=31, m_coarse=7, seed=8)
+    assert sides == [31, 15, 7]
+    dense = [A.to_dense() for A in levels]
+    Ps = [_dense_bilinear(sides[l + 1]) for l in range(len(sides) - 1)]
+
+    def cycle(l, rhs, x):
+        M = dense[l]
+        if l == len(dense) - 1:
+            return np.linalg.solve(M, rhs)
+        d = np.diag(M)
+        x = x + (rhs - M @ x) / d
+        ec = cycle(l + 1, Ps[l].T @ (rhs - M @ x), np.zeros(Ps[l].shape[1]))
+        x = x + Ps[l] @ ec
+        return x + (rhs - M @ x) / d
+
+    x0 = np.random.default_rng(9).normal(size=levels[0].n)
+    ref = cycle(0, b, x0)
+    got = oracle.MGOracle(levels, sides, mode="cold").vcycle(b, x0.copy(), 1, 1)
+    np.testing.assert_allclose(got, ref, rtol=1e-11, atol=1e-13 * np.max(np.abs(ref)))
