@@ -151,6 +151,28 @@ class GabpSolver:
 
     ``A`` is any object with ``n``, ``indptr`` (int64), ``indices`` (int32,
     sorted per row) and ``data`` (float64) arrays, e.g. ``problems.CSR``.
+
+    Keyword arguments (the fields of ``gabp_options``):
+
+    * ``precision``: ``"fp64"`` (messages, beliefs, residual in double),
+      ``"fp32"`` (float messages, double residual checks) or ``"fp32_ir"``
+      (float GaBP inside double iterative refinement; solves only);
+    * ``layout``: ``"auto"`` (per-diagonal layout when the matrix has at most
+      16 distinct diagonals), ``"stencil"`` or ``"csr"`` (any pattern);
+    * ``check_every``: sweeps between residual checks of a solve;
+    * ``use_graphs``: replay each chunk of sweeps from a captured CUDA graph;
+    * ``ir_inner_max``, ``ir_inner_tol``: float sweeps per refinement step at
+      most, and the inner relative residual that ends a step (``fp32_ir``);
+    * ``block_size``: threads per block of the sweep kernel (0: the default);
+    * ``freeze_lambda``: precomputed precision messages (Sec. 4.2): 1 on,
+      0 off, -1 on for ``fp32_ir`` and off otherwise;
+    * ``reorder``: CSR layout only: reverse Cuthill-McKee renumbering inside
+      the library (1), none (0), or when it at least halves the mean index
+      distance of coupled unknowns (-1); invisible at the interface;
+    * ``stream``: a ``torch.cuda.Stream`` (default: the current stream).
+
+    The product path has no CPU fallback: without the compiled library, or
+    without a GPU, construction raises.
     """
 
     def __init__(self, A, precision: str = "fp64", layout: str = "auto", check_every: int = 10,
