@@ -714,3 +714,76 @@ def test_vcycle_composition_is_dense_jacobi_multigrid(family):
     ref = cycle(0, b, x0)
     got = oracle.MGOracle(levels, sides, mode="cold").vcycle(b, x0.copy(), 1, 1)
     np.testing.assert_allclose(got, ref, rtol=1e-11, atol=1e-13 * np.max(np.abs(ref)))
+
+
+# --------------------------------------------------------------------------
+# the workload generators discretise the stated operators (truncation error)
+# --------------------------------------------------------------------------
+def _grid_fn(m):
+    h = 1.0 / (m + 1)
+    x = (np.arange(m) + 1) * h
+    X, Y = np.meshgrid(x, x)  # X[iy, ix]
+    return h, X, Y
+
+
+def _truncation(m, make, exact, skip=0):
+    """Largest |A u / h^2 - L u| over the nodes at least `skip` rows from the boundary."""
+    h, X, Y = _grid_fn(m)
+    u = (np.sin(np.pi * X) * np.sin(np.pi * Y)).reshape(-1)  # zero on the Dirichlet boundary
+    A = make(m, h, X, Y)
+    err = (A.matvec(u) / h ** 2 - exact(X, Y).reshape(-1)).reshape(m, m)
+    return np.max(np.abs(err[skip:m - skip, skip:m - skip]))
+
+
+@pytest.mark.parametrize("case", ["laplace", "variable_D", "upwind", "aniso9", "aniso9_upwind"])
+def test_generators_are_consistent_discretisations(case):
+    """Rows times h^2: A u / h^2 tends to -div(D grad u) + v . grad u (5-point,
+    harmonic face means) or -u_xx - eps u_yy + v . grad u (9-point) as h -> 0,
+    at second order without convection and first order with upwind convection
+    (v = hv / h fixed in physical units).  With a variable D the faces on the
+    Dirichlet boundary take the node's own D (the diffusion field is given per
+    node), an O(h) change of one coefficient: consistency is checked off the
+    boundary rows and the boundary convention directly."""
+    pi = np.pi
+    s = lambda X, Y: np.sin(pi * X) * np.sin(pi * Y)
+    ux = lambda X, Y: pi * np.cos(pi * X) * np.sin(pi * Y)
+    uy = lambda X, Y: pi * np.sin(pi * X) * np.cos(pi * Y)
+    vx, vy, eps = 3.0, -2.0, 0.01
+    if case == "laplace":
+        make = lambda m, h, X, Y: P.convdiff_5pt(m, None, (0.0, 0.0))
+        exact = lambda X, Y: 2 * pi ** 2 * s(X, Y)
+        order = 2
+    elif case == "variable_D":
+        Df = lambda X, Y: 1.0 + 0.5 * X + 0.25 * Y * Y
+        make = lambda m, h, X, Y: P.convdiff_5pt(m, Df(X, Y), (0.0, 0.0))
+        # -div(D grad u) = -(D_x u_x + D_y u_y) + D * 2 pi^2 u
+        exact = lambda X, Y: -(0.5 * ux(X, Y) + 0.5 * Y * uy(X, Y)) + Df(X, Y) * 2 * pi ** 2 * s(X, Y)
+        order = 2
+    elif case == "upwind":
+        make = lambda m, h, X, Y: P.convdiff_5pt(m, None, (h * vx, h * vy))
+        exact = lambda X, Y: 2 * pi ** 2 * s(X, Y) + vx * ux(X, Y) + vy * uy(X, Y)
+        order = 1
+    elif case == "aniso9":
+        make = lambda m, h, X, Y: P.convdiff_9pt_aniso(m, eps, (0.0, 0.0))
+        exact = lambda X, Y: (1 + eps) * pi ** 2 * s(X, Y)
+        order = 2
+    else:
+        make = lambda m, h, X, Y: P.convdiff_9pt_aniso(m, eps, (h * vx, h * vy))
+        exact = lambda X, Y: (1 + eps) * pi ** 2 * s(X, Y) + vx * ux(X, Y) + vy * uy(X, Y)
+        order = 1
+    skip = 1 if case == "variable_D" else 0
+    e1, e2 = _truncation(63, make, exact, skip), _truncation(127, make, exact, skip)
+    rate = np.log2(e1 / e2)
+    if case == "variable_D":
+        m = 15
+        h, X, Y = _grid_fn(m)
+        D = Df(X, Y)
+        M = make(m, h, X, Y).to_dense()
+        for iy in range(m):
+            r = iy * m  # the west face of the first node of each grid row lies on the boundary
+            assert M[r, r] == pytest.approx(D[iy, 0] + 2 * D[iy, 0] * D[iy, 1] / (D[iy, 0] + D[iy, 1])
+                                            + (2 * D[iy, 0] * D[iy - 1, 0] / (D[iy, 0] + D[iy - 1, 0]) if iy > 0 else D[iy, 0])
+                                            + (2 * D[iy, 0] * D[iy + 1, 0] / (D[iy, 0] + D[iy + 1, 0]) if iy < m - 1 else D[iy, 0]),
+                                            rel=1e-14)
+    assert e2 < (0.2 if order == 1 else 2e-3) * np.max(np.abs(exact(*_grid_fn(127)[1:])))
+    assert order - 0.25 <= rate <= order + 0.25
