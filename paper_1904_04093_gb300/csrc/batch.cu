@@ -90,14 +90,19 @@ struct ClusterTeam {
     }
     __device__ void sync() { cl.sync(); }
     __device__ unsigned *flags() { return &root->flags; }
-    __device__ double max(double v)
+    // Team maximum of v.  With fl != nullptr also the team's error flags:
+    // read after the first cluster barrier (every flag set before the call is
+    // visible) and before the second (no thread can set one in between), so
+    // every thread of the team gets the same value.
+    __device__ double max(double v, unsigned *fl = nullptr)
     {
         cta_max_partial(v, *sh);
         cl.sync();
         double m = 0.0;
         const unsigned nb = cl.num_blocks();
         for (unsigned r = 0; r < nb; ++r) m = fmax(m, cl.map_shared_rank(sh, r)->red[32]);
-        cl.sync();  // every CTA has read the partials before they are overwritten
+        if (fl) *fl = *(volatile unsigned *)&root->flags;
+        cl.sync();  // every CTA has read the partials and the flags before they change
         return m;
     }
 };
@@ -109,11 +114,13 @@ struct CtaTeam {
     __device__ CtaTeam(BatchShared *s) : sh(s), t0(threadIdx.x), nt(blockDim.x) {}
     __device__ void sync() { __syncthreads(); }
     __device__ unsigned *flags() { return &sh->flags; }
-    __device__ double max(double v)
+    // As ClusterTeam::max: the flags are read between two block barriers.
+    __device__ double max(double v, unsigned *fl = nullptr)
     {
         cta_max_partial(v, *sh);
         __syncthreads();
         const double m = sh->red[32];
+        if (fl) *fl = *(volatile unsigned *)&sh->flags;
         __syncthreads();
         return m;
     }
@@ -180,9 +187,9 @@ __device__ void batch_sweeps(const BatchSys<T> &S, int n, const int *off, const 
 }
 
 // Freezes the precision messages of S once the last sweep changed none of them
-// by more than `rel` times the largest (returns the new frozen state): gains
-// g = a / (P_s - L[rev]) from the current state, both L and both P buffers
-// set to the current ones.
+// by more than `rel` times the largest and no error flag is set (returns the
+// new frozen state): gains g = a / (P_s - L[rev]) from the current state, both
+// L and both P buffers set to the current ones.
 template <typename T, int K, typename Team>
 __device__ bool batch_maybe_freeze(const BatchSys<T> &S, int n, const int *off, const int *krev,
                                    int cur, double rel, Team &tm)
@@ -196,9 +203,10 @@ __device__ bool batch_maybe_freeze(const BatchSys<T> &S, int n, const int *off, 
             dm = fmax(dm, fabs(l1 - (double)__ldcg(Lp + (size_t)k * n + r)));
             lm = fmax(lm, fabs(l1));
         }
-    dm = tm.max(dm);
+    unsigned fl = 0u;
+    dm = tm.max(dm, &fl);
     lm = tm.max(lm);
-    if (!(dm <= rel * lm)) return false;
+    if (fl || !(dm <= rel * lm)) return false;
     T *Lo = cur ? S.L0 : S.L1, *Pc = cur ? S.P1 : S.P0, *Po = cur ? S.P0 : S.P1;
     for (int r = tm.t0; r < n; r += tm.nt) {
 #pragma unroll
@@ -222,6 +230,13 @@ __device__ bool batch_maybe_freeze(const BatchSys<T> &S, int n, const int *off, 
 // Solves system `id` with team `tm` (every thread of the team calls this with
 // the same arguments; all control flow below is uniform across the team).
 //
+// Invariant that keeps it uniform: no branch reads the shared error word
+// `flags` directly.  Threads set bits in it at any time (a breakdown in a
+// sweep, a non-finite residual), and a fast thread may already be sweeping
+// the next chunk while a slow one finishes the previous check; every decision
+// is taken on the snapshot `fl` that tm.max() returns, read between two team
+// barriers and therefore the same in every thread.
+//
 // refine = 0: plain GaBP on A x = b (Algorithm 1).
 // refine = 1: GaBP in the message precision inside double iterative
 // refinement: x accumulates in double, every refinement step solves
@@ -240,6 +255,7 @@ __device__ void solve_system(const BatchSys<T> &S, int id, const double *b, doub
     const int n = S.n, t0 = tm.t0, nt = tm.nt;
     const int *off = tm.sh->off, *krev = tm.sh->krev;
     unsigned *flags = tm.flags();
+    unsigned fl = 0u;  // team-uniform snapshot of *flags (see above)
     // zero messages: P = diag, B = b (plain) or the first refinement rhs b / ||b||
     double bm = 0.0;
     for (int r = t0; r < n; r += nt) bm = fmax(bm, fabs(b[r]));
@@ -271,13 +287,12 @@ __device__ void solve_system(const BatchSys<T> &S, int id, const double *b, doub
             const int kk = min(check_every, max_iter - it);
             batch_sweeps<T, K>(S, n, off, krev, kk, cur, x, tm, frozen);
             it += kk;
-            if (freeze && !frozen && !*flags) frozen = batch_maybe_freeze<T, K>(S, n, off, krev, cur, frz_rel, tm);
+            if (freeze && !frozen) frozen = batch_maybe_freeze<T, K>(S, n, off, krev, cur, frz_rel, tm);
             bool nan = false;
             double rm = batch_residual<T, K>(S, n, off, b, 1.0, x, nullptr, t0, nt, nan);
             if (nan) atomicOr(flags, 2u);
-            rm = tm.max(rm);
+            rm = tm.max(rm, &fl);
             rr = rm / bnorm;
-            const unsigned fl = *flags;
             if (fl & 1u) status = GABP_E_BREAKDOWN;
             else if ((fl & 2u) || !(rr <= 1e8)) status = GABP_E_DIVERGED;
             else if (rr <= tol) status = GABP_OK;
@@ -312,17 +327,17 @@ __device__ void solve_system(const BatchSys<T> &S, int id, const double *b, doub
                 batch_sweeps<T, K>(S, n, off, krev, kk, cur, S.e, tm, frozen);
                 inner += kk;
                 it += kk;
-                if (freeze && !frozen && !*flags)
+                if (freeze && !frozen)
                     frozen = batch_maybe_freeze<T, K>(S, n, off, krev, cur, frz_rel, tm);
                 bool nan = false;
                 double rin = batch_residual<T, K>(S, n, off, S.r, 1.0 / scale, S.e, nullptr, t0,
                                                   nt, nan);
                 if (nan) atomicOr(flags, 2u);
-                rin = tm.max(rin);
-                if (*flags) break;
+                rin = tm.max(rin, &fl);
+                if (fl) break;
                 if (rin <= inner_tol) break;
             }
-            if (*flags & 1u) {
+            if (fl & 1u) {
                 status = GABP_E_BREAKDOWN;
                 break;
             }
@@ -332,10 +347,10 @@ __device__ void solve_system(const BatchSys<T> &S, int id, const double *b, doub
             bool nan = false;
             double rm = batch_residual<T, K>(S, n, off, b, 1.0, x, S.r, t0, nt, nan);
             if (nan) atomicOr(flags, 2u);
-            rm = tm.max(rm);
+            rm = tm.max(rm, &fl);
             rr = rm / bnorm;
             scale = rm;
-            if ((*flags & 2u) || !(rr <= 1e8)) status = GABP_E_DIVERGED;
+            if ((fl & 2u) || !(rr <= 1e8)) status = GABP_E_DIVERGED;
             else if (rr <= tol) status = GABP_OK;
         }
     }

@@ -56,6 +56,7 @@ __all__ = [
     "convdiff_5pt_torch",
     "sparse_random_m_matrix",
     "permute_symmetric",
+    "late_breakdown_tree",
 ]
 
 
@@ -288,6 +289,61 @@ def permute_symmetric(A: CSR, seed: int):
     inv[perm] = np.arange(A.n)
     rows = np.repeat(np.arange(A.n, dtype=np.int64), np.diff(A.indptr))
     return _coo_to_csr(A.n, inv[rows], inv[A.indices.astype(np.int64)], A.data.copy()), perm
+
+
+def late_breakdown_tree(m: int, a: int, x0: int | None = None) -> CSR:
+    """A non-singular 5-point grid matrix on which flood GaBP first meets a
+    zero denominator at sweep ``a + 1``.
+
+    Node ``j = (x0, a)`` has two arms of ``a`` nodes each: one to its left
+    along grid row ``a`` and one above it along grid column ``x0``; a further
+    node ``j + m`` hangs below ``j``.  These ``2a + 2`` nodes form a tree and
+    are coupled to nothing else; every other grid node belongs to a 5-point
+    Laplacian (diagonal 4, couplings -1) among the non-tree nodes.
+
+    Values: arm leaves have diagonal 1, other arm nodes 1.5; along an arm the
+    entry towards ``j`` is -1 and the entry towards the leaf -0.5; ``A_jj = 1``
+    with -0.5 towards both arms, ``A_{j, j+m} = 1``, ``A_{j+m, j} = -1``,
+    ``A_{j+m, j+m} = 2``.  Eliminating an arm from its leaf towards ``j``
+    gives pivots of exactly 1 (``1.5 - 0.5 * 1 / 1``), so the Schur complement
+    of ``j`` with both arms eliminated is ``1 - 2 * 0.5 = 0``: the principal
+    submatrix on the arms and ``j`` is singular, while ``A`` is not.  GaBP on
+    a tree is that elimination (Sec. 2.1-2.2), and the message ``j -> j+m``
+    divides by this pivot once the leaves' information has reached ``j``.
+    Every value and every partial sum of the exact pivots is a short binary
+    fraction, so the zero is exact in float and double.  No ball of the tree
+    around one node is the singular set, so every belief stays finite.
+    """
+    if x0 is None:
+        x0 = a
+    if not (a >= 1 and x0 >= a and x0 < m and a + 1 < m):
+        raise ValueError("need 1 <= a <= x0 < m and a + 1 < m")
+    y0 = a
+    tree = {(x0, y0), (x0, y0 + 1)}
+    tree |= {(x0 - i, y0) for i in range(1, a + 1)}
+    tree |= {(x0, y0 - i) for i in range(1, a + 1)}
+    c = np.zeros((m, m, 5))  # neighbours (0,-1), (-1,0), (0,0), (1,0), (0,1)
+    nb = ((0, (0, -1)), (1, (-1, 0)), (3, (1, 0)), (4, (0, 1)))
+    for y in range(m):
+        for x in range(m):
+            if (x, y) in tree:
+                continue
+            c[y, x, 2] = 4.0
+            for k, (dx, dy) in nb:
+                if 0 <= x + dx < m and 0 <= y + dy < m and (x + dx, y + dy) not in tree:
+                    c[y, x, k] = -1.0
+    for i in range(1, a + 1):
+        # arm along row y0 (towards j: +x), arm along column x0 (towards j: +y)
+        c[y0, x0 - i, 2] = c[y0 - i, x0, 2] = 1.0 if i == a else 1.5
+        c[y0, x0 - i, 3] = c[y0 - i, x0, 4] = -1.0
+        if i < a:
+            c[y0, x0 - i, 1] = c[y0 - i, x0, 0] = -0.5
+    c[y0, x0, 2] = 1.0
+    c[y0, x0, 1] = c[y0, x0, 0] = -0.5
+    c[y0, x0, 4] = 1.0
+    c[y0 + 1, x0, 2] = 2.0
+    c[y0 + 1, x0, 0] = -1.0
+    return stencil_csr(m, _OFF5, c)
 
 
 def paper_toy5_pattern(seed: int = 7) -> CSR:

@@ -162,6 +162,41 @@ def test_batch_faults_stay_per_system(g):
     assert rel(host(xs[0]), xs_) <= 1e-8 and rel(host(xs[3]), xs_) <= 1e-8
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32_ir"])
+@pytest.mark.parametrize("m,shape", [(20, (256, 1)), (96, (256, 2)), (96, (512, 4))])
+def test_batch_breakdown_after_passed_checks(g, prec, m, shape):
+    """A breakdown that first appears after two passed residual checks.
+
+    problems.late_breakdown_tree is a non-singular matrix whose first zero
+    denominator comes at sweep a + 1 = 15 (pinned on the oracle in
+    test_oracle_pins); with checks every 5 sweeps the checks after sweeps 5 and
+    10 pass and the breakdown is set inside the third chunk.  The system
+    returns BREAKDOWN after 15 sweeps, its neighbours in the batch converge to
+    their single-solve results.  At m = 96 the system is solved by a whole
+    cluster (at least 4 rows per cluster thread), at m = 20 by one CTA."""
+    a = 14
+    Ab = P.late_breakdown_tree(m, a, a + 2)
+    bb = np.random.default_rng(5).uniform(-1, 1, Ab.n)
+    ref = oracle.solve(Ab, bb, 1e-12, 100)
+    assert ref["status"] == oracle.BREAKDOWN and ref["iters"] == a + 1
+    Ag, bg = P.config_c1(m=20)
+    systems = [(Ag, bg), (Ab, bb), (Ag, bg)]
+    solvers = [g.GabpSolver(A, prec, layout="stencil", check_every=5) for A, _ in systems]
+    batch = g.Batch(solvers, check_every=5)
+    batch.set_shape(*shape)
+    xs, its, rrs, sts = batch.solve([dev(b) for _, b in systems], 1e-10, 3000)
+    assert sts == [g.OK, g.BREAKDOWN, g.OK]
+    assert its[1] == a + 1
+    single = g.GabpSolver(Ab, prec, layout="stencil", check_every=5)
+    _, it1, _, st1 = single.solve(dev(bb), 1e-10, 3000)
+    assert st1 == g.BREAKDOWN and it1 == a + 1
+    for i in (0, 2):
+        s1 = g.GabpSolver(Ag, prec, layout="stencil", check_every=5)
+        x1, it1, _, st1 = s1.solve(dev(bg), 1e-10, 3000)
+        assert st1 == g.OK and its[i] == it1
+        assert rel(host(xs[i]), host(x1)) <= 1e-14
+
+
 @pytest.mark.parametrize("block", [256, 512])
 def test_batch_sixteen_cta_clusters(g, block):
     """Clusters of 16 CTAs (the non-portable size): systems with at least 4

@@ -193,6 +193,44 @@ def test_computation_tree_brute_force(case):
 # --------------------------------------------------------------------------
 # Sec. 3.4: the printed 7x7 matrix has rho(|R~|) ~ 1.03 and GaBP diverges.
 # --------------------------------------------------------------------------
+@pytest.mark.parametrize("m,a", [(20, 14), (96, 14), (24, 18)])
+def test_late_breakdown_tree_first_breaks_at_sweep_a_plus_one(m, a):
+    """GaBP on a tree is Gaussian elimination (Sec. 2.1-2.2), so a zero pivot of
+    the elimination towards the root is a zero denominator of the message it
+    feeds, and it appears once the information from the farthest leaf has
+    arrived: sweep a + 1 for arms of a nodes.  The pivot itself is checked by
+    dense algebra: the Schur complement of node j with both arms eliminated is
+    0, while A is well conditioned.  Up to sweep a every denominator is non-zero
+    and every belief finite (the oracle's stopping test would pass at any
+    check interval), and the oracle's Algorithm 1 loop stops with BREAKDOWN at
+    sweep a + 1."""
+    x0 = a + 2
+    A = P.late_breakdown_tree(m, a, x0)
+    M = A.to_dense()
+    j = x0 + m * a
+    arms = [x0 - i + m * a for i in range(1, a + 1)] + [x0 + m * (a - i) for i in range(1, a + 1)]
+    S = np.array(arms)
+    schur = M[j, j] - M[j, S] @ np.linalg.solve(M[np.ix_(S, S)], M[S, j])
+    assert abs(schur) <= 1e-12
+    # the tree is coupled to nothing else (A is block diagonal up to the
+    # numbering) and its own block is well conditioned
+    T = np.array(arms + [j, j + m])
+    rest = np.setdiff1d(np.arange(A.n), T)
+    assert not np.any(M[np.ix_(T, rest)]) and not np.any(M[np.ix_(rest, T)])
+    assert np.linalg.cond(M[np.ix_(T, T)]) < 1e3
+    b = np.random.default_rng(5).uniform(-1, 1, A.n)
+    lt, mm = oracle.zero_state(A)
+    for t in range(1, a + 1):
+        x, beta, st = oracle.sweeps(A, b, 1, lt, mm)
+        assert st == oracle.OK, t
+        assert np.all(np.isfinite(x)) and np.min(np.abs(beta)) >= 0.25
+        assert oracle.residual_inf(A, b, x) / np.max(np.abs(b)) <= 10.0
+    x, beta, st = oracle.sweeps(A, b, 1, lt, mm)
+    assert st == oracle.BREAKDOWN
+    r = oracle.solve(A, b, 1e-12, 10 * a)
+    assert r["status"] == oracle.BREAKDOWN and r["iters"] == a + 1
+
+
 def test_paper_7x7_diverges():
     M = np.loadtxt(os.path.join(GOLDEN, "paper_7x7.txt"))
     R = np.abs(M) / np.abs(np.diag(M))[:, None]
