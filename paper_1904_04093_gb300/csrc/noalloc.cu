@@ -87,6 +87,9 @@ __global__ void __launch_bounds__(256) k_sweep_noalloc(
     for (int64_t p = (bad ? hi : lo); p < hi; ++p) {
         const int s = indices[p];
         double lam = 0.0, mu = 0.0;
+        // columns must ascend strictly within the row, or the searches above
+        // and below would miss entries (a duplicate or unsorted row)
+        if (p > lo && s <= indices[p - 1]) bad |= NA_BAD_INDEX;
         if (s < 0 || s >= n) {
             bad |= NA_BAD_INDEX;
         } else if (s != r && data[p] != 0.0) {
@@ -177,7 +180,8 @@ extern "C" gabp_status gabp_sweep_noalloc(int32_t n, int64_t nnz, const int64_t 
     if ((e = cudaMemcpyAsync(&hflags, flags, sizeof(unsigned), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
         (e = cudaStreamSynchronize(s)) != cudaSuccess)
         return fail(GABP_E_CUDA, std::string("status read: ") + cudaGetErrorString(e));
-    if (hflags & NA_BAD_INDEX) return fail(GABP_E_BAD_CSR, "row pointer or column index out of range");
+    if (hflags & NA_BAD_INDEX)
+        return fail(GABP_E_BAD_CSR, "row pointer or column index out of range, or columns not ascending");
     if (hflags & NA_ZERO_DIAG) return fail(GABP_E_ZERO_DIAG, "missing or zero diagonal entry");
     if (hflags & NA_BREAKDOWN) return fail(GABP_E_BREAKDOWN, "zero or non-finite message denominator");
     return GABP_OK;
