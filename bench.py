@@ -39,11 +39,25 @@ if ROOT not in sys.path:
 TOL = 1e-10
 MAX_ITER = 200000
 IR_INNER_MAX = 400    # float sweeps per refinement step (restarting early beats long inner solves)
-# DRAM read + write bytes per launch of k_sweep_stencil<double,4> at 2048 x 2048, measured with
-# ncu (profiles/traffic_sweep_fp64_2048.md); valid for that kernel version and size only.
+# DRAM read + write bytes per launch of k_sweep_stencil<double,4> at 2048 x 2048: the mean of
+# three launches captured with
+#   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum
+#       --clock-control none -k regex:k_sweep_stencil -s 100 -c 3
+#       python bench.py --only fp64 --steps 1 --warmup 3
+# on a GB300.  It holds only for the kernel it was taken on, identified by the SHA-256 of the
+# source that defines it (the per-row update, the kernel and its launcher); the bench reports
+# null once that source differs.
 TRAFFIC_FP64_SWEEP_2048 = 971.92e6
-SM_COUNT = 152
-FP64_PER_CYCLE = 2    # FP64 arithmetic instructions per cycle per SM (GB300)
+TRAFFIC_SOURCES = (("paper_1904_04093_gb300/csrc/sweep_row.cuh", None),
+                   ("paper_1904_04093_gb300/csrc/kernels.cu", "k_sweep_stencil(\n    int n, StencilParams sp"),
+                   ("paper_1904_04093_gb300/csrc/kernels.cu", "cudaError_t launch_sweep(const DevLayout"))
+TRAFFIC_SOURCES_SHA256 = "7e917b46fd25e8badf043a5ae8410e36fb7fef45e659c459f064ac2d185c5e1d"
+# FP64 operations per directed edge of the message update in its stored form (Sec. 2.3 rule):
+# d = P_s - L[rev] (1), 1/d (1), L' = c q (1), B_s - M[rev] (1), M' = a (.) q (2), P' += L',
+# B' += M' (2).  The kernel issues 10 on the FP64 pipe: the reciprocal is the hardware
+# approximation (off the FP64 pipe) plus three FMAs of a Newton-Raphson step.
+FP64_OPS_PER_EDGE = 8
+FP64_ISSUED_PER_EDGE = 10
 
 
 def parse():
@@ -54,6 +68,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--m", type=int, default=2048, help="grid side of the workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="headline line only: skip the short runs of the other workloads")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU sample")
     ap.add_argument("--only", choices=["all", "fp64", "mixed", "sweeps"], default="all",
                     help="profiling runs: time only one solver (no e2e, no CPU sample); "
@@ -144,6 +160,29 @@ class ClockSampler:
         med = sm[len(sm) // 2] if sm else None
         return {"sm_mhz": med, "sm_max_mhz": max(smax) if smax else None,
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def sources_sha256(parts) -> str:
+    """SHA-256 over source texts: a whole file (start None) or the function that begins
+    at `start` up to its closing brace at the start of a line."""
+    import hashlib
+    h = hashlib.sha256()
+    for rel, start in parts:
+        with open(os.path.join(ROOT, rel)) as f:
+            text = f.read()
+        if start is not None:
+            i = text.index(start)
+            text = text[i:text.index("\n}\n", i)]
+        h.update(text.encode())
+    return h.hexdigest()
+
+
+def fp64_sweep_traffic(m: int):
+    """ncu DRAM bytes of one FP64 sweep launch, or None if the workload or the kernel
+    sources differ from the capture's."""
+    if m != 2048 or TRAFFIC_SOURCES_SHA256 is None:
+        return None
+    return TRAFFIC_FP64_SWEEP_2048 if sources_sha256(TRAFFIC_SOURCES) == TRAFFIC_SOURCES_SHA256 else None
 
 
 def measured_peaks():
@@ -265,16 +304,19 @@ def accuracy_vs_fp64(A, b, bd, solvers, ref="fp64"):
     and ||A^{-1}||_inf = ||A^{-1} 1||_inf.  With y the FP64 solve of A y = 1,
     ||A^{-1}||_inf <= ||y||_inf / (1 - ||1 - A y||_inf), and every pair of solutions
     obeys ||x - x64||_inf <= ||A^{-1}||_inf (||b - A x||_inf + ||b - A x64||_inf).
-    Residuals are taken on the host in FP64 from the returned vectors."""
+    Residuals are taken on the host in FP64 from the returned vectors, and by the library
+    (gabp_residual, gabp_residual_2norm) in the infinity norm and the 2-norm."""
     import numpy as np
     import torch
 
     bmax = float(np.max(np.abs(b)))
-    xs, rinf = {}, {}
+    b2 = float(np.linalg.norm(b))
+    xs, rinf, norms = {}, {}, {}
     for name, s in solvers.items():
         x, _, _, st = s.solve(bd, TOL, MAX_ITER)
         xs[name] = x.cpu().numpy()
         rinf[name] = float(np.max(np.abs(b - A.matvec(xs[name]))))
+        norms[name] = s.residual_norms(bd, x)  # the library's infinity and 2-norm residuals
     y, _, _, _ = solvers[ref].solve(torch.ones_like(bd), TOL, MAX_ITER)
     y = y.cpu().numpy()
     ry = float(np.max(np.abs(1.0 - A.matvec(y))))
@@ -285,7 +327,9 @@ def accuracy_vs_fp64(A, b, bd, solvers, ref="fp64"):
                     "and at convergence in the parity tests)",
            "norm_inv_A_inf_upper": inv_norm, "min_A_inv_1": float(np.min(y))}
     for name, x in xs.items():
-        e = {"rr_host": rinf[name] / bmax}
+        e = {"rr_host": rinf[name] / bmax,
+             "rr_2_host": float(np.linalg.norm(b - A.matvec(x))) / b2,
+             "rr_2": norms[name]["rr_2"], "rr_inf": norms[name]["rr_inf"]}
         if name != ref:
             e["err_vs_fp64"] = float(np.max(np.abs(x - x64))) / xmax
             e["err_bound"] = inv_norm * (rinf[name] + rinf[ref]) / xmax
@@ -382,6 +426,9 @@ def run_ours(args):
     mean_ms32 = sir.time_sweeps(bd, nsw, frozen=True) / nsw
     sweep_ms64 = s64.time_sweeps(bd, nsw) / nsw
     sweep_ms32 = sir.time_sweeps(bd, nsw) / nsw
+    # the FP64 pipe's ceiling, measured on this GPU under the same clocks: instructions per SM
+    # cycle of independent fma and add chains (gabp_fp64_peak; mul runs at the same rate)
+    pk = {op: g.fp64_peak(op, 500) for op in ("fma", "add")}
     clocks = sampler.stop() if sampler else None
 
     # end to end through the C ABI with host buffers (copies inside the timed region)
@@ -414,13 +461,17 @@ def run_ours(args):
     ach32 = info32["sweep_bytes"] / (sweep_ms32 / 1e3) / 1e9
     achm64 = info["mean_sweep_bytes"] / (mean_ms64 / 1e3) / 1e9
     achm32 = info32["mean_sweep_bytes"] / (mean_ms32 / 1e3) / 1e9
-    # FP64 sweep: algorithmic FP64 operations per directed edge (Sec. 2.3 rule in the
-    # stored form): d = P - L (1), 1/d (1), L' = c q (1), B - M (1), M' = a (.) q (2),
-    # P' += L', B' += M' (2) = 8; peak = FP64 instructions per cycle x SMs x SM clock
-    sm_mhz = (clocks or {}).get("sm_mhz") or 2070.0
-    fp64_peak = FP64_PER_CYCLE * SM_COUNT * sm_mhz * 1e6 / 1e12  # T ops/s
-    fp64_ops = 8.0 * edges
-    fp64_ach = fp64_ops / (sweep_ms64 / 1e3) / 1e12
+    # FP64 sweep against the measured FP64 pipe: algorithmic operations per directed edge
+    # (FP64_OPS_PER_EDGE) over the launch time; peak = measured instructions per SM cycle x SMs
+    # x the median SM clock of the timed region
+    per_cycle = min(v["per_cycle_per_sm"] for v in pk.values())
+    sms = pk["fma"]["sms"]
+    sm_mhz = (clocks or {}).get("sm_mhz") or pk["fma"]["clock_mhz"]
+    fp64_peak = per_cycle * sms * sm_mhz * 1e6 / 1e12  # T instructions/s
+    fp64_ach = FP64_OPS_PER_EDGE * edges / (sweep_ms64 / 1e3) / 1e12
+    fp64_issued = FP64_ISSUED_PER_EDGE * edges / (sweep_ms64 / 1e3) / 1e12
+    # the general-CSR bytes of the scope table (56 B per directed edge + 44 B per node in FP64)
+    survey_bytes64 = 56.0 * edges + 44.0 * n
 
     if rank != 0:
         if world > 1:
@@ -471,11 +522,18 @@ def run_ours(args):
             "kernel": "k_sweep_stencil<double,4> (message sweep of the FP64 solve)",
             "bound": "alu", "achieved": fp64_ach, "peak": fp64_peak, "unit": "TFLOP/s",
             "frac": fp64_ach / fp64_peak,
-            "traffic": TRAFFIC_FP64_SWEEP_2048 if args.m == 2048 else None,
-            "op_convention": "FP64 arithmetic instructions, add/mul/fma/reciprocal = 1 each; "
-                             "8 per directed edge; peak = 2 per cycle per SM x 152 SMs x median SM clock",
+            "traffic": fp64_sweep_traffic(args.m),
+            "op_convention": f"FP64 operations, add/mul/fma/reciprocal = 1 each, {FP64_OPS_PER_EDGE} "
+                             "per directed edge; peak = measured FP64 instructions per SM cycle "
+                             f"(gabp_fp64_peak: {per_cycle:.4f}) x {sms} SMs x median SM clock of "
+                             "the timed region (measured, not MEASURED_PEAKS.json, which has no FP64 figure)",
+            "issued_per_edge": FP64_ISSUED_PER_EDGE, "issued_frac": fp64_issued / fp64_peak,
+            "fp64_peak_measured": {op: {k: v[k] for k in ("per_cycle_per_sm", "per_second", "clock_mhz", "ms")}
+                                   for op, v in pk.items()},
             "launch_ms": sweep_ms64, "hbm_achieved_GBs": ach64, "hbm_frac": ach64 / peak,
             "bytes_per_launch": info["sweep_bytes"], "hbm_peak_source": f"{peak_kind} hbm_gbs",
+            "survey_bytes_per_launch": survey_bytes64,
+            "hbm_frac_survey_bytes": survey_bytes64 / (sweep_ms64 / 1e3) / 1e9 / peak,
         },
         "roofline_other_kernels": {
             "k_sweep_stencil<float,4>": {"bound": "hbm", "achieved": ach32, "peak": peak, "unit": "GB/s",
@@ -494,10 +552,42 @@ def run_ours(args):
         "clocks": clocks,
         "cpu_baseline": cpu,
     }
+    if world == 1 and not args.no_secondary:
+        for sv in (s64, sfz, sir, sln):
+            sv.close()
+        line["secondary"] = measure_secondary(args)
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def measure_secondary(args):
+    """The other hot-path workloads, each a short run (2 timed steps after 1 warm-up)
+    inside the headline line: the 4095^2 GaBP-smoothed V-cycle, the 512-system batch,
+    the 512^2 differentiable solve, the 2047^2 5-point multigrid, the CSR layout and the
+    coloured / line schedules at 2048^2, under their own clock record."""
+    import copy
+    import torch
+    sub = copy.copy(args)
+    sub.steps, sub.warmup = 2, 1
+    sub.only, sub.schedule, sub.prec, sub.order = "all", "all", "all", "natural"
+    sub.csr_orders = ("natural",)
+    out = {}
+    sampler = ClockSampler(gpu_index_for(0))
+    sampler.start()
+    for name, fn in (("mg_aniso9_4095", measure_mg), ("batch_512", measure_batch),
+                     ("adjoint_512", measure_adjoint), ("mg5_2047", measure_mg5),
+                     ("csr_2048", measure_csr), ("schedules_2048", measure_schedules)):
+        t0 = time.perf_counter()
+        try:
+            out[name] = fn(sub)
+        except Exception as e:  # a failing secondary must not hide the headline line
+            out[name] = {"error": f"{type(e).__name__}: {e}"}
+        out[name]["wall_s"] = time.perf_counter() - t0
+        torch.cuda.empty_cache()
+    out["clocks"] = sampler.stop()
+    return out
 
 
 def _timed_region(fn, steps):
@@ -514,7 +604,7 @@ def _timed_region(fn, steps):
     return e0.elapsed_time(e1) / steps, out
 
 
-def run_batch(args):
+def measure_batch(args):
     """Many convection-diffusion systems (sides 16..smax, log-normal diffusion, cell
     Peclet U[0.1, 2], flow angle U[0, 2 pi)) in one persistent launch, float
     messages inside double refinement, every system to rr <= 1e-6."""
@@ -551,11 +641,16 @@ def run_batch(args):
                          "frac": sweep_bytes / (ms / 1e3) / 1e9 / peak,
                          "note": "lower bound on bytes: mean-message sweep bytes per sweep, residual "
                                  "checks excluded; critical path = the slowest system"}}
-    print(json.dumps(line), flush=True)
+    return line
+
+
+
+def run_batch(args):
+    print(json.dumps(measure_batch(args)), flush=True)
     return 0
 
 
-def run_mg(args):
+def measure_mg(args):
     """GaBP-smoothed V(2,2) cycles on the 9-point anisotropic hierarchy (eps 0.01),
     float smoothing, double residuals and transfers, direct coarse solve; the flood
     smoother (Sec. 2.2) and the 4-colour smoother (Sec. 5.1), each to rr <= 1e-10."""
@@ -590,8 +685,7 @@ def run_mg(args):
         mg.close()
     info = solvers[0].info()  # the colored schedule is the last one set
     if "flood" not in out or "colored" not in out:
-        print(json.dumps({"metric": "GaBP-smoothed multigrid, V(2,2) to rr <= 1e-10", "schedules": out}), flush=True)
-        return 0
+        return {"metric": "GaBP-smoothed multigrid, V(2,2) to rr <= 1e-10", "schedules": out}
     ach_f = info["sweep_bytes"] / (out["flood"]["fine_sweep_ms"] / 1e3) / 1e9
     ach = info["colored_sweep_bytes"] / (out["colored"]["fine_sweep_ms"] / 1e3) / 1e9
     line = {"metric": "GaBP-smoothed multigrid, V(2,2) to rr <= 1e-10", "value": out["colored"]["solve_s"] * 1e3,
@@ -609,11 +703,16 @@ def run_mg(args):
                                "achieved": ach_f, "peak": peak, "unit": "GB/s", "frac": ach_f / peak,
                                "launch_ms": out["flood"]["fine_sweep_ms"],
                                "bytes_per_launch": info["sweep_bytes"]}}
-    print(json.dumps(line), flush=True)
+    return line
+
+
+
+def run_mg(args):
+    print(json.dumps(measure_mg(args)), flush=True)
     return 0
 
 
-def run_mg5(args):
+def measure_mg5(args):
     """GaBP-smoothed V-cycles on the 5-point convection-diffusion hierarchy of the
     headline problem (log-normal diffusion, flow angle 0.3, cell Peclet 1 on the
     finest grid; sides 2^J - 1 from 2047 to 31): red-black and line-GaBP smoothers
@@ -658,11 +757,16 @@ def run_mg5(args):
         line["roofline"] = {"kernel": "k_sweep_parity_std<float,4> (finest level, red-black = 2 launches)",
                             "bound": "hbm", "achieved": c["GBps"], "peak": peak, "unit": "GB/s",
                             "frac": c["GBps"] / peak, "peak_kind": kind}
-    print(json.dumps(line), flush=True)
+    return line
+
+
+
+def run_mg5(args):
+    print(json.dumps(measure_mg5(args)), flush=True)
     return 0
 
 
-def run_schedules(args):
+def measure_schedules(args):
     """The coloured (red-black, Sec. 5.1) and line (Algorithm 2 with grid rows
     and columns as large regions) schedules on the convection-diffusion
     workload: FP64 and mixed precision, each to rr <= 1e-10."""
@@ -716,11 +820,16 @@ def run_schedules(args):
         line["roofline"] = {"kernel": "k_sweep_parity<float,4> (red-black, mixed inner sweeps)",
                             "bound": "hbm", "achieved": cf["sweep_GBps"], "peak": peak,
                             "unit": "GB/s", "frac": cf["sweep_GBps"] / peak, "peak_kind": kind}
-    print(json.dumps(line), flush=True)
+    return line
+
+
+
+def run_schedules(args):
+    print(json.dumps(measure_schedules(args)), flush=True)
     return 0
 
 
-def run_csr(args):
+def measure_csr(args):
     """The convection-diffusion workload on the general CSR layout (edge-parallel
     sweeps with the reverse-edge index), in natural node order and after a
     seeded random symmetric permutation (an unstructured numbering): FP64 and
@@ -740,9 +849,8 @@ def run_csr(args):
         prec = "fp32" if args.prec == "all" else ("fp64" if args.prec == "fp64" else "fp32")
         s = g.GabpSolver(A, prec, layout="csr")
         ms = s.time_sweeps(torch.as_tensor(b, device="cuda"), 6) / 6
-        print(json.dumps({"only": "sweeps", "m": args.m, "order": args.order, "prec": prec,
-                          "sweep_ms": ms, "GBps": s.info()["sweep_bytes"] / (ms / 1e3) / 1e9}))
-        return 0
+        return {"only": "sweeps", "m": args.m, "order": args.order, "prec": prec,
+                "sweep_ms": ms, "GBps": s.info()["sweep_bytes"] / (ms / 1e3) / 1e9}
     out = {}
     for order in ("natural", "permuted"):
         if order == "natural":
@@ -792,7 +900,7 @@ def run_csr(args):
             "config": {"workload": f"convdiff2d_5pt_upwind_lognormal_{args.m}x{args.m}_csr",
                        "orders": "natural = lexicographic grid order; permuted = seeded random "
                                  "symmetric permutation (seed 1002), renumbered internally by "
-                                 "reverse Cuthill-McKee (reorder default)",
+                                 "reverse Cuthill-McKee (reorder default))",
                        "l2": "inputs larger than L2"},
             "time_to_1e-10_ms": {o: {p: out[o][p]["ms"] for p in ("fp64", "fp32_ir")} for o in out},
             "solves": out,
@@ -800,11 +908,16 @@ def run_csr(args):
                          "bound": "hbm", "achieved": f32["sweep_GBps"], "peak": peak, "unit": "GB/s",
                          "frac": f32["sweep_GBps"] / peak, "peak_kind": kind,
                          "bytes_per_launch": f32["sweep_bytes"], "launch_ms": f32["sweep_ms"]}}
-    print(json.dumps(line), flush=True)
+    return line
+
+
+
+def run_csr(args):
+    print(json.dumps(measure_csr(args)), flush=True)
     return 0
 
 
-def run_adjoint(args):
+def measure_adjoint(args):
     """Differentiable solve at 512^2: forward (mixed) + adjoint (mixed) + edge gradient."""
     import math as _m
     import numpy as np
@@ -852,7 +965,12 @@ def run_adjoint(args):
             "schedules": per,
             "note": "host wall clock of the whole step: GPU assembly of A(theta), forward solve, "
                     "adjoint solve, edge gradient and the chain to theta"}
-    print(json.dumps(line), flush=True)
+    return line
+
+
+
+def run_adjoint(args):
+    print(json.dumps(measure_adjoint(args)), flush=True)
     return 0
 
 

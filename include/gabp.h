@@ -239,6 +239,18 @@ gabp_status gabp_residual(gabp_ctx *ctx, const double *b, const double *x, doubl
                           double *rinf, double *binf);
 
 /*
+ * 2-norms of the residual and of the right-hand side: *r2 = ||b - A x||_2,
+ * *b2 = ||b||_2 (host doubles), logged beside the infinity norm that
+ * Algorithm 1 stops on.  The residual is formed in double as in
+ * gabp_residual; the sums of squares run over a fixed partition of the
+ * unknowns in a fixed order, so repeated calls give identical results.
+ * Synchronises the context's stream.  Errors: GABP_E_INVALID_ARG, GABP_E_OOM,
+ * GABP_E_CUDA.
+ */
+gabp_status gabp_residual_2norm(gabp_ctx *ctx, const double *b, const double *x, double *r2,
+                                double *b2);
+
+/*
  * Copies the message state out (device arrays in setup slot order, as
  * double): lam[p] = tilde-Lambda_ji A_ji (the message's correction to the
  * diagonal of row i) and m[p] = m_ji for the slot p of entry (i, j).  Either
@@ -279,6 +291,35 @@ gabp_status gabp_get_info(gabp_ctx *ctx, gabp_info *info);
 gabp_status gabp_time_sweeps(gabp_ctx *ctx, const double *b, int nsweeps, int frozen, float *ms);
 
 /*
+ * Measured FP64 instruction throughput of the current device, the ceiling of
+ * the double message sweep (which is bound by the FP64 pipe, not by HBM).  No
+ * counterpart in the paper, whose cost model counts serial FLOPs only
+ * (Sec. 4.2).  One resident wave of blocks, each thread running eight
+ * independent chains of `iters` x 16 instructions of one kind: op 0 = fma,
+ * 1 = add, 2 = mul, 3 = rcp.approx.ftz.f64.  Every block records its SM and
+ * the SM cycle counter, so per_cycle_per_sm does not depend on the clock;
+ * per_second comes from CUDA events around the launch and clock_mhz =
+ * per_second / (per_cycle_per_sm x sms).  Allocates and frees small scratch
+ * buffers and its own stream, synchronises the device's work on that stream.
+ * Errors: GABP_E_INVALID_ARG (op outside 0..3, iters < 1, out NULL),
+ * GABP_E_CUDA.
+ */
+typedef struct {
+    int sms;                     /* SMs of the device */
+    int sms_seen;                /* SMs that ran a block of the wave */
+    int blocks;                  /* blocks launched (one wave) */
+    float ms;                    /* device time of the timed launch */
+    double instructions;         /* instructions of the kind retired in the timed launch */
+    double per_cycle_per_sm;     /* mean over SMs of instructions per SM cycle */
+    double per_cycle_per_sm_min; /* slowest SM */
+    double per_cycle_per_sm_max; /* fastest SM */
+    double per_second;           /* instructions per second of the whole device */
+    double clock_mhz;            /* SM clock implied by the two rates */
+} gabp_peak_result;
+
+gabp_status gabp_fp64_peak(int op, int iters, gabp_peak_result *out);
+
+/*
  * The paper has no counterpart to this entry point: it serves callers that
  * cannot allocate device memory (code that runs while another component owns
  * every allocation, such as a framework's memory arena or a loop that forbids
@@ -292,13 +333,16 @@ gabp_status gabp_time_sweeps(gabp_ctx *ctx, const double *b, int nsweeps, int fr
  * loading the library holds until the process exits, so n <= 65536 and
  * nnz <= 262144; larger sizes return GABP_E_INVALID_ARG without launching.
  * The first call on a device looks up that array's address
- * (cudaGetSymbolAddress); make it before any stream capture.  Every call
- * shares the one array and leaves its last contents there (each call starts
- * from zero messages and clears the error word itself), so calls whose work
- * overlaps on the GPU race and give undefined results.  Enqueued on `stream`
- * (a cudaStream_t, NULL = default), then synchronised to read the status:
- * GABP_E_BAD_CSR / GABP_E_ZERO_DIAG for an index out of range or a missing
- * diagonal found on the device, GABP_E_BREAKDOWN as in gabp_sweep.
+ * (cudaGetSymbolAddress); make that first call before any stream capture
+ * begins.  Every call shares the one array and leaves its last contents there
+ * (each call starts from zero messages and clears the error word itself), so
+ * calls whose work overlaps on the GPU (other streams, other host threads)
+ * race and give undefined results.  Each call is synchronous: it enqueues its
+ * sweeps on `stream` (a cudaStream_t, NULL = default), copies the error word
+ * to host memory and synchronises `stream` before it returns the status:
+ * GABP_E_BAD_CSR for a row pointer or column index out of range or columns
+ * not strictly ascending in a row, GABP_E_ZERO_DIAG for a missing or zero
+ * diagonal, both found on the device, and GABP_E_BREAKDOWN as in gabp_sweep.
  */
 gabp_status gabp_sweep_noalloc(int32_t n, int64_t nnz, const int64_t *indptr,
                                const int32_t *indices, const double *data, const double *b,

@@ -17,7 +17,7 @@ from . import build as _build
 
 __all__ = [
     "GabpError", "GabpSolver", "Multigrid", "Batch", "load", "library_path", "STATUS",
-    "OK", "BREAKDOWN", "DIVERGED", "NOT_CONVERGED",
+    "OK", "BREAKDOWN", "DIVERGED", "NOT_CONVERGED", "fp64_peak",
 ]
 
 OK, INVALID_ARG, BAD_CSR, ZERO_DIAG, BREAKDOWN, DIVERGED, NOT_CONVERGED, CUDA_ERR, OOM = range(9)
@@ -51,6 +51,14 @@ class Info(ctypes.Structure):
                 ("residual_bytes", ctypes.c_double), ("device_bytes", ctypes.c_size_t),
                 ("parity_layout", ctypes.c_int), ("colored_sweep_bytes", ctypes.c_double),
                 ("reordered", ctypes.c_int)]
+
+
+class PeakResult(ctypes.Structure):
+    _fields_ = [("sms", ctypes.c_int), ("sms_seen", ctypes.c_int), ("blocks", ctypes.c_int),
+                ("ms", ctypes.c_float), ("instructions", ctypes.c_double),
+                ("per_cycle_per_sm", ctypes.c_double), ("per_cycle_per_sm_min", ctypes.c_double),
+                ("per_cycle_per_sm_max", ctypes.c_double), ("per_second", ctypes.c_double),
+                ("clock_mhz", ctypes.c_double)]
 
 
 _lib = None
@@ -89,10 +97,12 @@ def load() -> ctypes.CDLL:
         "gabp_solve_transpose": (I, [P, P, P, D, I, PI, PD]),
         "gabp_edge_grad": (I, [P, P, P, P]),
         "gabp_residual": (I, [P, P, P, P, PD, PD]),
+        "gabp_residual_2norm": (I, [P, P, P, PD, PD]),
         "gabp_get_state": (I, [P, P, P]),
         "gabp_set_state": (I, [P, P, P]),
         "gabp_get_info": (I, [P, ctypes.POINTER(Info)]),
         "gabp_time_sweeps": (I, [P, P, I, I, PF]),
+        "gabp_fp64_peak": (I, [I, I, ctypes.POINTER(PeakResult)]),
         "mg_setup": (I, [I, ctypes.POINTER(P), ctypes.POINTER(ctypes.c_int32), D, I, P, ctypes.POINTER(P)]),
         "mg_vcycle": (I, [P, I, I, I, P, P]),
         "mg_solve": (I, [P, P, P, D, I, I, I, PI, PD]),
@@ -115,6 +125,17 @@ def load() -> ctypes.CDLL:
 def launch_count() -> int:
     """Kernel launches the library has enqueued in this process so far."""
     return int(load().gabp_launch_count())
+
+
+_PEAK_OPS = {"fma": 0, "add": 1, "mul": 2, "rcp": 3}
+
+
+def fp64_peak(op: str = "fma", iters: int = 1000) -> dict:
+    """Measured FP64 instruction throughput of the current device (gabp_fp64_peak):
+    instructions per SM cycle (clock-independent), per second, and the implied clock."""
+    r = PeakResult()
+    _check(load().gabp_fp64_peak(_PEAK_OPS[op], int(iters), ctypes.byref(r)))
+    return {f: getattr(r, f) for f, _ in PeakResult._fields_}
 
 
 def _err(st: int) -> GabpError:
@@ -313,6 +334,16 @@ class GabpSolver:
         _check(load().gabp_residual(self._h, _dev_vec(b, self.n, "b"), _dev_vec(x, self.n, "x"),
                                     rp, ctypes.byref(rinf), ctypes.byref(binf)))
         return r, float(rinf.value), float(binf.value)
+
+    def residual_norms(self, b, x) -> dict:
+        """Relative residual of ``x`` in the infinity norm (the stopping quantity of
+        Algorithm 1) and in the 2-norm: ``{"rr_inf": ..., "rr_2": ...}``."""
+        _, rinf, binf = self.residual(b, x)
+        r2, b2 = ctypes.c_double(), ctypes.c_double()
+        _check(load().gabp_residual_2norm(self._h, _dev_vec(b, self.n, "b"), _dev_vec(x, self.n, "x"),
+                                          ctypes.byref(r2), ctypes.byref(b2)))
+        return {"rr_inf": rinf / binf if binf > 0 else 0.0,
+                "rr_2": r2.value / b2.value if b2.value > 0 else 0.0}
 
     def get_state(self):
         torch = _torch()

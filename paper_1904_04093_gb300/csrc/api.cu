@@ -104,6 +104,7 @@ struct gabp_ctx {
     double *bres = nullptr;   // rhs of the residual checks (double)
     double *xbuf = nullptr;   // beliefs of the last sweep of a chunk
     double *b0 = nullptr, *xacc = nullptr, *rbuf = nullptr;  // refinement (lazy)
+    double *sq_part = nullptr, *h_sq_part = nullptr;         // 2-norm partial sums (lazy)
     void *g = nullptr;           // frozen mean-message gains a_e / d_e (lazy)
     unsigned char *color = nullptr;  // coloured schedule (lazy); ncolors == 0: flood
     int ncolors = 0;
@@ -1266,6 +1267,7 @@ void gabp_destroy(gabp_ctx *ctx)
     for (auto &g : ctx->graphs) cudaGraphExecDestroy(g.exec);
     free_all(ctx->allocs);
     if (ctx->hstat) cudaFreeHost(ctx->hstat);
+    if (ctx->h_sq_part) cudaFreeHost(ctx->h_sq_part);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
@@ -1625,6 +1627,46 @@ gabp_status gabp_residual(gabp_ctx *ctx, const double *b, const double *x, doubl
         CK(launch_residual(ctx->L, ctx->a64, ctx->diag64, b, x, r, &ctx->dstat[1], ctx->stream));
     }
     if (rinf || binf) CKS(read_status(ctx, 1, rinf, binf, nullptr));
+    return GABP_OK;
+}
+
+gabp_status gabp_residual_2norm(gabp_ctx *ctx, const double *b, const double *x, double *r2,
+                                double *b2)
+{
+    if (!ctx || ((!b || !x) && ctx->n > 0) || !r2 || !b2) return fail(GABP_E_INVALID_ARG, "null argument");
+    CKS(set_dev(ctx->dev));
+    *r2 = *b2 = 0.0;
+    if (ctx->n == 0) return GABP_OK;
+    CKS(ensure_ir(ctx));
+    const size_t pbytes = 2 * (size_t)kSumsqBlocks * sizeof(double);
+    if (!ctx->sq_part) CKS(dalloc(ctx, (void **)&ctx->sq_part, pbytes));
+    if (!ctx->h_sq_part) {
+        cudaError_t e = cudaMallocHost(&ctx->h_sq_part, pbytes);
+        if (e != cudaSuccess) {
+            ctx->h_sq_part = nullptr;
+            return fail_cuda(e, "cudaMallocHost");
+        }
+    }
+    // r = b - A x in the internal order (rbuf); b in the same order (b0)
+    CK(cudaMemsetAsync(&ctx->dstat[1], 0, sizeof(DevStatus), ctx->stream));
+    const double *bi = b, *xi = x;
+    if (ctx->reordered) {
+        CK(launch_permute(ctx->n, ctx->d_perm, b, ctx->b0, 0, ctx->stream));
+        CK(launch_permute(ctx->n, ctx->d_perm, x, ctx->xacc, 0, ctx->stream));
+        bi = ctx->b0;
+        xi = ctx->xacc;
+    }
+    CK(launch_residual(ctx->L, ctx->a64, ctx->diag64, bi, xi, ctx->rbuf, &ctx->dstat[1], ctx->stream));
+    CK(launch_sumsq2(ctx->rbuf, bi, ctx->n, ctx->sq_part, kSumsqBlocks, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->h_sq_part, ctx->sq_part, pbytes, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    double sr = 0.0, sb = 0.0;
+    for (int i = 0; i < kSumsqBlocks; ++i) {
+        sr += ctx->h_sq_part[2 * i];
+        sb += ctx->h_sq_part[2 * i + 1];
+    }
+    *r2 = std::sqrt(sr);
+    *b2 = std::sqrt(sb);
     return GABP_OK;
 }
 

@@ -106,6 +106,10 @@ cudaError_t launch_residual(const DevLayout &L, const double *a64, const double 
                             const double *b, const double *x, double *r, DevStatus *st,
                             cudaStream_t s);
 cudaError_t launch_convert_d2f(const double *in, float *out, int64_t n, cudaStream_t s);
+// per-block partial sums of u^2 and v^2 (part: 2 * nblocks doubles), a fixed order on every call
+constexpr int kSumsqBlocks = 1024;
+cudaError_t launch_sumsq2(const double *u, const double *v, int64_t n, double *part, int nblocks,
+                          cudaStream_t s);
 cudaError_t launch_copy_vec(const double *in, double *out, int64_t n, cudaStream_t s);
 // out = in / ||in||_inf (scale read from st->rmax) in double, and as precision prec into outT
 cudaError_t launch_scale_rhs(const double *in, const DevStatus *st, double *out, void *outT,

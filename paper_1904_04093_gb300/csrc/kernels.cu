@@ -831,6 +831,44 @@ cudaError_t launch_residual(const DevLayout &L, const double *a64, const double 
     return cudaGetLastError();
 }
 
+// Per-block partial sums of u^2 and v^2 over a fixed grid-stride partition:
+// part[2 * block] = sum u_i^2, part[2 * block + 1] = sum v_i^2, each in the
+// same order on every call (thread sums, then a fixed tree in shared memory).
+__global__ void __launch_bounds__(256) k_sumsq2(const double *__restrict__ u,
+                                                const double *__restrict__ v, int64_t n,
+                                                double *__restrict__ part)
+{
+    __shared__ double su[256], sv[256];
+    double a = 0.0, c = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        a = fma(u[i], u[i], a);
+        c = fma(v[i], v[i], c);
+    }
+    su[threadIdx.x] = a;
+    sv[threadIdx.x] = c;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) {
+            su[threadIdx.x] += su[threadIdx.x + w];
+            sv[threadIdx.x] += sv[threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        part[2 * blockIdx.x] = su[0];
+        part[2 * blockIdx.x + 1] = sv[0];
+    }
+}
+
+cudaError_t launch_sumsq2(const double *u, const double *v, int64_t n, double *part, int nblocks,
+                          cudaStream_t s)
+{
+    k_sumsq2<<<nblocks, 256, 0, s>>>(u, v, n, part);
+    count_launches(s, 1);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_convert_d2f(const double *in, float *out, int64_t n, cudaStream_t s)
 {
     if (n == 0) return cudaSuccess;

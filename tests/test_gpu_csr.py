@@ -8,14 +8,16 @@ rows without off-diagonal entries, sizes that leave a ragged last block, and
 full-size grids in natural and in randomly permuted node order.
 
 Tolerances as in the other parity tests: one sweep from an identical state
-<= 1e-12 relative, trajectories and converged solutions <= 1e-10 (double);
-float messages within 1e-5 of the oracle after 50 sweeps.
+<= 1e-12 relative, normwise and element by element (tests/parity_util.py),
+trajectories and converged solutions <= 1e-10 (double); float messages within
+1e-5 of the oracle after 50 sweeps.
 """
 import numpy as np
 import pytest
 
 import oracle
 import problems as P
+from parity_util import sweep_scales, worst_elementwise
 
 pytestmark = pytest.mark.gpu
 
@@ -91,17 +93,22 @@ def test_single_sweep_from_injected_state(g, name):
     oracle.sweeps(A, _rhs(A.n, 2), 3, lt, mm)
     edge = (A.data != 0) & (np.repeat(np.arange(A.n), np.diff(A.indptr)) != A.indices)
     mm = np.where(edge, np.random.default_rng(3).uniform(-1, 1, A.nnz), 0.0)
-    x_o, _ = oracle.beliefs(A, b, lt, mm)
+    x_o, beta_o = oracle.beliefs(A, b, lt, mm)
     lt2, mm2, st = oracle.update(A, b, lt, mm)
     assert st == oracle.OK
+    lc, lc2 = oracle.diag_contrib(A, lt), oracle.diag_contrib(A, lt2)
     s = g.GabpSolver(A, "fp64", layout="csr")
     assert s.info()["layout"] == "csr"
-    s.set_state(dev(oracle.diag_contrib(A, lt)), dev(mm))
+    s.set_state(dev(lc), dev(mm))
     x = s.sweep(dev(b), 1)
     lam, m = s.get_state()
     assert rel(host(x), x_o) <= 1e-12
-    assert rel(host(lam), oracle.diag_contrib(A, lt2)) <= 1e-12
+    assert rel(host(lam), lc2) <= 1e-12
     assert rel(host(m), mm2) <= 1e-12
+    sx, sl, sm = sweep_scales(A, b, lc, mm, x_o, beta_o, lc2, mm2)
+    assert worst_elementwise(host(x), x_o, sx) <= 1e-12
+    assert worst_elementwise(host(lam), lc2, sl) <= 1e-12
+    assert worst_elementwise(host(m), mm2, sm) <= 1e-12
     s.close()
 
 
@@ -192,14 +199,22 @@ def test_fullsize_csr_first_sweeps_elementwise(g, c2, order):
         A, perm = P.permute_symmetric(A, 1002)
         b = b[perm]
     lt, mm = oracle.zero_state(A)
-    x_o, _, _ = oracle.sweeps(A, b, 3, lt, mm)
+    oracle.sweeps(A, b, 2, lt, mm)
+    x_o, beta_o = oracle.beliefs(A, b, lt, mm)
+    lt3, mm3, st = oracle.update(A, b, lt, mm)
+    assert st == oracle.OK
+    lc, lc3 = oracle.diag_contrib(A, lt), oracle.diag_contrib(A, lt3)
+    sx, sl, sm = sweep_scales(A, b, lc, mm, x_o, beta_o, lc3, mm3)
     s = g.GabpSolver(A, "fp64", layout="csr")
     assert s.info()["layout"] == "csr"
     x = host(s.sweep(dev(b), 3))
-    lam, m = s.get_state()
+    lam, m = (host(t) for t in s.get_state())
     assert rel(x, x_o) <= 1e-12
-    assert rel(host(m), mm) <= 1e-12
-    assert rel(host(lam), oracle.diag_contrib(A, lt)) <= 1e-12
+    assert rel(m, mm3) <= 1e-12
+    assert rel(lam, lc3) <= 1e-12
+    assert worst_elementwise(x, x_o, sx) <= 1e-12
+    assert worst_elementwise(lam, lc3, sl) <= 1e-12
+    assert worst_elementwise(m, mm3, sm) <= 1e-12
     s.close()
 
 

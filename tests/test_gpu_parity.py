@@ -1,9 +1,11 @@
 """GPU parity: the CUDA library through its C ABI against the FP64 CPU oracle.
 
 Tolerances (double precision): one sweep from an identical state <= 1e-12
-relative (max-norm error over the max-norm of the oracle's value), a
-50-sweep trajectory <= 1e-10, converged solutions <= 1e-10.  Float results
-state their error against the oracle in the assertion bounds.
+relative, both normwise (max-norm error over the max-norm of the oracle's
+value) and element by element (every output within 1e-12 of the magnitude of
+the terms it is computed from, tests/parity_util.py); a 50-sweep trajectory
+<= 1e-10, converged solutions <= 1e-10.  Float results state their error
+against the oracle in the assertion bounds.
 """
 import math
 
@@ -12,6 +14,7 @@ import pytest
 
 import oracle
 import problems as P
+from parity_util import sweep_scales, worst_elementwise
 
 pytestmark = pytest.mark.gpu
 
@@ -85,13 +88,18 @@ def test_single_sweep_from_injected_state(g, name, layout):
     x_o, beta_o = oracle.beliefs(A, b, lt, mm)
     lt2, mm2, st = oracle.update(A, b, lt, mm)
     assert st == oracle.OK
+    lc, lc2 = oracle.diag_contrib(A, lt), oracle.diag_contrib(A, lt2)
     s = g.GabpSolver(A, "fp64", layout=layout)
-    s.set_state(dev(oracle.diag_contrib(A, lt)), dev(mm))
+    s.set_state(dev(lc), dev(mm))
     x = s.sweep(dev(b), 1)
     lam, m = s.get_state()
     assert rel(host(x), x_o) <= 1e-12
-    assert rel(host(lam), oracle.diag_contrib(A, lt2)) <= 1e-12
+    assert rel(host(lam), lc2) <= 1e-12
     assert rel(host(m), mm2) <= 1e-12
+    sx, sl, sm = sweep_scales(A, b, lc, mm, x_o, beta_o, lc2, mm2)
+    assert worst_elementwise(host(x), x_o, sx) <= 1e-12
+    assert worst_elementwise(host(lam), lc2, sl) <= 1e-12
+    assert worst_elementwise(host(m), mm2, sm) <= 1e-12
     s.close()
 
 
@@ -577,17 +585,34 @@ def c2():
     return P.config_c2()
 
 
-def test_fullsize_first_sweeps_elementwise(g, c2):
-    A, b = c2
+def _third_sweep(A, b):
+    """Oracle beliefs of sweep 3 and the state after it, with the element-wise
+    scales of that sweep (taken from the state after two sweeps)."""
     lt, mm = oracle.zero_state(A)
-    x_o, _, _ = oracle.sweeps(A, b, 3, lt, mm)
+    oracle.sweeps(A, b, 2, lt, mm)
+    x_o, beta_o = oracle.beliefs(A, b, lt, mm)
+    lt3, mm3, st = oracle.update(A, b, lt, mm)
+    assert st == oracle.OK
+    lc, lc3 = oracle.diag_contrib(A, lt), oracle.diag_contrib(A, lt3)
+    return x_o, lc3, mm3, sweep_scales(A, b, lc, mm, x_o, beta_o, lc3, mm3)
+
+
+def test_fullsize_first_sweeps_elementwise(g, c2):
+    """Three sweeps of the 2048^2 workload: beliefs, precision and mean messages
+    against the oracle, normwise and element by element."""
+    A, b = c2
+    x_o, lc3, mm3, (sx, sl, sm) = _third_sweep(A, b)
     s = g.GabpSolver(A, "fp64")
     assert s.info()["layout"] == "stencil"
     x = host(s.sweep(dev(b), 3))
-    lam, m = s.get_state()
+    lam, m = (host(t) for t in s.get_state())
     assert rel(x, x_o) <= 1e-12
-    assert rel(host(m), mm) <= 1e-12
-    del lam, m
+    assert rel(lam, lc3) <= 1e-12
+    assert rel(m, mm3) <= 1e-12
+    assert worst_elementwise(x, x_o, sx) <= 1e-12
+    assert worst_elementwise(lam, lc3, sl) <= 1e-12
+    assert worst_elementwise(m, mm3, sm) <= 1e-12
+    s.close()
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32_ir"])
@@ -682,3 +707,25 @@ def test_power_of_two_scaling_is_exact(g, name, layout, schedule, prec, k):
                 np.testing.assert_array_equal(u1 / s, u0)
             else:
                 assert rel(u1 / s, u0) <= 1e-5
+
+
+# --------------------------------------------------------------------------
+# the 2-norm residual logged beside the infinity norm
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("layout,reorder", [("auto", -1), ("csr", 1)])
+def test_residual_2norm(g, layout, reorder):
+    """gabp_residual_2norm against the host: ||b - A x||_2 / ||b||_2 of an
+    iterate far from convergence (no cancellation, so the two agree to rounding),
+    bitwise repeatable, and the same through an internally renumbered context."""
+    A = MATS["random_300"] if layout == "csr" else MATS["lognormal_33"]
+    b = _rhs(A.n, 8)
+    s = g.GabpSolver(A, "fp64", layout=layout, reorder=reorder)
+    x = s.sweep(dev(b), 4)
+    xh = host(x)
+    ref = np.linalg.norm(b - A.matvec(xh)) / np.linalg.norm(b)
+    r1 = s.residual_norms(dev(b), x)
+    r2 = s.residual_norms(dev(b), x)
+    assert r1 == r2
+    assert r1["rr_2"] == pytest.approx(ref, rel=1e-12)
+    assert r1["rr_inf"] == pytest.approx(np.max(np.abs(b - A.matvec(xh))) / np.max(np.abs(b)), rel=1e-12)
+    s.close()
