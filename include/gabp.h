@@ -452,6 +452,21 @@ gabp_status mg_vcycle(mg_ctx *mg, int levels, int nu_pre, int nu_post, const dou
 gabp_status mg_solve(mg_ctx *mg, const double *b, double *x, double tol, int max_cycles,
                      int nu_pre, int nu_post, int *cycles, double *relres);
 
+/*
+ * Chooses how a cycle moves between levels.  fused = 1 (the default whenever
+ * every level is a grid stencil inside the 3 x 3 neighbourhood): the
+ * residual, the full-weighting restriction and the pre-smoothing correction
+ * in one kernel, the bilinear prolongation, the coarse-grid correction and the
+ * post-smoothing residual in another, each writing the next smoother's
+ * right-hand side in its precision.  fused = 0: one kernel per step
+ * (residual, restriction, prolongation, correction, conversion).  Both
+ * compute the same operations in the same order.  The transfers are the
+ * V-cycle of Sec. 4 with Algorithm 3 as the smoother either way.
+ * Errors: GABP_E_INVALID_ARG (null context, or fused = 1 on levels that do not
+ * allow it), GABP_E_CUDA.
+ */
+gabp_status mg_set_fused(mg_ctx *mg, int fused);
+
 void mg_destroy(mg_ctx *mg);
 
 #ifdef __cplusplus

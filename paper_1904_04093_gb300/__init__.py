@@ -107,6 +107,7 @@ def load() -> ctypes.CDLL:
         "mg_vcycle": (I, [P, I, I, I, P, P]),
         "mg_solve": (I, [P, P, P, D, I, I, I, PI, PD]),
         "mg_destroy": (None, [P]),
+        "mg_set_fused": (I, [P, I]),
         "gabp_batch_setup": (I, [I, ctypes.POINTER(P), I, P, ctypes.POINTER(P)]),
         "gabp_batch_tune": (I, [P, ctypes.POINTER(P), ctypes.POINTER(P), D, I, PI, PI]),
         "gabp_batch_set_shape": (I, [P, I, I]),
@@ -388,6 +389,11 @@ class Multigrid:
             self.close()
         except Exception:
             pass
+
+    def set_fused(self, fused: bool):
+        """Fused transfer kernels (default where the levels allow them) or one kernel per
+        step; the two compute the same operations in the same order (mg_set_fused)."""
+        _check(load().mg_set_fused(self._h, int(bool(fused))))
 
     def vcycle(self, b, x, nu_pre: int, nu_post: int, levels: int = 0):
         _check(load().mg_vcycle(self._h, int(levels), int(nu_pre), int(nu_post),

@@ -135,6 +135,9 @@ struct gabp_ctx {
     void *laFVn = nullptr, *laBVn = nullptr, *lSVn = nullptr;  // the same in natural order
     void *lprevH = nullptr, *lprevV = nullptr;
     bool lprev_valid = false;
+    // parity-class layout: messages reset lazily (bit 0 precision, bit 1 mean); the
+    // next sweep reads every class that has not sent in it yet as zero
+    unsigned zero_pending = 0;
     bool frozen = false;         // precision messages frozen (both L and P buffers equal)
     bool frozen_transposed = false;
     DevStatus *dstat = nullptr;  // [0] chunk checks, [1] refinement / misc, [2] Lambda change
@@ -195,6 +198,11 @@ struct mg_ctx {
     cudaStream_t cap_stream = nullptr;
     std::vector<CycleGraph> graphs;
     unsigned *hflags = nullptr;  // pinned: each level's breakdown flags after a replay
+    // fused transfers (mg.cu): every level a grid stencil inside the 3 x 3
+    // neighbourhood; tbuf holds the finest level's x + e between restriction and
+    // prolongation
+    bool fusable = false, fused = false;
+    double *tbuf = nullptr;
 };
 
 namespace {
@@ -532,11 +540,19 @@ cudaError_t sweep_once(gabp_ctx *ctx, bool transposed, double *x, cudaStream_t s
         return launch_transpose(pr, m, ctx->MVt, ctx->MV, s);
     }
     if (ctx->parity) {
-        for (const PhaseClasses &ph : ctx->phases) {
+        const unsigned zp = ctx->zero_pending;
+        ctx->zero_pending = 0;
+        for (size_t j = 0; j < ctx->phases.size(); ++j) {
+            const PhaseClasses &ph = ctx->phases[j];
             if (ph.nq == 0) continue;
+            // classes of the colours after this phase: they have not sent in this sweep
+            unsigned later = 0;
+            for (size_t k = j + 1; k < ctx->phases.size(); ++k)
+                for (int t = 0; t < ctx->phases[k].nq; ++t) later |= 1u << ctx->phases[k].q[t];
             cudaError_t e = launch_sweep_parity(ctx->pg, ph, ctx->prec, transposed ? ctx->paT : ctx->pa,
                                                 ctx->pc, ctx->diagT, ctx->bT, ctx->Lm[c0],
-                                                ctx->Mm[c0], x, &ctx->dstat[0].flags, s);
+                                                ctx->Mm[c0], x, &ctx->dstat[0].flags,
+                                                (zp & 1u) ? later : 0u, (zp & 2u) ? later : 0u, s);
             if (e != cudaSuccess) return e;
         }
         return cudaSuccess;
@@ -1866,7 +1882,30 @@ gabp_status mg_setup(int levels, gabp_ctx *const *level_ctx, const int32_t *grid
         return bail(fail_cuda(e, "cudaStreamCreate"));
     // every level works on the multigrid stream
     for (auto *c : mg->lv) c->stream = mg->stream;
+    mg->fusable = true;
+    for (int l = 0; l < levels; ++l) {
+        const gabp_ctx *c = mg->lv[l];
+        if (c->L.kind != GABP_LAYOUT_STENCIL || !mg_fusable(c->L.sp, mg->side[l])) mg->fusable = false;
+    }
+    if (mg->fusable && levels > 1) {
+        if ((s = dalloc(mg, (void **)&mg->tbuf, (size_t)mg->lv[0]->n * sizeof(double))) != GABP_OK) return bail(s);
+    }
+    mg->fused = mg->fusable;
     *out = mg;
+    return GABP_OK;
+}
+
+gabp_status mg_set_fused(mg_ctx *mg, int fused)
+{
+    if (!mg) return fail(GABP_E_INVALID_ARG, "null multigrid context");
+    if (fused && !mg->fusable) return fail(GABP_E_INVALID_ARG, "levels are not 3 x 3 grid stencils: no fused transfers");
+    CKS(set_dev(mg->dev));
+    if (mg->stream) CK(cudaStreamSynchronize(mg->stream));
+    if (mg->fused != (fused != 0)) {
+        for (auto &g : mg->graphs) cudaGraphExecDestroy(g.exec);
+        mg->graphs.clear();
+    }
+    mg->fused = fused != 0;
     return GABP_OK;
 }
 
@@ -1889,7 +1928,7 @@ namespace {
 // to b because x is zero (every level below the finest starts from zero), or
 // already in the level's residual buffer (the finest level's convergence check
 // computed it for the same x).
-enum MgRes { MG_RES_COMPUTE, MG_RES_XZERO, MG_RES_READY };
+enum MgRes { MG_RES_COMPUTE, MG_RES_XZERO, MG_RES_READY, MG_RES_BT };
 
 // Algorithm 3 on level l: r = b - A x; nu GaBP sweeps on A e = r; x += e.
 gabp_status mg_smooth(mg_ctx *mg, int l, const double *b, double *x, int nu, MgRes res)
@@ -1942,14 +1981,114 @@ gabp_status mg_cycle(mg_ctx *mg, int l, int last, int nu_pre, int nu_post, const
     return GABP_OK;
 }
 
+// ---- fused transfers (mg.cu) ----
+//
+// The same cycle with the right-hand side of every smoother call produced by
+// the kernel before it, in the smoother's precision: the restriction kernel
+// writes the coarse level's (as its rhs b and its sweep input bT), the
+// prolongation kernel the post-smoothing one, the convergence check of
+// mg_solve the next pre-smoothing one (MG_RES_READY).  Levels below the
+// finest start from x = 0, so their x is first written by the prolongation
+// (no clearing pass) and their pre-smoothing correction e is read directly.
+
+// The smoother's right-hand side in bT for the cases no kernel has written.
+gabp_status mg_fused_rhs(mg_ctx *mg, int l, const double *b, const double *x, MgRes res)
+{
+    gabp_ctx *c = mg->lv[l];
+    cudaStream_t s = mg->stream;
+    if (res == MG_RES_XZERO) {
+        if (c->prec == 1) CK(launch_convert_d2f(b, (float *)c->bT, c->n, s));
+        else if (b != c->bres) CK(cudaMemcpyAsync(c->bres, b, (size_t)c->n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    } else if (res == MG_RES_COMPUTE) {
+        CK(launch_residual2(c->L, c->a64, c->diag64, b, x, c->bres, c->prec == 1 ? (float *)c->bT : nullptr,
+                            &c->dstat[1], s));
+    }
+    return GABP_OK;
+}
+
+// Algorithm 3's nu sweeps on A e = r with r already in bT; e in the level's xbuf.
+gabp_status mg_fused_sweeps(mg_ctx *mg, int l, int nu)
+{
+    gabp_ctx *c = mg->lv[l];
+    cudaStream_t s = mg->stream;
+    if (c->lines_m > 0) CK(launch_transpose(c->prec, c->lines_m, c->bT, c->lbT, s));
+    const bool lam = mg->mode == MG_SMOOTH_COLD, mean = mg->mode != MG_SMOOTH_PERSIST;
+    if (c->parity && nu > 0) {
+        // no clearing pass: the first sweep reads the classes that have not sent yet as zero
+        if (lam) c->frozen = false;
+        c->zero_pending |= (lam ? 1u : 0u) | (mean ? 2u : 0u);
+    } else if (lam || mean) {
+        CKS(zero_messages(c, lam, mean));
+    }
+    CKS(aggregate(c));
+    for (int i = 0; i < nu; ++i) CK(sweep_once(c, false, i == nu - 1 ? c->xbuf : nullptr, s));
+    return GABP_OK;
+}
+
+gabp_status mg_cycle_fused(mg_ctx *mg, int l, int last, int nu_pre, int nu_post, const double *b,
+                           double *x, MgRes top)
+{
+    cudaStream_t s = mg->stream;
+    gabp_ctx *c = mg->lv[l];
+    const size_t nb = (size_t)c->n * sizeof(double);
+    const bool xzero = top == MG_RES_XZERO || top == MG_RES_BT;
+    if (l == last) {
+        if (l == mg->levels - 1) {
+            CK(launch_dense_gemv(mg->coarse_inv, b, x, mg->nc, s));
+        } else {
+            // truncated hierarchy: smooth on the last used level instead of a direct solve
+            CKS(mg_fused_rhs(mg, l, b, x, top));
+            CKS(mg_fused_sweeps(mg, l, std::max(1, nu_pre + nu_post)));
+            if (xzero) CK(cudaMemcpyAsync(x, c->xbuf, nb, cudaMemcpyDeviceToDevice, s));
+            else CK(launch_axpy(x, c->xbuf, 1.0, c->n, s));
+        }
+        return GABP_OK;
+    }
+    if (nu_pre > 0) {
+        CKS(mg_fused_rhs(mg, l, b, x, top));
+        CKS(mg_fused_sweeps(mg, l, nu_pre));
+    }
+    const double *E = nu_pre > 0 ? c->xbuf : nullptr;
+    const double *X = xzero ? nullptr : x;
+    // x1 = x + e is kept in tbuf for the prolongation when x is not zero (finest level)
+    double *T = nullptr;
+    if (X && E) T = mg->tbuf;
+    else if (X) CK(cudaMemcpyAsync(mg->tbuf, X, nb, cudaMemcpyDeviceToDevice, s));
+    gabp_ctx *cc = mg->lv[l + 1];
+    CK(launch_mg_restrict_residual(c->L.sp, mg->side[l], c->a64, c->diag64, b, X, E, T, mg->scale,
+                                   mg->b[l + 1], cc->prec == 1 ? (float *)cc->bT : nullptr,
+                                   cc->prec == 0 ? cc->bres : nullptr, s));
+    CKS(mg_cycle_fused(mg, l + 1, last, nu_pre, nu_post, mg->b[l + 1], mg->x[l + 1], MG_RES_BT));
+    // x2 = x1 + P e_c into x, and the post-smoothing right-hand side b - A x2
+    const double *Xin = X ? mg->tbuf : nullptr;
+    const double *Ein = X ? nullptr : E;
+    CK(launch_mg_prolong_residual(c->L.sp, mg->side[l], c->a64, c->diag64, b, Xin, Ein,
+                                  mg->x[l + 1], x, c->prec == 0 ? c->bres : nullptr,
+                                  c->prec == 1 ? (float *)c->bT : nullptr, s));
+    if (nu_post > 0) {
+        CKS(mg_fused_sweeps(mg, l, nu_post));
+        CK(launch_axpy(x, c->xbuf, 1.0, c->n, s));
+    }
+    return GABP_OK;
+}
+
+gabp_status mg_cycle_any(mg_ctx *mg, int l, int last, int nu_pre, int nu_post, const double *b,
+                         double *x, MgRes top)
+{
+    if (mg->fused) return mg_cycle_fused(mg, l, last, nu_pre, nu_post, b, x, top);
+    return mg_cycle(mg, l, last, nu_pre, nu_post, b, x, top);
+}
+
 // After a cycle of mg_solve: the convergence residual b - A x of the finest
-// level (left in its residual buffer for the next cycle), its maxima and every
-// level's breakdown flags copied to pinned host memory.
+// level (left in its residual buffer for the next cycle, and with fused
+// transfers also in its sweep input), its maxima and every level's breakdown
+// flags copied to pinned host memory.
 gabp_status mg_cycle_tail(mg_ctx *mg, const double *b, double *x, cudaStream_t s)
 {
     gabp_ctx *f = mg->lv[0];
     CK(cudaMemsetAsync(mg->dstat, 0, sizeof(DevStatus), s));
-    CK(launch_residual(f->L, f->a64, f->diag64, b, x, f->bres, mg->dstat, s));
+    CK(launch_residual2(f->L, f->a64, f->diag64, b, x, f->bres,
+                        mg->fused && f->prec == 1 ? (float *)f->bT : nullptr, mg->dstat, s));
     CK(cudaMemcpyAsync(mg->hstat, mg->dstat, sizeof(DevStatus), cudaMemcpyDeviceToHost, s));
     for (int l = 0; l < mg->levels; ++l)
         CK(cudaMemcpyAsync(&mg->hflags[l], &mg->lv[l]->dstat[0].flags, sizeof(unsigned),
@@ -1989,7 +2128,7 @@ gabp_status mg_cycle_graph(mg_ctx *mg, const double *b, double *x, int nu_pre, i
         gabp_status st = GABP_OK;
         cudaError_t e = cudaStreamBeginCapture(mg->cap_stream, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
-            st = mg_cycle(mg, 0, mg->levels - 1, nu_pre, nu_post, b, x, MG_RES_READY);
+            st = mg_cycle_any(mg, 0, mg->levels - 1, nu_pre, nu_post, b, x, MG_RES_READY);
             if (st == GABP_OK) st = mg_cycle_tail(mg, b, x, mg->cap_stream);
             e = cudaStreamEndCapture(mg->cap_stream, &graph);
         }
@@ -2038,7 +2177,7 @@ gabp_status mg_vcycle(mg_ctx *mg, int levels, int nu_pre, int nu_post, const dou
     CKS(set_dev(mg->dev));
     const int last = (levels == 0 ? mg->levels : levels) - 1;
     for (auto *c : mg->lv) CK(cudaMemsetAsync(&c->dstat[0].flags, 0, sizeof(unsigned), mg->stream));
-    CKS(mg_cycle(mg, 0, last, nu_pre, nu_post, b, x, MG_RES_COMPUTE));
+    CKS(mg_cycle_any(mg, 0, last, nu_pre, nu_post, b, x, MG_RES_COMPUTE));
     return mg_check_flags(mg);
 }
 
@@ -2063,13 +2202,13 @@ gabp_status mg_solve(mg_ctx *mg, const double *b, double *x, double tol, int max
     while (st == GABP_E_NOT_CONVERGED && c < max_cycles) {
         if (c == 0) {
             // the first cycle starts from x = 0
-            CKS(mg_cycle(mg, 0, mg->levels - 1, nu_pre, nu_post, b, x, MG_RES_XZERO));
+            CKS(mg_cycle_any(mg, 0, mg->levels - 1, nu_pre, nu_post, b, x, MG_RES_XZERO));
             CKS(mg_cycle_tail(mg, b, x, s));
         } else if (mg_graph_safe(mg, nu_pre, nu_post)) {
             // later cycles reuse the check's residual of the same x: one graph replay each
             CKS(mg_cycle_graph(mg, b, x, nu_pre, nu_post));
         } else {
-            CKS(mg_cycle(mg, 0, mg->levels - 1, nu_pre, nu_post, b, x, MG_RES_READY));
+            CKS(mg_cycle_any(mg, 0, mg->levels - 1, nu_pre, nu_post, b, x, MG_RES_READY));
             CKS(mg_cycle_tail(mg, b, x, s));
         }
         ++c;

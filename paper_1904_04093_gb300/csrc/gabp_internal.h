@@ -105,6 +105,10 @@ cudaError_t launch_aggregate(const DevLayout &L, int prec, const void *diag, con
 cudaError_t launch_residual(const DevLayout &L, const double *a64, const double *diag64,
                             const double *b, const double *x, double *r, DevStatus *st,
                             cudaStream_t s);
+// the same, the residual also written in float into rf (nullable; stencil layout only)
+cudaError_t launch_residual2(const DevLayout &L, const double *a64, const double *diag64,
+                             const double *b, const double *x, double *r, float *rf,
+                             DevStatus *st, cudaStream_t s);
 cudaError_t launch_convert_d2f(const double *in, float *out, int64_t n, cudaStream_t s);
 // per-block partial sums of u^2 and v^2 (part: 2 * nblocks doubles), a fixed order on every call
 constexpr int kSumsqBlocks = 1024;
@@ -125,9 +129,12 @@ cudaError_t launch_parity_convert(const ParityGrid &g, int prec, int to_class, c
                                   void *dst, cudaStream_t s);
 // One in-place phase of the coloured schedule over the classes of ph:
 // a, c in class layout; diag, b in natural order; Lo, Mo the class-layout state.
+// zl, zm: parity classes whose precision / mean messages read as zero (the
+// first sweep after a reset of the messages, instead of clearing the arrays)
 cudaError_t launch_sweep_parity(const ParityGrid &g, const PhaseClasses &ph, int prec,
                                 const void *a, const void *c, const void *diag, const void *b,
-                                void *Lo, void *Mo, double *x, unsigned *flags, cudaStream_t s);
+                                void *Lo, void *Mo, double *x, unsigned *flags, unsigned zl,
+                                unsigned zm, cudaStream_t s);
 cudaError_t launch_get_state(const int64_t *slotmap, int64_t nnz, int prec, const void *Lm,
                              const void *Mm, double *lam, double *m, cudaStream_t s);
 cudaError_t launch_set_state(const int64_t *slotmap, int64_t nnz, int prec, const double *lam,
@@ -202,6 +209,21 @@ cudaError_t launch_transpose_coeffs(const DevLayout &L, int prec, const void *a,
 // multigrid transfers on square grids (lexicographic, m_f = 2 m_c + 1)
 cudaError_t launch_restrict_fw(const double *rf, int mf, double scale, double *rc, cudaStream_t s);
 cudaError_t launch_prolong_add(const double *ec, int mc, double *xf, cudaStream_t s);
+// fused transfers (mg.cu) on an m x m grid level whose stencil lies in the 3 x 3
+// neighbourhood (mg_fusable): x1 = X + E (nullable terms) and, optionally, x1 into
+// T for the tile's own points; r = b - A x1 restricted by full weighting, times
+// scale, into rc (double) and optionally rcf (float) / rcd (a second double copy)
+bool mg_fusable(const StencilParams &sp, int m);
+cudaError_t launch_mg_restrict_residual(const StencilParams &sp, int mf, const double *a64,
+                                        const double *diag64, const double *b, const double *X,
+                                        const double *E, double *T, double scale, double *rc,
+                                        float *rcf, double *rcd, cudaStream_t s);
+// x2 = Xin + Ein + P ec (nullable Xin, Ein) into Xout (Xout may not alias Xin or
+// Ein); r = b - A x2 into r (double) and / or rf (float)
+cudaError_t launch_mg_prolong_residual(const StencilParams &sp, int mf, const double *a64,
+                                       const double *diag64, const double *b, const double *Xin,
+                                       const double *Ein, const double *ec, double *Xout,
+                                       double *r, float *rf, cudaStream_t s);
 // y = M x for a dense row-major n x n matrix (coarse-grid solve)
 cudaError_t launch_dense_gemv(const double *M, const double *x, double *y, int n, cudaStream_t s);
 

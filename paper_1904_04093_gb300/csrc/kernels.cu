@@ -418,7 +418,7 @@ template <int K>
 __global__ void __launch_bounds__(256) k_residual_stencil(
     int n, StencilParams sp, const double *__restrict__ a64, const double *__restrict__ diag64,
     const double *__restrict__ b, const double *__restrict__ x, double *__restrict__ r,
-    DevStatus *st)
+    float *__restrict__ rf, DevStatus *st)
 {
     constexpr int KK = K > 0 ? K : 1;
     unsigned long long rbits = 0ull, bbits = 0ull;
@@ -449,6 +449,7 @@ __global__ void __launch_bounds__(256) k_residual_stencil(
 #pragma unroll
             for (int k = 0; k < K; ++k) acc = fma(av[u][k], xv[u][k], acc);
             if (r) r[i] = acc;
+            if (rf) rf[i] = (float)acc;
             const unsigned long long ab = abs_bits(acc);
             if (ab > 0x7ff0000000000000ull) nan = true;
             else rbits = max(rbits, ab);
@@ -803,12 +804,20 @@ cudaError_t launch_residual(const DevLayout &L, const double *a64, const double 
                             const double *b, const double *x, double *r, DevStatus *st,
                             cudaStream_t s)
 {
+    return launch_residual2(L, a64, diag64, b, x, r, nullptr, st, s);
+}
+
+cudaError_t launch_residual2(const DevLayout &L, const double *a64, const double *diag64,
+                             const double *b, const double *x, double *r, float *rf,
+                             DevStatus *st, cudaStream_t s)
+{
     if (L.n == 0) return cudaSuccess;
+    if (rf && L.kind != GABP_LAYOUT_STENCIL) return cudaErrorInvalidValue;
     const int block = 256, grid = grid_for(L.n, block, 152 * 16);
     if (L.kind == GABP_LAYOUT_STENCIL) {
-#define GABP_RES_CASE(KK)                                                                \
-    case KK:                                                                             \
-        k_residual_stencil<KK><<<grid, block, 0, s>>>(L.n, L.sp, a64, diag64, b, x, r, st); \
+#define GABP_RES_CASE(KK)                                                                   \
+    case KK:                                                                                \
+        k_residual_stencil<KK><<<grid, block, 0, s>>>(L.n, L.sp, a64, diag64, b, x, r, rf, st); \
         break;
         switch (L.sp.K) {
             GABP_RES_CASE(0)

@@ -78,6 +78,9 @@ __global__ void k_parity_convert(ParityGrid g, int to_class, const T *__restrict
     }
 }
 
+// zl, zm: classes whose precision / mean messages read as zero (bit q for
+// class q): after a reset of the messages the first sweep reads the classes
+// that have not sent yet as zero instead of clearing the arrays first.
 template <typename T, int K>
 __global__ void __launch_bounds__(256) k_sweep_parity(ParityGrid g, PhaseClasses ph,
                                                       const T *__restrict__ a,
@@ -85,7 +88,8 @@ __global__ void __launch_bounds__(256) k_sweep_parity(ParityGrid g, PhaseClasses
                                                       const T *__restrict__ diag,
                                                       const T *__restrict__ b, T *Lo, T *Mo,
                                                       double *__restrict__ x,
-                                                      unsigned *__restrict__ flags)
+                                                      unsigned *__restrict__ flags, unsigned zl,
+                                                      unsigned zm)
 {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long end = ph.nq >= 4 ? ph.start[4] : ph.nq == 3 ? ph.start[3] : ph.nq == 2 ? ph.start[2] : ph.start[1];
@@ -112,11 +116,11 @@ __global__ void __launch_bounds__(256) k_sweep_parity(ParityGrid g, PhaseClasses
     for (int k = 0; k < K; ++k) {
         const int nx = sx + g.dx[k], ny = sy + g.dy[k];
         const bool in = in_grid(g, nx, ny);
+        const unsigned qn = (unsigned)((nx & 1) | ((ny & 1) << 1));
         const long long src = in ? (long long)g.krev[k] * n + class_pos(g, nx, ny)
                                  : (long long)k * n + pos;  // any valid address
-        const T l = Lo[src], mm = Mo[src];
-        lin[k] = in ? l : T(0);
-        min_[k] = in ? mm : T(0);
+        lin[k] = in && !((zl >> qn) & 1u) ? Lo[src] : T(0);
+        min_[k] = in && !((zm >> qn) & 1u) ? Mo[src] : T(0);
         av[k] = a[(long long)k * n + pos];
         cv[k] = c[(long long)k * n + pos];
     }
@@ -162,7 +166,8 @@ __device__ __forceinline__ void parity_node(const ParityGrid &g, unsigned cx, un
                                             const T *__restrict__ a, const T *__restrict__ c,
                                             const T *__restrict__ diag,
                                             const T *__restrict__ b, T *Lo, T *Mo,
-                                            double *__restrict__ x, bool &bad)
+                                            double *__restrict__ x, bool &bad, unsigned zl,
+                                            unsigned zm)
 {
     constexpr int Q = PX | (PY << 1);
     const unsigned m = (unsigned)g.m, n = m * m;
@@ -179,9 +184,8 @@ __device__ __forceinline__ void parity_node(const ParityGrid &g, unsigned cx, un
             in ? (unsigned)(K - 1 - k) * n + (unsigned)g.base[qt] +
                      (cy + dy2) * (unsigned)g.w[qt] + (cx + dx2)
                : (unsigned)k * n + pos;  // any valid address
-        const T l = Lo[src], mm = Mo[src];
-        lin[k] = in ? l : T(0);
-        min_[k] = in ? mm : T(0);
+        lin[k] = in && !((zl >> qt) & 1u) ? Lo[src] : T(0);
+        min_[k] = in && !((zm >> qt) & 1u) ? Mo[src] : T(0);
         av[k] = a[(unsigned)k * n + pos];
         cv[k] = c[(unsigned)k * n + pos];
     }
@@ -213,7 +217,8 @@ __global__ void __launch_bounds__(256) k_sweep_parity_std(ParityGrid g, PhaseCla
                                                           const T *__restrict__ diag,
                                                           const T *__restrict__ b, T *Lo, T *Mo,
                                                           double *__restrict__ x,
-                                                          unsigned *__restrict__ flags)
+                                                          unsigned *__restrict__ flags,
+                                                          unsigned zl, unsigned zm)
 {
     const int z = blockIdx.z;
     const int q = z == 0 ? ph.q[0] : z == 1 ? ph.q[1] : z == 2 ? ph.q[2] : ph.q[3];
@@ -221,10 +226,10 @@ __global__ void __launch_bounds__(256) k_sweep_parity_std(ParityGrid g, PhaseCla
     if (cx >= (unsigned)pick4(g.w, q) || cy >= (unsigned)pick4(g.h, q)) return;
     bool bad = false;
     switch (q) {
-        case 0: parity_node<T, K, 0, 0>(g, cx, cy, a, c, diag, b, Lo, Mo, x, bad); break;
-        case 1: parity_node<T, K, 1, 0>(g, cx, cy, a, c, diag, b, Lo, Mo, x, bad); break;
-        case 2: parity_node<T, K, 0, 1>(g, cx, cy, a, c, diag, b, Lo, Mo, x, bad); break;
-        default: parity_node<T, K, 1, 1>(g, cx, cy, a, c, diag, b, Lo, Mo, x, bad); break;
+        case 0: parity_node<T, K, 0, 0>(g, cx, cy, a, c, diag, b, Lo, Mo, x, bad, zl, zm); break;
+        case 1: parity_node<T, K, 1, 0>(g, cx, cy, a, c, diag, b, Lo, Mo, x, bad, zl, zm); break;
+        case 2: parity_node<T, K, 0, 1>(g, cx, cy, a, c, diag, b, Lo, Mo, x, bad, zl, zm); break;
+        default: parity_node<T, K, 1, 1>(g, cx, cy, a, c, diag, b, Lo, Mo, x, bad, zl, zm); break;
     }
     if (bad) atomicOr(flags, FLAG_BREAKDOWN);
 }
@@ -248,7 +253,8 @@ cudaError_t launch_parity_convert(const ParityGrid &g, int prec, int to_class, c
 
 cudaError_t launch_sweep_parity(const ParityGrid &g, const PhaseClasses &ph, int prec,
                                 const void *a, const void *c, const void *diag, const void *b,
-                                void *Lo, void *Mo, double *x, unsigned *flags, cudaStream_t s)
+                                void *Lo, void *Mo, double *x, unsigned *flags, unsigned zl,
+                                unsigned zm, cudaStream_t s)
 {
     const long long nodes = ph.start[ph.nq];
     if (nodes == 0) return cudaSuccess;
@@ -266,20 +272,20 @@ cudaError_t launch_sweep_parity(const ParityGrid &g, const PhaseClasses &ph, int
             if (prec == 0)
                 k_sweep_parity_std<double, 4><<<grid3, block, 0, s>>>(
                     g, ph, (const double *)a, (const double *)c, (const double *)diag,
-                    (const double *)b, (double *)Lo, (double *)Mo, x, flags);
+                    (const double *)b, (double *)Lo, (double *)Mo, x, flags, zl, zm);
             else
                 k_sweep_parity_std<float, 4><<<grid3, block, 0, s>>>(
                     g, ph, (const float *)a, (const float *)c, (const float *)diag,
-                    (const float *)b, (float *)Lo, (float *)Mo, x, flags);
+                    (const float *)b, (float *)Lo, (float *)Mo, x, flags, zl, zm);
         } else {
             if (prec == 0)
                 k_sweep_parity_std<double, 8><<<grid3, block, 0, s>>>(
                     g, ph, (const double *)a, (const double *)c, (const double *)diag,
-                    (const double *)b, (double *)Lo, (double *)Mo, x, flags);
+                    (const double *)b, (double *)Lo, (double *)Mo, x, flags, zl, zm);
             else
                 k_sweep_parity_std<float, 8><<<grid3, block, 0, s>>>(
                     g, ph, (const float *)a, (const float *)c, (const float *)diag,
-                    (const float *)b, (float *)Lo, (float *)Mo, x, flags);
+                    (const float *)b, (float *)Lo, (float *)Mo, x, flags, zl, zm);
         }
         return cudaGetLastError();
     }
@@ -289,11 +295,11 @@ cudaError_t launch_sweep_parity(const ParityGrid &g, const PhaseClasses &ph, int
         if (prec == 0)                                                                            \
             k_sweep_parity<double, KK><<<grid, 256, 0, s>>>(                                      \
                 g, ph, (const double *)a, (const double *)c, (const double *)diag,                \
-                (const double *)b, (double *)Lo, (double *)Mo, x, flags);                         \
+                (const double *)b, (double *)Lo, (double *)Mo, x, flags, zl, zm);                         \
         else                                                                                      \
             k_sweep_parity<float, KK><<<grid, 256, 0, s>>>(                                       \
                 g, ph, (const float *)a, (const float *)c, (const float *)diag,                   \
-                (const float *)b, (float *)Lo, (float *)Mo, x, flags);                            \
+                (const float *)b, (float *)Lo, (float *)Mo, x, flags, zl, zm);                            \
         break;
     switch (g.K) {
         GABP_PAR_CASE(2)
