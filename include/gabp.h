@@ -363,22 +363,29 @@ gabp_status gabp_sweep_noalloc(int32_t n, int64_t nnz, const int64_t *indptr,
  * device) into a batch.  The batch uses the contexts' coefficient and message
  * buffers (their message state is overwritten by batch solves); the contexts
  * stay owned by the caller and must outlive the batch.  Systems are queued
- * largest first.
+ * largest first.  check_every: sweeps between residual checks, or 0 to let
+ * gabp_batch_tune choose it (starting from 10).
  */
 gabp_status gabp_batch_setup(int nsys, gabp_ctx *const *systems, int check_every, void *stream,
                              gabp_batch **out);
 
 /*
- * Autotuner: times a whole batched solve (tolerance `tol`, sweep cap
- * `max_iter`, as gabp_batch_solve) for each launch shape -- 256 or 512
- * threads per CTA x 1, 2, 4, 8 or 16 CTAs per thread-block cluster (16
- * where the non-portable cluster size fits), as many
- * clusters as can be resident -- and keeps the fastest.  Under a shape,
- * systems with at least 4 rows per cluster thread are each solved by a whole
- * cluster, the rest by single CTAs.  b, x: host arrays of nsys device
- * pointers (n_i doubles each); x receives scratch values.  The first
- * gabp_batch_solve tunes itself (with its own tol and max_iter) unless a
- * shape was set.  block / cluster (nullable) receive the choice.
+ * Autotuner: times whole batched solves (tolerance `tol`, sweep cap
+ * `max_iter`, as gabp_batch_solve) and keeps the fastest setting, in three
+ * stages.  (1) The launch shape: 256 or 512 threads per CTA x 1, 2, 4, 8 or
+ * 16 CTAs per thread-block cluster (16 where the non-portable cluster size
+ * fits), as many clusters as can be resident.  (2) At that shape, the rows
+ * each thread keeps in flight in the sweeps with frozen precision messages
+ * (1, or 2 for 5- and 9-point systems: the edges per thread of one step are
+ * rows x diagonals) and, with clusters, the rows per cluster thread from
+ * which a system is solved by a whole cluster instead of one CTA (2, 4 or 8).
+ * (3) Only for a batch set up with check_every 0: the residual check
+ * interval, 10 or 20 (a system may then sweep up to that many times past its
+ * tolerance); otherwise the setup's interval is kept.  b, x: host arrays of
+ * nsys device pointers (n_i doubles each); x receives scratch values.  The
+ * first gabp_batch_solve tunes itself (with its own tol and max_iter) unless
+ * a shape was set.  block / cluster (nullable) receive the shape;
+ * gabp_batch_params the rest.
  */
 gabp_status gabp_batch_tune(gabp_batch *batch, const double *const *b, double *const *x, double tol,
                             int max_iter, int *block, int *cluster);
@@ -386,6 +393,18 @@ gabp_status gabp_batch_tune(gabp_batch *batch, const double *const *b, double *c
 /* Sets the launch shape without tuning: block 256 or 512, cluster 1, 2, 4, 8 or 16
  * (GABP_E_INVALID_ARG when the shape cannot be resident). */
 gabp_status gabp_batch_set_shape(gabp_batch *batch, int block, int cluster);
+
+/*
+ * Sets the other tuned parameters (0 keeps one): rows in flight per thread
+ * (1, or 2 for 5- and 9-point systems), rows per cluster thread from which a
+ * system takes a whole cluster (default 4), residual check interval (default:
+ * the setup's).  Any setting gives each system the iterates of gabp_solve with
+ * that check interval.  Errors: GABP_E_INVALID_ARG.
+ */
+gabp_status gabp_batch_set_params(gabp_batch *batch, int rows, int min_rows, int check_every);
+
+/* The parameters in use (each pointer nullable). */
+gabp_status gabp_batch_params(gabp_batch *batch, int *rows, int *min_rows, int *check_every);
 
 /*
  * Solves every system A_i x_i = b_i from zero messages in one persistent

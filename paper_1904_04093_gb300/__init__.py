@@ -113,6 +113,8 @@ def load() -> ctypes.CDLL:
         "gabp_batch_set_shape": (I, [P, I, I]),
         "gabp_batch_solve": (I, [P, ctypes.POINTER(P), ctypes.POINTER(P), D, I, PI, PD, PI]),
         "gabp_batch_info": (I, [P, PI, PI, PI]),
+        "gabp_batch_set_params": (I, [P, I, I, I]),
+        "gabp_batch_params": (I, [P, PI, PI, PI]),
         "gabp_batch_destroy": (None, [P]),
     }
     for name, (res, args) in sigs.items():
@@ -455,10 +457,18 @@ class Batch:
     def set_shape(self, block: int, cluster: int):
         _check(load().gabp_batch_set_shape(self._h, int(block), int(cluster)))
 
+    def set_params(self, rows: int = 0, min_rows: int = 0, check_every: int = 0):
+        """Rows in flight per thread, rows per cluster thread for a cluster team, check
+        interval (0 keeps one; gabp_batch_set_params)."""
+        _check(load().gabp_batch_set_params(self._h, int(rows), int(min_rows), int(check_every)))
+
     def info(self):
         blk, cs, grid = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         _check(load().gabp_batch_info(self._h, ctypes.byref(blk), ctypes.byref(cs), ctypes.byref(grid)))
-        return {"block": blk.value, "cluster": cs.value, "grid": grid.value}
+        r, mr, ce = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(load().gabp_batch_params(self._h, ctypes.byref(r), ctypes.byref(mr), ctypes.byref(ce)))
+        return {"block": blk.value, "cluster": cs.value, "grid": grid.value, "rows": r.value,
+                "min_rows": mr.value, "check_every": ce.value}
 
     def solve(self, bs, tol: float, max_iter: int, xs=None):
         """Returns ``(xs, iters, relres, status)`` (lists over systems)."""

@@ -155,6 +155,10 @@ struct gabp_batch {
     int freeze = 0;                    // freeze precision messages per system once converged
     double inner_tol = 1e-3;
     int block = 0, cs = 0, grid = 0, nbig = 0, sms = 0;  // launch shape (0 = not tuned)
+    int rows = 1;       // rows in flight per thread in the mean-message sweeps
+    int min_rows = 4;   // a system takes a whole cluster from this many rows per cluster thread
+    int check_every0 = 10;  // the check interval given at setup
+    bool check_auto = false;  // setup asked for a tuned check interval (check_every 0)
     std::vector<gabp_ctx *> sys;
     void *d_sys = nullptr;            // descriptors
     int *d_order = nullptr;           // largest first
@@ -2252,7 +2256,7 @@ gabp_status gabp_batch_setup(int nsys, gabp_ctx *const *systems, int check_every
 {
     if (!out) return fail(GABP_E_INVALID_ARG, "out is NULL");
     *out = nullptr;
-    if (nsys < 1 || !systems || check_every < 1) return fail(GABP_E_INVALID_ARG, "bad argument");
+    if (nsys < 1 || !systems || check_every < 0) return fail(GABP_E_INVALID_ARG, "bad argument");
     for (int i = 0; i < nsys; ++i) {
         const gabp_ctx *c = systems[i];
         if (!c) return fail(GABP_E_INVALID_ARG, "null system context");
@@ -2275,7 +2279,9 @@ gabp_status gabp_batch_setup(int nsys, gabp_ctx *const *systems, int check_every
     bt->nsys = nsys;
     bt->prec = systems[0]->prec;
     bt->K = systems[0]->L.sp.K;
-    bt->check_every = check_every;
+    bt->check_auto = check_every == 0;
+    bt->check_every = check_every > 0 ? check_every : 10;
+    bt->check_every0 = bt->check_every;
     bt->refine = systems[0]->opt.precision == GABP_FP32_IR ? 1 : 0;
     bt->inner_max = systems[0]->opt.ir_inner_max > 0 ? systems[0]->opt.ir_inner_max : 400;
     bt->inner_tol = systems[0]->opt.ir_inner_tol > 0 ? systems[0]->opt.ir_inner_tol : 1e-3;
@@ -2318,10 +2324,10 @@ gabp_status gabp_batch_setup(int nsys, gabp_ctx *const *systems, int check_every
 
 namespace {
 
-// Systems solved by whole clusters: those with at least 4 rows per cluster thread.
+// Systems solved by whole clusters: those with at least min_rows rows per cluster thread.
 int batch_nbig(const gabp_batch *bt, int block, int cs)
 {
-    const int64_t thr = 4LL * block * cs;
+    const int64_t thr = (int64_t)bt->min_rows * block * cs;
     int nb = 0;
     for (auto *c : bt->sys)
         if (c->n >= thr) ++nb;
@@ -2338,11 +2344,11 @@ cudaError_t batch_enqueue(gabp_batch *bt, int block, int cs, int grid, double to
     if ((e = cudaMemcpyAsync(bt->d_x, bt->h_x, pb, cudaMemcpyHostToDevice, s)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(bt->d_queue, 0, 2 * sizeof(int), s)) != cudaSuccess) return e;
     e = bt->prec == 0
-            ? launch_batch<double>(bt->K, cs, grid, block, bt->d_sys, bt->d_order, bt->nsys, nbig, bt->d_b,
-                                   bt->d_x, bt->d_queue, tol, max_iter, bt->check_every, bt->refine,
+            ? launch_batch<double>(bt->K, bt->rows, cs, grid, block, bt->d_sys, bt->d_order, bt->nsys, nbig,
+                                   bt->d_b, bt->d_x, bt->d_queue, tol, max_iter, bt->check_every, bt->refine,
                                    bt->inner_tol, bt->inner_max, bt->freeze, bt->d_res, s)
-            : launch_batch<float>(bt->K, cs, grid, block, bt->d_sys, bt->d_order, bt->nsys, nbig, bt->d_b,
-                                  bt->d_x, bt->d_queue, tol, max_iter, bt->check_every, bt->refine,
+            : launch_batch<float>(bt->K, bt->rows, cs, grid, block, bt->d_sys, bt->d_order, bt->nsys, nbig,
+                                  bt->d_b, bt->d_x, bt->d_queue, tol, max_iter, bt->check_every, bt->refine,
                                   bt->inner_tol, bt->inner_max, bt->freeze, bt->d_res, s);
     if (e != cudaSuccess) return e;
     count_launches(s, 1);
@@ -2363,10 +2369,15 @@ gabp_status batch_stage(gabp_batch *bt, const double *const *b, double *const *x
 
 }  // namespace
 
+static int batch_clusters(const gabp_batch *bt, int cs, int blk)
+{
+    return bt->prec == 0 ? batch_max_clusters<double>(bt->K, bt->rows, cs, blk)
+                         : batch_max_clusters<float>(bt->K, bt->rows, cs, blk);
+}
+
 static gabp_status batch_set_shape(gabp_batch *bt, int blk, int cs)
 {
-    const int nc = bt->prec == 0 ? batch_max_clusters<double>(bt->K, cs, blk)
-                                 : batch_max_clusters<float>(bt->K, cs, blk);
+    const int nc = batch_clusters(bt, cs, blk);
     if (nc < 1) return fail(GABP_E_INVALID_ARG, "launch shape does not fit the batched kernel");
     const int grid = nc * cs;  // every cluster resident: a persistent launch
     if (bt->exec && (bt->block != blk || bt->cs != cs || bt->grid != grid)) {
@@ -2389,34 +2400,116 @@ gabp_status gabp_batch_set_shape(gabp_batch *bt, int block, int cluster)
     return batch_set_shape(bt, block, cluster);
 }
 
+gabp_status gabp_batch_set_params(gabp_batch *bt, int rows, int min_rows, int check_every)
+{
+    if (!bt || rows < 0 || min_rows < 0 || check_every < 0) return fail(GABP_E_INVALID_ARG, "bad argument");
+    if (rows > 0 && !batch_rows_supported(bt->K, rows))
+        return fail(GABP_E_INVALID_ARG, "rows in flight: 1, or 2 for 5- and 9-point systems");
+    CKS(set_dev(bt->dev));
+    if (bt->exec) {
+        cudaGraphExecDestroy(bt->exec);
+        bt->exec = nullptr;
+    }
+    if (rows > 0) bt->rows = rows;
+    if (min_rows > 0) bt->min_rows = min_rows;
+    if (check_every > 0) bt->check_every = check_every;
+    if (bt->block > 0) return batch_set_shape(bt, bt->block, bt->cs);  // resident clusters may change
+    return GABP_OK;
+}
+
+gabp_status gabp_batch_params(gabp_batch *bt, int *rows, int *min_rows, int *check_every)
+{
+    if (!bt) return fail(GABP_E_INVALID_ARG, "null batch");
+    if (rows) *rows = bt->rows;
+    if (min_rows) *min_rows = bt->min_rows;
+    if (check_every) *check_every = bt->check_every;
+    return GABP_OK;
+}
+
+// One timed solve of the staged batch with the current parameters and shape
+// (blk, cs); a negative time when the shape does not fit.
+static gabp_status batch_trial(gabp_batch *bt, int blk, int cs, double tol, int max_iter, float *ms)
+{
+    *ms = -1.0f;
+    const int nc = batch_clusters(bt, cs, blk);
+    if (nc < 1) return GABP_OK;
+    const int save_block = bt->block, save_cs = bt->cs;
+    bt->block = blk;  // batch_nbig reads the parameters of the shape being tried
+    bt->cs = cs;
+    CK(cudaEventRecord(bt->ev0, bt->stream));
+    cudaError_t e = batch_enqueue(bt, blk, cs, nc * cs, tol, max_iter, bt->stream);
+    bt->block = save_block;
+    bt->cs = save_cs;
+    if (e != cudaSuccess) return fail_cuda(e, "batch trial");
+    CK(cudaEventRecord(bt->ev1, bt->stream));
+    CK(cudaEventSynchronize(bt->ev1));
+    CK(cudaEventElapsedTime(ms, bt->ev0, bt->ev1));
+    return GABP_OK;
+}
+
 gabp_status gabp_batch_tune(gabp_batch *bt, const double *const *b, double *const *x, double tol,
                             int max_iter, int *block, int *cluster)
 {
     if (!bt || max_iter < 1 || !(tol >= 0.0)) return fail(GABP_E_INVALID_ARG, "bad argument");
     CKS(set_dev(bt->dev));
     CKS(batch_stage(bt, b, x));
+    if (bt->exec) {
+        cudaGraphExecDestroy(bt->exec);
+        bt->exec = nullptr;
+    }
+    // stage 1: block size x cluster size, one row in flight, the setup's check interval
+    bt->rows = 1;
+    bt->min_rows = 4;
+    bt->check_every = bt->check_every0;
     const int blocks[] = {256, 512};
     const int clusters[] = {1, 2, 4, 8, 16};  // 16: non-portable cluster size, where it fits
-    float best = -1.0f;
+    float best = -1.0f, ms = 0.0f;
     int bb = 0, bc = 0;
     for (int blk : blocks)
         for (int cs : clusters) {
-            const int nc = bt->prec == 0 ? batch_max_clusters<double>(bt->K, cs, blk)
-                                         : batch_max_clusters<float>(bt->K, cs, blk);
-            if (nc < 1) continue;
-            CK(cudaEventRecord(bt->ev0, bt->stream));
-            CK(batch_enqueue(bt, blk, cs, nc * cs, tol, max_iter, bt->stream));
-            CK(cudaEventRecord(bt->ev1, bt->stream));
-            CK(cudaEventSynchronize(bt->ev1));
-            float ms = 0.0f;
-            CK(cudaEventElapsedTime(&ms, bt->ev0, bt->ev1));
-            if (best < 0.0f || ms < best) {
+            CKS(batch_trial(bt, blk, cs, tol, max_iter, &ms));
+            if (ms >= 0.0f && (best < 0.0f || ms < best)) {
                 best = ms;
                 bb = blk;
                 bc = cs;
             }
         }
     if (best < 0.0f) return fail(GABP_E_CUDA, "no launch shape fits the batched kernel");
+    // stage 2: rows in flight per thread (the edges per thread of a mean sweep are
+    // rows x diagonals) and, with clusters, the rows per cluster thread from which a
+    // system takes a whole cluster
+    int br = 1, bm = 4;
+    const int rows_try[] = {1, 2}, minr_try[] = {2, 4, 8};
+    for (int r : rows_try) {
+        if (!batch_rows_supported(bt->K, r)) continue;
+        for (int mr : minr_try) {
+            if (bc == 1 && mr != 4) continue;  // no cluster teams: the threshold does not matter
+            if (r == 1 && mr == 4) continue;   // stage 1's setting
+            bt->rows = r;
+            bt->min_rows = mr;
+            CKS(batch_trial(bt, bb, bc, tol, max_iter, &ms));
+            if (ms >= 0.0f && ms < best) {
+                best = ms;
+                br = r;
+                bm = mr;
+            }
+        }
+    }
+    bt->rows = br;
+    bt->min_rows = bm;
+    // stage 3 (only for a batch set up with a tuned check interval): residual checks
+    // half as often (each check is a residual pass and team reductions; a system may
+    // then run up to that many sweeps past its tolerance)
+    int bce = bt->check_every0;
+    if (bt->check_auto) {
+        bt->check_every = 2 * bt->check_every0;
+        CKS(batch_trial(bt, bb, bc, tol, max_iter, &ms));
+        if (ms >= 0.0f && ms < best) {
+            best = ms;
+            bce = bt->check_every;
+        }
+    }
+    bt->check_every = bce;
     CKS(batch_set_shape(bt, bb, bc));
     if (block) *block = bb;
     if (cluster) *cluster = bc;

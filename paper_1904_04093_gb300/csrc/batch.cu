@@ -129,30 +129,103 @@ struct CtaTeam {
 // Residual max_r |rhs_r - (A y)_r| in double, rhs_r = src[r] * scale, over this
 // thread's rows; writes rhs - A y into `out` when not null.  src and y are
 // read coherently (written earlier in this launch).
-template <typename T, int K>
+// R rows of a thread are in flight at once: rows r0 + u nt, u < R, all loads
+// issued before the arithmetic (the neighbour loads at a clamped, always valid
+// index; a padded slot has a = 0 and drops its value).
+template <typename T, int K, int R>
 __device__ double batch_residual(const BatchSys<T> &S, int n, const int *off, const double *src,
                                  double scale, const double *y, double *out, int t0, int nt,
                                  bool &nan)
 {
+    constexpr int KK = K > 0 ? K : 1;
     double rm = 0.0;
-    for (int r = t0; r < n; r += nt) {
-        double acc = __ldcg(src + r) * scale - S.diag64[r] * __ldcg(y + r);
+    for (int r0 = t0; r0 < n; r0 += R * nt) {
+        double sv[R], dv[R], yv[R], av[R][KK], ys[R][KK];
 #pragma unroll
-        for (int k = 0; k < K; ++k) {
-            const double ae = S.a64[(size_t)k * n + r];
-            if (ae != 0.0) acc += ae * __ldcg(y + r + off[k]);
+        for (int u = 0; u < R; ++u) {
+            const int r = min(r0 + u * nt, n - 1);
+            sv[u] = __ldcg(src + r);
+            dv[u] = S.diag64[r];
+            yv[u] = __ldcg(y + r);
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                av[u][k] = S.a64[(size_t)k * n + r];
+                int q = r + off[k];
+                q = q < 0 ? 0 : (q >= n ? n - 1 : q);
+                ys[u][k] = __ldcg(y + q);
+            }
         }
-        if (out) out[r] = acc;
-        const double v = fabs(acc);
-        if (v != v) nan = true;
-        else rm = fmax(rm, v);
+#pragma unroll
+        for (int u = 0; u < R; ++u) {
+            const int r = r0 + u * nt;
+            if (r >= n) continue;
+            double acc = sv[u] * scale - dv[u] * yv[u];
+#pragma unroll
+            for (int k = 0; k < K; ++k)
+                if (av[u][k] != 0.0) acc += av[u][k] * ys[u][k];
+            if (out) out[r] = acc;
+            const double v = fabs(acc);
+            if (v != v) nan = true;
+            else rm = fmax(rm, v);
+        }
     }
     return rm;
 }
 
+// The loads of one row of the mean-message update with frozen precision
+// messages, and the update itself: the arithmetic of sweep_row_mean_stencil,
+// split so that several rows' loads can be in flight before any update.
+template <typename T, int K>
+struct MeanRow {
+    T ge[K > 0 ? K : 1], bs[K > 0 ? K : 1], mr[K > 0 ? K : 1];
+    T bb, bx, px;
+};
+
+template <typename T, int K>
+__device__ __forceinline__ void mean_row_load(int r, int n, const int *off, const int *krev,
+                                              const T *g, const T *b, const T *P, const T *Min,
+                                              const T *Bin, bool belief, MeanRow<T, K> &M)
+{
+    const size_t nn = (size_t)n;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        M.ge[k] = __ldcg(g + (size_t)k * nn + r);
+        int s = r + off[k];
+        s = s < 0 ? 0 : (s >= n ? n - 1 : s);
+        M.bs[k] = __ldcg(Bin + s);
+        M.mr[k] = __ldcg(Min + (size_t)krev[k] * nn + s);
+    }
+    M.bb = __ldcg(b + r);
+    if (belief) {
+        M.bx = __ldcg(Bin + r);
+        M.px = __ldcg(P + r);
+    }
+}
+
+template <typename T, int K>
+__device__ __forceinline__ void mean_row_update(int r, int n, const MeanRow<T, K> &M, T *Mout,
+                                                T *Bout, double *x)
+{
+    const size_t nn = (size_t)n;
+    T bn = M.bb;
+    if (x) x[r] = (double)(M.bx / M.px);
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const T mu = nonzero(M.ge[k]) ? M.ge[k] * (M.bs[k] - M.mr[k]) : T(0);
+        Mout[(size_t)k * nn + r] = mu;
+        bn += mu;
+    }
+    Bout[r] = bn;
+}
+
 // `kk` flood sweeps of system S from state `cur` (beliefs of the last go to y);
 // with frozen precision messages only the mean messages move.
-template <typename T, int K, typename Team>
+// With frozen precision messages (where a batched solve spends most of its
+// sweeps) R rows of a thread are in flight at once (rows r0 + u nt, u < R):
+// every load of the R rows, then their updates, with the per-row arithmetic
+// of the single-system mean sweep.  Full sweeps take one row at a time (the
+// row state of two would not fit the registers).
+template <typename T, int K, int R, typename Team>
 __device__ void batch_sweeps(const BatchSys<T> &S, int n, const int *off, const int *krev, int kk,
                              int &cur, double *y, Team &tm, bool frozen)
 {
@@ -162,9 +235,19 @@ __device__ void batch_sweeps(const BatchSys<T> &S, int n, const int *off, const 
             T *Bin = cur ? S.B1 : S.B0, *Bout = cur ? S.B0 : S.B1;
             T *Pc = cur ? S.P1 : S.P0;
             double *yo = j == kk - 1 ? y : nullptr;
-            for (int r = tm.t0; r < n; r += tm.nt)
-                sweep_row_mean_stencil<T, K, true>(r, n, off, krev, S.g, S.bT, Pc, Min, Bin, Mout,
-                                                   Bout, yo);
+            for (int r0 = tm.t0; r0 < n; r0 += R * tm.nt) {
+                MeanRow<T, K> rows[R];
+#pragma unroll
+                for (int u = 0; u < R; ++u) {
+                    const int r = r0 + u * tm.nt;
+                    if (r < n) mean_row_load<T, K>(r, n, off, krev, S.g, S.bT, Pc, Min, Bin, yo != nullptr, rows[u]);
+                }
+#pragma unroll
+                for (int u = 0; u < R; ++u) {
+                    const int r = r0 + u * tm.nt;
+                    if (r < n) mean_row_update<T, K>(r, n, rows[u], Mout, Bout, yo);
+                }
+            }
             tm.sync();
             cur ^= 1;
         }
@@ -244,7 +327,7 @@ __device__ bool batch_maybe_freeze(const BatchSys<T> &S, int n, const int *off, 
 // they do not depend on the right-hand side) for at most inner_max sweeps or
 // until its own relative residual <= inner_tol, then x += ||r|| e and
 // r = b - A x in double; max_iter caps the total sweeps.
-template <typename T, int K, typename Team>
+template <typename T, int K, int R, typename Team>
 __device__ void solve_system(const BatchSys<T> &S, int id, const double *b, double *x, Team &tm,
                              double tol, int max_iter, int check_every, int refine,
                              double inner_tol, int inner_max, int freeze, BatchResult *res,
@@ -285,11 +368,11 @@ __device__ void solve_system(const BatchSys<T> &S, int id, const double *b, doub
     if (!refine) {
         while (status == GABP_E_NOT_CONVERGED && it < max_iter) {
             const int kk = min(check_every, max_iter - it);
-            batch_sweeps<T, K>(S, n, off, krev, kk, cur, x, tm, frozen);
+            batch_sweeps<T, K, R>(S, n, off, krev, kk, cur, x, tm, frozen);
             it += kk;
             if (freeze && !frozen) frozen = batch_maybe_freeze<T, K>(S, n, off, krev, cur, frz_rel, tm);
             bool nan = false;
-            double rm = batch_residual<T, K>(S, n, off, b, 1.0, x, nullptr, t0, nt, nan);
+            double rm = batch_residual<T, K, 1>(S, n, off, b, 1.0, x, nullptr, t0, nt, nan);
             if (nan) atomicOr(flags, 2u);
             rm = tm.max(rm, &fl);
             rr = rm / bnorm;
@@ -324,13 +407,13 @@ __device__ void solve_system(const BatchSys<T> &S, int id, const double *b, doub
             int inner = 0;
             while (inner < inner_max && it < max_iter) {
                 const int kk = min(min(check_every, inner_max - inner), max_iter - it);
-                batch_sweeps<T, K>(S, n, off, krev, kk, cur, S.e, tm, frozen);
+                batch_sweeps<T, K, R>(S, n, off, krev, kk, cur, S.e, tm, frozen);
                 inner += kk;
                 it += kk;
                 if (freeze && !frozen)
                     frozen = batch_maybe_freeze<T, K>(S, n, off, krev, cur, frz_rel, tm);
                 bool nan = false;
-                double rin = batch_residual<T, K>(S, n, off, S.r, 1.0 / scale, S.e, nullptr, t0,
+                double rin = batch_residual<T, K, 1>(S, n, off, S.r, 1.0 / scale, S.e, nullptr, t0,
                                                   nt, nan);
                 if (nan) atomicOr(flags, 2u);
                 rin = tm.max(rin, &fl);
@@ -345,7 +428,7 @@ __device__ void solve_system(const BatchSys<T> &S, int id, const double *b, doub
             for (int r = t0; r < n; r += nt) x[r] = __ldcg(x + r) + scale * __ldcg(S.e + r);
             tm.sync();
             bool nan = false;
-            double rm = batch_residual<T, K>(S, n, off, b, 1.0, x, S.r, t0, nt, nan);
+            double rm = batch_residual<T, K, 1>(S, n, off, b, 1.0, x, S.r, t0, nt, nan);
             if (nan) atomicOr(flags, 2u);
             rm = tm.max(rm, &fl);
             rr = rm / bnorm;
@@ -369,7 +452,7 @@ __device__ void solve_system(const BatchSys<T> &S, int id, const double *b, doub
 // launch is read back with coherent loads (sweep_row_stencil<..., true>,
 // __ldcg), never through the non-coherent read-only path; the barriers order
 // it across the team.
-template <typename T, int K>
+template <typename T, int K, int R>
 __global__ void __launch_bounds__(512) k_batch_solve(
     const BatchSys<T> *__restrict__ sys, const int *__restrict__ order, int nsys, int nbig,
     const double *const *__restrict__ bptr, double *const *__restrict__ xptr, int *queue,
@@ -395,7 +478,7 @@ __global__ void __launch_bounds__(512) k_batch_solve(
                 sh.off[tid] = sys[id].off[tid];
                 sh.krev[tid] = sys[id].krev[tid];
             }
-            solve_system<T, K>(sys[id], id, bptr[id], xptr[id], tm, tol, max_iter, check_every,
+            solve_system<T, K, R>(sys[id], id, bptr[id], xptr[id], tm, tol, max_iter, check_every,
                                refine, inner_tol, inner_max, freeze, res, rank0 && tid == 0);
         }
     }
@@ -414,7 +497,7 @@ __global__ void __launch_bounds__(512) k_batch_solve(
             sh.off[tid] = sys[id].off[tid];
             sh.krev[tid] = sys[id].krev[tid];
         }
-        solve_system<T, K>(sys[id], id, bptr[id], xptr[id], tm, tol, max_iter, check_every, refine,
+        solve_system<T, K, R>(sys[id], id, bptr[id], xptr[id], tm, tol, max_iter, check_every, refine,
                            inner_tol, inner_max, freeze, res, tid == 0);
     }
 }
@@ -423,20 +506,20 @@ __global__ void __launch_bounds__(512) k_batch_solve(
 
 // Clusters above the portable 8 CTAs (16 on this GPU) need the kernel's
 // non-portable attribute; set before every occupancy query and launch.
-template <typename T, int K>
+template <typename T, int K, int R>
 void allow_big_clusters()
 {
-    if (cudaFuncSetAttribute(k_batch_solve<T, K>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
+    if (cudaFuncSetAttribute(k_batch_solve<T, K, R>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
         cudaGetLastError();
 }
 
-template <typename T, int K>
+template <typename T, int K, int R>
 cudaError_t launch_batch_k(int cs, int grid, int block, const void *sys, const int *order, int nsys,
                            int nbig, const double *const *bptr, double *const *xptr, int *queue, double tol,
                            int max_iter, int check_every, int refine, double inner_tol,
                            int inner_max, int freeze, void *res, cudaStream_t s)
 {
-    if (cs > 8) allow_big_clusters<T, K>();
+    if (cs > 8) allow_big_clusters<T, K, R>();
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid, 1, 1);
     cfg.blockDim = dim3(block, 1, 1);
@@ -449,39 +532,42 @@ cudaError_t launch_batch_k(int cs, int grid, int block, const void *sys, const i
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_batch_solve<T, K>, (const BatchSys<T> *)sys, order, nsys, nbig, bptr,
+    return cudaLaunchKernelEx(&cfg, k_batch_solve<T, K, R>, (const BatchSys<T> *)sys, order, nsys, nbig, bptr,
                               xptr, queue, tol, max_iter, check_every, refine, inner_tol, inner_max,
                               freeze, (BatchResult *)res);
 }
 
+// Rows in flight per thread: 1 for every diagonal count, 2 also for the 5- and
+// 9-point orders (K = 4, 8).
+bool batch_rows_supported(int K, int rows) { return rows == 1 || (rows == 2 && (K == 4 || K == 8)); }
+
 template <typename T>
-cudaError_t launch_batch(int K, int cs, int grid, int block, const void *sys, const int *order,
+cudaError_t launch_batch(int K, int rows, int cs, int grid, int block, const void *sys, const int *order,
                          int nsys, int nbig, const double *const *bptr, double *const *xptr, int *queue,
                          double tol, int max_iter, int check_every, int refine, double inner_tol,
                          int inner_max, int freeze, void *res, cudaStream_t s)
 {
-#define GABP_BATCH_CASE(KK)                                                                     \
-    case KK:                                                                                    \
-        return launch_batch_k<T, KK>(cs, grid, block, sys, order, nsys, nbig, bptr, xptr, queue, tol, \
-                                     max_iter, check_every, refine, inner_tol, inner_max, freeze, \
-                                     res, s);
-    switch (K) {
-        GABP_BATCH_CASE(0)
-        GABP_BATCH_CASE(2)
-        GABP_BATCH_CASE(4)
-        GABP_BATCH_CASE(6)
-        GABP_BATCH_CASE(8)
-        default:
-            return cudaErrorInvalidValue;
-    }
+#define GABP_BATCH_CASE(KK, RR)                                                                       \
+    if (K == KK && rows == RR)                                                                        \
+        return launch_batch_k<T, KK, RR>(cs, grid, block, sys, order, nsys, nbig, bptr, xptr, queue, tol, \
+                                         max_iter, check_every, refine, inner_tol, inner_max, freeze, \
+                                         res, s);
+    GABP_BATCH_CASE(0, 1)
+    GABP_BATCH_CASE(2, 1)
+    GABP_BATCH_CASE(4, 1)
+    GABP_BATCH_CASE(6, 1)
+    GABP_BATCH_CASE(8, 1)
+    GABP_BATCH_CASE(4, 2)
+    GABP_BATCH_CASE(8, 2)
 #undef GABP_BATCH_CASE
+    return cudaErrorInvalidValue;
 }
 
 // Clusters of `cs` CTAs of `block` threads that can be resident at once (0 = none).
-template <typename T, int K>
+template <typename T, int K, int R>
 int batch_max_clusters_k(int cs, int block)
 {
-    if (cs > 8) allow_big_clusters<T, K>();
+    if (cs > 8) allow_big_clusters<T, K, R>();
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(cs, 1, 1);
     cfg.blockDim = dim3(block, 1, 1);
@@ -493,7 +579,7 @@ int batch_max_clusters_k(int cs, int block)
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     int nc = 0;
-    if (cudaOccupancyMaxActiveClusters(&nc, k_batch_solve<T, K>, &cfg) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveClusters(&nc, k_batch_solve<T, K, R>, &cfg) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
@@ -501,26 +587,28 @@ int batch_max_clusters_k(int cs, int block)
 }
 
 template <typename T>
-int batch_max_clusters(int K, int cs, int block)
+int batch_max_clusters(int K, int rows, int cs, int block)
 {
+    if (!batch_rows_supported(K, rows)) return 0;
+    if (rows == 2) return K == 4 ? batch_max_clusters_k<T, 4, 2>(cs, block) : batch_max_clusters_k<T, 8, 2>(cs, block);
     switch (K) {
-        case 0: return batch_max_clusters_k<T, 0>(cs, block);
-        case 2: return batch_max_clusters_k<T, 2>(cs, block);
-        case 4: return batch_max_clusters_k<T, 4>(cs, block);
-        case 6: return batch_max_clusters_k<T, 6>(cs, block);
-        case 8: return batch_max_clusters_k<T, 8>(cs, block);
+        case 0: return batch_max_clusters_k<T, 0, 1>(cs, block);
+        case 2: return batch_max_clusters_k<T, 2, 1>(cs, block);
+        case 4: return batch_max_clusters_k<T, 4, 1>(cs, block);
+        case 6: return batch_max_clusters_k<T, 6, 1>(cs, block);
+        case 8: return batch_max_clusters_k<T, 8, 1>(cs, block);
         default: return 0;
     }
 }
 
-template cudaError_t launch_batch<float>(int, int, int, int, const void *, const int *, int, int,
+template cudaError_t launch_batch<float>(int, int, int, int, int, const void *, const int *, int, int,
                                          const double *const *, double *const *, int *, double,
                                          int, int, int, double, int, int, void *, cudaStream_t);
-template cudaError_t launch_batch<double>(int, int, int, int, const void *, const int *, int, int,
+template cudaError_t launch_batch<double>(int, int, int, int, int, const void *, const int *, int, int,
                                           const double *const *, double *const *, int *, double,
                                           int, int, int, double, int, int, void *, cudaStream_t);
-template int batch_max_clusters<float>(int, int, int);
-template int batch_max_clusters<double>(int, int, int);
+template int batch_max_clusters<float>(int, int, int, int);
+template int batch_max_clusters<double>(int, int, int, int);
 
 void fill_batch_sys(int prec, void *dst, int n, const StencilParams &sp, const void *a, const void *c,
                     const void *diag, const double *a64, const double *diag64, void *const L[2],

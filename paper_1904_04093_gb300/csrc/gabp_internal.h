@@ -228,15 +228,17 @@ cudaError_t launch_mg_prolong_residual(const StencilParams &sp, int mf, const do
 cudaError_t launch_dense_gemv(const double *M, const double *x, double *y, int n, cudaStream_t s);
 
 // ---- batched persistent solver (batch.cu) ----
-// cs = CTAs per thread-block cluster (1..8), grid a multiple of cs; the first
-// nbig systems of `order` are solved by whole clusters, the rest by single CTAs
+// cs = CTAs per thread-block cluster (1..16), grid a multiple of cs; the first
+// nbig systems of `order` are solved by whole clusters, the rest by single CTAs;
+// rows = rows in flight per thread (batch_rows_supported)
+bool batch_rows_supported(int K, int rows);
 template <typename T>
-cudaError_t launch_batch(int K, int cs, int grid, int block, const void *sys, const int *order,
+cudaError_t launch_batch(int K, int rows, int cs, int grid, int block, const void *sys, const int *order,
                          int nsys, int nbig, const double *const *bptr, double *const *xptr, int *queue,
                          double tol, int max_iter, int check_every, int refine, double inner_tol,
                          int inner_max, int freeze, void *res, cudaStream_t s);
 template <typename T>
-int batch_max_clusters(int K, int cs, int block);
+int batch_max_clusters(int K, int rows, int cs, int block);
 void fill_batch_sys(int prec, void *dst, int n, const StencilParams &sp, const void *a, const void *c,
                     const void *diag, const double *a64, const double *diag64, void *const L[2],
                     void *const M[2], void *const P[2], void *const B[2], void *bT, double *e,

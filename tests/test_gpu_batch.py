@@ -53,7 +53,38 @@ def test_batch_equals_single_solves(g, check_every, shape):
         assert rel(host(x), host(xs1)) <= 1e-14
 
 
+@pytest.mark.parametrize("rows,min_rows", [(2, 4), (2, 2), (1, 8)])
+def test_batch_params_keep_single_solve_iterates(g, rows, min_rows):
+    """Two rows in flight per thread in the mean-message sweeps, and other
+    thresholds for cluster teams, leave each system's iterates those of
+    gabp_solve (frozen precision messages on, so the mean sweeps run)."""
+    systems = _systems(nsys=7, smin=16, smax=72, seed=23)
+    solvers = [g.GabpSolver(A, "fp64", check_every=5, freeze_lambda=1) for A, _ in systems]
+    batch = g.Batch(solvers, check_every=5)
+    batch.set_shape(256, 2)
+    batch.set_params(rows=rows, min_rows=min_rows)
+    info = batch.info()
+    assert info["rows"] == rows and info["min_rows"] == min_rows and info["check_every"] == 5
+    xs, its, rrs, sts = batch.solve([dev(b) for _, b in systems], 1e-10, 5000)
+    assert all(s == g.OK for s in sts)
+    ref = g.Batch([g.GabpSolver(A, "fp64", check_every=5, freeze_lambda=1) for A, _ in systems],
+                  check_every=5)
+    ref.set_shape(256, 2)
+    x1, it1, rr1, st1 = ref.solve([dev(b) for _, b in systems], 1e-10, 5000)
+    assert its == it1
+    for a, b_ in zip(xs, x1):
+        assert torch.equal(a, b_)
+
+
+def test_batch_rows_refused_for_other_stencils(g):
+    A = P.tridiag(64, 2.0, -1.0, -0.5)  # two diagonals
+    batch = g.Batch([g.GabpSolver(A, "fp64", layout="stencil")], check_every=5)
+    with pytest.raises(g.GabpError):
+        batch.set_params(rows=2)
+
+
 def test_batch_matches_oracle(g):
+    """Tuned on its first solve: an explicit check interval (here 1) is kept."""
     systems = _systems(nsys=5, seed=11)
     solvers = [g.GabpSolver(A, "fp64", check_every=1) for A, _ in systems]
     batch = g.Batch(solvers, check_every=1)
@@ -82,9 +113,11 @@ def test_batch_float_workload_tolerance(g):
     (the batched workload's target)."""
     systems = _systems(nsys=12, smin=16, smax=64, seed=13)
     solvers = [g.GabpSolver(A, "fp32_ir") for A, _ in systems]
-    batch = g.Batch(solvers, check_every=10)
+    batch = g.Batch(solvers, check_every=0)  # the check interval tuned as well
     blk, cs = batch.tune([dev(b) for _, b in systems], 1e-6, 20000)
     assert blk in (256, 512) and cs in (1, 2, 4, 8, 16)
+    info = batch.info()
+    assert info["rows"] in (1, 2) and info["min_rows"] in (2, 4, 8) and info["check_every"] in (10, 20)
     xs, its, rrs, sts = batch.solve([dev(b) for _, b in systems], 1e-6, 20000)
     assert all(s == g.OK for s in sts)
     for (A, b), x, rr in zip(systems, xs, rrs):
@@ -236,7 +269,7 @@ def test_batch_full_workload(g):
     systems = P.config_c4_batch(nsys=512, smax=256)
     solvers = [g.GabpSolver(A, "fp32_ir") for A, _ in systems]
     bs = [dev(b) for _, b in systems]
-    batch = g.Batch(solvers, check_every=10)
+    batch = g.Batch(solvers, check_every=0)  # as the bench runs it: check interval tuned too
     batch.tune(bs, 1e-6, 20000)
     xs, its, rrs, sts = batch.solve(bs, 1e-6, 20000)
     assert all(s == g.OK for s in sts)
