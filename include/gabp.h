@@ -73,7 +73,8 @@ typedef struct {
     int layout;          /* gabp_layout */
     int check_every;     /* sweeps between residual checks in gabp_solve (>= 1) */
     int use_graphs;      /* 1: replay each chunk of sweeps as a captured CUDA graph */
-    int ir_inner_max;    /* GABP_FP32_IR: float sweeps per refinement step, at most */
+    int ir_inner_max;    /* GABP_FP32_IR: float sweeps per refinement step, at most
+                            (0: 150 under the line schedule, 400 otherwise) */
     double ir_inner_tol; /* GABP_FP32_IR: inner relative residual that ends a refinement step */
     int block_size;      /* threads per block of the sweep kernel (0 = tuned default) */
     int freeze_lambda;   /* precomputed precision messages (Sec. 4.2): 1 on, 0 off,
@@ -86,10 +87,11 @@ typedef struct {
 } gabp_options;
 
 /* Fills `opt` with the defaults: FP64, auto layout, check_every 10, graphs on,
- * ir_inner_max 400, ir_inner_tol 1e-3, block_size 0, freeze_lambda -1, reorder -1.
- * (Short refinement steps win: restarting the float solve on a fresh double
- * residual every few hundred sweeps reaches 1e-10 in fewer total sweeps
- * than long inner solves.) */
+ * ir_inner_max 0 (400, or 150 under the line schedule), ir_inner_tol 1e-3,
+ * block_size 0, freeze_lambda -1, reorder -1.  (Short refinement steps win:
+ * restarting the float solve on a fresh double residual every few hundred
+ * sweeps -- fewer for line GaBP, whose fast initial phase is shorter --
+ * reaches 1e-10 in fewer total sweeps than long inner solves.) */
 void gabp_default_options(gabp_options *opt);
 
 /* Text for a status code (static storage). */
@@ -101,6 +103,14 @@ const char *gabp_last_error(void);
 /* Number of CUDA kernel launches this library has enqueued in the process so
  * far (a replayed graph counts each kernel it contains). */
 unsigned long long gabp_launch_count(void);
+
+/* 1 for the bounds-checked build of the library (compiled with GABP_DEBUG:
+ * kernels test the indices they compute or read -- CSR row pointers, columns
+ * and reverse edges, parity-class positions, multigrid tile indices, and that
+ * a stored non-zero coefficient has its neighbour inside the grid -- skip an
+ * access that fails and report it as GABP_E_CUDA "a device index check
+ * failed"), 0 for the release build.  No counterpart in the paper. */
+int gabp_debug_build(void);
 
 /*
  * Builds a context for the n x n CSR matrix A (host arrays, copied; Sec. 2.3:

@@ -65,7 +65,9 @@ _lib = None
 
 
 def library_path() -> str:
-    return _build.LIB
+    """``libgabp.so``, or the bounds-checked ``libgabp_debug.so`` when the environment
+    sets ``GABP_DEBUG=1`` (built by ``build.build(debug=True)``)."""
+    return _build.LIB_DEBUG if os.environ.get("GABP_DEBUG") == "1" else _build.LIB
 
 
 def load() -> ctypes.CDLL:
@@ -85,6 +87,7 @@ def load() -> ctypes.CDLL:
         "gabp_status_str": (ctypes.c_char_p, [I]),
         "gabp_last_error": (ctypes.c_char_p, []),
         "gabp_launch_count": (ctypes.c_ulonglong, []),
+        "gabp_debug_build": (I, []),
         "gabp_setup": (I, [ctypes.c_int32, I64, P, P, P, ctypes.POINTER(Options), P, ctypes.POINTER(P)]),
         "gabp_set_values": (I, [P, P]),
         "gabp_set_values_device": (I, [P, P]),
@@ -186,7 +189,8 @@ class GabpSolver:
     * ``check_every``: sweeps between residual checks of a solve;
     * ``use_graphs``: replay each chunk of sweeps from a captured CUDA graph;
     * ``ir_inner_max``, ``ir_inner_tol``: float sweeps per refinement step at
-      most, and the inner relative residual that ends a step (``fp32_ir``);
+      most (0: 150 under the line schedule, 400 otherwise), and the inner
+      relative residual that ends a step (``fp32_ir``);
     * ``block_size``: threads per block of the sweep kernel (0: the default);
     * ``freeze_lambda``: precomputed precision messages (Sec. 4.2): 1 on,
       0 off, -1 on for ``fp32_ir`` and off otherwise;
@@ -200,7 +204,7 @@ class GabpSolver:
     """
 
     def __init__(self, A, precision: str = "fp64", layout: str = "auto", check_every: int = 10,
-                 use_graphs: bool = True, ir_inner_max: int = 400, ir_inner_tol: float = 1e-3,
+                 use_graphs: bool = True, ir_inner_max: int = 0, ir_inner_tol: float = 1e-3,
                  block_size: int = 0, freeze_lambda: int = -1, reorder: int = -1, stream=None):
         L = load()
         torch = _torch()

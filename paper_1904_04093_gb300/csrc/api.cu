@@ -52,6 +52,13 @@ double bits_to_double(unsigned long long u)
     return d;
 }
 
+// The bounds-checked build's index flag as an error (never set in release builds).
+gabp_status index_error(unsigned fl)
+{
+    if (fl & FLAG_INDEX) return fail(GABP_E_CUDA, "a device index check failed (bounds-checked build)");
+    return GABP_OK;
+}
+
 struct GraphEntry {
     int k, parity, transposed, frozen;
     cudaGraphExec_t exec;
@@ -575,7 +582,8 @@ cudaError_t sweep_once(gabp_ctx *ctx, bool transposed, double *x, cudaStream_t s
     if (ctx->frozen) {
         ctx->cur = c1;
         return launch_sweep_mean(ctx->L, ctx->prec, ctx->g, ctx->bT, ctx->P[c0], ctx->Mm[c0],
-                                 ctx->B[c0], ctx->Mm[c1], ctx->B[c1], x, block_of(ctx), s);
+                                 ctx->B[c0], ctx->Mm[c1], ctx->B[c1], x, block_of(ctx),
+                                 &ctx->dstat[0].flags, s);
     }
     SweepArgs a;
     a.n = ctx->n;
@@ -818,6 +826,7 @@ gabp_status solve_plain(gabp_ctx *ctx, const double *b, double *x, double tol, i
             CKS(run_chunk(ctx, k, transposed));
             it += k;
             const DevStatus h = ctx->hstat[0];
+            if (h.flags & FLAG_INDEX) { st = index_error(h.flags); break; }
             if (freeze_enabled(ctx) && !(h.flags & FLAG_BREAKDOWN)) CKS(maybe_freeze(ctx, transposed));
             rr = bits_to_double(h.rmax) / binf;
             if (h.flags & FLAG_BREAKDOWN) { st = fail(GABP_E_BREAKDOWN, "zero or non-finite message denominator"); break; }
@@ -855,7 +864,10 @@ gabp_status solve_ir(gabp_ctx *ctx, const double *b, double *x, double tol, int 
     gabp_status st = GABP_E_NOT_CONVERGED;
     CKS(zero_messages(ctx, true, true));
     const int every = std::max(1, ctx->opt.check_every);
-    const int inner_max = ctx->opt.ir_inner_max > 0 ? ctx->opt.ir_inner_max : 400;
+    // float sweeps per refinement step: a restarted solve re-uses GaBP's fast initial
+    // phase, which is shorter for line GaBP (measured on the 2048^2 workload: 400 sweeps
+    // per step for the flood schedule, 150 for lines)
+    const int inner_max = ctx->opt.ir_inner_max > 0 ? ctx->opt.ir_inner_max : (ctx->lines_m > 0 ? 150 : 400);
     const double inner_tol = ctx->opt.ir_inner_tol > 0 ? ctx->opt.ir_inner_tol : 1e-3;
     if (bn == 0.0) st = GABP_OK;
     for (int outer = 0; st == GABP_E_NOT_CONVERGED && outer < 200 && total < max_iter; ++outer) {
@@ -871,6 +883,7 @@ gabp_status solve_ir(gabp_ctx *ctx, const double *b, double *x, double tol, int 
             inner += k;
             total += k;
             const DevStatus h = ctx->hstat[0];
+            if (h.flags & FLAG_INDEX) { st = index_error(h.flags); break; }
             if (freeze_enabled(ctx) && !(h.flags & FLAG_BREAKDOWN)) CKS(maybe_freeze(ctx, transposed));
             if (h.flags & FLAG_BREAKDOWN) { st = fail(GABP_E_BREAKDOWN, "zero or non-finite message denominator"); break; }
             const double rin = bits_to_double(h.rmax);  // ||r/s||_inf == 1
@@ -885,6 +898,7 @@ gabp_status solve_ir(gabp_ctx *ctx, const double *b, double *x, double tol, int 
         double rinf = 0.0;
         unsigned fl = 0;
         CKS(read_status(ctx, 1, &rinf, nullptr, &fl));
+        if (fl & FLAG_INDEX) { st = index_error(fl); break; }
         rr = rinf / bn;
         if ((fl & FLAG_NAN) || !std::isfinite(rr) || rr > kDivergence) { st = fail(GABP_E_DIVERGED, "residual diverged"); break; }
         if (rr <= tol) st = GABP_OK;
@@ -1047,7 +1061,7 @@ void gabp_default_options(gabp_options *opt)
     opt->layout = GABP_LAYOUT_AUTO;
     opt->check_every = 10;
     opt->use_graphs = 1;
-    opt->ir_inner_max = 400;
+    opt->ir_inner_max = 0;  // by schedule: 400 flood / coloured, 150 lines
     opt->ir_inner_tol = 1e-3;
     opt->block_size = 0;
     opt->freeze_lambda = -1;
@@ -1077,6 +1091,8 @@ const char *gabp_status_str(gabp_status s)
 const char *gabp_last_error(void) { return g_last_error.c_str(); }
 
 unsigned long long gabp_launch_count(void) { return launch_count(); }
+
+int gabp_debug_build(void) { return kIndexChecks ? 1 : 0; }
 
 gabp_status gabp_setup(int32_t n, int64_t nnz, const int64_t *indptr, const int32_t *indices,
                        const double *data, const gabp_options *opt, void *stream, gabp_ctx **out)
@@ -1555,6 +1571,7 @@ gabp_status gabp_sweep(gabp_ctx *ctx, const double *b, int nsweeps, double *x)
     if (xo != x && nsweeps > 0) CKS(store_vector(ctx, xo, x, ctx->stream));
     unsigned fl = 0;
     CKS(read_status(ctx, 0, nullptr, nullptr, &fl));
+    CKS(index_error(fl));
     if (fl & FLAG_BREAKDOWN) return fail(GABP_E_BREAKDOWN, "zero or non-finite message denominator");
     return GABP_OK;
 }
@@ -1581,6 +1598,7 @@ gabp_status gabp_time_sweeps(gabp_ctx *ctx, const double *b, int nsweeps, int fr
     CK(cudaEventElapsedTime(ms, ctx->ev0, ctx->ev1));
     unsigned fl = 0;
     CKS(read_status(ctx, 0, nullptr, nullptr, &fl));
+    CKS(index_error(fl));
     if (fl & FLAG_BREAKDOWN) return fail(GABP_E_BREAKDOWN, "zero or non-finite message denominator");
     return GABP_OK;
 }
@@ -1646,7 +1664,11 @@ gabp_status gabp_residual(gabp_ctx *ctx, const double *b, const double *x, doubl
     } else {
         CK(launch_residual(ctx->L, ctx->a64, ctx->diag64, b, x, r, &ctx->dstat[1], ctx->stream));
     }
-    if (rinf || binf) CKS(read_status(ctx, 1, rinf, binf, nullptr));
+    if (rinf || binf || kIndexChecks) {
+        unsigned fl = 0;
+        CKS(read_status(ctx, 1, rinf, binf, &fl));
+        CKS(index_error(fl));
+    }
     return GABP_OK;
 }
 
@@ -2061,14 +2083,14 @@ gabp_status mg_cycle_fused(mg_ctx *mg, int l, int last, int nu_pre, int nu_post,
     gabp_ctx *cc = mg->lv[l + 1];
     CK(launch_mg_restrict_residual(c->L.sp, mg->side[l], c->a64, c->diag64, b, X, E, T, mg->scale,
                                    mg->b[l + 1], cc->prec == 1 ? (float *)cc->bT : nullptr,
-                                   cc->prec == 0 ? cc->bres : nullptr, s));
+                                   cc->prec == 0 ? cc->bres : nullptr, &c->dstat[0].flags, s));
     CKS(mg_cycle_fused(mg, l + 1, last, nu_pre, nu_post, mg->b[l + 1], mg->x[l + 1], MG_RES_BT));
     // x2 = x1 + P e_c into x, and the post-smoothing right-hand side b - A x2
     const double *Xin = X ? mg->tbuf : nullptr;
     const double *Ein = X ? nullptr : E;
     CK(launch_mg_prolong_residual(c->L.sp, mg->side[l], c->a64, c->diag64, b, Xin, Ein,
                                   mg->x[l + 1], x, c->prec == 0 ? c->bres : nullptr,
-                                  c->prec == 1 ? (float *)c->bT : nullptr, s));
+                                  c->prec == 1 ? (float *)c->bT : nullptr, &c->dstat[0].flags, s));
     if (nu_post > 0) {
         CKS(mg_fused_sweeps(mg, l, nu_post));
         CK(launch_axpy(x, c->xbuf, 1.0, c->n, s));
@@ -2167,8 +2189,10 @@ gabp_status mg_check_flags(mg_ctx *mg)
         CK(cudaMemcpyAsync(&c->hstat[0].flags, &c->dstat[0].flags, sizeof(unsigned), cudaMemcpyDeviceToHost, mg->stream));
     }
     CK(cudaStreamSynchronize(mg->stream));
-    for (auto *c : mg->lv)
+    for (auto *c : mg->lv) {
+        CKS(index_error(c->hstat[0].flags));
         if (c->hstat[0].flags & FLAG_BREAKDOWN) return fail(GABP_E_BREAKDOWN, "zero or non-finite message denominator in a smoother");
+    }
     return GABP_OK;
 }
 
@@ -2219,9 +2243,12 @@ gabp_status mg_solve(mg_ctx *mg, const double *b, double *x, double tol, int max
         CK(cudaStreamSynchronize(s));
         rr = bits_to_double(mg->hstat->rmax) / bn;
         gabp_status fs = GABP_OK;
-        for (int l = 0; l < mg->levels; ++l)
+        for (int l = 0; l < mg->levels; ++l) {
             if (mg->hflags[l] & FLAG_BREAKDOWN)
                 fs = fail(GABP_E_BREAKDOWN, "zero or non-finite message denominator in a smoother");
+            if (mg->hflags[l] & FLAG_INDEX) fs = index_error(mg->hflags[l]);
+        }
+        if (fs == GABP_OK) fs = index_error(mg->hstat->flags);
         if (fs != GABP_OK) { st = fs; break; }
         if ((mg->hstat->flags & FLAG_NAN) || !std::isfinite(rr) || rr > kDivergence) { st = fail(GABP_E_DIVERGED, "residual diverged"); break; }
         if (rr <= tol) st = GABP_OK;

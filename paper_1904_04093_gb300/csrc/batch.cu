@@ -54,7 +54,7 @@ namespace cg = cooperative_groups;
 // Shared per-CTA state of the batched kernel.
 struct BatchShared {
     int idx;             // system index taken from a queue
-    unsigned flags;      // 1 breakdown, 2 non-finite residual
+    unsigned flags;      // 1 breakdown, 2 non-finite residual, 4 failed index check
     double red[33];      // reduction scratch; red[32] = this CTA's partial result
     int off[8], krev[8]; // diagonals of the current system
 };
@@ -179,6 +179,7 @@ template <typename T, int K>
 struct MeanRow {
     T ge[K > 0 ? K : 1], bs[K > 0 ? K : 1], mr[K > 0 ? K : 1];
     T bb, bx, px;
+    bool oob;  // bounds-checked build: a non-zero gain whose neighbour is outside [0, n)
 };
 
 template <typename T, int K>
@@ -187,10 +188,12 @@ __device__ __forceinline__ void mean_row_load(int r, int n, const int *off, cons
                                               const T *Bin, bool belief, MeanRow<T, K> &M)
 {
     const size_t nn = (size_t)n;
+    M.oob = false;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
         M.ge[k] = __ldcg(g + (size_t)k * nn + r);
         int s = r + off[k];
+        if (kIndexChecks && nonzero(M.ge[k]) && (s < 0 || s >= n)) M.oob = true;
         s = s < 0 ? 0 : (s >= n ? n - 1 : s);
         M.bs[k] = __ldcg(Bin + s);
         M.mr[k] = __ldcg(Min + (size_t)krev[k] * nn + s);
@@ -203,8 +206,8 @@ __device__ __forceinline__ void mean_row_load(int r, int n, const int *off, cons
 }
 
 template <typename T, int K>
-__device__ __forceinline__ void mean_row_update(int r, int n, const MeanRow<T, K> &M, T *Mout,
-                                                T *Bout, double *x)
+__device__ __forceinline__ unsigned mean_row_update(int r, int n, const MeanRow<T, K> &M, T *Mout,
+                                                    T *Bout, double *x)
 {
     const size_t nn = (size_t)n;
     T bn = M.bb;
@@ -216,6 +219,7 @@ __device__ __forceinline__ void mean_row_update(int r, int n, const MeanRow<T, K
         bn += mu;
     }
     Bout[r] = bn;
+    return kIndexChecks && M.oob ? 4u : 0u;
 }
 
 // `kk` flood sweeps of system S from state `cur` (beliefs of the last go to y);
@@ -235,6 +239,7 @@ __device__ void batch_sweeps(const BatchSys<T> &S, int n, const int *off, const 
             T *Bin = cur ? S.B1 : S.B0, *Bout = cur ? S.B0 : S.B1;
             T *Pc = cur ? S.P1 : S.P0;
             double *yo = j == kk - 1 ? y : nullptr;
+            unsigned bad = 0u;
             for (int r0 = tm.t0; r0 < n; r0 += R * tm.nt) {
                 MeanRow<T, K> rows[R];
 #pragma unroll
@@ -245,9 +250,10 @@ __device__ void batch_sweeps(const BatchSys<T> &S, int n, const int *off, const 
 #pragma unroll
                 for (int u = 0; u < R; ++u) {
                     const int r = r0 + u * tm.nt;
-                    if (r < n) mean_row_update<T, K>(r, n, rows[u], Mout, Bout, yo);
+                    if (r < n) bad |= mean_row_update<T, K>(r, n, rows[u], Mout, Bout, yo);
                 }
             }
+            if (kIndexChecks && bad) atomicOr(tm.flags(), bad);
             tm.sync();
             cur ^= 1;
         }
@@ -259,11 +265,11 @@ __device__ void batch_sweeps(const BatchSys<T> &S, int n, const int *off, const 
         T *Pin = cur ? S.P1 : S.P0, *Pout = cur ? S.P0 : S.P1;
         T *Bin = cur ? S.B1 : S.B0, *Bout = cur ? S.B0 : S.B1;
         double *yo = j == kk - 1 ? y : nullptr;
-        bool bad = false;
+        unsigned bad = 0u;  // FLAG_BREAKDOWN (1), and FLAG_INDEX (4) in the bounds-checked build
         for (int r = tm.t0; r < n; r += tm.nt)
             bad |= sweep_row_stencil<T, K, true>(r, n, off, krev, S.a, S.c, S.diag, S.bT, Lin, Min,
                                                  Pin, Bin, Lout, Mout, Pout, Bout, yo);
-        if (bad) atomicOr(tm.flags(), 1u);
+        if (bad) atomicOr(tm.flags(), bad);
         tm.sync();
         cur ^= 1;
     }
@@ -376,7 +382,8 @@ __device__ void solve_system(const BatchSys<T> &S, int id, const double *b, doub
             if (nan) atomicOr(flags, 2u);
             rm = tm.max(rm, &fl);
             rr = rm / bnorm;
-            if (fl & 1u) status = GABP_E_BREAKDOWN;
+            if (fl & 4u) status = GABP_E_CUDA;  // bounds-checked build: an index check failed
+            else if (fl & 1u) status = GABP_E_BREAKDOWN;
             else if ((fl & 2u) || !(rr <= 1e8)) status = GABP_E_DIVERGED;
             else if (rr <= tol) status = GABP_OK;
         }
@@ -420,8 +427,8 @@ __device__ void solve_system(const BatchSys<T> &S, int id, const double *b, doub
                 if (fl) break;
                 if (rin <= inner_tol) break;
             }
-            if (fl & 1u) {
-                status = GABP_E_BREAKDOWN;
+            if (fl & 5u) {
+                status = (fl & 4u) ? GABP_E_CUDA : GABP_E_BREAKDOWN;
                 break;
             }
             // x += ||r|| e ;  r = b - A x

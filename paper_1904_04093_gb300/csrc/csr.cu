@@ -51,7 +51,7 @@ __global__ void __launch_bounds__(kCsrBlock, csr_min_blocks(sizeof(T) == 8, EPT)
     const T *__restrict__ diag, const T *__restrict__ b, const T *__restrict__ Lin,
     const T *__restrict__ Min, const T *__restrict__ Pin, const T *__restrict__ Bin,
     T *__restrict__ Lout, T *__restrict__ Mout, T *__restrict__ Pout, T *__restrict__ Bout,
-    double *__restrict__ x, unsigned *__restrict__ flags)
+    double *__restrict__ x, unsigned *__restrict__ flags, int nslots)
 {
     constexpr int WT = 32 * EPT;
     constexpr int NW = kCsrBlock / 32;
@@ -65,15 +65,21 @@ __global__ void __launch_bounds__(kCsrBlock, csr_min_blocks(sizeof(T) == 8, EPT)
     const int r = r0 + lane;
     int lo = 0, hi = 0;
     T pn = T(0), bn = T(0);
+    bool oob = false;  // bounds-checked build: an index outside its array (access skipped)
     if (own) {
         lo = rowptr[r];
         hi = rowptr[r + 1];
+        if (kIndexChecks && !(0 <= lo && lo <= hi && hi <= nslots)) {
+            oob = true;
+            lo = hi = 0;
+        }
         if (kFull) pn = diag[r];
         bn = b[r];
         if (x) x[r] = (double)(Bin[r] / Pin[r]);
     }
-    const int e0 = __shfl_sync(0xffffffffu, lo, 0);
-    const int e1 = __shfl_sync(0xffffffffu, hi, nrows - 1);
+    int e0 = __shfl_sync(0xffffffffu, lo, 0);
+    int e1 = __shfl_sync(0xffffffffu, hi, nrows - 1);
+    if (kIndexChecks && __any_sync(0xffffffffu, oob)) e0 = e1 = 0;  // no slot range to walk
     T *wL = sL + (kFull ? w * WT : 0);
     T *wM = sM + w * WT;
     bool bad = false;
@@ -88,6 +94,11 @@ __global__ void __launch_bounds__(kCsrBlock, csr_min_blocks(sizeof(T) == 8, EPT)
             rs[j] = rev[e];
             ae[j] = a[e];
             if (kFull) ce[j] = c[e];
+            if (kIndexChecks && !((unsigned)cs[j] < (unsigned)n && (unsigned)rs[j] < (unsigned)nslots)) {
+                oob = true;
+                cs[j] = rs[j] = 0;
+                ae[j] = T(0);
+            }
         }
 #pragma unroll
         for (int j = 0; j < EPT; ++j) {
@@ -137,6 +148,7 @@ __global__ void __launch_bounds__(kCsrBlock, csr_min_blocks(sizeof(T) == 8, EPT)
         Bout[r] = bn;
     }
     if (bad) atomicOr(flags, FLAG_BREAKDOWN);
+    if (kIndexChecks && oob && flags) atomicOr(flags, FLAG_INDEX);
 }
 
 // Slots handled per thread and tile: the smallest power of two at least the
@@ -162,7 +174,7 @@ cudaError_t launch_T(const DevLayout &L, const void *a, const void *c, const voi
         k_sweep_csr<T, E, kFull><<<grid, kCsrBlock, 0, s>>>(                                    \
             L.n, L.rowptr, L.col, L.rev, (const T *)a, (const T *)c, (const T *)diag,           \
             (const T *)b, (const T *)Lin, (const T *)Min, (const T *)Pin, (const T *)Bin,       \
-            (T *)Lout, (T *)Mout, (T *)Pout, (T *)Bout, x, flags);                              \
+            (T *)Lout, (T *)Mout, (T *)Pout, (T *)Bout, x, flags, (int)L.slots);                \
         break;
     switch (ept_for(L)) {
         GABP_CSR_CASE(1)
@@ -189,13 +201,13 @@ cudaError_t launch_sweep_csr_edge(const DevLayout &L, int prec, const SweepArgs 
 
 cudaError_t launch_sweep_mean_csr_edge(const DevLayout &L, int prec, const void *g, const void *b,
                                        const void *P, const void *Min, const void *Bin, void *Mout,
-                                       void *Bout, double *x, cudaStream_t s)
+                                       void *Bout, double *x, unsigned *flags, cudaStream_t s)
 {
     if (prec == 0)
         return launch_T<double, false>(L, g, nullptr, nullptr, b, nullptr, Min, P, Bin, nullptr,
-                                       Mout, nullptr, Bout, x, nullptr, s);
+                                       Mout, nullptr, Bout, x, flags, s);
     return launch_T<float, false>(L, g, nullptr, nullptr, b, nullptr, Min, P, Bin, nullptr, Mout,
-                                  nullptr, Bout, x, nullptr, s);
+                                  nullptr, Bout, x, flags, s);
 }
 
 }  // namespace gabp

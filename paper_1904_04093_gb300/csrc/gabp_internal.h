@@ -61,7 +61,20 @@ struct DevStatus {
     unsigned int flags;
     unsigned int pad;
 };
-enum : unsigned { FLAG_BREAKDOWN = 1u, FLAG_NAN = 2u };
+enum : unsigned { FLAG_BREAKDOWN = 1u, FLAG_NAN = 2u, FLAG_INDEX = 4u };
+
+// The bounds-checked build (compiled with -DGABP_DEBUG, gabp_debug_build()
+// returns 1): kernels test the indices they compute or read (CSR columns,
+// reverse edges and row pointers, parity-class positions, multigrid tile
+// indices, and that a stored non-zero coefficient has its neighbour inside the
+// grid), skip an access that fails and set FLAG_INDEX in their status word;
+// the host turns the flag into GABP_E_CUDA.  Release builds compile the tests
+// out (kIndexChecks false).
+#ifdef GABP_DEBUG
+constexpr bool kIndexChecks = true;
+#else
+constexpr bool kIndexChecks = false;
+#endif
 
 // Pointers one sweep kernel launch needs (T = float or double, erased).
 struct SweepArgs {
@@ -98,7 +111,7 @@ cudaError_t launch_sweep(const DevLayout &L, int prec, const SweepArgs &a, int b
 cudaError_t launch_sweep_csr_edge(const DevLayout &L, int prec, const SweepArgs &a, cudaStream_t s);
 cudaError_t launch_sweep_mean_csr_edge(const DevLayout &L, int prec, const void *g, const void *b,
                                        const void *P, const void *Min, const void *Bin, void *Mout,
-                                       void *Bout, double *x, cudaStream_t s);
+                                       void *Bout, double *x, unsigned *flags, cudaStream_t s);
 cudaError_t launch_aggregate(const DevLayout &L, int prec, const void *diag, const void *b,
                              const void *Lm, const void *Mm, void *P, void *B, cudaStream_t s);
 // r = b - A x in double with off-diagonal coefficients a64 = -A (layout slots), max |r|, |b| into st
@@ -146,7 +159,7 @@ cudaError_t launch_freeze(const DevLayout &L, int prec, const void *a, const voi
                           void *g, unsigned *flags, cudaStream_t s);
 cudaError_t launch_sweep_mean(const DevLayout &L, int prec, const void *g, const void *b,
                               const void *P, const void *Min, const void *Bin, void *Mout,
-                              void *Bout, double *x, int block, cudaStream_t s);
+                              void *Bout, double *x, int block, unsigned *flags, cudaStream_t s);
 cudaError_t launch_lambda_change(int64_t slots, int prec, const void *L0, const void *L1,
                                  DevStatus *st, cudaStream_t s);
 // one colour phase of the coloured schedule (in place on L, M, P, B)
@@ -212,18 +225,19 @@ cudaError_t launch_prolong_add(const double *ec, int mc, double *xf, cudaStream_
 // fused transfers (mg.cu) on an m x m grid level whose stencil lies in the 3 x 3
 // neighbourhood (mg_fusable): x1 = X + E (nullable terms) and, optionally, x1 into
 // T for the tile's own points; r = b - A x1 restricted by full weighting, times
-// scale, into rc (double) and optionally rcf (float) / rcd (a second double copy)
+// scale, into rc (double) and optionally rcf (float) / rcd (a second double copy);
+// flags: the status word of the bounds-checked build
 bool mg_fusable(const StencilParams &sp, int m);
 cudaError_t launch_mg_restrict_residual(const StencilParams &sp, int mf, const double *a64,
                                         const double *diag64, const double *b, const double *X,
                                         const double *E, double *T, double scale, double *rc,
-                                        float *rcf, double *rcd, cudaStream_t s);
+                                        float *rcf, double *rcd, unsigned *flags, cudaStream_t s);
 // x2 = Xin + Ein + P ec (nullable Xin, Ein) into Xout (Xout may not alias Xin or
 // Ein); r = b - A x2 into r (double) and / or rf (float)
 cudaError_t launch_mg_prolong_residual(const StencilParams &sp, int mf, const double *a64,
                                        const double *diag64, const double *b, const double *Xin,
                                        const double *Ein, const double *ec, double *Xout,
-                                       double *r, float *rf, cudaStream_t s);
+                                       double *r, float *rf, unsigned *flags, cudaStream_t s);
 // y = M x for a dense row-major n x n matrix (coarse-grid solve)
 cudaError_t launch_dense_gemv(const double *M, const double *x, double *y, int n, cudaStream_t s);
 

@@ -61,9 +61,9 @@ __global__ void __launch_bounds__(256) k_sweep_stencil(
 {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n) return;
-    if (sweep_row_stencil<T, K>(r, n, sp.off, sp.krev, a, c, diag, b, Lin, Min, Pin, Bin, Lout,
-                                Mout, Pout, Bout, x))
-        atomicOr(flags, FLAG_BREAKDOWN);
+    const unsigned f = sweep_row_stencil<T, K>(r, n, sp.off, sp.krev, a, c, diag, b, Lin, Min, Pin,
+                                               Bin, Lout, Mout, Pout, Bout, x);
+    if (f) atomicOr(flags, f);
 }
 
 // ---------------------------------------------------------------------------
@@ -129,7 +129,7 @@ template <typename T, int K>
 __global__ void __launch_bounds__(256) k_sweep_mean_stencil(
     int n, StencilParams sp, const T *__restrict__ g, const T *__restrict__ b,
     const T *__restrict__ P, const T *__restrict__ Min, const T *__restrict__ Bin,
-    T *__restrict__ Mout, T *__restrict__ Bout, double *__restrict__ x)
+    T *__restrict__ Mout, T *__restrict__ Bout, double *__restrict__ x, unsigned *flags)
 {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n) return;
@@ -140,6 +140,7 @@ __global__ void __launch_bounds__(256) k_sweep_mean_stencil(
         const size_t e = (size_t)k * nn + r;
         ge[k] = g[e];
         int s = r + sp.off[k];
+        if (kIndexChecks && nonzero(ge[k]) && (s < 0 || s >= n)) atomicOr(flags, FLAG_INDEX);
         s = s < 0 ? 0 : (s >= n ? n - 1 : s);
         bs[k] = Bin[s];
         mr[k] = Min[(size_t)sp.krev[k] * nn + s];
@@ -436,8 +437,9 @@ __global__ void __launch_bounds__(256) k_residual_stencil(
 #pragma unroll
             for (int k = 0; k < K; ++k) {
                 int s = i + sp.off[k];
-                s = s < 0 ? 0 : (s >= n ? n - 1 : s);
                 av[u][k] = a64[(size_t)k * nn + i];
+                if (kIndexChecks && av[u][k] != 0.0 && (s < 0 || s >= n)) atomicOr(&st->flags, FLAG_INDEX);
+                s = s < 0 ? 0 : (s >= n ? n - 1 : s);
                 xv[u][k] = x[s];
             }
         }
@@ -467,12 +469,23 @@ __global__ void __launch_bounds__(256) k_residual_csr(
 {
     double rmax = 0.0, bmax = 0.0;
     bool nan = false;
+    const int nslots = kIndexChecks ? rowptr[n] : 0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const double bi = b[i];
         double acc = bi - diag64[i] * x[i];
-        for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+        int e0 = rowptr[i], e1 = rowptr[i + 1];
+        if (kIndexChecks && !(0 <= e0 && e0 <= e1 && e1 <= nslots)) {
+            atomicOr(&st->flags, FLAG_INDEX);
+            e0 = e1 = 0;
+        }
+        for (int e = e0; e < e1; ++e) {
             const double ae = a64[e];
-            if (ae != 0.0) acc += ae * x[col[e]];
+            const int j = col[e];
+            if (kIndexChecks && (unsigned)j >= (unsigned)n) {
+                atomicOr(&st->flags, FLAG_INDEX);
+                continue;
+            }
+            if (ae != 0.0) acc += ae * x[j];
         }
         if (r) r[i] = acc;
         const double v = fabs(acc);
@@ -1111,7 +1124,7 @@ cudaError_t launch_freeze(const DevLayout &L, int prec, const void *a, const voi
 
 cudaError_t launch_sweep_mean(const DevLayout &L, int prec, const void *g, const void *b,
                               const void *P, const void *Min, const void *Bin, void *Mout,
-                              void *Bout, double *x, int block, cudaStream_t s)
+                              void *Bout, double *x, int block, unsigned *flags, cudaStream_t s)
 {
     if (L.n == 0) return cudaSuccess;
     count_launches(s, 1);
@@ -1123,11 +1136,11 @@ cudaError_t launch_sweep_mean(const DevLayout &L, int prec, const void *g, const
         if (prec == 0)                                                                         \
             k_sweep_mean_stencil<double, KK><<<grid, block, 0, s>>>(                           \
                 L.n, L.sp, (const double *)g, (const double *)b, (const double *)P,             \
-                (const double *)Min, (const double *)Bin, (double *)Mout, (double *)Bout, x);  \
+                (const double *)Min, (const double *)Bin, (double *)Mout, (double *)Bout, x, flags); \
         else                                                                                   \
             k_sweep_mean_stencil<float, KK><<<grid, block, 0, s>>>(                            \
                 L.n, L.sp, (const float *)g, (const float *)b, (const float *)P,                \
-                (const float *)Min, (const float *)Bin, (float *)Mout, (float *)Bout, x);      \
+                (const float *)Min, (const float *)Bin, (float *)Mout, (float *)Bout, x, flags);  \
         break;
         switch (L.sp.K) {
             GABP_MEAN_CASE(0)
@@ -1144,7 +1157,7 @@ cudaError_t launch_sweep_mean(const DevLayout &L, int prec, const void *g, const
         }
 #undef GABP_MEAN_CASE
     } else {
-        return launch_sweep_mean_csr_edge(L, prec, g, b, P, Min, Bin, Mout, Bout, x, s);
+        return launch_sweep_mean_csr_edge(L, prec, g, b, P, Min, Bin, Mout, Bout, x, flags, s);
     }
     return cudaGetLastError();
 }

@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(256) k_mg_restrict_residual(
     int mf, Dirs dir, const double *__restrict__ a64, const double *__restrict__ diag64,
     const double *__restrict__ b, const double *__restrict__ X, const double *__restrict__ E,
     double *__restrict__ T, double scale, double *__restrict__ rc, float *__restrict__ rcf,
-    double *__restrict__ rcd)
+    double *__restrict__ rcd, unsigned *flags)
 {
     constexpr int XW = 2 * RX + 3, XH = 2 * RY + 3, RW = 2 * RX + 1, RH = 2 * RY + 1;
     __shared__ double xs[XH][XW];
@@ -102,6 +102,11 @@ __global__ void __launch_bounds__(256) k_mg_restrict_residual(
     for (int t = threadIdx.x; t < rw * rh; t += blockDim.x) {
         const int ly = t / rw, lx = t - ly * rw;
         const int64_t i = (int64_t)(2 * J0 + ly) * mf + (2 * I0 + lx);
+        if (kIndexChecks && (i < 0 || i >= n)) {
+            atomicOr(flags, FLAG_INDEX);
+            rs[ly][lx] = 0.0;
+            continue;
+        }
         double acc = fma(-diag64[i], xs[ly + 1][lx + 1], b[i]);
 #pragma unroll
         for (int k = 0; k < K; ++k) acc = fma(a64[k * n + i], xs[ly + 1 + dir.dy[k]][lx + 1 + dir.dx[k]], acc);
@@ -116,6 +121,10 @@ __global__ void __launch_bounds__(256) k_mg_restrict_residual(
         const double crn = rs[ly - 1][lx - 1] + rs[ly - 1][lx + 1] + rs[ly + 1][lx - 1] + rs[ly + 1][lx + 1];
         const double v = scale * (4.0 * ctr + 2.0 * edg + crn) * (1.0 / 16.0);
         const int64_t ic = (int64_t)(J0 + cj) * mc + (I0 + ci);
+        if (kIndexChecks && (ic < 0 || ic >= (int64_t)mc * mc)) {
+            atomicOr(flags, FLAG_INDEX);
+            continue;
+        }
         rc[ic] = v;
         if (rcf) rcf[ic] = (float)v;
         if (rcd) rcd[ic] = v;
@@ -127,7 +136,7 @@ __global__ void __launch_bounds__(256) k_mg_prolong_residual(
     int mf, Dirs dir, const double *__restrict__ a64, const double *__restrict__ diag64,
     const double *__restrict__ b, const double *__restrict__ Xin, const double *__restrict__ Ein,
     const double *__restrict__ ec, double *__restrict__ Xout, double *__restrict__ r,
-    float *__restrict__ rf)
+    float *__restrict__ rf, unsigned *flags)
 {
     constexpr int XW = PX + 2, XH = PY + 2;
     __shared__ double xs[XH][XW];
@@ -151,6 +160,10 @@ __global__ void __launch_bounds__(256) k_mg_prolong_residual(
         const int fx = x0 + lx, fy = y0 + ly;
         if (fx >= mf || fy >= mf) continue;
         const int64_t i = (int64_t)fy * mf + fx;
+        if (kIndexChecks && (i < 0 || i >= n)) {
+            atomicOr(flags, FLAG_INDEX);
+            continue;
+        }
         double acc = fma(-diag64[i], xs[ly + 1][lx + 1], b[i]);
 #pragma unroll
         for (int k = 0; k < K; ++k) acc = fma(a64[k * n + i], xs[ly + 1 + dir.dy[k]][lx + 1 + dir.dx[k]], acc);
@@ -186,7 +199,7 @@ bool mg_fusable(const StencilParams &sp, int m)
 cudaError_t launch_mg_restrict_residual(const StencilParams &sp, int mf, const double *a64,
                                         const double *diag64, const double *b, const double *X,
                                         const double *E, double *T, double scale, double *rc,
-                                        float *rcf, double *rcd, cudaStream_t s)
+                                        float *rcf, double *rcd, unsigned *flags, cudaStream_t s)
 {
     Dirs d;
     if (!grid_dirs(sp, mf, d) || mf % 2 == 0) return cudaErrorInvalidValue;
@@ -194,9 +207,9 @@ cudaError_t launch_mg_restrict_residual(const StencilParams &sp, int mf, const d
     if (mc < 1) return cudaErrorInvalidValue;
     const dim3 grid((unsigned)((mc + RX - 1) / RX), (unsigned)((mc + RY - 1) / RY));
     if (sp.K == 4)
-        k_mg_restrict_residual<4><<<grid, 256, 0, s>>>(mf, d, a64, diag64, b, X, E, T, scale, rc, rcf, rcd);
+        k_mg_restrict_residual<4><<<grid, 256, 0, s>>>(mf, d, a64, diag64, b, X, E, T, scale, rc, rcf, rcd, flags);
     else if (sp.K == 8)
-        k_mg_restrict_residual<8><<<grid, 256, 0, s>>>(mf, d, a64, diag64, b, X, E, T, scale, rc, rcf, rcd);
+        k_mg_restrict_residual<8><<<grid, 256, 0, s>>>(mf, d, a64, diag64, b, X, E, T, scale, rc, rcf, rcd, flags);
     else
         return cudaErrorInvalidValue;
     count_launches(s, 1);
@@ -206,15 +219,15 @@ cudaError_t launch_mg_restrict_residual(const StencilParams &sp, int mf, const d
 cudaError_t launch_mg_prolong_residual(const StencilParams &sp, int mf, const double *a64,
                                        const double *diag64, const double *b, const double *Xin,
                                        const double *Ein, const double *ec, double *Xout,
-                                       double *r, float *rf, cudaStream_t s)
+                                       double *r, float *rf, unsigned *flags, cudaStream_t s)
 {
     Dirs d;
     if (!grid_dirs(sp, mf, d) || mf % 2 == 0) return cudaErrorInvalidValue;
     const dim3 grid((unsigned)((mf + PX - 1) / PX), (unsigned)((mf + PY - 1) / PY));
     if (sp.K == 4)
-        k_mg_prolong_residual<4><<<grid, 256, 0, s>>>(mf, d, a64, diag64, b, Xin, Ein, ec, Xout, r, rf);
+        k_mg_prolong_residual<4><<<grid, 256, 0, s>>>(mf, d, a64, diag64, b, Xin, Ein, ec, Xout, r, rf, flags);
     else if (sp.K == 8)
-        k_mg_prolong_residual<8><<<grid, 256, 0, s>>>(mf, d, a64, diag64, b, Xin, Ein, ec, Xout, r, rf);
+        k_mg_prolong_residual<8><<<grid, 256, 0, s>>>(mf, d, a64, diag64, b, Xin, Ein, ec, Xout, r, rf, flags);
     else
         return cudaErrorInvalidValue;
     count_launches(s, 1);

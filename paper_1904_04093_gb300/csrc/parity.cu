@@ -117,8 +117,12 @@ __global__ void __launch_bounds__(256) k_sweep_parity(ParityGrid g, PhaseClasses
         const int nx = sx + g.dx[k], ny = sy + g.dy[k];
         const bool in = in_grid(g, nx, ny);
         const unsigned qn = (unsigned)((nx & 1) | ((ny & 1) << 1));
-        const long long src = in ? (long long)g.krev[k] * n + class_pos(g, nx, ny)
-                                 : (long long)k * n + pos;  // any valid address
+        long long src = in ? (long long)g.krev[k] * n + class_pos(g, nx, ny)
+                           : (long long)k * n + pos;  // any valid address
+        if (kIndexChecks && (src < 0 || src >= (long long)K * n)) {
+            atomicOr(flags, FLAG_INDEX);
+            src = 0;
+        }
         lin[k] = in && !((zl >> qn) & 1u) ? Lo[src] : T(0);
         min_[k] = in && !((zm >> qn) & 1u) ? Mo[src] : T(0);
         av[k] = a[(long long)k * n + pos];
@@ -167,11 +171,15 @@ __device__ __forceinline__ void parity_node(const ParityGrid &g, unsigned cx, un
                                             const T *__restrict__ diag,
                                             const T *__restrict__ b, T *Lo, T *Mo,
                                             double *__restrict__ x, bool &bad, unsigned zl,
-                                            unsigned zm)
+                                            unsigned zm, bool &bad_index)
 {
     constexpr int Q = PX | (PY << 1);
     const unsigned m = (unsigned)g.m, n = m * m;
     const unsigned pos = (unsigned)g.base[Q] + cy * (unsigned)g.w[Q] + cx;
+    if (kIndexChecks && pos >= n) {  // nothing of this node is touched
+        bad_index = true;
+        return;
+    }
     const unsigned sx = 2u * cx + PX, sy = 2u * cy + PY;
     T lin[K], min_[K], av[K], cv[K];
 #pragma unroll
@@ -180,10 +188,14 @@ __device__ __forceinline__ void parity_node(const ParityGrid &g, unsigned cx, un
         const int qt = ((PX + dx) & 1) | (((PY + dy) & 1) << 1);
         const int dx2 = floor_half(PX + dx), dy2 = floor_half(PY + dy);
         const bool in = (sx + dx < m) && (sy + dy < m);  // unsigned: -1 wraps high
-        const unsigned src =
+        unsigned src =
             in ? (unsigned)(K - 1 - k) * n + (unsigned)g.base[qt] +
                      (cy + dy2) * (unsigned)g.w[qt] + (cx + dx2)
                : (unsigned)k * n + pos;  // any valid address
+        if (kIndexChecks && (src >= (unsigned)K * n || pos >= n)) {
+            bad_index = true;
+            src = 0;
+        }
         lin[k] = in && !((zl >> qt) & 1u) ? Lo[src] : T(0);
         min_[k] = in && !((zm >> qt) & 1u) ? Mo[src] : T(0);
         av[k] = a[(unsigned)k * n + pos];
@@ -224,14 +236,15 @@ __global__ void __launch_bounds__(256) k_sweep_parity_std(ParityGrid g, PhaseCla
     const int q = z == 0 ? ph.q[0] : z == 1 ? ph.q[1] : z == 2 ? ph.q[2] : ph.q[3];
     const unsigned cx = blockIdx.x * blockDim.x + threadIdx.x, cy = blockIdx.y;
     if (cx >= (unsigned)pick4(g.w, q) || cy >= (unsigned)pick4(g.h, q)) return;
-    bool bad = false;
+    bool bad = false, bad_index = false;
     switch (q) {
-        case 0: parity_node<T, K, 0, 0>(g, cx, cy, a, c, diag, b, Lo, Mo, x, bad, zl, zm); break;
-        case 1: parity_node<T, K, 1, 0>(g, cx, cy, a, c, diag, b, Lo, Mo, x, bad, zl, zm); break;
-        case 2: parity_node<T, K, 0, 1>(g, cx, cy, a, c, diag, b, Lo, Mo, x, bad, zl, zm); break;
-        default: parity_node<T, K, 1, 1>(g, cx, cy, a, c, diag, b, Lo, Mo, x, bad, zl, zm); break;
+        case 0: parity_node<T, K, 0, 0>(g, cx, cy, a, c, diag, b, Lo, Mo, x, bad, zl, zm, bad_index); break;
+        case 1: parity_node<T, K, 1, 0>(g, cx, cy, a, c, diag, b, Lo, Mo, x, bad, zl, zm, bad_index); break;
+        case 2: parity_node<T, K, 0, 1>(g, cx, cy, a, c, diag, b, Lo, Mo, x, bad, zl, zm, bad_index); break;
+        default: parity_node<T, K, 1, 1>(g, cx, cy, a, c, diag, b, Lo, Mo, x, bad, zl, zm, bad_index); break;
     }
     if (bad) atomicOr(flags, FLAG_BREAKDOWN);
+    if (kIndexChecks && bad_index) atomicOr(flags, FLAG_INDEX);
 }
 
 }  // namespace

@@ -3,6 +3,8 @@
 
 #include <cuda_runtime.h>
 
+#include "gabp_internal.h"
+
 namespace gabp {
 
 // d == 0 or d not finite, decided on the bit pattern (integer pipe): the
@@ -77,6 +79,7 @@ struct StencilRow {
     T ae[K > 0 ? K : 1], ce[K > 0 ? K : 1], ps[K > 0 ? K : 1], bs[K > 0 ? K : 1],
         lr[K > 0 ? K : 1], mr[K > 0 ? K : 1];
     T dg, bb, bx, px;
+    bool oob;  // bounds-checked build: a non-zero coefficient whose neighbour is outside [0, n)
 };
 
 template <typename T, int K, bool kCoherent = false>
@@ -87,12 +90,14 @@ __device__ __forceinline__ void stencil_row_load(
     const T *__restrict__ Bin, bool belief, StencilRow<T, K> &R)
 {
     const size_t nn = (size_t)n;
+    R.oob = false;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
         const size_t e = (size_t)k * nn + r;
         R.ae[k] = a[e];
         R.ce[k] = c[e];
         int s = r + off[k];
+        if (kIndexChecks && nonzero(R.ae[k]) && (s < 0 || s >= n)) R.oob = true;
         s = s < 0 ? 0 : (s >= n ? n - 1 : s);
         const size_t er = (size_t)krev[k] * nn + s;
         R.ps[k] = ld_state<kCoherent>(Pin + s);
@@ -108,11 +113,13 @@ __device__ __forceinline__ void stencil_row_load(
     }
 }
 
+// Returns FLAG_BREAKDOWN on a zero or non-finite denominator (and, in the
+// bounds-checked build, FLAG_INDEX for a row whose layout is inconsistent).
 template <typename T, int K>
-__device__ __forceinline__ bool stencil_row_update(int r, int n, const StencilRow<T, K> &R,
-                                                   T *__restrict__ Lout, T *__restrict__ Mout,
-                                                   T *__restrict__ Pout, T *__restrict__ Bout,
-                                                   double *__restrict__ x)
+__device__ __forceinline__ unsigned stencil_row_update(int r, int n, const StencilRow<T, K> &R,
+                                                       T *__restrict__ Lout, T *__restrict__ Mout,
+                                                       T *__restrict__ Pout, T *__restrict__ Bout,
+                                                       double *__restrict__ x)
 {
     const size_t nn = (size_t)n;
     T pn = R.dg;
@@ -137,7 +144,7 @@ __device__ __forceinline__ bool stencil_row_update(int r, int n, const StencilRo
     }
     Pout[r] = pn;
     Bout[r] = bn;
-    return bad;
+    return (bad ? FLAG_BREAKDOWN : 0u) | (kIndexChecks && R.oob ? FLAG_INDEX : 0u);
 }
 
 // Flood update of row r in the stencil (per-diagonal) layout: slot k*n + r
@@ -149,10 +156,10 @@ __device__ __forceinline__ bool stencil_row_update(int r, int n, const StencilRo
 // belief before the update).  All loads of the row are issued before any
 // arithmetic: the reverse-edge gathers use an index clamped into [0, n), so
 // they are always in bounds and need not wait for a_e; a padded slot
-// (a_e == 0) discards what it loaded.  Returns true on a zero or non-finite
-// denominator.
+// (a_e == 0) discards what it loaded.  Returns the status bits of
+// stencil_row_update.
 template <typename T, int K, bool kCoherent = false>
-__device__ __forceinline__ bool sweep_row_stencil(
+__device__ __forceinline__ unsigned sweep_row_stencil(
     int r, int n, const int *off, const int *krev, const T *__restrict__ a,
     const T *__restrict__ c, const T *__restrict__ diag, const T *__restrict__ b,
     const T *__restrict__ Lin, const T *__restrict__ Min, const T *__restrict__ Pin,
@@ -166,19 +173,23 @@ __device__ __forceinline__ bool sweep_row_stencil(
 
 // Mean-message update of row r with frozen precision messages (the fixed
 // gains g_e = a_e / d_e): M'[e] = g_e (B_s - M[rev e]), B'_r = b_r + sum M'.
+// Returns FLAG_INDEX (bounds-checked build only) for a non-zero gain whose
+// neighbour lies outside [0, n), else 0.
 template <typename T, int K, bool kCoherent = false>
-__device__ __forceinline__ void sweep_row_mean_stencil(
+__device__ __forceinline__ unsigned sweep_row_mean_stencil(
     int r, int n, const int *off, const int *krev, const T *__restrict__ g,
     const T *__restrict__ b, const T *__restrict__ P, const T *__restrict__ Min,
     const T *__restrict__ Bin, T *__restrict__ Mout, T *__restrict__ Bout, double *__restrict__ x)
 {
     const size_t nn = (size_t)n;
     T ge[K > 0 ? K : 1], bs[K > 0 ? K : 1], mr[K > 0 ? K : 1];
+    bool oob = false;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
         const size_t e = (size_t)k * nn + r;
         ge[k] = ld_state<kCoherent>(g + e);
         int s = r + off[k];
+        if (kIndexChecks && nonzero(ge[k]) && (s < 0 || s >= n)) oob = true;
         s = s < 0 ? 0 : (s >= n ? n - 1 : s);
         bs[k] = ld_state<kCoherent>(Bin + s);
         mr[k] = ld_state<kCoherent>(Min + (size_t)krev[k] * nn + s);
@@ -192,6 +203,7 @@ __device__ __forceinline__ void sweep_row_mean_stencil(
         bn += mu;
     }
     Bout[r] = bn;
+    return kIndexChecks && oob ? FLAG_INDEX : 0u;
 }
 
 }  // namespace gabp

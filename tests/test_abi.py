@@ -49,7 +49,7 @@ def test_status_strings_and_defaults(lib):
     opt = g.Options()
     lib.gabp_default_options(ctypes.byref(opt))
     assert opt.precision == 0 and opt.check_every == 10 and opt.use_graphs == 1
-    assert opt.ir_inner_max == 400 and abs(opt.ir_inner_tol - 1e-3) < 1e-18
+    assert opt.ir_inner_max == 0 and abs(opt.ir_inner_tol - 1e-3) < 1e-18  # 0: by schedule
     assert opt.freeze_lambda == -1 and opt.block_size == 0
 
 
