@@ -85,6 +85,8 @@ def parse():
                          "schedules / csr print secondary lines for the other hot-path workloads")
     ap.add_argument("--nsys", type=int, default=512, help="batch: number of systems")
     ap.add_argument("--smax", type=int, default=256, help="batch: largest grid side")
+    ap.add_argument("--shape", default=None,
+                    help="batch: BLOCK,CLUSTER launch shape instead of the autotuner (profiling runs)")
     return ap.parse_args()
 
 
@@ -620,7 +622,11 @@ def measure_batch(args):
     solvers = [g.GabpSolver(A, "fp32_ir") for A, _ in systems]
     bs = [torch.as_tensor(b, device="cuda") for _, b in systems]
     batch = g.Batch(solvers, check_every=0)  # 0: the tuner chooses the check interval too
-    blk, cs = batch.tune(bs, 1e-6, 20000)
+    if getattr(args, "shape", None):
+        blk, cs = (int(v) for v in args.shape.split(","))
+        batch.set_shape(blk, cs)
+    else:
+        blk, cs = batch.tune(bs, 1e-6, 20000)
     xs, its, rrs, sts = batch.solve(bs, 1e-6, 20000)
     for _ in range(max(0, args.warmup - 1)):
         batch.solve(bs, 1e-6, 20000, xs)
