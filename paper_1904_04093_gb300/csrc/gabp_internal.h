@@ -232,12 +232,14 @@ cudaError_t launch_mg_restrict_residual(const StencilParams &sp, int mf, const d
                                         const double *diag64, const double *b, const double *X,
                                         const double *E, double *T, double scale, double *rc,
                                         float *rcf, double *rcd, unsigned *flags, cudaStream_t s);
-// x2 = Xin + Ein + P ec (nullable Xin, Ein) into Xout (Xout may not alias Xin or
-// Ein); r = b - A x2 into r (double) and / or rf (float)
+// x2 = Xin + Ein + P (ec + ec2) (nullable Xin, Ein, ec2; the coarse sum is formed
+// before the interpolation) into Xout (Xout may not alias Xin or Ein);
+// r = b - A x2 into r (double) and / or rf (float)
 cudaError_t launch_mg_prolong_residual(const StencilParams &sp, int mf, const double *a64,
                                        const double *diag64, const double *b, const double *Xin,
-                                       const double *Ein, const double *ec, double *Xout,
-                                       double *r, float *rf, unsigned *flags, cudaStream_t s);
+                                       const double *Ein, const double *ec, const double *ec2,
+                                       double *Xout, double *r, float *rf, unsigned *flags,
+                                       cudaStream_t s);
 // y = M x for a dense row-major n x n matrix (coarse-grid solve)
 cudaError_t launch_dense_gemv(const double *M, const double *x, double *y, int n, cudaStream_t s);
 

@@ -651,7 +651,9 @@ __global__ void k_prolong_add(const double *__restrict__ ec, int mc, double *__r
     xf[idx] += v;
 }
 
-// y = M x, one warp per row of a dense row-major matrix.
+// y = M x, one warp per row of a dense row-major matrix.  A lane keeps four
+// partial sums, so four pairs of loads are in flight per step instead of one
+// dependent chain through the row.
 __global__ void k_dense_gemv(const double *__restrict__ M, const double *__restrict__ x,
                              double *__restrict__ y, int n)
 {
@@ -659,8 +661,16 @@ __global__ void k_dense_gemv(const double *__restrict__ M, const double *__restr
     const int lane = threadIdx.x & 31;
     if (row >= n) return;
     const double *Mr = M + (int64_t)row * n;
-    double acc = 0.0;
-    for (int j = lane; j < n; j += 32) acc += Mr[j] * x[j];
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    int j = lane;
+    for (; j + 96 < n; j += 128) {
+        a0 = fma(Mr[j], x[j], a0);
+        a1 = fma(Mr[j + 32], x[j + 32], a1);
+        a2 = fma(Mr[j + 64], x[j + 64], a2);
+        a3 = fma(Mr[j + 96], x[j + 96], a3);
+    }
+    for (; j < n; j += 32) a0 = fma(Mr[j], x[j], a0);
+    double acc = (a0 + a1) + (a2 + a3);
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (lane == 0) y[row] = acc;
 }
@@ -1006,7 +1016,7 @@ cudaError_t launch_prolong_add(const double *ec, int mc, double *xf, cudaStream_
 cudaError_t launch_dense_gemv(const double *M, const double *x, double *y, int n, cudaStream_t s)
 {
     if (n == 0) return cudaSuccess;
-    const int rows_per_block = 8;
+    const int rows_per_block = 4;
     k_dense_gemv<<<(n + rows_per_block - 1) / rows_per_block, 32 * rows_per_block, 0, s>>>(M, x,
                                                                                           y, n);
     count_launches(s, 1);

@@ -11,55 +11,44 @@
 //    full-weighting restriction of r onto those coarse points (the coarse
 //    right-hand side, in double and in the coarse smoother's precision); x1
 //    is written out for the tile's own points when a later step needs it.
-//  k_mg_prolong_residual: x2 = x1 + P e_c (bilinear interpolation of the
-//    coarse solution) on a tile with a halo, written out for the tile's own
-//    points, and r = b - A x2 there, in double and / or float (the
-//    post-smoothing right-hand side).
+//  k_mg_prolong_residual: the coarse solution x_c (+ its post-smoothing
+//    correction e_c, when the coarse level left the sum to this kernel) on
+//    the tile's coarse patch, x2 = x1 + P x_c (bilinear interpolation) on a
+//    tile with a halo, written out for the tile's own points, and
+//    r = b - A x2 there, in double and / or float (the post-smoothing
+//    right-hand side).
 //
 // The fine residual and the interpolated correction stay in shared memory, so
 // a level's transfers read the matrix once per residual and write no
 // intermediate vector.  Every operation is done in the order the separate
 // kernels use (x + e, the residual's fma chain in slot order, the
-// restriction's sums), so the results are theirs.  A tile recomputes the
-// residual on one line of fine points beyond its own in each direction (about
-// 5 % extra at 32 x 16 coarse points per tile).  Grids are lexicographic,
-// m_f = 2 m_c + 1, the stencil inside the 3 x 3 neighbourhood.
+// restriction's sums, the interpolation's sums), so the results are theirs.
+// A tile recomputes the residual on one line of fine points beyond its own in
+// each direction.  Each level takes the large tiles when they give the GPU
+// enough CTAs, else small ones: a CTA walks its tile in a few dependent rounds
+// of loads, and on a coarse level with few tiles those rounds are the
+// kernel's whole duration.  Grids are lexicographic, m_f = 2 m_c + 1, the
+// stencil inside the 3 x 3 neighbourhood.
 #include <cuda_runtime.h>
 
 #include "gabp_internal.h"
 
+#ifndef GABP_MG_BIG_TILES_MIN
+#define GABP_MG_BIG_TILES_MIN 608
+#endif
+
 namespace gabp {
 namespace {
 
-constexpr int RX = 32, RY = 16;  // coarse points per restriction tile
-constexpr int PX = 64, PY = 16;  // fine points per prolongation tile
+// coarse points per restriction tile, fine points per prolongation tile
+constexpr int RX = 32, RY = 16, RXS = 8, RYS = 8;
+constexpr int PX = 64, PY = 16, PXS = 16, PYS = 16;
+// fewer large tiles than this (4 per SM) and a level takes the small ones
+constexpr int kBigTilesMin = GABP_MG_BIG_TILES_MIN;
 
 struct Dirs {
     int dx[8], dy[8];
 };
-
-__device__ __forceinline__ double coarse_v(const double *__restrict__ ec, int mc, int I, int J)
-{
-    return (I >= 0 && I < mc && J >= 0 && J < mc) ? ec[(int64_t)J * mc + I] : 0.0;
-}
-
-// Bilinear interpolation at fine point (fx, fy) (the rule of k_prolong_add).
-__device__ __forceinline__ double prolong_at(const double *__restrict__ ec, int mc, int fx, int fy)
-{
-    if (fx & 1) {
-        const int I = (fx - 1) >> 1;
-        if (fy & 1) return coarse_v(ec, mc, I, (fy - 1) >> 1);
-        return 0.5 * (coarse_v(ec, mc, I, (fy >> 1) - 1) + coarse_v(ec, mc, I, fy >> 1));
-    }
-    const int I0 = (fx >> 1) - 1, I1 = fx >> 1;
-    if (fy & 1) {
-        const int J = (fy - 1) >> 1;
-        return 0.5 * (coarse_v(ec, mc, I0, J) + coarse_v(ec, mc, I1, J));
-    }
-    const int J0 = (fy >> 1) - 1, J1 = fy >> 1;
-    return 0.25 * (coarse_v(ec, mc, I0, J0) + coarse_v(ec, mc, I1, J0) + coarse_v(ec, mc, I0, J1) +
-                   coarse_v(ec, mc, I1, J1));
-}
 
 __device__ __forceinline__ double sum_or_zero(const double *__restrict__ X,
                                               const double *__restrict__ E, int64_t i)
@@ -67,24 +56,24 @@ __device__ __forceinline__ double sum_or_zero(const double *__restrict__ X,
     return X ? (E ? X[i] + E[i] : X[i]) : (E ? E[i] : 0.0);
 }
 
-template <int K>
+template <int K, int TX, int TY>
 __global__ void __launch_bounds__(256) k_mg_restrict_residual(
     int mf, Dirs dir, const double *__restrict__ a64, const double *__restrict__ diag64,
     const double *__restrict__ b, const double *__restrict__ X, const double *__restrict__ E,
     double *__restrict__ T, double scale, double *__restrict__ rc, float *__restrict__ rcf,
     double *__restrict__ rcd, unsigned *flags)
 {
-    constexpr int XW = 2 * RX + 3, XH = 2 * RY + 3, RW = 2 * RX + 1, RH = 2 * RY + 1;
+    constexpr int XW = 2 * TX + 3, XH = 2 * TY + 3, RW = 2 * TX + 1, RH = 2 * TY + 1;
     __shared__ double xs[XH][XW];
     __shared__ double rs[RH][RW];
     const int mc = (mf - 1) / 2;
     const int64_t n = (int64_t)mf * mf;
-    const int I0 = blockIdx.x * RX, J0 = blockIdx.y * RY;
-    const int nI = min(RX, mc - I0), nJ = min(RY, mc - J0);
+    const int I0 = blockIdx.x * TX, J0 = blockIdx.y * TY;
+    const int nI = min(TX, mc - I0), nJ = min(TY, mc - J0);
     // own fine points [2 I0, ox1) x [2 J0, oy1); the last tile of a row or column
     // also owns the grid's last fine line
-    const int ox1 = I0 + RX >= mc ? mf : 2 * (I0 + RX);
-    const int oy1 = J0 + RY >= mc ? mf : 2 * (J0 + RY);
+    const int ox1 = I0 + TX >= mc ? mf : 2 * (I0 + TX);
+    const int oy1 = J0 + TY >= mc ? mf : 2 * (J0 + TY);
     const int fx0 = 2 * I0 - 1, fy0 = 2 * J0 - 1;
     for (int t = threadIdx.x; t < XW * XH; t += blockDim.x) {
         const int ly = t / XW, lx = t - ly * XW;
@@ -131,32 +120,69 @@ __global__ void __launch_bounds__(256) k_mg_restrict_residual(
     }
 }
 
-template <int K>
+// Bilinear interpolation at fine point (fx, fy) (the rule of k_prolong_add)
+// from the coarse patch cs, whose entry [j][i] is the coarse point
+// (cx0 + i, cy0 + j) (zero outside the coarse grid).
+template <int CW>
+__device__ __forceinline__ double prolong_at(const double (*cs)[CW], int cx0, int cy0, int fx, int fy)
+{
+    if (fx & 1) {
+        const int i = ((fx - 1) >> 1) - cx0;
+        if (fy & 1) return cs[((fy - 1) >> 1) - cy0][i];
+        const int j1 = (fy >> 1) - cy0;
+        return 0.5 * (cs[j1 - 1][i] + cs[j1][i]);
+    }
+    const int i1 = (fx >> 1) - cx0;
+    if (fy & 1) {
+        const int j = ((fy - 1) >> 1) - cy0;
+        return 0.5 * (cs[j][i1 - 1] + cs[j][i1]);
+    }
+    const int j1 = (fy >> 1) - cy0;
+    return 0.25 * (cs[j1 - 1][i1 - 1] + cs[j1 - 1][i1] + cs[j1][i1 - 1] + cs[j1][i1]);
+}
+
+template <int K, int TX, int TY>
 __global__ void __launch_bounds__(256) k_mg_prolong_residual(
     int mf, Dirs dir, const double *__restrict__ a64, const double *__restrict__ diag64,
     const double *__restrict__ b, const double *__restrict__ Xin, const double *__restrict__ Ein,
-    const double *__restrict__ ec, double *__restrict__ Xout, double *__restrict__ r,
-    float *__restrict__ rf, unsigned *flags)
+    const double *__restrict__ ec, const double *__restrict__ ec2, double *__restrict__ Xout,
+    double *__restrict__ r, float *__restrict__ rf, unsigned *flags)
 {
-    constexpr int XW = PX + 2, XH = PY + 2;
+    // fine points x0 - 1 .. x0 + TX interpolate from coarse points
+    // x0 / 2 - 1 .. x0 / 2 + TX / 2 (TX even), likewise in y
+    constexpr int XW = TX + 2, XH = TY + 2, CW = TX / 2 + 2, CH = TY / 2 + 2;
+    static_assert(TX % 2 == 0 && TY % 2 == 0, "tiles start on even fine points");
+    __shared__ double cs[CH][CW];
     __shared__ double xs[XH][XW];
     const int mc = (mf - 1) / 2;
     const int64_t n = (int64_t)mf * mf;
-    const int x0 = blockIdx.x * PX, y0 = blockIdx.y * PY;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int cx0 = x0 / 2 - 1, cy0 = y0 / 2 - 1;
+    for (int t = threadIdx.x; t < CW * CH; t += blockDim.x) {
+        const int ly = t / CW, lx = t - ly * CW;
+        const int I = cx0 + lx, J = cy0 + ly;
+        double v = 0.0;
+        if (I >= 0 && I < mc && J >= 0 && J < mc) {
+            const int64_t i = (int64_t)J * mc + I;
+            v = ec2 ? ec[i] + ec2[i] : ec[i];
+        }
+        cs[ly][lx] = v;
+    }
+    __syncthreads();
     for (int t = threadIdx.x; t < XW * XH; t += blockDim.x) {
         const int ly = t / XW, lx = t - ly * XW;
         const int fx = x0 - 1 + lx, fy = y0 - 1 + ly;
         double v = 0.0;
         if (fx >= 0 && fx < mf && fy >= 0 && fy < mf) {
             const int64_t i = (int64_t)fy * mf + fx;
-            v = sum_or_zero(Xin, Ein, i) + prolong_at(ec, mc, fx, fy);
-            if (lx >= 1 && lx <= PX && ly >= 1 && ly <= PY) Xout[i] = v;
+            v = sum_or_zero(Xin, Ein, i) + prolong_at<CW>(cs, cx0, cy0, fx, fy);
+            if (lx >= 1 && lx <= TX && ly >= 1 && ly <= TY) Xout[i] = v;
         }
         xs[ly][lx] = v;
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < PX * PY; t += blockDim.x) {
-        const int ly = t / PX, lx = t - ly * PX;
+    for (int t = threadIdx.x; t < TX * TY; t += blockDim.x) {
+        const int ly = t / TX, lx = t - ly * TX;
         const int fx = x0 + lx, fy = y0 + ly;
         if (fx >= mf || fy >= mf) continue;
         const int64_t i = (int64_t)fy * mf + fx;
@@ -188,6 +214,39 @@ bool grid_dirs(const StencilParams &sp, int m, Dirs &d)
     return true;
 }
 
+template <int K>
+cudaError_t restrict_k(int mf, const Dirs &d, const double *a64, const double *diag64, const double *b,
+                       const double *X, const double *E, double *T, double scale, double *rc, float *rcf,
+                       double *rcd, unsigned *flags, cudaStream_t s)
+{
+    const int mc = (mf - 1) / 2;
+    const unsigned gx = (unsigned)((mc + RX - 1) / RX), gy = (unsigned)((mc + RY - 1) / RY);
+    if ((int64_t)gx * gy >= kBigTilesMin)
+        k_mg_restrict_residual<K, RX, RY><<<dim3(gx, gy), 256, 0, s>>>(mf, d, a64, diag64, b, X, E, T, scale,
+                                                                       rc, rcf, rcd, flags);
+    else
+        k_mg_restrict_residual<K, RXS, RYS>
+            <<<dim3((unsigned)((mc + RXS - 1) / RXS), (unsigned)((mc + RYS - 1) / RYS)), 256, 0, s>>>(
+                mf, d, a64, diag64, b, X, E, T, scale, rc, rcf, rcd, flags);
+    return cudaGetLastError();
+}
+
+template <int K>
+cudaError_t prolong_k(int mf, const Dirs &d, const double *a64, const double *diag64, const double *b,
+                      const double *Xin, const double *Ein, const double *ec, const double *ec2, double *Xout,
+                      double *r, float *rf, unsigned *flags, cudaStream_t s)
+{
+    const unsigned gx = (unsigned)((mf + PX - 1) / PX), gy = (unsigned)((mf + PY - 1) / PY);
+    if ((int64_t)gx * gy >= kBigTilesMin)
+        k_mg_prolong_residual<K, PX, PY><<<dim3(gx, gy), 256, 0, s>>>(mf, d, a64, diag64, b, Xin, Ein, ec, ec2,
+                                                                      Xout, r, rf, flags);
+    else
+        k_mg_prolong_residual<K, PXS, PYS>
+            <<<dim3((unsigned)((mf + PXS - 1) / PXS), (unsigned)((mf + PYS - 1) / PYS)), 256, 0, s>>>(
+                mf, d, a64, diag64, b, Xin, Ein, ec, ec2, Xout, r, rf, flags);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 bool mg_fusable(const StencilParams &sp, int m)
@@ -203,35 +262,28 @@ cudaError_t launch_mg_restrict_residual(const StencilParams &sp, int mf, const d
 {
     Dirs d;
     if (!grid_dirs(sp, mf, d) || mf % 2 == 0) return cudaErrorInvalidValue;
-    const int mc = (mf - 1) / 2;
-    if (mc < 1) return cudaErrorInvalidValue;
-    const dim3 grid((unsigned)((mc + RX - 1) / RX), (unsigned)((mc + RY - 1) / RY));
-    if (sp.K == 4)
-        k_mg_restrict_residual<4><<<grid, 256, 0, s>>>(mf, d, a64, diag64, b, X, E, T, scale, rc, rcf, rcd, flags);
-    else if (sp.K == 8)
-        k_mg_restrict_residual<8><<<grid, 256, 0, s>>>(mf, d, a64, diag64, b, X, E, T, scale, rc, rcf, rcd, flags);
-    else
-        return cudaErrorInvalidValue;
+    if ((mf - 1) / 2 < 1) return cudaErrorInvalidValue;
+    cudaError_t e;
+    if (sp.K == 4) e = restrict_k<4>(mf, d, a64, diag64, b, X, E, T, scale, rc, rcf, rcd, flags, s);
+    else if (sp.K == 8) e = restrict_k<8>(mf, d, a64, diag64, b, X, E, T, scale, rc, rcf, rcd, flags, s);
+    else return cudaErrorInvalidValue;
     count_launches(s, 1);
-    return cudaGetLastError();
+    return e;
 }
 
 cudaError_t launch_mg_prolong_residual(const StencilParams &sp, int mf, const double *a64,
                                        const double *diag64, const double *b, const double *Xin,
-                                       const double *Ein, const double *ec, double *Xout,
-                                       double *r, float *rf, unsigned *flags, cudaStream_t s)
+                                       const double *Ein, const double *ec, const double *ec2,
+                                       double *Xout, double *r, float *rf, unsigned *flags, cudaStream_t s)
 {
     Dirs d;
     if (!grid_dirs(sp, mf, d) || mf % 2 == 0) return cudaErrorInvalidValue;
-    const dim3 grid((unsigned)((mf + PX - 1) / PX), (unsigned)((mf + PY - 1) / PY));
-    if (sp.K == 4)
-        k_mg_prolong_residual<4><<<grid, 256, 0, s>>>(mf, d, a64, diag64, b, Xin, Ein, ec, Xout, r, rf, flags);
-    else if (sp.K == 8)
-        k_mg_prolong_residual<8><<<grid, 256, 0, s>>>(mf, d, a64, diag64, b, Xin, Ein, ec, Xout, r, rf, flags);
-    else
-        return cudaErrorInvalidValue;
+    cudaError_t e;
+    if (sp.K == 4) e = prolong_k<4>(mf, d, a64, diag64, b, Xin, Ein, ec, ec2, Xout, r, rf, flags, s);
+    else if (sp.K == 8) e = prolong_k<8>(mf, d, a64, diag64, b, Xin, Ein, ec, ec2, Xout, r, rf, flags, s);
+    else return cudaErrorInvalidValue;
     count_launches(s, 1);
-    return cudaGetLastError();
+    return e;
 }
 
 }  // namespace gabp

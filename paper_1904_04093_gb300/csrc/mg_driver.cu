@@ -256,9 +256,12 @@ gabp_status mg_fused_sweeps(mg_ctx *mg, int l, int nu)
     return GABP_OK;
 }
 
+// With post_e (a level below the finest), the level's final x + e is left to
+// the caller's prolongation: *post_e = e (or nullptr when x is already final).
 gabp_status mg_cycle_fused(mg_ctx *mg, int l, int last, int nu_pre, int nu_post, const double *b,
-                           double *x, MgRes top)
+                           double *x, MgRes top, const double **post_e = nullptr)
 {
+    if (post_e) *post_e = nullptr;
     cudaStream_t s = mg->stream;
     gabp_ctx *c = mg->lv[l];
     const size_t nb = (size_t)c->n * sizeof(double);
@@ -289,16 +292,18 @@ gabp_status mg_cycle_fused(mg_ctx *mg, int l, int last, int nu_pre, int nu_post,
     CK(launch_mg_restrict_residual(c->L.sp, mg->side[l], c->a64, c->diag64, b, X, E, T, mg->scale,
                                    mg->b[l + 1], cc->prec == 1 ? (float *)cc->bT : nullptr,
                                    cc->prec == 0 ? cc->bres : nullptr, &c->dstat[0].flags, s));
-    CKS(mg_cycle_fused(mg, l + 1, last, nu_pre, nu_post, mg->b[l + 1], mg->x[l + 1], MG_RES_BT));
-    // x2 = x1 + P e_c into x, and the post-smoothing right-hand side b - A x2
+    const double *ec2 = nullptr;
+    CKS(mg_cycle_fused(mg, l + 1, last, nu_pre, nu_post, mg->b[l + 1], mg->x[l + 1], MG_RES_BT, &ec2));
+    // x2 = x1 + P (x_c + e_c) into x, and the post-smoothing right-hand side b - A x2
     const double *Xin = X ? mg->tbuf : nullptr;
     const double *Ein = X ? nullptr : E;
     CK(launch_mg_prolong_residual(c->L.sp, mg->side[l], c->a64, c->diag64, b, Xin, Ein,
-                                  mg->x[l + 1], x, c->prec == 0 ? c->bres : nullptr,
+                                  mg->x[l + 1], ec2, x, c->prec == 0 ? c->bres : nullptr,
                                   c->prec == 1 ? (float *)c->bT : nullptr, &c->dstat[0].flags, s));
     if (nu_post > 0) {
         CKS(mg_fused_sweeps(mg, l, nu_post));
-        CK(launch_axpy(x, c->xbuf, 1.0, c->n, s));
+        if (post_e) *post_e = c->xbuf;
+        else CK(launch_axpy(x, c->xbuf, 1.0, c->n, s));
     }
     return GABP_OK;
 }
