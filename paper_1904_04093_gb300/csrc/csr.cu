@@ -53,6 +53,8 @@ __global__ void __launch_bounds__(kCsrBlock, csr_min_blocks(sizeof(T) == 8, EPT)
     T *__restrict__ Lout, T *__restrict__ Mout, T *__restrict__ Pout, T *__restrict__ Bout,
     double *__restrict__ x, unsigned *__restrict__ flags, int nslots)
 {
+    pdl_wait();
+    pdl_trigger();
     constexpr int WT = 32 * EPT;
     constexpr int NW = kCsrBlock / 32;
     __shared__ T sL[kFull ? NW * WT : 1];
@@ -171,7 +173,7 @@ cudaError_t launch_T(const DevLayout &L, const void *a, const void *c, const voi
     if (grid == 0) return cudaSuccess;
 #define GABP_CSR_CASE(E)                                                                        \
     case E:                                                                                     \
-        k_sweep_csr<T, E, kFull><<<grid, kCsrBlock, 0, s>>>(                                    \
+        launch_pdl(k_sweep_csr<T, E, kFull>, grid, kCsrBlock, 0, s,                                     \
             L.n, L.rowptr, L.col, L.rev, (const T *)a, (const T *)c, (const T *)diag,           \
             (const T *)b, (const T *)Lin, (const T *)Min, (const T *)Pin, (const T *)Bin,       \
             (T *)Lout, (T *)Mout, (T *)Pout, (T *)Bout, x, flags, (int)L.slots);                \

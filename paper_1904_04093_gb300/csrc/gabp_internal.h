@@ -5,11 +5,63 @@
 #include <stdint.h>
 
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/gabp.h"
 
+// Programmatic dependent launch (sm_90 and later): a kernel launched through
+// launch_pdl may be placed on the SMs while the kernel before it in the
+// stream is still finishing; it waits in pdl_wait() until that kernel has
+// completed and its writes are visible, so every such kernel calls pdl_wait()
+// before its first access to global memory.  What overlaps is the launch and
+// the placement of CTAs on the SMs the previous kernel has left, never a
+// memory access, so the results are those of plain stream order.
+// pdl_trigger() lets the next kernel be launched once every CTA of this one
+// has passed it.  Building with -DGABP_PDL=0 gives plain launches.
+#ifndef GABP_PDL
+#define GABP_PDL 1
+#endif
+
 namespace gabp {
+
+__device__ __forceinline__ void pdl_wait()
+{
+#if GABP_PDL
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+#endif
+}
+
+__device__ __forceinline__ void pdl_trigger()
+{
+#if GABP_PDL
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+#endif
+}
+
+// Launches kernel k (whose body starts with pdl_wait) with programmatic
+// stream serialisation; the arguments are converted to k's parameter types.
+// Errors are returned and also left for cudaGetLastError.
+template <typename... P, typename... A>
+cudaError_t launch_pdl(void (*k)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, A &&...args)
+{
+#if GABP_PDL
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k, std::forward<A>(args)...);
+#else
+    k<<<grid, block, smem, s>>>(std::forward<A>(args)...);
+    return cudaGetLastError();
+#endif
+}
 
 constexpr int KMAX = 16;  // most off-diagonal diagonals the stencil layout takes
 

@@ -59,6 +59,8 @@ __global__ void __launch_bounds__(256) k_sweep_stencil(
     T *__restrict__ Lout, T *__restrict__ Mout, T *__restrict__ Pout, T *__restrict__ Bout,
     double *__restrict__ x, unsigned *__restrict__ flags)
 {
+    pdl_wait();
+    pdl_trigger();
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n) return;
     const unsigned f = sweep_row_stencil<T, K>(r, n, sp.off, sp.krev, a, c, diag, b, Lin, Min, Pin,
@@ -83,6 +85,8 @@ __global__ void __launch_bounds__(256) k_freeze_stencil(int n, StencilParams sp,
                                                         T *__restrict__ g,
                                                         unsigned *__restrict__ flags)
 {
+    pdl_wait();
+    pdl_trigger();
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n) return;
     const size_t nn = (size_t)n;
@@ -109,6 +113,8 @@ __global__ void k_freeze_csr(int n, const int *__restrict__ rowptr, const int *_
                              const T *__restrict__ P, const T *__restrict__ Lm,
                              T *__restrict__ g, unsigned *__restrict__ flags)
 {
+    pdl_wait();
+    pdl_trigger();
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n) return;
     bool bad = false;
@@ -131,6 +137,8 @@ __global__ void __launch_bounds__(256) k_sweep_mean_stencil(
     const T *__restrict__ P, const T *__restrict__ Min, const T *__restrict__ Bin,
     T *__restrict__ Mout, T *__restrict__ Bout, double *__restrict__ x, unsigned *flags)
 {
+    pdl_wait();
+    pdl_trigger();
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n) return;
     const size_t nn = (size_t)n;
@@ -180,6 +188,8 @@ __global__ void __launch_bounds__(256) k_sweep_color_stencil_gather(
     const T *__restrict__ a, const T *__restrict__ c, T *Lm, T *Mm, T *P, T *B,
     double *__restrict__ x, unsigned *__restrict__ flags)
 {
+    pdl_wait();
+    pdl_trigger();
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n) return;
     const size_t nn = (size_t)n;
@@ -223,6 +233,8 @@ __global__ void __launch_bounds__(256) k_sweep_color_stencil(
     const T *__restrict__ a, const T *__restrict__ c, T *Lm, T *Mm, T *P, T *B,
     double *__restrict__ x, unsigned *__restrict__ flags)
 {
+    pdl_wait();
+    pdl_trigger();
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n) return;
     const size_t nn = (size_t)n;
@@ -265,6 +277,8 @@ __global__ void __launch_bounds__(256) k_sweep_color_csr(
     const T *__restrict__ c, T *Lm, T *Mm, T *P, T *B, double *__restrict__ x,
     unsigned *__restrict__ flags)
 {
+    pdl_wait();
+    pdl_trigger();
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n) return;
     if (color[r] == cphase) {
@@ -303,6 +317,8 @@ __global__ void k_aggregate_stencil(int n, int K, const T *__restrict__ diag,
                                     const T *__restrict__ Mm, T *__restrict__ P,
                                     T *__restrict__ B)
 {
+    pdl_wait();
+    pdl_trigger();
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n) return;
     T p = diag[r], q = b[r];
@@ -319,6 +335,8 @@ __global__ void k_aggregate_csr(int n, const int *__restrict__ rowptr, const T *
                                 const T *__restrict__ b, const T *__restrict__ Lm,
                                 const T *__restrict__ Mm, T *__restrict__ P, T *__restrict__ B)
 {
+    pdl_wait();
+    pdl_trigger();
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n) return;
     T p = diag[r], q = b[r];
@@ -421,6 +439,8 @@ __global__ void __launch_bounds__(256) k_residual_stencil(
     const double *__restrict__ b, const double *__restrict__ x, double *__restrict__ r,
     float *__restrict__ rf, DevStatus *st)
 {
+    pdl_wait();
+    pdl_trigger();
     constexpr int KK = K > 0 ? K : 1;
     unsigned long long rbits = 0ull, bbits = 0ull;
     bool nan = false;
@@ -467,6 +487,8 @@ __global__ void __launch_bounds__(256) k_residual_csr(
     const double *__restrict__ b, const double *__restrict__ x, double *__restrict__ r,
     DevStatus *st)
 {
+    pdl_wait();
+    pdl_trigger();
     double rmax = 0.0, bmax = 0.0;
     bool nan = false;
     const int nslots = kIndexChecks ? rowptr[n] : 0;
@@ -500,6 +522,8 @@ template <typename T>
 __global__ void __launch_bounds__(256) k_lambda_change(int64_t slots, const T *__restrict__ L0,
                                                        const T *__restrict__ L1, DevStatus *st)
 {
+    pdl_wait();
+    pdl_trigger();
     double dmax = 0.0, lmax = 0.0;
     bool nan = false;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < slots;
@@ -518,6 +542,8 @@ __global__ void __launch_bounds__(256) k_lambda_change(int64_t slots, const T *_
 // ---------------------------------------------------------------------------
 __global__ void k_d2f(const double *__restrict__ in, float *__restrict__ out, int64_t n)
 {
+    pdl_wait();
+    pdl_trigger();
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
         out[i] = (float)in[i];
@@ -525,6 +551,8 @@ __global__ void k_d2f(const double *__restrict__ in, float *__restrict__ out, in
 
 __global__ void k_f2d(const float *__restrict__ in, double *__restrict__ out, int64_t n)
 {
+    pdl_wait();
+    pdl_trigger();
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
         out[i] = (double)in[i];
@@ -532,6 +560,8 @@ __global__ void k_f2d(const float *__restrict__ in, double *__restrict__ out, in
 
 __global__ void k_copy(const double *__restrict__ in, double *__restrict__ out, int64_t n)
 {
+    pdl_wait();
+    pdl_trigger();
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
         out[i] = in[i];
@@ -541,6 +571,8 @@ template <typename T>
 __global__ void k_scale_rhs(const double *__restrict__ in, const DevStatus *st,
                             double *__restrict__ out, T *__restrict__ outT, int64_t n)
 {
+    pdl_wait();
+    pdl_trigger();
     const double s = __longlong_as_double((long long)st->rmax);
     const double inv = s > 0.0 ? 1.0 / s : 0.0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -554,6 +586,8 @@ __global__ void k_scale_rhs(const double *__restrict__ in, const DevStatus *st,
 __global__ void k_axpy_status(double *__restrict__ x, const double *__restrict__ e,
                               const DevStatus *st, int64_t n)
 {
+    pdl_wait();
+    pdl_trigger();
     const double s = __longlong_as_double((long long)st->rmax);
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
@@ -563,6 +597,8 @@ __global__ void k_axpy_status(double *__restrict__ x, const double *__restrict__
 __global__ void k_axpy(double *__restrict__ x, const double *__restrict__ e, double alpha,
                        int64_t n)
 {
+    pdl_wait();
+    pdl_trigger();
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
         x[i] += alpha * e[i];
@@ -573,6 +609,8 @@ __global__ void k_get_state(const int64_t *__restrict__ slotmap, int64_t nnz,
                             const T *__restrict__ Lm, const T *__restrict__ Mm,
                             double *__restrict__ lam, double *__restrict__ m)
 {
+    pdl_wait();
+    pdl_trigger();
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nnz;
          p += (int64_t)gridDim.x * blockDim.x) {
         const int64_t q = slotmap[p];
@@ -586,6 +624,8 @@ __global__ void k_set_state(const int64_t *__restrict__ slotmap, int64_t nnz,
                             const double *__restrict__ lam, const double *__restrict__ m,
                             T *__restrict__ Lm, T *__restrict__ Mm)
 {
+    pdl_wait();
+    pdl_trigger();
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nnz;
          p += (int64_t)gridDim.x * blockDim.x) {
         const int64_t q = slotmap[p];
@@ -599,6 +639,8 @@ __global__ void k_edge_grad(int n, const int64_t *__restrict__ indptr,
                             const int *__restrict__ indices, const double *__restrict__ lam,
                             const double *__restrict__ x, double *__restrict__ dA)
 {
+    pdl_wait();
+    pdl_trigger();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const double li = lam[i];
@@ -609,6 +651,8 @@ __global__ void k_edge_grad(int n, const int64_t *__restrict__ indptr,
 __global__ void k_restrict_fw(const double *__restrict__ rf, int mf, double scale,
                               double *__restrict__ rc)
 {
+    pdl_wait();
+    pdl_trigger();
     const int mc = (mf - 1) / 2;
     const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (idx >= (int64_t)mc * mc) return;
@@ -628,6 +672,8 @@ __device__ __forceinline__ double coarse_at(const double *__restrict__ ec, int m
 // Bilinear interpolation (Trottenberg eq. 2.3.7) added onto the fine grid.
 __global__ void k_prolong_add(const double *__restrict__ ec, int mc, double *__restrict__ xf)
 {
+    pdl_wait();
+    pdl_trigger();
     const int mf = 2 * mc + 1;
     const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (idx >= (int64_t)mf * mf) return;
@@ -657,6 +703,8 @@ __global__ void k_prolong_add(const double *__restrict__ ec, int mc, double *__r
 __global__ void k_dense_gemv(const double *__restrict__ M, const double *__restrict__ x,
                              double *__restrict__ y, int n)
 {
+    pdl_wait();
+    pdl_trigger();
     const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (row >= n) return;
@@ -680,6 +728,8 @@ template <typename T>
 __global__ void k_transpose_stencil(int n, StencilParams sp, const T *__restrict__ a,
                                     T *__restrict__ aT)
 {
+    pdl_wait();
+    pdl_trigger();
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n) return;
     for (int k = 0; k < sp.K; ++k) {
@@ -694,6 +744,8 @@ template <typename T>
 __global__ void k_transpose_csr(int64_t slots, const int *__restrict__ rev, const T *__restrict__ a,
                                 T *__restrict__ aT)
 {
+    pdl_wait();
+    pdl_trigger();
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < slots;
          e += (int64_t)gridDim.x * blockDim.x)
         aT[e] = a[rev[e]];
@@ -708,6 +760,8 @@ __global__ void k_values_scatter(int64_t nnz, int n, const int64_t *__restrict__
                                  const double *__restrict__ data, double *__restrict__ a64,
                                  double *__restrict__ diag64)
 {
+    pdl_wait();
+    pdl_trigger();
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nnz; p += stride) {
         const int64_t e = slotmap[p];
@@ -724,6 +778,8 @@ __global__ void k_coeffs_c(const DevLayout L, const double *__restrict__ a64,
                            const double *__restrict__ diag64, T *__restrict__ a, T *__restrict__ c,
                            T *__restrict__ diagT)
 {
+    pdl_wait();
+    pdl_trigger();
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < L.slots; e += stride) {
         double ar = 0.0;
@@ -762,7 +818,7 @@ cudaError_t sweep_stencil_T(const DevLayout &L, const SweepArgs &a, int block, c
     T *Lo = (T *)a.Lout, *Mo = (T *)a.Mout, *Po = (T *)a.Pout, *Bo = (T *)a.Bout;
 #define GABP_SWEEP_CASE(KK)                                                                 \
     case KK:                                                                                \
-        k_sweep_stencil<T, KK><<<grid, block, 0, s>>>(L.n, L.sp, A, C, D, Bv, Li, Mi, Pi,  \
+        launch_pdl(k_sweep_stencil<T, KK>, grid, block, 0, s, L.n, L.sp, A, C, D, Bv, Li, Mi, Pi,  \
                                                        Bi, Lo, Mo, Po, Bo, a.x, a.flags); \
         break;
     switch (L.sp.K) {
@@ -802,20 +858,20 @@ cudaError_t launch_aggregate(const DevLayout &L, int prec, const void *diag, con
     const int block = 256, grid = (L.n + block - 1) / block;
     if (L.kind == GABP_LAYOUT_STENCIL) {
         if (prec == 0)
-            k_aggregate_stencil<double><<<grid, block, 0, s>>>(
+            launch_pdl(k_aggregate_stencil<double>, grid, block, 0, s,
                 L.n, L.sp.K, (const double *)diag, (const double *)b, (const double *)Lm,
                 (const double *)Mm, (double *)P, (double *)B);
         else
-            k_aggregate_stencil<float><<<grid, block, 0, s>>>(
+            launch_pdl(k_aggregate_stencil<float>, grid, block, 0, s,
                 L.n, L.sp.K, (const float *)diag, (const float *)b, (const float *)Lm,
                 (const float *)Mm, (float *)P, (float *)B);
     } else {
         if (prec == 0)
-            k_aggregate_csr<double><<<grid, block, 0, s>>>(
+            launch_pdl(k_aggregate_csr<double>, grid, block, 0, s,
                 L.n, L.rowptr, (const double *)diag, (const double *)b, (const double *)Lm,
                 (const double *)Mm, (double *)P, (double *)B);
         else
-            k_aggregate_csr<float><<<grid, block, 0, s>>>(
+            launch_pdl(k_aggregate_csr<float>, grid, block, 0, s,
                 L.n, L.rowptr, (const float *)diag, (const float *)b, (const float *)Lm,
                 (const float *)Mm, (float *)P, (float *)B);
     }
@@ -840,7 +896,7 @@ cudaError_t launch_residual2(const DevLayout &L, const double *a64, const double
     if (L.kind == GABP_LAYOUT_STENCIL) {
 #define GABP_RES_CASE(KK)                                                                   \
     case KK:                                                                                \
-        k_residual_stencil<KK><<<grid, block, 0, s>>>(L.n, L.sp, a64, diag64, b, x, r, rf, st); \
+        launch_pdl(k_residual_stencil<KK>, grid, block, 0, s, L.n, L.sp, a64, diag64, b, x, r, rf, st); \
         break;
         switch (L.sp.K) {
             GABP_RES_CASE(0)
@@ -857,7 +913,7 @@ cudaError_t launch_residual2(const DevLayout &L, const double *a64, const double
         }
 #undef GABP_RES_CASE
     } else {
-        k_residual_csr<<<grid, block, 0, s>>>(L.n, L.rowptr, L.col, a64, diag64, b, x, r, st);
+        launch_pdl(k_residual_csr, grid, block, 0, s, L.n, L.rowptr, L.col, a64, diag64, b, x, r, st);
     }
     count_launches(s, 1);
     return cudaGetLastError();
@@ -870,6 +926,8 @@ __global__ void __launch_bounds__(256) k_sumsq2(const double *__restrict__ u,
                                                 const double *__restrict__ v, int64_t n,
                                                 double *__restrict__ part)
 {
+    pdl_wait();
+    pdl_trigger();
     __shared__ double su[256], sv[256];
     double a = 0.0, c = 0.0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -896,7 +954,7 @@ __global__ void __launch_bounds__(256) k_sumsq2(const double *__restrict__ u,
 cudaError_t launch_sumsq2(const double *u, const double *v, int64_t n, double *part, int nblocks,
                           cudaStream_t s)
 {
-    k_sumsq2<<<nblocks, 256, 0, s>>>(u, v, n, part);
+    launch_pdl(k_sumsq2, nblocks, 256, 0, s, u, v, n, part);
     count_launches(s, 1);
     return cudaGetLastError();
 }
@@ -904,7 +962,7 @@ cudaError_t launch_sumsq2(const double *u, const double *v, int64_t n, double *p
 cudaError_t launch_convert_d2f(const double *in, float *out, int64_t n, cudaStream_t s)
 {
     if (n == 0) return cudaSuccess;
-    k_d2f<<<grid_for(n, 256), 256, 0, s>>>(in, out, n);
+    launch_pdl(k_d2f, grid_for(n, 256), 256, 0, s, in, out, n);
     count_launches(s, 1);
     return cudaGetLastError();
 }
@@ -913,9 +971,9 @@ cudaError_t launch_to_double(int prec, const void *in, double *out, int64_t n, c
 {
     if (n == 0) return cudaSuccess;
     if (prec == 0) {
-        k_copy<<<grid_for(n, 256), 256, 0, s>>>((const double *)in, out, n);
+        launch_pdl(k_copy, grid_for(n, 256), 256, 0, s, (const double *)in, out, n);
     } else {
-        k_f2d<<<grid_for(n, 256), 256, 0, s>>>((const float *)in, out, n);
+        launch_pdl(k_f2d, grid_for(n, 256), 256, 0, s, (const float *)in, out, n);
     }
     count_launches(s, 1);
     return cudaGetLastError();
@@ -924,7 +982,7 @@ cudaError_t launch_to_double(int prec, const void *in, double *out, int64_t n, c
 cudaError_t launch_copy_vec(const double *in, double *out, int64_t n, cudaStream_t s)
 {
     if (n == 0) return cudaSuccess;
-    k_copy<<<grid_for(n, 256), 256, 0, s>>>(in, out, n);
+    launch_pdl(k_copy, grid_for(n, 256), 256, 0, s, in, out, n);
     count_launches(s, 1);
     return cudaGetLastError();
 }
@@ -934,9 +992,9 @@ cudaError_t launch_scale_rhs(const double *in, const DevStatus *st, double *out,
 {
     if (n == 0) return cudaSuccess;
     if (prec == 0 || outT == nullptr)
-        k_scale_rhs<double><<<grid_for(n, 256), 256, 0, s>>>(in, st, out, nullptr, n);
+        launch_pdl(k_scale_rhs<double>, grid_for(n, 256), 256, 0, s, in, st, out, nullptr, n);
     else
-        k_scale_rhs<float><<<grid_for(n, 256), 256, 0, s>>>(in, st, out, (float *)outT, n);
+        launch_pdl(k_scale_rhs<float>, grid_for(n, 256), 256, 0, s, in, st, out, (float *)outT, n);
     count_launches(s, 1);
     return cudaGetLastError();
 }
@@ -945,7 +1003,7 @@ cudaError_t launch_axpy_status(double *x, const double *e, const DevStatus *st, 
                                cudaStream_t s)
 {
     if (n == 0) return cudaSuccess;
-    k_axpy_status<<<grid_for(n, 256), 256, 0, s>>>(x, e, st, n);
+    launch_pdl(k_axpy_status, grid_for(n, 256), 256, 0, s, x, e, st, n);
     count_launches(s, 1);
     return cudaGetLastError();
 }
@@ -953,7 +1011,7 @@ cudaError_t launch_axpy_status(double *x, const double *e, const DevStatus *st, 
 cudaError_t launch_axpy(double *x, const double *e, double alpha, int64_t n, cudaStream_t s)
 {
     if (n == 0) return cudaSuccess;
-    k_axpy<<<grid_for(n, 256), 256, 0, s>>>(x, e, alpha, n);
+    launch_pdl(k_axpy, grid_for(n, 256), 256, 0, s, x, e, alpha, n);
     count_launches(s, 1);
     return cudaGetLastError();
 }
@@ -963,10 +1021,10 @@ cudaError_t launch_get_state(const int64_t *slotmap, int64_t nnz, int prec, cons
 {
     if (nnz == 0) return cudaSuccess;
     if (prec == 0)
-        k_get_state<double><<<grid_for(nnz, 256), 256, 0, s>>>(
+        launch_pdl(k_get_state<double>, grid_for(nnz, 256), 256, 0, s,
             slotmap, nnz, (const double *)Lm, (const double *)Mm, lam, m);
     else
-        k_get_state<float><<<grid_for(nnz, 256), 256, 0, s>>>(
+        launch_pdl(k_get_state<float>, grid_for(nnz, 256), 256, 0, s,
             slotmap, nnz, (const float *)Lm, (const float *)Mm, lam, m);
     count_launches(s, 1);
     return cudaGetLastError();
@@ -977,10 +1035,10 @@ cudaError_t launch_set_state(const int64_t *slotmap, int64_t nnz, int prec, cons
 {
     if (nnz == 0) return cudaSuccess;
     if (prec == 0)
-        k_set_state<double><<<grid_for(nnz, 256), 256, 0, s>>>(slotmap, nnz, lam, m,
+        launch_pdl(k_set_state<double>, grid_for(nnz, 256), 256, 0, s, slotmap, nnz, lam, m,
                                                                (double *)Lm, (double *)Mm);
     else
-        k_set_state<float><<<grid_for(nnz, 256), 256, 0, s>>>(slotmap, nnz, lam, m,
+        launch_pdl(k_set_state<float>, grid_for(nnz, 256), 256, 0, s, slotmap, nnz, lam, m,
                                                               (float *)Lm, (float *)Mm);
     count_launches(s, 1);
     return cudaGetLastError();
@@ -990,7 +1048,7 @@ cudaError_t launch_edge_grad(int n, const int64_t *indptr, const int *indices, c
                              const double *x, double *dA, cudaStream_t s)
 {
     if (n == 0) return cudaSuccess;
-    k_edge_grad<<<(n + 255) / 256, 256, 0, s>>>(n, indptr, indices, lam, x, dA);
+    launch_pdl(k_edge_grad, (n + 255) / 256, 256, 0, s, n, indptr, indices, lam, x, dA);
     count_launches(s, 1);
     return cudaGetLastError();
 }
@@ -1000,7 +1058,7 @@ cudaError_t launch_restrict_fw(const double *rf, int mf, double scale, double *r
     const int mc = (mf - 1) / 2;
     const int64_t nc = (int64_t)mc * mc;
     if (nc == 0) return cudaSuccess;
-    k_restrict_fw<<<(int)((nc + 255) / 256), 256, 0, s>>>(rf, mf, scale, rc);
+    launch_pdl(k_restrict_fw, (int)((nc + 255) / 256), 256, 0, s, rf, mf, scale, rc);
     count_launches(s, 1);
     return cudaGetLastError();
 }
@@ -1008,7 +1066,7 @@ cudaError_t launch_restrict_fw(const double *rf, int mf, double scale, double *r
 cudaError_t launch_prolong_add(const double *ec, int mc, double *xf, cudaStream_t s)
 {
     const int64_t nf = (int64_t)(2 * mc + 1) * (2 * mc + 1);
-    k_prolong_add<<<(int)((nf + 255) / 256), 256, 0, s>>>(ec, mc, xf);
+    launch_pdl(k_prolong_add, (int)((nf + 255) / 256), 256, 0, s, ec, mc, xf);
     count_launches(s, 1);
     return cudaGetLastError();
 }
@@ -1017,7 +1075,7 @@ cudaError_t launch_dense_gemv(const double *M, const double *x, double *y, int n
 {
     if (n == 0) return cudaSuccess;
     const int rows_per_block = 4;
-    k_dense_gemv<<<(n + rows_per_block - 1) / rows_per_block, 32 * rows_per_block, 0, s>>>(M, x,
+    launch_pdl(k_dense_gemv, (n + rows_per_block - 1) / rows_per_block, 32 * rows_per_block, 0, s, M, x,
                                                                                           y, n);
     count_launches(s, 1);
     return cudaGetLastError();
@@ -1027,6 +1085,8 @@ cudaError_t launch_dense_gemv(const double *M, const double *x, double *y, int n
 __global__ void k_permute(int n, const int *__restrict__ idx, const double *__restrict__ in,
                           double *__restrict__ out, int scatter)
 {
+    pdl_wait();
+    pdl_trigger();
     const int stride = gridDim.x * blockDim.x;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         if (scatter) out[idx[i]] = in[i];
@@ -1038,7 +1098,7 @@ cudaError_t launch_permute(int n, const int *idx, const double *in, double *out,
                            cudaStream_t s)
 {
     if (n == 0) return cudaSuccess;
-    k_permute<<<grid_for(n, 256), 256, 0, s>>>(n, idx, in, out, scatter);
+    launch_pdl(k_permute, grid_for(n, 256), 256, 0, s, n, idx, in, out, scatter);
     count_launches(s, 1);
     return cudaGetLastError();
 }
@@ -1049,13 +1109,13 @@ cudaError_t launch_coeffs_from_values(const DevLayout &L, int prec, int64_t nnz,
                                       void *c, void *diagT, cudaStream_t s)
 {
     if (L.n == 0) return cudaSuccess;
-    k_values_scatter<<<grid_for(std::max<int64_t>(nnz, L.n), 256), 256, 0, s>>>(nnz, L.n, slotmap, diagpos,
+    launch_pdl(k_values_scatter, grid_for(std::max<int64_t>(nnz, L.n), 256), 256, 0, s, nnz, L.n, slotmap, diagpos,
                                                                               data, a64, diag64);
     const int grid = grid_for(std::max<int64_t>(L.slots, L.n), 256);
     if (prec == 0)
-        k_coeffs_c<double><<<grid, 256, 0, s>>>(L, a64, diag64, (double *)a, (double *)c, (double *)diagT);
+        launch_pdl(k_coeffs_c<double>, grid, 256, 0, s, L, a64, diag64, (double *)a, (double *)c, (double *)diagT);
     else
-        k_coeffs_c<float><<<grid, 256, 0, s>>>(L, a64, diag64, (float *)a, (float *)c, (float *)diagT);
+        launch_pdl(k_coeffs_c<float>, grid, 256, 0, s, L, a64, diag64, (float *)a, (float *)c, (float *)diagT);
     count_launches(s, 2);
     return cudaGetLastError();
 }
@@ -1067,18 +1127,18 @@ cudaError_t launch_transpose_coeffs(const DevLayout &L, int prec, const void *a,
     if (L.kind == GABP_LAYOUT_STENCIL) {
         const int grid = (L.n + 255) / 256;
         if (prec == 0)
-            k_transpose_stencil<double><<<grid, 256, 0, s>>>(L.n, L.sp, (const double *)a,
+            launch_pdl(k_transpose_stencil<double>, grid, 256, 0, s, L.n, L.sp, (const double *)a,
                                                               (double *)aT);
         else
-            k_transpose_stencil<float><<<grid, 256, 0, s>>>(L.n, L.sp, (const float *)a,
+            launch_pdl(k_transpose_stencil<float>, grid, 256, 0, s, L.n, L.sp, (const float *)a,
                                                              (float *)aT);
     } else {
         if (L.slots == 0) return cudaSuccess;
         if (prec == 0)
-            k_transpose_csr<double><<<grid_for(L.slots, 256), 256, 0, s>>>(
+            launch_pdl(k_transpose_csr<double>, grid_for(L.slots, 256), 256, 0, s,
                 L.slots, L.rev, (const double *)a, (double *)aT);
         else
-            k_transpose_csr<float><<<grid_for(L.slots, 256), 256, 0, s>>>(
+            launch_pdl(k_transpose_csr<float>, grid_for(L.slots, 256), 256, 0, s,
                 L.slots, L.rev, (const float *)a, (float *)aT);
     }
     count_launches(s, 1);
@@ -1095,12 +1155,12 @@ cudaError_t launch_freeze(const DevLayout &L, int prec, const void *a, const voi
 #define GABP_FRZ_CASE(KK)                                                                     \
     case KK:                                                                                  \
         if (prec == 0)                                                                        \
-            k_freeze_stencil<double, KK><<<grid, 256, 0, s>>>(L.n, L.sp, (const double *)a,    \
+            launch_pdl(k_freeze_stencil<double, KK>, grid, 256, 0, s, L.n, L.sp, (const double *)a,    \
                                                               (const double *)P,              \
                                                               (const double *)Lm, (double *)g, \
                                                               flags);                         \
         else                                                                                  \
-            k_freeze_stencil<float, KK><<<grid, 256, 0, s>>>(L.n, L.sp, (const float *)a,      \
+            launch_pdl(k_freeze_stencil<float, KK>, grid, 256, 0, s, L.n, L.sp, (const float *)a,      \
                                                              (const float *)P,                \
                                                              (const float *)Lm, (float *)g,   \
                                                              flags);                          \
@@ -1121,11 +1181,11 @@ cudaError_t launch_freeze(const DevLayout &L, int prec, const void *a, const voi
 #undef GABP_FRZ_CASE
     } else {
         if (prec == 0)
-            k_freeze_csr<double><<<grid, 256, 0, s>>>(L.n, L.rowptr, L.col, L.rev, (const double *)a,
+            launch_pdl(k_freeze_csr<double>, grid, 256, 0, s, L.n, L.rowptr, L.col, L.rev, (const double *)a,
                                                       (const double *)P, (const double *)Lm,
                                                       (double *)g, flags);
         else
-            k_freeze_csr<float><<<grid, 256, 0, s>>>(L.n, L.rowptr, L.col, L.rev, (const float *)a,
+            launch_pdl(k_freeze_csr<float>, grid, 256, 0, s, L.n, L.rowptr, L.col, L.rev, (const float *)a,
                                                      (const float *)P, (const float *)Lm,
                                                      (float *)g, flags);
     }
@@ -1144,11 +1204,11 @@ cudaError_t launch_sweep_mean(const DevLayout &L, int prec, const void *g, const
 #define GABP_MEAN_CASE(KK)                                                                     \
     case KK:                                                                                   \
         if (prec == 0)                                                                         \
-            k_sweep_mean_stencil<double, KK><<<grid, block, 0, s>>>(                           \
+            launch_pdl(k_sweep_mean_stencil<double, KK>, grid, block, 0, s,                            \
                 L.n, L.sp, (const double *)g, (const double *)b, (const double *)P,             \
                 (const double *)Min, (const double *)Bin, (double *)Mout, (double *)Bout, x, flags); \
         else                                                                                   \
-            k_sweep_mean_stencil<float, KK><<<grid, block, 0, s>>>(                            \
+            launch_pdl(k_sweep_mean_stencil<float, KK>, grid, block, 0, s,                             \
                 L.n, L.sp, (const float *)g, (const float *)b, (const float *)P,                \
                 (const float *)Min, (const float *)Bin, (float *)Mout, (float *)Bout, x, flags);  \
         break;
@@ -1179,9 +1239,9 @@ cudaError_t launch_lambda_change(int64_t slots, int prec, const void *L0, const 
     count_launches(s, 1);
     const int grid = grid_for(slots, 256, 152 * 8);
     if (prec == 0)
-        k_lambda_change<double><<<grid, 256, 0, s>>>(slots, (const double *)L0, (const double *)L1, st);
+        launch_pdl(k_lambda_change<double>, grid, 256, 0, s, slots, (const double *)L0, (const double *)L1, st);
     else
-        k_lambda_change<float><<<grid, 256, 0, s>>>(slots, (const float *)L0, (const float *)L1, st);
+        launch_pdl(k_lambda_change<float>, grid, 256, 0, s, slots, (const float *)L0, (const float *)L1, st);
     return cudaGetLastError();
 }
 
@@ -1198,20 +1258,20 @@ cudaError_t launch_sweep_color(const DevLayout &L, int prec, const unsigned char
     case KK:                                                                                     \
         if (cm) {                                                                                \
             if (prec == 0)                                                                       \
-                k_sweep_color_stencil<double, KK><<<grid, 256, 0, s>>>(                          \
+                launch_pdl(k_sweep_color_stencil<double, KK>, grid, 256, 0, s,                           \
                     L.n, L.sp, *cm, color, cphase, (const double *)a, (const double *)c,         \
                     (double *)Lm, (double *)Mm, (double *)P, (double *)B, x, flags);             \
             else                                                                                 \
-                k_sweep_color_stencil<float, KK><<<grid, 256, 0, s>>>(                           \
+                launch_pdl(k_sweep_color_stencil<float, KK>, grid, 256, 0, s,                            \
                     L.n, L.sp, *cm, color, cphase, (const float *)a, (const float *)c,           \
                     (float *)Lm, (float *)Mm, (float *)P, (float *)B, x, flags);                 \
         } else {                                                                                 \
             if (prec == 0)                                                                       \
-                k_sweep_color_stencil_gather<double, KK><<<grid, 256, 0, s>>>(                   \
+                launch_pdl(k_sweep_color_stencil_gather<double, KK>, grid, 256, 0, s,                    \
                     L.n, L.sp, color, cphase, (const double *)a, (const double *)c,              \
                     (double *)Lm, (double *)Mm, (double *)P, (double *)B, x, flags);             \
             else                                                                                 \
-                k_sweep_color_stencil_gather<float, KK><<<grid, 256, 0, s>>>(                    \
+                launch_pdl(k_sweep_color_stencil_gather<float, KK>, grid, 256, 0, s,                     \
                     L.n, L.sp, color, cphase, (const float *)a, (const float *)c, (float *)Lm,   \
                     (float *)Mm, (float *)P, (float *)B, x, flags);                              \
         }                                                                                        \
@@ -1232,11 +1292,11 @@ cudaError_t launch_sweep_color(const DevLayout &L, int prec, const unsigned char
 #undef GABP_COL_CASE
     } else {
         if (prec == 0)
-            k_sweep_color_csr<double><<<grid, 256, 0, s>>>(
+            launch_pdl(k_sweep_color_csr<double>, grid, 256, 0, s,
                 L.n, L.rowptr, L.col, L.rev, color, cphase, (const double *)a, (const double *)c,
                 (double *)Lm, (double *)Mm, (double *)P, (double *)B, x, flags);
         else
-            k_sweep_color_csr<float><<<grid, 256, 0, s>>>(
+            launch_pdl(k_sweep_color_csr<float>, grid, 256, 0, s,
                 L.n, L.rowptr, L.col, L.rev, color, cphase, (const float *)a, (const float *)c,
                 (float *)Lm, (float *)Mm, (float *)P, (float *)B, x, flags);
     }

@@ -231,6 +231,8 @@ __global__ void __launch_bounds__(kLineMaxThreads) k_line_scan(
     double *__restrict__ x, int x_transposed, unsigned *__restrict__ flags,
     T *__restrict__ aF, T *__restrict__ aB, T *__restrict__ sinv)
 {
+    pdl_wait();
+    pdl_trigger();
     extern __shared__ __align__(16) unsigned char line_smem[];
     __shared__ Xf<T> wF[kLineMaxWarps], wB[kLineMaxWarps];
     __shared__ T stF[kLineMaxWarps][3], stB[kLineMaxWarps][3];
@@ -478,6 +480,8 @@ __global__ void __launch_bounds__(kLineMaxThreads) k_line_mean(
     const T *__restrict__ b, const T *__restrict__ Moth, T *__restrict__ Mown,
     T *__restrict__ yws, double *__restrict__ x, int x_transposed)
 {
+    pdl_wait();
+    pdl_trigger();
     extern __shared__ __align__(16) unsigned char line_smem[];
     __shared__ T wF[kLineMaxWarps][2], wB[kLineMaxWarps][2], yinF[kLineMaxWarps],
         yinB[kLineMaxWarps];
@@ -627,6 +631,8 @@ __global__ void __launch_bounds__(kLineMaxThreads) k_line_mean_reg(
     const T *__restrict__ b, const T *__restrict__ Moth, T *__restrict__ Mown,
     double *__restrict__ x, int x_transposed, int vec)
 {
+    pdl_wait();
+    pdl_trigger();
     __shared__ T wF[kLineMaxWarps][2], wB[kLineMaxWarps][2], yinF[kLineMaxWarps],
         yinB[kLineMaxWarps];
     const int line = blockIdx.x, tid = threadIdx.x, NT = blockDim.x;
@@ -750,6 +756,8 @@ __global__ void __launch_bounds__(1024, 1) k_line_mean_cols(
     const T *__restrict__ b, const T *__restrict__ Moth, T *__restrict__ Mown,
     double *__restrict__ x)
 {
+    pdl_wait();
+    pdl_trigger();
     constexpr int QW = 32 / kColLines;  // chunks of each line per warp
     __shared__ T wF[32][kColLines][2], wB[32][kColLines][2], yinF[32][kColLines],
         yinB[32][kColLines];
@@ -855,6 +863,8 @@ constexpr int kTile = 64;
 template <typename T>
 __global__ void __launch_bounds__(256) k_transpose(int m, const T *__restrict__ in, T *__restrict__ out)
 {
+    pdl_wait();
+    pdl_trigger();
     __shared__ T tile[kTile][kTile + 1];
     const int bx = blockIdx.x * kTile, by = blockIdx.y * kTile;
 #pragma unroll
@@ -882,6 +892,8 @@ __global__ void k_line_couplings_transpose(int m, int64_t total, const T *__rest
                                            const T *__restrict__ sup, T *__restrict__ subT,
                                            T *__restrict__ supT)
 {
+    pdl_wait();
+    pdl_trigger();
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < total; p += stride) {
         const int i = (int)(p % m);
@@ -903,6 +915,8 @@ __global__ void k_line_couplings_from_stencil(int n, int m, StencilParams sp,
                                               T *__restrict__ subV, T *__restrict__ supV,
                                               T *__restrict__ diagV)
 {
+    pdl_wait();
+    pdl_trigger();
     int kw = -1, ke = -1, ks = -1, kn = -1;
     for (int k = 0; k < sp.K; ++k) {
         if (sp.off[k] == -1) kw = k;
@@ -960,13 +974,13 @@ cudaError_t launch_T(int m, const void *sub, const void *sup, const void *diag, 
     const int nt = line_threads(prec, m);
     const size_t smem = line_smem_bytes(prec, m);
     if (smem <= kLineSmemMax) {
-        k_line_scan<T, true, kFreeze><<<m, nt, smem, s>>>(
+        launch_pdl(k_line_scan<T, true, kFreeze>, m, nt, smem, s,
             m, (const T *)sub, (const T *)sup, (const T *)diag, (const T *)b, (const T *)Loth,
             (const T *)Moth, (T *)Lown, (T *)Mown, nullptr, nullptr, x, x_transposed, flags,
             (T *)aF, (T *)aB, (T *)sinv);
     } else {
         if (!f || !y) return cudaErrorInvalidValue;
-        k_line_scan<T, false, kFreeze><<<m, nt, 0, s>>>(
+        launch_pdl(k_line_scan<T, false, kFreeze>, m, nt, 0, s,
             m, (const T *)sub, (const T *)sup, (const T *)diag, (const T *)b, (const T *)Loth,
             (const T *)Moth, (T *)Lown, (T *)Mown, (T *)f, (T *)y, x, x_transposed, flags,
             (T *)aF, (T *)aB, (T *)sinv);
@@ -987,7 +1001,7 @@ cudaError_t launch_mean_T(int m, const void *aF, const void *aB, const void *sin
         const int vec = m % (16 / (int)sizeof(T)) == 0;
 #define GABP_MEAN_REG(CC)                                                                       \
     case CC:                                                                                    \
-        k_line_mean_reg<T, CC><<<m, nt, 0, s>>>(m, (const T *)aF, (const T *)aB,                \
+        launch_pdl(k_line_mean_reg<T, CC>, m, nt, 0, s, m, (const T *)aF, (const T *)aB,                \
                                                 (const T *)sinv, (const T *)b, (const T *)Moth, \
                                                 (T *)Mown, x, x_transposed, vec);               \
         break;
@@ -1007,12 +1021,12 @@ cudaError_t launch_mean_T(int m, const void *aF, const void *aB, const void *sin
     const int nt = line_threads(1, m);  // little arithmetic per element: the wider split
     const size_t smem = line_mean_smem_bytes(prec, m);
     if (smem <= kLineSmemMax) {
-        k_line_mean<T, true><<<m, nt, smem, s>>>(m, (const T *)aF, (const T *)aB, (const T *)sinv,
+        launch_pdl(k_line_mean<T, true>, m, nt, smem, s, m, (const T *)aF, (const T *)aB, (const T *)sinv,
                                                  (const T *)b, (const T *)Moth, (T *)Mown, nullptr,
                                                  x, x_transposed);
     } else {
         if (!y) return cudaErrorInvalidValue;
-        k_line_mean<T, false><<<m, nt, 0, s>>>(m, (const T *)aF, (const T *)aB, (const T *)sinv,
+        launch_pdl(k_line_mean<T, false>, m, nt, 0, s, m, (const T *)aF, (const T *)aB, (const T *)sinv,
                                                (const T *)b, (const T *)Moth, (T *)Mown, (T *)y, x,
                                                x_transposed);
     }
@@ -1086,11 +1100,11 @@ cudaError_t launch_line_mean_cols(int prec, int m, const void *aF, const void *a
     const int nt = ((nch + qw - 1) / qw) * 32;
     const int grid = (m + kColLines - 1) / kColLines;
     if (C == 8)
-        k_line_mean_cols<float, 8><<<grid, nt, 0, s>>>(m, (const float *)aF, (const float *)aB,
+        launch_pdl(k_line_mean_cols<float, 8>, grid, nt, 0, s, m, (const float *)aF, (const float *)aB,
                                                        (const float *)sinv, (const float *)b,
                                                        (const float *)Moth, (float *)Mown, x);
     else
-        k_line_mean_cols<float, 16><<<grid, nt, 0, s>>>(m, (const float *)aF, (const float *)aB,
+        launch_pdl(k_line_mean_cols<float, 16>, grid, nt, 0, s, m, (const float *)aF, (const float *)aB,
                                                         (const float *)sinv, (const float *)b,
                                                         (const float *)Moth, (float *)Mown, x);
     return cudaGetLastError();
@@ -1117,11 +1131,11 @@ cudaError_t launch_line_couplings_from_stencil(int prec, int m, const StencilPar
     count_launches(s, 1);
     const int grid = std::min((n + 255) / 256, 152 * 16);
     if (prec == 0)
-        k_line_couplings_from_stencil<double><<<grid, 256, 0, s>>>(
+        launch_pdl(k_line_couplings_from_stencil<double>, grid, 256, 0, s,
             n, m, sp, a64, diag64, (double *)subH, (double *)supH, (double *)subV, (double *)supV,
             (double *)diagV);
     else
-        k_line_couplings_from_stencil<float><<<grid, 256, 0, s>>>(
+        launch_pdl(k_line_couplings_from_stencil<float>, grid, 256, 0, s,
             n, m, sp, a64, diag64, (float *)subH, (float *)supH, (float *)subV, (float *)supV,
             (float *)diagV);
     return cudaGetLastError();
@@ -1135,11 +1149,11 @@ cudaError_t launch_line_couplings_transpose(int prec, int m, const void *sub, co
     const int64_t total = (int64_t)m * m;
     const int grid = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
     if (prec == 0)
-        k_line_couplings_transpose<double><<<grid, 256, 0, s>>>(m, total, (const double *)sub,
+        launch_pdl(k_line_couplings_transpose<double>, grid, 256, 0, s, m, total, (const double *)sub,
                                                                (const double *)sup, (double *)subT,
                                                                (double *)supT);
     else
-        k_line_couplings_transpose<float><<<grid, 256, 0, s>>>(m, total, (const float *)sub,
+        launch_pdl(k_line_couplings_transpose<float>, grid, 256, 0, s, m, total, (const float *)sub,
                                                               (const float *)sup, (float *)subT,
                                                               (float *)supT);
     return cudaGetLastError();
@@ -1151,9 +1165,9 @@ cudaError_t launch_transpose(int prec, int m, const void *in, void *out, cudaStr
     count_launches(s, 1);
     const dim3 block(32, 8), grid((m + kTile - 1) / kTile, (m + kTile - 1) / kTile);
     if (prec == 0)
-        k_transpose<double><<<grid, block, 0, s>>>(m, (const double *)in, (double *)out);
+        launch_pdl(k_transpose<double>, grid, block, 0, s, m, (const double *)in, (double *)out);
     else
-        k_transpose<float><<<grid, block, 0, s>>>(m, (const float *)in, (float *)out);
+        launch_pdl(k_transpose<float>, grid, block, 0, s, m, (const float *)in, (float *)out);
     return cudaGetLastError();
 }
 

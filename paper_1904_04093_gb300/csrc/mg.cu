@@ -63,6 +63,8 @@ __global__ void __launch_bounds__(256) k_mg_restrict_residual(
     double *__restrict__ T, double scale, double *__restrict__ rc, float *__restrict__ rcf,
     double *__restrict__ rcd, unsigned *flags)
 {
+    pdl_wait();
+    pdl_trigger();
     constexpr int XW = 2 * TX + 3, XH = 2 * TY + 3, RW = 2 * TX + 1, RH = 2 * TY + 1;
     __shared__ double xs[XH][XW];
     __shared__ double rs[RH][RW];
@@ -148,6 +150,8 @@ __global__ void __launch_bounds__(256) k_mg_prolong_residual(
     const double *__restrict__ ec, const double *__restrict__ ec2, double *__restrict__ Xout,
     double *__restrict__ r, float *__restrict__ rf, unsigned *flags)
 {
+    pdl_wait();
+    pdl_trigger();
     // fine points x0 - 1 .. x0 + TX interpolate from coarse points
     // x0 / 2 - 1 .. x0 / 2 + TX / 2 (TX even), likewise in y
     constexpr int XW = TX + 2, XH = TY + 2, CW = TX / 2 + 2, CH = TY / 2 + 2;
@@ -222,13 +226,11 @@ cudaError_t restrict_k(int mf, const Dirs &d, const double *a64, const double *d
     const int mc = (mf - 1) / 2;
     const unsigned gx = (unsigned)((mc + RX - 1) / RX), gy = (unsigned)((mc + RY - 1) / RY);
     if ((int64_t)gx * gy >= kBigTilesMin)
-        k_mg_restrict_residual<K, RX, RY><<<dim3(gx, gy), 256, 0, s>>>(mf, d, a64, diag64, b, X, E, T, scale,
-                                                                       rc, rcf, rcd, flags);
-    else
-        k_mg_restrict_residual<K, RXS, RYS>
-            <<<dim3((unsigned)((mc + RXS - 1) / RXS), (unsigned)((mc + RYS - 1) / RYS)), 256, 0, s>>>(
-                mf, d, a64, diag64, b, X, E, T, scale, rc, rcf, rcd, flags);
-    return cudaGetLastError();
+        return launch_pdl(k_mg_restrict_residual<K, RX, RY>, dim3(gx, gy), 256, 0, s, mf, d, a64, diag64, b, X,
+                          E, T, scale, rc, rcf, rcd, flags);
+    return launch_pdl(k_mg_restrict_residual<K, RXS, RYS>,
+                      dim3((unsigned)((mc + RXS - 1) / RXS), (unsigned)((mc + RYS - 1) / RYS)), 256, 0, s, mf, d,
+                      a64, diag64, b, X, E, T, scale, rc, rcf, rcd, flags);
 }
 
 template <int K>
@@ -238,13 +240,11 @@ cudaError_t prolong_k(int mf, const Dirs &d, const double *a64, const double *di
 {
     const unsigned gx = (unsigned)((mf + PX - 1) / PX), gy = (unsigned)((mf + PY - 1) / PY);
     if ((int64_t)gx * gy >= kBigTilesMin)
-        k_mg_prolong_residual<K, PX, PY><<<dim3(gx, gy), 256, 0, s>>>(mf, d, a64, diag64, b, Xin, Ein, ec, ec2,
-                                                                      Xout, r, rf, flags);
-    else
-        k_mg_prolong_residual<K, PXS, PYS>
-            <<<dim3((unsigned)((mf + PXS - 1) / PXS), (unsigned)((mf + PYS - 1) / PYS)), 256, 0, s>>>(
-                mf, d, a64, diag64, b, Xin, Ein, ec, ec2, Xout, r, rf, flags);
-    return cudaGetLastError();
+        return launch_pdl(k_mg_prolong_residual<K, PX, PY>, dim3(gx, gy), 256, 0, s, mf, d, a64, diag64, b, Xin,
+                          Ein, ec, ec2, Xout, r, rf, flags);
+    return launch_pdl(k_mg_prolong_residual<K, PXS, PYS>,
+                      dim3((unsigned)((mf + PXS - 1) / PXS), (unsigned)((mf + PYS - 1) / PYS)), 256, 0, s, mf, d,
+                      a64, diag64, b, Xin, Ein, ec, ec2, Xout, r, rf, flags);
 }
 
 }  // namespace

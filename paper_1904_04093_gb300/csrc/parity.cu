@@ -55,6 +55,8 @@ template <typename T>
 __global__ void k_parity_convert(ParityGrid g, int to_class, const T *__restrict__ src,
                                  T *__restrict__ dst)
 {
+    pdl_wait();
+    pdl_trigger();
     const long long n = (long long)g.m * g.m;
     const long long total = n * g.K;
     for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
@@ -91,6 +93,8 @@ __global__ void __launch_bounds__(256) k_sweep_parity(ParityGrid g, PhaseClasses
                                                       unsigned *__restrict__ flags, unsigned zl,
                                                       unsigned zm)
 {
+    pdl_wait();
+    pdl_trigger();
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long end = ph.nq >= 4 ? ph.start[4] : ph.nq == 3 ? ph.start[3] : ph.nq == 2 ? ph.start[2] : ph.start[1];
     if (t >= end) return;
@@ -232,6 +236,8 @@ __global__ void __launch_bounds__(256) k_sweep_parity_std(ParityGrid g, PhaseCla
                                                           unsigned *__restrict__ flags,
                                                           unsigned zl, unsigned zm)
 {
+    pdl_wait();
+    pdl_trigger();
     const int z = blockIdx.z;
     const int q = z == 0 ? ph.q[0] : z == 1 ? ph.q[1] : z == 2 ? ph.q[2] : ph.q[3];
     const unsigned cx = blockIdx.x * blockDim.x + threadIdx.x, cy = blockIdx.y;
@@ -258,9 +264,9 @@ cudaError_t launch_parity_convert(const ParityGrid &g, int prec, int to_class, c
     const long long want = (total + 255) / 256;
     const int grid = (int)(want < 152 * 32 ? want : 152 * 32);
     if (prec == 0)
-        k_parity_convert<double><<<grid, 256, 0, s>>>(g, to_class, (const double *)src, (double *)dst);
+        launch_pdl(k_parity_convert<double>, grid, 256, 0, s, g, to_class, (const double *)src, (double *)dst);
     else
-        k_parity_convert<float><<<grid, 256, 0, s>>>(g, to_class, (const float *)src, (float *)dst);
+        launch_pdl(k_parity_convert<float>, grid, 256, 0, s, g, to_class, (const float *)src, (float *)dst);
     return cudaGetLastError();
 }
 
@@ -283,20 +289,20 @@ cudaError_t launch_sweep_parity(const ParityGrid &g, const PhaseClasses &ph, int
         if (hmax > 65535) return cudaErrorInvalidValue;
         if (g.K == 4) {
             if (prec == 0)
-                k_sweep_parity_std<double, 4><<<grid3, block, 0, s>>>(
+                launch_pdl(k_sweep_parity_std<double, 4>, grid3, block, 0, s,
                     g, ph, (const double *)a, (const double *)c, (const double *)diag,
                     (const double *)b, (double *)Lo, (double *)Mo, x, flags, zl, zm);
             else
-                k_sweep_parity_std<float, 4><<<grid3, block, 0, s>>>(
+                launch_pdl(k_sweep_parity_std<float, 4>, grid3, block, 0, s,
                     g, ph, (const float *)a, (const float *)c, (const float *)diag,
                     (const float *)b, (float *)Lo, (float *)Mo, x, flags, zl, zm);
         } else {
             if (prec == 0)
-                k_sweep_parity_std<double, 8><<<grid3, block, 0, s>>>(
+                launch_pdl(k_sweep_parity_std<double, 8>, grid3, block, 0, s,
                     g, ph, (const double *)a, (const double *)c, (const double *)diag,
                     (const double *)b, (double *)Lo, (double *)Mo, x, flags, zl, zm);
             else
-                k_sweep_parity_std<float, 8><<<grid3, block, 0, s>>>(
+                launch_pdl(k_sweep_parity_std<float, 8>, grid3, block, 0, s,
                     g, ph, (const float *)a, (const float *)c, (const float *)diag,
                     (const float *)b, (float *)Lo, (float *)Mo, x, flags, zl, zm);
         }
@@ -306,11 +312,11 @@ cudaError_t launch_sweep_parity(const ParityGrid &g, const PhaseClasses &ph, int
 #define GABP_PAR_CASE(KK)                                                                         \
     case KK:                                                                                      \
         if (prec == 0)                                                                            \
-            k_sweep_parity<double, KK><<<grid, 256, 0, s>>>(                                      \
+            launch_pdl(k_sweep_parity<double, KK>, grid, 256, 0, s,                                       \
                 g, ph, (const double *)a, (const double *)c, (const double *)diag,                \
                 (const double *)b, (double *)Lo, (double *)Mo, x, flags, zl, zm);                         \
         else                                                                                      \
-            k_sweep_parity<float, KK><<<grid, 256, 0, s>>>(                                       \
+            launch_pdl(k_sweep_parity<float, KK>, grid, 256, 0, s,                                        \
                 g, ph, (const float *)a, (const float *)c, (const float *)diag,                   \
                 (const float *)b, (float *)Lo, (float *)Mo, x, flags, zl, zm);                            \
         break;
