@@ -45,13 +45,14 @@ IR_INNER_MAX = 400    # float sweeps per refinement step (restarting early beats
 #       --clock-control none -k regex:k_sweep_stencil -s 100 -c 3
 #       python bench.py --only fp64 --steps 1 --warmup 3
 # on a GB300.  It holds only for the kernel it was taken on, identified by the SHA-256 of the
-# source that defines it (the per-row update, the kernel and its launcher); the bench reports
+# source that defines it (the per-row update, the kernel and its launchers); the bench reports
 # null once that source differs.
-TRAFFIC_FP64_SWEEP_2048 = 971.82e6
+TRAFFIC_FP64_SWEEP_2048 = 971.83e6
 TRAFFIC_SOURCES = (("paper_1904_04093_gb300/csrc/sweep_row.cuh", None),
                    ("paper_1904_04093_gb300/csrc/kernels.cu", "k_sweep_stencil(\n    int n, StencilParams sp"),
+                   ("paper_1904_04093_gb300/csrc/kernels.cu", "cudaError_t sweep_stencil_T(const DevLayout"),
                    ("paper_1904_04093_gb300/csrc/kernels.cu", "cudaError_t launch_sweep(const DevLayout"))
-TRAFFIC_SOURCES_SHA256 = "c3a80e6ab70b7c981a24a8bd51c391297772c20cb300182fad480caba424f110"
+TRAFFIC_SOURCES_SHA256 = "329a669eeacb05a4204ebc9744f589597a0071112a783fbe66e3585ac6c8bf3c"
 # FP64 operations per directed edge of the message update in its stored form (Sec. 2.3 rule):
 # d = P_s - L[rev] (1), 1/d (1), L' = c q (1), B_s - M[rev] (1), M' = a (.) q (2), P' += L',
 # B' += M' (2).  The kernel issues 10 on the FP64 pipe: the reciprocal is the hardware

@@ -45,6 +45,9 @@ constexpr int RX = 32, RY = 16, RXS = 8, RYS = 8;
 constexpr int PX = 64, PY = 16, PXS = 16, PYS = 16;
 // fewer large tiles than this (4 per SM) and a level takes the small ones
 constexpr int kBigTilesMin = GABP_MG_BIG_TILES_MIN;
+constexpr int kMgThreads = 256;  // threads per CTA of both kernels
+// at most this many small restriction tiles (two per SM) and they prefetch
+constexpr int kPrefetchTilesMax = 304;
 
 struct Dirs {
     int dx[8], dy[8];
@@ -56,8 +59,8 @@ __device__ __forceinline__ double sum_or_zero(const double *__restrict__ X,
     return X ? (E ? X[i] + E[i] : X[i]) : (E ? E[i] : 0.0);
 }
 
-template <int K, int TX, int TY>
-__global__ void __launch_bounds__(256) k_mg_restrict_residual(
+template <int K, int TX, int TY, bool kPre>
+__global__ void __launch_bounds__(kMgThreads) k_mg_restrict_residual(
     int mf, Dirs dir, const double *__restrict__ a64, const double *__restrict__ diag64,
     const double *__restrict__ b, const double *__restrict__ X, const double *__restrict__ E,
     double *__restrict__ T, double scale, double *__restrict__ rc, float *__restrict__ rcf,
@@ -77,6 +80,28 @@ __global__ void __launch_bounds__(256) k_mg_restrict_residual(
     const int ox1 = I0 + TX >= mc ? mf : 2 * (I0 + TX);
     const int oy1 = J0 + TY >= mc ? mf : 2 * (J0 + TY);
     const int fx0 = 2 * I0 - 1, fy0 = 2 * J0 - 1;
+    const int rw = 2 * nI + 1, rh = 2 * nJ + 1;
+    // kPre (small tiles on a level that fills one wave at most): a thread's
+    // residual points, two at most, have their matrix entries loaded first, so
+    // those loads are in flight while x1 is staged; on larger levels the
+    // registers this takes cost more occupancy than the overlap gains
+    constexpr int NR = (RW * RH + kMgThreads - 1) / kMgThreads;
+    static_assert(!kPre || NR <= 2, "prefetch holds two residual points per thread");
+    constexpr int NP = kPre ? NR : 1;
+    double pd[NP], pb[NP], pa[NP][K > 0 ? K : 1];
+    if constexpr (kPre) {
+#pragma unroll
+        for (int u = 0; u < NR; ++u) {
+            const int t = threadIdx.x + u * kMgThreads;
+            const int ly = t / rw, lx = t - ly * rw;
+            const int64_t i = (int64_t)(2 * J0 + ly) * mf + (2 * I0 + lx);
+            const bool ok = t < rw * rh && !(kIndexChecks && (i < 0 || i >= n));
+            pd[u] = ok ? diag64[i] : 0.0;
+            pb[u] = ok ? b[i] : 0.0;
+#pragma unroll
+            for (int k = 0; k < K; ++k) pa[u][k] = ok ? a64[k * n + i] : 0.0;
+        }
+    }
     for (int t = threadIdx.x; t < XW * XH; t += blockDim.x) {
         const int ly = t / XW, lx = t - ly * XW;
         const int fx = fx0 + lx, fy = fy0 + ly;
@@ -89,19 +114,37 @@ __global__ void __launch_bounds__(256) k_mg_restrict_residual(
         xs[ly][lx] = v;
     }
     __syncthreads();
-    const int rw = 2 * nI + 1, rh = 2 * nJ + 1;
-    for (int t = threadIdx.x; t < rw * rh; t += blockDim.x) {
-        const int ly = t / rw, lx = t - ly * rw;
-        const int64_t i = (int64_t)(2 * J0 + ly) * mf + (2 * I0 + lx);
-        if (kIndexChecks && (i < 0 || i >= n)) {
-            atomicOr(flags, FLAG_INDEX);
-            rs[ly][lx] = 0.0;
-            continue;
-        }
-        double acc = fma(-diag64[i], xs[ly + 1][lx + 1], b[i]);
+    if constexpr (kPre) {
 #pragma unroll
-        for (int k = 0; k < K; ++k) acc = fma(a64[k * n + i], xs[ly + 1 + dir.dy[k]][lx + 1 + dir.dx[k]], acc);
-        rs[ly][lx] = acc;
+        for (int u = 0; u < NR; ++u) {
+            const int t = threadIdx.x + u * kMgThreads;
+            if (t >= rw * rh) break;
+            const int ly = t / rw, lx = t - ly * rw;
+            const int64_t i = (int64_t)(2 * J0 + ly) * mf + (2 * I0 + lx);
+            if (kIndexChecks && (i < 0 || i >= n)) {
+                atomicOr(flags, FLAG_INDEX);
+                rs[ly][lx] = 0.0;
+                continue;
+            }
+            double acc = fma(-pd[u], xs[ly + 1][lx + 1], pb[u]);
+#pragma unroll
+            for (int k = 0; k < K; ++k) acc = fma(pa[u][k], xs[ly + 1 + dir.dy[k]][lx + 1 + dir.dx[k]], acc);
+            rs[ly][lx] = acc;
+        }
+    } else {
+        for (int t = threadIdx.x; t < rw * rh; t += blockDim.x) {
+            const int ly = t / rw, lx = t - ly * rw;
+            const int64_t i = (int64_t)(2 * J0 + ly) * mf + (2 * I0 + lx);
+            if (kIndexChecks && (i < 0 || i >= n)) {
+                atomicOr(flags, FLAG_INDEX);
+                rs[ly][lx] = 0.0;
+                continue;
+            }
+            double acc = fma(-diag64[i], xs[ly + 1][lx + 1], b[i]);
+#pragma unroll
+            for (int k = 0; k < K; ++k) acc = fma(a64[k * n + i], xs[ly + 1 + dir.dy[k]][lx + 1 + dir.dx[k]], acc);
+            rs[ly][lx] = acc;
+        }
     }
     __syncthreads();
     for (int t = threadIdx.x; t < nI * nJ; t += blockDim.x) {
@@ -144,7 +187,7 @@ __device__ __forceinline__ double prolong_at(const double (*cs)[CW], int cx0, in
 }
 
 template <int K, int TX, int TY>
-__global__ void __launch_bounds__(256) k_mg_prolong_residual(
+__global__ void __launch_bounds__(kMgThreads) k_mg_prolong_residual(
     int mf, Dirs dir, const double *__restrict__ a64, const double *__restrict__ diag64,
     const double *__restrict__ b, const double *__restrict__ Xin, const double *__restrict__ Ein,
     const double *__restrict__ ec, const double *__restrict__ ec2, double *__restrict__ Xout,
@@ -162,7 +205,19 @@ __global__ void __launch_bounds__(256) k_mg_prolong_residual(
     const int64_t n = (int64_t)mf * mf;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const int cx0 = x0 / 2 - 1, cy0 = y0 / 2 - 1;
-    for (int t = threadIdx.x; t < CW * CH; t += blockDim.x) {
+    // the tile's x1 = Xin + Ein is loaded first, so its loads are in flight
+    // while the coarse patch is staged
+    constexpr int NXS = XW * XH, NU = (NXS + kMgThreads - 1) / kMgThreads;
+    double x1[NU];
+#pragma unroll
+    for (int u = 0; u < NU; ++u) {
+        const int t = threadIdx.x + u * kMgThreads;
+        const int ly = t / XW, lx = t - ly * XW;
+        const int fx = x0 - 1 + lx, fy = y0 - 1 + ly;
+        x1[u] = t < NXS && fx >= 0 && fx < mf && fy >= 0 && fy < mf
+                    ? sum_or_zero(Xin, Ein, (int64_t)fy * mf + fx) : 0.0;
+    }
+    for (int t = threadIdx.x; t < CW * CH; t += kMgThreads) {
         const int ly = t / CW, lx = t - ly * CW;
         const int I = cx0 + lx, J = cy0 + ly;
         double v = 0.0;
@@ -173,19 +228,21 @@ __global__ void __launch_bounds__(256) k_mg_prolong_residual(
         cs[ly][lx] = v;
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < XW * XH; t += blockDim.x) {
+#pragma unroll
+    for (int u = 0; u < NU; ++u) {
+        const int t = threadIdx.x + u * kMgThreads;
+        if (t >= NXS) break;
         const int ly = t / XW, lx = t - ly * XW;
         const int fx = x0 - 1 + lx, fy = y0 - 1 + ly;
         double v = 0.0;
         if (fx >= 0 && fx < mf && fy >= 0 && fy < mf) {
-            const int64_t i = (int64_t)fy * mf + fx;
-            v = sum_or_zero(Xin, Ein, i) + prolong_at<CW>(cs, cx0, cy0, fx, fy);
-            if (lx >= 1 && lx <= TX && ly >= 1 && ly <= TY) Xout[i] = v;
+            v = x1[u] + prolong_at<CW>(cs, cx0, cy0, fx, fy);
+            if (lx >= 1 && lx <= TX && ly >= 1 && ly <= TY) Xout[(int64_t)fy * mf + fx] = v;
         }
         xs[ly][lx] = v;
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < TX * TY; t += blockDim.x) {
+    for (int t = threadIdx.x; t < TX * TY; t += kMgThreads) {
         const int ly = t / TX, lx = t - ly * TX;
         const int fx = x0 + lx, fy = y0 + ly;
         if (fx >= mf || fy >= mf) continue;
@@ -226,11 +283,14 @@ cudaError_t restrict_k(int mf, const Dirs &d, const double *a64, const double *d
     const int mc = (mf - 1) / 2;
     const unsigned gx = (unsigned)((mc + RX - 1) / RX), gy = (unsigned)((mc + RY - 1) / RY);
     if ((int64_t)gx * gy >= kBigTilesMin)
-        return launch_pdl(k_mg_restrict_residual<K, RX, RY>, dim3(gx, gy), 256, 0, s, mf, d, a64, diag64, b, X,
+        return launch_pdl(k_mg_restrict_residual<K, RX, RY, false>, dim3(gx, gy), kMgThreads, 0, s, mf, d, a64,
+                          diag64, b, X, E, T, scale, rc, rcf, rcd, flags);
+    const dim3 gs((unsigned)((mc + RXS - 1) / RXS), (unsigned)((mc + RYS - 1) / RYS));
+    if ((int64_t)gs.x * gs.y > kPrefetchTilesMax)
+        return launch_pdl(k_mg_restrict_residual<K, RXS, RYS, false>, gs, kMgThreads, 0, s, mf, d, a64, diag64, b, X,
                           E, T, scale, rc, rcf, rcd, flags);
-    return launch_pdl(k_mg_restrict_residual<K, RXS, RYS>,
-                      dim3((unsigned)((mc + RXS - 1) / RXS), (unsigned)((mc + RYS - 1) / RYS)), 256, 0, s, mf, d,
-                      a64, diag64, b, X, E, T, scale, rc, rcf, rcd, flags);
+    return launch_pdl(k_mg_restrict_residual<K, RXS, RYS, true>, gs, kMgThreads, 0, s, mf, d, a64, diag64, b, X, E,
+                      T, scale, rc, rcf, rcd, flags);
 }
 
 template <int K>
@@ -240,10 +300,10 @@ cudaError_t prolong_k(int mf, const Dirs &d, const double *a64, const double *di
 {
     const unsigned gx = (unsigned)((mf + PX - 1) / PX), gy = (unsigned)((mf + PY - 1) / PY);
     if ((int64_t)gx * gy >= kBigTilesMin)
-        return launch_pdl(k_mg_prolong_residual<K, PX, PY>, dim3(gx, gy), 256, 0, s, mf, d, a64, diag64, b, Xin,
+        return launch_pdl(k_mg_prolong_residual<K, PX, PY>, dim3(gx, gy), kMgThreads, 0, s, mf, d, a64, diag64, b, Xin,
                           Ein, ec, ec2, Xout, r, rf, flags);
     return launch_pdl(k_mg_prolong_residual<K, PXS, PYS>,
-                      dim3((unsigned)((mf + PXS - 1) / PXS), (unsigned)((mf + PYS - 1) / PYS)), 256, 0, s, mf, d,
+                      dim3((unsigned)((mf + PXS - 1) / PXS), (unsigned)((mf + PYS - 1) / PYS)), kMgThreads, 0, s, mf, d,
                       a64, diag64, b, Xin, Ein, ec, ec2, Xout, r, rf, flags);
 }
 
