@@ -176,8 +176,11 @@ void gabp_destroy(gabp_ctx *ctx);
  * Under schedule 2 the precision messages freeze as under the flood schedule
  * (freeze_lambda): once both families' messages stop changing, the lines'
  * elimination multipliers are stored and later sweeps move only the mean
- * messages.  They are not frozen under schedule 1; the batched solver always
- * floods.
+ * messages.  Under schedule 1 they freeze likewise on the parity-class layout
+ * (once they moved by less than rounding between two checks, the gains
+ * a_e / d_e of every slot and the aggregates P are stored and a phase moves
+ * only the mean messages: gabp_info.colored_mean_sweep_bytes); other
+ * colourings are not frozen.  The batched solver always floods.
  */
 gabp_status gabp_set_schedule(gabp_ctx *ctx, int schedule, const int32_t *color, int *ncolors);
 
@@ -287,6 +290,7 @@ typedef struct {
     int parity_layout;      /* 1: the coloured schedule runs on the parity-class layout */
     double colored_sweep_bytes; /* compulsory DRAM bytes of one sweep on that layout */
     int reordered;          /* 1: the unknowns are renumbered internally (gabp_options.reorder) */
+    double colored_mean_sweep_bytes; /* the same with frozen precision messages */
 } gabp_info;
 
 gabp_status gabp_get_info(gabp_ctx *ctx, gabp_info *info);
@@ -343,13 +347,13 @@ gabp_status gabp_fp64_peak(int op, int iters, gabp_peak_result *out);
  * loading the library holds until the process exits, so n <= 65536 and
  * nnz <= 262144; larger sizes return GABP_E_INVALID_ARG without launching.
  * The first call on a device looks up that array's address
- * (cudaGetSymbolAddress); make that first call before any stream capture
- * begins.  Every call shares the one array and leaves its last contents there
- * (each call starts from zero messages and clears the error word itself), so
- * calls whose work overlaps on the GPU (other streams, other host threads)
- * race and give undefined results.  Each call is synchronous: it enqueues its
- * sweeps on `stream` (a cudaStream_t, NULL = default), copies the error word
- * to host memory and synchronises `stream` before it returns the status:
+ * (cudaGetSymbolAddress).  Every call shares the one array and leaves its
+ * last contents there (each call starts from zero messages and clears the
+ * error word itself), so calls whose work overlaps on the GPU (other streams,
+ * other host threads) race and give undefined results.  Each call is
+ * synchronous: it enqueues its sweeps on `stream` (a cudaStream_t, NULL =
+ * default), copies the error word to host memory and synchronises `stream`
+ * before it returns the status:
  * GABP_E_BAD_CSR for a row pointer or column index out of range or columns
  * not strictly ascending in a row, GABP_E_ZERO_DIAG for a missing or zero
  * diagonal, both found on the device, and GABP_E_BREAKDOWN as in gabp_sweep.

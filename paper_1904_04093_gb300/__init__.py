@@ -50,7 +50,7 @@ class Info(ctypes.Structure):
                 ("mean_sweep_bytes", ctypes.c_double),
                 ("residual_bytes", ctypes.c_double), ("device_bytes", ctypes.c_size_t),
                 ("parity_layout", ctypes.c_int), ("colored_sweep_bytes", ctypes.c_double),
-                ("reordered", ctypes.c_int)]
+                ("reordered", ctypes.c_int), ("colored_mean_sweep_bytes", ctypes.c_double)]
 
 
 class PeakResult(ctypes.Structure):

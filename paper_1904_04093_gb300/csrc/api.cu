@@ -642,6 +642,9 @@ gabp_status gabp_get_info(gabp_ctx *ctx, gabp_info *info)
     // parity-class coloured sweep: per slot a, c, incoming L, M read and L', M'
     // written; per node diag and b read (no aggregates)
     info->colored_sweep_bytes = 6.0 * p * S + 2.0 * p * n;
+    // with frozen precision messages: per slot the gain and the incoming M read, M'
+    // written; per node b read (the frozen P only on sweeps that form the beliefs)
+    info->colored_mean_sweep_bytes = 3.0 * p * S + 1.0 * p * n;
     return GABP_OK;
 }
 

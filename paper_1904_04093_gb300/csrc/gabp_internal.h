@@ -203,11 +203,17 @@ cudaError_t launch_parity_convert(const ParityGrid &g, int prec, int to_class, c
 // One in-place phase of the coloured schedule over the classes of ph:
 // a, c in class layout; diag, b in natural order; Lo, Mo the class-layout state.
 // zl, zm: parity classes whose precision / mean messages read as zero (the
-// first sweep after a reset of the messages, instead of clearing the arrays)
+// first sweep after a reset of the messages, instead of clearing the arrays).
+// mean = 1 (frozen precision messages): a = the gains, diag = the frozen
+// aggregates P (natural order), only Mo moves; c, Lo, zl unused.
 cudaError_t launch_sweep_parity(const ParityGrid &g, const PhaseClasses &ph, int prec,
                                 const void *a, const void *c, const void *diag, const void *b,
                                 void *Lo, void *Mo, double *x, unsigned *flags, unsigned zl,
-                                unsigned zm, cudaStream_t s);
+                                unsigned zm, int mean, cudaStream_t s);
+// Frozen precision messages on the class layout: gains g = a / (P_s - L[rev])
+// (class layout) and the aggregates P (natural order) from the current Lo.
+cudaError_t launch_freeze_parity(const ParityGrid &g, int prec, const void *a, const void *diag,
+                                 const void *Lo, void *gains, void *Pf, unsigned *flags, cudaStream_t s);
 cudaError_t launch_get_state(const int64_t *slotmap, int64_t nnz, int prec, const void *Lm,
                              const void *Mm, double *lam, double *m, cudaStream_t s);
 cudaError_t launch_set_state(const int64_t *slotmap, int64_t nnz, int prec, const double *lam,

@@ -124,6 +124,7 @@ struct gabp_ctx {
     void *laFV = nullptr, *laBV = nullptr, *lSV = nullptr;
     void *laFVn = nullptr, *laBVn = nullptr, *lSVn = nullptr;  // the same in natural order
     void *lprevH = nullptr, *lprevV = nullptr;
+    void *pprevL = nullptr;  // parity-class layout: the precision messages at the previous check
     bool lprev_valid = false;
     // parity-class layout: messages reset lazily (bit 0 precision, bit 1 mean); the
     // next sweep reads every class that has not sent in it yet as zero

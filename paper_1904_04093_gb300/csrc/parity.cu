@@ -83,7 +83,11 @@ __global__ void k_parity_convert(ParityGrid g, int to_class, const T *__restrict
 // zl, zm: classes whose precision / mean messages read as zero (bit q for
 // class q): after a reset of the messages the first sweep reads the classes
 // that have not sent yet as zero instead of clearing the arrays first.
-template <typename T, int K>
+// kMean (frozen precision messages, Sec. 4.2): a holds the gains g = a / d of
+// the node's outgoing slots, diag the frozen aggregate P (natural order, read
+// only for the belief), and only the mean messages move,
+// M' = g (B - M[rev]); c, Lo and zl are unused.
+template <typename T, int K, bool kMean>
 __global__ void __launch_bounds__(256) k_sweep_parity(ParityGrid g, PhaseClasses ph,
                                                       const T *__restrict__ a,
                                                       const T *__restrict__ c,
@@ -127,17 +131,24 @@ __global__ void __launch_bounds__(256) k_sweep_parity(ParityGrid g, PhaseClasses
             atomicOr(flags, FLAG_INDEX);
             src = 0;
         }
-        lin[k] = in && !((zl >> qn) & 1u) ? Lo[src] : T(0);
+        if (!kMean) lin[k] = in && !((zl >> qn) & 1u) ? Lo[src] : T(0);
         min_[k] = in && !((zm >> qn) & 1u) ? Mo[src] : T(0);
         av[k] = a[(long long)k * n + pos];
-        cv[k] = c[(long long)k * n + pos];
+        if (!kMean) cv[k] = c[(long long)k * n + pos];
     }
-    T P = diag[s], B = b[s];
+    T B = b[s];
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-        P += lin[k];
-        B += min_[k];
+    for (int k = 0; k < K; ++k) B += min_[k];
+    if (kMean) {
+        if (x) x[s] = (double)(B / diag[s]);
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+            if (nonzero(av[k])) Mo[(long long)k * n + pos] = av[k] * (B - min_[k]);
+        return;
     }
+    T P = diag[s];
+#pragma unroll
+    for (int k = 0; k < K; ++k) P += lin[k];
     if (x) x[s] = (double)(B / P);
     bool bad = false;
 #pragma unroll
@@ -148,6 +159,55 @@ __global__ void __launch_bounds__(256) k_sweep_parity(ParityGrid g, PhaseClasses
         const T qd = fast_rcp(d);
         Lo[(long long)k * n + pos] = cv[k] * qd;
         Mo[(long long)k * n + pos] = av[k] * (B - min_[k]) * qd;
+    }
+    if (bad) atomicOr(flags, FLAG_BREAKDOWN);
+}
+
+// Freezing of the precision messages on the class layout (every node of every
+// class): P_s = diag_s + sum of its incoming L into Pf (natural order), and for
+// each outgoing slot the gain g = a / (P_s - L[rev]) (zero where a = 0).
+template <typename T, int K>
+__global__ void __launch_bounds__(256) k_freeze_parity(ParityGrid g, const T *__restrict__ a,
+                                                       const T *__restrict__ diag,
+                                                       const T *__restrict__ Lo,
+                                                       T *__restrict__ gains, T *__restrict__ Pf,
+                                                       unsigned *__restrict__ flags)
+{
+    pdl_wait();
+    pdl_trigger();
+    const long long n = (long long)g.m * g.m;
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    int q, sx, sy;
+    class_node(g, p, q, sx, sy);
+    T lin[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const int nx = sx + g.dx[k], ny = sy + g.dy[k];
+        const bool in = in_grid(g, nx, ny);
+        long long src = in ? (long long)g.krev[k] * n + class_pos(g, nx, ny) : 0;
+        if (kIndexChecks && (src < 0 || src >= (long long)K * n)) {
+            atomicOr(flags, FLAG_INDEX);
+            src = 0;
+        }
+        lin[k] = in ? Lo[src] : T(0);
+    }
+    const long long s = (long long)sy * g.m + sx;
+    T P = diag[s];
+#pragma unroll
+    for (int k = 0; k < K; ++k) P += lin[k];
+    Pf[s] = P;
+    bool bad = false;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const T ak = a[(long long)k * n + p];
+        T ge = T(0);
+        if (nonzero(ak)) {
+            const T d = P - lin[k];
+            bad |= bad_den(d);
+            ge = ak * fast_rcp(d);
+        }
+        gains[(long long)k * n + p] = ge;
     }
     if (bad) atomicOr(flags, FLAG_BREAKDOWN);
 }
@@ -168,8 +228,9 @@ __device__ constexpr int floor_half(int v) { return v >= 0 ? v / 2 : -((-v + 1) 
 
 // One node (cx, cy) of the class (PX, PY): the neighbour in direction k lies
 // in the class QT at class row cy + DY2 and column cx + DX2, all known at
-// compile time; only the grid edge is tested at run time.
-template <typename T, int K, int PX, int PY>
+// compile time; only the grid edge is tested at run time.  kMean as in
+// k_sweep_parity.
+template <typename T, int K, int PX, int PY, bool kMean>
 __device__ __forceinline__ void parity_node(const ParityGrid &g, unsigned cx, unsigned cy,
                                             const T *__restrict__ a, const T *__restrict__ c,
                                             const T *__restrict__ diag,
@@ -200,18 +261,25 @@ __device__ __forceinline__ void parity_node(const ParityGrid &g, unsigned cx, un
             bad_index = true;
             src = 0;
         }
-        lin[k] = in && !((zl >> qt) & 1u) ? Lo[src] : T(0);
+        if (!kMean) lin[k] = in && !((zl >> qt) & 1u) ? Lo[src] : T(0);
         min_[k] = in && !((zm >> qt) & 1u) ? Mo[src] : T(0);
         av[k] = a[(unsigned)k * n + pos];
-        cv[k] = c[(unsigned)k * n + pos];
+        if (!kMean) cv[k] = c[(unsigned)k * n + pos];
     }
     const unsigned s = sy * m + sx;
-    T P = diag[s], B = b[s];
+    T B = b[s];
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-        P += lin[k];
-        B += min_[k];
+    for (int k = 0; k < K; ++k) B += min_[k];
+    if (kMean) {
+        if (x) x[s] = (double)(B / diag[s]);
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+            if (nonzero(av[k])) Mo[(unsigned)k * n + pos] = av[k] * (B - min_[k]);
+        return;
     }
+    T P = diag[s];
+#pragma unroll
+    for (int k = 0; k < K; ++k) P += lin[k];
     if (x) x[s] = (double)(B / P);
 #pragma unroll
     for (int k = 0; k < K; ++k) {
@@ -226,7 +294,7 @@ __device__ __forceinline__ void parity_node(const ParityGrid &g, unsigned cx, un
 
 // Standard orders: block (x, y, z) = (class columns, class row, class of the
 // phase), so a thread finds its node without division.
-template <typename T, int K>
+template <typename T, int K, bool kMean>
 __global__ void __launch_bounds__(256) k_sweep_parity_std(ParityGrid g, PhaseClasses ph,
                                                           const T *__restrict__ a,
                                                           const T *__restrict__ c,
@@ -244,10 +312,10 @@ __global__ void __launch_bounds__(256) k_sweep_parity_std(ParityGrid g, PhaseCla
     if (cx >= (unsigned)pick4(g.w, q) || cy >= (unsigned)pick4(g.h, q)) return;
     bool bad = false, bad_index = false;
     switch (q) {
-        case 0: parity_node<T, K, 0, 0>(g, cx, cy, a, c, diag, b, Lo, Mo, x, bad, zl, zm, bad_index); break;
-        case 1: parity_node<T, K, 1, 0>(g, cx, cy, a, c, diag, b, Lo, Mo, x, bad, zl, zm, bad_index); break;
-        case 2: parity_node<T, K, 0, 1>(g, cx, cy, a, c, diag, b, Lo, Mo, x, bad, zl, zm, bad_index); break;
-        default: parity_node<T, K, 1, 1>(g, cx, cy, a, c, diag, b, Lo, Mo, x, bad, zl, zm, bad_index); break;
+        case 0: parity_node<T, K, 0, 0, kMean>(g, cx, cy, a, c, diag, b, Lo, Mo, x, bad, zl, zm, bad_index); break;
+        case 1: parity_node<T, K, 1, 0, kMean>(g, cx, cy, a, c, diag, b, Lo, Mo, x, bad, zl, zm, bad_index); break;
+        case 2: parity_node<T, K, 0, 1, kMean>(g, cx, cy, a, c, diag, b, Lo, Mo, x, bad, zl, zm, bad_index); break;
+        default: parity_node<T, K, 1, 1, kMean>(g, cx, cy, a, c, diag, b, Lo, Mo, x, bad, zl, zm, bad_index); break;
     }
     if (bad) atomicOr(flags, FLAG_BREAKDOWN);
     if (kIndexChecks && bad_index) atomicOr(flags, FLAG_INDEX);
@@ -270,14 +338,14 @@ cudaError_t launch_parity_convert(const ParityGrid &g, int prec, int to_class, c
     return cudaGetLastError();
 }
 
-cudaError_t launch_sweep_parity(const ParityGrid &g, const PhaseClasses &ph, int prec,
-                                const void *a, const void *c, const void *diag, const void *b,
-                                void *Lo, void *Mo, double *x, unsigned *flags, unsigned zl,
-                                unsigned zm, cudaStream_t s)
+namespace {
+
+template <typename T, bool kMean>
+cudaError_t sweep_parity_T(const ParityGrid &g, const PhaseClasses &ph, const T *a, const T *c,
+                           const T *diag, const T *b, T *Lo, T *Mo, double *x, unsigned *flags,
+                           unsigned zl, unsigned zm, cudaStream_t s)
 {
     const long long nodes = ph.start[ph.nq];
-    if (nodes == 0) return cudaSuccess;
-    count_launches(s, 1);
     if (g.std_order) {
         int wmax = 0, hmax = 0;
         for (int j = 0; j < ph.nq; ++j) {
@@ -287,49 +355,70 @@ cudaError_t launch_sweep_parity(const ParityGrid &g, const PhaseClasses &ph, int
         const int block = wmax >= 256 ? 256 : ((wmax + 31) / 32) * 32;
         const dim3 grid3((unsigned)((wmax + block - 1) / block), (unsigned)hmax, (unsigned)ph.nq);
         if (hmax > 65535) return cudaErrorInvalidValue;
-        if (g.K == 4) {
-            if (prec == 0)
-                launch_pdl(k_sweep_parity_std<double, 4>, grid3, block, 0, s,
-                    g, ph, (const double *)a, (const double *)c, (const double *)diag,
-                    (const double *)b, (double *)Lo, (double *)Mo, x, flags, zl, zm);
-            else
-                launch_pdl(k_sweep_parity_std<float, 4>, grid3, block, 0, s,
-                    g, ph, (const float *)a, (const float *)c, (const float *)diag,
-                    (const float *)b, (float *)Lo, (float *)Mo, x, flags, zl, zm);
-        } else {
-            if (prec == 0)
-                launch_pdl(k_sweep_parity_std<double, 8>, grid3, block, 0, s,
-                    g, ph, (const double *)a, (const double *)c, (const double *)diag,
-                    (const double *)b, (double *)Lo, (double *)Mo, x, flags, zl, zm);
-            else
-                launch_pdl(k_sweep_parity_std<float, 8>, grid3, block, 0, s,
-                    g, ph, (const float *)a, (const float *)c, (const float *)diag,
-                    (const float *)b, (float *)Lo, (float *)Mo, x, flags, zl, zm);
-        }
-        return cudaGetLastError();
+        if (g.K == 4)
+            return launch_pdl(k_sweep_parity_std<T, 4, kMean>, grid3, block, 0, s, g, ph, a, c, diag, b, Lo, Mo,
+                              x, flags, zl, zm);
+        return launch_pdl(k_sweep_parity_std<T, 8, kMean>, grid3, block, 0, s, g, ph, a, c, diag, b, Lo, Mo, x,
+                          flags, zl, zm);
     }
     const int grid = (int)((nodes + 255) / 256);
-#define GABP_PAR_CASE(KK)                                                                         \
-    case KK:                                                                                      \
-        if (prec == 0)                                                                            \
-            launch_pdl(k_sweep_parity<double, KK>, grid, 256, 0, s,                                       \
-                g, ph, (const double *)a, (const double *)c, (const double *)diag,                \
-                (const double *)b, (double *)Lo, (double *)Mo, x, flags, zl, zm);                         \
-        else                                                                                      \
-            launch_pdl(k_sweep_parity<float, KK>, grid, 256, 0, s,                                        \
-                g, ph, (const float *)a, (const float *)c, (const float *)diag,                   \
-                (const float *)b, (float *)Lo, (float *)Mo, x, flags, zl, zm);                            \
-        break;
     switch (g.K) {
-        GABP_PAR_CASE(2)
-        GABP_PAR_CASE(4)
-        GABP_PAR_CASE(6)
-        GABP_PAR_CASE(8)
-        default:
-            return cudaErrorInvalidValue;
+        case 2: return launch_pdl(k_sweep_parity<T, 2, kMean>, grid, 256, 0, s, g, ph, a, c, diag, b, Lo, Mo, x, flags, zl, zm);
+        case 4: return launch_pdl(k_sweep_parity<T, 4, kMean>, grid, 256, 0, s, g, ph, a, c, diag, b, Lo, Mo, x, flags, zl, zm);
+        case 6: return launch_pdl(k_sweep_parity<T, 6, kMean>, grid, 256, 0, s, g, ph, a, c, diag, b, Lo, Mo, x, flags, zl, zm);
+        case 8: return launch_pdl(k_sweep_parity<T, 8, kMean>, grid, 256, 0, s, g, ph, a, c, diag, b, Lo, Mo, x, flags, zl, zm);
+        default: return cudaErrorInvalidValue;
     }
-#undef GABP_PAR_CASE
-    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t freeze_parity_T(const ParityGrid &g, const T *a, const T *diag, const T *Lo, T *gains, T *Pf,
+                            unsigned *flags, cudaStream_t s)
+{
+    const long long n = (long long)g.m * g.m;
+    const int grid = (int)((n + 255) / 256);
+    switch (g.K) {
+        case 2: return launch_pdl(k_freeze_parity<T, 2>, grid, 256, 0, s, g, a, diag, Lo, gains, Pf, flags);
+        case 4: return launch_pdl(k_freeze_parity<T, 4>, grid, 256, 0, s, g, a, diag, Lo, gains, Pf, flags);
+        case 6: return launch_pdl(k_freeze_parity<T, 6>, grid, 256, 0, s, g, a, diag, Lo, gains, Pf, flags);
+        case 8: return launch_pdl(k_freeze_parity<T, 8>, grid, 256, 0, s, g, a, diag, Lo, gains, Pf, flags);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_sweep_parity(const ParityGrid &g, const PhaseClasses &ph, int prec,
+                                const void *a, const void *c, const void *diag, const void *b,
+                                void *Lo, void *Mo, double *x, unsigned *flags, unsigned zl,
+                                unsigned zm, int mean, cudaStream_t s)
+{
+    if (ph.start[ph.nq] == 0) return cudaSuccess;
+    count_launches(s, 1);
+    if (prec == 0) {
+        if (mean)
+            return sweep_parity_T<double, true>(g, ph, (const double *)a, (const double *)c, (const double *)diag,
+                                                (const double *)b, (double *)Lo, (double *)Mo, x, flags, zl, zm, s);
+        return sweep_parity_T<double, false>(g, ph, (const double *)a, (const double *)c, (const double *)diag,
+                                             (const double *)b, (double *)Lo, (double *)Mo, x, flags, zl, zm, s);
+    }
+    if (mean)
+        return sweep_parity_T<float, true>(g, ph, (const float *)a, (const float *)c, (const float *)diag,
+                                           (const float *)b, (float *)Lo, (float *)Mo, x, flags, zl, zm, s);
+    return sweep_parity_T<float, false>(g, ph, (const float *)a, (const float *)c, (const float *)diag,
+                                        (const float *)b, (float *)Lo, (float *)Mo, x, flags, zl, zm, s);
+}
+
+cudaError_t launch_freeze_parity(const ParityGrid &g, int prec, const void *a, const void *diag,
+                                 const void *Lo, void *gains, void *Pf, unsigned *flags, cudaStream_t s)
+{
+    if (g.m == 0) return cudaSuccess;
+    count_launches(s, 1);
+    if (prec == 0)
+        return freeze_parity_T<double>(g, (const double *)a, (const double *)diag, (const double *)Lo,
+                                       (double *)gains, (double *)Pf, flags, s);
+    return freeze_parity_T<float>(g, (const float *)a, (const float *)diag, (const float *)Lo, (float *)gains,
+                                  (float *)Pf, flags, s);
 }
 
 }  // namespace gabp

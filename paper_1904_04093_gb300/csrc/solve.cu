@@ -122,10 +122,13 @@ cudaError_t sweep_once(gabp_ctx *ctx, bool transposed, double *x, cudaStream_t s
             unsigned later = 0;
             for (size_t k = j + 1; k < ctx->phases.size(); ++k)
                 for (int t = 0; t < ctx->phases[k].nq; ++t) later |= 1u << ctx->phases[k].q[t];
-            cudaError_t e = launch_sweep_parity(ctx->pg, ph, ctx->prec, transposed ? ctx->paT : ctx->pa,
-                                                ctx->pc, ctx->diagT, ctx->bT, ctx->Lm[c0],
-                                                ctx->Mm[c0], x, &ctx->dstat[0].flags,
-                                                (zp & 1u) ? later : 0u, (zp & 2u) ? later : 0u, s);
+            // frozen precision messages: the gains and the frozen aggregates P
+            // (in P[0]) stand for the coefficients and the diagonal
+            const bool fz = ctx->frozen;
+            cudaError_t e = launch_sweep_parity(
+                ctx->pg, ph, ctx->prec, fz ? ctx->g : (transposed ? ctx->paT : ctx->pa), fz ? nullptr : ctx->pc,
+                fz ? ctx->P[0] : ctx->diagT, ctx->bT, ctx->Lm[c0], ctx->Mm[c0], x, &ctx->dstat[0].flags,
+                (zp & 1u) ? later : 0u, (zp & 2u) ? later : 0u, fz ? 1 : 0, s);
             if (e != cudaSuccess) return e;
         }
         return cudaSuccess;
@@ -338,12 +341,45 @@ gabp_status maybe_freeze_lines(gabp_ctx *ctx, double rel, bool transposed)
     return GABP_OK;
 }
 
+// Parity-class layout (coloured schedule in place): the gains of every
+// outgoing slot and the aggregates P from the current precision messages.
+gabp_status freeze_parity(gabp_ctx *ctx, bool transposed)
+{
+    if (!ctx->g) CKS(dalloc(ctx, &ctx->g, (size_t)ctx->L.slots * esz(ctx->prec)));
+    CK(launch_freeze_parity(ctx->pg, ctx->prec, transposed ? ctx->paT : ctx->pa, ctx->diagT, ctx->Lm[ctx->cur],
+                            ctx->g, ctx->P[0], &ctx->dstat[0].flags, ctx->stream));
+    ctx->frozen = true;
+    return GABP_OK;
+}
+
+// Parity-class layout: freezes once the precision messages moved by at most
+// `rel` times their largest value since the previous check (the update is in
+// place, so the previous state is a copy taken at that check).
+gabp_status maybe_freeze_parity(gabp_ctx *ctx, double rel, bool transposed)
+{
+    const size_t S = (size_t)ctx->L.slots * esz(ctx->prec);
+    if (!ctx->pprevL) CKS(dalloc(ctx, &ctx->pprevL, S));
+    if (ctx->lprev_valid) {
+        CK(cudaMemsetAsync(&ctx->dstat[2], 0, sizeof(DevStatus), ctx->stream));
+        CK(launch_lambda_change(ctx->L.slots, ctx->prec, ctx->pprevL, ctx->Lm[ctx->cur], &ctx->dstat[2],
+                                ctx->stream));
+        double dmax = 0.0, lmax = 0.0;
+        unsigned fl = 0;
+        CKS(read_status(ctx, 2, &dmax, &lmax, &fl));
+        if (!(fl & FLAG_NAN) && dmax <= rel * lmax) return freeze_parity(ctx, transposed);
+    }
+    CK(cudaMemcpyAsync(ctx->pprevL, ctx->Lm[ctx->cur], S, cudaMemcpyDeviceToDevice, ctx->stream));
+    ctx->lprev_valid = true;
+    return GABP_OK;
+}
+
 // Freezes once the last sweep changed no precision message by more than
 // `rel` times the largest one (rounding level).
 gabp_status maybe_freeze(gabp_ctx *ctx, bool transposed)
 {
     if (ctx->frozen) return GABP_OK;
     if (ctx->lines_m > 0) return maybe_freeze_lines(ctx, ctx->prec == 0 ? 1e-14 : 1e-6, transposed);
+    if (ctx->parity) return maybe_freeze_parity(ctx, ctx->prec == 0 ? 1e-14 : 1e-6, transposed);
     const double rel = ctx->prec == 0 ? 1e-14 : 1e-6;
     CK(cudaMemsetAsync(&ctx->dstat[2], 0, sizeof(DevStatus), ctx->stream));
     CK(launch_lambda_change(ctx->L.slots, ctx->prec, ctx->Lm[ctx->cur ^ 1], ctx->Lm[ctx->cur],
@@ -357,7 +393,8 @@ gabp_status maybe_freeze(gabp_ctx *ctx, bool transposed)
 
 bool freeze_enabled(const gabp_ctx *ctx)
 {
-    if (ctx->ncolors > 0) return false;  // frozen sweeps: flood and line schedules
+    // frozen sweeps: flood, line and coloured (parity-class layout) schedules
+    if (ctx->ncolors > 0 && !ctx->parity) return false;
     if (ctx->opt.freeze_lambda < 0) return ctx->opt.precision == GABP_FP32_IR;
     return ctx->opt.freeze_lambda > 0;
 }

@@ -446,6 +446,51 @@ def test_colored_solve_matches_oracle(g, name):
     assert it == flood["iters"]
 
 
+@pytest.mark.parametrize("name", ["c1_32", "aniso9_31"])
+def test_colored_frozen_precision_messages(g, name):
+    """Frozen precision messages under the coloured schedule (Sec. 4.2 with
+    Sec. 5.1) on the parity-class layout: once they stop changing, the gains and
+    aggregates are stored and a phase moves only the mean messages.  The FP64
+    solve and the transposed solve reach the oracle's coloured solutions (same
+    sweeps up to one), the context ends frozen (its frozen sweep can be timed),
+    and the mixed-precision solve, which freezes by default, reaches 1e-10 on
+    host-checked residuals."""
+    A = MATS[name]
+    m = int(round(A.n ** 0.5))
+    nc = COLORED[name]
+    colors = oracle.grid_colors(m, nc)
+    b = _rhs(A.n, 39)
+    ref = oracle.solve(A, b, 1e-10, 5000, color=colors, ncolors=nc)
+    assert ref["status"] == oracle.OK
+    s = g.GabpSolver(A, "fp64", check_every=1, freeze_lambda=1)
+    s.set_schedule("colored", colors)
+    assert s.info()["parity_layout"] == 1
+    x, it, rr, st = s.solve(dev(b), 1e-10, 5000)
+    assert st == g.OK and rr <= 1e-10
+    assert abs(it - ref["iters"]) <= 1
+    assert rel(host(x), ref["x"]) <= 1e-9
+    assert s.time_sweeps(dev(b), 3, frozen=True) > 0.0
+    ref_t = oracle.solve(A.transpose(), b, 1e-10, 5000, color=colors, ncolors=nc)
+    lam, it, rr, st = s.solve_transpose(dev(b), 1e-10, 5000)
+    assert st == g.OK and abs(it - ref_t["iters"]) <= 1
+    assert rel(host(lam), ref_t["x"]) <= 1e-9
+    plain = g.GabpSolver(A, "fp64", check_every=1, freeze_lambda=0)
+    plain.set_schedule("colored", colors)
+    plain.solve(dev(b), 1e-10, 5000)
+    with pytest.raises(g.GabpError):
+        plain.time_sweeps(dev(b), 3, frozen=True)
+    sm = g.GabpSolver(A, "fp32_ir", check_every=5)
+    sm.set_schedule("colored", colors)
+    x, it, rr, st = sm.solve(dev(b), 1e-10, 20000)
+    assert st == g.OK and rr <= 1e-10
+    r = b - A.to_dense() @ host(x)
+    assert np.max(np.abs(r)) / np.max(np.abs(b)) <= 1.05e-10
+    assert rel(host(x), np.linalg.solve(A.to_dense(), b)) <= 1e-8
+    assert sm.time_sweeps(dev(b), 3, frozen=True) > 0.0
+    for t in (s, plain, sm):
+        t.close()
+
+
 def test_invalid_coloring_rejected(g):
     A = MATS["c1_32"]
     s = g.GabpSolver(A, "fp64")
