@@ -52,7 +52,7 @@ TRAFFIC_SOURCES = (("paper_1904_04093_gb300/csrc/sweep_row.cuh", None),
                    ("paper_1904_04093_gb300/csrc/kernels.cu", "k_sweep_stencil(\n    int n, StencilParams sp"),
                    ("paper_1904_04093_gb300/csrc/kernels.cu", "cudaError_t sweep_stencil_T(const DevLayout"),
                    ("paper_1904_04093_gb300/csrc/kernels.cu", "cudaError_t launch_sweep(const DevLayout"))
-TRAFFIC_SOURCES_SHA256 = "329a669eeacb05a4204ebc9744f589597a0071112a783fbe66e3585ac6c8bf3c"
+TRAFFIC_SOURCES_SHA256 = "5bf602e6485b7ef22a57a7027efe77ca3de383f3e2f222e4a3b49298d98e62d2"
 # FP64 operations per directed edge of the message update in its stored form (Sec. 2.3 rule):
 # d = P_s - L[rev] (1), 1/d (1), L' = c q (1), B_s - M[rev] (1), M' = a (.) q (2), P' += L',
 # B' += M' (2).  The kernel issues 10 on the FP64 pipe: the reciprocal is the hardware

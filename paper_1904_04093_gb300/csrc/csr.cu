@@ -171,12 +171,12 @@ cudaError_t launch_T(const DevLayout &L, const void *a, const void *c, const voi
 {
     const int grid = (L.n + kCsrBlock - 1) / kCsrBlock;
     if (grid == 0) return cudaSuccess;
-#define GABP_CSR_CASE(E)                                                                        \
-    case E:                                                                                     \
-        launch_pdl(k_sweep_csr<T, E, kFull>, grid, kCsrBlock, 0, s,                                     \
-            L.n, L.rowptr, L.col, L.rev, (const T *)a, (const T *)c, (const T *)diag,           \
-            (const T *)b, (const T *)Lin, (const T *)Min, (const T *)Pin, (const T *)Bin,       \
-            (T *)Lout, (T *)Mout, (T *)Pout, (T *)Bout, x, flags, (int)L.slots);                \
+#define GABP_CSR_CASE(E)                                                                                       \
+    case E:                                                                                                    \
+        launch_pdl(k_sweep_csr<T, E, kFull>, grid, kCsrBlock, 0, s, L.n, L.rowptr, L.col, L.rev, (const T *)a, \
+                   (const T *)c, (const T *)diag, (const T *)b, (const T *)Lin, (const T *)Min,                \
+                   (const T *)Pin, (const T *)Bin, (T *)Lout, (T *)Mout, (T *)Pout, (T *)Bout, x, flags,       \
+                   (int)L.slots);                                                                              \
         break;
     switch (ept_for(L)) {
         GABP_CSR_CASE(1)

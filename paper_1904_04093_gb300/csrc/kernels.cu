@@ -816,10 +816,10 @@ cudaError_t sweep_stencil_T(const DevLayout &L, const SweepArgs &a, int block, c
     const T *Li = (const T *)a.Lin, *Mi = (const T *)a.Min, *Pi = (const T *)a.Pin,
             *Bi = (const T *)a.Bin;
     T *Lo = (T *)a.Lout, *Mo = (T *)a.Mout, *Po = (T *)a.Pout, *Bo = (T *)a.Bout;
-#define GABP_SWEEP_CASE(KK)                                                                 \
-    case KK:                                                                                \
-        launch_pdl(k_sweep_stencil<T, KK>, grid, block, 0, s, L.n, L.sp, A, C, D, Bv, Li, Mi, Pi,  \
-                                                       Bi, Lo, Mo, Po, Bo, a.x, a.flags); \
+#define GABP_SWEEP_CASE(KK)                                                                                   \
+    case KK:                                                                                                  \
+        launch_pdl(k_sweep_stencil<T, KK>, grid, block, 0, s, L.n, L.sp, A, C, D, Bv, Li, Mi, Pi, Bi, Lo, Mo, \
+                   Po, Bo, a.x, a.flags);                                                                     \
         break;
     switch (L.sp.K) {
         GABP_SWEEP_CASE(0)
@@ -858,22 +858,18 @@ cudaError_t launch_aggregate(const DevLayout &L, int prec, const void *diag, con
     const int block = 256, grid = (L.n + block - 1) / block;
     if (L.kind == GABP_LAYOUT_STENCIL) {
         if (prec == 0)
-            launch_pdl(k_aggregate_stencil<double>, grid, block, 0, s,
-                L.n, L.sp.K, (const double *)diag, (const double *)b, (const double *)Lm,
-                (const double *)Mm, (double *)P, (double *)B);
+            launch_pdl(k_aggregate_stencil<double>, grid, block, 0, s, L.n, L.sp.K, (const double *)diag,
+                       (const double *)b, (const double *)Lm, (const double *)Mm, (double *)P, (double *)B);
         else
-            launch_pdl(k_aggregate_stencil<float>, grid, block, 0, s,
-                L.n, L.sp.K, (const float *)diag, (const float *)b, (const float *)Lm,
-                (const float *)Mm, (float *)P, (float *)B);
+            launch_pdl(k_aggregate_stencil<float>, grid, block, 0, s, L.n, L.sp.K, (const float *)diag,
+                       (const float *)b, (const float *)Lm, (const float *)Mm, (float *)P, (float *)B);
     } else {
         if (prec == 0)
-            launch_pdl(k_aggregate_csr<double>, grid, block, 0, s,
-                L.n, L.rowptr, (const double *)diag, (const double *)b, (const double *)Lm,
-                (const double *)Mm, (double *)P, (double *)B);
+            launch_pdl(k_aggregate_csr<double>, grid, block, 0, s, L.n, L.rowptr, (const double *)diag,
+                       (const double *)b, (const double *)Lm, (const double *)Mm, (double *)P, (double *)B);
         else
-            launch_pdl(k_aggregate_csr<float>, grid, block, 0, s,
-                L.n, L.rowptr, (const float *)diag, (const float *)b, (const float *)Lm,
-                (const float *)Mm, (float *)P, (float *)B);
+            launch_pdl(k_aggregate_csr<float>, grid, block, 0, s, L.n, L.rowptr, (const float *)diag,
+                       (const float *)b, (const float *)Lm, (const float *)Mm, (float *)P, (float *)B);
     }
     count_launches(s, 1);
     return cudaGetLastError();
@@ -894,8 +890,8 @@ cudaError_t launch_residual2(const DevLayout &L, const double *a64, const double
     if (rf && L.kind != GABP_LAYOUT_STENCIL) return cudaErrorInvalidValue;
     const int block = 256, grid = grid_for(L.n, block, 152 * 16);
     if (L.kind == GABP_LAYOUT_STENCIL) {
-#define GABP_RES_CASE(KK)                                                                   \
-    case KK:                                                                                \
+#define GABP_RES_CASE(KK)                                                                               \
+    case KK:                                                                                            \
         launch_pdl(k_residual_stencil<KK>, grid, block, 0, s, L.n, L.sp, a64, diag64, b, x, r, rf, st); \
         break;
         switch (L.sp.K) {
@@ -1021,11 +1017,11 @@ cudaError_t launch_get_state(const int64_t *slotmap, int64_t nnz, int prec, cons
 {
     if (nnz == 0) return cudaSuccess;
     if (prec == 0)
-        launch_pdl(k_get_state<double>, grid_for(nnz, 256), 256, 0, s,
-            slotmap, nnz, (const double *)Lm, (const double *)Mm, lam, m);
+        launch_pdl(k_get_state<double>, grid_for(nnz, 256), 256, 0, s, slotmap, nnz, (const double *)Lm,
+                   (const double *)Mm, lam, m);
     else
-        launch_pdl(k_get_state<float>, grid_for(nnz, 256), 256, 0, s,
-            slotmap, nnz, (const float *)Lm, (const float *)Mm, lam, m);
+        launch_pdl(k_get_state<float>, grid_for(nnz, 256), 256, 0, s, slotmap, nnz, (const float *)Lm,
+                   (const float *)Mm, lam, m);
     count_launches(s, 1);
     return cudaGetLastError();
 }
@@ -1035,11 +1031,11 @@ cudaError_t launch_set_state(const int64_t *slotmap, int64_t nnz, int prec, cons
 {
     if (nnz == 0) return cudaSuccess;
     if (prec == 0)
-        launch_pdl(k_set_state<double>, grid_for(nnz, 256), 256, 0, s, slotmap, nnz, lam, m,
-                                                               (double *)Lm, (double *)Mm);
+        launch_pdl(k_set_state<double>, grid_for(nnz, 256), 256, 0, s, slotmap, nnz, lam, m, (double *)Lm,
+                   (double *)Mm);
     else
-        launch_pdl(k_set_state<float>, grid_for(nnz, 256), 256, 0, s, slotmap, nnz, lam, m,
-                                                              (float *)Lm, (float *)Mm);
+        launch_pdl(k_set_state<float>, grid_for(nnz, 256), 256, 0, s, slotmap, nnz, lam, m, (float *)Lm,
+                   (float *)Mm);
     count_launches(s, 1);
     return cudaGetLastError();
 }
@@ -1075,8 +1071,7 @@ cudaError_t launch_dense_gemv(const double *M, const double *x, double *y, int n
 {
     if (n == 0) return cudaSuccess;
     const int rows_per_block = 4;
-    launch_pdl(k_dense_gemv, (n + rows_per_block - 1) / rows_per_block, 32 * rows_per_block, 0, s, M, x,
-                                                                                          y, n);
+    launch_pdl(k_dense_gemv, (n + rows_per_block - 1) / rows_per_block, 32 * rows_per_block, 0, s, M, x, y, n);
     count_launches(s, 1);
     return cudaGetLastError();
 }
@@ -1109,11 +1104,12 @@ cudaError_t launch_coeffs_from_values(const DevLayout &L, int prec, int64_t nnz,
                                       void *c, void *diagT, cudaStream_t s)
 {
     if (L.n == 0) return cudaSuccess;
-    launch_pdl(k_values_scatter, grid_for(std::max<int64_t>(nnz, L.n), 256), 256, 0, s, nnz, L.n, slotmap, diagpos,
-                                                                              data, a64, diag64);
+    launch_pdl(k_values_scatter, grid_for(std::max<int64_t>(nnz, L.n), 256), 256, 0, s, nnz, L.n, slotmap,
+               diagpos, data, a64, diag64);
     const int grid = grid_for(std::max<int64_t>(L.slots, L.n), 256);
     if (prec == 0)
-        launch_pdl(k_coeffs_c<double>, grid, 256, 0, s, L, a64, diag64, (double *)a, (double *)c, (double *)diagT);
+        launch_pdl(k_coeffs_c<double>, grid, 256, 0, s, L, a64, diag64, (double *)a, (double *)c,
+                   (double *)diagT);
     else
         launch_pdl(k_coeffs_c<float>, grid, 256, 0, s, L, a64, diag64, (float *)a, (float *)c, (float *)diagT);
     count_launches(s, 2);
@@ -1128,18 +1124,17 @@ cudaError_t launch_transpose_coeffs(const DevLayout &L, int prec, const void *a,
         const int grid = (L.n + 255) / 256;
         if (prec == 0)
             launch_pdl(k_transpose_stencil<double>, grid, 256, 0, s, L.n, L.sp, (const double *)a,
-                                                              (double *)aT);
+                       (double *)aT);
         else
-            launch_pdl(k_transpose_stencil<float>, grid, 256, 0, s, L.n, L.sp, (const float *)a,
-                                                             (float *)aT);
+            launch_pdl(k_transpose_stencil<float>, grid, 256, 0, s, L.n, L.sp, (const float *)a, (float *)aT);
     } else {
         if (L.slots == 0) return cudaSuccess;
         if (prec == 0)
-            launch_pdl(k_transpose_csr<double>, grid_for(L.slots, 256), 256, 0, s,
-                L.slots, L.rev, (const double *)a, (double *)aT);
+            launch_pdl(k_transpose_csr<double>, grid_for(L.slots, 256), 256, 0, s, L.slots, L.rev,
+                       (const double *)a, (double *)aT);
         else
-            launch_pdl(k_transpose_csr<float>, grid_for(L.slots, 256), 256, 0, s,
-                L.slots, L.rev, (const float *)a, (float *)aT);
+            launch_pdl(k_transpose_csr<float>, grid_for(L.slots, 256), 256, 0, s, L.slots, L.rev,
+                       (const float *)a, (float *)aT);
     }
     count_launches(s, 1);
     return cudaGetLastError();
@@ -1152,18 +1147,14 @@ cudaError_t launch_freeze(const DevLayout &L, int prec, const void *a, const voi
     const int grid = (L.n + 255) / 256;
     count_launches(s, 1);
     if (L.kind == GABP_LAYOUT_STENCIL) {
-#define GABP_FRZ_CASE(KK)                                                                     \
-    case KK:                                                                                  \
-        if (prec == 0)                                                                        \
-            launch_pdl(k_freeze_stencil<double, KK>, grid, 256, 0, s, L.n, L.sp, (const double *)a,    \
-                                                              (const double *)P,              \
-                                                              (const double *)Lm, (double *)g, \
-                                                              flags);                         \
-        else                                                                                  \
-            launch_pdl(k_freeze_stencil<float, KK>, grid, 256, 0, s, L.n, L.sp, (const float *)a,      \
-                                                             (const float *)P,                \
-                                                             (const float *)Lm, (float *)g,   \
-                                                             flags);                          \
+#define GABP_FRZ_CASE(KK)                                                                           \
+    case KK:                                                                                        \
+        if (prec == 0)                                                                              \
+            launch_pdl(k_freeze_stencil<double, KK>, grid, 256, 0, s, L.n, L.sp, (const double *)a, \
+                       (const double *)P, (const double *)Lm, (double *)g, flags);                  \
+        else                                                                                        \
+            launch_pdl(k_freeze_stencil<float, KK>, grid, 256, 0, s, L.n, L.sp, (const float *)a,   \
+                       (const float *)P, (const float *)Lm, (float *)g, flags);                     \
         break;
         switch (L.sp.K) {
             GABP_FRZ_CASE(0)
@@ -1182,12 +1173,10 @@ cudaError_t launch_freeze(const DevLayout &L, int prec, const void *a, const voi
     } else {
         if (prec == 0)
             launch_pdl(k_freeze_csr<double>, grid, 256, 0, s, L.n, L.rowptr, L.col, L.rev, (const double *)a,
-                                                      (const double *)P, (const double *)Lm,
-                                                      (double *)g, flags);
+                       (const double *)P, (const double *)Lm, (double *)g, flags);
         else
             launch_pdl(k_freeze_csr<float>, grid, 256, 0, s, L.n, L.rowptr, L.col, L.rev, (const float *)a,
-                                                     (const float *)P, (const float *)Lm,
-                                                     (float *)g, flags);
+                       (const float *)P, (const float *)Lm, (float *)g, flags);
     }
     return cudaGetLastError();
 }
@@ -1201,16 +1190,16 @@ cudaError_t launch_sweep_mean(const DevLayout &L, int prec, const void *g, const
     if (L.kind == GABP_LAYOUT_STENCIL) {
         if (block > 256) block = 256;
         const int grid = (L.n + block - 1) / block;
-#define GABP_MEAN_CASE(KK)                                                                     \
-    case KK:                                                                                   \
-        if (prec == 0)                                                                         \
-            launch_pdl(k_sweep_mean_stencil<double, KK>, grid, block, 0, s,                            \
-                L.n, L.sp, (const double *)g, (const double *)b, (const double *)P,             \
-                (const double *)Min, (const double *)Bin, (double *)Mout, (double *)Bout, x, flags); \
-        else                                                                                   \
-            launch_pdl(k_sweep_mean_stencil<float, KK>, grid, block, 0, s,                             \
-                L.n, L.sp, (const float *)g, (const float *)b, (const float *)P,                \
-                (const float *)Min, (const float *)Bin, (float *)Mout, (float *)Bout, x, flags);  \
+#define GABP_MEAN_CASE(KK)                                                                                \
+    case KK:                                                                                              \
+        if (prec == 0)                                                                                    \
+            launch_pdl(k_sweep_mean_stencil<double, KK>, grid, block, 0, s, L.n, L.sp, (const double *)g, \
+                       (const double *)b, (const double *)P, (const double *)Min, (const double *)Bin,    \
+                       (double *)Mout, (double *)Bout, x, flags);                                         \
+        else                                                                                              \
+            launch_pdl(k_sweep_mean_stencil<float, KK>, grid, block, 0, s, L.n, L.sp, (const float *)g,   \
+                       (const float *)b, (const float *)P, (const float *)Min, (const float *)Bin,        \
+                       (float *)Mout, (float *)Bout, x, flags);                                           \
         break;
         switch (L.sp.K) {
             GABP_MEAN_CASE(0)
@@ -1254,27 +1243,27 @@ cudaError_t launch_sweep_color(const DevLayout &L, int prec, const unsigned char
     count_launches(s, 1);
     const int grid = (L.n + 255) / 256;
     if (L.kind == GABP_LAYOUT_STENCIL) {
-#define GABP_COL_CASE(KK)                                                                        \
-    case KK:                                                                                     \
-        if (cm) {                                                                                \
-            if (prec == 0)                                                                       \
-                launch_pdl(k_sweep_color_stencil<double, KK>, grid, 256, 0, s,                           \
-                    L.n, L.sp, *cm, color, cphase, (const double *)a, (const double *)c,         \
-                    (double *)Lm, (double *)Mm, (double *)P, (double *)B, x, flags);             \
-            else                                                                                 \
-                launch_pdl(k_sweep_color_stencil<float, KK>, grid, 256, 0, s,                            \
-                    L.n, L.sp, *cm, color, cphase, (const float *)a, (const float *)c,           \
-                    (float *)Lm, (float *)Mm, (float *)P, (float *)B, x, flags);                 \
-        } else {                                                                                 \
-            if (prec == 0)                                                                       \
-                launch_pdl(k_sweep_color_stencil_gather<double, KK>, grid, 256, 0, s,                    \
-                    L.n, L.sp, color, cphase, (const double *)a, (const double *)c,              \
-                    (double *)Lm, (double *)Mm, (double *)P, (double *)B, x, flags);             \
-            else                                                                                 \
-                launch_pdl(k_sweep_color_stencil_gather<float, KK>, grid, 256, 0, s,                     \
-                    L.n, L.sp, color, cphase, (const float *)a, (const float *)c, (float *)Lm,   \
-                    (float *)Mm, (float *)P, (float *)B, x, flags);                              \
-        }                                                                                        \
+#define GABP_COL_CASE(KK)                                                                                      \
+    case KK:                                                                                                   \
+        if (cm) {                                                                                              \
+            if (prec == 0)                                                                                     \
+                launch_pdl(k_sweep_color_stencil<double, KK>, grid, 256, 0, s, L.n, L.sp, *cm, color, cphase,  \
+                           (const double *)a, (const double *)c, (double *)Lm, (double *)Mm, (double *)P,      \
+                           (double *)B, x, flags);                                                             \
+            else                                                                                               \
+                launch_pdl(k_sweep_color_stencil<float, KK>, grid, 256, 0, s, L.n, L.sp, *cm, color, cphase,   \
+                           (const float *)a, (const float *)c, (float *)Lm, (float *)Mm, (float *)P,           \
+                           (float *)B, x, flags);                                                              \
+        } else {                                                                                               \
+            if (prec == 0)                                                                                     \
+                launch_pdl(k_sweep_color_stencil_gather<double, KK>, grid, 256, 0, s, L.n, L.sp, color,        \
+                           cphase, (const double *)a, (const double *)c, (double *)Lm, (double *)Mm,           \
+                           (double *)P, (double *)B, x, flags);                                                \
+            else                                                                                               \
+                launch_pdl(k_sweep_color_stencil_gather<float, KK>, grid, 256, 0, s, L.n, L.sp, color, cphase, \
+                           (const float *)a, (const float *)c, (float *)Lm, (float *)Mm, (float *)P,           \
+                           (float *)B, x, flags);                                                              \
+        }                                                                                                      \
         break;
         switch (L.sp.K) {
             GABP_COL_CASE(0)
@@ -1292,13 +1281,13 @@ cudaError_t launch_sweep_color(const DevLayout &L, int prec, const unsigned char
 #undef GABP_COL_CASE
     } else {
         if (prec == 0)
-            launch_pdl(k_sweep_color_csr<double>, grid, 256, 0, s,
-                L.n, L.rowptr, L.col, L.rev, color, cphase, (const double *)a, (const double *)c,
-                (double *)Lm, (double *)Mm, (double *)P, (double *)B, x, flags);
+            launch_pdl(k_sweep_color_csr<double>, grid, 256, 0, s, L.n, L.rowptr, L.col, L.rev, color, cphase,
+                       (const double *)a, (const double *)c, (double *)Lm, (double *)Mm, (double *)P,
+                       (double *)B, x, flags);
         else
-            launch_pdl(k_sweep_color_csr<float>, grid, 256, 0, s,
-                L.n, L.rowptr, L.col, L.rev, color, cphase, (const float *)a, (const float *)c,
-                (float *)Lm, (float *)Mm, (float *)P, (float *)B, x, flags);
+            launch_pdl(k_sweep_color_csr<float>, grid, 256, 0, s, L.n, L.rowptr, L.col, L.rev, color, cphase,
+                       (const float *)a, (const float *)c, (float *)Lm, (float *)Mm, (float *)P, (float *)B,
+                       x, flags);
     }
     return cudaGetLastError();
 }

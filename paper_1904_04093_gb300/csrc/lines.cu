@@ -974,16 +974,14 @@ cudaError_t launch_T(int m, const void *sub, const void *sup, const void *diag, 
     const int nt = line_threads(prec, m);
     const size_t smem = line_smem_bytes(prec, m);
     if (smem <= kLineSmemMax) {
-        launch_pdl(k_line_scan<T, true, kFreeze>, m, nt, smem, s,
-            m, (const T *)sub, (const T *)sup, (const T *)diag, (const T *)b, (const T *)Loth,
-            (const T *)Moth, (T *)Lown, (T *)Mown, nullptr, nullptr, x, x_transposed, flags,
-            (T *)aF, (T *)aB, (T *)sinv);
+        launch_pdl(k_line_scan<T, true, kFreeze>, m, nt, smem, s, m, (const T *)sub, (const T *)sup,
+                   (const T *)diag, (const T *)b, (const T *)Loth, (const T *)Moth, (T *)Lown, (T *)Mown,
+                   nullptr, nullptr, x, x_transposed, flags, (T *)aF, (T *)aB, (T *)sinv);
     } else {
         if (!f || !y) return cudaErrorInvalidValue;
-        launch_pdl(k_line_scan<T, false, kFreeze>, m, nt, 0, s,
-            m, (const T *)sub, (const T *)sup, (const T *)diag, (const T *)b, (const T *)Loth,
-            (const T *)Moth, (T *)Lown, (T *)Mown, (T *)f, (T *)y, x, x_transposed, flags,
-            (T *)aF, (T *)aB, (T *)sinv);
+        launch_pdl(k_line_scan<T, false, kFreeze>, m, nt, 0, s, m, (const T *)sub, (const T *)sup,
+                   (const T *)diag, (const T *)b, (const T *)Loth, (const T *)Moth, (T *)Lown, (T *)Mown,
+                   (T *)f, (T *)y, x, x_transposed, flags, (T *)aF, (T *)aB, (T *)sinv);
     }
     return cudaGetLastError();
 }
@@ -999,11 +997,10 @@ cudaError_t launch_mean_T(int m, const void *aF, const void *aB, const void *sin
     if ((long long)C * kLineMaxThreads >= m) {
         const int nt = ((m + C - 1) / C + 31) / 32 * 32;
         const int vec = m % (16 / (int)sizeof(T)) == 0;
-#define GABP_MEAN_REG(CC)                                                                       \
-    case CC:                                                                                    \
-        launch_pdl(k_line_mean_reg<T, CC>, m, nt, 0, s, m, (const T *)aF, (const T *)aB,                \
-                                                (const T *)sinv, (const T *)b, (const T *)Moth, \
-                                                (T *)Mown, x, x_transposed, vec);               \
+#define GABP_MEAN_REG(CC)                                                                                 \
+    case CC:                                                                                              \
+        launch_pdl(k_line_mean_reg<T, CC>, m, nt, 0, s, m, (const T *)aF, (const T *)aB, (const T *)sinv, \
+                   (const T *)b, (const T *)Moth, (T *)Mown, x, x_transposed, vec);                       \
         break;
         switch (C) {
             GABP_MEAN_REG(1)
@@ -1022,13 +1019,11 @@ cudaError_t launch_mean_T(int m, const void *aF, const void *aB, const void *sin
     const size_t smem = line_mean_smem_bytes(prec, m);
     if (smem <= kLineSmemMax) {
         launch_pdl(k_line_mean<T, true>, m, nt, smem, s, m, (const T *)aF, (const T *)aB, (const T *)sinv,
-                                                 (const T *)b, (const T *)Moth, (T *)Mown, nullptr,
-                                                 x, x_transposed);
+                   (const T *)b, (const T *)Moth, (T *)Mown, nullptr, x, x_transposed);
     } else {
         if (!y) return cudaErrorInvalidValue;
         launch_pdl(k_line_mean<T, false>, m, nt, 0, s, m, (const T *)aF, (const T *)aB, (const T *)sinv,
-                                               (const T *)b, (const T *)Moth, (T *)Mown, (T *)y, x,
-                                               x_transposed);
+                   (const T *)b, (const T *)Moth, (T *)Mown, (T *)y, x, x_transposed);
     }
     return cudaGetLastError();
 }
@@ -1101,12 +1096,10 @@ cudaError_t launch_line_mean_cols(int prec, int m, const void *aF, const void *a
     const int grid = (m + kColLines - 1) / kColLines;
     if (C == 8)
         launch_pdl(k_line_mean_cols<float, 8>, grid, nt, 0, s, m, (const float *)aF, (const float *)aB,
-                                                       (const float *)sinv, (const float *)b,
-                                                       (const float *)Moth, (float *)Mown, x);
+                   (const float *)sinv, (const float *)b, (const float *)Moth, (float *)Mown, x);
     else
         launch_pdl(k_line_mean_cols<float, 16>, grid, nt, 0, s, m, (const float *)aF, (const float *)aB,
-                                                        (const float *)sinv, (const float *)b,
-                                                        (const float *)Moth, (float *)Mown, x);
+                   (const float *)sinv, (const float *)b, (const float *)Moth, (float *)Mown, x);
     return cudaGetLastError();
 }
 
@@ -1131,13 +1124,11 @@ cudaError_t launch_line_couplings_from_stencil(int prec, int m, const StencilPar
     count_launches(s, 1);
     const int grid = std::min((n + 255) / 256, 152 * 16);
     if (prec == 0)
-        launch_pdl(k_line_couplings_from_stencil<double>, grid, 256, 0, s,
-            n, m, sp, a64, diag64, (double *)subH, (double *)supH, (double *)subV, (double *)supV,
-            (double *)diagV);
+        launch_pdl(k_line_couplings_from_stencil<double>, grid, 256, 0, s, n, m, sp, a64, diag64,
+                   (double *)subH, (double *)supH, (double *)subV, (double *)supV, (double *)diagV);
     else
-        launch_pdl(k_line_couplings_from_stencil<float>, grid, 256, 0, s,
-            n, m, sp, a64, diag64, (float *)subH, (float *)supH, (float *)subV, (float *)supV,
-            (float *)diagV);
+        launch_pdl(k_line_couplings_from_stencil<float>, grid, 256, 0, s, n, m, sp, a64, diag64,
+                   (float *)subH, (float *)supH, (float *)subV, (float *)supV, (float *)diagV);
     return cudaGetLastError();
 }
 
@@ -1150,12 +1141,10 @@ cudaError_t launch_line_couplings_transpose(int prec, int m, const void *sub, co
     const int grid = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
     if (prec == 0)
         launch_pdl(k_line_couplings_transpose<double>, grid, 256, 0, s, m, total, (const double *)sub,
-                                                               (const double *)sup, (double *)subT,
-                                                               (double *)supT);
+                   (const double *)sup, (double *)subT, (double *)supT);
     else
         launch_pdl(k_line_couplings_transpose<float>, grid, 256, 0, s, m, total, (const float *)sub,
-                                                              (const float *)sup, (float *)subT,
-                                                              (float *)supT);
+                   (const float *)sup, (float *)subT, (float *)supT);
     return cudaGetLastError();
 }
 
