@@ -339,6 +339,65 @@ def test_colored_sweeps_match_oracle(g, name, layout):
     assert rel(host(mg_), mm) <= 1e-10
 
 
+def _colored_sweep_reference(A, b, colors, nc, lt, mm):
+    """One coloured sweep composed of flood updates, colour by colour (Sec. 5.1):
+    the nodes of colour c form their beliefs and replace the messages they send
+    from the state left by the colours before them.  Returns the beliefs, the
+    new state (as effects on the rows) and the element-wise scales of each
+    output, taken from the state its phase read."""
+    cols = A.indices.astype(np.int64)
+    sender = colors[cols]
+    lt_c, mm_c = lt.copy(), mm.copy()
+    x_r, sx = np.zeros(A.n), np.zeros(A.n)
+    sl, sm = np.zeros(A.nnz), np.zeros(A.nnz)
+    for c in range(nc):
+        x_c, beta_c = oracle.beliefs(A, b, lt_c, mm_c)
+        lt2, mm2, st = oracle.update(A, b, lt_c, mm_c)
+        assert st == oracle.OK
+        sxc, slc, smc = sweep_scales(A, b, oracle.diag_contrib(A, lt_c), mm_c, x_c, beta_c,
+                                     oracle.diag_contrib(A, lt2), mm2)
+        sel = sender == c
+        lt_c = np.where(sel, lt2, lt_c)
+        mm_c = np.where(sel, mm2, mm_c)
+        sl[sel], sm[sel] = slc[sel], smc[sel]
+        own = colors == c
+        x_r[own], sx[own] = x_c[own], sxc[own]
+    return x_r, oracle.diag_contrib(A, lt_c), mm_c, sx, sl, sm
+
+
+@pytest.mark.parametrize("layout", ["auto", "csr"])
+@pytest.mark.parametrize("name", list(COLORED))
+def test_colored_single_sweep_elementwise(g, name, layout):
+    """One coloured sweep from an injected state, element by element: every
+    belief and message within 1e-12 of the magnitude of the terms its phase
+    computed it from (the composition of flood updates it is checked against
+    equals the oracle's coloured sweep)."""
+    A = MATS[name]
+    m = int(round(A.n ** 0.5))
+    colors = oracle.grid_colors(m, COLORED[name]) if COLORED[name] else _greedy_colors(A)
+    nc = int(colors.max()) + 1
+    b = _rhs(A.n, 43)
+    lt, mm = oracle.zero_state(A)
+    oracle.sweeps(A, _rhs(A.n, 44), 3, lt, mm)
+    edge = (A.data != 0) & (np.repeat(np.arange(A.n), np.diff(A.indptr)) != A.indices)
+    mm = np.where(edge, np.random.default_rng(45).uniform(-1, 1, A.nnz), 0.0)
+    x_r, lc_r, mm_r, sx, sl, sm = _colored_sweep_reference(A, b, colors, nc, lt, mm)
+    lt_o, mm_o = lt.copy(), mm.copy()
+    x_o, _, st = oracle.sweeps_colored(A, b, colors, nc, 1, lt_o, mm_o)
+    assert st == oracle.OK
+    assert rel(x_r, x_o) <= 1e-14 and rel(lc_r, oracle.diag_contrib(A, lt_o)) <= 1e-14
+    assert rel(mm_r, mm_o) <= 1e-14
+    s = g.GabpSolver(A, "fp64", layout=layout)
+    s.set_schedule("colored", None if COLORED[name] is None else colors)
+    s.set_state(dev(oracle.diag_contrib(A, lt)), dev(mm))
+    x = host(s.sweep(dev(b), 1))
+    lam, mg_ = (host(t) for t in s.get_state())
+    assert worst_elementwise(x, x_r, sx) <= 1e-12
+    assert worst_elementwise(lam, lc_r, sl) <= 1e-12
+    assert worst_elementwise(mg_, mm_r, sm) <= 1e-12
+    s.close()
+
+
 @pytest.mark.parametrize("name", ["c1_32", "lognormal_33"])
 def test_colored_three_colours_on_slot_layout(g, name):
     """(x + 2y) mod 3 colours a 5-point grid properly but is no union of parity
