@@ -74,7 +74,7 @@ typedef struct {
     int check_every;     /* sweeps between residual checks in gabp_solve (>= 1) */
     int use_graphs;      /* 1: replay each chunk of sweeps as a captured CUDA graph */
     int ir_inner_max;    /* GABP_FP32_IR: float sweeps per refinement step, at most
-                            (0: 150 under the line schedule, 400 otherwise) */
+                            (0: 150 under the line and coloured schedules, 400 otherwise) */
     double ir_inner_tol; /* GABP_FP32_IR: inner relative residual that ends a refinement step */
     int block_size;      /* threads per block of the sweep kernel (0 = tuned default) */
     int freeze_lambda;   /* precomputed precision messages (Sec. 4.2): 1 on, 0 off,
@@ -87,11 +87,12 @@ typedef struct {
 } gabp_options;
 
 /* Fills `opt` with the defaults: FP64, auto layout, check_every 10, graphs on,
- * ir_inner_max 0 (400, or 150 under the line schedule), ir_inner_tol 1e-3,
- * block_size 0, freeze_lambda -1, reorder -1.  (Short refinement steps win:
- * restarting the float solve on a fresh double residual every few hundred
- * sweeps -- fewer for line GaBP, whose fast initial phase is shorter --
- * reaches 1e-10 in fewer total sweeps than long inner solves.) */
+ * ir_inner_max 0 (400, or 150 under the line and coloured schedules),
+ * ir_inner_tol 1e-3, block_size 0, freeze_lambda -1, reorder -1.  (Short
+ * refinement steps win: restarting the float solve on a fresh double residual
+ * every few hundred sweeps -- fewer for line and coloured GaBP, whose fast
+ * initial phase is shorter -- reaches 1e-10 in fewer total sweeps than long
+ * inner solves.) */
 void gabp_default_options(gabp_options *opt);
 
 /* Text for a status code (static storage). */

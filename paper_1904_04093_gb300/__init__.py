@@ -189,8 +189,8 @@ class GabpSolver:
     * ``check_every``: sweeps between residual checks of a solve;
     * ``use_graphs``: replay each chunk of sweeps from a captured CUDA graph;
     * ``ir_inner_max``, ``ir_inner_tol``: float sweeps per refinement step at
-      most (0: 150 under the line schedule, 400 otherwise), and the inner
-      relative residual that ends a step (``fp32_ir``);
+      most (0: 150 under the line and coloured schedules, 400 otherwise), and
+      the inner relative residual that ends a step (``fp32_ir``);
     * ``block_size``: threads per block of the sweep kernel (0: the default);
     * ``freeze_lambda``: precomputed precision messages (Sec. 4.2): 1 on,
       0 off, -1 on for ``fp32_ir`` and off otherwise;

@@ -464,9 +464,10 @@ gabp_status solve_ir(gabp_ctx *ctx, const double *b, double *x, double tol, int 
     CKS(zero_messages(ctx, true, true));
     const int every = std::max(1, ctx->opt.check_every);
     // float sweeps per refinement step: a restarted solve re-uses GaBP's fast initial
-    // phase, which is shorter for line GaBP (measured on the 2048^2 workload: 400 sweeps
-    // per step for the flood schedule, 150 for lines)
-    const int inner_max = ctx->opt.ir_inner_max > 0 ? ctx->opt.ir_inner_max : (ctx->lines_m > 0 ? 150 : 400);
+    // phase, which is shorter for line and coloured GaBP (measured on the 2048^2
+    // workload: 400 sweeps per step for the flood schedule, 150 for lines and red-black)
+    const int inner_max = ctx->opt.ir_inner_max > 0 ? ctx->opt.ir_inner_max
+                                                    : (ctx->lines_m > 0 || ctx->ncolors > 0 ? 150 : 400);
     const double inner_tol = ctx->opt.ir_inner_tol > 0 ? ctx->opt.ir_inner_tol : 1e-3;
     if (bn == 0.0) st = GABP_OK;
     for (int outer = 0; st == GABP_E_NOT_CONVERGED && outer < 200 && total < max_iter; ++outer) {
