@@ -55,10 +55,12 @@ TRAFFIC_SOURCES = (("paper_1904_04093_gb300/csrc/sweep_row.cuh", None),
 TRAFFIC_SOURCES_SHA256 = "5bf602e6485b7ef22a57a7027efe77ca3de383f3e2f222e4a3b49298d98e62d2"
 # FP64 operations per directed edge of the message update in its stored form (Sec. 2.3 rule):
 # d = P_s - L[rev] (1), 1/d (1), L' = c q (1), B_s - M[rev] (1), M' = a (.) q (2), P' += L',
-# B' += M' (2).  The kernel issues 10 on the FP64 pipe: the reciprocal is the hardware
-# approximation (off the FP64 pipe) plus three FMAs of a Newton-Raphson step.
+# B' += M' (2).  The kernel issues 11 FP64-pipe instructions per edge: 4 adds, 3 multiplies
+# and 3 FMAs (the reciprocal's Newton-Raphson step), as ncu's per-opcode thread-instruction
+# counters give at 1024 x 1024, and the reciprocal's hardware approximation, which ncu's
+# FP64-pipe instruction count shows occupying the same pipe (11.0 per slot).
 FP64_OPS_PER_EDGE = 8
-FP64_ISSUED_PER_EDGE = 10
+FP64_ISSUED_PER_EDGE = 11
 
 
 def parse():
