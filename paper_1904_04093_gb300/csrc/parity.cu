@@ -229,24 +229,34 @@ __device__ constexpr int floor_half(int v) { return v >= 0 ? v / 2 : -((-v + 1) 
 // One node (cx, cy) of the class (PX, PY): the neighbour in direction k lies
 // in the class QT at class row cy + DY2 and column cx + DX2, all known at
 // compile time; only the grid edge is tested at run time.  kMean as in
-// k_sweep_parity.
+// k_sweep_parity.  parity_load issues every load of the node (the belief's P
+// up front as well), parity_store does its arithmetic and writes.
+template <typename T, int K>
+struct ParityNode {
+    T lin[K], min_[K], av[K], cv[K];
+    T B, P;
+    unsigned pos, s;
+    bool valid;
+};
+
 template <typename T, int K, int PX, int PY, bool kMean>
-__device__ __forceinline__ void parity_node(const ParityGrid &g, unsigned cx, unsigned cy,
+__device__ __forceinline__ void parity_load(const ParityGrid &g, unsigned cx, unsigned cy,
                                             const T *__restrict__ a, const T *__restrict__ c,
-                                            const T *__restrict__ diag,
-                                            const T *__restrict__ b, T *Lo, T *Mo,
-                                            double *__restrict__ x, bool &bad, unsigned zl,
-                                            unsigned zm, bool &bad_index)
+                                            const T *__restrict__ diag, const T *__restrict__ b,
+                                            const T *Lo, const T *Mo, bool want_p, unsigned zl, unsigned zm,
+                                            bool &bad_index, ParityNode<T, K> &N)
 {
     constexpr int Q = PX | (PY << 1);
     const unsigned m = (unsigned)g.m, n = m * m;
+    N.valid = cx < (unsigned)g.w[Q] && cy < (unsigned)g.h[Q];
+    if (!N.valid) return;
     const unsigned pos = (unsigned)g.base[Q] + cy * (unsigned)g.w[Q] + cx;
     if (kIndexChecks && pos >= n) {  // nothing of this node is touched
         bad_index = true;
+        N.valid = false;
         return;
     }
     const unsigned sx = 2u * cx + PX, sy = 2u * cy + PY;
-    T lin[K], min_[K], av[K], cv[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) {
         const int dx = std_dx<K>(k), dy = std_dy<K>(k);
@@ -257,39 +267,62 @@ __device__ __forceinline__ void parity_node(const ParityGrid &g, unsigned cx, un
             in ? (unsigned)(K - 1 - k) * n + (unsigned)g.base[qt] +
                      (cy + dy2) * (unsigned)g.w[qt] + (cx + dx2)
                : (unsigned)k * n + pos;  // any valid address
-        if (kIndexChecks && (src >= (unsigned)K * n || pos >= n)) {
+        if (kIndexChecks && src >= (unsigned)K * n) {
             bad_index = true;
             src = 0;
         }
-        if (!kMean) lin[k] = in && !((zl >> qt) & 1u) ? Lo[src] : T(0);
-        min_[k] = in && !((zm >> qt) & 1u) ? Mo[src] : T(0);
-        av[k] = a[(unsigned)k * n + pos];
-        if (!kMean) cv[k] = c[(unsigned)k * n + pos];
+        if (!kMean) N.lin[k] = in && !((zl >> qt) & 1u) ? Lo[src] : T(0);
+        N.min_[k] = in && !((zm >> qt) & 1u) ? Mo[src] : T(0);
+        N.av[k] = a[(unsigned)k * n + pos];
+        if (!kMean) N.cv[k] = c[(unsigned)k * n + pos];
     }
-    const unsigned s = sy * m + sx;
-    T B = b[s];
+    N.pos = pos;
+    N.s = sy * m + sx;
+    N.B = b[N.s];
+    N.P = (!kMean || want_p) ? diag[N.s] : T(1);
+}
+
+template <typename T, int K, bool kMean>
+__device__ __forceinline__ void parity_store(const ParityGrid &g, ParityNode<T, K> &N, T *Lo, T *Mo,
+                                             double *__restrict__ x, bool &bad)
+{
+    if (!N.valid) return;
+    const unsigned n = (unsigned)g.m * (unsigned)g.m;
+    T B = N.B;
 #pragma unroll
-    for (int k = 0; k < K; ++k) B += min_[k];
+    for (int k = 0; k < K; ++k) B += N.min_[k];
     if (kMean) {
-        if (x) x[s] = (double)(B / diag[s]);
+        if (x) x[N.s] = (double)(B / N.P);
 #pragma unroll
         for (int k = 0; k < K; ++k)
-            if (nonzero(av[k])) Mo[(unsigned)k * n + pos] = av[k] * (B - min_[k]);
+            if (nonzero(N.av[k])) Mo[(unsigned)k * n + N.pos] = N.av[k] * (B - N.min_[k]);
         return;
     }
-    T P = diag[s];
+    T P = N.P;
 #pragma unroll
-    for (int k = 0; k < K; ++k) P += lin[k];
-    if (x) x[s] = (double)(B / P);
+    for (int k = 0; k < K; ++k) P += N.lin[k];
+    if (x) x[N.s] = (double)(B / P);
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-        if (!nonzero(av[k])) continue;
-        const T d = P - lin[k];
+        if (!nonzero(N.av[k])) continue;  // no recipient: the slot stays zero
+        const T d = P - N.lin[k];
         bad |= bad_den(d);
         const T qd = fast_rcp(d);
-        Lo[(unsigned)k * n + pos] = cv[k] * qd;
-        Mo[(unsigned)k * n + pos] = av[k] * (B - min_[k]) * qd;
+        Lo[(unsigned)k * n + N.pos] = N.cv[k] * qd;
+        Mo[(unsigned)k * n + N.pos] = N.av[k] * (B - N.min_[k]) * qd;
     }
+}
+
+template <typename T, int K, int PX, int PY, bool kMean>
+__device__ __forceinline__ void parity_node(const ParityGrid &g, unsigned cx, unsigned cy,
+                                            const T *__restrict__ a, const T *__restrict__ c,
+                                            const T *__restrict__ diag, const T *__restrict__ b, T *Lo,
+                                            T *Mo, double *__restrict__ x, bool &bad, unsigned zl,
+                                            unsigned zm, bool &bad_index)
+{
+    ParityNode<T, K> N;
+    parity_load<T, K, PX, PY, kMean>(g, cx, cy, a, c, diag, b, Lo, Mo, x != nullptr, zl, zm, bad_index, N);
+    parity_store<T, K, kMean>(g, N, Lo, Mo, x, bad);
 }
 
 // Standard orders: block (x, y, z) = (class columns, class row, class of the
@@ -309,7 +342,6 @@ __global__ void __launch_bounds__(256) k_sweep_parity_std(ParityGrid g, PhaseCla
     const int z = blockIdx.z;
     const int q = z == 0 ? ph.q[0] : z == 1 ? ph.q[1] : z == 2 ? ph.q[2] : ph.q[3];
     const unsigned cx = blockIdx.x * blockDim.x + threadIdx.x, cy = blockIdx.y;
-    if (cx >= (unsigned)pick4(g.w, q) || cy >= (unsigned)pick4(g.h, q)) return;
     bool bad = false, bad_index = false;
     switch (q) {
         case 0: parity_node<T, K, 0, 0, kMean>(g, cx, cy, a, c, diag, b, Lo, Mo, x, bad, zl, zm, bad_index); break;
