@@ -264,10 +264,10 @@ cudaError_t launch_line_freeze(int prec, int m, const void *sub, const void *sup
 bool line_cols_natural(int prec, int m);
 cudaError_t launch_line_mean_cols(int prec, int m, const void *aF, const void *aB,
                                   const void *sinv, const void *b, const void *Moth, void *Mown,
-                                  double *x, cudaStream_t s);
+                                  double *x, unsigned *flags, cudaStream_t s);
 cudaError_t launch_line_mean(int prec, int m, const void *aF, const void *aB, const void *sinv,
                              const void *b, const void *Moth, void *Mown, void *y, double *x,
-                             int x_transposed, cudaStream_t s);
+                             int x_transposed, unsigned *flags, cudaStream_t s);
 // raises the kernel's dynamic shared-memory limit for lines of length m (once, at setup)
 cudaError_t prepare_line_kernels(int prec, int m);
 cudaError_t launch_transpose(int prec, int m, const void *in, void *out, cudaStream_t s);

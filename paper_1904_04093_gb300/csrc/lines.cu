@@ -238,6 +238,10 @@ __global__ void __launch_bounds__(kLineMaxThreads) k_line_scan(
     __shared__ T stF[kLineMaxWarps][3], stB[kLineMaxWarps][3];
 
     const int line = blockIdx.x, tid = threadIdx.x, NT = blockDim.x;
+    if (kIndexChecks && line >= m) {  // the grid is m lines by construction
+        if (tid == 0) atomicOr(flags, FLAG_INDEX);
+        return;
+    }
     const int lane = tid & 31, w = tid >> 5, NW = NT >> 5;
     const size_t base = (size_t)line * m;
     const T *gd = diag + base, *gLo = Loth + base, *gb = b + base, *gMo = Moth + base;
@@ -478,7 +482,7 @@ template <typename T, bool kSmem>
 __global__ void __launch_bounds__(kLineMaxThreads) k_line_mean(
     int m, const T *__restrict__ aF, const T *__restrict__ aB, const T *__restrict__ sinv,
     const T *__restrict__ b, const T *__restrict__ Moth, T *__restrict__ Mown,
-    T *__restrict__ yws, double *__restrict__ x, int x_transposed)
+    T *__restrict__ yws, double *__restrict__ x, int x_transposed, unsigned *__restrict__ flags)
 {
     pdl_wait();
     pdl_trigger();
@@ -487,6 +491,10 @@ __global__ void __launch_bounds__(kLineMaxThreads) k_line_mean(
         yinB[kLineMaxWarps];
 
     const int line = blockIdx.x, tid = threadIdx.x, NT = blockDim.x;
+    if (kIndexChecks && line >= m) {  // the grid is m lines by construction
+        if (tid == 0) atomicOr(flags, FLAG_INDEX);
+        return;
+    }
     const int lane = tid & 31, w = tid >> 5, NW = NT >> 5;
     const size_t base = (size_t)line * m;
     const T *gb = b + base, *gMo = Moth + base;
@@ -629,13 +637,17 @@ template <typename T, int C>
 __global__ void __launch_bounds__(kLineMaxThreads) k_line_mean_reg(
     int m, const T *__restrict__ aF, const T *__restrict__ aB, const T *__restrict__ sinv,
     const T *__restrict__ b, const T *__restrict__ Moth, T *__restrict__ Mown,
-    double *__restrict__ x, int x_transposed, int vec)
+    double *__restrict__ x, int x_transposed, int vec, unsigned *__restrict__ flags)
 {
     pdl_wait();
     pdl_trigger();
     __shared__ T wF[kLineMaxWarps][2], wB[kLineMaxWarps][2], yinF[kLineMaxWarps],
         yinB[kLineMaxWarps];
     const int line = blockIdx.x, tid = threadIdx.x, NT = blockDim.x;
+    if (kIndexChecks && (line >= m || (long long)NT * C < m)) {  // m lines of at most NT chunks
+        if (tid == 0) atomicOr(flags, FLAG_INDEX);
+        return;
+    }
     const int lane = tid & 31, w = tid >> 5, NW = NT >> 5;
     const size_t base = (size_t)line * m;
     const int lo = tid * C;
@@ -754,7 +766,7 @@ template <typename T, int C>
 __global__ void __launch_bounds__(1024, 1) k_line_mean_cols(
     int m, const T *__restrict__ aF, const T *__restrict__ aB, const T *__restrict__ sinv,
     const T *__restrict__ b, const T *__restrict__ Moth, T *__restrict__ Mown,
-    double *__restrict__ x)
+    double *__restrict__ x, unsigned *__restrict__ flags)
 {
     pdl_wait();
     pdl_trigger();
@@ -763,6 +775,10 @@ __global__ void __launch_bounds__(1024, 1) k_line_mean_cols(
         yinB[32][kColLines];
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, NW = blockDim.x >> 5;
     const int li = lane % kColLines, q = lane / kColLines;
+    if (kIndexChecks && (int)blockIdx.x * kColLines >= m) {  // the grid covers the m columns
+        if (tid == 0) atomicOr(flags, FLAG_INDEX);
+        return;
+    }
     const int xc = blockIdx.x * kColLines + li;
     const int lo = (QW * w + q) * C;
     const int n = xc < m ? max(0, min(C, m - lo)) : 0;
@@ -989,7 +1005,7 @@ cudaError_t launch_T(int m, const void *sub, const void *sup, const void *diag, 
 template <typename T>
 cudaError_t launch_mean_T(int m, const void *aF, const void *aB, const void *sinv, const void *b,
                           const void *Moth, void *Mown, void *y, double *x, int x_transposed,
-                          cudaStream_t s)
+                          unsigned *flags, cudaStream_t s)
 {
     // register form: chunks of a power-of-two length C <= 16 over at most 256 threads
     int C = 1;
@@ -1000,7 +1016,7 @@ cudaError_t launch_mean_T(int m, const void *aF, const void *aB, const void *sin
 #define GABP_MEAN_REG(CC)                                                                                 \
     case CC:                                                                                              \
         launch_pdl(k_line_mean_reg<T, CC>, m, nt, 0, s, m, (const T *)aF, (const T *)aB, (const T *)sinv, \
-                   (const T *)b, (const T *)Moth, (T *)Mown, x, x_transposed, vec);                       \
+                   (const T *)b, (const T *)Moth, (T *)Mown, x, x_transposed, vec, flags);                \
         break;
         switch (C) {
             GABP_MEAN_REG(1)
@@ -1019,11 +1035,11 @@ cudaError_t launch_mean_T(int m, const void *aF, const void *aB, const void *sin
     const size_t smem = line_mean_smem_bytes(prec, m);
     if (smem <= kLineSmemMax) {
         launch_pdl(k_line_mean<T, true>, m, nt, smem, s, m, (const T *)aF, (const T *)aB, (const T *)sinv,
-                   (const T *)b, (const T *)Moth, (T *)Mown, nullptr, x, x_transposed);
+                   (const T *)b, (const T *)Moth, (T *)Mown, nullptr, x, x_transposed, flags);
     } else {
         if (!y) return cudaErrorInvalidValue;
         launch_pdl(k_line_mean<T, false>, m, nt, 0, s, m, (const T *)aF, (const T *)aB, (const T *)sinv,
-                   (const T *)b, (const T *)Moth, (T *)Mown, (T *)y, x, x_transposed);
+                   (const T *)b, (const T *)Moth, (T *)Mown, (T *)y, x, x_transposed, flags);
     }
     return cudaGetLastError();
 }
@@ -1084,7 +1100,7 @@ bool line_cols_natural(int prec, int m) { return prec == 1 && m >= 1 && m <= 128
 
 cudaError_t launch_line_mean_cols(int prec, int m, const void *aF, const void *aB,
                                   const void *sinv, const void *b, const void *Moth, void *Mown,
-                                  double *x, cudaStream_t s)
+                                  double *x, unsigned *flags, cudaStream_t s)
 {
     if (m == 0) return cudaSuccess;
     if (!line_cols_natural(prec, m)) return cudaErrorInvalidValue;
@@ -1096,22 +1112,22 @@ cudaError_t launch_line_mean_cols(int prec, int m, const void *aF, const void *a
     const int grid = (m + kColLines - 1) / kColLines;
     if (C == 8)
         launch_pdl(k_line_mean_cols<float, 8>, grid, nt, 0, s, m, (const float *)aF, (const float *)aB,
-                   (const float *)sinv, (const float *)b, (const float *)Moth, (float *)Mown, x);
+                   (const float *)sinv, (const float *)b, (const float *)Moth, (float *)Mown, x, flags);
     else
         launch_pdl(k_line_mean_cols<float, 16>, grid, nt, 0, s, m, (const float *)aF, (const float *)aB,
-                   (const float *)sinv, (const float *)b, (const float *)Moth, (float *)Mown, x);
+                   (const float *)sinv, (const float *)b, (const float *)Moth, (float *)Mown, x, flags);
     return cudaGetLastError();
 }
 
 cudaError_t launch_line_mean(int prec, int m, const void *aF, const void *aB, const void *sinv,
                              const void *b, const void *Moth, void *Mown, void *y, double *x,
-                             int x_transposed, cudaStream_t s)
+                             int x_transposed, unsigned *flags, cudaStream_t s)
 {
     if (m == 0) return cudaSuccess;
     count_launches(s, 1);
     if (prec == 0)
-        return launch_mean_T<double>(m, aF, aB, sinv, b, Moth, Mown, y, x, x_transposed, s);
-    return launch_mean_T<float>(m, aF, aB, sinv, b, Moth, Mown, y, x, x_transposed, s);
+        return launch_mean_T<double>(m, aF, aB, sinv, b, Moth, Mown, y, x, x_transposed, flags, s);
+    return launch_mean_T<float>(m, aF, aB, sinv, b, Moth, Mown, y, x, x_transposed, flags, s);
 }
 
 cudaError_t launch_line_couplings_from_stencil(int prec, int m, const StencilParams &sp,

@@ -78,21 +78,21 @@ cudaError_t sweep_once(gabp_ctx *ctx, bool transposed, double *x, cudaStream_t s
         const int m = ctx->lines_m, pr = ctx->prec;
         cudaError_t e;
         if ((e = launch_line_mean(pr, m, ctx->laFH, ctx->laBH, ctx->lSH, ctx->bT, ctx->MV, ctx->MH,
-                                  ctx->ly, nullptr, 0, s)) != cudaSuccess)
+                                  ctx->ly, nullptr, 0, &ctx->dstat[0].flags, s)) != cudaSuccess)
             return e;
         return launch_line_mean_cols(pr, m, ctx->laFVn, ctx->laBVn, ctx->lSVn, ctx->bT, ctx->MH,
-                                     ctx->MV, x, s);
+                                     ctx->MV, x, &ctx->dstat[0].flags, s);
     }
     if (ctx->lines_m > 0 && ctx->frozen) {
         // frozen precision messages: the mean messages move, rows then columns
         const int m = ctx->lines_m, pr = ctx->prec;
         cudaError_t e;
         if ((e = launch_line_mean(pr, m, ctx->laFH, ctx->laBH, ctx->lSH, ctx->bT, ctx->MV, ctx->MH,
-                                  ctx->ly, nullptr, 0, s)) != cudaSuccess)
+                                  ctx->ly, nullptr, 0, &ctx->dstat[0].flags, s)) != cudaSuccess)
             return e;
         if ((e = launch_transpose(pr, m, ctx->MH, ctx->MHt, s)) != cudaSuccess) return e;
         if ((e = launch_line_mean(pr, m, ctx->laFV, ctx->laBV, ctx->lSV, ctx->lbT, ctx->MHt,
-                                  ctx->MVt, ctx->ly, x, 1, s)) != cudaSuccess)
+                                  ctx->MVt, ctx->ly, x, 1, &ctx->dstat[0].flags, s)) != cudaSuccess)
             return e;
         return launch_transpose(pr, m, ctx->MVt, ctx->MV, s);
     }

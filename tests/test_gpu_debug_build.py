@@ -2,9 +2,10 @@
 or read and report a failed test through the status word (no trap, no access
 outside an array).  This runs a subset of the GPU parity tests (single sweeps
 and trajectories against the oracle on the stencil, CSR and parity-class
-layouts, fused and separate multigrid cycles, batched solves) in a child
-process on the checked library: every one must pass with no index check
-failing, i.e. the release kernels' indices are in range on those cases."""
+layouts, line GaBP sweeps and solves, fused and separate multigrid cycles,
+batched solves) in a child process on the checked library: every one must
+pass with no index check failing, i.e. the release kernels' indices are in
+range on those cases."""
 import os
 import subprocess
 import sys
@@ -29,11 +30,12 @@ def test_parity_subset_on_bounds_checked_build():
     assert probe.returncode == 0, probe.stderr
     assert probe.stdout.strip().endswith(" 1") and "libgabp_debug.so" in probe.stdout
     sel = ("single_sweep or trajectory or first_update or vcycle or fused or batch_equals "
-           "or colored or residual_2norm")
+           "or colored or residual_2norm or line_sweeps or line_solve_matches or line_frozen_precision "
+           "or line_tiny or natural_columns or line_transposed")
     run = subprocess.run(
         [sys.executable, "-m", "pytest", "-q", "-x", "-m", "gpu", "-k", sel,
          "tests/test_gpu_parity.py", "tests/test_gpu_csr.py", "tests/test_gpu_mg_fused.py",
-         "tests/test_gpu_batch.py"],
+         "tests/test_gpu_batch.py", "tests/test_gpu_lines.py"],
         cwd=ROOT, env=env, capture_output=True, text=True, timeout=1500)
     tail = (run.stdout + run.stderr)[-3000:]
     assert run.returncode == 0, tail
