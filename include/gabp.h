@@ -389,8 +389,9 @@ gabp_status gabp_batch_setup(int nsys, gabp_ctx *const *systems, int check_every
  * `max_iter`, as gabp_batch_solve) and keeps the fastest setting, in three
  * stages.  (1) The launch shape: 256 or 512 threads per CTA x 1, 2, 4, 8 or
  * 16 CTAs per thread-block cluster (16 where the non-portable cluster size
- * fits), as many clusters as can be resident.  (2) At that shape, the rows
- * each thread keeps in flight in the sweeps with frozen precision messages
+ * fits), as many clusters as can be resident.  (2) At the two fastest
+ * shapes (its settings can reorder them), the rows each thread keeps in
+ * flight in the sweeps with frozen precision messages
  * (1, or 2 for 5- and 9-point systems: the edges per thread of one step are
  * rows x diagonals) and, with clusters, the rows per cluster thread from
  * which a system is solved by a whole cluster instead of one CTA (2, 4 or 8).

@@ -237,38 +237,57 @@ gabp_status gabp_batch_tune(gabp_batch *bt, const double *const *b, double *cons
     bt->check_every = bt->check_every0;
     const int blocks[] = {256, 512};
     const int clusters[] = {1, 2, 4, 8, 16};  // 16: non-portable cluster size, where it fits
-    float best = -1.0f, ms = 0.0f;
-    int bb = 0, bc = 0;
+    // the two fastest shapes go on to stage 2: its parameters can reorder them
+    float best = -1.0f, second = -1.0f, ms = 0.0f;
+    int bb = 0, bc = 0, sb = 0, sc = 0;
     for (int blk : blocks)
         for (int cs : clusters) {
             CKS(batch_trial(bt, blk, cs, tol, max_iter, &ms));
-            if (ms >= 0.0f && (best < 0.0f || ms < best)) {
+            if (ms < 0.0f) continue;
+            if (best < 0.0f || ms < best) {
+                second = best;
+                sb = bb;
+                sc = bc;
                 best = ms;
                 bb = blk;
                 bc = cs;
+            } else if (second < 0.0f || ms < second) {
+                second = ms;
+                sb = blk;
+                sc = cs;
             }
         }
     if (best < 0.0f) return fail(GABP_E_CUDA, "no launch shape fits the batched kernel");
     // stage 2: rows in flight per thread (the edges per thread of a mean sweep are
     // rows x diagonals) and, with clusters, the rows per cluster thread from which a
-    // system takes a whole cluster
+    // system takes a whole cluster, on each of the two shapes
     int br = 1, bm = 4;
     const int rows_try[] = {1, 2}, minr_try[] = {2, 4, 8};
-    for (int r : rows_try) {
-        if (!batch_rows_supported(bt->K, r)) continue;
-        for (int mr : minr_try) {
-            if (bc == 1 && mr != 4) continue;  // no cluster teams: the threshold does not matter
-            if (r == 1 && mr == 4) continue;   // stage 1's setting
-            bt->rows = r;
-            bt->min_rows = mr;
-            CKS(batch_trial(bt, bb, bc, tol, max_iter, &ms));
-            if (ms >= 0.0f && ms < best) {
-                best = ms;
-                br = r;
-                bm = mr;
+    const int shapes[2][2] = {{bb, bc}, {sb, sc}};
+    const int nshapes = second < 0.0f ? 1 : 2;
+    int fb = bb, fc = bc;
+    for (int k = 0; k < nshapes; ++k) {
+        const int blk = shapes[k][0], cs = shapes[k][1];
+        for (int r : rows_try) {
+            if (!batch_rows_supported(bt->K, r)) continue;
+            for (int mr : minr_try) {
+                if (cs == 1 && mr != 4) continue;     // no cluster teams: the threshold does not matter
+                if (k == 0 && r == 1 && mr == 4) continue;  // stage 1's setting of the best shape
+                bt->rows = r;
+                bt->min_rows = mr;
+                CKS(batch_trial(bt, blk, cs, tol, max_iter, &ms));
+                if (ms >= 0.0f && ms < best) {
+                    best = ms;
+                    br = r;
+                    bm = mr;
+                    fb = blk;
+                    fc = cs;
+                }
             }
         }
     }
+    bb = fb;
+    bc = fc;
     bt->rows = br;
     bt->min_rows = bm;
     // stage 3 (only for a batch set up with a tuned check interval): residual checks
