@@ -653,8 +653,8 @@ def measure_batch(args):
             "roofline": {"kernel": "k_batch_solve<float,4>", "bound": "hbm",
                          "achieved": sweep_bytes / (ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
                          "frac": sweep_bytes / (ms / 1e3) / 1e9 / peak,
-                         "note": "lower bound on bytes: mean-message sweep bytes per sweep, residual "
-                                 "checks excluded; critical path = the slowest system"}}
+                         "note": "lower bound on bytes: every sweep of every system counted as a "
+                                 "mean-message sweep, residual checks excluded"}}
     return line
 
 
