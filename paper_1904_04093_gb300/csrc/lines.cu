@@ -853,21 +853,22 @@ __global__ void __launch_bounds__(1024, 1) k_line_mean_cols(
         eba = T(1);
         ebb = T(0);
     }
-    T yf[C];
-    T y = efa * yinF[w][li] + efb;
-#pragma unroll
-    for (int j = 0; j < C; ++j) {
-        y = a[j] * y + r[j];
-        yf[j] = y;
-    }
+    // the backward recurrence first, its values in place of the multipliers c
+    // (no longer needed), then the forward one and the outputs
     T yb = eba * yinB[w][li] + ebb;
 #pragma unroll
     for (int j = C - 1; j >= 0; --j) {
         yb = c[j] * yb + r[j];
+        c[j] = yb;
+    }
+    T y = efa * yinF[w][li] + efb;
+#pragma unroll
+    for (int j = 0; j < C; ++j) {
+        y = a[j] * y + r[j];
         if (j < n) {
             const size_t idx = (size_t)(lo + j) * m + xc;
-            Mown[idx] = (yf[j] - r[j]) + (yb - r[j]);
-            if (x) x[idx] = (double)(((yf[j] - r[j]) + yb) * sinv[idx]);
+            Mown[idx] = (y - r[j]) + (c[j] - r[j]);
+            if (x) x[idx] = (double)(((y - r[j]) + c[j]) * sinv[idx]);
         }
     }
 }
