@@ -833,3 +833,32 @@ def test_residual_2norm(g, layout, reorder):
     assert r1["rr_2"] == pytest.approx(ref, rel=1e-12)
     assert r1["rr_inf"] == pytest.approx(np.max(np.abs(b - A.matvec(xh))) / np.max(np.abs(b)), rel=1e-12)
     s.close()
+
+
+@pytest.mark.parametrize("precision,schedule", [("fp64", "flood"), ("fp32_ir", "colored"), ("fp32_ir", "lines")])
+def test_side_stream_matches_default_stream(g, precision, schedule):
+    """The library on a stream of its own (eager sweeps launched with
+    programmatic dependent launch, graph-replayed solve chunks) gives the bits
+    it gives on the default stream."""
+    A = MATS["c1_32"]
+    b = _rhs(A.n, 50)
+    bd = dev(b)
+    torch.cuda.synchronize()
+    ref = g.GabpSolver(A, precision)
+    if schedule != "flood":
+        ref.set_schedule(schedule)
+    x0 = host(ref.sweep(bd, 7))
+    xs0, it0, rr0, st0 = ref.solve(bd, 1e-10, 20000)
+    side = torch.cuda.Stream()
+    s = g.GabpSolver(A, precision, stream=side)
+    if schedule != "flood":
+        s.set_schedule(schedule)
+    with torch.cuda.stream(side):
+        x1 = s.sweep(bd, 7)
+        xs1, it1, rr1, st1 = s.solve(bd, 1e-10, 20000)
+    side.synchronize()
+    assert st0 == st1 == g.OK and it0 == it1
+    assert np.array_equal(host(x1), x0)
+    assert torch.equal(xs1, xs0)
+    ref.close()
+    s.close()
