@@ -391,6 +391,18 @@ gabp_status maybe_freeze(gabp_ctx *ctx, bool transposed)
     return GABP_OK;
 }
 
+#ifndef GABP_FREEZE_PROBE
+#define GABP_FREEZE_PROBE 5
+#endif
+// Sweeps per chunk while the precision messages may still freeze: a freeze is
+// decided at the end of a chunk, so shorter chunks stop the full sweeps sooner
+// after the messages have converged (0: the check interval throughout).
+int chunk_before_freeze(const gabp_ctx *ctx, int every)
+{
+    if (GABP_FREEZE_PROBE <= 0 || ctx->frozen || !freeze_enabled(ctx)) return every;
+    return std::min(every, GABP_FREEZE_PROBE);
+}
+
 bool freeze_enabled(const gabp_ctx *ctx)
 {
     // frozen sweeps: flood, line and coloured (parity-class layout) schedules
@@ -421,7 +433,7 @@ gabp_status solve_plain(gabp_ctx *ctx, const double *b, double *x, double tol, i
     } else {
         const int every = std::max(1, ctx->opt.check_every);
         while (it < max_iter) {
-            const int k = std::min(every, max_iter - it);
+            const int k = std::min(chunk_before_freeze(ctx, every), max_iter - it);
             CKS(run_chunk(ctx, k, transposed));
             it += k;
             const DevStatus h = ctx->hstat[0];
@@ -478,7 +490,7 @@ gabp_status solve_ir(gabp_ctx *ctx, const double *b, double *x, double tol, int 
         CKS(aggregate(ctx));
         int inner = 0;
         while (inner < inner_max && total < max_iter) {
-            const int k = std::min(std::min(every, inner_max - inner), max_iter - total);
+            const int k = std::min(std::min(chunk_before_freeze(ctx, every), inner_max - inner), max_iter - total);
             CKS(run_chunk(ctx, k, transposed));
             inner += k;
             total += k;
