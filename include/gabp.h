@@ -217,7 +217,8 @@ gabp_status gabp_sweep(gabp_ctx *ctx, const double *b, int nsweeps, double *x);
  * refinement steps since they do not depend on the right-hand side, Sec.
  * 2.3) and `max_iter` caps the total float sweeps.  With freeze_lambda the
  * precision messages are frozen once a sweep changes none of them by more
- * than rounding (1e-14 relative in double, 1e-6 in float): they do not depend
+ * than rounding (1e-14 relative in double, 1e-6 in float; until then a solve
+ * checks every min(check_every, 5) sweeps): they do not depend
  * on b (Sec. 2.3) and the paper precomputes them (Sec. 4.2); from then on a
  * sweep moves only the mean messages with the fixed gains a_e / d_e, which is
  * the same update up to rounding.  x (device, n doubles)
