@@ -566,7 +566,8 @@ __global__ void __launch_bounds__(kLineMaxThreads) k_line_mean(
             yinF[v] = y;
             y = wF[v][0] * y + wF[v][1];
         }
-        y = T(0);
+    } else if (tid == (NW > 1 ? 32 : 1)) {  // the backward scan on warp 1 when there is one
+        T y = T(0);
         for (int v = NW - 1; v >= 0; --v) {
             yinB[v] = y;
             y = wB[v][0] * y + wB[v][1];
@@ -701,7 +702,8 @@ __global__ void __launch_bounds__(kLineMaxThreads) k_line_mean_reg(
             yinF[v] = y;
             y = wF[v][0] * y + wF[v][1];
         }
-        y = T(0);
+    } else if (tid == (NW > 1 ? 32 : 1)) {  // the backward scan on warp 1 when there is one
+        T y = T(0);
         for (int v = NW - 1; v >= 0; --v) {
             yinB[v] = y;
             y = wB[v][0] * y + wB[v][1];
@@ -759,10 +761,14 @@ __global__ void __launch_bounds__(kLineMaxThreads) k_line_mean_reg(
 // l / kColLines of C consecutive rows y (node y m + x).  A warp instruction
 // then touches row segments of kColLines adjacent columns.  The chunk maps of
 // a line are scanned across its lanes (shuffles by multiples of kColLines),
-// then across the warps (one thread per line and direction).  Float
-// messages, lines of at most 128 C rows.
+// then across the warps (one thread per line and direction, the two
+// directions on two warps).  Float messages, lines of at most 128 C rows.
+// kFull: every chunk of the grid is a whole chunk inside the matrix (m a
+// multiple of 32 / kColLines chunks of C), so the loads and stores go
+// unguarded; the guarded form of the same kernel measured 25.6 against
+// 18.5 us at 2048 x 2048.
 constexpr int kColLines = 8;  // 8 adjacent columns: 32-byte row segments (4 lines measured slower)
-template <typename T, int C>
+template <typename T, int C, bool kFull>
 __global__ void __launch_bounds__(1024, 1) k_line_mean_cols(
     int m, const T *__restrict__ aF, const T *__restrict__ aB, const T *__restrict__ sinv,
     const T *__restrict__ b, const T *__restrict__ Moth, T *__restrict__ Mown,
@@ -785,7 +791,7 @@ __global__ void __launch_bounds__(1024, 1) k_line_mean_cols(
     T r[C], a[C], c[C];
 #pragma unroll
     for (int j = 0; j < C; ++j) {
-        if (j < n) {
+        if (kFull || j < n) {
             const size_t idx = (size_t)(lo + j) * m + xc;
             r[j] = b[idx] + Moth[idx];
             a[j] = aF[idx];
@@ -828,14 +834,15 @@ __global__ void __launch_bounds__(1024, 1) k_line_mean_cols(
         wB[w][li][1] = bb;
     }
     __syncthreads();
+    const int bw = NW > 1 ? 32 : kColLines;  // the backward scan's first thread: warp 1 when there is one
     if (tid < kColLines) {
         T y = T(0);
         for (int v = 0; v < NW; ++v) {
             yinF[v][tid] = y;
             y = wF[v][tid][0] * y + wF[v][tid][1];
         }
-    } else if (tid < 2 * kColLines) {
-        const int l2 = tid - kColLines;
+    } else if (tid >= bw && tid < bw + kColLines) {
+        const int l2 = tid - bw;
         T y = T(0);
         for (int v = NW - 1; v >= 0; --v) {
             yinB[v][l2] = y;
@@ -865,7 +872,7 @@ __global__ void __launch_bounds__(1024, 1) k_line_mean_cols(
 #pragma unroll
     for (int j = 0; j < C; ++j) {
         y = a[j] * y + r[j];
-        if (j < n) {
+        if (kFull || j < n) {
             const size_t idx = (size_t)(lo + j) * m + xc;
             Mown[idx] = (y - r[j]) + (c[j] - r[j]);
             if (x) x[idx] = (double)(((y - r[j]) + c[j]) * sinv[idx]);
@@ -1111,12 +1118,19 @@ cudaError_t launch_line_mean_cols(int prec, int m, const void *aF, const void *a
     const int qw = 32 / kColLines;                 // chunks of each line per warp
     const int nt = ((nch + qw - 1) / qw) * 32;
     const int grid = (m + kColLines - 1) / kColLines;
-    if (C == 8)
-        launch_pdl(k_line_mean_cols<float, 8>, grid, nt, 0, s, m, (const float *)aF, (const float *)aB,
-                   (const float *)sinv, (const float *)b, (const float *)Moth, (float *)Mown, x, flags);
-    else
-        launch_pdl(k_line_mean_cols<float, 16>, grid, nt, 0, s, m, (const float *)aF, (const float *)aB,
-                   (const float *)sinv, (const float *)b, (const float *)Moth, (float *)Mown, x, flags);
+    // every thread's chunk whole and inside the matrix (the grid's columns too: C qw is a multiple of kColLines)
+    const bool full = m % (C * qw) == 0;
+#define GABP_MEAN_COLS(CC, FULL)                                                                         \
+    launch_pdl(k_line_mean_cols<float, CC, FULL>, grid, nt, 0, s, m, (const float *)aF, (const float *)aB, \
+               (const float *)sinv, (const float *)b, (const float *)Moth, (float *)Mown, x, flags)
+    if (C == 8) {
+        if (full) GABP_MEAN_COLS(8, true);
+        else GABP_MEAN_COLS(8, false);
+    } else {
+        if (full) GABP_MEAN_COLS(16, true);
+        else GABP_MEAN_COLS(16, false);
+    }
+#undef GABP_MEAN_COLS
     return cudaGetLastError();
 }
 

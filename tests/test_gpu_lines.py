@@ -287,15 +287,16 @@ def test_line_tiny_grids(g, m, precision):
     assert rel(host(xs), np.linalg.solve(A.to_dense(), b)) <= 1e-9
 
 
-@pytest.mark.parametrize("m", [45, 300, 777, 1100, 2601, 4096])
+@pytest.mark.parametrize("m", [20, 32, 45, 64, 300, 777, 1024, 1100, 2048, 2601, 4096])
 def test_line_frozen_float_natural_columns_against_oracle(g, m):
     """Float frozen sweeps: up to 2048 nodes per line the column family is read
     and written in the natural node order (one CTA per 8 adjacent columns, a
-    ragged last group at 45, 777, 1100), beyond that through transposes (2601,
-    4096).  After the precision messages froze, one frozen sweep agrees on
-    sampled lines with the oracle's full update of those regions from the same
-    state (Algorithm 2; float rounding and the freeze threshold bound the
-    difference), beliefs included."""
+    ragged last group at 20, 45, 777, 1100; every chunk whole, the unguarded
+    form, at 32, 64, 1024, 2048; one warp per CTA at 20 and 32), beyond that
+    through transposes (2601, 4096).  After the precision messages froze, one
+    frozen sweep agrees on sampled lines with the oracle's full update of those
+    regions from the same state (Algorithm 2; float rounding and the freeze
+    threshold bound the difference), beliefs included."""
     A, b = P.config_c2(m=m, seed=m)
     s = g.GabpSolver(A, "fp32", check_every=5, freeze_lambda=1)
     s.set_schedule("lines")
