@@ -830,14 +830,17 @@ def measure_schedules(args):
                     r["frozen_sweep_GBps"] = inf["colored_mean_sweep_bytes"] / (fz / 1e3) / 1e9
             out[f"{schedule}_{name}"] = r
             s.close()
-    head = out.get("colored_fp64") or next(iter(out.values()))
+    head_key = "colored_fp64" if "colored_fp64" in out else next(iter(out))
+    head = out[head_key]
+    label = {"colored": "red-black", "lines": "line", "flood": "flood"}[head_key.split("_")[0]]
     cf = out.get("colored_fp32_ir")
-    line = {"metric": "red-black GaBP time to rr <= 1e-10", "value": head["ms"], "unit": "ms",
+    line = {"metric": f"{label} GaBP time to rr <= 1e-10 ({head_key})", "value": head["ms"], "unit": "ms",
             "higher_is_better": False, "steps": args.steps, "dtype": "f64 (and f32 + f64 refinement)",
             "data": "synthetic",
             "config": {"workload": f"convdiff2d_5pt_upwind_lognormal_{args.m}x{args.m}",
                        "schedules": "colored = red-black on the parity-class layout; "
-                                    "lines = rows then columns, one CTA per line (block scan)"},
+                                    "lines = rows then columns, one CTA per line (block scan; "
+                                    "frozen float columns: one CTA per 8 columns)"},
             "solves": out}
     if cf:
         line["roofline"] = {"kernel": "k_sweep_parity_std<float,4> (red-black, full sweeps of the mixed solver)",
