@@ -188,7 +188,12 @@ gabp_status gabp_set_schedule(gabp_ctx *ctx, int schedule, const int32_t *color,
 /*
  * Line schedule: copies the node messages out (device arrays of n doubles,
  * natural node order): LH/MH = (Lambda, m) from each node's row region,
- * LV/MV from its column region.  Any pointer may be NULL.
+ * LV/MV from its column region.  Any pointer may be NULL.  Float lines of at
+ * most 2048 nodes with frozen precision messages hand the row messages to the
+ * column phase as b + m; a sweep that writes beliefs (every solve chunk,
+ * gabp_sweep, a multigrid smoother) stores m again.  After sweeps that wrote
+ * none (gabp_time_sweeps), MH is (b + m) - b with the context's current
+ * right-hand side, so read it before loading another one.
  */
 gabp_status gabp_get_line_state(gabp_ctx *ctx, double *LH, double *MH, double *LV, double *MV);
 

@@ -603,7 +603,10 @@ gabp_status gabp_get_line_state(gabp_ctx *ctx, double *LH, double *MH, double *L
     CKS(set_dev(ctx->dev));
     const int64_t n = ctx->n;
     if (LH) CK(launch_to_double(ctx->prec, ctx->LH, LH, n, ctx->stream));
-    if (MH) CK(launch_to_double(ctx->prec, ctx->MH, MH, n, ctx->stream));
+    if (MH && ctx->mh_sum)  // folded by the last sweep: b + m' back to m' with the current b
+        CK(launch_line_unfold(n, ctx->MH, ctx->bT, MH, ctx->stream));
+    else if (MH)
+        CK(launch_to_double(ctx->prec, ctx->MH, MH, n, ctx->stream));
     if (LV) CK(launch_to_double(ctx->prec, ctx->LV, LV, n, ctx->stream));
     if (MV) CK(launch_to_double(ctx->prec, ctx->MV, MV, n, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));

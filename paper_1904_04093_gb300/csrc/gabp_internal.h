@@ -259,15 +259,19 @@ cudaError_t launch_line_freeze(int prec, int m, const void *sub, const void *sup
                                const void *diag, const void *Loth, void *f, void *y, void *aF,
                                void *aB, void *sinv, unsigned *flags, cudaStream_t s);
 // the frozen column phase on the natural node order (no transposes): float
-// messages and m <= 2048 only (line_cols_natural); aF, aB, sinv, b, Moth, Mown
-// and x in natural order
+// messages and m <= 2048 only (line_cols_natural); aF, aB, sinv, b, S, Mown
+// and x in natural order; S = b + m'_row as the row phase left it (sum_out),
+// replaced by the row messages S - b when x is written
 bool line_cols_natural(int prec, int m);
 cudaError_t launch_line_mean_cols(int prec, int m, const void *aF, const void *aB,
-                                  const void *sinv, const void *b, const void *Moth, void *Mown,
+                                  const void *sinv, const void *b, void *S, void *Mown,
                                   double *x, unsigned *flags, cudaStream_t s);
+// sum_out (float, lines of at most 4096): Mown = b + m' for the natural-order column phase
 cudaError_t launch_line_mean(int prec, int m, const void *aF, const void *aB, const void *sinv,
                              const void *b, const void *Moth, void *Mown, void *y, double *x,
-                             int x_transposed, unsigned *flags, cudaStream_t s);
+                             int x_transposed, int sum_out, unsigned *flags, cudaStream_t s);
+// out = S - b in double: the row messages back from their folded form
+cudaError_t launch_line_unfold(int64_t n, const void *S, const void *b, double *out, cudaStream_t s);
 // raises the kernel's dynamic shared-memory limit for lines of length m (once, at setup)
 cudaError_t prepare_line_kernels(int prec, int m);
 cudaError_t launch_transpose(int prec, int m, const void *in, void *out, cudaStream_t s);

@@ -131,6 +131,9 @@ struct gabp_ctx {
     unsigned zero_pending = 0;
     bool frozen = false;         // precision messages frozen (both L and P buffers equal)
     bool frozen_transposed = false;
+    // the row mean messages MH hold b + m' (the last sweep was a frozen
+    // natural-order float sweep that wrote no beliefs)
+    bool mh_sum = false;
     DevStatus *dstat = nullptr;  // [0] chunk checks, [1] refinement / misc, [2] Lambda change
     DevStatus *hstat = nullptr;  // pinned host mirror
     std::vector<GraphEntry> graphs;

@@ -634,7 +634,9 @@ __device__ __forceinline__ void load_chunk(T (&v)[C], const T *__restrict__ p, i
 // registers (no shared-memory staging): the loads are issued up front as
 // vectors, the chunk maps, the block scan and the recurrences then run on
 // registers.  Used when the line splits into at most 256 chunks of C <= 16.
-template <typename T, int C>
+// kSumOut: Mown receives b + m' (the sum the column phase on the natural
+// order starts from) instead of m'.
+template <typename T, int C, bool kSumOut = false>
 __global__ void __launch_bounds__(kLineMaxThreads) k_line_mean_reg(
     int m, const T *__restrict__ aF, const T *__restrict__ aB, const T *__restrict__ sinv,
     const T *__restrict__ b, const T *__restrict__ Moth, T *__restrict__ Mown,
@@ -661,7 +663,11 @@ __global__ void __launch_bounds__(kLineMaxThreads) k_line_mean_reg(
     load_chunk<T, C>(a, aF + p0, n, vec != 0, T(1));
     load_chunk<T, C>(c, aB + p0, n, vec != 0, T(1));
 #pragma unroll
-    for (int j = 0; j < C; ++j) r[j] += mo[j];
+    for (int j = 0; j < C; ++j) {
+        const T bj = r[j];
+        r[j] += mo[j];
+        if (kSumOut) mo[j] = bj;  // b kept for the output sum
+    }
 
     T fa = T(1), fb = T(0), ba = T(1), bb = T(0);
 #pragma unroll
@@ -737,6 +743,10 @@ __global__ void __launch_bounds__(kLineMaxThreads) k_line_mean_reg(
             x[x_transposed ? (size_t)(lo + j) * m + line : base + lo + j] =
                 (double)(((yf[j] - r[j]) + yb) * sinv[base + lo + j]);
     }
+    if (kSumOut) {
+#pragma unroll
+        for (int j = 0; j < C; ++j) mu[j] = mo[j] + mu[j];  // the same rounding as the reader's b + m'
+    }
     constexpr int V = 16 / sizeof(T);
     if (C % V == 0 && vec && n == C) {
 #pragma unroll
@@ -763,16 +773,21 @@ __global__ void __launch_bounds__(kLineMaxThreads) k_line_mean_reg(
 // a line are scanned across its lanes (shuffles by multiples of kColLines),
 // then across the warps (one thread per line and direction, the two
 // directions on two warps).  Float messages, lines of at most 128 C rows.
+// The row family's messages arrive folded into the right-hand side, S = b +
+// m'_row (written so by the row phase), which is the r the recurrences start
+// from: one array fewer to read.  A sweep that writes the beliefs x also reads
+// b and leaves the row messages themselves, S - b, in S's place (kX: the
+// form of the sweeps that write x).
 // kFull: every chunk of the grid is a whole chunk inside the matrix (m a
 // multiple of 32 / kColLines chunks of C), so the loads and stores go
 // unguarded; the guarded form of the same kernel measured 25.6 against
 // 18.5 us at 2048 x 2048.
 constexpr int kColLines = 8;  // 8 adjacent columns: 32-byte row segments (4 lines measured slower)
-template <typename T, int C, bool kFull>
+template <typename T, int C, bool kFull, bool kX>
 __global__ void __launch_bounds__(1024, 1) k_line_mean_cols(
     int m, const T *__restrict__ aF, const T *__restrict__ aB, const T *__restrict__ sinv,
-    const T *__restrict__ b, const T *__restrict__ Moth, T *__restrict__ Mown,
-    double *__restrict__ x, unsigned *__restrict__ flags)
+    const T *__restrict__ b, T *S, T *__restrict__ Mown, double *__restrict__ x,
+    unsigned *__restrict__ flags)
 {
     pdl_wait();
     pdl_trigger();
@@ -793,7 +808,7 @@ __global__ void __launch_bounds__(1024, 1) k_line_mean_cols(
     for (int j = 0; j < C; ++j) {
         if (kFull || j < n) {
             const size_t idx = (size_t)(lo + j) * m + xc;
-            r[j] = b[idx] + Moth[idx];
+            r[j] = S[idx];
             a[j] = aF[idx];
             c[j] = aB[idx];
         } else {  // identity steps
@@ -875,7 +890,10 @@ __global__ void __launch_bounds__(1024, 1) k_line_mean_cols(
         if (kFull || j < n) {
             const size_t idx = (size_t)(lo + j) * m + xc;
             Mown[idx] = (y - r[j]) + (c[j] - r[j]);
-            if (x) x[idx] = (double)(((y - r[j]) + c[j]) * sinv[idx]);
+            if (kX) {
+                x[idx] = (double)(((y - r[j]) + c[j]) * sinv[idx]);
+                S[idx] = r[j] - b[idx];  // read by this thread only, above
+            }
         }
     }
 }
@@ -1010,21 +1028,38 @@ cudaError_t launch_T(int m, const void *sub, const void *sup, const void *diag, 
     return cudaGetLastError();
 }
 
+// The register form, with the folded output (float only) when sum_out.
+template <typename T, int CC>
+void launch_mean_reg(bool sum_out, int m, int nt, const void *aF, const void *aB, const void *sinv,
+                     const void *b, const void *Moth, void *Mown, double *x, int x_transposed, int vec,
+                     unsigned *flags, cudaStream_t s)
+{
+    if constexpr (sizeof(T) == 4) {
+        if (sum_out) {
+            launch_pdl(k_line_mean_reg<T, CC, true>, m, nt, 0, s, m, (const T *)aF, (const T *)aB,
+                       (const T *)sinv, (const T *)b, (const T *)Moth, (T *)Mown, x, x_transposed, vec, flags);
+            return;
+        }
+    }
+    launch_pdl(k_line_mean_reg<T, CC, false>, m, nt, 0, s, m, (const T *)aF, (const T *)aB, (const T *)sinv,
+               (const T *)b, (const T *)Moth, (T *)Mown, x, x_transposed, vec, flags);
+}
+
 template <typename T>
 cudaError_t launch_mean_T(int m, const void *aF, const void *aB, const void *sinv, const void *b,
                           const void *Moth, void *Mown, void *y, double *x, int x_transposed,
-                          unsigned *flags, cudaStream_t s)
+                          bool sum_out, unsigned *flags, cudaStream_t s)
 {
+    if (sum_out && sizeof(T) != 4) return cudaErrorInvalidValue;
     // register form: chunks of a power-of-two length C <= 16 over at most 256 threads
     int C = 1;
     while (C < 16 && (long long)C * kLineMaxThreads < m) C *= 2;
     if ((long long)C * kLineMaxThreads >= m) {
         const int nt = ((m + C - 1) / C + 31) / 32 * 32;
         const int vec = m % (16 / (int)sizeof(T)) == 0;
-#define GABP_MEAN_REG(CC)                                                                                 \
-    case CC:                                                                                              \
-        launch_pdl(k_line_mean_reg<T, CC>, m, nt, 0, s, m, (const T *)aF, (const T *)aB, (const T *)sinv, \
-                   (const T *)b, (const T *)Moth, (T *)Mown, x, x_transposed, vec, flags);                \
+#define GABP_MEAN_REG(CC)                                                                                   \
+    case CC:                                                                                                \
+        launch_mean_reg<T, CC>(sum_out, m, nt, aF, aB, sinv, b, Moth, Mown, x, x_transposed, vec, flags, s); \
         break;
         switch (C) {
             GABP_MEAN_REG(1)
@@ -1038,6 +1073,7 @@ cudaError_t launch_mean_T(int m, const void *aF, const void *aB, const void *sin
 #undef GABP_MEAN_REG
         return cudaGetLastError();
     }
+    if (sum_out) return cudaErrorInvalidValue;  // the folded output has the register form only
     const int prec = sizeof(T) == 8 ? 0 : 1;
     const int nt = line_threads(1, m);  // little arithmetic per element: the wider split
     const size_t smem = line_mean_smem_bytes(prec, m);
@@ -1107,7 +1143,7 @@ cudaError_t launch_line_freeze(int prec, int m, const void *sub, const void *sup
 bool line_cols_natural(int prec, int m) { return prec == 1 && m >= 1 && m <= 128 * 16; }
 
 cudaError_t launch_line_mean_cols(int prec, int m, const void *aF, const void *aB,
-                                  const void *sinv, const void *b, const void *Moth, void *Mown,
+                                  const void *sinv, const void *b, void *S, void *Mown,
                                   double *x, unsigned *flags, cudaStream_t s)
 {
     if (m == 0) return cudaSuccess;
@@ -1120,9 +1156,15 @@ cudaError_t launch_line_mean_cols(int prec, int m, const void *aF, const void *a
     const int grid = (m + kColLines - 1) / kColLines;
     // every thread's chunk whole and inside the matrix (the grid's columns too: C qw is a multiple of kColLines)
     const bool full = m % (C * qw) == 0;
-#define GABP_MEAN_COLS(CC, FULL)                                                                         \
-    launch_pdl(k_line_mean_cols<float, CC, FULL>, grid, nt, 0, s, m, (const float *)aF, (const float *)aB, \
-               (const float *)sinv, (const float *)b, (const float *)Moth, (float *)Mown, x, flags)
+#define GABP_MEAN_COLS(CC, FULL)                                                                           \
+    if (x)                                                                                                 \
+        launch_pdl(k_line_mean_cols<float, CC, FULL, true>, grid, nt, 0, s, m, (const float *)aF,            \
+                   (const float *)aB, (const float *)sinv, (const float *)b, (float *)S, (float *)Mown, x, \
+                   flags);                                                                                 \
+    else                                                                                                   \
+        launch_pdl(k_line_mean_cols<float, CC, FULL, false>, grid, nt, 0, s, m, (const float *)aF,           \
+                   (const float *)aB, (const float *)sinv, (const float *)b, (float *)S, (float *)Mown, x, \
+                   flags)
     if (C == 8) {
         if (full) GABP_MEAN_COLS(8, true);
         else GABP_MEAN_COLS(8, false);
@@ -1136,13 +1178,33 @@ cudaError_t launch_line_mean_cols(int prec, int m, const void *aF, const void *a
 
 cudaError_t launch_line_mean(int prec, int m, const void *aF, const void *aB, const void *sinv,
                              const void *b, const void *Moth, void *Mown, void *y, double *x,
-                             int x_transposed, unsigned *flags, cudaStream_t s)
+                             int x_transposed, int sum_out, unsigned *flags, cudaStream_t s)
 {
     if (m == 0) return cudaSuccess;
     count_launches(s, 1);
     if (prec == 0)
-        return launch_mean_T<double>(m, aF, aB, sinv, b, Moth, Mown, y, x, x_transposed, flags, s);
-    return launch_mean_T<float>(m, aF, aB, sinv, b, Moth, Mown, y, x, x_transposed, flags, s);
+        return launch_mean_T<double>(m, aF, aB, sinv, b, Moth, Mown, y, x, x_transposed, sum_out != 0,
+                                     flags, s);
+    return launch_mean_T<float>(m, aF, aB, sinv, b, Moth, Mown, y, x, x_transposed, sum_out != 0, flags, s);
+}
+
+// out_i = S_i - b_i in double (exact for two floats of nearby magnitude)
+__global__ void k_line_unfold(int64_t n, const float *__restrict__ S, const float *__restrict__ b,
+                              double *__restrict__ out)
+{
+    pdl_wait();
+    pdl_trigger();
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = (double)S[i] - (double)b[i];
+}
+
+cudaError_t launch_line_unfold(int64_t n, const void *S, const void *b, double *out, cudaStream_t s)
+{
+    if (n == 0) return cudaSuccess;
+    count_launches(s, 1);
+    const int grid = (int)std::min<int64_t>((n + 255) / 256, 152 * 16);
+    launch_pdl(k_line_unfold, grid, 256, 0, s, n, (const float *)S, (const float *)b, out);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_line_couplings_from_stencil(int prec, int m, const StencilParams &sp,

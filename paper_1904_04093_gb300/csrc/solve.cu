@@ -23,6 +23,7 @@ gabp_status zero_messages(gabp_ctx *ctx, bool lam, bool mean)
         if (lam) CK(cudaMemsetAsync(ctx->LV, 0, nb, ctx->stream));
         if (mean) CK(cudaMemsetAsync(ctx->MH, 0, nb, ctx->stream));
         if (mean) CK(cudaMemsetAsync(ctx->MV, 0, nb, ctx->stream));
+        if (mean) ctx->mh_sum = false;
     }
     if (lam) CK(cudaMemsetAsync(ctx->Lm[ctx->cur], 0, bytes, ctx->stream));
     if (mean) CK(cudaMemsetAsync(ctx->Mm[ctx->cur], 0, bytes, ctx->stream));
@@ -74,12 +75,14 @@ cudaError_t sweep_once(gabp_ctx *ctx, bool transposed, double *x, cudaStream_t s
     void *lsH = transposed ? ctx->lsubHT : ctx->lsubH, *luH = transposed ? ctx->lsupHT : ctx->lsupH;
     void *lsV = transposed ? ctx->lsubVT : ctx->lsubV, *luV = transposed ? ctx->lsupVT : ctx->lsupV;
     if (ctx->lines_m > 0 && ctx->frozen && line_cols_natural(ctx->prec, ctx->lines_m)) {
-        // frozen precision messages, both families in the natural order: no transposes
+        // frozen precision messages, both families in the natural order: no transposes; the
+        // row phase hands b + m'_row to the column phase, which restores m'_row when it writes x
         const int m = ctx->lines_m, pr = ctx->prec;
         cudaError_t e;
         if ((e = launch_line_mean(pr, m, ctx->laFH, ctx->laBH, ctx->lSH, ctx->bT, ctx->MV, ctx->MH,
-                                  ctx->ly, nullptr, 0, &ctx->dstat[0].flags, s)) != cudaSuccess)
+                                  ctx->ly, nullptr, 0, 1, &ctx->dstat[0].flags, s)) != cudaSuccess)
             return e;
+        ctx->mh_sum = x == nullptr;
         return launch_line_mean_cols(pr, m, ctx->laFVn, ctx->laBVn, ctx->lSVn, ctx->bT, ctx->MH,
                                      ctx->MV, x, &ctx->dstat[0].flags, s);
     }
@@ -87,18 +90,20 @@ cudaError_t sweep_once(gabp_ctx *ctx, bool transposed, double *x, cudaStream_t s
         // frozen precision messages: the mean messages move, rows then columns
         const int m = ctx->lines_m, pr = ctx->prec;
         cudaError_t e;
+        ctx->mh_sum = false;
         if ((e = launch_line_mean(pr, m, ctx->laFH, ctx->laBH, ctx->lSH, ctx->bT, ctx->MV, ctx->MH,
-                                  ctx->ly, nullptr, 0, &ctx->dstat[0].flags, s)) != cudaSuccess)
+                                  ctx->ly, nullptr, 0, 0, &ctx->dstat[0].flags, s)) != cudaSuccess)
             return e;
         if ((e = launch_transpose(pr, m, ctx->MH, ctx->MHt, s)) != cudaSuccess) return e;
         if ((e = launch_line_mean(pr, m, ctx->laFV, ctx->laBV, ctx->lSV, ctx->lbT, ctx->MHt,
-                                  ctx->MVt, ctx->ly, x, 1, &ctx->dstat[0].flags, s)) != cudaSuccess)
+                                  ctx->MVt, ctx->ly, x, 1, 0, &ctx->dstat[0].flags, s)) != cudaSuccess)
             return e;
         return launch_transpose(pr, m, ctx->MVt, ctx->MV, s);
     }
     if (ctx->lines_m > 0) {
         // Algorithm 2 over the rows (natural order), then the columns (transposed order)
         const int m = ctx->lines_m, pr = ctx->prec;
+        ctx->mh_sum = false;
         unsigned *fl = &ctx->dstat[0].flags;
         cudaError_t e;
         if ((e = launch_line_phase(pr, m, lsH, luH, ctx->diagT, ctx->bT, ctx->LV,
@@ -209,6 +214,7 @@ gabp_status run_chunk(gabp_ctx *ctx, int k, bool transposed)
             ctx->graphs.push_back({k, parity, (int)transposed, frozen, exec});
         }
         CK(cudaGraphLaunch(exec, ctx->stream));
+        ctx->mh_sum = false;  // a chunk's last sweep writes the beliefs
         int per_sweep = ctx->ncolors > 0 ? ctx->ncolors : 1;
         if (ctx->lines_m > 0)
             per_sweep = !ctx->frozen ? 6 : (line_cols_natural(ctx->prec, ctx->lines_m) ? 2 : 4);

@@ -294,24 +294,33 @@ def test_line_frozen_float_natural_columns_against_oracle(g, m):
     ragged last group at 20, 45, 777, 1100; every chunk whole, the unguarded
     form, at 32, 64, 1024, 2048; one warp per CTA at 20 and 32), beyond that
     through transposes (2601, 4096).  After the precision messages froze, one
-    frozen sweep agrees on sampled lines with the oracle's full update of those
-    regions from the same state (Algorithm 2; float rounding and the freeze
-    threshold bound the difference), beliefs included."""
+    frozen sweep that writes no beliefs agrees on sampled lines with the
+    oracle's full update of those regions from the same state (Algorithm 2;
+    float rounding and the freeze threshold bound the difference); its row
+    messages, which the natural-order phases hand over as b + m', read back as
+    m'.  Then one full sweep (gabp_sweep) agrees too, beliefs included."""
     A, b = P.config_c2(m=m, seed=m)
     s = g.GabpSolver(A, "fp32", check_every=5, freeze_lambda=1)
     s.set_schedule("lines")
     _, it, _, st = s.solve(dev(b), 1e-30, 600)
     assert st == g.NOT_CONVERGED and it == 600
     s.time_sweeps(dev(b), 1, frozen=True)  # raises unless the solve froze Lambda
+    prev = {k: host(v) for k, v in s.get_line_state().items()}
+    s.time_sweeps(dev(b), 1, frozen=True)  # one frozen sweep, no beliefs written
     before = {k: host(v) for k, v in s.get_line_state().items()}
+    cols = (0, m // 2 + 3, m - 1) if m <= 2601 else (5, m - 1)
+    k = m // 3
+    lam, mu, _ = oracle.line_region_update(A, m, b, "row", k, prev["LV"], prev["MV"])
+    assert rel(_line_slice(before["MH"], m, "row", k), mu) <= 1e-4
+    for kc in cols:
+        lam, mu, _ = oracle.line_region_update(A, m, b, "col", kc, before["LH"], before["MH"])
+        assert rel(_line_slice(before["MV"], m, "col", kc), mu) <= 1e-4
     x = host(s.sweep(dev(b), 1))
     after = {k: host(v) for k, v in s.get_line_state().items()}
-    cols = (0, m // 2 + 3, m - 1) if m <= 2601 else (5, m - 1)
-    for k in cols:
-        lam, mu, xl = oracle.line_region_update(A, m, b, "col", k, after["LH"], after["MH"])
-        assert rel(_line_slice(after["MV"], m, "col", k), mu) <= 1e-4
-        assert rel(_line_slice(x, m, "col", k), xl) <= 1e-4
-    k = m // 3
+    for kc in cols:
+        lam, mu, xl = oracle.line_region_update(A, m, b, "col", kc, after["LH"], after["MH"])
+        assert rel(_line_slice(after["MV"], m, "col", kc), mu) <= 1e-4
+        assert rel(_line_slice(x, m, "col", kc), xl) <= 1e-4
     lam, mu, _ = oracle.line_region_update(A, m, b, "row", k, before["LV"], before["MV"])
     assert rel(_line_slice(after["MH"], m, "row", k), mu) <= 1e-4
     s.close()
